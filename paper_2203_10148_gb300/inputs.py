@@ -1,0 +1,285 @@
+"""Seeded synthetic workloads for PiTSBiCG (Riahi, arXiv 2203.10148).
+
+This module only *builds inputs*: grids, coefficients, initial values and the
+serving request stream.  It holds none of the method's arithmetic (no
+propagator, no block operator, no Krylov step), so both the CUDA path and the
+FP64 oracle can consume the same arrays without sharing any code that computes
+the method.
+
+Random numbers come from a counter-based SplitMix64 stream (Steele, Lea &
+Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014): output
+``i`` of a stream with key ``k`` is ``mix64(k + (i+1) * 0x9E3779B97F4A7C15)``.
+Uniforms take the top 53 bits; normals use the Box-Muller transform.  The
+generator is plain integer arithmetic, so it gives identical arrays on x86 and
+Arm hosts and across numpy versions.
+
+Workload recipes (the paper's experiments are FEM runs in FreeFem++ on
+problems of the form of eq. (9), Sec. 4; those are not reproducible here, so
+seeded finite-difference workloads of the same family stand in for them):
+
+* ``heat1d``   -- u_t = nu u_xx on (0,1), Dirichlet 0, M interior points,
+                  h = 1/(M+1); fine = implicit Euler (IE) m steps per slice,
+                  coarse = IE 1 step per slice; u0 = sin(pi x) + 0.5 sin(3 pi x)
+                  + N(0, sigma^2) noise.
+* ``heat2d``   -- u_t = nu (u_xx + u_yy) on the unit square, Dirichlet 0,
+                  n x n interior points, h = 1/(n+1); fine = RK4 m steps per
+                  slice, coarse = IE 1 step; u0 = sum of Gaussian bumps.
+* ``advdiff2d``-- u_t = nu Lap u - v . grad u on the periodic unit square,
+                  n x n points x_i = i/n; v = curl of a random stream function
+                  (8 Fourier modes) scaled to max |v| = 1; upwind advection,
+                  central diffusion; fine = RK4 with
+                  dt = min(0.4 h/|v|max, 0.2 h^2/nu); coarse = IE 1 step.
+* ``dense``    -- y' = A y, A = -(S S^T/M + 0.1 I) + 0.5 (K - K^T)/sqrt(M);
+                  fine = RK4 with ``steps`` steps per slice (applied as one
+                  precomputed dense propagator), coarse = IE 1 step.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Default seeds of the named workloads (one per configuration family).
+SEED_HEAT1D = 0x50495400
+SEED_HEAT2D = 0x50495401
+SEED_ADVDIFF2D = 0x50495402
+SEED_SERVING = 0x50495300
+SEED_DENSE = 0x50495404
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+class SeededStream:
+    """Counter-based SplitMix64 stream; ``draws`` advance a 64-bit counter."""
+
+    def __init__(self, seed: int):
+        self.key = np.uint64(int(seed) & 0xFFFFFFFFFFFFFFFF)
+        self.counter = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        idx = np.arange(self.counter + 1, self.counter + n + 1, dtype=np.uint64)
+        self.counter += n
+        with np.errstate(over="ignore"):
+            z = self.key + idx * _GAMMA
+        return _mix64(z)
+
+    def uniform(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        u = (self.u64(n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+        return lo + (hi - lo) * u
+
+    def normal(self, n: int, sigma: float = 1.0) -> np.ndarray:
+        m = (n + 1) // 2
+        u1 = 1.0 - self.uniform(m)          # (0, 1]
+        u2 = self.uniform(m)
+        r = np.sqrt(-2.0 * np.log(u1))
+        z = np.concatenate([r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)])
+        return sigma * z[:n]
+
+    def integers(self, lo: int, hi: int, n: int) -> np.ndarray:
+        """Uniform integers in the closed range [lo, hi]."""
+        u = self.uniform(n)
+        return (lo + np.floor(u * (hi - lo + 1))).astype(np.int64).clip(lo, hi)
+
+
+@dataclasses.dataclass
+class Workload:
+    """One PiT problem (or a batch of problems sharing one operator).
+
+    ``y0`` has shape (batch, M); ``M = nx * ny`` with row-major 2D states
+    (index j * nx + i, j the y index).  ``fine`` and ``coarse`` are
+    (stepper, steps per slice) with stepper in {"ie", "rk4"}.
+    """
+
+    name: str
+    kind: str
+    nx: int
+    ny: int
+    nu: float
+    T: float
+    N: int
+    fine: Tuple[str, int]
+    coarse: Tuple[str, int]
+    y0: np.ndarray
+    vx: Optional[np.ndarray] = None
+    vy: Optional[np.ndarray] = None
+    A: Optional[np.ndarray] = None
+    tol: float = 1e-6
+    precision: str = "fp64"
+    arrival: float = 0.0
+
+    @property
+    def M(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def batch(self) -> int:
+        return self.y0.shape[0]
+
+    @property
+    def dT(self) -> float:
+        return self.T / self.N
+
+    def member(self, b: int) -> "Workload":
+        return dataclasses.replace(self, y0=self.y0[b:b + 1].copy())
+
+    def describe(self) -> dict:
+        return {"workload": self.name, "kind": self.kind, "grid": [self.nx, self.ny],
+                "M": self.M, "N": self.N, "batch": self.batch, "T": self.T, "nu": self.nu,
+                "fine": list(self.fine), "coarse": list(self.coarse), "tol": self.tol,
+                "precision": self.precision}
+
+
+def heat1d(M: int = 63, nu: float = 0.1, T: float = 1.0, N: int = 16,
+           fine_steps: int = 100, coarse_steps: int = 1, noise: float = 1e-3,
+           batch: int = 1, seed: int = SEED_HEAT1D, tol: float = 1e-10) -> Workload:
+    s = SeededStream(seed)
+    x = np.arange(1, M + 1) / (M + 1.0)
+    base = np.sin(np.pi * x) + 0.5 * np.sin(3.0 * np.pi * x)
+    y0 = np.stack([base + s.normal(M, noise) for _ in range(batch)])
+    return Workload(f"heat1d_M{M}_N{N}", "heat1d", M, 1, nu, T, N, ("ie", fine_steps),
+                    ("ie", coarse_steps), y0, tol=tol, precision="fp64")
+
+
+def gaussian_bumps(s: SeededStream, n: int, count: int) -> np.ndarray:
+    """Sum of ``count`` Gaussian bumps on the n x n interior grid, h = 1/(n+1)."""
+    h = 1.0 / (n + 1)
+    xs = np.arange(1, n + 1) * h
+    X, Y = np.meshgrid(xs, xs, indexing="xy")      # X varies along columns (i)
+    a = s.uniform(count)
+    w = s.uniform(count, 0.03, 0.1)
+    c = s.uniform(2 * count, 0.2, 0.8).reshape(count, 2)
+    u = np.zeros((n, n))
+    for j in range(count):
+        r2 = (X - c[j, 0]) ** 2 + (Y - c[j, 1]) ** 2
+        u += a[j] * np.exp(-r2 / (2.0 * w[j] ** 2))
+    return u.reshape(-1)
+
+
+def heat2d(n: int = 128, nu: float = 1e-2, T: float = 1.0, N: int = 512,
+           fine_steps: int = 50, coarse_steps: int = 1, bumps: int = 8,
+           batch: int = 1, seed: int = SEED_HEAT2D, tol: float = 1e-6,
+           precision: str = "mixed") -> Workload:
+    s = SeededStream(seed)
+    y0 = np.stack([gaussian_bumps(s, n, bumps) for _ in range(batch)])
+    return Workload(f"heat2d_{n}x{n}_N{N}", "heat2d", n, n, nu, T, N, ("rk4", fine_steps),
+                    ("ie", coarse_steps), y0, tol=tol, precision=precision)
+
+
+def _integer_modes(s: SeededStream, count: int, kmax: int) -> np.ndarray:
+    out = []
+    while len(out) < count:
+        k = s.integers(-kmax, kmax, 2)
+        if k[0] != 0 or k[1] != 0:
+            out.append(k)
+    return np.array(out, dtype=np.float64)
+
+
+def advdiff2d_rk4_steps(n: int, nu: float, dT: float, vmax: float = 1.0) -> int:
+    """RK4 steps per slice: dt = min(0.4 h/|v|max, 0.2 h^2/nu), h = 1/n."""
+    h = 1.0 / n
+    dt = min(0.4 * h / vmax, 0.2 * h * h / nu)
+    return int(math.ceil(dT / dt - 1e-12))
+
+
+def advdiff2d(n: int = 512, nu: float = 5e-3, T: float = 0.5, N: int = 256,
+              fine_steps: Optional[int] = None, coarse_steps: int = 1,
+              psi_modes: int = 8, u_modes: int = 16, batch: int = 1,
+              seed: int = SEED_ADVDIFF2D, tol: float = 1e-6,
+              precision: str = "mixed") -> Workload:
+    s = SeededStream(seed)
+    xs = np.arange(n) / float(n)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    k = _integer_modes(s, psi_modes, 4)
+    a = s.normal(psi_modes)
+    phi = s.uniform(psi_modes, 0.0, 2.0 * np.pi)
+    dpsi_dx = np.zeros((n, n))
+    dpsi_dy = np.zeros((n, n))
+    for j in range(psi_modes):
+        arg = 2.0 * np.pi * (k[j, 0] * X + k[j, 1] * Y) + phi[j]
+        dpsi_dx += a[j] * 2.0 * np.pi * k[j, 0] * np.cos(arg)
+        dpsi_dy += a[j] * 2.0 * np.pi * k[j, 1] * np.cos(arg)
+    vx, vy = dpsi_dy, -dpsi_dx
+    scale = 1.0 / np.max(np.sqrt(vx * vx + vy * vy))
+    vx, vy = vx * scale, vy * scale
+    y0s = []
+    for _ in range(batch):
+        kk = _integer_modes(s, u_modes, 4)
+        b = s.normal(u_modes)
+        th = s.uniform(u_modes, 0.0, 2.0 * np.pi)
+        u = np.zeros((n, n))
+        for j in range(u_modes):
+            u += b[j] * np.cos(2.0 * np.pi * (kk[j, 0] * X + kk[j, 1] * Y) + th[j]) / np.hypot(*kk[j])
+        y0s.append(u.reshape(-1))
+    if fine_steps is None:
+        fine_steps = advdiff2d_rk4_steps(n, nu, T / N)
+    return Workload(f"advdiff2d_{n}x{n}_N{N}", "advdiff2d", n, n, nu, T, N, ("rk4", fine_steps),
+                    ("ie", coarse_steps), np.stack(y0s), vx=vx.reshape(-1).copy(),
+                    vy=vy.reshape(-1).copy(), tol=tol, precision=precision)
+
+
+def dense(M: int = 1024, T: float = 10.0, N: int = 4096, fine_steps: int = 200,
+          coarse_steps: int = 1, batch: int = 1, seed: int = SEED_DENSE,
+          tol: float = 1e-6, precision: str = "mixed") -> Workload:
+    s = SeededStream(seed)
+    S = s.normal(M * M).reshape(M, M)
+    K = s.normal(M * M).reshape(M, M)
+    A = -(S @ S.T / M + 0.1 * np.eye(M)) + 0.5 * (K - K.T) / math.sqrt(M)
+    y0 = np.stack([s.normal(M) for _ in range(batch)])
+    return Workload(f"dense_M{M}_N{N}", "dense", M, 1, 0.0, T, N, ("rk4", fine_steps),
+                    ("ie", coarse_steps), y0, A=A, tol=tol, precision=precision)
+
+
+def serving_request(j: int, rate: float = 200.0, seed: int = SEED_SERVING,
+                    m1d: Tuple[int, int] = (63, 4095), n2d: Tuple[int, int] = (32, 256),
+                    nslices: Tuple[int, int] = (16, 1024),
+                    nu_range: Tuple[float, float] = (1e-3, 1e-1)) -> Tuple[float, Workload]:
+    """Request ``j`` of the serving stream: (inter-arrival gap in s, workload).
+
+    Half the requests are 1D heat (IE fine, 100 steps per slice), half 2D heat
+    (RK4 fine, m = max(50, ceil(dT nu / (0.2 h^2)))); T = 1; coarse = IE 1 step.
+    """
+    s = SeededStream(seed + j)
+    gap = -math.log(1.0 - float(s.uniform(1)[0])) / rate
+    is2d = bool(s.uniform(1)[0] >= 0.5)
+    N = int(s.integers(nslices[0], nslices[1], 1)[0])
+    nu = float(math.exp(s.uniform(1, math.log(nu_range[0]), math.log(nu_range[1]))[0]))
+    if not is2d:
+        M = int(s.integers(m1d[0], m1d[1], 1)[0])
+        x = np.arange(1, M + 1) / (M + 1.0)
+        kk = s.integers(1, 8, 4)
+        a = s.normal(4)
+        u = sum(a[i] / kk[i] * np.sin(kk[i] * np.pi * x) for i in range(4))
+        w = Workload(f"req{j}_heat1d_M{M}_N{N}", "heat1d", M, 1, nu, 1.0, N, ("ie", 100),
+                     ("ie", 1), u[None, :].copy(), tol=1e-6, precision="mixed")
+    else:
+        n = int(s.integers(n2d[0], n2d[1], 1)[0])
+        h = 1.0 / (n + 1)
+        m = max(50, int(math.ceil((1.0 / N) * nu / (0.2 * h * h))))
+        u = gaussian_bumps(s, n, 4)
+        w = Workload(f"req{j}_heat2d_{n}x{n}_N{N}", "heat2d", n, n, nu, 1.0, N, ("rk4", m),
+                     ("ie", 1), u[None, :].copy(), tol=1e-6, precision="mixed")
+    return gap, w
+
+
+def serving_stream(count: int = 4096, rate: float = 200.0, seed: int = SEED_SERVING,
+                   **kw) -> List[Workload]:
+    """Poisson request stream; each workload's ``arrival`` is its arrival time (s)."""
+    t = 0.0
+    out = []
+    for j in range(count):
+        gap, w = serving_request(j, rate, seed, **kw)
+        t += gap
+        w.arrival = t
+        out.append(w)
+    return out
