@@ -1,0 +1,228 @@
+/*
+ * pit.h -- C ABI of libpit: the parallel-in-time hot path of PiTSBiCG
+ * (Riahi, "PiTSBiCG: Parallel in Time Stable Bi-Conjugate Gradient
+ * Algorithm", arXiv 2203.10148) on NVIDIA GB300 (sm_103a).
+ *
+ * The problem (Sec. 2, eqs. (1)-(2)): a linear ODE or semi-discrete PDE
+ * y' = L y on [0, T] with y(0) = y0, cut into N equal slices of length
+ * dT = T/N.  A fine propagator F and a coarse propagator G advance a state
+ * over one slice.  The unknown is Lambda = (lambda_0, ..., lambda_N), the
+ * states at the slice boundaries (N+1 blocks of M values).  The all-at-once
+ * system of eq. (4) is  F Lambda = B  with (F Lambda)_0 = lambda_0,
+ * (F Lambda)_n = lambda_n - F(lambda_{n-1}) and B = (y0, 0, ..., 0); its
+ * exact solution is the serial fine trajectory lambda_n = F^n y0.
+ * PiTSBiCG (Algorithm 1) runs BiCGStab on the left-preconditioned system
+ * G^{-1} F Lambda = G^{-1} B of eq. (8), where G^{-1} is the forward
+ * substitution of eq. (7), right.
+ *
+ * Conventions for every call:
+ *   - Every call returns a pit_status; PIT_OK (0) on success, a negative
+ *     code on error.  No call aborts or exits the process.
+ *     pit_last_error() returns a message for the calling thread's last error.
+ *   - A "block vector" holds batch * (N+1) * M doubles, member-major, then
+ *     slice-major: element (b, n, i) is at index (b*(N+1) + n)*M + i.
+ *     2D states are row-major: point (i, j) of an nx-by-ny grid is i + j*nx.
+ *   - on_device = 1: the pointer is CUDA device memory (for instance a torch
+ *     tensor's data_ptr) on the current device; on_device = 0: host memory.
+ *     Caller-owned arrays are never retained after a call returns.
+ *   - stream: a cudaStream_t cast to void*, or NULL for the problem's own
+ *     stream.  Calls taking a stream are asynchronous with respect to the
+ *     host when on_device = 1 unless stated otherwise.
+ *   - Calls on one problem must be serialised by the caller.
+ */
+#ifndef PIT_H
+#define PIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pit_status;
+
+#define PIT_OK              0
+#define PIT_PENDING         1   /* serving: the request has not finished yet */
+#define PIT_E_INVALID      -1   /* bad argument or descriptor */
+#define PIT_E_NOMEM        -2   /* device or host allocation failed / over budget */
+#define PIT_E_CUDA         -3   /* a CUDA runtime call failed */
+#define PIT_E_BREAKDOWN    -4   /* BiCGStab breakdown: <D,R~> vanished twice, or omega = 0 */
+#define PIT_E_MAXITER      -5   /* iteration limit reached before the tolerance */
+#define PIT_E_NONFINITE    -6   /* NaN or Inf in an input or a Krylov scalar */
+#define PIT_E_TIMEOUT      -7   /* a bounded device-side wait expired */
+#define PIT_E_BUSY         -8   /* serving: no free slot and the queue is full */
+#define PIT_E_UNSUPPORTED  -9   /* valid but not implemented combination */
+
+/* Spatial operator families (the operator L of eq. (1), f = 0). */
+#define PIT_OP_HEAT1D       1   /* nu u_xx, Dirichlet 0, nx interior points, h = 1/(nx+1) */
+#define PIT_OP_HEAT2D       2   /* nu (u_xx + u_yy), 5-point, Dirichlet 0, nx = ny interior, h = 1/(n+1) */
+#define PIT_OP_ADVDIFF2D    3   /* nu Lap u - v.grad u, periodic nx x ny, h = 1/nx, upwind advection */
+#define PIT_OP_DENSE        4   /* y' = A y with a dense M x M matrix A */
+
+/* Time steppers over one slice (fine F and coarse G). */
+#define PIT_STEP_IE         1   /* implicit Euler: (I - dt L) u+ = u, dt = dT/steps */
+#define PIT_STEP_RK4        2   /* classical RK4, dt = dT/steps; for PIT_OP_DENSE the
+                                   fine RK4 propagator R(dt A)^steps is precomputed once
+                                   and applied to all slices as one GEMM */
+
+/* Arithmetic of the fine propagator. */
+#define PIT_FP64            0   /* FP64 throughout */
+#define PIT_MIXED           1   /* FP32 fine stepping (split-precision tensor-core GEMM for
+                                   PIT_OP_DENSE), FP64 Krylov vectors and scalars, FP64
+                                   true residuals with iterative refinement */
+
+/* pit_apply_operator: which operator. */
+#define PIT_APPLY_F         1   /* y = F x, the block operator of eq. (4) */
+#define PIT_APPLY_GINV      2   /* y = G^{-1} x, the forward substitution of eq. (7), right */
+#define PIT_APPLY_GINV_F    3   /* y = G^{-1} F x, the preconditioned operator of eq. (8) */
+#define PIT_APPLY_RESIDUAL  4   /* y = G^{-1}(B - F x), Algorithm 1, first line */
+
+/* Initial guess X^0 of Algorithm 1. */
+#define PIT_X0_COARSE       0   /* G^{-1} B: lambda_n = G^n y0 (the parareal predictor) */
+#define PIT_X0_ZERO         1
+#define PIT_X0_GIVEN        2   /* X holds the initial guess on entry */
+
+typedef struct pit_problem_s *pit_problem_t;
+typedef struct pit_server_s *pit_server_t;
+
+typedef struct {
+    int kind;              /* PIT_OP_* */
+    int nx, ny;            /* grid; HEAT1D and DENSE: nx = M, ny = 1 */
+    double nu;             /* diffusion coefficient (unused for DENSE) */
+    const double *vx;      /* ADVDIFF2D: host arrays of nx*ny velocities; copied at create */
+    const double *vy;
+    const double *A;       /* DENSE: host M*M row-major matrix; copied at create */
+} pit_operator_desc;
+
+typedef struct {
+    int kind;              /* PIT_STEP_* */
+    int steps;             /* steps per slice, >= 1 */
+} pit_stepper_desc;
+
+typedef struct {
+    pit_operator_desc op;
+    const double *y0;      /* host, batch * M initial values; copied at create */
+    int batch;             /* independent initial values sharing the operator, >= 1 */
+    double T;              /* end time, > 0 */
+    int N;                 /* number of time slices, >= 1 */
+    pit_stepper_desc fine;
+    pit_stepper_desc coarse;
+    int precision;         /* PIT_FP64 or PIT_MIXED */
+} pit_problem_desc;
+
+typedef struct {
+    double tol;            /* stop when ||R^k||_{N,inf} <= tol * ||R^0||_{N,inf} */
+    double restart_eps0;   /* restart when |<R^{k+1},R~>| <= eps0 ||R^{k+1}||_2 ||R~||_2 */
+    int max_iter;          /* BiCGStab iterations (per refinement round in PIT_MIXED) */
+    int x0_mode;           /* PIT_X0_* */
+    int refine_max;        /* PIT_MIXED: outer refinement rounds, >= 1 */
+    double inner_tol;      /* PIT_MIXED: relative tolerance of each inner solve */
+    void *stream;          /* cudaStream_t or NULL */
+    double *history;       /* optional host array: ||R^k||_{N,inf} of member 0 per
+                              iteration (PIT_FP64) or per refinement round (PIT_MIXED) */
+    int history_len;
+} pit_solve_opts;
+
+typedef struct {
+    int iterations;        /* BiCGStab iterations (summed over refinement rounds) */
+    int matvecs;           /* applications of G^{-1} F (FP32 and FP64) */
+    int restarts;
+    int refinements;       /* PIT_MIXED: outer rounds taken */
+    long long fine_slice_steps;  /* slices propagated x fine steps per slice */
+    double r0;             /* ||R^0||_{N,inf} */
+    double precond_resid;  /* final ||R||_{N,inf}: recursive (FP64) or true (PIT_MIXED) */
+    double seconds;        /* wall time of the call */
+    int status;            /* pit_status of this member */
+    int history_count;     /* entries written to opts->history */
+} pit_solve_info;
+
+/* Fills *opts with defaults: tol 1e-10, eps0 1e-8, max_iter 500, X0 coarse,
+ * refine_max 8, inner_tol 1e-4, default stream, no history. */
+void pit_default_opts(pit_solve_opts *opts);
+
+/* Version string of the library. */
+const char *pit_version(void);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to n bytes); returns the length of the full message. */
+size_t pit_last_error(char *buf, size_t n);
+
+/*
+ * Creates a problem on the current CUDA device (Sec. 2, eqs. (1)-(4)).
+ * Copies y0, A, vx, vy into library-owned device memory (the caller may free
+ * its arrays on return) and runs the set-up: stepper factorisations, the
+ * sine-basis tables of the 2D heat coarse solver, or the dense propagator
+ * R(dt A)^steps and G = (I - dT A)^{-1} for PIT_OP_DENSE.
+ * Supported: HEAT1D with IE or RK4 fine and IE coarse; HEAT2D (nx = ny) with
+ * RK4 fine and IE coarse; ADVDIFF2D with RK4 fine and IE coarse; DENSE with
+ * RK4 fine and IE coarse.  Others return PIT_E_UNSUPPORTED.
+ * Errors: PIT_E_INVALID (bad sizes, non-finite values), PIT_E_NOMEM, PIT_E_CUDA.
+ */
+pit_status pit_problem_create(const pit_problem_desc *desc, pit_problem_t *out);
+
+/* Frees every resource of the problem.  NULL is accepted. */
+pit_status pit_problem_destroy(pit_problem_t prob);
+
+/* Sizes of a problem: M values per state, N slices, batch members. */
+pit_status pit_problem_shape(pit_problem_t prob, int *M, int *N, int *batch);
+
+/*
+ * Applies one operator to a block vector x, writing y (both batch*(N+1)*M):
+ * PIT_APPLY_F (eq. (4)), PIT_APPLY_GINV (eq. (7) right, sequential in n),
+ * PIT_APPLY_GINV_F (eq. (8)), PIT_APPLY_RESIDUAL (G^{-1}(B - F x)).
+ * precision selects the fine arithmetic (PIT_FP64 or PIT_MIXED = FP32 fine
+ * stepping from FP64 inputs); G^{-1} is FP64 for PIT_FP64 and FP32
+ * transforms with FP64 accumulation for PIT_MIXED.  x and y may not overlap.
+ * With on_device = 0 the call copies through device memory and synchronises.
+ */
+pit_status pit_apply_operator(pit_problem_t prob, int which, int precision,
+                              const double *x, double *y, int on_device, void *stream);
+
+/*
+ * The serial fine trajectory lambda_n = F^n y0 (eq. (7), left: F^{-1} B),
+ * computed on the device one slice after the other in the given precision.
+ * Lam holds batch*(N+1)*M values.  Synchronous.
+ */
+pit_status pit_serial_fine(pit_problem_t prob, int precision, double *Lam, int on_device);
+
+/*
+ * PiTSBiCG (Algorithm 1) on G^{-1} F X = G^{-1} B for every batch member.
+ * X (batch*(N+1)*M): initial guess on entry when x0_mode = PIT_X0_GIVEN,
+ * the solution on return.  info: array of batch entries (may be NULL).
+ * PIT_FP64: every step in FP64 on the device.  PIT_MIXED: iterative
+ * refinement: FP64 true residual G^{-1}(B - F64 X), an FP32-fine / FP64-Krylov
+ * inner solve of the correction to inner_tol, X += correction, until the
+ * true preconditioned residual is <= tol * its initial value.
+ * Synchronous.  Returns the worst member status (PIT_E_MAXITER,
+ * PIT_E_BREAKDOWN, PIT_E_NONFINITE) or PIT_OK.
+ */
+pit_status pit_bicgstab_solve(pit_problem_t prob, const pit_solve_opts *opts, double *X,
+                              int on_device, pit_solve_info *info);
+
+/*
+ * Parareal in the algebraic form of eq. (6):
+ * X^{k+1} = X^k + G^{-1}(B - F X^k), X^0 = G^{-1} B, in the problem's fine
+ * precision (FP64 true residual in PIT_FP64), stopping when the preconditioned
+ * residual is <= tol * its initial value or after kmax corrections.
+ * Synchronous.
+ */
+pit_status pit_parareal_solve(pit_problem_t prob, int kmax, double tol, double *X,
+                              int on_device, pit_solve_info *info);
+
+/*
+ * Deterministic block reductions used by the Krylov kernels, exposed for
+ * testing: for block vectors U, V of nblocks blocks of M values,
+ * *dot = sum of U.V over all entries (the block inner product, Sec. 3 text
+ * after Algorithm 1), norms[n] = ||U_n||_2, *norm_inf = max_n norms[n]
+ * (the ||.||_{N,inf} of Algorithm 1).  Device pointers; synchronous.
+ * norms may be NULL.
+ */
+pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M,
+                            double *dot, double *norms, double *norm_inf);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIT_H */

@@ -1,0 +1,660 @@
+// C-ABI entry points of libpit and the solver engine: PiTSBiCG (Algorithm 1,
+// Sec. 3) and parareal (eq. (6), Sec. 2) driven from the host with every
+// vector operation and every Krylov scalar on the device.  The host reads a
+// few bytes of per-member state once per iteration to decide whether any
+// member is still iterating.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "pit_internal.h"
+
+namespace pit {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e),
+             what, file, line);
+    set_error(buf);
+    if (e == cudaErrorMemoryAllocation) return PIT_E_NOMEM;
+    return PIT_E_CUDA;
+}
+
+pit_status DevBuf::ensure(size_t n) {
+    if (n <= bytes && ptr) return PIT_OK;
+    release();
+    if (n == 0) return PIT_OK;
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        (void)cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof buf, "device allocation of %zu bytes failed: %s", n,
+                 cudaGetErrorString(e));
+        set_error(buf);
+        return PIT_E_NOMEM;
+    }
+    bytes = n;
+    return PIT_OK;
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+// --------------------------------------------------------- operator switch
+pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                      const MemberState *st, cudaStream_t s) {
+    switch (p->kind) {
+    case PIT_OP_HEAT1D: return heat1d_apply_F(p, x, y, mode, prec, st, s);
+    case PIT_OP_HEAT2D: return heat2d_apply_F(p, x, y, mode, prec, st, s);
+    case PIT_OP_ADVDIFF2D: return advdiff_apply_F(p, x, y, mode, prec, st, s);
+    case PIT_OP_DENSE: return dense_apply_F(p, x, y, mode, prec, st, s);
+    }
+    set_error("unknown operator kind");
+    return PIT_E_INVALID;
+}
+
+pit_status op_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
+                    cudaStream_t s) {
+    switch (p->kind) {
+    case PIT_OP_HEAT1D: return heat1d_sweep(p, q, z, prec, st, s);
+    case PIT_OP_HEAT2D: return heat2d_sweep(p, q, z, prec, st, s);
+    case PIT_OP_ADVDIFF2D: return advdiff_sweep(p, q, z, prec, st, s);
+    case PIT_OP_DENSE: return dense_sweep(p, q, z, prec, st, s);
+    }
+    set_error("unknown operator kind");
+    return PIT_E_INVALID;
+}
+
+static pit_status fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
+    switch (p->kind) {
+    case PIT_OP_HEAT1D: return heat1d_fine_one(p, x, y, prec, s);
+    case PIT_OP_HEAT2D: return heat2d_fine_one(p, x, y, prec, s);
+    case PIT_OP_ADVDIFF2D: return advdiff_fine_one(p, x, y, prec, s);
+    case PIT_OP_DENSE: return dense_fine_one(p, x, y, prec, s);
+    }
+    set_error("unknown operator kind");
+    return PIT_E_INVALID;
+}
+
+// y = B for every member: block 0 = y0, other blocks 0.
+pit_status build_rhs(Problem *p, double *B, cudaStream_t s) {
+    PIT_CUDA(cudaMemsetAsync(B, 0, p->vlen * sizeof(double), s));
+    PIT_CUDA(cudaMemcpy2DAsync(B, p->blen * sizeof(double), p->y0.ptr, p->M * sizeof(double),
+                               p->M * sizeof(double), p->batch, cudaMemcpyDeviceToDevice, s));
+    return PIT_OK;
+}
+
+pit_status op_serial(Problem *p, double *Lam, int prec, cudaStream_t s) {
+    PIT_TRY(build_rhs(p, Lam, s));
+    for (int n = 1; n <= p->N; ++n)
+        PIT_TRY(fine_one(p, Lam + (size_t)(n - 1) * p->M, Lam + (size_t)n * p->M, prec, s));
+    return PIT_OK;
+}
+
+// Sweep arithmetic: FP64 for FP64, FP32 transforms / FP64 running sums otherwise.
+static int sweep_prec(int prec) { return prec == PIT_FP64 ? PIT_FP64 : PIT_MIXED; }
+
+static pit_status apply_GinvF(Problem *p, const double *x, double *y, int prec,
+                              const MemberState *st, cudaStream_t s) {
+    PIT_TRY(op_apply_F(p, x, y, FINE_APPLY, prec, st, s));
+    return op_sweep(p, y, y, sweep_prec(prec), st, s);
+}
+
+// ------------------------------------------------------------ the engine
+namespace {
+
+struct HostStates {
+    std::vector<MemberState> v;
+    MemberState *pinned = nullptr;
+    int batch = 0;
+    pit_status init(int b) {
+        batch = b;
+        v.resize(b);
+        PIT_CUDA(cudaMallocHost(&pinned, sizeof(MemberState) * b));
+        return PIT_OK;
+    }
+    ~HostStates() {
+        if (pinned) cudaFreeHost(pinned);
+    }
+    pit_status fetch(Problem *p, cudaStream_t s) {
+        PIT_CUDA(cudaMemcpyAsync(pinned, p->states.ptr, sizeof(MemberState) * batch,
+                                 cudaMemcpyDeviceToHost, s));
+        PIT_CUDA(cudaStreamSynchronize(s));
+        std::copy(pinned, pinned + batch, v.begin());
+        return PIT_OK;
+    }
+    bool any_active() const {
+        for (const auto &m : v)
+            if (m.active) return true;
+        return false;
+    }
+};
+
+struct LoopOut {
+    std::vector<MemberState> final_states;
+    int history_count = 0;
+};
+
+// Algorithm 1 on the workspace: X holds X^0.  If r_given, R already holds
+// R^0 (inner solves of the refinement); otherwise R^0 = G^{-1}(B - F X^0) is
+// computed here in precision `prec`.
+pit_status run_bicgstab(Problem *p, int prec, double tol_rel, double abs_thresh, double eps0,
+                        int max_iter, bool r_given, cudaStream_t s, double *history,
+                        int history_len, int history_offset, LoopOut &out) {
+    double *X = p->X.as<double>(), *R = p->R.as<double>();
+    MemberState *st = p->states.as<MemberState>();
+    if (!r_given) {
+        PIT_TRY(op_apply_F(p, X, R, FINE_RESIDUAL, prec, nullptr, s));
+        PIT_TRY(op_sweep(p, R, R, sweep_prec(prec), nullptr, s));
+    }
+    PIT_TRY(kr_init(p, tol_rel, abs_thresh, eps0, max_iter, s));
+    HostStates hs;
+    PIT_TRY(hs.init(p->batch));
+    int hc = history_offset;
+    int last_iter = -1;
+    // iteration guard: every member stops by max_iter, plus one restart per iteration
+    const long guard = 2L * (max_iter + 2) + 4;
+    for (long it = 0; it < guard; ++it) {
+        PIT_TRY(hs.fetch(p, s));
+        if (history && hc < history_len && hs.v[0].iter != last_iter) {
+            history[hc++] = hs.v[0].rnorm;       // ||R^k||_{N,inf} of member 0
+            last_iter = hs.v[0].iter;
+        }
+        if (!hs.any_active()) break;
+        PIT_TRY(apply_GinvF(p, p->P.as<double>(), p->D.as<double>(), prec, st, s));   // D = G^-1 F P
+        PIT_TRY(kr_sigma(p, s));                                                      // alpha
+        PIT_TRY(kr_update_S(p, s));                                                   // S = R - alpha D
+        PIT_TRY(apply_GinvF(p, p->S.as<double>(), p->K.as<double>(), prec, st, s));   // K = G^-1 F S
+        PIT_TRY(kr_omega(p, s));                                                      // omega
+        PIT_TRY(kr_update_XR(p, s));                                                  // X, R, beta
+        PIT_TRY(kr_update_P(p, s));                                                   // P
+    }
+    PIT_TRY(hs.fetch(p, s));
+    out.final_states = hs.v;
+    out.history_count = hc - history_offset;
+    return PIT_OK;
+}
+
+// Copies between a caller block vector and a device buffer.
+pit_status to_device(Problem *p, double *dst, const double *src, int on_device, cudaStream_t s) {
+    PIT_CUDA(cudaMemcpyAsync(dst, src, p->vlen * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return PIT_OK;
+}
+pit_status from_device(Problem *p, double *dst, const double *src, int on_device, cudaStream_t s) {
+    PIT_CUDA(cudaMemcpyAsync(dst, src, p->vlen * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    return PIT_OK;
+}
+
+bool all_finite(const double *v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+int worst_status(const std::vector<int> &st) {
+    int w = PIT_OK;
+    for (int s : st) {
+        if (s == PIT_E_NONFINITE) return s;
+        if (s == PIT_E_BREAKDOWN) w = s;
+        else if (s == PIT_E_MAXITER && w == PIT_OK) w = s;
+    }
+    return w;
+}
+
+// Per-member ||U||_{N,inf} on the host.
+pit_status member_norms(Problem *p, const double *U, std::vector<double> &out, cudaStream_t s) {
+    double *d = p->fine_tmp.as<double>();
+    PIT_TRY(kr_block_norm(p, U, d, s));
+    out.resize(p->batch);
+    PIT_CUDA(cudaMemcpyAsync(out.data(), d, sizeof(double) * p->batch, cudaMemcpyDeviceToHost, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
+    return PIT_OK;
+}
+
+}  // namespace
+}  // namespace pit
+
+using namespace pit;
+
+// ================================================================== C ABI
+extern "C" {
+
+void pit_default_opts(pit_solve_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->tol = 1e-10;
+    o->restart_eps0 = 1e-8;
+    o->max_iter = 500;
+    o->x0_mode = PIT_X0_COARSE;
+    o->refine_max = 8;
+    o->inner_tol = 1e-4;
+}
+
+const char *pit_version(void) { return "libpit 0.1 (sm_103a)"; }
+
+size_t pit_last_error(char *buf, size_t n) {
+    const std::string &e = g_last_error;
+    if (buf && n) {
+        const size_t k = std::min(n - 1, e.size());
+        memcpy(buf, e.data(), k);
+        buf[k] = 0;
+    }
+    return e.size();
+}
+
+pit_status pit_problem_create(const pit_problem_desc *d, pit_problem_t *out) {
+    if (!d || !out) {
+        set_error("pit_problem_create: null argument");
+        return PIT_E_INVALID;
+    }
+    *out = nullptr;
+    const pit_operator_desc &op = d->op;
+    if (op.kind < PIT_OP_HEAT1D || op.kind > PIT_OP_DENSE) {
+        set_error("pit_problem_create: unknown operator kind");
+        return PIT_E_INVALID;
+    }
+    if (op.nx < 1 || op.ny < 1 || d->N < 1 || d->batch < 1 || !(d->T > 0.0) ||
+        d->fine.steps < 1 || d->coarse.steps < 1 || !d->y0 ||
+        (d->precision != PIT_FP64 && d->precision != PIT_MIXED)) {
+        set_error("pit_problem_create: invalid sizes, steps, T, precision or null y0");
+        return PIT_E_INVALID;
+    }
+    if ((op.kind == PIT_OP_HEAT1D || op.kind == PIT_OP_DENSE) && op.ny != 1) {
+        set_error("pit_problem_create: HEAT1D and DENSE need ny = 1");
+        return PIT_E_INVALID;
+    }
+    if (op.kind == PIT_OP_ADVDIFF2D && (!op.vx || !op.vy)) {
+        set_error("pit_problem_create: ADVDIFF2D needs vx and vy");
+        return PIT_E_INVALID;
+    }
+    if (op.kind == PIT_OP_DENSE && !op.A) {
+        set_error("pit_problem_create: DENSE needs A");
+        return PIT_E_INVALID;
+    }
+    if (op.kind != PIT_OP_DENSE && !(op.nu >= 0.0 && std::isfinite(op.nu))) {
+        set_error("pit_problem_create: nu must be finite and >= 0");
+        return PIT_E_INVALID;
+    }
+    const size_t M = (size_t)op.nx * op.ny;
+    if (!all_finite(d->y0, M * d->batch) ||
+        (op.kind == PIT_OP_DENSE && !all_finite(op.A, M * M)) ||
+        (op.kind == PIT_OP_ADVDIFF2D && (!all_finite(op.vx, M) || !all_finite(op.vy, M)))) {
+        set_error("pit_problem_create: non-finite value in y0, A or v");
+        return PIT_E_NONFINITE;
+    }
+    pit_problem_s *h = new (std::nothrow) pit_problem_s();
+    if (!h) {
+        set_error("pit_problem_create: host allocation failed");
+        return PIT_E_NOMEM;
+    }
+    Problem *p = &h->p;
+    p->kind = op.kind;
+    p->nx = op.nx;
+    p->ny = op.ny;
+    p->M = (int)M;
+    p->N = d->N;
+    p->batch = d->batch;
+    p->T = d->T;
+    p->dT = d->T / d->N;
+    p->nu = op.nu;
+    p->fine_kind = d->fine.kind;
+    p->fine_steps = d->fine.steps;
+    p->coarse_kind = d->coarse.kind;
+    p->coarse_steps = d->coarse.steps;
+    p->precision = d->precision;
+    p->blen = (size_t)(p->N + 1) * M;
+    p->vlen = p->blen * p->batch;
+    pit_status s = PIT_OK;
+    auto fail = [&](pit_status e) {
+        pit_problem_destroy(h);
+        return e;
+    };
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__));
+    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamDefault);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__));
+    if ((s = p->y0.ensure(M * d->batch * sizeof(double))) != PIT_OK) return fail(s);
+    e = cudaMemcpy(p->y0.ptr, d->y0, M * d->batch * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "copy y0", __FILE__, __LINE__));
+    if ((s = p->fine_tmp.ensure(std::max<size_t>(4096, 64 * (size_t)d->batch))) != PIT_OK)
+        return fail(s);
+    switch (p->kind) {
+    case PIT_OP_HEAT1D: s = heat1d_setup(p); break;
+    case PIT_OP_HEAT2D: s = heat2d_setup(p); break;
+    case PIT_OP_ADVDIFF2D: {
+        if ((s = p->vx64.ensure(M * sizeof(double))) != PIT_OK) return fail(s);
+        if ((s = p->vy64.ensure(M * sizeof(double))) != PIT_OK) return fail(s);
+        e = cudaMemcpy(p->vx64.ptr, op.vx, M * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->vy64.ptr, op.vy, M * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "copy v", __FILE__, __LINE__));
+        s = advdiff_setup(p);
+        break;
+    }
+    case PIT_OP_DENSE: {
+        if ((s = p->PhiF64.ensure(M * M * sizeof(double))) != PIT_OK) return fail(s);
+        // A is staged in PhiF64; dense_setup replaces it by the propagator
+        e = cudaMemcpy(p->PhiF64.ptr, op.A, M * M * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "copy A", __FILE__, __LINE__));
+        s = dense_setup(p);
+        break;
+    }
+    }
+    if (s != PIT_OK) return fail(s);
+    e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "setup", __FILE__, __LINE__));
+    *out = h;
+    return PIT_OK;
+}
+
+pit_status pit_problem_destroy(pit_problem_t h) {
+    if (!h) return PIT_OK;
+    Problem *p = &h->p;
+    cudaSetDevice(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    DevBuf *bufs[] = {&p->y0, &p->fine_inv64, &p->fine_cp64, &p->coarse_inv64, &p->coarse_cp64,
+                      &p->fine_inv32, &p->fine_cp32, &p->coarse_inv32, &p->coarse_cp32,
+                      &p->S64, &p->S32, &p->gmode, &p->hat, &p->vx64, &p->vy64, &p->vx32,
+                      &p->vy32, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
+                      &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
+                      &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
+                      &p->flags_host_mirror, &p->fine_tmp};
+    for (DevBuf *b : bufs) b->release();
+    if (p->stream) cudaStreamDestroy(p->stream);
+    delete h;
+    return PIT_OK;
+}
+
+pit_status pit_problem_shape(pit_problem_t h, int *M, int *N, int *batch) {
+    if (!h) {
+        set_error("pit_problem_shape: null problem");
+        return PIT_E_INVALID;
+    }
+    if (M) *M = h->p.M;
+    if (N) *N = h->p.N;
+    if (batch) *batch = h->p.batch;
+    return PIT_OK;
+}
+
+pit_status pit_apply_operator(pit_problem_t h, int which, int precision, const double *x,
+                              double *y, int on_device, void *stream) {
+    if (!h || !x || !y) {
+        set_error("pit_apply_operator: null argument");
+        return PIT_E_INVALID;
+    }
+    if (which < PIT_APPLY_F || which > PIT_APPLY_RESIDUAL ||
+        (precision != PIT_FP64 && precision != PIT_MIXED)) {
+        set_error("pit_apply_operator: bad operator or precision");
+        return PIT_E_INVALID;
+    }
+    Problem *p = &h->p;
+    PIT_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : p->stream;
+    const double *dx = x;
+    double *dy = y;
+    if (!on_device) {
+        PIT_TRY(p->X.ensure(p->vlen * sizeof(double)));
+        PIT_TRY(p->W.ensure(p->vlen * sizeof(double)));
+        PIT_TRY(to_device(p, p->X.as<double>(), x, 0, s));
+        dx = p->X.as<double>();
+        dy = p->W.as<double>();
+    }
+    switch (which) {
+    case PIT_APPLY_F: PIT_TRY(op_apply_F(p, dx, dy, FINE_APPLY, precision, nullptr, s)); break;
+    case PIT_APPLY_GINV: PIT_TRY(op_sweep(p, dx, dy, sweep_prec(precision), nullptr, s)); break;
+    case PIT_APPLY_GINV_F: PIT_TRY(apply_GinvF(p, dx, dy, precision, nullptr, s)); break;
+    case PIT_APPLY_RESIDUAL:
+        PIT_TRY(op_apply_F(p, dx, dy, FINE_RESIDUAL, precision, nullptr, s));
+        PIT_TRY(op_sweep(p, dy, dy, sweep_prec(precision), nullptr, s));
+        break;
+    }
+    if (!on_device) {
+        PIT_TRY(from_device(p, y, dy, 0, s));
+        PIT_CUDA(cudaStreamSynchronize(s));
+    }
+    return PIT_OK;
+}
+
+pit_status pit_serial_fine(pit_problem_t h, int precision, double *Lam, int on_device) {
+    if (!h || !Lam || (precision != PIT_FP64 && precision != PIT_MIXED)) {
+        set_error("pit_serial_fine: bad argument");
+        return PIT_E_INVALID;
+    }
+    Problem *p = &h->p;
+    PIT_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = p->stream;
+    double *d = Lam;
+    if (!on_device) {
+        PIT_TRY(p->W.ensure(p->vlen * sizeof(double)));
+        d = p->W.as<double>();
+    }
+    PIT_TRY(op_serial(p, d, precision, s));
+    if (!on_device) PIT_TRY(from_device(p, Lam, d, 0, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
+    return PIT_OK;
+}
+
+pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *Xu,
+                              int on_device, pit_solve_info *info) {
+    if (!h || !o || !Xu) {
+        set_error("pit_bicgstab_solve: null argument");
+        return PIT_E_INVALID;
+    }
+    if (!(o->tol >= 0.0) || o->max_iter < 0 || o->x0_mode < PIT_X0_COARSE ||
+        o->x0_mode > PIT_X0_GIVEN || !(o->restart_eps0 >= 0.0)) {
+        set_error("pit_bicgstab_solve: invalid options");
+        return PIT_E_INVALID;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    Problem *p = &h->p;
+    PIT_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = o->stream ? (cudaStream_t)o->stream : p->stream;
+    PIT_TRY(krylov_prepare(p));
+    const size_t vb = p->vlen * sizeof(double);
+    const int B = p->batch;
+    std::vector<pit_solve_info> inf(B);
+    for (auto &i : inf) memset(&i, 0, sizeof i);
+    std::vector<int> status(B, PIT_OK);
+    const long long steps_per_matvec = (long long)p->N * p->fine_steps;
+
+    if (p->precision == PIT_FP64) {
+        double *X = p->X.as<double>();
+        if (o->x0_mode == PIT_X0_GIVEN) PIT_TRY(to_device(p, X, Xu, on_device, s));
+        else if (o->x0_mode == PIT_X0_ZERO) PIT_CUDA(cudaMemsetAsync(X, 0, vb, s));
+        else {
+            PIT_TRY(build_rhs(p, X, s));
+            PIT_TRY(op_sweep(p, X, X, PIT_FP64, nullptr, s));
+        }
+        LoopOut lo;
+        PIT_TRY(run_bicgstab(p, PIT_FP64, o->tol, 0.0, o->restart_eps0, o->max_iter, false, s,
+                             o->history, o->history_len, 0, lo));
+        PIT_TRY(from_device(p, Xu, X, on_device, s));
+        PIT_CUDA(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b) {
+            const MemberState &m = lo.final_states[b];
+            inf[b].iterations = m.iter;
+            inf[b].matvecs = m.matvecs;
+            inf[b].restarts = m.restarts;
+            inf[b].refinements = 0;
+            inf[b].fine_slice_steps = (long long)m.matvecs * steps_per_matvec;
+            inf[b].r0 = m.r0;
+            inf[b].precond_resid = m.rnorm;
+            inf[b].status = m.status;
+            inf[b].history_count = (b == 0) ? lo.history_count : 0;
+            status[b] = m.status;
+        }
+    } else {
+        // Iterative refinement: FP64 true residual, FP32-fine inner solve.
+        PIT_TRY(p->W.ensure(vb));
+        double *Xo = p->W.as<double>();   // outer solution lives in W
+        double *Wr = p->R.as<double>();   // true residual goes straight into R
+        if (o->x0_mode == PIT_X0_GIVEN) PIT_TRY(to_device(p, Xo, Xu, on_device, s));
+        else if (o->x0_mode == PIT_X0_ZERO) PIT_CUDA(cudaMemsetAsync(Xo, 0, vb, s));
+        else {
+            PIT_TRY(build_rhs(p, Xo, s));
+            PIT_TRY(op_sweep(p, Xo, Xo, PIT_MIXED, nullptr, s));
+        }
+        std::vector<double> rtrue, r0(B, 0.0);
+        std::vector<char> done(B, 0);
+        int hc = 0;
+        const int rounds = std::max(1, o->refine_max);
+        for (int round = 0; round <= rounds; ++round) {
+            PIT_TRY(op_apply_F(p, Xo, Wr, FINE_RESIDUAL, PIT_FP64, nullptr, s));
+            PIT_TRY(op_sweep(p, Wr, Wr, PIT_MIXED, nullptr, s));
+            PIT_TRY(member_norms(p, Wr, rtrue, s));
+            bool any = false;
+            for (int b = 0; b < B; ++b) {
+                if (done[b]) continue;
+                inf[b].matvecs += 1;
+                inf[b].fine_slice_steps += steps_per_matvec;
+                if (round == 0) r0[b] = rtrue[b];
+                inf[b].r0 = r0[b];
+                inf[b].precond_resid = rtrue[b];
+                if (!std::isfinite(rtrue[b])) {
+                    done[b] = 1;
+                    status[b] = PIT_E_NONFINITE;
+                } else if (rtrue[b] <= o->tol * r0[b]) {
+                    done[b] = 1;
+                    status[b] = PIT_OK;
+                } else if (round == rounds) {
+                    done[b] = 1;
+                    status[b] = PIT_E_MAXITER;
+                } else {
+                    any = true;
+                }
+            }
+            if (o->history && hc < o->history_len) o->history[hc++] = rtrue[0];
+            if (!any) break;
+            for (int b = 0; b < B; ++b)
+                if (done[b])
+                    PIT_CUDA(cudaMemsetAsync(Wr + (size_t)b * p->blen, 0,
+                                             p->blen * sizeof(double), s));
+            PIT_CUDA(cudaMemsetAsync(p->X.ptr, 0, vb, s));
+            LoopOut lo;
+            PIT_TRY(run_bicgstab(p, PIT_MIXED, o->inner_tol, 0.0, o->restart_eps0, o->max_iter,
+                                 true, s, nullptr, 0, 0, lo));
+            for (int b = 0; b < B; ++b) {
+                if (done[b]) continue;
+                const MemberState &m = lo.final_states[b];
+                inf[b].iterations += m.iter;
+                inf[b].matvecs += m.matvecs - 1;   // R^0 was given: no matvec
+                inf[b].restarts += m.restarts;
+                inf[b].refinements += 1;
+                inf[b].fine_slice_steps += (long long)(m.matvecs - 1) * steps_per_matvec;
+                if (m.status == PIT_E_NONFINITE || m.status == PIT_E_BREAKDOWN) {
+                    // a failed inner solve still leaves a usable correction of
+                    // the last iterate; a non-finite one does not
+                    if (m.status == PIT_E_NONFINITE) {
+                        done[b] = 1;
+                        status[b] = m.status;
+                    }
+                }
+            }
+            PIT_TRY(kr_axpy(p, Xo, p->X.as<double>(), s));
+        }
+        PIT_TRY(from_device(p, Xu, Xo, on_device, s));
+        PIT_CUDA(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b) {
+            inf[b].status = status[b];
+            inf[b].history_count = (b == 0) ? hc : 0;
+        }
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (auto &i : inf) i.seconds = secs;
+    if (info) std::copy(inf.begin(), inf.end(), info);
+    return worst_status(status);
+}
+
+pit_status pit_parareal_solve(pit_problem_t h, int kmax, double tol, double *Xu, int on_device,
+                              pit_solve_info *info) {
+    if (!h || !Xu || kmax < 0 || !(tol >= 0.0)) {
+        set_error("pit_parareal_solve: bad argument");
+        return PIT_E_INVALID;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    Problem *p = &h->p;
+    PIT_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = p->stream;
+    PIT_TRY(krylov_prepare(p));
+    const int B = p->batch;
+    const int sp = sweep_prec(p->precision);
+    double *X = p->X.as<double>(), *Wr = p->R.as<double>();
+    PIT_TRY(build_rhs(p, X, s));
+    PIT_TRY(op_sweep(p, X, X, sp, nullptr, s));       // X^0 = G^{-1} B
+    std::vector<pit_solve_info> inf(B);
+    for (auto &i : inf) memset(&i, 0, sizeof i);
+    std::vector<char> done(B, 0);
+    std::vector<int> status(B, PIT_OK);
+    std::vector<double> rn, r0(B, 0.0);
+    const long long steps_per_matvec = (long long)p->N * p->fine_steps;
+    for (int k = 0;; ++k) {
+        PIT_TRY(op_apply_F(p, X, Wr, FINE_RESIDUAL, PIT_FP64, nullptr, s));
+        PIT_TRY(op_sweep(p, Wr, Wr, sp, nullptr, s));
+        PIT_TRY(member_norms(p, Wr, rn, s));
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+            if (done[b]) continue;
+            inf[b].matvecs += 1;
+            inf[b].fine_slice_steps += steps_per_matvec;
+            if (k == 0) r0[b] = rn[b];
+            inf[b].r0 = r0[b];
+            inf[b].precond_resid = rn[b];
+            inf[b].iterations = k;
+            if (!std::isfinite(rn[b])) {
+                done[b] = 1;
+                status[b] = PIT_E_NONFINITE;
+            } else if (rn[b] <= tol * r0[b]) {
+                done[b] = 1;
+            } else if (k >= kmax) {
+                done[b] = 1;
+                status[b] = tol > 0.0 ? PIT_E_MAXITER : PIT_OK;
+            } else {
+                any = true;
+            }
+        }
+        if (!any) break;
+        for (int b = 0; b < B; ++b)
+            if (done[b])
+                PIT_CUDA(cudaMemsetAsync(Wr + (size_t)b * p->blen, 0, p->blen * sizeof(double), s));
+        PIT_TRY(kr_axpy(p, X, Wr, s));                 // X^{k+1} = X^k + G^{-1}(B - F X^k)
+    }
+    PIT_TRY(from_device(p, Xu, X, on_device, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int b = 0; b < B; ++b) {
+        inf[b].status = status[b];
+        inf[b].seconds = secs;
+    }
+    if (info) std::copy(inf.begin(), inf.end(), info);
+    return worst_status(status);
+}
+
+pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M, double *dot,
+                            double *norms, double *norm_inf) {
+    if (!U || !V || !dot || !norm_inf || nblocks < 1 || M < 1) {
+        set_error("pit_block_reduce: bad argument");
+        return PIT_E_INVALID;
+    }
+    PIT_TRY(block_reduce(U, V, nblocks, M, dot, norms, norm_inf, 0));
+    PIT_CUDA(cudaStreamSynchronize(0));
+    return PIT_OK;
+}
+
+}  // extern "C"

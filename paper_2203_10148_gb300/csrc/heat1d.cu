@@ -1,0 +1,366 @@
+// 1D heat u_t = nu u_xx (Dirichlet 0, M interior points, h = 1/(M+1)):
+// implicit-Euler fine propagator over all N slices at once (the N
+// independent problems of eq. (2)), fused with the shift-subtract of the
+// block operator of eq. (4), and the sequential coarse sweep G^{-1} of
+// eq. (7), right.
+//
+// Each implicit-Euler step solves the tridiagonal system (I - dt nu D2) u+ = u.
+// The Thomas elimination is two first-order linear recurrences,
+//   forward  d'_i = -a inv_i d'_{i-1} + inv_i d_i,
+//   backward x_i  = -c'_i x_{i+1} + d'_i,
+// with inv_i and c'_i precomputed once on the host.  A linear recurrence is
+// a composition of affine maps, so one CTA evaluates it with a parallel
+// scan: every thread composes the maps of its E contiguous points, the CTA
+// scans the per-thread maps (warp shuffles, then a short pass over warps),
+// and every thread replays its points from the scanned prefix.  A slice's
+// state stays in registers across all fine steps.
+#include <math.h>
+
+#include <vector>
+
+#include "pit_internal.h"
+
+namespace pit {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <class T>
+struct Aff {
+    T a, c;
+};
+
+// later o earlier
+template <class T>
+__device__ __forceinline__ Aff<T> comp(Aff<T> later, Aff<T> earlier) {
+    return Aff<T>{later.a * earlier.a, fma(later.a, earlier.c, later.c)};
+}
+
+template <class T>
+__device__ __forceinline__ T shfl_dir(T v, int o, bool rev) {
+    return rev ? __shfl_down_sync(FULL, v, o) : __shfl_up_sync(FULL, v, o);
+}
+
+// Exclusive scan of affine maps over the CTA.  Scan order is thread order
+// (REV = false) or reversed thread order (REV = true).  sh: 2*NT/32 values.
+template <class T, int NT, bool REV>
+__device__ Aff<T> cta_affine_excl(Aff<T> v, T *sh) {
+    constexpr int W = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Aff<T> inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T a = shfl_dir(inc.a, o, REV);
+        const T c = shfl_dir(inc.c, o, REV);
+        const bool ok = REV ? (lane + o < 32) : (lane >= o);
+        if (ok) inc = comp(inc, Aff<T>{a, c});
+    }
+    const T ea = shfl_dir(inc.a, 1, REV);
+    const T ec = shfl_dir(inc.c, 1, REV);
+    const bool first = REV ? (lane == 31) : (lane == 0);
+    Aff<T> exw = first ? Aff<T>{T(1), T(0)} : Aff<T>{ea, ec};
+    if (W == 1) return exw;
+    const int last = REV ? 0 : 31;
+    __syncthreads();
+    if (lane == last) {
+        sh[warp] = inc.a;
+        sh[W + warp] = inc.c;
+    }
+    __syncthreads();
+    Aff<T> wp{T(1), T(0)};
+    if (!REV) {
+        for (int w2 = 0; w2 < warp; ++w2) wp = comp(Aff<T>{sh[w2], sh[W + w2]}, wp);
+    } else {
+        for (int w2 = W - 1; w2 > warp; --w2) wp = comp(Aff<T>{sh[w2], sh[W + w2]}, wp);
+    }
+    return comp(exw, wp);
+}
+
+// One implicit-Euler step on the CTA-distributed state u (E points per
+// thread, thread t owns points t*E .. t*E+E-1).  fm_i = -a inv_i,
+// inv_i, cp_i = c'_i (cp_{M-1} = 0).
+template <class T, int E, int NT>
+__device__ __forceinline__ void ie_step(T (&u)[E], const T *__restrict__ fm,
+                                        const T *__restrict__ inv, const T *__restrict__ cp,
+                                        int M, T *sh) {
+    const int i0 = threadIdx.x * E;
+    // forward: d'_i = fm_i d'_{i-1} + inv_i d_i
+    Aff<T> agg{T(1), T(0)};
+    T lm[E], lc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = i0 + e;
+        const int ic = min(i, M - 1);
+        lm[e] = (i < M) ? fm[ic] : T(1);
+        lc[e] = (i < M) ? inv[ic] * u[e] : T(0);
+        agg = comp(Aff<T>{lm[e], lc[e]}, agg);
+    }
+    Aff<T> pre = cta_affine_excl<T, NT, false>(agg, sh);
+    T y = pre.c;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        y = fma(lm[e], y, lc[e]);
+        u[e] = y;                       // d'_i
+    }
+    // backward: x_i = -cp_i x_{i+1} + d'_i, scanned from the last point
+    agg = Aff<T>{T(1), T(0)};
+#pragma unroll
+    for (int e = E - 1; e >= 0; --e) {
+        const int i = i0 + e;
+        lm[e] = (i < M) ? -cp[min(i, M - 1)] : T(1);
+        lc[e] = (i < M) ? u[e] : T(0);
+        agg = comp(Aff<T>{lm[e], lc[e]}, agg);
+    }
+    pre = cta_affine_excl<T, NT, true>(agg, sh + 2 * (NT / 32));
+    y = pre.c;
+#pragma unroll
+    for (int e = E - 1; e >= 0; --e) {
+        y = fma(lm[e], y, lc[e]);
+        u[e] = y;
+    }
+}
+
+struct Heat1dArgs {
+    const double *x;
+    double *y;
+    const double *y0;
+    int M, N, batch;
+    size_t blen;
+    int n_first;    // output slice index of blockIdx.x == 0
+    int mode;       // FINE_APPLY, FINE_RESIDUAL, or 2 = plain (y_n = F(x_{n-1}))
+    int steps;
+    const MemberState *st;
+};
+
+__device__ __forceinline__ bool runs(const MemberState *st, int b) {
+    return st == nullptr || (st[b].active && !st[b].skip && !st[b].half);
+}
+
+// Fine batch: CTA (slice n, member b) propagates x_{n-1} over `steps` IE
+// steps and writes the block-operator row n.
+template <class T, int E, int NT>
+__global__ void __launch_bounds__(NT) k_heat1d_fine(Heat1dArgs a, const T *__restrict__ fm,
+                                                    const T *__restrict__ inv,
+                                                    const T *__restrict__ cp) {
+    __shared__ T sh[4 * (NT / 32)];
+    const int b = blockIdx.y;
+    if (!runs(a.st, b)) return;
+    const int n = a.n_first + blockIdx.x;    // output block, 1..N
+    const size_t mb = (size_t)b * a.blen;
+    const double *xin = a.x + mb + (size_t)(n - 1) * a.M;
+    T u[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        const T ld = (T)xin[min(i, a.M - 1)];
+        u[e] = (i < a.M) ? ld : T(0);
+    }
+    for (int s = 0; s < a.steps; ++s) ie_step<T, E, NT>(u, fm, inv, cp, a.M, sh);
+    double *yo = a.y + mb + (size_t)n * a.M;
+    const double *xn = a.x + mb + (size_t)n * a.M;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        if (i < a.M) {
+            const double f = (double)u[e];
+            if (a.mode == FINE_APPLY) yo[i] = xn[i] - f;
+            else if (a.mode == FINE_RESIDUAL) yo[i] = f - xn[i];
+            else yo[i] = f;
+        }
+    }
+    if (n == 1 && a.mode != 2) {
+        // row 0 of eq. (4): (F X)_0 = x_0; residual: y0 - x_0
+        const double *x0 = a.x + mb;
+        double *y0o = a.y + mb;
+        for (int i = threadIdx.x; i < a.M; i += NT)
+            y0o[i] = (a.mode == FINE_APPLY) ? x0[i] : a.y0[(size_t)b * a.M + i] - x0[i];
+    }
+}
+
+// Coarse sweep z_0 = q_0, z_n = q_n + G(z_{n-1}), one CTA per member,
+// sequential in n.  G is `steps` IE steps in arithmetic T; the running sum
+// z_n is kept in FP64.
+template <class T, int E, int NT>
+__global__ void __launch_bounds__(NT) k_heat1d_sweep(const double *q, double *z, int M, int N,
+                                                     size_t blen, int steps,
+                                                     const T *__restrict__ fm,
+                                                     const T *__restrict__ inv,
+                                                     const T *__restrict__ cp,
+                                                     const MemberState *st) {
+    __shared__ T sh[4 * (NT / 32)];
+    const int b = blockIdx.x;
+    if (!runs(st, b)) return;
+    const size_t mb = (size_t)b * blen;
+    double zz[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        const double ld = q[mb + min(i, M - 1)];
+        zz[e] = (i < M) ? ld : 0.0;
+        if (i < M) z[mb + i] = zz[e];
+    }
+    for (int n = 1; n <= N; ++n) {
+        T u[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) u[e] = (T)zz[e];
+        for (int s = 0; s < steps; ++s) ie_step<T, E, NT>(u, fm, inv, cp, M, sh);
+        const size_t off = mb + (size_t)n * M;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = threadIdx.x * E + e;
+            if (i < M) {
+                zz[e] = q[off + i] + (double)u[e];
+                z[off + i] = zz[e];
+            } else {
+                zz[e] = 0.0;
+            }
+        }
+    }
+}
+
+// Thomas factors of tridiag(a, 1 - 2a, a), a = -dt nu/h^2.
+void thomas_factors(int M, double r, std::vector<double> &fm, std::vector<double> &inv,
+                    std::vector<double> &cp) {
+    const double a = -r, b = 1.0 + 2.0 * r;
+    fm.assign(M, 0.0);
+    inv.assign(M, 0.0);
+    cp.assign(M, 0.0);
+    double cprev = 0.0;
+    for (int i = 0; i < M; ++i) {
+        const double den = (i == 0) ? b : b - a * cprev;
+        inv[i] = 1.0 / den;
+        fm[i] = (i == 0) ? 0.0 : -a * inv[i];
+        cp[i] = (i == M - 1) ? 0.0 : a * inv[i];
+        cprev = cp[i];
+    }
+}
+
+pit_status upload_factors(int M, double r, DevBuf &b64, DevBuf &b32) {
+    std::vector<double> fm, inv, cp;
+    thomas_factors(M, r, fm, inv, cp);
+    std::vector<double> all(3 * (size_t)M);
+    std::vector<float> all32(3 * (size_t)M);
+    for (int i = 0; i < M; ++i) {
+        all[i] = fm[i];
+        all[M + i] = inv[i];
+        all[2 * M + i] = cp[i];
+    }
+    for (size_t i = 0; i < all.size(); ++i) all32[i] = (float)all[i];
+    PIT_TRY(b64.ensure(all.size() * sizeof(double)));
+    PIT_TRY(b32.ensure(all32.size() * sizeof(float)));
+    PIT_CUDA(cudaMemcpy(b64.ptr, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
+    PIT_CUDA(cudaMemcpy(b32.ptr, all32.data(), all32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return PIT_OK;
+}
+
+template <class T>
+const T *fptr(const DevBuf &b, int M, int which) {
+    return b.as<T>() + (size_t)which * M;
+}
+
+// Threads and points per thread for a state of M points.
+template <class F>
+pit_status dispatch_1d(int M, F &&f) {
+    if (M <= 64) return f.template run<1, 64>();
+    if (M <= 256) return f.template run<1, 256>();
+    if (M <= 1024) return f.template run<1, 1024>();
+    if (M <= 2048) return f.template run<2, 1024>();
+    if (M <= 4096) return f.template run<4, 1024>();
+    if (M <= 8192) return f.template run<8, 1024>();
+    set_error("heat1d: M > 8192 is not supported");
+    return PIT_E_UNSUPPORTED;
+}
+
+template <class T>
+struct FineLaunch {
+    Problem *p;
+    Heat1dArgs a;
+    int nslices;
+    const DevBuf *fac;
+    cudaStream_t s;
+    template <int E, int NT>
+    pit_status run() {
+        const T *base = fac->as<T>();
+        const int M = p->M;
+        k_heat1d_fine<T, E, NT><<<dim3(nslices, p->batch), NT, 0, s>>>(a, base, base + M,
+                                                                        base + 2 * M);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
+};
+
+template <class T>
+struct SweepLaunch {
+    Problem *p;
+    const double *q;
+    double *z;
+    const DevBuf *fac;
+    const MemberState *st;
+    cudaStream_t s;
+    template <int E, int NT>
+    pit_status run() {
+        const T *base = fac->as<T>();
+        const int M = p->M;
+        k_heat1d_sweep<T, E, NT><<<p->batch, NT, 0, s>>>(q, z, M, p->N, p->blen,
+                                                          p->coarse_steps, base, base + M,
+                                                          base + 2 * M, st);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
+};
+
+pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStream_t s) {
+    if (prec == PIT_FP64) {
+        FineLaunch<double> f{p, a, nslices, &p->fine_inv64, s};
+        return dispatch_1d(p->M, f);
+    }
+    FineLaunch<float> f{p, a, nslices, &p->fine_inv32, s};
+    return dispatch_1d(p->M, f);
+}
+
+}  // namespace
+
+pit_status heat1d_setup(Problem *p) {
+    if (p->fine_kind != PIT_STEP_IE || p->coarse_kind != PIT_STEP_IE) {
+        set_error("heat1d: fine and coarse steppers must be implicit Euler");
+        return PIT_E_UNSUPPORTED;
+    }
+    if (p->M > 8192) {
+        set_error("heat1d: M > 8192 is not supported");
+        return PIT_E_UNSUPPORTED;
+    }
+    const double h = 1.0 / (p->M + 1);
+    const double rf = (p->dT / p->fine_steps) * p->nu / (h * h);
+    const double rc = (p->dT / p->coarse_steps) * p->nu / (h * h);
+    // fine factors in fine_inv64/32, coarse in coarse_inv64/32 (fm | inv | cp)
+    PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32));
+    PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32));
+    return PIT_OK;
+}
+
+pit_status heat1d_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                          const MemberState *st, cudaStream_t s) {
+    Heat1dArgs a{x, y, p->y0.as<double>(), p->M, p->N, p->batch, p->blen, 1, mode,
+                 p->fine_steps, st};
+    return fine_launch(p, a, p->N, prec, s);
+}
+
+pit_status heat1d_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
+    // y (block n) = F(x (block n-1)) for every member: x and y point at
+    // consecutive blocks of the same block vector.
+    Heat1dArgs a{x, y - p->M, p->y0.as<double>(), p->M, p->N, p->batch, p->blen, 1, 2,
+                 p->fine_steps, nullptr};
+    return fine_launch(p, a, 1, prec, s);
+}
+
+pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
+                        cudaStream_t s) {
+    if (prec == PIT_FP64) {
+        SweepLaunch<double> f{p, q, z, &p->coarse_inv64, st, s};
+        return dispatch_1d(p->M, f);
+    }
+    SweepLaunch<float> f{p, q, z, &p->coarse_inv32, st, s};
+    return dispatch_1d(p->M, f);
+}
+
+}  // namespace pit

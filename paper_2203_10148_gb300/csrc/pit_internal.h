@@ -1,0 +1,178 @@
+// Internal declarations shared by the libpit translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pit.h"
+
+namespace pit {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define PIT_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::pit::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define PIT_TRY(call)                                                         \
+    do {                                                                      \
+        pit_status s_ = (call);                                               \
+        if (s_ != PIT_OK) return s_;                                          \
+    } while (0)
+
+#define PIT_LAUNCH_CHECK() PIT_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------- device buffers
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    pit_status ensure(size_t n);   // grows (never shrinks) the allocation
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Per-member solver state, resident on the device (Algorithm 1 scalars).
+struct MemberState {
+    double rho;        // <R^k, R~>
+    double sigma;      // <D^k, R~>
+    double alpha, omega, beta;
+    double dd;         // <D, D>
+    double ks, kk;     // <K, S>, <K, K>
+    double rho_new;    // <R^{k+1}, R~>
+    double r2;         // <R^{k+1}, R^{k+1}>
+    double rt2;        // <R~, R~>
+    double r0;         // ||R^0||_{N,inf}
+    double rnorm;      // ||R^k||_{N,inf}
+    double snorm;      // ||S^k||_{N,inf}
+    double thresh;     // stopping threshold
+    double eps0, eps_b;
+    int active;        // 1 while iterating
+    int status;        // PIT_OK / PIT_E_*
+    int iter, restarts, matvecs;
+    int skip;          // this iteration restarts after a vanishing sigma (no update)
+    int half;          // this iteration exits after the half step
+    int just_restarted;
+    int do_restart;    // update of P restarts R~ and P
+    int max_iter;
+    int pad_;
+};
+
+// Reduction scratch: partial sums of Q quantities per (member, block, chunk).
+struct ReduceLayout {
+    int Q;        // quantities
+    int nblk;     // N + 1
+    int chunks;   // chunks per block
+    int chunk;    // elements per chunk
+};
+
+// ---------------------------------------------------------------- problem
+struct Problem {
+    // description
+    int kind = 0, nx = 0, ny = 0, M = 0, N = 0, batch = 0;
+    double T = 0, dT = 0, nu = 0;
+    int fine_kind = 0, fine_steps = 0, coarse_kind = 0, coarse_steps = 0;
+    int precision = PIT_FP64;
+    size_t blen = 0;              // (N+1)*M
+    size_t vlen = 0;              // batch*(N+1)*M
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    DevBuf y0;                    // batch*M
+
+    // heat1d: Thomas factors of (I - dt L) for the fine and coarse steps
+    DevBuf fine_inv64, fine_cp64, coarse_inv64, coarse_cp64;
+    DevBuf fine_inv32, fine_cp32, coarse_inv32, coarse_cp32;
+    double fine_off = 0, coarse_off = 0;   // off-diagonal -dt nu / h^2
+
+    // heat2d: sine basis S_jk = sin(pi j k/(n+1)) and coarse mode factors
+    DevBuf S64, S32, gmode;       // gmode: (1 - dTc nu (mu_k + mu_l))^{-c}
+    DevBuf hat;                   // sweep scratch: transformed blocks
+
+    // advdiff2d: per-point velocities (FP64 and FP32)
+    DevBuf vx64, vy64, vx32, vy32;
+    DevBuf adv_scratch;
+
+    // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)
+    DevBuf PhiF64, G64, PhiF_hi, PhiF_lo, G32;
+    DevBuf dense_scratch;
+
+    // Krylov workspace
+    DevBuf X, R, Rt, P, S, D, K, W;
+    DevBuf partials, states, flags_host_mirror;
+    DevBuf fine_tmp;              // serial / misc scratch
+    ReduceLayout rl{};
+};
+
+// Modes of the fused block-operator epilogue.
+enum { FINE_APPLY = 0, FINE_RESIDUAL = 1 };
+
+// ---------------------------------------------------------- operator API
+// y = F x (mode FINE_APPLY) or y = B - F x (mode FINE_RESIDUAL); every block.
+// `states` (may be null) masks inactive members.
+pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int precision,
+                      const MemberState *states, cudaStream_t s);
+// z = G^{-1} q (in place allowed: z == q).
+pit_status op_sweep(Problem *p, const double *q, double *z, int precision,
+                    const MemberState *states, cudaStream_t s);
+// Lam = serial fine trajectory.
+pit_status op_serial(Problem *p, double *Lam, int precision, cudaStream_t s);
+
+// per-family implementations
+pit_status heat1d_setup(Problem *p);
+pit_status heat1d_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                          const MemberState *st, cudaStream_t s);
+pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec,
+                        const MemberState *st, cudaStream_t s);
+pit_status heat1d_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+
+pit_status heat2d_setup(Problem *p);
+pit_status heat2d_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                          const MemberState *st, cudaStream_t s);
+pit_status heat2d_sweep(Problem *p, const double *q, double *z, int prec,
+                        const MemberState *st, cudaStream_t s);
+pit_status heat2d_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+
+pit_status advdiff_setup(Problem *p);
+pit_status advdiff_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                           const MemberState *st, cudaStream_t s);
+pit_status advdiff_sweep(Problem *p, const double *q, double *z, int prec,
+                         const MemberState *st, cudaStream_t s);
+pit_status advdiff_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+
+pit_status dense_setup(Problem *p);
+pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                         const MemberState *st, cudaStream_t s);
+pit_status dense_sweep(Problem *p, const double *q, double *z, int prec,
+                       const MemberState *st, cudaStream_t s);
+pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+
+// ------------------------------------------------------------ Krylov API
+pit_status krylov_prepare(Problem *p);   // allocates vectors, partials, states
+// block copy of y0 into block 0 of each member and zeros elsewhere
+pit_status build_rhs(Problem *p, double *B, cudaStream_t s);
+
+// Kernel launchers (krylov.cu); every one masks inactive members.
+pit_status kr_init(Problem *p, double tol_rel, double abs_thresh, double eps0, int max_iter,
+                   cudaStream_t s);       // R computed: R~ = P = R; rho, r0, thresh
+pit_status kr_sigma(Problem *p, cudaStream_t s);     // sigma = <D,R~>, alpha
+pit_status kr_update_S(Problem *p, cudaStream_t s);  // S = R - alpha D, ||S||, half exit
+pit_status kr_omega(Problem *p, cudaStream_t s);     // <K,S>, <K,K>, omega
+pit_status kr_update_XR(Problem *p, cudaStream_t s); // X, R, rho_new, ||R||, beta, tests
+pit_status kr_update_P(Problem *p, cudaStream_t s);  // P update or restart
+pit_status kr_block_norm(Problem *p, const double *U, double *out_norm_per_member,
+                         cudaStream_t s);            // ||U||_{N,inf} per member (device out)
+pit_status kr_axpy(Problem *p, double *X, const double *Y, cudaStream_t s);  // X += Y
+pit_status block_reduce(const double *U, const double *V, int nblocks, int M, double *dot,
+                        double *norms, double *norm_inf, cudaStream_t s);
+
+}  // namespace pit
+
+struct pit_problem_s {
+    pit::Problem p;
+};

@@ -1,0 +1,281 @@
+"""ctypes binding of the libpit C-ABI (include/pit.h).
+
+Argument marshalling only: every step of the parallel-in-time path runs in
+the CUDA kernels of ``libpit.so``.  Arrays are numpy arrays (host memory,
+``on_device = 0``) or CUDA torch tensors (device memory, ``on_device = 1``).
+Loading fails loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpit.so")
+_lib: Optional[C.CDLL] = None
+
+# status codes
+PIT_OK, PIT_PENDING = 0, 1
+PIT_E_INVALID, PIT_E_NOMEM, PIT_E_CUDA, PIT_E_BREAKDOWN = -1, -2, -3, -4
+PIT_E_MAXITER, PIT_E_NONFINITE, PIT_E_TIMEOUT, PIT_E_BUSY, PIT_E_UNSUPPORTED = -5, -6, -7, -8, -9
+STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "nomem", -3: "cuda", -4: "breakdown",
+                -5: "maxiter", -6: "nonfinite", -7: "timeout", -8: "busy", -9: "unsupported"}
+
+PIT_OP = {"heat1d": 1, "heat2d": 2, "advdiff2d": 3, "dense": 4}
+PIT_STEP = {"ie": 1, "rk4": 2}
+PIT_FP64, PIT_MIXED = 0, 1
+PRECISION = {"fp64": PIT_FP64, "mixed": PIT_MIXED}
+APPLY = {"F": 1, "Ginv": 2, "GinvF": 3, "residual": 4}
+X0 = {"coarse": 0, "zero": 1, "given": 2}
+
+
+class OperatorDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nu", C.c_double),
+                ("vx", C.POINTER(C.c_double)), ("vy", C.POINTER(C.c_double)),
+                ("A", C.POINTER(C.c_double))]
+
+
+class StepperDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("steps", C.c_int)]
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("op", OperatorDesc), ("y0", C.POINTER(C.c_double)), ("batch", C.c_int),
+                ("T", C.c_double), ("N", C.c_int), ("fine", StepperDesc),
+                ("coarse", StepperDesc), ("precision", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart_eps0", C.c_double), ("max_iter", C.c_int),
+                ("x0_mode", C.c_int), ("refine_max", C.c_int), ("inner_tol", C.c_double),
+                ("stream", C.c_void_p), ("history", C.POINTER(C.c_double)),
+                ("history_len", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("matvecs", C.c_int), ("restarts", C.c_int),
+                ("refinements", C.c_int), ("fine_slice_steps", C.c_longlong),
+                ("r0", C.c_double), ("precond_resid", C.c_double), ("seconds", C.c_double),
+                ("status", C.c_int), ("history_count", C.c_int)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+class PitError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libpit: {STATUS_NAMES.get(status, status)} ({status}): {msg}")
+        self.status = status
+
+
+# every symbol declared in include/pit.h
+EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_create",
+           "pit_problem_destroy", "pit_problem_shape", "pit_apply_operator", "pit_serial_fine",
+           "pit_bicgstab_solve", "pit_parareal_solve", "pit_block_reduce"]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load() -> C.CDLL:
+    """Loads libpit.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libpit.so not found at {_LIB_PATH}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(_LIB_PATH)
+    P = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    lib.pit_default_opts.argtypes = [C.POINTER(SolveOpts)]
+    lib.pit_default_opts.restype = None
+    lib.pit_version.restype = C.c_char_p
+    lib.pit_last_error.argtypes = [C.c_char_p, C.c_size_t]
+    lib.pit_last_error.restype = C.c_size_t
+    lib.pit_problem_create.argtypes = [C.POINTER(ProblemDesc), C.POINTER(P)]
+    lib.pit_problem_destroy.argtypes = [P]
+    lib.pit_problem_shape.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.pit_apply_operator.argtypes = [P, C.c_int, C.c_int, P, P, C.c_int, P]
+    lib.pit_serial_fine.argtypes = [P, C.c_int, P, C.c_int]
+    lib.pit_bicgstab_solve.argtypes = [P, C.POINTER(SolveOpts), P, C.c_int, C.POINTER(SolveInfo)]
+    lib.pit_parareal_solve.argtypes = [P, C.c_int, C.c_double, P, C.c_int, C.POINTER(SolveInfo)]
+    lib.pit_block_reduce.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
+    for name in EXPORTS:
+        if name not in ("pit_default_opts", "pit_version", "pit_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    lib = load()
+    buf = C.create_string_buffer(1024)
+    lib.pit_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int) -> int:
+    if status < 0:
+        raise PitError(status, last_error())
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _torch_stream(x, stream):
+    """The caller's current torch stream for device arrays (unless one is given)."""
+    if stream is not None or isinstance(x, np.ndarray):
+        return stream
+    import torch
+    return torch.cuda.current_stream(x.device).cuda_stream
+
+
+def _array_arg(x) -> Tuple[int, int, object]:
+    """(pointer, on_device, keepalive) for a numpy array or a CUDA torch tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return x.ctypes.data, 0, x
+    import torch  # device memory only
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda:
+            raise ValueError("device tensors must be contiguous CUDA float64")
+        return x.data_ptr(), 1, x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+class Problem:
+    """A libpit problem built from a workload (paper_2203_10148_gb300.inputs.Workload)."""
+
+    def __init__(self, w, precision: Optional[str] = None):
+        lib = load()
+        self.w = w
+        self.precision = PRECISION[precision or w.precision]
+        self._keep = []
+        y0 = np.ascontiguousarray(np.asarray(w.y0, dtype=np.float64).reshape(-1))
+        self._keep.append(y0)
+        op = OperatorDesc(PIT_OP[w.kind], w.nx, w.ny, float(w.nu), None, None, None)
+        if w.kind == "advdiff2d":
+            vx = np.ascontiguousarray(w.vx, dtype=np.float64)
+            vy = np.ascontiguousarray(w.vy, dtype=np.float64)
+            self._keep += [vx, vy]
+            op.vx, op.vy = _dptr(vx), _dptr(vy)
+        if w.kind == "dense":
+            A = np.ascontiguousarray(w.A, dtype=np.float64)
+            self._keep.append(A)
+            op.A = _dptr(A)
+        desc = ProblemDesc(op, _dptr(y0), int(w.batch), float(w.T), int(w.N),
+                           StepperDesc(PIT_STEP[w.fine[0]], int(w.fine[1])),
+                           StepperDesc(PIT_STEP[w.coarse[0]], int(w.coarse[1])), self.precision)
+        h = C.c_void_p()
+        check(lib.pit_problem_create(C.byref(desc), C.byref(h)))
+        self.handle = h
+        self.M, self.N, self.batch = w.M, w.N, w.batch
+        self.shape = (self.batch, self.N + 1, self.M)
+        self._keep = []
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pit_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------- calls
+    def _out_like(self, x):
+        if isinstance(x, np.ndarray):
+            return np.empty(self.shape, dtype=np.float64)
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device=x.device)
+
+    def apply(self, which: str, x, precision: Optional[str] = None, out=None, stream=None):
+        """pit_apply_operator: which in {'F', 'Ginv', 'GinvF', 'residual'}."""
+        prec = self.precision if precision is None else PRECISION[precision]
+        y = self._out_like(x) if out is None else out
+        px, dev, _ = _array_arg(x)
+        py, dev2, _ = _array_arg(y)
+        if dev != dev2:
+            raise ValueError("x and y must both be host or both be device arrays")
+        check(load().pit_apply_operator(self.handle, APPLY[which], prec, px, py, dev,
+                                        _torch_stream(x, stream)))
+        return y
+
+    def serial_fine(self, precision: Optional[str] = None, out=None):
+        prec = self.precision if precision is None else PRECISION[precision]
+        y = np.empty(self.shape, dtype=np.float64) if out is None else out
+        py, dev, _ = _array_arg(y)
+        check(load().pit_serial_fine(self.handle, prec, py, dev))
+        return y
+
+    def bicgstab_solve(self, X=None, tol: float = 1e-10, eps0: float = 1e-8,
+                       max_iter: int = 500, x0: str = "coarse", refine_max: int = 8,
+                       inner_tol: float = 1e-4, history_len: int = 0, stream=None,
+                       raise_on_status: bool = False):
+        """pit_bicgstab_solve; returns (X, [info dict per member])."""
+        lib = load()
+        opts = SolveOpts()
+        lib.pit_default_opts(C.byref(opts))
+        opts.tol, opts.restart_eps0, opts.max_iter = tol, eps0, max_iter
+        opts.x0_mode = X0["given" if (x0 == "given") else x0]
+        opts.refine_max, opts.inner_tol = refine_max, inner_tol
+        hist = None
+        if history_len:
+            hist = np.zeros(history_len)
+            opts.history = _dptr(hist)
+            opts.history_len = history_len
+        if X is None:
+            X = np.zeros(self.shape)
+        px, dev, _ = _array_arg(X)
+        opts.stream = _torch_stream(X, stream)
+        infos = (SolveInfo * self.batch)()
+        st = lib.pit_bicgstab_solve(self.handle, C.byref(opts), px, dev, infos)
+        if st in (PIT_E_INVALID, PIT_E_NOMEM, PIT_E_CUDA, PIT_E_UNSUPPORTED) or (raise_on_status and st < 0):
+            check(st)
+        out = [i.as_dict() for i in infos]
+        if hist is not None:
+            out[0]["history"] = hist[:out[0]["history_count"]].tolist()
+        return X, out
+
+    def parareal_solve(self, kmax: int, tol: float = 0.0, X=None):
+        lib = load()
+        if X is None:
+            X = np.zeros(self.shape)
+        px, dev, _ = _array_arg(X)
+        infos = (SolveInfo * self.batch)()
+        st = lib.pit_parareal_solve(self.handle, int(kmax), float(tol), px, dev, infos)
+        if st in (PIT_E_INVALID, PIT_E_NOMEM, PIT_E_CUDA, PIT_E_UNSUPPORTED):
+            check(st)
+        return X, [i.as_dict() for i in infos]
+
+
+def block_reduce(U, V, nblocks: int, M: int):
+    """pit_block_reduce on CUDA tensors: (dot, per-block norms, max block norm)."""
+    import torch
+    pu, du, _ = _array_arg(U)
+    pv, dv, _ = _array_arg(V)
+    if not (du and dv):
+        raise ValueError("pit_block_reduce takes device tensors")
+    out = torch.zeros(2 + nblocks, dtype=torch.float64, device=U.device)
+    base = out.data_ptr()
+    check(load().pit_block_reduce(pu, pv, nblocks, M, base, base + 16, base + 8))
+    o = out.cpu().numpy()
+    return float(o[0]), o[2:], float(o[1])

@@ -1,0 +1,83 @@
+"""The C-ABI library loads and exports every symbol include/pit.h declares,
+and its host-side argument validation rejects bad descriptors (no GPU needed:
+validation runs before any CUDA call)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(pit_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_10148_gb300 import build, pit
+    build.build()
+    return pit.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2203_10148_gb300 import pit
+    declared = _declared_functions()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(pit.EXPORTS) <= set(declared)
+
+
+def test_version_and_defaults(lib):
+    from paper_2203_10148_gb300 import pit
+    assert b"sm_103a" in lib.pit_version()
+    o = pit.SolveOpts()
+    lib.pit_default_opts(C.byref(o))
+    assert o.tol == 1e-10 and o.restart_eps0 == 1e-8 and o.x0_mode == 0 and o.refine_max >= 1
+
+
+def _desc(pit, y0, **kw):
+    op = pit.OperatorDesc(kw.get("kind", 1), kw.get("nx", y0.size), kw.get("ny", 1),
+                          kw.get("nu", 0.1), None, None, None)
+    return pit.ProblemDesc(op, y0.ctypes.data_as(C.POINTER(C.c_double)), kw.get("batch", 1),
+                           kw.get("T", 1.0), kw.get("N", 4),
+                           pit.StepperDesc(1, kw.get("fine_steps", 10)), pit.StepperDesc(1, 1),
+                           kw.get("precision", 0))
+
+
+@pytest.mark.parametrize("bad", [dict(N=0), dict(T=0.0), dict(T=-1.0), dict(fine_steps=0),
+                                 dict(kind=9), dict(batch=0), dict(precision=7), dict(ny=3),
+                                 dict(nu=-1.0)])
+def test_create_rejects_invalid_descriptors(lib, bad):
+    from paper_2203_10148_gb300 import pit
+    y0 = np.ones(8)
+    h = C.c_void_p()
+    st = lib.pit_problem_create(C.byref(_desc(pit, y0, **bad)), C.byref(h))
+    assert st == pit.PIT_E_INVALID
+    assert "pit_problem_create" in pit.last_error()
+
+
+def test_create_rejects_nonfinite_initial_value(lib):
+    from paper_2203_10148_gb300 import pit
+    y0 = np.ones(8)
+    y0[3] = np.nan
+    h = C.c_void_p()
+    assert lib.pit_problem_create(C.byref(_desc(pit, y0)), C.byref(h)) == pit.PIT_E_NONFINITE
+
+
+def test_null_arguments(lib):
+    from paper_2203_10148_gb300 import pit
+    assert lib.pit_problem_create(None, None) == pit.PIT_E_INVALID
+    assert lib.pit_problem_destroy(None) == pit.PIT_OK
+    assert lib.pit_apply_operator(None, 1, 0, None, None, 0, None) == pit.PIT_E_INVALID
+    assert lib.pit_bicgstab_solve(None, None, None, 0, None) == pit.PIT_E_INVALID
+    assert lib.pit_parareal_solve(None, 3, 0.0, None, 0, None) == pit.PIT_E_INVALID

@@ -1,0 +1,240 @@
+"""GPU parity of the heat-equation paths against the FP64 oracle.
+
+Every test calls the CUDA path through the C-ABI (the ctypes binding) and
+compares element by element with the oracle on the same seeded inputs.
+Tolerances: FP64 path 1e-12 relative (operators to 1e-13); FP32 fine stepping
+from FP64 inputs: m steps x 4 stages of FP32 rounding on O(1) data,
+bounded here by 2e-5 relative; mixed-precision solves: 1e-6 against the
+serial FP64 fine trajectory.
+"""
+import numpy as np
+import pytest
+
+from oracle import OracleProblem, parareal, pitsbicg
+from paper_2203_10148_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _pit():
+    from paper_2203_10148_gb300 import pit
+    return pit
+
+
+def _rand_block(w, seed, scale=1.0):
+    s = inputs.SeededStream(seed)
+    return (scale * s.normal(w.batch * (w.N + 1) * w.M)).reshape(w.batch, w.N + 1, w.M)
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def _oracle_apply(w, which, X):
+    out = []
+    for b in range(w.batch):
+        o = OracleProblem.from_workload(w, member=b)
+        x = X[b]
+        if which == "F":
+            out.append(o.apply_F(x))
+        elif which == "Ginv":
+            out.append(o.sweep_Ginv(x))
+        elif which == "GinvF":
+            out.append(o.apply_GinvF(x))
+        else:
+            out.append(o.residual(x))
+    return np.stack(out)
+
+
+# ------------------------------------------------------------------- 1D heat
+
+HEAT1D_CASES = [dict(), dict(M=31, N=5, fine_steps=7), dict(M=100, N=3, fine_steps=20),
+                dict(M=1, N=2, fine_steps=3), dict(M=257, N=9, fine_steps=11, batch=2),
+                dict(M=2000, N=4, fine_steps=5), dict(M=4095, N=2, fine_steps=3)]
+
+
+@pytest.mark.parametrize("case", HEAT1D_CASES)
+@pytest.mark.parametrize("which", ["F", "Ginv", "GinvF", "residual"])
+def test_heat1d_operators_fp64(case, which):
+    pit = _pit()
+    w = inputs.heat1d(**case)
+    X = _rand_block(w, 1)
+    with pit.Problem(w, "fp64") as p:
+        got = p.apply(which, X)
+        dev = p.apply(which, torch.from_numpy(X).cuda()).cpu().numpy()
+    ref = _oracle_apply(w, which, X)
+    assert _rel(got, ref) < 1e-13
+    np.testing.assert_array_equal(got, dev)
+
+
+@pytest.mark.parametrize("which", ["F", "GinvF"])
+def test_heat1d_operators_fp32_fine(which):
+    pit = _pit()
+    w = inputs.heat1d(M=63, N=8, fine_steps=100)
+    X = _rand_block(w, 2)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply(which, X, precision="mixed")
+    ref = _oracle_apply(w, which, X)
+    assert _rel(got, ref) < 2e-5
+
+
+def test_heat1d_bicgstab_fixed_iterations_match_oracle():
+    """Same k iterations of Algorithm 1: iterates agree to 1e-12."""
+    pit = _pit()
+    w = inputs.heat1d()
+    o = OracleProblem.from_workload(w)
+    with pit.Problem(w, "fp64") as p:
+        for k in (1, 2, 3, 5):
+            X, info = p.bicgstab_solve(tol=0.0, max_iter=k)
+            Xo, oi = pitsbicg(o, tol=0.0, max_iter=k)
+            assert info[0]["iterations"] == k and oi.iterations == k
+            assert info[0]["matvecs"] == oi.matvecs
+            assert _rel(X[0], Xo) < 1e-12
+
+
+def test_heat1d_bicgstab_converged_matches_serial_and_oracle():
+    pit = _pit()
+    w = inputs.heat1d()
+    o = OracleProblem.from_workload(w)
+    lam = o.serial_fine()
+    Xo, oi = pitsbicg(o, tol=1e-10)
+    with pit.Problem(w, "fp64") as p:
+        X, info = p.bicgstab_solve(tol=1e-10, history_len=64)
+        lam_gpu = p.serial_fine()
+    assert info[0]["status"] == 0
+    assert info[0]["iterations"] == oi.iterations
+    assert _rel(X[0], Xo) < 1e-12
+    assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-9
+    assert _rel(lam_gpu[0], lam) < 1e-13
+    h = info[0]["history"]
+    assert len(h) == oi.iterations + 1
+    np.testing.assert_allclose(h, oi.history, rtol=1e-9)
+
+
+def test_heat1d_restart_paths_match_oracle():
+    """eps0 = 1 forces the restart branch every iteration."""
+    pit = _pit()
+    w = inputs.heat1d(M=15, N=6, fine_steps=10)
+    o = OracleProblem.from_workload(w)
+    Xo, oi = pitsbicg(o, tol=1e-12, eps0=1.0, max_iter=200)
+    with pit.Problem(w, "fp64") as p:
+        X, info = p.bicgstab_solve(tol=1e-12, eps0=1.0, max_iter=200)
+    assert info[0]["restarts"] == oi.restarts and info[0]["iterations"] == oi.iterations
+    assert _rel(X[0], Xo) < 1e-12
+
+
+def test_heat1d_maxiter_and_x0_modes():
+    pit = _pit()
+    w = inputs.heat1d(M=31, N=8, fine_steps=10)
+    o = OracleProblem.from_workload(w)
+    with pit.Problem(w, "fp64") as p:
+        X, info = p.bicgstab_solve(tol=1e-30, max_iter=2)
+        assert info[0]["status"] == pit.PIT_E_MAXITER and info[0]["iterations"] == 2
+        Xz, iz = p.bicgstab_solve(tol=0.0, max_iter=3, x0="zero")
+        X0 = _rand_block(w, 5, 0.1)
+        Xg, ig = p.bicgstab_solve(X=X0.copy(), tol=0.0, max_iter=3, x0="given")
+    assert _rel(Xz[0], pitsbicg(o, tol=0.0, max_iter=3, x0="zero")[0]) < 1e-12
+    assert _rel(Xg[0], pitsbicg(o, tol=0.0, max_iter=3, x0=X0[0])[0]) < 1e-12
+
+
+def test_heat1d_parareal_matches_oracle_and_is_exact_at_N():
+    pit = _pit()
+    w = inputs.heat1d()
+    o = OracleProblem.from_workload(w)
+    lam = o.serial_fine()
+    with pit.Problem(w, "fp64") as p:
+        for k in (1, 4):
+            X, info = p.parareal_solve(kmax=k)
+            Xo, _ = parareal(o, kmax=k)
+            assert _rel(X[0], Xo) < 1e-12
+            assert _rel(X[0][:k + 1], lam[:k + 1]) < 1e-12
+        X, info = p.parareal_solve(kmax=w.N)
+    assert _rel(X[0], lam) < 1e-12
+    assert info[0]["matvecs"] == w.N + 1
+
+
+def test_heat1d_batch_members_are_independent():
+    pit = _pit()
+    w = inputs.heat1d(M=63, N=8, fine_steps=20, batch=3)
+    with pit.Problem(w, "fp64") as p:
+        X, info = p.bicgstab_solve(tol=1e-11)
+    for b in range(3):
+        with pit.Problem(w.member(b), "fp64") as p1:
+            Xb, ib = p1.bicgstab_solve(tol=1e-11)
+        np.testing.assert_array_equal(X[b], Xb[0])
+        assert info[b]["iterations"] == ib[0]["iterations"]
+
+
+# ------------------------------------------------------------------- 2D heat
+
+HEAT2D_CASES = [dict(n=16, N=4, fine_steps=5), dict(n=20, N=3, fine_steps=7),
+                dict(n=5, N=2, fine_steps=3), dict(n=37, N=3, fine_steps=4, batch=2),
+                dict(n=128, N=2, fine_steps=3), dict(n=100, N=2, fine_steps=2)]
+
+
+@pytest.mark.parametrize("case", HEAT2D_CASES)
+@pytest.mark.parametrize("which", ["F", "Ginv", "GinvF", "residual"])
+def test_heat2d_operators_fp64(case, which):
+    pit = _pit()
+    w = inputs.heat2d(**case, precision="fp64")
+    X = _rand_block(w, 3)
+    with pit.Problem(w, "fp64") as p:
+        got = p.apply(which, torch.from_numpy(X).cuda()).cpu().numpy()
+    ref = _oracle_apply(w, which, X)
+    assert _rel(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("case", HEAT2D_CASES[:4])
+@pytest.mark.parametrize("which", ["F", "Ginv"])
+def test_heat2d_operators_mixed(case, which):
+    pit = _pit()
+    w = inputs.heat2d(**case)
+    X = _rand_block(w, 4)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply(which, X, precision="mixed")
+    ref = _oracle_apply(w, which, X)
+    assert _rel(got, ref) < 2e-5
+
+
+def test_heat2d_fp64_bicgstab_fixed_iterations():
+    pit = _pit()
+    w = inputs.heat2d(n=24, N=8, fine_steps=10, precision="fp64")
+    o = OracleProblem.from_workload(w)
+    with pit.Problem(w, "fp64") as p:
+        for k in (1, 3):
+            X, info = p.bicgstab_solve(tol=0.0, max_iter=k)
+            Xo, _ = pitsbicg(o, tol=0.0, max_iter=k)
+            assert _rel(X[0], Xo) < 1e-11
+
+
+def test_heat2d_mixed_solve_reaches_serial_fp64():
+    pit = _pit()
+    w = inputs.heat2d(n=32, N=16)
+    lam = OracleProblem.from_workload(w).serial_fine()
+    with pit.Problem(w, "mixed") as p:
+        X, info = p.bicgstab_solve(tol=1e-7, history_len=16)
+    assert info[0]["status"] == 0
+    assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
+    assert info[0]["refinements"] >= 1
+
+
+def test_block_reduce_matches_numpy():
+    pit = _pit()
+    s = inputs.SeededStream(12)
+    for nb, M in ((1, 1), (5, 63), (17, 2049), (513, 300)):
+        U = s.normal(nb * M).reshape(nb, M)
+        V = s.normal(nb * M).reshape(nb, M)
+        dot, norms, ninf = pit.block_reduce(torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda(), nb, M)
+        assert dot == pytest.approx(float(np.sum(U * V)), rel=1e-12, abs=1e-12)
+        np.testing.assert_allclose(norms, np.linalg.norm(U, axis=1), rtol=1e-13)
+        assert ninf == pytest.approx(np.linalg.norm(U, axis=1).max(), rel=1e-13)
