@@ -1,0 +1,411 @@
+"""PiTSBiCG throughput on GB300: PiT solves/s at rel err <= 1e-6 against the FP64 path.
+
+Workload (default): 2D heat u_t = nu Lap u on the unit square, 128 x 128
+interior points, nu = 1e-2, T = 1, N = 512 slices, fine = 50 RK4 steps per
+slice in FP32, coarse = one implicit-Euler step, FP64 Krylov vectors and
+scalars, FP64 true residuals with iterative refinement, relative tolerance
+1e-6; initial values = 8 seeded Gaussian bumps per member.
+
+One step = one PiTSBiCG solve (Algorithm 1 with refinement) of a batch of
+independent initial values, through pit_bicgstab_solve on device-resident
+inputs.  `value` = solves/s over all ranks (weak scaling: every rank solves
+its own batch; no collective on the data path).  `e2e` = the same through the
+host-pointer C-ABI call, with the H2D copy of y0 and the D2H copy of the
+solution inside the timed region.
+
+--impl reference times the FP64 CPU oracle (test infrastructure, not the
+product) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import math
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_10148_gb300 import inputs  # noqa: E402
+
+GOLDEN_SOLVE = os.path.join(ROOT, "tests", "golden", "oracle_solve_heat2d_128_N512.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FINE_SRC = os.path.join(ROOT, "paper_2203_10148_gb300", "csrc", "heat2d.cu")
+
+FLOP_PER_POINT_STEP = 28       # RK4 Horner: 4 stages x (3 add + 2 FMA) = 4 x 7 flop
+FP32_LANES_PER_SM = 128
+FP64_FLOP_PER_CLK_PER_SM = 4   # 1.25 TFLOP/s nominal FP64 at 2.07 GHz on 152 SMs
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--N", type=int, default=512)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, rank, step=0):
+    seed = inputs.SEED_HEAT2D + 7919 * rank + 104729 * step
+    return inputs.heat2d(n=args.n, N=args.N, batch=args.batch, seed=seed, tol=1e-6)
+
+
+# ---------------------------------------------------------------- helpers
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS))
+    except Exception:
+        return None
+
+
+def src_hash(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    try:
+        t = json.load(open(TRAFFIC))
+        e = t.get(kernel)
+        if e and e.get("source_sha") == src_hash(FINE_SRC):
+            return e
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, device_index=0):
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9 or r[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(w, slices):
+    """Times the FP64 oracle's G^{-1}F on a bounded sample: the fine propagator
+    on `slices` of the N slices (scaled to N) plus one full sequential sweep."""
+    from oracle import OracleProblem
+    o = OracleProblem.from_workload(w.member(0))
+    X = np.tile(o.y0, (slices, 1))
+    t0 = time.perf_counter()
+    o.F(X)
+    t_f = (time.perf_counter() - t0) * (w.N / slices)
+    Q = np.zeros((w.N + 1, w.M))
+    Q[0] = o.y0
+    t0 = time.perf_counter()
+    o.sweep_Ginv(Q)
+    t_s = time.perf_counter() - t0
+    return t_f, t_s
+
+
+def oracle_matvecs():
+    try:
+        g = json.load(open(GOLDEN_SOLVE))
+        return int(g["matvecs"]), g
+    except Exception:
+        return None, None
+
+
+def cpu_baseline(w, slices=32):
+    mv, g = oracle_matvecs()
+    t_f, t_s = oracle_sample(w, slices)
+    t_mv = t_f + t_s
+    out = {"unit": "solves/s", "cores": 1, "kind": "oracle",
+           "sample": (f"FP64 numpy/scipy oracle, 1 thread: fine propagator on {slices} of "
+                      f"{w.N} slices (x{w.N // slices}) + one full coarse sweep = "
+                      f"{t_mv:.2f} s per G^-1F matvec; x {mv} matvecs of the oracle's own "
+                      f"Algorithm 1 solve of this workload (tests/golden)"),
+           "seconds_per_matvec": t_mv,
+           "fine_slice_steps_per_s": w.N * w.fine[1] / t_f}
+    out["value"] = (1.0 / (t_mv * mv)) if mv else None
+    return out
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args, 0)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, slices=8)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.median(vals)) if vals and vals[0] else None
+    cb["value"] = v
+    line = {"impl": "reference", "metric": "PiT solves/s (rel err <= 1e-6 vs FP64 path)",
+            "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "batch": w.batch, "grid": [w.nx, w.ny], "N": w.N,
+                       "fine": list(w.fine), "coarse": list(w.coarse), "tol": 1e-6},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world,
+                                device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_10148_gb300 import pit
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    w = workload(args, rank)
+    shape = (w.batch, w.N + 1, w.M)
+    K, W = args.steps, args.warmup
+    # distinct initial values per step, resident on the device
+    y0s = [torch.from_numpy(workload(args, rank, step=s).y0.copy()).to(dev) for s in range(K + W)]
+    prob = pit.Problem(w, "mixed")
+    X = torch.zeros(shape, dtype=torch.float64, device=dev)
+    solve_kw = dict(tol=1e-6, max_iter=200, refine_max=8, inner_tol=args.inner_tol)
+
+    def one(step):
+        prob.set_y0(y0s[step])
+        return prob.bicgstab_solve(X, stream=stream.cuda_stream, **solve_kw)[1]
+
+    with torch.cuda.stream(stream):
+        for s in range(W):
+            one(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prob.set_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    infos = []
+    launches0 = pit.kernel_launches()
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                    f"clocks_rank{rank}.csv"))
+    with clk:
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for s in range(K):
+                infos.append(one(W + s))
+                ev[s + 1].record(stream)
+        torch.cuda.synchronize()
+    launches = pit.kernel_launches() - launches0
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    timing = prob.timing()
+    prob.set_timing(False)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solves = w.batch * K * world
+    value = solves / (total_ms / 1e3)
+    slice_steps = sum(i["fine_slice_steps"] for inf in infos for i in inf) * world
+    # accuracy of the last step against the FP64 serial fine trajectory (FP64 path)
+    lam = torch.empty(shape, dtype=torch.float64, device=dev)
+    prob.serial_fine("fp64", out=lam)
+    d = (X - lam).reshape(w.batch, -1)
+    rel = (d.norm(dim=1) / lam.reshape(w.batch, -1).norm(dim=1)).max().item()
+    relN = ((X[:, -1] - lam[:, -1]).norm(dim=1) / lam[:, -1].norm(dim=1)).max().item()
+    statuses = sorted({i["status_name"] for inf in infos for i in inf})
+
+    line = None
+    if rank == 0:
+        peaks = load_peaks()
+        clocks = clk.summary(local)
+        # dominant single-kernel class and its roofline
+        fine = {k: timing[k] for k in ("fine_fp32", "fine_fp64")}
+        dom = max(fine, key=lambda k: fine[k][1])
+        calls, ms = timing[dom]
+        avg_ms = ms / max(calls, 1)
+        sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        flop = w.batch * w.N * w.fine[1] * w.M * FLOP_PER_POINT_STEP
+        if dom == "fine_fp32":
+            peak = 2 * FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12
+            kname = "k_heat2d_fine<float>"
+        else:
+            peak = FP64_FLOP_PER_CLK_PER_SM * nsm * sm_max * 1e6 / 1e12
+            kname = "k_heat2d_fine<double>"
+        achieved = flop / (avg_ms / 1e3) / 1e12
+        tr = traffic_for(kname)
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "launch_ms": avg_ms, "launches": calls,
+                "peak_source": f"derived: {'2 x 128 FP32 lanes' if dom == 'fine_fp32' else '4 FP64 flop/clk'} x {nsm} SMs x {sm_max:.0f} MHz"}
+        breakdown = {k: {"calls": c, "ms": m, "share": m / total_ms} for k, (c, m) in timing.items()}
+        line = {"metric": "PiT solves/s (rel err <= 1e-6 vs FP64 path)", "value": value,
+                "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 fine / f64 krylov", "data": "synthetic",
+                "config": {"workload": w.name, "batch_per_gpu": w.batch, "grid": [w.nx, w.ny],
+                           "N": w.N, "fine": list(w.fine), "coarse": list(w.coarse),
+                           "precision": "mixed", "tol": 1e-6, "inner_tol": args.inner_tol,
+                           "l2": "working set > L2 (9 Krylov vectors x %.0f MB)" % (w.batch * (w.N + 1) * w.M * 8 / 1e6),
+                           "parallelism": f"replicas x{world}"},
+                "fine_slice_steps_per_s": slice_steps / (total_ms / 1e3),
+                "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                               "p99": float(np.percentile(step_ms, 99))},
+                "rel_err_max": rel, "rel_err_lambda_N": relN, "status": statuses,
+                "iterations": [i["iterations"] for inf in infos for i in inf],
+                "refinements": [i["refinements"] for inf in infos for i in inf],
+                "matvecs": [i["matvecs"] for inf in infos for i in inf],
+                "gpu_launches": int(launches), "roofline": roof, "breakdown": breakdown,
+                "clocks": clocks}
+        if rel > 1e-6:
+            line["invalid"] = f"rel err {rel:.3e} > 1e-6"
+
+    # end-to-end through host buffers
+    if not args.no_e2e:
+        hx = torch.empty(shape, dtype=torch.float64).pin_memory()
+        hy0 = [torch.from_numpy(workload(args, rank, step=s).y0.copy()).pin_memory()
+               for s in range(K + W)]
+        hx_np = hx.numpy()
+
+        def one_host(step):
+            prob.set_y0(hy0[step].numpy())
+            return prob.bicgstab_solve(hx_np, **solve_kw)[1]
+
+        for s in range(W):
+            one_host(s)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for s in range(K):
+            one_host(W + s)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        if rank == 0:
+            line["e2e"] = {"value": solves / e2e_s, "unit": "solves/s",
+                           "h2d_bytes_per_step": w.batch * w.M * 8,
+                           "d2h_bytes_per_step": w.batch * (w.N + 1) * w.M * 8}
+
+    # the plain FP64 GPU path on the same workload, for comparison
+    if rank == 0 and not args.no_fp64_path:
+        w1 = workload(args, 0)
+        p64 = pit.Problem(w1.member(0), "fp64")
+        X64 = torch.zeros((1, w1.N + 1, w1.M), dtype=torch.float64, device=dev)
+        p64.bicgstab_solve(X64, tol=1e-6, max_iter=200)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, i64 = p64.bicgstab_solve(X64, tol=1e-6, max_iter=200)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        lam64 = torch.empty_like(X64)
+        p64.serial_fine("fp64", out=lam64)
+        e64 = ((X64 - lam64).norm() / lam64.norm()).item()
+        line["fp64_path"] = {"value": 1.0 / t64, "unit": "solves/s", "iterations": i64[0]["iterations"],
+                             "matvecs": i64[0]["matvecs"], "rel_err": e64}
+        p64.close()
+
+    if rank == 0 and not args.no_cpu:
+        try:
+            line["cpu_baseline"] = cpu_baseline(workload(args, 0))
+        except Exception as e:  # the baseline is context; never fail the bench line
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1,
+                                    "kind": "oracle", "sample": f"failed: {e}"}
+    prob.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -221,6 +221,37 @@ pit_status pit_parareal_solve(pit_problem_t prob, int kmax, double tol, double *
 pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M,
                             double *dot, double *norms, double *norm_inf);
 
+/*
+ * Replaces the initial values y0 (batch * M doubles, host or device) of an
+ * existing problem; the operator and its set-up are kept.  Synchronous.
+ * Errors: PIT_E_INVALID, PIT_E_NONFINITE (host arrays only), PIT_E_CUDA.
+ */
+pit_status pit_problem_set_y0(pit_problem_t prob, const double *y0, int on_device);
+
+/* ---------------------------------------------------------- diagnostics */
+
+/* Number of kernels libpit has launched in this process (all problems). */
+unsigned long long pit_kernel_launches(void);
+
+/* Operator classes timed by pit_get_timing. */
+#define PIT_TIME_FINE_FP32   0   /* fine batch, FP32 stepping (one kernel per call) */
+#define PIT_TIME_FINE_FP64   1   /* fine batch, FP64 stepping (one kernel per call) */
+#define PIT_TIME_SWEEP_MIXED 2   /* coarse sweep, FP32 transforms */
+#define PIT_TIME_SWEEP_FP64  3   /* coarse sweep, FP64 */
+#define PIT_TIME_KRYLOV      4   /* fused BiCGStab vector kernels and finishers */
+#define PIT_TIME_CLASSES     5
+
+/*
+ * enable = 1: every later operator application of this problem is bracketed
+ * by CUDA events on the stream it runs on, and the elapsed times are summed
+ * per class; enable = 0 stops recording.  Resets the sums.
+ */
+pit_status pit_set_timing(pit_problem_t prob, int enable);
+
+/* Calls and summed milliseconds of one class since pit_set_timing(prob, 1).
+ * Synchronises the problem's pending events. */
+pit_status pit_get_timing(pit_problem_t prob, int cls, long long *calls, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

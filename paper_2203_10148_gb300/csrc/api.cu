@@ -16,6 +16,8 @@
 
 namespace pit {
 
+std::atomic<unsigned long long> g_launches{0};
+
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
 
@@ -54,6 +56,81 @@ void DevBuf::release() {
     ptr = nullptr;
     bytes = 0;
 }
+
+// ------------------------------------------------------------ op timing
+cudaEvent_t OpTimer::get() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+pit_status OpTimer::begin(int cls, cudaStream_t s, Rec &r) {
+    if (pending.size() > 4096) PIT_TRY(resolve());
+    r.cls = cls;
+    r.a = get();
+    r.b = get();
+    if (!r.a || !r.b) {
+        set_error("cudaEventCreate failed");
+        return PIT_E_CUDA;
+    }
+    PIT_CUDA(cudaEventRecord(r.a, s));
+    return PIT_OK;
+}
+
+pit_status OpTimer::end(Rec &r, cudaStream_t s) {
+    PIT_CUDA(cudaEventRecord(r.b, s));
+    pending.push_back(r);
+    return PIT_OK;
+}
+
+pit_status OpTimer::resolve() {
+    for (Rec &r : pending) {
+        PIT_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        PIT_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.cls] += t;
+        calls[r.cls] += 1;
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    pending.clear();
+    return PIT_OK;
+}
+
+void OpTimer::reset() {
+    for (Rec &r : pending) {
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    pending.clear();
+    for (int i = 0; i < PIT_TIME_CLASSES; ++i) {
+        calls[i] = 0;
+        ms[i] = 0.0;
+    }
+}
+
+void OpTimer::destroy() {
+    reset();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+}
+
+#define PIT_TIMED(p, cls, s, call)                                            \
+    do {                                                                      \
+        ::pit::OpTimer::Rec r_{};                                             \
+        const bool on_ = (p)->timer.enabled;                                  \
+        if (on_) PIT_TRY((p)->timer.begin((cls), (s), r_));                   \
+        PIT_TRY(call);                                                        \
+        if (on_) PIT_TRY((p)->timer.end(r_, (s)));                            \
+    } while (0)
+
+static int fine_cls(int prec) { return prec == PIT_FP64 ? PIT_TIME_FINE_FP64 : PIT_TIME_FINE_FP32; }
+static int sweep_cls(int prec) { return prec == PIT_FP64 ? PIT_TIME_SWEEP_FP64 : PIT_TIME_SWEEP_MIXED; }
 
 // --------------------------------------------------------- operator switch
 pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
@@ -109,10 +186,22 @@ pit_status op_serial(Problem *p, double *Lam, int prec, cudaStream_t s) {
 // Sweep arithmetic: FP64 for FP64, FP32 transforms / FP64 running sums otherwise.
 static int sweep_prec(int prec) { return prec == PIT_FP64 ? PIT_FP64 : PIT_MIXED; }
 
+static pit_status timed_F(Problem *p, const double *x, double *y, int mode, int prec,
+                          const MemberState *st, cudaStream_t s) {
+    PIT_TIMED(p, fine_cls(prec), s, op_apply_F(p, x, y, mode, prec, st, s));
+    return PIT_OK;
+}
+
+static pit_status timed_sweep(Problem *p, const double *q, double *z, int prec,
+                              const MemberState *st, cudaStream_t s) {
+    PIT_TIMED(p, sweep_cls(sweep_prec(prec)), s, op_sweep(p, q, z, sweep_prec(prec), st, s));
+    return PIT_OK;
+}
+
 static pit_status apply_GinvF(Problem *p, const double *x, double *y, int prec,
                               const MemberState *st, cudaStream_t s) {
-    PIT_TRY(op_apply_F(p, x, y, FINE_APPLY, prec, st, s));
-    return op_sweep(p, y, y, sweep_prec(prec), st, s);
+    PIT_TRY(timed_F(p, x, y, FINE_APPLY, prec, st, s));
+    return timed_sweep(p, y, y, prec, st, s);
 }
 
 // ------------------------------------------------------------ the engine
@@ -159,10 +248,10 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, double abs_thresh,
     double *X = p->X.as<double>(), *R = p->R.as<double>();
     MemberState *st = p->states.as<MemberState>();
     if (!r_given) {
-        PIT_TRY(op_apply_F(p, X, R, FINE_RESIDUAL, prec, nullptr, s));
-        PIT_TRY(op_sweep(p, R, R, sweep_prec(prec), nullptr, s));
+        PIT_TRY(timed_F(p, X, R, FINE_RESIDUAL, prec, nullptr, s));
+        PIT_TRY(timed_sweep(p, R, R, prec, nullptr, s));
     }
-    PIT_TRY(kr_init(p, tol_rel, abs_thresh, eps0, max_iter, s));
+    PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_init(p, tol_rel, abs_thresh, eps0, max_iter, s));
     HostStates hs;
     PIT_TRY(hs.init(p->batch));
     int hc = history_offset;
@@ -177,12 +266,12 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, double abs_thresh,
         }
         if (!hs.any_active()) break;
         PIT_TRY(apply_GinvF(p, p->P.as<double>(), p->D.as<double>(), prec, st, s));   // D = G^-1 F P
-        PIT_TRY(kr_sigma(p, s));                                                      // alpha
-        PIT_TRY(kr_update_S(p, s));                                                   // S = R - alpha D
+        PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_sigma(p, s));                             // alpha
+        PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_update_S(p, s));                          // S = R - alpha D
         PIT_TRY(apply_GinvF(p, p->S.as<double>(), p->K.as<double>(), prec, st, s));   // K = G^-1 F S
-        PIT_TRY(kr_omega(p, s));                                                      // omega
-        PIT_TRY(kr_update_XR(p, s));                                                  // X, R, beta
-        PIT_TRY(kr_update_P(p, s));                                                   // P
+        PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_omega(p, s));                             // omega
+        PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_update_XR(p, s));                         // X, R, beta
+        PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_update_P(p, s));                          // P
     }
     PIT_TRY(hs.fetch(p, s));
     out.final_states = hs.v;
@@ -377,6 +466,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp};
     for (DevBuf *b : bufs) b->release();
+    p->timer.destroy();
     if (p->stream) cudaStreamDestroy(p->stream);
     delete h;
     return PIT_OK;
@@ -516,8 +606,8 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
         int hc = 0;
         const int rounds = std::max(1, o->refine_max);
         for (int round = 0; round <= rounds; ++round) {
-            PIT_TRY(op_apply_F(p, Xo, Wr, FINE_RESIDUAL, PIT_FP64, nullptr, s));
-            PIT_TRY(op_sweep(p, Wr, Wr, PIT_MIXED, nullptr, s));
+            PIT_TRY(timed_F(p, Xo, Wr, FINE_RESIDUAL, PIT_FP64, nullptr, s));
+            PIT_TRY(timed_sweep(p, Wr, Wr, PIT_MIXED, nullptr, s));
             PIT_TRY(member_norms(p, Wr, rtrue, s));
             bool any = false;
             for (int b = 0; b < B; ++b) {
@@ -605,8 +695,8 @@ pit_status pit_parareal_solve(pit_problem_t h, int kmax, double tol, double *Xu,
     std::vector<double> rn, r0(B, 0.0);
     const long long steps_per_matvec = (long long)p->N * p->fine_steps;
     for (int k = 0;; ++k) {
-        PIT_TRY(op_apply_F(p, X, Wr, FINE_RESIDUAL, PIT_FP64, nullptr, s));
-        PIT_TRY(op_sweep(p, Wr, Wr, sp, nullptr, s));
+        PIT_TRY(timed_F(p, X, Wr, FINE_RESIDUAL, PIT_FP64, nullptr, s));
+        PIT_TRY(timed_sweep(p, Wr, Wr, sp, nullptr, s));
         PIT_TRY(member_norms(p, Wr, rn, s));
         bool any = false;
         for (int b = 0; b < B; ++b) {
@@ -644,6 +734,48 @@ pit_status pit_parareal_solve(pit_problem_t h, int kmax, double tol, double *Xu,
     }
     if (info) std::copy(inf.begin(), inf.end(), info);
     return worst_status(status);
+}
+
+pit_status pit_problem_set_y0(pit_problem_t h, const double *y0, int on_device) {
+    if (!h || !y0) {
+        set_error("pit_problem_set_y0: null argument");
+        return PIT_E_INVALID;
+    }
+    Problem *p = &h->p;
+    const size_t n = (size_t)p->M * p->batch;
+    if (!on_device && !all_finite(y0, n)) {
+        set_error("pit_problem_set_y0: non-finite value in y0");
+        return PIT_E_NONFINITE;
+    }
+    PIT_CUDA(cudaSetDevice(p->device));
+    PIT_CUDA(cudaMemcpyAsync(p->y0.ptr, y0, n * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             p->stream));
+    PIT_CUDA(cudaStreamSynchronize(p->stream));
+    return PIT_OK;
+}
+
+unsigned long long pit_kernel_launches(void) { return g_launches.load(); }
+
+pit_status pit_set_timing(pit_problem_t h, int enable) {
+    if (!h) {
+        set_error("pit_set_timing: null problem");
+        return PIT_E_INVALID;
+    }
+    h->p.timer.reset();
+    h->p.timer.enabled = enable != 0;
+    return PIT_OK;
+}
+
+pit_status pit_get_timing(pit_problem_t h, int cls, long long *calls, double *ms) {
+    if (!h || cls < 0 || cls >= PIT_TIME_CLASSES) {
+        set_error("pit_get_timing: bad argument");
+        return PIT_E_INVALID;
+    }
+    PIT_TRY(h->p.timer.resolve());
+    if (calls) *calls = h->p.timer.calls[cls];
+    if (ms) *ms = h->p.timer.ms[cls];
+    return PIT_OK;
 }
 
 pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M, double *dot,

@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
+#include <vector>
 
 #include "pit.h"
 
@@ -26,7 +28,13 @@ pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line
         if (s_ != PIT_OK) return s_;                                          \
     } while (0)
 
-#define PIT_LAUNCH_CHECK() PIT_CUDA(cudaGetLastError())
+extern std::atomic<unsigned long long> g_launches;
+
+#define PIT_LAUNCH_CHECK()                                                    \
+    do {                                                                      \
+        g_launches.fetch_add(1, std::memory_order_relaxed);                   \
+        PIT_CUDA(cudaGetLastError());                                         \
+    } while (0)
 
 // ------------------------------------------------------- device buffers
 struct DevBuf {
@@ -71,6 +79,25 @@ struct ReduceLayout {
     int chunk;    // elements per chunk
 };
 
+// Event timing of operator applications (diagnostics).
+struct OpTimer {
+    bool enabled = false;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    long long calls[PIT_TIME_CLASSES] = {};
+    double ms[PIT_TIME_CLASSES] = {};
+    cudaEvent_t get();
+    pit_status begin(int cls, cudaStream_t s, Rec &r);
+    pit_status end(Rec &r, cudaStream_t s);
+    pit_status resolve();
+    void reset();
+    void destroy();
+};
+
 // ---------------------------------------------------------------- problem
 struct Problem {
     // description
@@ -107,6 +134,7 @@ struct Problem {
     DevBuf partials, states, flags_host_mirror;
     DevBuf fine_tmp;              // serial / misc scratch
     ReduceLayout rl{};
+    OpTimer timer;
 };
 
 // Modes of the fused block-operator epilogue.

@@ -75,7 +75,10 @@ class PitError(RuntimeError):
 # every symbol declared in include/pit.h
 EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_create",
            "pit_problem_destroy", "pit_problem_shape", "pit_apply_operator", "pit_serial_fine",
-           "pit_bicgstab_solve", "pit_parareal_solve", "pit_block_reduce"]
+           "pit_bicgstab_solve", "pit_parareal_solve", "pit_block_reduce",
+           "pit_problem_set_y0", "pit_kernel_launches", "pit_set_timing", "pit_get_timing"]
+
+TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4}
 
 
 def lib_path() -> str:
@@ -106,8 +109,13 @@ def load() -> C.CDLL:
     lib.pit_bicgstab_solve.argtypes = [P, C.POINTER(SolveOpts), P, C.c_int, C.POINTER(SolveInfo)]
     lib.pit_parareal_solve.argtypes = [P, C.c_int, C.c_double, P, C.c_int, C.POINTER(SolveInfo)]
     lib.pit_block_reduce.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
+    lib.pit_problem_set_y0.argtypes = [P, P, C.c_int]
+    lib.pit_kernel_launches.argtypes = []
+    lib.pit_kernel_launches.restype = C.c_ulonglong
+    lib.pit_set_timing.argtypes = [P, C.c_int]
+    lib.pit_get_timing.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
     for name in EXPORTS:
-        if name not in ("pit_default_opts", "pit_version", "pit_last_error"):
+        if name not in ("pit_default_opts", "pit_version", "pit_last_error", "pit_kernel_launches"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -255,6 +263,23 @@ class Problem:
             out[0]["history"] = hist[:out[0]["history_count"]].tolist()
         return X, out
 
+    def set_y0(self, y0):
+        """pit_problem_set_y0: new initial values (batch x M), host or device."""
+        p, dev, _ = _array_arg(y0)
+        check(load().pit_problem_set_y0(self.handle, p, dev))
+
+    def set_timing(self, enable: bool = True):
+        check(load().pit_set_timing(self.handle, int(enable)))
+
+    def timing(self) -> dict:
+        """{class: (calls, milliseconds)} since set_timing(True)."""
+        out = {}
+        for name, cls in TIME_CLASSES.items():
+            calls, ms = C.c_longlong(), C.c_double()
+            check(load().pit_get_timing(self.handle, cls, C.byref(calls), C.byref(ms)))
+            out[name] = (calls.value, ms.value)
+        return out
+
     def parareal_solve(self, kmax: int, tol: float = 0.0, X=None):
         lib = load()
         if X is None:
@@ -265,6 +290,10 @@ class Problem:
         if st in (PIT_E_INVALID, PIT_E_NOMEM, PIT_E_CUDA, PIT_E_UNSUPPORTED):
             check(st)
         return X, [i.as_dict() for i in infos]
+
+
+def kernel_launches() -> int:
+    return int(load().pit_kernel_launches())
 
 
 def block_reduce(U, V, nblocks: int, M: int):
