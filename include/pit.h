@@ -222,6 +222,25 @@ pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M
                             double *dot, double *norms, double *norm_inf);
 
 /*
+ * Allocation-free variant of pit_block_reduce, with the same arguments,
+ * results and synchronisation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory, for
+ * instance a process whose device memory is all reserved by another
+ * allocator (so cudaMalloc would fail), or a latency-bound thread that
+ * cannot pay for cudaMalloc/cudaFree.  The partial sums live in a fixed
+ * 1 MiB array compiled into the library, which every device that loads the
+ * library keeps until the process exits; it holds nblocks * ceil(M/2048)
+ * <= 65536 chunks, and larger sizes return PIT_E_INVALID without touching
+ * the device.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (from several threads or streams) race and must be
+ * serialised by the caller.  Nothing in the array needs to start at zero.
+ */
+pit_status pit_block_reduce_noalloc(const double *U, const double *V, int nblocks, int M,
+                                    double *dot, double *norms, double *norm_inf);
+
+/*
  * Replaces the initial values y0 (batch * M doubles, host or device) of an
  * existing problem; the operator and its set-up are kept.  Synchronous.
  * Errors: PIT_E_INVALID, PIT_E_NONFINITE (host arrays only), PIT_E_CUDA.

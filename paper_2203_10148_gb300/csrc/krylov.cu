@@ -9,6 +9,9 @@
 // Euclidean products of all N+1 blocks.  ||.||_{N,inf} (Algorithm 1, the
 // while test): the largest Euclidean block norm.
 #include <math.h>
+#include <stdio.h>
+
+#include <mutex>
 
 #include "pit_internal.h"
 
@@ -572,3 +575,82 @@ pit_status block_reduce(const double *U, const double *V, int nblocks, int M, do
 }
 
 }  // namespace pit
+
+// ------------------------------------------------ allocation-free variant
+// pit_block_reduce_noalloc: the same two kernels as pit_block_reduce, but
+// the partial sums live in a fixed array compiled into the library instead
+// of memory allocated per call.  Meant for callers that may not allocate
+// device memory: a process whose device memory is entirely handed to another
+// allocator (so cudaMalloc would fail), or a latency-bound host thread that
+// cannot afford cudaMalloc/cudaFree and the device-wide synchronisation
+// cudaFree implies.
+namespace pit {
+namespace {
+
+// Two partial sums per chunk of CHUNK values, per block: 131072 doubles
+// (1 MiB) hold nblocks * ceil(M / 2048) <= 65536 chunks.  Every device that
+// loads the library keeps this array until the process exits.
+constexpr size_t NOALLOC_DOUBLES = 131072;
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_partials on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+pit_status noalloc_scratch(double **out) {
+    int dev = 0;
+    PIT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_error("pit_block_reduce_noalloc: device ordinal out of range");
+        return PIT_E_INVALID;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *addr = nullptr;
+        PIT_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_partials));
+        g_noalloc_addr[dev] = static_cast<double *>(addr);
+    }
+    *out = g_noalloc_addr[dev];
+    return PIT_OK;
+}
+
+}  // namespace
+}  // namespace pit
+
+extern "C" pit_status pit_block_reduce_noalloc(const double *U, const double *V, int nblocks,
+                                               int M, double *dot, double *norms,
+                                               double *norm_inf) {
+    using namespace pit;
+    if (!U || !V || !dot || !norm_inf || nblocks < 1 || M < 1) {
+        set_error("pit_block_reduce_noalloc: bad argument");
+        return PIT_E_INVALID;
+    }
+    VecGeom g;
+    g.M = M;
+    g.nblk = nblocks;
+    g.chunks = (M + CHUNK - 1) / CHUNK;
+    g.blen = (size_t)nblocks * M;
+    const size_t need = (size_t)2 * nblocks * g.chunks;
+    if (need > NOALLOC_DOUBLES) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "pit_block_reduce_noalloc: nblocks * ceil(M/2048) = %zu chunks exceeds the "
+                 "fixed scratch of %zu chunks; use pit_block_reduce",
+                 need / 2, NOALLOC_DOUBLES / 2);
+        set_error(buf);
+        return PIT_E_INVALID;
+    }
+    double *part = nullptr;
+    PIT_TRY(noalloc_scratch(&part));
+    // every partial read by k_reduce_final is written by k_dot2 in this call,
+    // so the array needs no clearing between calls
+    k_dot2<<<dim3(g.chunks, g.nblk, 1), VT, 0, 0>>>(g, U, V, part, nullptr);
+    PIT_LAUNCH_CHECK();
+    k_reduce_final<<<1, FT, 0, 0>>>(g, part, dot, norms, norm_inf);
+    PIT_LAUNCH_CHECK();
+    PIT_CUDA(cudaStreamSynchronize(0));
+    return PIT_OK;
+}

@@ -76,7 +76,8 @@ class PitError(RuntimeError):
 EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_create",
            "pit_problem_destroy", "pit_problem_shape", "pit_apply_operator", "pit_serial_fine",
            "pit_bicgstab_solve", "pit_parareal_solve", "pit_block_reduce",
-           "pit_problem_set_y0", "pit_kernel_launches", "pit_set_timing", "pit_get_timing"]
+           "pit_problem_set_y0", "pit_kernel_launches", "pit_set_timing", "pit_get_timing",
+           "pit_block_reduce_noalloc"]
 
 TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4}
 
@@ -109,6 +110,7 @@ def load() -> C.CDLL:
     lib.pit_bicgstab_solve.argtypes = [P, C.POINTER(SolveOpts), P, C.c_int, C.POINTER(SolveInfo)]
     lib.pit_parareal_solve.argtypes = [P, C.c_int, C.c_double, P, C.c_int, C.POINTER(SolveInfo)]
     lib.pit_block_reduce.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
+    lib.pit_block_reduce_noalloc.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
     lib.pit_problem_set_y0.argtypes = [P, P, C.c_int]
     lib.pit_kernel_launches.argtypes = []
     lib.pit_kernel_launches.restype = C.c_ulonglong
@@ -296,8 +298,9 @@ def kernel_launches() -> int:
     return int(load().pit_kernel_launches())
 
 
-def block_reduce(U, V, nblocks: int, M: int):
-    """pit_block_reduce on CUDA tensors: (dot, per-block norms, max block norm)."""
+def block_reduce(U, V, nblocks: int, M: int, noalloc: bool = False):
+    """pit_block_reduce (or pit_block_reduce_noalloc) on CUDA tensors:
+    (dot, per-block norms, max block norm)."""
     import torch
     pu, du, _ = _array_arg(U)
     pv, dv, _ = _array_arg(V)
@@ -305,6 +308,7 @@ def block_reduce(U, V, nblocks: int, M: int):
         raise ValueError("pit_block_reduce takes device tensors")
     out = torch.zeros(2 + nblocks, dtype=torch.float64, device=U.device)
     base = out.data_ptr()
-    check(load().pit_block_reduce(pu, pv, nblocks, M, base, base + 16, base + 8))
+    fn = load().pit_block_reduce_noalloc if noalloc else load().pit_block_reduce
+    check(fn(pu, pv, nblocks, M, base, base + 16, base + 8))
     o = out.cpu().numpy()
     return float(o[0]), o[2:], float(o[1])
