@@ -44,8 +44,14 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FINE_SRC = os.path.join(ROOT, "paper_2203_10148_gb300", "csrc", "heat2d.cu")
 
 FLOP_PER_POINT_STEP = 28       # RK4 Horner: 4 stages x (3 add + 2 FMA) = 4 x 7 flop
+# pipe operations per point and fine step (FADD, FMUL, FFMA count one each):
+# FP32 4 stages x 5; float-float 4 stages x 64 FP32 ops (3 + 1 TwoSum-based
+# additions of 11, an exact scaling of 2, a product of 7); FP64 4 x 5 FP64 ops
+OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 256, "fine_fp64": 20}
 FP32_LANES_PER_SM = 128
-FP64_FLOP_PER_CLK_PER_SM = 4   # 1.25 TFLOP/s nominal FP64 at 2.07 GHz on 152 SMs
+FP64_LANES_PER_SM = 2          # 1.25 TFLOP/s nominal FP64 = 2 FMA/clk/SM at 2.07 GHz x 152 SMs
+KERNEL_NAMES = {"fine_fp32": "k_heat2d_fine<float>", "fine_ff": "k_heat2d_fine<ff>",
+                "fine_fp64": "k_heat2d_fine<double>"}
 
 
 def parse():
@@ -60,7 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
-    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--tol", type=float, default=1e-7,
+                    help="tolerance relative to ||G^-1 B|| (error target 1e-6)")
     return ap.parse_args()
 
 
@@ -244,7 +252,8 @@ def run_ours(args):
     y0s = [torch.from_numpy(workload(args, rank, step=s).y0.copy()).to(dev) for s in range(K + W)]
     prob = pit.Problem(w, "mixed")
     X = torch.zeros(shape, dtype=torch.float64, device=dev)
-    solve_kw = dict(tol=1e-6, max_iter=200, refine_max=8, inner_tol=args.inner_tol)
+    solve_kw = dict(tol=args.tol, tol_mode="rhs", max_iter=200, refine_max=8,
+                    inner_tol=args.inner_tol, residual_precision="ff")
 
     def one(step):
         prob.set_y0(y0s[step])
@@ -294,27 +303,32 @@ def run_ours(args):
     if rank == 0:
         peaks = load_peaks()
         clocks = clk.summary(local)
-        # dominant single-kernel class and its roofline
-        fine = {k: timing[k] for k in ("fine_fp32", "fine_fp64")}
+        # dominant single-kernel class and its roofline (FP32 / FP64 pipe operations)
+        fine = {k: timing[k] for k in ("fine_fp32", "fine_ff", "fine_fp64")}
         dom = max(fine, key=lambda k: fine[k][1])
         calls, ms = timing[dom]
         avg_ms = ms / max(calls, 1)
         sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        flop = w.batch * w.N * w.fine[1] * w.M * FLOP_PER_POINT_STEP
-        if dom == "fine_fp32":
-            peak = 2 * FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12
-            kname = "k_heat2d_fine<float>"
-        else:
-            peak = FP64_FLOP_PER_CLK_PER_SM * nsm * sm_max * 1e6 / 1e12
-            kname = "k_heat2d_fine<double>"
-        achieved = flop / (avg_ms / 1e3) / 1e12
+        point_steps = w.batch * w.N * w.fine[1] * w.M
+        lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
+        peak = lanes * nsm * sm_max * 1e6 / 1e12
+        achieved = point_steps * OPS_PER_POINT_STEP[dom] / (avg_ms / 1e3) / 1e12
+        kname = KERNEL_NAMES[dom]
         tr = traffic_for(kname)
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
+                "unit": "Tops/s (%s pipe lane-ops)" % ("FP64" if dom == "fine_fp64" else "FP32"),
+                "frac": achieved / peak,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "algorithmic_bytes": 2 * 8 * point_steps // (w.fine[1]),
                 "launch_ms": avg_ms, "launches": calls,
-                "peak_source": f"derived: {'2 x 128 FP32 lanes' if dom == 'fine_fp32' else '4 FP64 flop/clk'} x {nsm} SMs x {sm_max:.0f} MHz"}
+                "flop_rate_tflops": point_steps * FLOP_PER_POINT_STEP / (avg_ms / 1e3) / 1e12,
+                "peak_source": f"derived: {lanes} lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz (max SM clock)"}
+        f32 = timing["fine_fp32"]
+        if f32[0]:
+            a32 = point_steps * OPS_PER_POINT_STEP["fine_fp32"] / (f32[1] / f32[0] / 1e3) / 1e12
+            roof["fine_fp32"] = {"launch_ms": f32[1] / f32[0], "achieved": a32,
+                                 "frac": a32 / (FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12)}
         breakdown = {k: {"calls": c, "ms": m, "share": m / total_ms} for k, (c, m) in timing.items()}
         line = {"metric": "PiT solves/s (rel err <= 1e-6 vs FP64 path)", "value": value,
                 "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -322,7 +336,8 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32 fine / f64 krylov", "data": "synthetic",
                 "config": {"workload": w.name, "batch_per_gpu": w.batch, "grid": [w.nx, w.ny],
                            "N": w.N, "fine": list(w.fine), "coarse": list(w.coarse),
-                           "precision": "mixed", "tol": 1e-6, "inner_tol": args.inner_tol,
+                           "precision": "mixed", "tol": args.tol, "tol_mode": "rhs",
+                           "inner_tol": args.inner_tol, "true_residual": "float-float",
                            "l2": "working set > L2 (9 Krylov vectors x %.0f MB)" % (w.batch * (w.N + 1) * w.M * 8 / 1e6),
                            "parallelism": f"replicas x{world}"},
                 "fine_slice_steps_per_s": slice_steps / (total_ms / 1e3),
@@ -372,10 +387,10 @@ def run_ours(args):
         w1 = workload(args, 0)
         p64 = pit.Problem(w1.member(0), "fp64")
         X64 = torch.zeros((1, w1.N + 1, w1.M), dtype=torch.float64, device=dev)
-        p64.bicgstab_solve(X64, tol=1e-6, max_iter=200)
+        p64.bicgstab_solve(X64, tol=args.tol, tol_mode="rhs", max_iter=200)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, i64 = p64.bicgstab_solve(X64, tol=1e-6, max_iter=200)
+        _, i64 = p64.bicgstab_solve(X64, tol=args.tol, tol_mode="rhs", max_iter=200)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         lam64 = torch.empty_like(X64)

@@ -69,8 +69,13 @@ typedef int pit_status;
 /* Arithmetic of the fine propagator. */
 #define PIT_FP64            0   /* FP64 throughout */
 #define PIT_MIXED           1   /* FP32 fine stepping (split-precision tensor-core GEMM for
-                                   PIT_OP_DENSE), FP64 Krylov vectors and scalars, FP64
-                                   true residuals with iterative refinement */
+                                   PIT_OP_DENSE), FP64 Krylov vectors and scalars, true
+                                   residuals in PIT_FF (HEAT2D) or FP64 with iterative
+                                   refinement */
+#define PIT_FF              2   /* float-float fine stepping: each value an unevaluated sum
+                                   of two FP32 numbers (about 48 significant bits) on the
+                                   FP32 pipe, FP64 inputs and outputs; HEAT2D only, other
+                                   operators treat it as PIT_FP64 */
 
 /* pit_apply_operator: which operator. */
 #define PIT_APPLY_F         1   /* y = F x, the block operator of eq. (4) */
@@ -122,7 +127,14 @@ typedef struct {
     double *history;       /* optional host array: ||R^k||_{N,inf} of member 0 per
                               iteration (PIT_FP64) or per refinement round (PIT_MIXED) */
     int history_len;
+    int residual_precision; /* PIT_MIXED: arithmetic of the fine propagations inside the
+                               true residual, PIT_FF (default) or PIT_FP64 */
+    int tol_mode;          /* PIT_TOL_R0 (default) or PIT_TOL_RHS */
 } pit_solve_opts;
+
+/* Reference of the relative tolerance. */
+#define PIT_TOL_R0          0   /* tol * ||R^0||_{N,inf}, R^0 the first (true) residual */
+#define PIT_TOL_RHS         1   /* tol * ||G^{-1} B||_{N,inf}, independent of X^0 */
 
 typedef struct {
     int iterations;        /* BiCGStab iterations (summed over refinement rounds) */
@@ -138,7 +150,8 @@ typedef struct {
 } pit_solve_info;
 
 /* Fills *opts with defaults: tol 1e-10, eps0 1e-8, max_iter 500, X0 coarse,
- * refine_max 8, inner_tol 1e-4, default stream, no history. */
+ * refine_max 8, inner_tol 1e-4, default stream, no history, float-float
+ * true residuals, tolerance relative to ||R^0||. */
 void pit_default_opts(pit_solve_opts *opts);
 
 /* Version string of the library. */
@@ -171,9 +184,9 @@ pit_status pit_problem_shape(pit_problem_t prob, int *M, int *N, int *batch);
  * Applies one operator to a block vector x, writing y (both batch*(N+1)*M):
  * PIT_APPLY_F (eq. (4)), PIT_APPLY_GINV (eq. (7) right, sequential in n),
  * PIT_APPLY_GINV_F (eq. (8)), PIT_APPLY_RESIDUAL (G^{-1}(B - F x)).
- * precision selects the fine arithmetic (PIT_FP64 or PIT_MIXED = FP32 fine
- * stepping from FP64 inputs); G^{-1} is FP64 for PIT_FP64 and FP32
- * transforms with FP64 accumulation for PIT_MIXED.  x and y may not overlap.
+ * precision selects the fine arithmetic (PIT_FP64, PIT_MIXED = FP32 fine
+ * stepping from FP64 inputs, or PIT_FF); G^{-1} is FP32 transforms with FP64
+ * accumulation for PIT_MIXED and FP64 otherwise.  x and y may not overlap.
  * With on_device = 0 the call copies through device memory and synchronises.
  */
 pit_status pit_apply_operator(pit_problem_t prob, int which, int precision,
@@ -258,7 +271,8 @@ unsigned long long pit_kernel_launches(void);
 #define PIT_TIME_SWEEP_MIXED 2   /* coarse sweep, FP32 transforms */
 #define PIT_TIME_SWEEP_FP64  3   /* coarse sweep, FP64 */
 #define PIT_TIME_KRYLOV      4   /* fused BiCGStab vector kernels and finishers */
-#define PIT_TIME_CLASSES     5
+#define PIT_TIME_FINE_FF     5   /* fine batch, float-float stepping (one kernel per call) */
+#define PIT_TIME_CLASSES     6
 
 /*
  * enable = 1: every later operator application of this problem is bracketed

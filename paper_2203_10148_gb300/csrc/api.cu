@@ -129,12 +129,15 @@ void OpTimer::destroy() {
         if (on_) PIT_TRY((p)->timer.end(r_, (s)));                            \
     } while (0)
 
-static int fine_cls(int prec) { return prec == PIT_FP64 ? PIT_TIME_FINE_FP64 : PIT_TIME_FINE_FP32; }
-static int sweep_cls(int prec) { return prec == PIT_FP64 ? PIT_TIME_SWEEP_FP64 : PIT_TIME_SWEEP_MIXED; }
+static int fine_cls(int prec) {
+    return prec == PIT_FP64 ? PIT_TIME_FINE_FP64 : prec == PIT_FF ? PIT_TIME_FINE_FF : PIT_TIME_FINE_FP32;
+}
+static int sweep_cls(int prec) { return prec == PIT_MIXED ? PIT_TIME_SWEEP_MIXED : PIT_TIME_SWEEP_FP64; }
 
 // --------------------------------------------------------- operator switch
 pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                       const MemberState *st, cudaStream_t s) {
+    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_apply_F(p, x, y, mode, prec, st, s);
     case PIT_OP_HEAT2D: return heat2d_apply_F(p, x, y, mode, prec, st, s);
@@ -158,6 +161,7 @@ pit_status op_sweep(Problem *p, const double *q, double *z, int prec, const Memb
 }
 
 static pit_status fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
+    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_fine_one(p, x, y, prec, s);
     case PIT_OP_HEAT2D: return heat2d_fine_one(p, x, y, prec, s);
@@ -183,8 +187,8 @@ pit_status op_serial(Problem *p, double *Lam, int prec, cudaStream_t s) {
     return PIT_OK;
 }
 
-// Sweep arithmetic: FP64 for FP64, FP32 transforms / FP64 running sums otherwise.
-static int sweep_prec(int prec) { return prec == PIT_FP64 ? PIT_FP64 : PIT_MIXED; }
+// Sweep arithmetic: FP32 transforms / FP64 running sums for PIT_MIXED, FP64 otherwise.
+static int sweep_prec(int prec) { return prec == PIT_MIXED ? PIT_MIXED : PIT_FP64; }
 
 static pit_status timed_F(Problem *p, const double *x, double *y, int mode, int prec,
                           const MemberState *st, cudaStream_t s) {
@@ -242,8 +246,8 @@ struct LoopOut {
 // Algorithm 1 on the workspace: X holds X^0.  If r_given, R already holds
 // R^0 (inner solves of the refinement); otherwise R^0 = G^{-1}(B - F X^0) is
 // computed here in precision `prec`.
-pit_status run_bicgstab(Problem *p, int prec, double tol_rel, double abs_thresh, double eps0,
-                        int max_iter, bool r_given, cudaStream_t s, double *history,
+pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_thresh,
+                        double eps0, int max_iter, bool r_given, cudaStream_t s, double *history,
                         int history_len, int history_offset, LoopOut &out) {
     double *X = p->X.as<double>(), *R = p->R.as<double>();
     MemberState *st = p->states.as<MemberState>();
@@ -334,6 +338,8 @@ void pit_default_opts(pit_solve_opts *o) {
     o->x0_mode = PIT_X0_COARSE;
     o->refine_max = 8;
     o->inner_tol = 1e-4;
+    o->residual_precision = PIT_FF;
+    o->tol_mode = PIT_TOL_R0;
 }
 
 const char *pit_version(void) { return "libpit 0.1 (sm_103a)"; }
@@ -490,7 +496,7 @@ pit_status pit_apply_operator(pit_problem_t h, int which, int precision, const d
         return PIT_E_INVALID;
     }
     if (which < PIT_APPLY_F || which > PIT_APPLY_RESIDUAL ||
-        (precision != PIT_FP64 && precision != PIT_MIXED)) {
+        (precision != PIT_FP64 && precision != PIT_MIXED && precision != PIT_FF)) {
         set_error("pit_apply_operator: bad operator or precision");
         return PIT_E_INVALID;
     }
@@ -523,7 +529,7 @@ pit_status pit_apply_operator(pit_problem_t h, int which, int precision, const d
 }
 
 pit_status pit_serial_fine(pit_problem_t h, int precision, double *Lam, int on_device) {
-    if (!h || !Lam || (precision != PIT_FP64 && precision != PIT_MIXED)) {
+    if (!h || !Lam || (precision != PIT_FP64 && precision != PIT_MIXED && precision != PIT_FF)) {
         set_error("pit_serial_fine: bad argument");
         return PIT_E_INVALID;
     }
@@ -548,7 +554,9 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
         return PIT_E_INVALID;
     }
     if (!(o->tol >= 0.0) || o->max_iter < 0 || o->x0_mode < PIT_X0_COARSE ||
-        o->x0_mode > PIT_X0_GIVEN || !(o->restart_eps0 >= 0.0)) {
+        o->x0_mode > PIT_X0_GIVEN || !(o->restart_eps0 >= 0.0) ||
+        (o->tol_mode != PIT_TOL_R0 && o->tol_mode != PIT_TOL_RHS) ||
+        (o->residual_precision != PIT_FF && o->residual_precision != PIT_FP64)) {
         set_error("pit_bicgstab_solve: invalid options");
         return PIT_E_INVALID;
     }
@@ -564,6 +572,16 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
     std::vector<int> status(B, PIT_OK);
     const long long steps_per_matvec = (long long)p->N * p->fine_steps;
 
+    // ||G^{-1} B||_{N,inf} per member when the tolerance is relative to it
+    // (with X^0 = G^{-1} B it is the norm of X^0, computed after X^0)
+    std::vector<double> rhsn(B, 0.0);
+    double *d_thr = p->fine_tmp.as<double>() + B;
+    if (o->tol_mode == PIT_TOL_RHS && o->x0_mode != PIT_X0_COARSE) {
+        double *tmp = p->D.as<double>();
+        PIT_TRY(build_rhs(p, tmp, s));
+        PIT_TRY(op_sweep(p, tmp, tmp, sweep_prec(p->precision), nullptr, s));
+        PIT_TRY(member_norms(p, tmp, rhsn, s));
+    }
     if (p->precision == PIT_FP64) {
         double *X = p->X.as<double>();
         if (o->x0_mode == PIT_X0_GIVEN) PIT_TRY(to_device(p, X, Xu, on_device, s));
@@ -571,9 +589,18 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
         else {
             PIT_TRY(build_rhs(p, X, s));
             PIT_TRY(op_sweep(p, X, X, PIT_FP64, nullptr, s));
+            if (o->tol_mode == PIT_TOL_RHS) PIT_TRY(member_norms(p, X, rhsn, s));
+        }
+        const double *thr = nullptr;
+        if (o->tol_mode == PIT_TOL_RHS) {
+            std::vector<double> t(B);
+            for (int b = 0; b < B; ++b) t[b] = o->tol * rhsn[b];
+            PIT_CUDA(cudaMemcpyAsync(d_thr, t.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+            PIT_CUDA(cudaStreamSynchronize(s));
+            thr = d_thr;
         }
         LoopOut lo;
-        PIT_TRY(run_bicgstab(p, PIT_FP64, o->tol, 0.0, o->restart_eps0, o->max_iter, false, s,
+        PIT_TRY(run_bicgstab(p, PIT_FP64, o->tol, thr, o->restart_eps0, o->max_iter, false, s,
                              o->history, o->history_len, 0, lo));
         PIT_TRY(from_device(p, Xu, X, on_device, s));
         PIT_CUDA(cudaStreamSynchronize(s));
@@ -592,6 +619,7 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
         }
     } else {
         // Iterative refinement: FP64 true residual, FP32-fine inner solve.
+        const int rprec = o->residual_precision == PIT_FP64 ? PIT_FP64 : PIT_FF;
         PIT_TRY(p->W.ensure(vb));
         double *Xo = p->W.as<double>();   // outer solution lives in W
         double *Wr = p->R.as<double>();   // true residual goes straight into R
@@ -600,13 +628,14 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
         else {
             PIT_TRY(build_rhs(p, Xo, s));
             PIT_TRY(op_sweep(p, Xo, Xo, PIT_MIXED, nullptr, s));
+            if (o->tol_mode == PIT_TOL_RHS) PIT_TRY(member_norms(p, Xo, rhsn, s));
         }
         std::vector<double> rtrue, r0(B, 0.0);
         std::vector<char> done(B, 0);
         int hc = 0;
         const int rounds = std::max(1, o->refine_max);
         for (int round = 0; round <= rounds; ++round) {
-            PIT_TRY(timed_F(p, Xo, Wr, FINE_RESIDUAL, PIT_FP64, nullptr, s));
+            PIT_TRY(timed_F(p, Xo, Wr, FINE_RESIDUAL, rprec, nullptr, s));
             PIT_TRY(timed_sweep(p, Wr, Wr, PIT_MIXED, nullptr, s));
             PIT_TRY(member_norms(p, Wr, rtrue, s));
             bool any = false;
@@ -620,7 +649,7 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
                 if (!std::isfinite(rtrue[b])) {
                     done[b] = 1;
                     status[b] = PIT_E_NONFINITE;
-                } else if (rtrue[b] <= o->tol * r0[b]) {
+                } else if (rtrue[b] <= o->tol * (o->tol_mode == PIT_TOL_RHS ? rhsn[b] : r0[b])) {
                     done[b] = 1;
                     status[b] = PIT_OK;
                 } else if (round == rounds) {
@@ -638,8 +667,8 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
                                              p->blen * sizeof(double), s));
             PIT_CUDA(cudaMemsetAsync(p->X.ptr, 0, vb, s));
             LoopOut lo;
-            PIT_TRY(run_bicgstab(p, PIT_MIXED, o->inner_tol, 0.0, o->restart_eps0, o->max_iter,
-                                 true, s, nullptr, 0, 0, lo));
+            PIT_TRY(run_bicgstab(p, PIT_MIXED, o->inner_tol, nullptr, o->restart_eps0,
+                                 o->max_iter, true, s, nullptr, 0, 0, lo));
             for (int b = 0; b < B; ++b) {
                 if (done[b]) continue;
                 const MemberState &m = lo.final_states[b];

@@ -26,11 +26,11 @@
 #include <vector>
 
 #include "pit_internal.h"
+#include "stencil_arith.cuh"
 
 namespace pit {
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
 constexpr int RY = 8;   // rows per thread tile
 constexpr int RX = 4;   // columns per thread tile
 
@@ -52,28 +52,26 @@ __device__ __forceinline__ bool runs(const MemberState *st, int b) {
     return st == nullptr || (st[b].active && !st[b].skip && !st[b].half);
 }
 
-template <class T>
-__device__ __forceinline__ T lap5(T vn, T vs, T vw, T ve, T vc) {
-    const T a = vn + vs;
-    const T b = vw + ve;
-    return fma(T(-4), vc, a + b);
-}
-
 // One CTA per (slice, member).  Threads: TXp * TYp (multiple of 32);
-// thread tiles with tx >= TX or ty >= TY hold zeros.
-template <class T>
+// thread tiles with tx >= TX or ty >= TY hold zeros.  V is the arithmetic
+// (float, double or float-float); u lives in registers for FP32 and in a
+// thread-private shared-memory layout (us[k * threads + tid]) otherwise.
+template <class V>
 __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
+    using A = Arith<V>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = blockIdx.y;
     if (!runs(a.st, b)) return;
     const int n = a.n;
     const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
     const int tx = tid % a.TXp, ty = tid / a.TXp;
-    const int TYp = blockDim.x / a.TXp;
+    const int TYp = nthr / a.TXp;
     const int W = a.TXp * RX;                     // row buffer width
-    T *rows = reinterpret_cast<T *>(smem_raw);    // [2 buf][2 top/bot][TYp][W]
-    T *us = rows + 4 * (size_t)TYp * W;           // FP64 only: u[n][n]
-    constexpr bool U_SMEM = sizeof(T) == 8;
+    V *ccs = reinterpret_cast<V *>(smem_raw);     // 4 stage coefficients (32 bytes)
+    V *rows = reinterpret_cast<V *>(smem_raw + 32);   // [2 buf][2 top/bot][TYp][W]
+    V *us = rows + 4 * (size_t)TYp * W;           // u, thread-private layout
+    constexpr bool U_SMEM = A::kUInSmem;
 
     const int i0 = tx * RX, j0 = ty * RY;
     const bool edge = (i0 + RX > n) || (j0 + RY > n);
@@ -81,75 +79,63 @@ __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
     const size_t mb = (size_t)b * a.blen;
     const double *xin = a.x + mb + (size_t)(slice - 1) * n * n;
 
-    T v[RY][RX];
-    T ur[U_SMEM ? 1 : RY][U_SMEM ? 1 : RX];
+    V v[RY][RX];
+    V ur[U_SMEM ? 1 : RY][U_SMEM ? 1 : RX];
 #pragma unroll
     for (int r = 0; r < RY; ++r)
 #pragma unroll
         for (int c = 0; c < RX; ++c) {
             const int i = i0 + c, j = j0 + r;
             const bool ok = (i < n && j < n);
-            const T ld = (T)xin[(size_t)min(j, n - 1) * n + min(i, n - 1)];
-            const T val = ok ? ld : T(0);
+            const V ld = A::from_d(xin[(size_t)min(j, n - 1) * n + min(i, n - 1)]);
+            const V val = A::sel(ok, ld, A::zero());
             v[r][c] = val;
-            if constexpr (U_SMEM) {
-                if (i < n && j < n) us[(size_t)j * n + i] = val;
-            } else {
-                ur[r][c] = val;
-            }
+            if constexpr (U_SMEM) us[(size_t)(r * RX + c) * nthr + tid] = val;
+            else ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = val;
         }
+    // stage coefficients dt/4, dt/3, dt/2, dt (times nu/h^2), converted once
+    if (tid < 4) ccs[tid] = A::from_d(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
     const bool west_zero = (tx == 0), east_zero = (tx == a.TXp - 1);
     const bool north_zero = (ty == 0), south_zero = (ty == TYp - 1);
     int buf = 0;
     for (int s = 0; s < a.steps; ++s) {
 #pragma unroll 1
         for (int stage = 0; stage < 4; ++stage) {
-            const double cd = stage == 0 ? a.c[0] : stage == 1 ? a.c[1] : stage == 2 ? a.c[2] : a.c[3];
-            const T cc = (T)cd;
             // publish the top and bottom rows of v
-            T *top = rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0;
-            T *bot = rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0;
-#pragma unroll
-            for (int c = 0; c < RX; ++c) {
-                top[c] = v[0][c];
-                bot[c] = v[RY - 1][c];
-            }
+            A::st4(rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0, v[0]);
+            A::st4(rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0, v[RY - 1]);
             __syncthreads();
-            T nrow[RX], srow[RX];
-            const T *nsrc = rows + ((size_t)(buf * 2 + 1) * TYp + (ty - 1)) * W + i0;
-            const T *ssrc = rows + ((size_t)(buf * 2 + 0) * TYp + (ty + 1)) * W + i0;
+            const V cc = ccs[stage];
+            V prev[RX];
+            // north neighbour row (the index stays inside the buffer where unused)
+            A::ld4(rows + ((size_t)(buf * 2 + 1) * TYp + (north_zero ? ty : ty - 1)) * W + i0, prev);
 #pragma unroll
-            for (int c = 0; c < RX; ++c) {
-                nrow[c] = north_zero ? T(0) : nsrc[c];
-                srow[c] = south_zero ? T(0) : ssrc[c];
-            }
-            T prev[RX];
-#pragma unroll
-            for (int c = 0; c < RX; ++c) prev[c] = nrow[c];
+            for (int c = 0; c < RX; ++c) prev[c] = A::sel(north_zero, A::zero(), prev[c]);
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
-                T w_in = __shfl_up_sync(FULL, v[r][RX - 1], 1);
-                T e_in = __shfl_down_sync(FULL, v[r][0], 1);
-                if (west_zero) w_in = T(0);
-                if (east_zero) e_in = T(0);
-                T cur[RX];
+                V srow[RX];
+                if (r == RY - 1) {
+                    A::ld4(rows + ((size_t)(buf * 2 + 0) * TYp + (south_zero ? ty : ty + 1)) * W + i0, srow);
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) srow[c] = A::sel(south_zero, A::zero(), srow[c]);
+                }
+                V w_in = A::shfl_up(v[r][RX - 1]);
+                V e_in = A::shfl_down(v[r][0]);
+                w_in = A::sel(west_zero, A::zero(), w_in);
+                e_in = A::sel(east_zero, A::zero(), e_in);
+                V cur[RX];
 #pragma unroll
                 for (int c = 0; c < RX; ++c) cur[c] = v[r][c];
 #pragma unroll
                 for (int c = 0; c < RX; ++c) {
-                    const T vn = prev[c];
-                    const T vs = (r < RY - 1) ? v[r + 1][c] : srow[c];
-                    const T vw = (c > 0) ? cur[c - 1] : w_in;
-                    const T ve = (c < RX - 1) ? cur[c + 1] : e_in;
-                    T u;
-                    if constexpr (U_SMEM) {
-                        const int i = i0 + c, j = j0 + r;
-                        const T uu = us[(size_t)min(j, n - 1) * n + min(i, n - 1)];
-                        u = (i < n && j < n) ? uu : T(0);
-                    } else {
-                        u = ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c];
-                    }
-                    v[r][c] = fma(cc, lap5(vn, vs, vw, ve, cur[c]), u);
+                    const V vn = prev[c];
+                    const V vs = (r < RY - 1) ? v[r + 1][c] : srow[c];
+                    const V vw = (c > 0) ? cur[c - 1] : w_in;
+                    const V ve = (c < RX - 1) ? cur[c + 1] : e_in;
+                    V u;
+                    if constexpr (U_SMEM) u = us[(size_t)(r * RX + c) * nthr + tid];
+                    else u = ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c];
+                    v[r][c] = A::stage(vn, vs, vw, ve, cur[c], u, cc);
                 }
 #pragma unroll
                 for (int c = 0; c < RX; ++c) prev[c] = cur[c];
@@ -159,25 +145,18 @@ __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
                 for (int r = 0; r < RY; ++r)
 #pragma unroll
                     for (int c = 0; c < RX; ++c)
-                        if (i0 + c >= n || j0 + r >= n) v[r][c] = T(0);
+                        if (i0 + c >= n || j0 + r >= n) v[r][c] = A::zero();
             }
             buf ^= 1;
         }
         // end of step: u <- v
-        if constexpr (U_SMEM) {
 #pragma unroll
-            for (int r = 0; r < RY; ++r)
+        for (int r = 0; r < RY; ++r)
 #pragma unroll
-                for (int c = 0; c < RX; ++c) {
-                    const int i = i0 + c, j = j0 + r;
-                    if (i < n && j < n) us[(size_t)j * n + i] = v[r][c];
-                }
-        } else {
-#pragma unroll
-            for (int r = 0; r < RY; ++r)
-#pragma unroll
-                for (int c = 0; c < RX; ++c) ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = v[r][c];
-        }
+            for (int c = 0; c < RX; ++c) {
+                if constexpr (U_SMEM) us[(size_t)(r * RX + c) * nthr + tid] = v[r][c];
+                else ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = v[r][c];
+            }
     }
     // epilogue: row `slice` of the block operator, FP64
     double *yo = a.y + mb + (size_t)slice * n * n;
@@ -189,7 +168,7 @@ __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
             const int i = i0 + c, j = j0 + r;
             if (i < n && j < n) {
                 const size_t k = (size_t)j * n + i;
-                const double f = (double)v[r][c];
+                const double f = A::to_d(v[r][c]);
                 if (a.mode == FINE_APPLY) yo[k] = xn[k] - f;
                 else if (a.mode == FINE_RESIDUAL) yo[k] = f - xn[k];
                 else yo[k] = f;
@@ -199,18 +178,42 @@ __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
         const double *x0 = a.x + mb;
         double *y0o = a.y + mb;
         const int nn = n * n;
-        for (int k = tid; k < nn; k += blockDim.x)
+        for (int k = tid; k < nn; k += nthr)
             y0o[k] = (a.mode == FINE_APPLY) ? x0[k] : a.y0[(size_t)b * nn + k] - x0[k];
     }
 }
 
 // ------------------------------------------------------- sine transforms
-// out_b = scale * (A_b S)^T for every n x n block b, i.e.
+// out_b = scale * (A_b S)^T for every n x n block b (n <= 128), i.e.
 // out_b[k][j] = scale * sum_i A_b[j][i] S[i][k].  Applied twice it gives
-// scale^2 S A S (S symmetric).  One CTA (256 threads, 8x8 outputs each) per
-// block; A_b is staged transposed in shared memory; S is staged in shared
-// memory (FP32) or read through L1/L2 (FP64).
+// scale^2 S A S (S symmetric).  One CTA of 256 threads per block; thread
+// (tx, ty) owns output rows j in {4ty..4ty+3, 64+4ty..64+4ty+3} and columns
+// k in {4tx..4tx+3, 64+4tx..64+4tx+3}, so the per-i operands are four
+// 16-byte shared loads (the S row loads contiguous across the lanes).  A_b is
+// staged transposed and both operands are zero-padded to 128, so the inner
+// loop has no conditionals.  S is staged in shared memory for FP32 and read
+// through L1/L2 for FP64.
 constexpr int PT = 256;
+constexpr int PN = 128;          // padded block edge
+constexpr int PLD = PN + 4;      // padded row of the staged operands
+
+template <class T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    __device__ static void ld(const float *p, float (&v)[4]) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    __device__ static void ld(const double *p, double (&v)[4]) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
 
 template <class Tin, class T, class Tout>
 __global__ void __launch_bounds__(PT) k_block_xS_T(const Tin *__restrict__ A, Tout *__restrict__ out,
@@ -221,53 +224,65 @@ __global__ void __launch_bounds__(PT) k_block_xS_T(const Tin *__restrict__ A, To
     const int blk = blockIdx.x;
     const int member = blk / nblk;
     if (!runs(st, member)) return;
-    const int ld = n + 4;                          // padded row of At
-    T *At = reinterpret_cast<T *>(smem_raw);       // At[i][j] = A[j][i]
-    T *Ss = At + (size_t)n * ld;                   // S[i][k] (FP32 only)
+    T *At = reinterpret_cast<T *>(smem_raw);       // At[i][j] = A[j][i], PN x PLD
+    T *Ss = At + (size_t)PN * PLD;                 // S[i][k] (FP32 only), PN x PLD
     const size_t nn = (size_t)n * n;
     const Tin *Ab = A + (size_t)blk * nn;
-    for (size_t q = threadIdx.x; q < nn; q += PT) {
-        const int j = (int)(q / n), i = (int)(q % n);
-        At[(size_t)i * ld + j] = (T)Ab[q];
-    }
-    if (S_SMEM)
-        for (size_t q = threadIdx.x; q < nn; q += PT) Ss[(q / n) * ld + (q % n)] = S[q];
-    __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int j0 = ty * 8, k0 = tx * 8;
-    if (j0 >= n || k0 >= n) return;
+    // stage A_b transposed and S, zero-padded to PN x PN
+    for (int j = ty; j < PN; j += 16)
+        for (int i = tx; i < PN; i += 16) {
+            const bool ok = (i < n && j < n);
+            const T v = ok ? (T)Ab[(size_t)min(j, n - 1) * n + min(i, n - 1)] : T(0);
+            At[(size_t)i * PLD + j] = v;
+            if (S_SMEM) Ss[(size_t)j * PLD + i] = ok ? S[(size_t)min(j, n - 1) * n + min(i, n - 1)] : T(0);
+        }
+    __syncthreads();
     T acc[8][8];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = T(0);
-    const int jn = min(8, n - j0), kn = min(8, n - k0);
+    const int ja = 4 * ty, jb = 64 + 4 * ty, ka = 4 * tx, kb = 64 + 4 * tx;
     for (int i = 0; i < n; ++i) {
-        T av[8], sv[8];
-        const T *arow = At + (size_t)i * ld + j0;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) av[r] = (r < jn) ? arow[min(r, jn - 1)] : T(0);
+        T a0[4], a1[4], s0[4], s1[4];
+        const T *arow = At + (size_t)i * PLD;
+        Vec4<T>::ld(arow + ja, a0);
+        Vec4<T>::ld(arow + jb, a1);
         if (S_SMEM) {
-            const T *srow = Ss + (size_t)i * ld + k0;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) sv[c] = (c < kn) ? srow[min(c, kn - 1)] : T(0);
+            const T *srow = Ss + (size_t)i * PLD;
+            Vec4<T>::ld(srow + ka, s0);
+            Vec4<T>::ld(srow + kb, s1);
         } else {
-            const T *srow = S + (size_t)i * n + k0;
+            const T *srow = S + (size_t)i * n;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) sv[c] = (c < kn) ? __ldg(srow + min(c, kn - 1)) : T(0);
+            for (int c = 0; c < 4; ++c) {
+                s0[c] = (ka + c < n) ? __ldg(srow + min(ka + c, n - 1)) : T(0);
+                s1[c] = (kb + c < n) ? __ldg(srow + min(kb + c, n - 1)) : T(0);
+            }
         }
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[r][c] = fma(av[r], sv[c], acc[r][c]);
+            for (int c = 0; c < 4; ++c) {
+                acc[r][c] = fma(a0[r], s0[c], acc[r][c]);
+                acc[r][c + 4] = fma(a0[r], s1[c], acc[r][c + 4]);
+                acc[r + 4][c] = fma(a1[r], s0[c], acc[r + 4][c]);
+                acc[r + 4][c + 4] = fma(a1[r], s1[c], acc[r + 4][c + 4]);
+            }
     }
     Tout *ob = out + (size_t)blk * nn;
     const T sc = (T)scale;
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
+    for (int c = 0; c < 8; ++c) {
+        const int k = (c < 4) ? ka + c : kb + c - 4;
+        if (k >= n) continue;
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
-            if (c < kn && r < jn) ob[(size_t)(k0 + c) * n + (j0 + r)] = (Tout)(sc * acc[r][c]);
+        for (int r = 0; r < 8; ++r) {
+            const int j = (r < 4) ? ja + r : jb + r - 4;
+            if (j < n) ob[(size_t)k * n + j] = (Tout)(sc * acc[r][c]);
+        }
+    }
 }
 
 // Chunked scan of zhat_n = qhat_n + g zhat_{n-1} over the N+1 blocks of each
@@ -326,10 +341,10 @@ __global__ void k_rec_apply(T *__restrict__ hat, const double *__restrict__ ends
 
 constexpr int REC_CHUNK = 16;   // blocks per scan chunk
 
-template <class T>
-size_t fine_smem(int TXp, int TYp, int n) {
-    size_t s = 4 * (size_t)TYp * TXp * RX * sizeof(T);
-    if (sizeof(T) == 8) s += (size_t)n * n * sizeof(T);
+template <class V>
+size_t fine_smem(int TXp, int TYp) {
+    size_t s = 32 + 4 * (size_t)TYp * TXp * RX * sizeof(V);
+    if (Arith<V>::kUInSmem) s += (size_t)TXp * TYp * RY * RX * sizeof(V);
     return s;
 }
 
@@ -350,7 +365,7 @@ pit_status launch_fine(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
     a.TXp = TXp;
     a.TY = TY;
     const int threads = TXp * TYp;
-    const size_t sm = fine_smem<T>(TXp, TYp, p->nx);
+    const size_t sm = fine_smem<T>(TXp, TYp);
     PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
     k_heat2d_fine<T><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
@@ -385,7 +400,7 @@ template <class Tin, class T, class Tout>
 pit_status launch_xS(Problem *p, const Tin *A, Tout *out, const T *S, double scale,
                      const MemberState *st, cudaStream_t s) {
     const int n = p->nx;
-    const size_t sm = (size_t)n * (n + 4) * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
+    const size_t sm = (size_t)PN * PLD * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
     PIT_CUDA(cudaFuncSetAttribute(k_block_xS_T<Tin, T, Tout>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int nblk = p->N + 1;
@@ -475,12 +490,14 @@ pit_status heat2d_apply_F(Problem *p, const double *x, double *y, int mode, int 
                           const MemberState *st, cudaStream_t s) {
     Heat2dArgs a = make_args(p, x, y, mode, st);
     if (prec == PIT_FP64) return launch_fine<double>(p, a, p->N, s);
+    if (prec == PIT_FF) return launch_fine<ff>(p, a, p->N, s);
     return launch_fine<float>(p, a, p->N, s);
 }
 
 pit_status heat2d_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
     Heat2dArgs a = make_args(p, x, y - (size_t)p->M, 2, nullptr);
     if (prec == PIT_FP64) return launch_fine<double>(p, a, 1, s);
+    if (prec == PIT_FF) return launch_fine<ff>(p, a, 1, s);
     return launch_fine<float>(p, a, 1, s);
 }
 

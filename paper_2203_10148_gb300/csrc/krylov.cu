@@ -261,7 +261,9 @@ __device__ void reduce_q(const VecGeom &g, const double *part, int b, int q, int
 enum FinishKind { F_INIT, F_SIGMA, F_S, F_OMEGA, F_R, F_NORM };
 
 struct InitArgs {
-    double tol_rel, abs_thresh, eps0, eps_b;
+    double tol_rel;
+    const double *abs_thresh;   // per-member absolute thresholds (device) or null
+    double eps0, eps_b;
     int max_iter;
 };
 
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(FT) k_finish(VecGeom g, const double *__restri
             m.r2 = s0;
             m.r0 = sqrt(m0);
             m.rnorm = m.r0;
-            m.thresh = ia.abs_thresh > 0.0 ? ia.abs_thresh : ia.tol_rel * m.r0;
+            m.thresh = ia.abs_thresh ? ia.abs_thresh[b] : ia.tol_rel * m.r0;
             m.eps0 = ia.eps0;
             m.eps_b = ia.eps_b;
             m.max_iter = ia.max_iter;
@@ -459,8 +461,8 @@ pit_status krylov_prepare(Problem *p) {
     return PIT_OK;
 }
 
-pit_status kr_init(Problem *p, double tol_rel, double abs_thresh, double eps0, int max_iter,
-                   cudaStream_t s) {
+pit_status kr_init(Problem *p, double tol_rel, const double *abs_thresh, double eps0,
+                   int max_iter, cudaStream_t s) {
     VecGeom g = geom(p);
     k_init<<<vgrid(p, g), VT, 0, s>>>(g, p->R.as<double>(), p->Rt.as<double>(),
                                       p->P.as<double>(), p->partials.as<double>(), nullptr);

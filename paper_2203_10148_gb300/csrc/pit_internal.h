@@ -186,8 +186,10 @@ pit_status krylov_prepare(Problem *p);   // allocates vectors, partials, states
 pit_status build_rhs(Problem *p, double *B, cudaStream_t s);
 
 // Kernel launchers (krylov.cu); every one masks inactive members.
-pit_status kr_init(Problem *p, double tol_rel, double abs_thresh, double eps0, int max_iter,
-                   cudaStream_t s);       // R computed: R~ = P = R; rho, r0, thresh
+// R computed: R~ = P = R; rho, r0; thresh = abs_thresh[b] (device array) if
+// given, else tol_rel * r0
+pit_status kr_init(Problem *p, double tol_rel, const double *abs_thresh, double eps0,
+                   int max_iter, cudaStream_t s);
 pit_status kr_sigma(Problem *p, cudaStream_t s);     // sigma = <D,R~>, alpha
 pit_status kr_update_S(Problem *p, cudaStream_t s);  // S = R - alpha D, ||S||, half exit
 pit_status kr_omega(Problem *p, cudaStream_t s);     // <K,S>, <K,K>, omega

@@ -26,7 +26,9 @@ STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "nomem", -3: "cuda", -
 PIT_OP = {"heat1d": 1, "heat2d": 2, "advdiff2d": 3, "dense": 4}
 PIT_STEP = {"ie": 1, "rk4": 2}
 PIT_FP64, PIT_MIXED = 0, 1
-PRECISION = {"fp64": PIT_FP64, "mixed": PIT_MIXED}
+PIT_FF = 2
+PRECISION = {"fp64": PIT_FP64, "mixed": PIT_MIXED, "ff": PIT_FF}
+TOL_MODE = {"r0": 0, "rhs": 1}
 APPLY = {"F": 1, "Ginv": 2, "GinvF": 3, "residual": 4}
 X0 = {"coarse": 0, "zero": 1, "given": 2}
 
@@ -51,7 +53,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart_eps0", C.c_double), ("max_iter", C.c_int),
                 ("x0_mode", C.c_int), ("refine_max", C.c_int), ("inner_tol", C.c_double),
                 ("stream", C.c_void_p), ("history", C.POINTER(C.c_double)),
-                ("history_len", C.c_int)]
+                ("history_len", C.c_int), ("residual_precision", C.c_int), ("tol_mode", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -79,7 +81,8 @@ EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_cre
            "pit_problem_set_y0", "pit_kernel_launches", "pit_set_timing", "pit_get_timing",
            "pit_block_reduce_noalloc"]
 
-TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4}
+TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4,
+                "fine_ff": 5}
 
 
 def lib_path() -> str:
@@ -239,7 +242,8 @@ class Problem:
     def bicgstab_solve(self, X=None, tol: float = 1e-10, eps0: float = 1e-8,
                        max_iter: int = 500, x0: str = "coarse", refine_max: int = 8,
                        inner_tol: float = 1e-4, history_len: int = 0, stream=None,
-                       raise_on_status: bool = False):
+                       raise_on_status: bool = False, tol_mode: str = "r0",
+                       residual_precision: str = "ff"):
         """pit_bicgstab_solve; returns (X, [info dict per member])."""
         lib = load()
         opts = SolveOpts()
@@ -247,6 +251,8 @@ class Problem:
         opts.tol, opts.restart_eps0, opts.max_iter = tol, eps0, max_iter
         opts.x0_mode = X0["given" if (x0 == "given") else x0]
         opts.refine_max, opts.inner_tol = refine_max, inner_tol
+        opts.tol_mode = TOL_MODE[tol_mode]
+        opts.residual_precision = PRECISION[residual_precision]
         hist = None
         if history_len:
             hist = np.zeros(history_len)

@@ -238,3 +238,45 @@ def test_block_reduce_matches_numpy():
         assert dot == pytest.approx(float(np.sum(U * V)), rel=1e-12, abs=1e-12)
         np.testing.assert_allclose(norms, np.linalg.norm(U, axis=1), rtol=1e-13)
         assert ninf == pytest.approx(np.linalg.norm(U, axis=1).max(), rel=1e-13)
+
+
+@pytest.mark.parametrize("case", [dict(n=16, N=4, fine_steps=5), dict(n=37, N=3, fine_steps=40, batch=2),
+                                  dict(n=128, N=3, fine_steps=400)])
+def test_heat2d_float_float_fine_matches_oracle(case):
+    """Float-float stepping (about 48 bits) agrees with the FP64 oracle to 1e-12
+    (RK4-stable cases: dt nu 8/h^2 below 2.78, so rounding is not amplified)."""
+    pit = _pit()
+    w = inputs.heat2d(**case)
+    X = _rand_block(w, 6)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("F", X, precision="ff")
+        lam = p.serial_fine("ff")
+    assert _rel(got, _oracle_apply(w, "F", X)) < 1e-12
+    assert _rel(lam[0], OracleProblem.from_workload(w).serial_fine()) < 1e-11
+
+
+@pytest.mark.parametrize("resid", ["ff", "fp64"])
+@pytest.mark.parametrize("tol_mode", ["r0", "rhs"])
+def test_heat2d_mixed_residual_precisions_and_tol_modes(resid, tol_mode):
+    pit = _pit()
+    w = inputs.heat2d(n=32, N=16)
+    lam = OracleProblem.from_workload(w).serial_fine()
+    with pit.Problem(w, "mixed") as p:
+        X, info = p.bicgstab_solve(tol=1e-8 if tol_mode == "rhs" else 1e-7, residual_precision=resid,
+                                   tol_mode=tol_mode, inner_tol=1e-5)
+    assert info[0]["status"] == 0
+    assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
+
+
+def test_tol_mode_rhs_fp64_threshold():
+    """PIT_TOL_RHS stops on ||R|| <= tol ||G^-1 B||; the oracle with the same
+    absolute threshold takes the same iterations."""
+    pit = _pit()
+    w = inputs.heat1d()
+    o = OracleProblem.from_workload(w)
+    rhs = np.max(np.linalg.norm(o.coarse_prediction(), axis=1))
+    Xo, oi = pitsbicg(o, tol=0.0, abs_tol=1e-9 * rhs)
+    with pit.Problem(w, "fp64") as p:
+        X, info = p.bicgstab_solve(tol=1e-9, tol_mode="rhs")
+    assert info[0]["iterations"] == oi.iterations
+    assert _rel(X[0], Xo) < 1e-12
