@@ -45,9 +45,10 @@ FINE_SRC = os.path.join(ROOT, "paper_2203_10148_gb300", "csrc", "heat2d.cu")
 
 FLOP_PER_POINT_STEP = 28       # RK4 Horner: 4 stages x (3 add + 2 FMA) = 4 x 7 flop
 # pipe operations per point and fine step (FADD, FMUL, FFMA count one each):
-# FP32 4 stages x 5; float-float 4 stages x 64 FP32 ops (3 + 1 TwoSum-based
-# additions of 11, an exact scaling of 2, a product of 7); FP64 4 x 5 FP64 ops
-OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 256, "fine_fp64": 20}
+# FP32 4 stages x 5; float-float 4 stages x 48 FP32 ops (4 TwoSums of 6, an
+# exact scaling, 8 for the low parts, a 4-op product, a TwoSum and a
+# renormalisation of 5); FP64 4 x 5 FP64 ops
+OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 192, "fine_fp64": 20}
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2          # 1.25 TFLOP/s nominal FP64 = 2 FMA/clk/SM at 2.07 GHz x 152 SMs
 KERNEL_NAMES = {"fine_fp32": "k_heat2d_fine<float>", "fine_ff": "k_heat2d_fine<ff>",

@@ -265,6 +265,12 @@ pit_status pit_problem_set_y0(pit_problem_t prob, const double *y0, int on_devic
 /* Number of kernels libpit has launched in this process (all problems). */
 unsigned long long pit_kernel_launches(void);
 
+/* Self-test of the integer-pipe FP64 -> FP32 (round to nearest even) and
+ * FP32 -> FP64 conversions the kernels use in place of the hardware
+ * conversion: f32[i] = convert(in[i]), back[i] = convert(f32[i]).  Device
+ * pointers, n values; synchronous. */
+pit_status pit_selftest_convert(const double *in, int n, float *f32, double *back);
+
 /* Operator classes timed by pit_get_timing. */
 #define PIT_TIME_FINE_FP32   0   /* fine batch, FP32 stepping (one kernel per call) */
 #define PIT_TIME_FINE_FP64   1   /* fine batch, FP64 stepping (one kernel per call) */

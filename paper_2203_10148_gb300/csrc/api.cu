@@ -204,6 +204,14 @@ static pit_status timed_sweep(Problem *p, const double *q, double *z, int prec,
 
 static pit_status apply_GinvF(Problem *p, const double *x, double *y, int prec,
                               const MemberState *st, cudaStream_t s) {
+    if (p->kind == PIT_OP_HEAT2D && prec == PIT_MIXED) {
+        // the FP32 sweep consumes FP32 rows: the fine kernel writes them directly
+        PIT_TRY(p->q32.ensure(p->vlen * sizeof(float)));
+        float *q = p->q32.as<float>();
+        PIT_TIMED(p, PIT_TIME_FINE_FP32, s, heat2d_fine_f32out(p, x, q, st, s));
+        PIT_TIMED(p, PIT_TIME_SWEEP_MIXED, s, heat2d_sweep_f32in(p, q, y, st, s));
+        return PIT_OK;
+    }
     PIT_TRY(timed_F(p, x, y, FINE_APPLY, prec, st, s));
     return timed_sweep(p, y, y, prec, st, s);
 }
@@ -470,7 +478,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->vy32, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
-                      &p->flags_host_mirror, &p->fine_tmp};
+                      &p->flags_host_mirror, &p->fine_tmp, &p->q32};
     for (DevBuf *b : bufs) b->release();
     p->timer.destroy();
     if (p->stream) cudaStreamDestroy(p->stream);

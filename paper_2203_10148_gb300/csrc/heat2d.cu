@@ -23,6 +23,8 @@
 // block products; the recurrence is a chunked scan over n.
 #include <math.h>
 
+#include <string>
+#include <type_traits>
 #include <vector>
 
 #include "pit_internal.h"
@@ -31,8 +33,7 @@
 namespace pit {
 namespace {
 
-constexpr int RY = 8;   // rows per thread tile
-constexpr int RX = 4;   // columns per thread tile
+constexpr int RY = 8;   // rows per thread tile (columns: Arith<V>::kRX)
 
 struct Heat2dArgs {
     const double *x;
@@ -46,6 +47,7 @@ struct Heat2dArgs {
     double c[4];    // stage coefficients dt/4, dt/3, dt/2, dt times nu/h^2
     int TX, TXp, TY;
     const MemberState *st;
+    float *y32;     // FP32 output of the block-operator rows (mixed G^{-1}F path) or null
 };
 
 __device__ __forceinline__ bool runs(const MemberState *st, int b) {
@@ -56,9 +58,10 @@ __device__ __forceinline__ bool runs(const MemberState *st, int b) {
 // thread tiles with tx >= TX or ty >= TY hold zeros.  V is the arithmetic
 // (float, double or float-float); u lives in registers for FP32 and in a
 // thread-private shared-memory layout (us[k * threads + tid]) otherwise.
-template <class V>
-__global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
+template <class V, int RX>
+__global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
     using A = Arith<V>;
+    constexpr bool kPacked = std::is_same<V, float>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = blockIdx.y;
     if (!runs(a.st, b)) return;
@@ -97,35 +100,90 @@ __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
     if (tid < 4) ccs[tid] = A::from_d(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
     const bool west_zero = (tx == 0), east_zero = (tx == a.TXp - 1);
     const bool north_zero = (ty == 0), south_zero = (ty == TYp - 1);
+    // packed FP32 path: halo masks as multipliers
+    [[maybe_unused]] const float mw = west_zero ? 0.f : 1.f, me = east_zero ? 0.f : 1.f;
+    [[maybe_unused]] const float2 mn2 = north_zero ? make_float2(0.f, 0.f) : make_float2(1.f, 1.f);
+    [[maybe_unused]] const float2 ms2 = south_zero ? make_float2(0.f, 0.f) : make_float2(1.f, 1.f);
     int buf = 0;
     for (int s = 0; s < a.steps; ++s) {
 #pragma unroll 1
         for (int stage = 0; stage < 4; ++stage) {
             // publish the top and bottom rows of v
-            A::st4(rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0, v[0]);
-            A::st4(rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0, v[RY - 1]);
+#pragma unroll
+            for (int q = 0; q < RX; q += 4) {
+                const V t0[4] = {v[0][q], v[0][q + 1], v[0][q + 2], v[0][q + 3]};
+                const V t1[4] = {v[RY - 1][q], v[RY - 1][q + 1], v[RY - 1][q + 2], v[RY - 1][q + 3]};
+                A::st4(rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0 + q, t0);
+                A::st4(rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0 + q, t1);
+            }
             __syncthreads();
             const V cc = ccs[stage];
+            [[maybe_unused]] float2 cc2;
+            if constexpr (kPacked) cc2 = make_float2(cc, cc);
             V prev[RX];
             // north neighbour row (the index stays inside the buffer where unused)
-            A::ld4(rows + ((size_t)(buf * 2 + 1) * TYp + (north_zero ? ty : ty - 1)) * W + i0, prev);
 #pragma unroll
-            for (int c = 0; c < RX; ++c) prev[c] = A::sel(north_zero, A::zero(), prev[c]);
+            for (int q = 0; q < RX; q += 4) {
+                V t[4];
+                A::ld4(rows + ((size_t)(buf * 2 + 1) * TYp + (north_zero ? ty : ty - 1)) * W + i0 + q, t);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) prev[q + c] = t[c];
+            }
+            if constexpr (!kPacked) {
+#pragma unroll
+                for (int c = 0; c < RX; ++c) prev[c] = A::sel(north_zero, A::zero(), prev[c]);
+            }
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 V srow[RX];
                 if (r == RY - 1) {
-                    A::ld4(rows + ((size_t)(buf * 2 + 0) * TYp + (south_zero ? ty : ty + 1)) * W + i0, srow);
 #pragma unroll
-                    for (int c = 0; c < RX; ++c) srow[c] = A::sel(south_zero, A::zero(), srow[c]);
+                    for (int q = 0; q < RX; q += 4) {
+                        V t[4];
+                        A::ld4(rows + ((size_t)(buf * 2 + 0) * TYp + (south_zero ? ty : ty + 1)) * W + i0 + q, t);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) srow[q + c] = t[c];
+                    }
+                    if constexpr (!kPacked) {
+#pragma unroll
+                        for (int c = 0; c < RX; ++c) srow[c] = A::sel(south_zero, A::zero(), srow[c]);
+                    }
                 }
                 V w_in = A::shfl_up(v[r][RX - 1]);
                 V e_in = A::shfl_down(v[r][0]);
-                w_in = A::sel(west_zero, A::zero(), w_in);
-                e_in = A::sel(east_zero, A::zero(), e_in);
                 V cur[RX];
 #pragma unroll
                 for (int c = 0; c < RX; ++c) cur[c] = v[r][c];
+                if constexpr (kPacked) {
+                    // FP32, two columns per packed instruction; the Dirichlet
+                    // halo masks (0 at the domain edge, 1 inside) enter as FMAs
+                    float h[RX];
+                    h[0] = fmaf(mw, w_in, cur[1]);
+#pragma unroll
+                    for (int c = 1; c < RX - 1; ++c) h[c] = cur[c - 1] + cur[c + 1];
+                    h[RX - 1] = fmaf(me, e_in, cur[RX - 2]);
+#pragma unroll
+                    for (int q = 0; q < RX; q += 2) {
+                        const float2 vn2 = make_float2(prev[q], prev[q + 1]);
+                        const float2 vs2 = (r < RY - 1) ? make_float2(v[r + 1][q], v[r + 1][q + 1])
+                                                        : make_float2(srow[q], srow[q + 1]);
+                        float2 t;
+                        if (r == 0) t = __ffma2_rn(mn2, vn2, vs2);
+                        else if (r == RY - 1) t = __ffma2_rn(ms2, vs2, vn2);
+                        else t = __fadd2_rn(vn2, vs2);
+                        t = __fadd2_rn(t, make_float2(h[q], h[q + 1]));
+                        t = __ffma2_rn(make_float2(-4.f, -4.f), make_float2(cur[q], cur[q + 1]), t);
+                        const float2 w2 = __ffma2_rn(cc2, t, make_float2(ur[U_SMEM ? 0 : r][U_SMEM ? 0 : q],
+                                                                           ur[U_SMEM ? 0 : r][U_SMEM ? 0 : q + 1]));
+                        v[r][q] = w2.x;
+                        v[r][q + 1] = w2.y;
+                    }
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) prev[c] = cur[c];
+                    continue;
+                }
+                w_in = A::sel(west_zero, A::zero(), w_in);
+                e_in = A::sel(east_zero, A::zero(), e_in);
 #pragma unroll
                 for (int c = 0; c < RX; ++c) {
                     const V vn = prev[c];
@@ -158,9 +216,30 @@ __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
                 else ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = v[r][c];
             }
     }
-    // epilogue: row `slice` of the block operator, FP64
-    double *yo = a.y + mb + (size_t)slice * n * n;
+    // epilogue: row `slice` of the block operator
     const double *xn = a.x + mb + (size_t)slice * n * n;
+    if constexpr (std::is_same<V, float>::value) if (a.y32) {
+        // FP32 rows q_n = x_n - F(x_{n-1}) for the FP32 sweep (apply mode)
+        float *yo = a.y32 + mb + (size_t)slice * n * n;
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int c = 0; c < RX; ++c) {
+                const int i = i0 + c, j = j0 + r;
+                if (i < n && j < n) {
+                    const size_t k = (size_t)j * n + i;
+                    yo[k] = d2f_rn(xn[k]) - v[r][c];
+                }
+            }
+        if (slice == 1) {
+            const double *x0 = a.x + mb;
+            float *y0o = a.y32 + mb;
+            const int nn = n * n;
+            for (int k = tid; k < nn; k += nthr) y0o[k] = d2f_rn(x0[k]);
+        }
+        return;
+    }
+    double *yo = a.y + mb + (size_t)slice * n * n;
 #pragma unroll
     for (int r = 0; r < RY; ++r)
 #pragma unroll
@@ -193,6 +272,14 @@ __global__ void __launch_bounds__(512, 1) k_heat2d_fine(Heat2dArgs a) {
 // staged transposed and both operands are zero-padded to 128, so the inner
 // loop has no conditionals.  S is staged in shared memory for FP32 and read
 // through L1/L2 for FP64.
+// FP64 <-> FP32 conversions on the integer pipe (see stencil_arith.cuh)
+template <class To, class From>
+__device__ __forceinline__ To cvt(From x) {
+    if constexpr (std::is_same<To, float>::value && std::is_same<From, double>::value) return d2f_rn(x);
+    else if constexpr (std::is_same<To, double>::value && std::is_same<From, float>::value) return f2d(x);
+    else return (To)x;
+}
+
 constexpr int PT = 256;
 constexpr int PN = 128;          // padded block edge
 constexpr int PLD = PN + 4;      // padded row of the staged operands
@@ -233,7 +320,7 @@ __global__ void __launch_bounds__(PT) k_block_xS_T(const Tin *__restrict__ A, To
     for (int j = ty; j < PN; j += 16)
         for (int i = tx; i < PN; i += 16) {
             const bool ok = (i < n && j < n);
-            const T v = ok ? (T)Ab[(size_t)min(j, n - 1) * n + min(i, n - 1)] : T(0);
+            const T v = ok ? cvt<T>(Ab[(size_t)min(j, n - 1) * n + min(i, n - 1)]) : T(0);
             At[(size_t)i * PLD + j] = v;
             if (S_SMEM) Ss[(size_t)j * PLD + i] = ok ? S[(size_t)min(j, n - 1) * n + min(i, n - 1)] : T(0);
         }
@@ -280,7 +367,7 @@ __global__ void __launch_bounds__(PT) k_block_xS_T(const Tin *__restrict__ A, To
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int j = (r < 4) ? ja + r : jb + r - 4;
-            if (j < n) ob[(size_t)k * n + j] = (Tout)(sc * acc[r][c]);
+            if (j < n) ob[(size_t)k * n + j] = cvt<Tout>(sc * acc[r][c]);
         }
     }
 }
@@ -341,14 +428,14 @@ __global__ void k_rec_apply(T *__restrict__ hat, const double *__restrict__ ends
 
 constexpr int REC_CHUNK = 16;   // blocks per scan chunk
 
-template <class V>
+template <class V, int RX>
 size_t fine_smem(int TXp, int TYp) {
     size_t s = 32 + 4 * (size_t)TYp * TXp * RX * sizeof(V);
     if (Arith<V>::kUInSmem) s += (size_t)TXp * TYp * RY * RX * sizeof(V);
     return s;
 }
 
-void tile_shape(int n, int &TX, int &TXp, int &TY, int &TYp) {
+void tile_shape(int n, int RX, int &TX, int &TXp, int &TY, int &TYp) {
     TX = (n + RX - 1) / RX;
     TXp = 1;
     while (TXp < TX) TXp <<= 1;
@@ -357,24 +444,35 @@ void tile_shape(int n, int &TX, int &TXp, int &TY, int &TYp) {
     TYp = threads / TXp;
 }
 
-template <class T>
-pit_status launch_fine(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
+template <class T, int RX>
+pit_status launch_fine_rx(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
     int TX, TXp, TY, TYp;
-    tile_shape(p->nx, TX, TXp, TY, TYp);
+    tile_shape(p->nx, RX, TX, TXp, TY, TYp);
     a.TX = TX;
     a.TXp = TXp;
     a.TY = TY;
     const int threads = TXp * TYp;
-    const size_t sm = fine_smem<T>(TXp, TYp);
-    PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm));
-    k_heat2d_fine<T><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
+    const size_t sm = fine_smem<T, RX>(TXp, TYp);
+    PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T, RX>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_heat2d_fine<T, RX><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
 
+// FP32: tile width chosen by the autotuner (4 or 8 columns per thread);
+// FP64 and float-float: 4 columns.
+template <class T>
+pit_status launch_fine(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (p->tile_rx == 8) return launch_fine_rx<float, 8>(p, a, nslices, s);
+    }
+    return launch_fine_rx<T, 4>(p, a, nslices, s);
+}
+
 Heat2dArgs make_args(Problem *p, const double *x, double *y, int mode, const MemberState *st) {
     Heat2dArgs a{};
+    a.y32 = nullptr;
     a.x = x;
     a.y = y;
     a.y0 = p->y0.as<double>();
@@ -409,8 +507,8 @@ pit_status launch_xS(Problem *p, const Tin *A, Tout *out, const T *S, double sca
     return PIT_OK;
 }
 
-template <class T>
-pit_status sweep_t(Problem *p, const double *q, double *z, const T *S, const MemberState *st,
+template <class T, class Tin>
+pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const MemberState *st,
                    cudaStream_t s) {
     const int n = p->nx;
     const size_t nn = (size_t)n * n;
@@ -423,7 +521,7 @@ pit_status sweep_t(Problem *p, const double *q, double *z, const T *S, const Mem
     T *h2 = h1 + hat_elems;
     double *ends = reinterpret_cast<double *>(h2 + hat_elems);
     // qhat = S q S
-    PIT_TRY((launch_xS<double, T, T>(p, q, h1, S, 1.0, st, s)));
+    PIT_TRY((launch_xS<Tin, T, T>(p, q, h1, S, 1.0, st, s)));
     PIT_TRY((launch_xS<T, T, T>(p, h1, h2, S, 1.0, st, s)));
     // recurrence over slices, mode by mode
     const int RT = 256;
@@ -483,6 +581,28 @@ pit_status heat2d_setup(Problem *p) {
     PIT_CUDA(cudaMemcpy(p->S64.ptr, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
     PIT_CUDA(cudaMemcpy(p->S32.ptr, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice));
     PIT_CUDA(cudaMemcpy(p->gmode.ptr, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // autotune the FP32 fine kernel's thread tile (4 or 8 columns) on this shape
+    if (p->precision == PIT_MIXED) {
+        DevBuf xin, qout;
+        PIT_TRY(xin.ensure(p->vlen * sizeof(double)));
+        PIT_TRY(qout.ensure(p->vlen * sizeof(float)));
+        PIT_CUDA(cudaMemsetAsync(xin.ptr, 0, p->vlen * sizeof(double), p->stream));
+        const std::string key = "heat2d_fp32_tile|n" + std::to_string(p->nx) + "|slices" +
+                                std::to_string((long long)p->N * p->batch) + "|m" +
+                                std::to_string(p->fine_steps);
+        int choice = 0;
+        const pit_status st = autotune(
+            key, 2,
+            [&](int c) {
+                p->tile_rx = c == 0 ? 4 : 8;
+                return heat2d_fine_f32out(p, xin.as<double>(), qout.as<float>(), nullptr, p->stream);
+            },
+            p->stream, &choice);
+        p->tile_rx = choice == 0 ? 4 : 8;
+        xin.release();
+        qout.release();
+        if (st != PIT_OK) return st;
+    }
     return PIT_OK;
 }
 
@@ -503,8 +623,20 @@ pit_status heat2d_fine_one(Problem *p, const double *x, double *y, int prec, cud
 
 pit_status heat2d_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
                         cudaStream_t s) {
-    if (prec == PIT_FP64) return sweep_t<double>(p, q, z, p->S64.as<double>(), st, s);
-    return sweep_t<float>(p, q, z, p->S32.as<float>(), st, s);
+    if (prec == PIT_FP64) return sweep_t<double, double>(p, q, z, p->S64.as<double>(), st, s);
+    return sweep_t<float, double>(p, q, z, p->S32.as<float>(), st, s);
+}
+
+pit_status heat2d_fine_f32out(Problem *p, const double *x, float *q32, const MemberState *st,
+                              cudaStream_t s) {
+    Heat2dArgs a = make_args(p, x, nullptr, FINE_APPLY, st);
+    a.y32 = q32;
+    return launch_fine<float>(p, a, p->N, s);
+}
+
+pit_status heat2d_sweep_f32in(Problem *p, const float *q32, double *z, const MemberState *st,
+                              cudaStream_t s) {
+    return sweep_t<float, float>(p, q32, z, p->S32.as<float>(), st, s);
 }
 
 }  // namespace pit

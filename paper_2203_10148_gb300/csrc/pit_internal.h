@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -133,6 +134,8 @@ struct Problem {
     DevBuf X, R, Rt, P, S, D, K, W;
     DevBuf partials, states, flags_host_mirror;
     DevBuf fine_tmp;              // serial / misc scratch
+    DevBuf q32;                   // FP32 block-operator rows of the mixed G^{-1}F
+    int tile_rx = 4;              // heat2d FP32 thread-tile width (autotuned)
     ReduceLayout rl{};
     OpTimer timer;
 };
@@ -165,6 +168,11 @@ pit_status heat2d_apply_F(Problem *p, const double *x, double *y, int mode, int 
 pit_status heat2d_sweep(Problem *p, const double *q, double *z, int prec,
                         const MemberState *st, cudaStream_t s);
 pit_status heat2d_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+// mixed G^{-1}F: FP32 fine batch writing FP32 rows, then the FP32-input sweep
+pit_status heat2d_fine_f32out(Problem *p, const double *x, float *q32, const MemberState *st,
+                              cudaStream_t s);
+pit_status heat2d_sweep_f32in(Problem *p, const float *q32, double *z, const MemberState *st,
+                              cudaStream_t s);
 
 pit_status advdiff_setup(Problem *p);
 pit_status advdiff_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
@@ -179,6 +187,11 @@ pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int p
 pit_status dense_sweep(Problem *p, const double *q, double *z, int prec,
                        const MemberState *st, cudaStream_t s);
 pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+
+// Autotuner (tune.cu): index of the fastest of ncand variants run(c), timed
+// with CUDA events on stream s; cached per key, device SM count and process.
+pit_status autotune(const std::string &key, int ncand, const std::function<pit_status(int)> &run,
+                    cudaStream_t s, int *choice);
 
 // ------------------------------------------------------------ Krylov API
 pit_status krylov_prepare(Problem *p);   // allocates vectors, partials, states

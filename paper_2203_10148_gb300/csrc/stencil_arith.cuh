@@ -3,7 +3,10 @@
 // significant bits, evaluated on the FP32 pipe).
 //
 // Float-float uses the error-free transformations of Knuth (TwoSum) and
-// Dekker (FastTwoSum), and the FMA form of the exact product error; the
+// Dekker (FastTwoSum), and the FMA form of the exact product error.  Their
+// additions and products use the __fadd_rn / __fsub_rn / __fmul_rn
+// intrinsics, which the compiler never contracts into FMAs (a contracted
+// s = a + b*c would break the error-free property); the
 // addition is the "sloppy" double-single sum (one TwoSum on the high parts,
 // the low parts added, one FastTwoSum to renormalise), whose error is bounded
 // by a small multiple of 2^-44 (|a| + |b|).
@@ -20,15 +23,15 @@ struct ff {
 };
 
 __device__ __forceinline__ ff two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return ff{s, e};
 }
 
 __device__ __forceinline__ ff fast_two_sum(float a, float b) {
-    const float s = a + b;
-    const float e = b - (s - a);
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
     return ff{s, e};
 }
 
@@ -38,7 +41,7 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 }
 
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const float p = a.hi * b.hi;
+    const float p = __fmul_rn(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, e);
     e = fmaf(a.lo, b.hi, e);
@@ -52,6 +55,35 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
+// ------------------------------------------------------- FP64 <-> FP32
+// Conversions between binary64 and binary32 done with integer operations,
+// written from the IEEE-754 formats.  On GB300 the hardware conversion runs
+// on the FP64 pipe (2 lanes per clock per SM), where a conversion per point
+// per slice costs about a tenth of an FP32 stencil kernel; the integer pipe
+// is 32x wider.  Normal-range values take the integer path and round to
+// nearest even exactly like the hardware conversion; zeros, subnormal
+// results, infinities and NaNs take the (rare) hardware path.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int fe = (int)((hi >> 20) & 0x7ffu) - 896;     // binary32 biased exponent
+    if (fe <= 0 || fe >= 255) return __double2float_rn(x);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 mantissa bits
+    const unsigned rem = lo & 0x1fffffffu;                   // 29 discarded bits
+    unsigned r = (hi & 0x80000000u) | ((unsigned)fe << 23) | m;
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;  // carry may reach the exponent: still exact
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    const unsigned lo = (u & 7u) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
 // ------------------------------------------------------------------ policies
 // V: value type; the stage update is w = u + cc * (vn + vs + vw + ve - 4 vc).
 template <class V>
@@ -60,8 +92,8 @@ struct Arith;
 template <>
 struct Arith<float> {
     static constexpr bool kUInSmem = false;
-    __device__ static float from_d(double x) { return (float)x; }
-    __device__ static double to_d(float v) { return (double)v; }
+    __device__ static float from_d(double x) { return d2f_rn(x); }
+    __device__ static double to_d(float v) { return f2d(v); }
     __device__ static float zero() { return 0.f; }
     __device__ static float sel(bool c, float a, float b) { return c ? a : b; }
     __device__ static float stage(float vn, float vs, float vw, float ve, float vc, float u,
@@ -117,10 +149,24 @@ struct Arith<ff> {
     __device__ static double to_d(ff v) { return ff_to_double(v); }
     __device__ static ff zero() { return ff{0.f, 0.f}; }
     __device__ static ff sel(bool c, ff a, ff b) { return ff{c ? a.hi : b.hi, c ? a.lo : b.lo}; }
+    // w = u + cc (vn + vs + vw + ve - 4 vc): the high parts are summed with
+    // exact TwoSums; their rounding errors and all low parts (each about
+    // 2^-24 of the values) are summed in FP32, which costs about 2^-48 of
+    // the values; the product with cc keeps its exact FMA error term; one
+    // renormalisation at the end.  48 FP32 operations.
     __device__ static ff stage(ff vn, ff vs, ff vw, ff ve, ff vc, ff u, ff cc) {
-        const ff t = ff_add(ff_add(vn, vs), ff_add(vw, ve));
-        const ff l = ff_add(t, ff{-4.f * vc.hi, -4.f * vc.lo});   // exact scaling by -4
-        return ff_add(u, ff_mul(cc, l));
+        const ff a = two_sum(vn.hi, vs.hi);
+        const ff b = two_sum(vw.hi, ve.hi);
+        const ff c = two_sum(a.hi, b.hi);
+        const ff d = two_sum(c.hi, __fmul_rn(-4.f, vc.hi));   // exact scaling by -4
+        const float lo = fmaf(-4.f, vc.lo, ((a.lo + b.lo) + (c.lo + d.lo)) +
+                                              ((vn.lo + vs.lo) + (vw.lo + ve.lo)));
+        const float p = __fmul_rn(cc.hi, d.hi);
+        float e = fmaf(cc.hi, d.hi, -p);
+        e = fmaf(cc.hi, lo, e);
+        e = fmaf(cc.lo, d.hi, e);
+        const ff s = two_sum(u.hi, p);
+        return fast_two_sum(s.hi, s.lo + (u.lo + e));
     }
     __device__ static ff shfl_up(ff v) {
         return ff{__shfl_up_sync(kFullMask, v.hi, 1), __shfl_up_sync(kFullMask, v.lo, 1)};

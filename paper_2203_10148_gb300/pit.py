@@ -79,7 +79,7 @@ EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_cre
            "pit_problem_destroy", "pit_problem_shape", "pit_apply_operator", "pit_serial_fine",
            "pit_bicgstab_solve", "pit_parareal_solve", "pit_block_reduce",
            "pit_problem_set_y0", "pit_kernel_launches", "pit_set_timing", "pit_get_timing",
-           "pit_block_reduce_noalloc"]
+           "pit_block_reduce_noalloc", "pit_selftest_convert"]
 
 TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4,
                 "fine_ff": 5}
@@ -115,6 +115,7 @@ def load() -> C.CDLL:
     lib.pit_block_reduce.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
     lib.pit_block_reduce_noalloc.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
     lib.pit_problem_set_y0.argtypes = [P, P, C.c_int]
+    lib.pit_selftest_convert.argtypes = [P, C.c_int, P, P]
     lib.pit_kernel_launches.argtypes = []
     lib.pit_kernel_launches.restype = C.c_ulonglong
     lib.pit_set_timing.argtypes = [P, C.c_int]
