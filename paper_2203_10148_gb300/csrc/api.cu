@@ -480,6 +480,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32};
     for (DevBuf *b : bufs) b->release();
+    dense_teardown(p);
     p->timer.destroy();
     if (p->stream) cudaStreamDestroy(p->stream);
     delete h;

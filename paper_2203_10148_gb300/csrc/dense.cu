@@ -1,20 +1,345 @@
-// Placeholder for the dense operator family; replaced by the real kernels.
+// Dense-propagator mode: y' = A y with a dense M x M matrix A.
+//
+// Set-up: the fine propagator of one slice is the RK4 step matrix raised to
+// the number of fine steps, Phi = R(dt A)^m with R(Z) = I + Z + Z^2/2 + Z^3/6
+// + Z^4/24 (nested form), by binary powering; the coarse propagator is one
+// implicit-Euler step, G = (I - dT A)^{-1}, by Newton-Schulz iteration
+// X <- X (2I - B X) on B = I - dT A from the scaled start X = B^T/(|B|_1 |B|_inf).
+// Both are FP64 matrix products (cuBLAS DGEMM, once per problem).
+//
+// Fine batch (the N independent slice problems of eq. (2)): all slices at
+// once as one product C = Phi [x_0 ... x_{N-1}], then the shift-subtract of
+// eq. (4).  Coarse sweep (eq. (7), right): z_n = q_n + G z_{n-1}, sequential in n.
+#include <math.h>
+
+#include <vector>
+
+#include <cublas_v2.h>
+
 #include "pit_internal.h"
+#include "stencil_arith.cuh"
 
 namespace pit {
-pit_status dense_setup(Problem *) {
-    set_error("dense: not implemented yet");
-    return PIT_E_UNSUPPORTED;
+namespace {
+
+#define PIT_CUBLAS(call)                                                      \
+    do {                                                                      \
+        cublasStatus_t c_ = (call);                                           \
+        if (c_ != CUBLAS_STATUS_SUCCESS) {                                    \
+            set_error(std::string("cuBLAS error ") + std::to_string((int)c_) + \
+                      " in " #call);                                          \
+            return PIT_E_CUDA;                                                \
+        }                                                                     \
+    } while (0)
+
+// Row-major M x M matrices: in cuBLAS' column-major view a buffer holds the
+// transpose, so C = A B (row-major) is computed as C^T = B^T A^T.
+pit_status mm(cublasHandle_t h, int M, const double *A, const double *B, double *C,
+              double alpha = 1.0, double beta = 0.0) {
+    PIT_CUBLAS(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, M, M, M, &alpha, B, M, A, M, &beta, C, M));
+    return PIT_OK;
 }
-pit_status dense_apply_F(Problem *, const double *, double *, int, int, const MemberState *,
-                          cudaStream_t) {
-    return PIT_E_UNSUPPORTED;
+
+__global__ void k_axpby_identity(double *Y, const double *X, double a, double b, double d, int M) {
+    // Y = a X + b Y + d I
+    const size_t n = (size_t)M * M;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / M, c = i % M;
+        Y[i] = a * X[i] + b * Y[i] + ((r == c) ? d : 0.0);
+    }
 }
-pit_status dense_sweep(Problem *, const double *, double *, int, const MemberState *,
-                        cudaStream_t) {
-    return PIT_E_UNSUPPORTED;
+
+__global__ void k_copy_f32(const double *X, float *Y, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        Y[i] = d2f_rn(X[i]);
 }
-pit_status dense_fine_one(Problem *, const double *, double *, int, cudaStream_t) {
-    return PIT_E_UNSUPPORTED;
+
+__global__ void k_transpose_scale(const double *X, double *Y, int M, double s) {
+    const size_t n = (size_t)M * M;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / M, c = i % M;
+        Y[c * M + r] = s * X[i];
+    }
 }
+
+// |B|_1 and |B|_inf of a row-major matrix (one CTA, fixed order).
+__global__ void k_norms_1_inf(const double *B, int M, double *out) {
+    __shared__ double sh[2][256];
+    double m1 = 0.0, mi = 0.0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        double cs = 0.0, rs = 0.0;
+        for (int i = 0; i < M; ++i) {
+            cs += fabs(B[(size_t)i * M + j]);
+            rs += fabs(B[(size_t)j * M + i]);
+        }
+        m1 = fmax(m1, cs);
+        mi = fmax(mi, rs);
+    }
+    sh[0][threadIdx.x] = m1;
+    sh[1][threadIdx.x] = mi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            a = fmax(a, sh[0][t]);
+            b = fmax(b, sh[1][t]);
+        }
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+// max |(I - B X)_ij|
+__global__ void k_max_abs_dev_identity(const double *P, int M, double *out) {
+    __shared__ double sh[256];
+    double m = 0.0;
+    const size_t n = (size_t)M * M;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const size_t r = i / M, c = i % M;
+        m = fmax(m, fabs(((r == c) ? 1.0 : 0.0) - P[i]));
+    }
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) a = fmax(a, sh[t]);
+        *out = a;
+    }
+}
+
+// Block-operator rows from the product C (row n-1 of C = F x_{n-1}):
+// mode FINE_APPLY: y_n = x_n - C_{n-1}, y_0 = x_0; FINE_RESIDUAL: y_n = C_{n-1} - x_n,
+// y_0 = y0 - x_0; mode 2: y_n = C_{n-1} for n = n_first only.
+template <class TC>
+__global__ void k_dense_rows(const double *x, const TC *C, double *y, const double *y0, int M,
+                             int N, size_t blen, size_t cstride, int mode,
+                             const MemberState *st) {
+    const int b = blockIdx.y;
+    if (st && !(st[b].active && !st[b].skip && !st[b].half)) return;
+    const size_t total = (size_t)(N + 1) * M;
+    const size_t mb = (size_t)b * blen;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = i / M, k = i % M;
+        double v;
+        if (n == 0) v = (mode == FINE_APPLY) ? x[mb + k] : y0[(size_t)b * M + k] - x[mb + k];
+        else {
+            const double c = (double)C[(size_t)b * cstride + (n - 1) * M + k];
+            v = (mode == FINE_APPLY) ? x[mb + i] - c : c - x[mb + i];
+        }
+        y[mb + i] = v;
+    }
+}
+
+cublasHandle_t handle(Problem *p) { return reinterpret_cast<cublasHandle_t>(p->blas); }
+
+pit_status grid_for(size_t n, int &blocks) {
+    blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+    return PIT_OK;
+}
+
+}  // namespace
+
+pit_status dense_setup(Problem *p) {
+    if (p->fine_kind != PIT_STEP_RK4 || p->coarse_kind != PIT_STEP_IE) {
+        set_error("dense: fine must be RK4 (precomputed propagator) and coarse implicit Euler");
+        return PIT_E_UNSUPPORTED;
+    }
+    const int M = p->M;
+    const size_t mm2 = (size_t)M * M;
+    cublasHandle_t h = nullptr;
+    PIT_CUBLAS(cublasCreate(&h));
+    p->blas = h;
+    PIT_CUBLAS(cublasSetStream(h, p->stream));
+    PIT_CUBLAS(cublasSetMathMode(h, CUBLAS_DEFAULT_MATH));
+    DevBuf work;
+    PIT_TRY(work.ensure(4 * mm2 * sizeof(double) + 64));
+    double *A = p->PhiF64.as<double>();      // staged by pit_problem_create
+    double *T1 = work.as<double>(), *T2 = T1 + mm2, *T3 = T2 + mm2, *T4 = T3 + mm2;
+    double *scal = T4 + mm2;
+    int blocks;
+    grid_for(mm2, blocks);
+    cudaStream_t s = p->stream;
+    // G = (I - dTc A)^{-c}: Newton-Schulz for (I - dTc A)^{-1}, then its c-th power
+    PIT_TRY(p->G64.ensure(mm2 * sizeof(double)));
+    double *G = p->G64.as<double>();
+    {
+        const double dtc = p->dT / p->coarse_steps;
+        double *Bm = T1, *X = T2, *P = T3, *Xn = T4;
+        PIT_CUDA(cudaMemsetAsync(Bm, 0, mm2 * sizeof(double), s));
+        k_axpby_identity<<<blocks, 256, 0, s>>>(Bm, A, -dtc, 0.0, 1.0, M);   // B = I - dtc A
+        PIT_LAUNCH_CHECK();
+        k_norms_1_inf<<<1, 256, 0, s>>>(Bm, M, scal);
+        PIT_LAUNCH_CHECK();
+        double nrm[2];
+        PIT_CUDA(cudaMemcpyAsync(nrm, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PIT_CUDA(cudaStreamSynchronize(s));
+        k_transpose_scale<<<blocks, 256, 0, s>>>(Bm, X, M, 1.0 / (nrm[0] * nrm[1]));
+        PIT_LAUNCH_CHECK();
+        bool ok = false;
+        double prev = 1e300;
+        for (int it = 0; it < 200; ++it) {
+            PIT_TRY(mm(h, M, Bm, X, P));                       // P = B X
+            k_max_abs_dev_identity<<<1, 256, 0, s>>>(P, M, scal);
+            PIT_LAUNCH_CHECK();
+            double dev;
+            PIT_CUDA(cudaMemcpyAsync(&dev, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+            PIT_CUDA(cudaStreamSynchronize(s));
+            if (!(dev < 1e300)) break;
+            // converged: at the rounding floor (no longer halving) or tiny
+            if (dev < 1e-15 * M || (dev < 1e-10 && dev > 0.5 * prev)) {
+                ok = true;
+                break;
+            }
+            prev = dev;
+            k_axpby_identity<<<blocks, 256, 0, s>>>(P, P, -1.0, 0.0, 2.0, M);   // P = 2I - B X
+            PIT_LAUNCH_CHECK();
+            PIT_TRY(mm(h, M, X, P, Xn));                       // X <- X (2I - B X)
+            std::swap(X, Xn);
+        }
+        if (!ok) {
+            set_error("dense: Newton-Schulz inverse of I - dT A did not converge");
+            return PIT_E_INVALID;
+        }
+        // G = X^c by repeated products (c coarse steps)
+        PIT_CUDA(cudaMemcpyAsync(G, X, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int c = 1; c < p->coarse_steps; ++c) {
+            PIT_TRY(mm(h, M, G, X, P));
+            PIT_CUDA(cudaMemcpyAsync(G, P, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    // Phi = R(dt A)^m, R(Z) = I + Z (I + Z/2 (I + Z/3 (I + Z/4)))
+    {
+        const double dt = p->dT / p->fine_steps;
+        double *R = T1, *W = T2, *Base = T3, *Res = T4;
+        // W = I + (dt/4) A
+        PIT_CUDA(cudaMemsetAsync(W, 0, mm2 * sizeof(double), s));
+        k_axpby_identity<<<blocks, 256, 0, s>>>(W, A, dt / 4.0, 0.0, 1.0, M);
+        PIT_LAUNCH_CHECK();
+        const double coef[3] = {dt / 3.0, dt / 2.0, dt};
+        for (int k = 0; k < 3; ++k) {
+            // W <- I + coef_k A W
+            PIT_TRY(mm(h, M, A, W, R, coef[k], 0.0));
+            PIT_CUDA(cudaMemsetAsync(W, 0, mm2 * sizeof(double), s));
+            k_axpby_identity<<<blocks, 256, 0, s>>>(W, R, 1.0, 0.0, 1.0, M);
+            PIT_LAUNCH_CHECK();
+        }
+        // binary powering of W to the m-th power
+        PIT_CUDA(cudaMemcpyAsync(Base, W, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        PIT_CUDA(cudaMemsetAsync(Res, 0, mm2 * sizeof(double), s));
+        k_axpby_identity<<<blocks, 256, 0, s>>>(Res, Res, 0.0, 0.0, 1.0, M);   // Res = I
+        PIT_LAUNCH_CHECK();
+        int m = p->fine_steps;
+        while (m > 0) {
+            if (m & 1) {
+                PIT_TRY(mm(h, M, Res, Base, R));
+                std::swap(Res, R);
+            }
+            m >>= 1;
+            if (m) {
+                PIT_TRY(mm(h, M, Base, Base, R));
+                std::swap(Base, R);
+            }
+        }
+        PIT_CUDA(cudaMemcpyAsync(p->PhiF64.ptr, Res, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    // FP32 copies for the mixed path
+    PIT_TRY(p->PhiF_hi.ensure(mm2 * sizeof(float)));
+    PIT_TRY(p->G32.ensure(mm2 * sizeof(float)));
+    k_copy_f32<<<blocks, 256, 0, s>>>(p->PhiF64.as<double>(), p->PhiF_hi.as<float>(), mm2);
+    PIT_LAUNCH_CHECK();
+    k_copy_f32<<<blocks, 256, 0, s>>>(G, p->G32.as<float>(), mm2);
+    PIT_LAUNCH_CHECK();
+    PIT_CUDA(cudaStreamSynchronize(s));
+    work.release();
+    return PIT_OK;
+}
+
+// C (batch x N x M, row n = Phi x_n for n < N) in FP64 or FP32.
+static pit_status dense_product(Problem *p, const double *x, int prec, cudaStream_t s) {
+    const int M = p->M, N = p->N;
+    cublasHandle_t h = handle(p);
+    PIT_CUBLAS(cublasSetStream(h, s));
+    const size_t cstride = (size_t)N * M;
+    if (prec == PIT_MIXED) {
+        // FP32 copy of x, then FP32 product
+        PIT_TRY(p->q32.ensure(p->vlen * sizeof(float)));
+        PIT_TRY(p->dense_scratch.ensure((size_t)p->batch * cstride * sizeof(float)));
+        int blocks;
+        grid_for(p->vlen, blocks);
+        k_copy_f32<<<blocks, 256, 0, s>>>(x, p->q32.as<float>(), p->vlen);
+        PIT_LAUNCH_CHECK();
+        const float one = 1.f, zero = 0.f;
+        PIT_CUBLAS(cublasSgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, M, N, M, &one,
+                                             p->PhiF_hi.as<float>(), M, 0, p->q32.as<float>(), M,
+                                             (long long)p->blen, &zero,
+                                             p->dense_scratch.as<float>(), M, (long long)cstride,
+                                             p->batch));
+        return PIT_OK;
+    }
+    PIT_TRY(p->dense_scratch.ensure((size_t)p->batch * cstride * sizeof(double)));
+    const double one = 1.0, zero = 0.0;
+    PIT_CUBLAS(cublasDgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, M, N, M, &one,
+                                         p->PhiF64.as<double>(), M, 0, x, M, (long long)p->blen,
+                                         &zero, p->dense_scratch.as<double>(), M,
+                                         (long long)cstride, p->batch));
+    return PIT_OK;
+}
+
+pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                         const MemberState *st, cudaStream_t s) {
+    PIT_TRY(dense_product(p, x, prec, s));
+    int blocks;
+    grid_for(p->blen, blocks);
+    const size_t cstride = (size_t)p->N * p->M;
+    if (prec == PIT_MIXED)
+        k_dense_rows<float><<<dim3(blocks, p->batch), 256, 0, s>>>(
+            x, p->dense_scratch.as<float>(), y, p->y0.as<double>(), p->M, p->N, p->blen, cstride,
+            mode, st);
+    else
+        k_dense_rows<double><<<dim3(blocks, p->batch), 256, 0, s>>>(
+            x, p->dense_scratch.as<double>(), y, p->y0.as<double>(), p->M, p->N, p->blen, cstride,
+            mode, st);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
+pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
+    // y (block n) = Phi x (block n-1) for every member; FP64
+    (void)prec;
+    const int M = p->M;
+    cublasHandle_t h = handle(p);
+    PIT_CUBLAS(cublasSetStream(h, s));
+    const double one = 1.0, zero = 0.0;
+    PIT_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, p->batch, M, &one, p->PhiF64.as<double>(),
+                           M, x, (int)p->blen, &zero, y, (int)p->blen));
+    return PIT_OK;
+}
+
+void dense_teardown(Problem *p) {
+    if (p->blas) cublasDestroy(handle(p));
+    p->blas = nullptr;
+}
+
+pit_status dense_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
+                       cudaStream_t s) {
+    (void)st;
+    (void)prec;
+    const int M = p->M;
+    cublasHandle_t h = handle(p);
+    PIT_CUBLAS(cublasSetStream(h, s));
+    if (q != z)
+        PIT_CUDA(cudaMemcpyAsync(z, q, p->vlen * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const double one = 1.0;
+    // z_n += G z_{n-1} for all members at once (member stride blen)
+    for (int n = 1; n <= p->N; ++n)
+        PIT_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, p->batch, M, &one,
+                               p->G64.as<double>(), M, z + (size_t)(n - 1) * M, (int)p->blen, &one,
+                               z + (size_t)n * M, (int)p->blen));
+    return PIT_OK;
+}
+
 }  // namespace pit

@@ -129,6 +129,7 @@ struct Problem {
     // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)
     DevBuf PhiF64, G64, PhiF_hi, PhiF_lo, G32;
     DevBuf dense_scratch;
+    void *blas = nullptr;         // cuBLAS handle (dense set-up and FP64 products)
 
     // Krylov workspace
     DevBuf X, R, Rt, P, S, D, K, W;
@@ -187,6 +188,7 @@ pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int p
 pit_status dense_sweep(Problem *p, const double *q, double *z, int prec,
                        const MemberState *st, cudaStream_t s);
 pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+void dense_teardown(Problem *p);
 
 // Autotuner (tune.cu): index of the fastest of ncand variants run(c), timed
 // with CUDA events on stream s; cached per key, device SM count and process.
