@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--workload", default="heat2d", choices=["heat2d", "dense"],
+                    help="heat2d: 2D heat 128^2, N = 512 (the headline); dense: M = 1024, N = 4096")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
@@ -81,6 +83,9 @@ def dist_env():
 
 
 def workload(args, rank, step=0):
+    if args.workload == "dense":
+        seed = inputs.SEED_DENSE + 7919 * rank + 104729 * step
+        return inputs.dense(batch=args.batch, seed=seed, tol=1e-6)
     seed = inputs.SEED_HEAT2D + 7919 * rank + 104729 * step
     return inputs.heat2d(n=args.n, N=args.N, batch=args.batch, seed=seed, tol=1e-6)
 
@@ -228,6 +233,56 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- roofline
+
+def roofline(w, timing, peaks, nsm):
+    """Roofline of the dominant fine-propagator kernel class, from the
+    per-class CUDA-event times recorded inside the timed solves."""
+    fine = {k: timing[k] for k in ("fine_fp32", "fine_ff", "fine_fp64") if timing[k][0]}
+    if not fine:
+        return None
+    dom = max(fine, key=lambda k: fine[k][1])
+    calls, ms = timing[dom]
+    avg_ms = ms / max(calls, 1)
+    sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+    if w.kind == "dense":
+        flop = 2.0 * w.batch * w.N * w.M * w.M                # one product Phi [x_0 .. x_N-1]
+        if dom == "fine_fp32":
+            bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
+            peak = 0.5 * bf16                                    # TF32 dense = BF16 / 2 (nominal)
+            exe = 3.0 * flop                                     # three TF32 products (hi*hi, hi*lo, lo*hi)
+            return {"bound": "tensor", "kernel": "k_dense_tf32x3 (tcgen05)", "achieved": exe / (avg_ms / 1e3) / 1e12,
+                    "peak": peak, "unit": "TFLOP/s (TF32)", "frac": exe / (avg_ms / 1e3) / 1e12 / peak,
+                    "traffic": None, "launch_ms": avg_ms, "launches": calls,
+                    "algorithmic_tflops": flop / (avg_ms / 1e3) / 1e12,
+                    "peak_source": "measured bf16 burst x 0.5 (nominal TF32/BF16 ratio), of measured"}
+        peak = FP64_LANES_PER_SM * 2 * nsm * sm_max * 1e6 / 1e12
+        return {"bound": "alu", "kernel": "cuBLAS DGEMM (FP64 true residual)",
+                "achieved": flop / (avg_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s (FP64)",
+                "frac": flop / (avg_ms / 1e3) / 1e12 / peak, "traffic": None, "launch_ms": avg_ms,
+                "launches": calls, "peak_source": "derived: 4 FP64 flop/clk/SM x SMs x max SM clock"}
+    point_steps = w.batch * w.N * w.fine[1] * w.M
+    lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
+    peak = lanes * nsm * sm_max * 1e6 / 1e12
+    achieved = point_steps * OPS_PER_POINT_STEP[dom] / (avg_ms / 1e3) / 1e12
+    kname = KERNEL_NAMES[dom]
+    tr = traffic_for(kname)
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+            "unit": "Tops/s (%s pipe lane-ops)" % ("FP64" if dom == "fine_fp64" else "FP32"),
+            "frac": achieved / peak,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "algorithmic_bytes": 2 * 8 * point_steps // (w.fine[1]),
+            "launch_ms": avg_ms, "launches": calls,
+            "flop_rate_tflops": point_steps * FLOP_PER_POINT_STEP / (avg_ms / 1e3) / 1e12,
+            "peak_source": f"derived: {lanes} lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz (max SM clock)"}
+    f32 = timing["fine_fp32"]
+    if f32[0]:
+        a32 = point_steps * OPS_PER_POINT_STEP["fine_fp32"] / (f32[1] / f32[0] / 1e3) / 1e12
+        roof["fine_fp32"] = {"launch_ms": f32[1] / f32[0], "achieved": a32,
+                             "frac": a32 / (FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12)}
+    return roof
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def run_ours(args):
@@ -304,32 +359,8 @@ def run_ours(args):
     if rank == 0:
         peaks = load_peaks()
         clocks = clk.summary(local)
-        # dominant single-kernel class and its roofline (FP32 / FP64 pipe operations)
-        fine = {k: timing[k] for k in ("fine_fp32", "fine_ff", "fine_fp64")}
-        dom = max(fine, key=lambda k: fine[k][1])
-        calls, ms = timing[dom]
-        avg_ms = ms / max(calls, 1)
-        sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
         nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        point_steps = w.batch * w.N * w.fine[1] * w.M
-        lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
-        peak = lanes * nsm * sm_max * 1e6 / 1e12
-        achieved = point_steps * OPS_PER_POINT_STEP[dom] / (avg_ms / 1e3) / 1e12
-        kname = KERNEL_NAMES[dom]
-        tr = traffic_for(kname)
-        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "Tops/s (%s pipe lane-ops)" % ("FP64" if dom == "fine_fp64" else "FP32"),
-                "frac": achieved / peak,
-                "traffic": tr["dram_bytes_per_launch"] if tr else None,
-                "algorithmic_bytes": 2 * 8 * point_steps // (w.fine[1]),
-                "launch_ms": avg_ms, "launches": calls,
-                "flop_rate_tflops": point_steps * FLOP_PER_POINT_STEP / (avg_ms / 1e3) / 1e12,
-                "peak_source": f"derived: {lanes} lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz (max SM clock)"}
-        f32 = timing["fine_fp32"]
-        if f32[0]:
-            a32 = point_steps * OPS_PER_POINT_STEP["fine_fp32"] / (f32[1] / f32[0] / 1e3) / 1e12
-            roof["fine_fp32"] = {"launch_ms": f32[1] / f32[0], "achieved": a32,
-                                 "frac": a32 / (FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12)}
+        roof = roofline(w, timing, peaks, nsm)
         breakdown = {k: {"calls": c, "ms": m, "share": m / total_ms} for k, (c, m) in timing.items()}
         line = {"metric": "PiT solves/s (rel err <= 1e-6 vs FP64 path)", "value": value,
                 "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,

@@ -187,6 +187,20 @@ pit_status op_serial(Problem *p, double *Lam, int prec, cudaStream_t s) {
     return PIT_OK;
 }
 
+// Reads (and clears) the problem's device error word; PIT_E_TIMEOUT when a
+// bounded device-side wait gave up.  Synchronises the stream.
+static pit_status check_errword(Problem *p, cudaStream_t s) {
+    int w = 0;
+    PIT_CUDA(cudaMemcpyAsync(&w, p->errword.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
+    if (w != 0) {
+        PIT_CUDA(cudaMemsetAsync(p->errword.ptr, 0, sizeof(int), s));
+        set_error("a bounded device-side wait (grid barrier) expired; results are invalid");
+        return PIT_E_TIMEOUT;
+    }
+    return PIT_OK;
+}
+
 // Sweep arithmetic: FP32 transforms / FP64 running sums for PIT_MIXED, FP64 otherwise.
 static int sweep_prec(int prec) { return prec == PIT_MIXED ? PIT_MIXED : PIT_FP64; }
 
@@ -438,6 +452,9 @@ pit_status pit_problem_create(const pit_problem_desc *d, pit_problem_t *out) {
     if (e != cudaSuccess) return fail(cuda_fail(e, "copy y0", __FILE__, __LINE__));
     if ((s = p->fine_tmp.ensure(std::max<size_t>(4096, 64 * (size_t)d->batch))) != PIT_OK)
         return fail(s);
+    if ((s = p->errword.ensure(sizeof(int))) != PIT_OK) return fail(s);
+    e = cudaMemset(p->errword.ptr, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "clear error word", __FILE__, __LINE__));
     switch (p->kind) {
     case PIT_OP_HEAT1D: s = heat1d_setup(p); break;
     case PIT_OP_HEAT2D: s = heat2d_setup(p); break;
@@ -478,7 +495,8 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->vy32, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
-                      &p->flags_host_mirror, &p->fine_tmp, &p->q32};
+                      &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32,
+                      &p->errword, &p->PhiTh, &p->PhiTl, &p->tc_split};
     for (DevBuf *b : bufs) b->release();
     dense_teardown(p);
     p->timer.destroy();
@@ -532,7 +550,7 @@ pit_status pit_apply_operator(pit_problem_t h, int which, int precision, const d
     }
     if (!on_device) {
         PIT_TRY(from_device(p, y, dy, 0, s));
-        PIT_CUDA(cudaStreamSynchronize(s));
+        PIT_TRY(check_errword(p, s));
     }
     return PIT_OK;
 }
@@ -552,8 +570,7 @@ pit_status pit_serial_fine(pit_problem_t h, int precision, double *Lam, int on_d
     }
     PIT_TRY(op_serial(p, d, precision, s));
     if (!on_device) PIT_TRY(from_device(p, Lam, d, 0, s));
-    PIT_CUDA(cudaStreamSynchronize(s));
-    return PIT_OK;
+    return check_errword(p, s);
 }
 
 pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *Xu,
@@ -706,8 +723,11 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
     }
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (auto &i : inf) i.seconds = secs;
+    const pit_status ew = check_errword(p, s);
+    if (ew != PIT_OK)
+        for (auto &i : inf) i.status = ew;
     if (info) std::copy(inf.begin(), inf.end(), info);
-    return worst_status(status);
+    return ew != PIT_OK ? ew : worst_status(status);
 }
 
 pit_status pit_parareal_solve(pit_problem_t h, int kmax, double tol, double *Xu, int on_device,
@@ -766,12 +786,13 @@ pit_status pit_parareal_solve(pit_problem_t h, int kmax, double tol, double *Xu,
     PIT_TRY(from_device(p, Xu, X, on_device, s));
     PIT_CUDA(cudaStreamSynchronize(s));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const pit_status ew = check_errword(p, s);
     for (int b = 0; b < B; ++b) {
-        inf[b].status = status[b];
+        inf[b].status = ew != PIT_OK ? ew : status[b];
         inf[b].seconds = secs;
     }
     if (info) std::copy(inf.begin(), inf.end(), info);
-    return worst_status(status);
+    return ew != PIT_OK ? ew : worst_status(status);
 }
 
 pit_status pit_problem_set_y0(pit_problem_t h, const double *y0, int on_device) {

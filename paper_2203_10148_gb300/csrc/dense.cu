@@ -141,6 +141,228 @@ pit_status grid_for(size_t n, int &blocks) {
     return PIT_OK;
 }
 
+
+// --------------------------------------------------- persistent coarse sweep
+// z_n = q_n + G z_{n-1} (eq. (7), right) as an exact chunked scan in one
+// cooperative launch.  The N+1 blocks are cut into C chunks of L blocks.
+//   phase 1: every chunk runs the recurrence from zero; only its last value
+//            w_c is kept (L sequential steps, the C chunks side by side);
+//   phase 2: carries e_c = w_c + G^L e_{c-1} into each chunk (C steps);
+//   phase 3: every chunk re-runs the recurrence from its carry and stores
+//            each z_n (L steps).
+// Every CTA keeps `rows` rows of G (and of G^L) in shared memory and computes
+// those rows of G v for all columns (chunks x members) each step; columns
+// live in global memory (read through L2) between steps, separated by a
+// grid barrier.  With C = 1 this is the plain sequential sweep.
+constexpr int SW_THREADS = 256;
+constexpr int SW_MAXROWS = 8;
+constexpr long long SW_SPIN_LIMIT = 1LL << 24;   // bounded barrier wait
+
+template <class T>
+struct SweepArgs {
+    const double *q;
+    double *z;
+    int M, N, batch;
+    size_t blen;
+    int L, C, rows;
+    const T *G, *GL;
+    T *Za, *Zb, *E;
+    unsigned *bar;        // [0] arrivals, [1] generation
+    int *err;
+    const MemberState *st;
+};
+
+// Grid-wide barrier with a bounded wait; false when it gave up (error set).
+__device__ bool grid_barrier(unsigned *bar, int *err, unsigned nblocks) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > SW_SPIN_LIMIT || *(volatile int *)err) {
+                    atomicExch(err, PIT_E_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <class T>
+__device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
+
+// Partial dot products of this CTA's rows of Gm with column v over
+// k in [k0, k1), accumulated into acc (per lane; reduced by the caller).
+template <class T>
+__device__ __forceinline__ void rows_dot(const T *Gm, const T *v, int M, int rows, int k0, int k1,
+                                         T (&acc)[SW_MAXROWS]) {
+    constexpr int U = 16;                 // column loads in flight per lane
+    const int lane = threadIdx.x & 31;
+    for (int kb = k0 + lane; kb < k1; kb += 32 * U) {
+        T xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = kb + 32 * u;
+            xv[u] = (k < k1) ? ld_cg(v + min(k, k1 - 1)) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = min(kb + 32 * u, k1 - 1);
+#pragma unroll
+            for (int r = 0; r < SW_MAXROWS; ++r)
+                if (r < rows) acc[r] = fma(Gm[(size_t)r * M + k], xv[u], acc[r]);
+        }
+    }
+}
+
+// out[col][row] = q_blk[row] + (Gm in[col])[row] for this CTA's rows and
+// every column col = (member b, chunk c) with blk = c*L + i <= N; columns
+// whose chunk has ended (or whose member is inactive) keep their value.
+// Warps split the columns, and split k as well when there are fewer columns
+// than warps; partial sums meet in shared memory.
+template <class T>
+__device__ void sweep_step(const SweepArgs<T> &a, const T *Gm, const T *in, T *out, int i,
+                           bool from_zero, bool store, int r0, T *red) {
+    constexpr int NW = SW_THREADS / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncols = a.batch * a.C;
+    const int S = ncols >= NW ? 1 : NW / ncols;        // k segments per column
+    const int per_round = NW / S;                        // columns per round
+    const int seg_len = (a.M + S - 1) / S;
+    for (int base = 0; base < ncols; base += per_round) {
+        const int cl = warp / S, seg = warp % S;
+        const int col = base + cl;
+        T acc[SW_MAXROWS];
+#pragma unroll
+        for (int r = 0; r < SW_MAXROWS; ++r) acc[r] = T(0);
+        if (col < ncols && !from_zero) {
+            const int k0 = seg * seg_len, k1 = min(a.M, k0 + seg_len);
+            rows_dot(Gm, in + (size_t)col * a.M, a.M, a.rows, k0, k1, acc);
+        }
+#pragma unroll
+        for (int r = 0; r < SW_MAXROWS; ++r) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int r = 0; r < SW_MAXROWS; ++r) red[(cl * NW + seg) * SW_MAXROWS + r] = acc[r];
+        }
+        __syncthreads();
+        // finalize: thread t -> (column in round, row)
+        const int t = threadIdx.x;
+        if (t < per_round * SW_MAXROWS) {
+            const int cl2 = t / SW_MAXROWS, r = t % SW_MAXROWS;
+            const int col2 = base + cl2, row = r0 + r;
+            if (col2 < ncols && r < a.rows && row < a.M) {
+                const int b = col2 / a.C, c = col2 % a.C;
+                const int blk = c * a.L + i;
+                const bool live = blk <= a.N &&
+                    (a.st == nullptr || (a.st[b].active && !a.st[b].skip && !a.st[b].half));
+                T val = T(0);
+                for (int sg = 0; sg < S; ++sg) val += red[(cl2 * NW + sg) * SW_MAXROWS + r];
+                T res;
+                if (live) {
+                    const size_t at = (size_t)b * a.blen + (size_t)blk * a.M + row;
+                    res = (T)a.q[at] + val;
+                    if (store) a.z[at] = (double)res;
+                } else {
+                    res = from_zero ? T(0) : ld_cg(in + (size_t)col2 * a.M + row);
+                }
+                __stcg(out + (size_t)col2 * a.M + row, res);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(SW_THREADS) k_dense_sweep(SweepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Gs = reinterpret_cast<T *>(smem_raw);
+    T *GLs = Gs + (size_t)SW_MAXROWS * a.M;
+    T *red = GLs + (size_t)SW_MAXROWS * a.M;    // (SW_THREADS / 32)^2 * SW_MAXROWS partials
+    const int r0 = blockIdx.x * a.rows;
+    const unsigned nb = gridDim.x;
+    for (size_t t = threadIdx.x; t < (size_t)a.rows * a.M; t += SW_THREADS) {
+        const int r = (int)(t / a.M), k = (int)(t % a.M);
+        const bool ok = r0 + r < a.M;
+        Gs[t] = ok ? a.G[(size_t)(r0 + r) * a.M + k] : T(0);
+        if (a.C > 1) GLs[t] = ok ? a.GL[(size_t)(r0 + r) * a.M + k] : T(0);
+    }
+    __syncthreads();
+    T *in = a.Za, *out = a.Zb;
+    if (a.C > 1) {
+        // phase 1: chunk-local recurrences from zero
+        for (int i = 0; i < a.L; ++i) {
+            sweep_step(a, Gs, in, out, i, i == 0, false, r0, red);
+            if (!grid_barrier(a.bar, a.err, nb)) return;
+            T *t = in; in = out; out = t;
+        }
+        // phase 2: carries E[c] = W[c-1] + G^L E[c-1], E[0] = 0 (columns of `in` hold W)
+        for (int c = 0; c < a.C; ++c) {
+            for (int b = 0; b < a.batch; ++b) {
+                T acc[SW_MAXROWS];
+#pragma unroll
+                for (int r = 0; r < SW_MAXROWS; ++r) acc[r] = T(0);
+                constexpr int NW = SW_THREADS / 32;
+                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                const int col = b * a.C + c;
+                const int seg_len = (a.M + NW - 1) / NW;
+                if (c > 0) {
+                    const int k0 = warp * seg_len, k1 = min(a.M, k0 + seg_len);
+                    rows_dot(GLs, a.E + (size_t)(col - 1) * a.M, a.M, a.rows, k0, k1, acc);
+                }
+#pragma unroll
+                for (int r = 0; r < SW_MAXROWS; ++r) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int r = 0; r < SW_MAXROWS; ++r) red[warp * SW_MAXROWS + r] = acc[r];
+                }
+                __syncthreads();
+                if (threadIdx.x < a.rows && r0 + (int)threadIdx.x < a.M) {
+                    const int r = threadIdx.x, row = r0 + r;
+                    T val = T(0);
+                    for (int w = 0; w < NW; ++w) val += red[w * SW_MAXROWS + r];
+                    const T wv = (c > 0) ? ld_cg(in + (size_t)(col - 1) * a.M + row) : T(0);
+                    __stcg(a.E + (size_t)col * a.M + row, wv + val);
+                }
+                __syncthreads();
+            }
+            if (!grid_barrier(a.bar, a.err, nb)) return;
+        }
+        // phase 3 starts from the carries
+        in = a.E;
+        out = a.Za;
+    }
+    // phase 3: re-run every chunk from its carry (zero when C = 1), storing z
+    T *ping = a.Za, *pong = a.Zb;
+    for (int i = 0; i < a.L; ++i) {
+        sweep_step(a, Gs, in, out, i, a.C == 1 && i == 0, true, r0, red);
+        if (!grid_barrier(a.bar, a.err, nb)) return;
+        in = out;
+        out = (out == ping) ? pong : ping;
+    }
+}
+
 }  // namespace
 
 pit_status dense_setup(Problem *p) {
@@ -246,6 +468,30 @@ pit_status dense_setup(Problem *p) {
         }
         PIT_CUDA(cudaMemcpyAsync(p->PhiF64.ptr, Res, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
+    // G^L for the chunked sweep of the mixed path, L = ceil(sqrt(N + 1))
+    {
+        int L = (int)ceil(sqrt((double)(p->N + 1)));
+        p->sweep_L = L;
+        double *Res = T1, *Base = T2, *R = T3;
+        PIT_CUDA(cudaMemcpyAsync(Base, G, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        PIT_CUDA(cudaMemsetAsync(Res, 0, mm2 * sizeof(double), s));
+        k_axpby_identity<<<blocks, 256, 0, s>>>(Res, Res, 0.0, 0.0, 1.0, M);
+        PIT_LAUNCH_CHECK();
+        while (L > 0) {
+            if (L & 1) {
+                PIT_TRY(mm(h, M, Res, Base, R));
+                std::swap(Res, R);
+            }
+            L >>= 1;
+            if (L) {
+                PIT_TRY(mm(h, M, Base, Base, R));
+                std::swap(Base, R);
+            }
+        }
+        PIT_TRY(p->GL32.ensure(mm2 * sizeof(float)));
+        k_copy_f32<<<blocks, 256, 0, s>>>(Res, p->GL32.as<float>(), mm2);
+        PIT_LAUNCH_CHECK();
+    }
     // FP32 copies for the mixed path
     PIT_TRY(p->PhiF_hi.ensure(mm2 * sizeof(float)));
     PIT_TRY(p->G32.ensure(mm2 * sizeof(float)));
@@ -253,6 +499,9 @@ pit_status dense_setup(Problem *p) {
     PIT_LAUNCH_CHECK();
     k_copy_f32<<<blocks, 256, 0, s>>>(G, p->G32.as<float>(), mm2);
     PIT_LAUNCH_CHECK();
+    // TF32 splits of Phi for the tensor-core product
+    p->use_tc = dense_tc_supported(p);
+    if (p->use_tc) PIT_TRY(dense_tc_split_phi(p));
     PIT_CUDA(cudaStreamSynchronize(s));
     work.release();
     return PIT_OK;
@@ -291,6 +540,7 @@ static pit_status dense_product(Problem *p, const double *x, int prec, cudaStrea
 
 pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                          const MemberState *st, cudaStream_t s) {
+    if (prec == PIT_MIXED && p->use_tc) return dense_tc_apply(p, x, y, nullptr, mode, st, s);
     PIT_TRY(dense_product(p, x, prec, s));
     int blocks;
     grid_for(p->blen, blocks);
@@ -324,17 +574,64 @@ void dense_teardown(Problem *p) {
     p->blas = nullptr;
 }
 
+template <class T>
+static pit_status persistent_sweep(Problem *p, const double *q, double *z, const T *G, const T *GL,
+                                   int L, int C, const MemberState *st, cudaStream_t s,
+                                   bool *launched) {
+    *launched = false;
+    int dev = 0, sms = 0, coop = 0;
+    PIT_CUDA(cudaGetDevice(&dev));
+    PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PIT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    const int M = p->M;
+    const int rows = (M + sms - 1) / sms;
+    if (!coop || rows > SW_MAXROWS) return PIT_OK;            // caller falls back
+    const int grid = (M + rows - 1) / rows;
+    const size_t smem = (2 * (size_t)SW_MAXROWS * M + (size_t)SW_MAXROWS * 64) * sizeof(T);
+    if (smem > 200 * 1024) return PIT_OK;
+    PIT_CUDA(cudaFuncSetAttribute(k_dense_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    int per_sm = 0;
+    PIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_sweep<T>, SW_THREADS,
+                                                           smem));
+    if (per_sm * sms < grid) return PIT_OK;
+    const size_t ncols = (size_t)p->batch * C;
+    const size_t colbytes = ncols * M * sizeof(T);
+    PIT_TRY(p->hat.ensure(3 * colbytes + 64));
+    T *Za = p->hat.as<T>();
+    T *Zb = Za + ncols * M;
+    T *E = Zb + ncols * M;
+    unsigned *bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(p->hat.ptr) + 3 * colbytes);
+    PIT_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    SweepArgs<T> a{q, z, M, p->N, p->batch, p->blen, L, C, rows, G, GL, Za, Zb, E, bar,
+                   p->errword.as<int>(), st};
+    void *args[] = {&a};
+    PIT_CUDA(cudaLaunchCooperativeKernel((const void *)k_dense_sweep<T>, dim3(grid), dim3(SW_THREADS),
+                                         args, smem, s));
+    PIT_LAUNCH_CHECK();
+    *launched = true;
+    return PIT_OK;
+}
+
 pit_status dense_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
                        cudaStream_t s) {
-    (void)st;
-    (void)prec;
+    bool done = false;
+    if (prec == PIT_MIXED) {
+        const int L = p->sweep_L, C = (p->N + L) / L;   // ceil((N + 1) / L)
+        PIT_TRY(persistent_sweep<float>(p, q, z, p->G32.as<float>(), p->GL32.as<float>(), L, C, st,
+                                        s, &done));
+    } else {
+        PIT_TRY(persistent_sweep<double>(p, q, z, p->G64.as<double>(), nullptr, p->N + 1, 1, st, s,
+                                         &done));
+    }
+    if (done) return PIT_OK;
+    // fallback: one FP64 product per slice
     const int M = p->M;
     cublasHandle_t h = handle(p);
     PIT_CUBLAS(cublasSetStream(h, s));
     if (q != z)
         PIT_CUDA(cudaMemcpyAsync(z, q, p->vlen * sizeof(double), cudaMemcpyDeviceToDevice, s));
     const double one = 1.0;
-    // z_n += G z_{n-1} for all members at once (member stride blen)
     for (int n = 1; n <= p->N; ++n)
         PIT_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, p->batch, M, &one,
                                p->G64.as<double>(), M, z + (size_t)(n - 1) * M, (int)p->blen, &one,

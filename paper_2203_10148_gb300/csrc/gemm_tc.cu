@@ -1,0 +1,358 @@
+// Dense fine propagator on the 5th-generation tensor cores (tcgen05):
+//   C[r][c] = sum_k X[r][k] Phi[c][k]      (r = member * (N+1) + slice, c = state index)
+// i.e. C row r = Phi x_r, for all slices of all members at once, in split
+// TF32 ("3xTF32"): X = Xh + Xl and Phi = Ph + Pl with each part a TF32
+// value, and C = Xh Ph^T + Xh Pl^T + Xl Ph^T accumulated in FP32 (the Xl Pl^T
+// term is below FP32 resolution).  The epilogue writes the block-operator
+// rows of eq. (4): y_{n+1} = x_{n+1} - C[r] (or the residual form).
+//
+// Kernel structure: one 128 x 128 output tile per CTA, K in 32-element
+// (128-byte) stages, 3-stage ring in shared memory filled by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) and drained by tcgen05.mma
+// (kind::tf32, M = 128, N = 128, K = 8 per instruction) issued by one
+// thread; the FP32 accumulator lives in tensor memory (128 columns) and is
+// read back by four warps with tcgen05.ld.  mbarriers hand stages between
+// the TMA thread, the MMA thread and the tensor core; every wait is
+// bounded and reports PIT_E_TIMEOUT through the problem's error word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "pit_internal.h"
+#include "stencil_arith.cuh"
+
+namespace pit {
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_STAGES = 3, TC_THREADS = 128;
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;                  // 16 KB per operand tile
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;                 // Ah, Al, Bh, Bl
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;  // + alignment + barriers
+constexpr long long TC_SPIN = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on the phase with the given parity; false (and the error
+// word set) when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+    for (long long i = 0; i < TC_SPIN; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 1023) == 1023 && *(volatile int *)err) return false;
+    }
+    atomicExch(err, PIT_E_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte offset),
+// descriptor version 1, swizzle mode 2 (128B).
+__device__ __forceinline__ uint64_t smem_desc(const void *tile) {
+    const uint64_t addr = smem_u32(tile);
+    return ((addr & 0x3FFFFull) >> 4) | (1ull << 16) | ((1024ull >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                            ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcEpilogue {
+    const double *x;      // block vector (batch x (N+1) x M)
+    double *y;            // FP64 rows (or null)
+    float *y32;           // FP32 rows (or null): q = fl32(x_{n+1}) - C
+    const double *y0;
+    int N, M, batch, mode;
+    size_t blen;
+    const MemberState *st;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                  int K, int R, TcEpilogue ep, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // 1024-byte aligned stage ring (the 128-byte swizzle repeats every 1024 bytes)
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + TC_STAGES * TC_STAGE_BYTES);
+    uint64_t *empty = full + TC_STAGES;
+    uint64_t *accum = empty + TC_STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+    const int KB = K / TC_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TC_BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    int last_kb[TC_STAGES];
+#pragma unroll
+    for (int s = 0; s < TC_STAGES; ++s) last_kb[s] = -1;
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % TC_STAGES;
+            const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, err)) break;
+            unsigned char *st = base + s * TC_STAGE_BYTES;
+            mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+            tma_load_2d(st, &tmAh, kb * TC_BK, m0, &full[s]);
+            tma_load_2d(st + TC_TILE_BYTES, &tmAl, kb * TC_BK, m0, &full[s]);
+            tma_load_2d(st + 2 * TC_TILE_BYTES, &tmBh, kb * TC_BK, n0, &full[s]);
+            tma_load_2d(st + 3 * TC_TILE_BYTES, &tmBl, kb * TC_BK, n0, &full[s]);
+            last_kb[s] = kb;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: three TF32 products per K step, one accumulator
+        bool ok = true;
+        for (int kb = 0; kb < KB && ok; ++kb) {
+            const int s = kb % TC_STAGES;
+            const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, err)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char *st = base + s * TC_STAGE_BYTES;
+            const uint64_t ah = smem_desc(st), al = smem_desc(st + TC_TILE_BYTES);
+            const uint64_t bh = smem_desc(st + 2 * TC_TILE_BYTES), bl = smem_desc(st + 3 * TC_TILE_BYTES);
+#pragma unroll
+            for (int j = 0; j < TC_BK / 8; ++j) {
+                const uint64_t adv = (uint64_t)(j * 32) >> 4;   // 8 TF32 = 32 bytes along K
+                mma_tf32(tmem, ah + adv, bh + adv, (kb > 0 || j > 0) ? 1u : 0u);
+                mma_tf32(tmem, ah + adv, bl + adv, 1u);
+                mma_tf32(tmem, al + adv, bh + adv, 1u);
+            }
+            mma_commit(&empty[s]);            // stage free once these products finish
+        }
+        mma_commit(accum);                    // accumulator complete
+    }
+    // epilogue: four warps, warp w reads TMEM lanes 32w..32w+31 (tile rows)
+    __syncwarp();
+    // warp-uniform: tcgen05.ld is a warp-collective instruction
+    const bool have = __all_sync(0xffffffffu, mbar_wait(accum, 0u, err) ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + warp * 32 + lane;
+    if (have) {
+        const int nb1 = ep.N + 1;
+        const int b = row / nb1, n = row % nb1;
+        const bool live = row < R && n < ep.N &&
+                          (ep.st == nullptr || (ep.st[b].active && !ep.st[b].skip && !ep.st[b].half));
+        const size_t mb = (size_t)b * ep.blen;
+        for (int cchunk = 0; cchunk < TC_BN / 32; ++cchunk) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cchunk * 32), v);
+            if (!live) continue;
+            const int c0 = n0 + cchunk * 32;
+            const double *xn = ep.x + mb + (size_t)(n + 1) * ep.M + c0;
+            if (ep.y32) {
+                float *yo = ep.y32 + mb + (size_t)(n + 1) * ep.M + c0;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) yo[i] = d2f_rn(xn[i]) - v[i];
+            } else {
+                double *yo = ep.y + mb + (size_t)(n + 1) * ep.M + c0;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const double f = f2d(v[i]);
+                    yo[i] = (ep.mode == FINE_APPLY) ? xn[i] - f : f - xn[i];
+                }
+            }
+            if (n == 0) {
+                // row 0 of eq. (4): x_0 (or y0 - x_0)
+                const double *x0 = ep.x + mb + c0;
+                if (ep.y32) {
+                    float *yo = ep.y32 + mb + c0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) yo[i] = d2f_rn(x0[i]);
+                } else {
+                    double *yo = ep.y + mb + c0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        yo[i] = (ep.mode == FINE_APPLY) ? x0[i] : ep.y0[(size_t)b * ep.M + c0 + i] - x0[i];
+                }
+            }
+        }
+    }
+    if (warp == 0 && lane == 0) {
+        // no TMA copy of this CTA may still be writing shared memory at exit
+#pragma unroll
+        for (int s = 0; s < TC_STAGES; ++s)
+            if (last_kb[s] >= 0) mbar_wait(&full[s], (uint32_t)(last_kb[s] / TC_STAGES) & 1u, err);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+    }
+}
+
+// hi = TF32 rounding of fl32(x), lo = TF32 rounding of the FP32 remainder.
+__global__ void k_split_tf32(const double *x, float *hi, float *lo, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float v = d2f_rn(x[i]);
+        uint32_t h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+        const float r = v - __uint_as_float(h);
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+        hi[i] = __uint_as_float(h);
+        lo[i] = __uint_as_float(l);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2D row-major FP32 matrix rows x cols (cols contiguous), box 32 x 128, 128B swizzle.
+pit_status make_map(CUtensorMap *tm, const float *ptr, int rows, int cols) {
+    auto fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available");
+        return PIT_E_CUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+    cuuint32_t box[2] = {TC_BK, TC_BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+        return PIT_E_CUDA;
+    }
+    return PIT_OK;
+}
+
+}  // namespace
+
+bool dense_tc_supported(const Problem *p) {
+    // tiles of 128 states; K in 32-element stages; 16-byte aligned rows
+    return p->M % TC_BN == 0 && p->M % TC_BK == 0 && encode_fn() != nullptr;
+}
+
+pit_status dense_tc_split_phi(Problem *p) {
+    const size_t mm2 = (size_t)p->M * p->M;
+    PIT_TRY(p->PhiTh.ensure(mm2 * sizeof(float)));
+    PIT_TRY(p->PhiTl.ensure(mm2 * sizeof(float)));
+    k_split_tf32<<<1024, 256, 0, p->stream>>>(p->PhiF64.as<double>(), p->PhiTh.as<float>(),
+                                              p->PhiTl.as<float>(), mm2);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
+// Block-operator rows of the dense fine batch on the tensor cores: y (FP64)
+// or y32 (FP32 rows for the mixed sweep).
+pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, int mode,
+                          const MemberState *st, cudaStream_t s) {
+    const int M = p->M;
+    const int R = p->batch * (p->N + 1);
+    const size_t n = (size_t)R * M;
+    PIT_TRY(p->tc_split.ensure(2 * n * sizeof(float)));
+    float *xh = p->tc_split.as<float>(), *xl = xh + n;
+    k_split_tf32<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(x, xh, xl, n);
+    PIT_LAUNCH_CHECK();
+    CUtensorMap tAh, tAl, tBh, tBl;
+    PIT_TRY(make_map(&tAh, xh, R, M));
+    PIT_TRY(make_map(&tAl, xl, R, M));
+    PIT_TRY(make_map(&tBh, p->PhiTh.as<float>(), M, M));
+    PIT_TRY(make_map(&tBl, p->PhiTl.as<float>(), M, M));
+    TcEpilogue ep{x, y, y32, p->y0.as<double>(), p->N, M, p->batch, mode, p->blen, st};
+    PIT_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    dim3 grid((R + TC_BM - 1) / TC_BM, M / TC_BN);
+    k_gemm_tf32x3<<<grid, TC_THREADS, TC_SMEM, s>>>(tAh, tAl, tBh, tBl, M, R, ep,
+                                                    p->errword.as<int>());
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
+}  // namespace pit

@@ -130,6 +130,11 @@ struct Problem {
     DevBuf PhiF64, G64, PhiF_hi, PhiF_lo, G32;
     DevBuf dense_scratch;
     void *blas = nullptr;         // cuBLAS handle (dense set-up and FP64 products)
+    DevBuf GL32;                  // G^L (FP32) for the chunked dense sweep
+    int sweep_L = 1;              // chunk length of the dense sweep
+    DevBuf errword;               // device-side error word of bounded waits (0 = none)
+    DevBuf PhiTh, PhiTl, tc_split;  // TF32 splits of Phi and of the input block vector
+    bool use_tc = false;          // dense FP32-class product on the tensor cores
 
     // Krylov workspace
     DevBuf X, R, Rt, P, S, D, K, W;
@@ -189,6 +194,10 @@ pit_status dense_sweep(Problem *p, const double *q, double *z, int prec,
                        const MemberState *st, cudaStream_t s);
 pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
 void dense_teardown(Problem *p);
+bool dense_tc_supported(const Problem *p);
+pit_status dense_tc_split_phi(Problem *p);
+pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, int mode,
+                          const MemberState *st, cudaStream_t s);
 
 // Autotuner (tune.cu): index of the fastest of ncand variants run(c), timed
 // with CUDA events on stream s; cached per key, device SM count and process.

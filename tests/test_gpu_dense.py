@@ -104,3 +104,46 @@ def test_dense_full_size_sampled():
     assert _rel(Y[rows], ref) < 1e-12
     assert _rel(Y32[rows], ref) < 1e-4
     np.testing.assert_array_equal(Y[0], X[0][0])
+
+
+@pytest.mark.parametrize("N", [1, 2, 8, 10, 63, 200])
+def test_dense_mixed_sweep_chunked_scan(N):
+    """The FP32 chunked scan of the coarse sweep (L = ceil(sqrt(N+1)) blocks per
+    chunk, partial last chunk) against the oracle's sequential forward
+    substitution of eq. (7): FP32 accuracy."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=96, N=N, T=N * 10.0 / 4096, fine_steps=10, batch=2)
+    X = _rand(w, 7)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("Ginv", X, precision="mixed")
+        got64 = p.apply("Ginv", X, precision="fp64")
+    ref = _oracle(w, "Ginv", X)
+    assert _rel(got, ref) < 2e-5
+    assert _rel(got64, ref) < 1e-12
+
+
+def test_dense_mixed_sweep_full_size():
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense()
+    X = _rand(w, 8)
+    o = OracleProblem.from_workload(w)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("Ginv", torch.from_numpy(X).cuda(), precision="mixed").cpu().numpy()[0]
+    ref = o.sweep_Ginv(X[0])
+    assert _rel(got, ref) < 1e-4
+
+
+@pytest.mark.parametrize("M,N,batch", [(128, 16, 1), (128, 16, 2), (256, 300, 1), (384, 5, 3)])
+def test_dense_tensor_core_product(M, N, batch):
+    """The tcgen05 3xTF32 product (M a multiple of 128): block-operator rows
+    against the oracle to FP32 accuracy, including partial row tiles."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=M, N=N, T=N * 10.0 / 4096, fine_steps=200, batch=batch)
+    X = _rand(w, 9)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("F", X, precision="mixed")
+        res = p.apply("residual", X, precision="mixed")
+    ref = _oracle(w, "F", X)
+    assert _rel(got, ref) < 2e-5
+    ref_res = _oracle(w, "residual", X)
+    assert _rel(res, ref_res) < 2e-5
