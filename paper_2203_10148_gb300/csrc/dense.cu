@@ -209,24 +209,61 @@ __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
 // Partial dot products of this CTA's rows of Gm with column v over
 // k in [k0, k1), accumulated into acc (per lane; reduced by the caller).
 template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using V = float4;
+    static constexpr int W = 4;
+};
+template <>
+struct Vec16<double> {
+    using V = double2;
+    static constexpr int W = 2;
+};
+
+__device__ __forceinline__ float4 ldcg16(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ double2 ldcg16(const double *p) { return __ldcg(reinterpret_cast<const double2 *>(p)); }
+__device__ __forceinline__ float vget(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vget(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
+
+// Partial dot products of the CTA's SW_MAXROWS rows of Gm (zero-padded)
+// with column v over k in [k0, k1), accumulated into acc (per lane; reduced
+// by the caller).  16-byte loads when M and the range allow it.
+template <class T>
 __device__ __forceinline__ void rows_dot(const T *Gm, const T *v, int M, int rows, int k0, int k1,
                                          T (&acc)[SW_MAXROWS]) {
-    constexpr int U = 16;                 // column loads in flight per lane
+    (void)rows;
+    constexpr int W = Vec16<T>::W;
     const int lane = threadIdx.x & 31;
-    for (int kb = k0 + lane; kb < k1; kb += 32 * U) {
-        T xv[U];
+    if ((M % W) == 0 && (k0 % W) == 0 && (k1 % W) == 0) {
+        constexpr int U = 4;              // 16-byte column loads in flight per lane
+        for (int kb = k0 + W * lane; kb < k1; kb += 32 * W * U) {
+            typename Vec16<T>::V xv[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = kb + 32 * u;
-            xv[u] = (k < k1) ? ld_cg(v + min(k, k1 - 1)) : T(0);
+            for (int u = 0; u < U; ++u) {
+                const int k = kb + 32 * W * u;
+                if (k < k1) xv[u] = ldcg16(v + k);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = kb + 32 * W * u;
+                if (k < k1) {
+#pragma unroll
+                    for (int r = 0; r < SW_MAXROWS; ++r) {
+                        const typename Vec16<T>::V g =
+                            *reinterpret_cast<const typename Vec16<T>::V *>(Gm + (size_t)r * M + k);
+#pragma unroll
+                        for (int e = 0; e < W; ++e) acc[r] = fma(vget(g, e), vget(xv[u], e), acc[r]);
+                    }
+                }
+            }
         }
+        return;
+    }
+    for (int k = k0 + lane; k < k1; k += 32) {
+        const T x = ld_cg(v + k);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = min(kb + 32 * u, k1 - 1);
-#pragma unroll
-            for (int r = 0; r < SW_MAXROWS; ++r)
-                if (r < rows) acc[r] = fma(Gm[(size_t)r * M + k], xv[u], acc[r]);
-        }
+        for (int r = 0; r < SW_MAXROWS; ++r) acc[r] = fma(Gm[(size_t)r * M + k], x, acc[r]);
     }
 }
 
@@ -243,7 +280,7 @@ __device__ void sweep_step(const SweepArgs<T> &a, const T *Gm, const T *in, T *o
     const int ncols = a.batch * a.C;
     const int S = ncols >= NW ? 1 : NW / ncols;        // k segments per column
     const int per_round = NW / S;                        // columns per round
-    const int seg_len = (a.M + S - 1) / S;
+    const int seg_len = (((a.M + S - 1) / S) + 3) & ~3;
     for (int base = 0; base < ncols; base += per_round) {
         const int cl = warp / S, seg = warp % S;
         const int col = base + cl;
@@ -292,16 +329,16 @@ __device__ void sweep_step(const SweepArgs<T> &a, const T *Gm, const T *in, T *o
 }
 
 template <class T>
-__global__ void __launch_bounds__(SW_THREADS) k_dense_sweep(SweepArgs<T> a) {
+__global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Gs = reinterpret_cast<T *>(smem_raw);
     T *GLs = Gs + (size_t)SW_MAXROWS * a.M;
     T *red = GLs + (size_t)SW_MAXROWS * a.M;    // (SW_THREADS / 32)^2 * SW_MAXROWS partials
     const int r0 = blockIdx.x * a.rows;
     const unsigned nb = gridDim.x;
-    for (size_t t = threadIdx.x; t < (size_t)a.rows * a.M; t += SW_THREADS) {
+    for (size_t t = threadIdx.x; t < (size_t)SW_MAXROWS * a.M; t += SW_THREADS) {
         const int r = (int)(t / a.M), k = (int)(t % a.M);
-        const bool ok = r0 + r < a.M;
+        const bool ok = r < a.rows && r0 + r < a.M;     // rows beyond this CTA's share: zero
         Gs[t] = ok ? a.G[(size_t)(r0 + r) * a.M + k] : T(0);
         if (a.C > 1) GLs[t] = ok ? a.GL[(size_t)(r0 + r) * a.M + k] : T(0);
     }
@@ -323,7 +360,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_dense_sweep(SweepArgs<T> a) {
                 constexpr int NW = SW_THREADS / 32;
                 const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
                 const int col = b * a.C + c;
-                const int seg_len = (a.M + NW - 1) / NW;
+                const int seg_len = (((a.M + NW - 1) / NW) + 3) & ~3;
                 if (c > 0) {
                     const int k0 = warp * seg_len, k1 = min(a.M, k0 + seg_len);
                     rows_dot(GLs, a.E + (size_t)(col - 1) * a.M, a.M, a.rows, k0, k1, acc);
