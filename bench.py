@@ -49,6 +49,9 @@ FLOP_PER_POINT_STEP = 28       # RK4 Horner: 4 stages x (3 add + 2 FMA) = 4 x 7 
 # exact scaling, 8 for the low parts, a 4-op product, a TwoSum and a
 # renormalisation of 5); FP64 4 x 5 FP64 ops
 OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 192, "fine_fp64": 20}
+# periodic advection-diffusion: 4 stages x 14 (5 for the Laplacian, 2 x 3 for the
+# upwind differences, 2 for the advection sum, 1 to combine)
+ADV_OPS_PER_POINT_STEP = 56
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2          # 1.25 TFLOP/s nominal FP64 = 2 FMA/clk/SM at 2.07 GHz x 152 SMs
 KERNEL_NAMES = {"fine_fp32": "k_heat2d_fine<float>", "fine_ff": "k_heat2d_fine<ff>",
@@ -62,8 +65,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=1)
-    ap.add_argument("--workload", default="heat2d", choices=["heat2d", "dense"],
-                    help="heat2d: 2D heat 128^2, N = 512 (the headline); dense: M = 1024, N = 4096")
+    ap.add_argument("--workload", default="heat2d", choices=["heat2d", "dense", "advdiff"],
+                    help="heat2d: 2D heat 128^2, N = 512 (the headline); dense: M = 1024, "
+                         "N = 4096; advdiff: periodic 512^2, N = 256")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
@@ -86,6 +90,9 @@ def workload(args, rank, step=0):
     if args.workload == "dense":
         seed = inputs.SEED_DENSE + 7919 * rank + 104729 * step
         return inputs.dense(batch=args.batch, seed=seed, tol=1e-6)
+    if args.workload == "advdiff":
+        seed = inputs.SEED_ADVDIFF2D + 7919 * rank + 104729 * step
+        return inputs.advdiff2d(batch=args.batch, seed=seed, tol=1e-6)
     seed = inputs.SEED_HEAT2D + 7919 * rank + 104729 * step
     return inputs.heat2d(n=args.n, N=args.N, batch=args.batch, seed=seed, tol=1e-6)
 
@@ -264,8 +271,9 @@ def roofline(w, timing, peaks, nsm):
     point_steps = w.batch * w.N * w.fine[1] * w.M
     lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
     peak = lanes * nsm * sm_max * 1e6 / 1e12
-    achieved = point_steps * OPS_PER_POINT_STEP[dom] / (avg_ms / 1e3) / 1e12
-    kname = KERNEL_NAMES[dom]
+    ops = ADV_OPS_PER_POINT_STEP if w.kind == "advdiff2d" else OPS_PER_POINT_STEP[dom]
+    achieved = point_steps * ops / (avg_ms / 1e3) / 1e12
+    kname = KERNEL_NAMES[dom] if w.kind == "heat2d" else "k_advdiff_fine<%s>" % dom
     tr = traffic_for(kname)
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "Tops/s (%s pipe lane-ops)" % ("FP64" if dom == "fine_fp64" else "FP32"),
@@ -277,7 +285,8 @@ def roofline(w, timing, peaks, nsm):
             "peak_source": f"derived: {lanes} lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz (max SM clock)"}
     f32 = timing["fine_fp32"]
     if f32[0]:
-        a32 = point_steps * OPS_PER_POINT_STEP["fine_fp32"] / (f32[1] / f32[0] / 1e3) / 1e12
+        ops32 = ADV_OPS_PER_POINT_STEP if w.kind == "advdiff2d" else OPS_PER_POINT_STEP["fine_fp32"]
+        a32 = point_steps * ops32 / (f32[1] / f32[0] / 1e3) / 1e12
         roof["fine_fp32"] = {"launch_ms": f32[1] / f32[0], "achieved": a32,
                              "frac": a32 / (FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12)}
     return roof
@@ -309,7 +318,8 @@ def run_ours(args):
     prob = pit.Problem(w, "mixed")
     X = torch.zeros(shape, dtype=torch.float64, device=dev)
     solve_kw = dict(tol=args.tol, tol_mode="rhs", max_iter=200, refine_max=8,
-                    inner_tol=args.inner_tol, residual_precision="ff")
+                    inner_tol=args.inner_tol,
+                    residual_precision="ff" if w.kind == "heat2d" else "fp64")
 
     def one(step):
         prob.set_y0(y0s[step])

@@ -1,20 +1,621 @@
-// Placeholder for the advdiff operator family; replaced by the real kernels.
+// 2D advection-diffusion u_t = nu Lap u - v . grad u on the periodic unit
+// square, n x n points x_i = i/n, h = 1/n: central 5-point diffusion,
+// first-order upwind advection (backward difference where the velocity
+// component is >= 0, forward where < 0).  With ax = vx/h, ay = vy/h and
+// nu_d = nu/h^2:
+//   L v = nu_d (vE + vW + vN + vS - 4 vC) - ax dX - ay dY,
+//   dX = vC - vW (ax >= 0) or vE - vC,  dY = vC - vN (ay >= 0) or vS - vC,
+// with N the row above (j - 1) and S the row below (j + 1).
+//
+// Fine batch (eq. (2), fused with the shift-subtract of eq. (4)): one
+// thread-block cluster per slice.  The n/32 CTAs of a cluster each hold 32
+// rows of the slice on chip for all RK4 steps (Horner form, as for the heat
+// equation); a thread owns a 4 x 8 tile; west/east halos come from the
+// neighbouring lanes by shuffle (across a warp boundary through a small
+// shared column buffer), north/south halos through a shared row buffer,
+// and the two rows at a CTA boundary from the neighbouring CTA's shared
+// memory (DSMEM), periodic across the cluster.  One cluster barrier per RK4
+// stage.
+//
+// Coarse sweep (eq. (7), right): G is one implicit-Euler step,
+// (I - dT L) w = b.  L has variable coefficients and is not symmetric, so no
+// transform diagonalises it; G is applied as a fixed linear operator: K
+// damped-Jacobi iterations w <- w + (2/3) D^{-1} (b - (I - dT L) w) started
+// from w = b (the IE step is the identity plus O(dT) on smooth modes, and
+// damped Jacobi removes the oscillatory part).  Any fixed linear
+// preconditioner leaves the solution of eq. (4) unchanged; only the
+// iteration count depends on it.  The sweep runs in one cooperative launch:
+// each CTA owns a band of rows, and exchanges its edge rows with the two
+// neighbouring bands through global memory with per-CTA progress flags
+// (bounded waits).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <type_traits>
+#include <vector>
+
 #include "pit_internal.h"
+#include "stencil_arith.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pit {
-pit_status advdiff_setup(Problem *) {
-    set_error("advdiff: not implemented yet");
+namespace {
+
+constexpr int AD_RY = 4, AD_RX = 8;          // thread tile
+constexpr int AD_ROWS = 32;                  // rows per CTA (cluster size = n / 32)
+constexpr int AD_TY = AD_ROWS / AD_RY;       // 8 thread rows per CTA
+
+struct AdvArgs {
+    const double *x;
+    double *y;
+    float *y32;
+    const double *y0;
+    const void *ax, *ay;   // per-point coefficients (float or double), row-major n x n
+    int n, N, batch;
+    size_t blen;
+    int n_first, mode, steps;
+    double c[4];           // stage coefficients dt/4, dt/3, dt/2, dt
+    double nud;            // nu / h^2
+    const MemberState *st;
+};
+
+__device__ __forceinline__ bool adv_runs(const MemberState *st, int b) {
+    return st == nullptr || (st[b].active && !st[b].skip && !st[b].half);
+}
+
+template <class T>
+__device__ __forceinline__ T adv_stage(T vn, T vs, T vw, T ve, T vc, T u, T cc, T nud, T ax,
+                                       T ay) {
+    const T lap = fma(T(-4), vc, (ve + vw) + (vn + vs));
+    const T dX = (ax >= T(0)) ? (vc - vw) : (ve - vc);
+    const T dY = (ay >= T(0)) ? (vc - vn) : (vs - vc);
+    const T adv = fma(ay, dY, ax * dX);
+    return fma(cc, fma(nud, lap, -adv), u);
+}
+
+// One cluster of CS = n/32 CTAs per (slice, member).  Threads: TX * 8 with
+// TX = n/8 thread columns (n <= 512).  T = float (state in registers,
+// coefficients in shared memory) or double (state in shared memory,
+// coefficients read through L1).
+template <class T, bool DBUF>
+__global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
+    constexpr bool FP32 = std::is_same<T, float>::value;
+    constexpr int NB = DBUF ? 2 : 1;               // row-buffer copies
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int n = a.n;
+    const int CS = n / AD_ROWS;
+    const int rank = (int)cluster.block_rank();
+    const int slice_lin = blockIdx.x / CS;          // cluster index = (member, slice)
+    const int b = slice_lin / a.N;
+    const int slice = a.n_first + slice_lin % a.N;  // output block
+    // inactive member: the whole cluster leaves before any cluster barrier
+    if (!adv_runs(a.st, b)) return;
+    const bool active = true;
+    const int TX = n / AD_RX;
+    const int nthr = blockDim.x;
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int lane = tid & 31, warp_in_row = tx / 32;
+    const int i0 = tx * AD_RX;
+    const int jl0 = ty * AD_RY;                      // local row
+    const int j0 = rank * AD_ROWS + jl0;             // global row
+    // shared memory: [cc 4][rowbuf NB x 2 x TY x n][colbuf NB x TY x 4 x RY][u or coefficients]
+    T *ccs = reinterpret_cast<T *>(smem_raw);
+    T *rowbuf = reinterpret_cast<T *>(smem_raw + 32);
+    T *colbuf = rowbuf + (size_t)NB * 2 * AD_TY * n;
+    T *tail = colbuf + NB * AD_TY * 4 * AD_RY;
+    if (tid < 4) ccs[tid] = (T)(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
+    const size_t mb = (size_t)b * a.blen;
+    const size_t nn = (size_t)n * n;
+    const double *xin = a.x + mb + (size_t)(slice - 1) * nn;
+
+    T v[AD_RY][AD_RX];
+    T ur[FP32 ? AD_RY : 1][FP32 ? AD_RX : 1];
+    T *us = tail;                                    // double: u thread-private
+    T *cax = tail, *cay = tail + (size_t)AD_RY * AD_RX * nthr;   // float: coefficients
+    const T *gax = reinterpret_cast<const T *>(a.ax);
+    const T *gay = reinterpret_cast<const T *>(a.ay);
+#pragma unroll
+    for (int r = 0; r < AD_RY; ++r)
+#pragma unroll
+        for (int c = 0; c < AD_RX; ++c) {
+            const size_t k = (size_t)(j0 + r) * n + (i0 + c);
+            const int slot = (r * AD_RX + c) * nthr + tid;
+            T val = T(0);
+            if (active) {
+                if constexpr (FP32) val = d2f_rn(xin[k]);
+                else val = xin[k];
+            }
+            v[r][c] = val;
+            if constexpr (FP32) {
+                ur[FP32 ? r : 0][FP32 ? c : 0] = val;
+                cax[slot] = gax[k];
+                cay[slot] = gay[k];
+            } else {
+                us[slot] = val;
+            }
+        }
+    const T nud = (T)a.nud;
+    int buf = 0;
+    const int up_rank = (rank + CS - 1) % CS, down_rank = (rank + 1) % CS;
+    for (int s = 0; s < a.steps; ++s) {
+#pragma unroll 1
+        for (int stage = 0; stage < 4; ++stage) {
+            // single buffer: every read of the previous stage's rows is done first
+            if (!DBUF) cluster.sync();
+            // publish top / bottom rows and the warp-edge columns
+            T *top = rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + ty) * n + i0;
+            T *bot = rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + ty) * n + i0;
+#pragma unroll
+            for (int c = 0; c < AD_RX; ++c) {
+                top[c] = v[0][c];
+                bot[c] = v[AD_RY - 1][c];
+            }
+            if (lane == 0 || lane == 31) {
+                // colbuf[buf][ty][slot][r]: slot 0/1 = west column of warp 0/1,
+                // slot 2/3 = east column of warp 0/1
+                T *cb = colbuf + ((size_t)(buf * AD_TY + ty) * 4 + (lane == 0 ? 0 : 2) + warp_in_row) * AD_RY;
+#pragma unroll
+                for (int r = 0; r < AD_RY; ++r) cb[r] = (lane == 0) ? v[r][0] : v[r][AD_RX - 1];
+            }
+            cluster.sync();
+            const T cc = ccs[stage];
+            // north / south rows: from the thread row above / below, across the
+            // CTA edge from the neighbouring CTA's shared memory (periodic)
+            T prev[AD_RX];
+            {
+                const T *src = (ty > 0) ? rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + (ty - 1)) * n + i0
+                                        : cluster.map_shared_rank(rowbuf, up_rank) +
+                                              ((size_t)(buf * 2 + 1) * AD_TY + (AD_TY - 1)) * n + i0;
+#pragma unroll
+                for (int c = 0; c < AD_RX; ++c) prev[c] = src[c];
+            }
+            // west/east neighbours of the tile's first/last column (periodic in x)
+            const int row_base = (tid / 32) * 32;   // lanes of this warp
+            const bool row_in_warp = TX <= 32;
+#pragma unroll
+            for (int r = 0; r < AD_RY; ++r) {
+                T w_in, e_in;
+                if (row_in_warp) {
+                    // the thread row lies in one warp: lanes tx-1 / tx+1 modulo TX
+                    const int seg = (lane / TX) * TX;
+                    w_in = __shfl_sync(kFullMask, v[r][AD_RX - 1], seg + (tx + TX - 1) % TX);
+                    e_in = __shfl_sync(kFullMask, v[r][0], seg + (tx + 1) % TX);
+                } else {
+                    // two warps per thread row: the edge lanes read the other warp's column
+                    w_in = __shfl_up_sync(kFullMask, v[r][AD_RX - 1], 1);
+                    e_in = __shfl_down_sync(kFullMask, v[r][0], 1);
+                    const int other = 1 - warp_in_row;
+                    if (lane == 0)
+                        w_in = colbuf[((size_t)(buf * AD_TY + ty) * 4 + 2 + other) * AD_RY + r];
+                    if (lane == 31)
+                        e_in = colbuf[((size_t)(buf * AD_TY + ty) * 4 + 0 + other) * AD_RY + r];
+                }
+                (void)row_base;
+                T cur[AD_RX];
+#pragma unroll
+                for (int c = 0; c < AD_RX; ++c) cur[c] = v[r][c];
+                T srow[AD_RX];
+                if (r == AD_RY - 1) {
+                    const T *srs = (ty < AD_TY - 1) ? rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + (ty + 1)) * n + i0
+                                                    : cluster.map_shared_rank(rowbuf, down_rank) +
+                                                          ((size_t)(buf * 2 + 0) * AD_TY + 0) * n + i0;
+#pragma unroll
+                    for (int c = 0; c < AD_RX; ++c) srow[c] = srs[c];
+                }
+#pragma unroll
+                for (int c = 0; c < AD_RX; ++c) {
+                    const T vn = prev[c];
+                    const T vs = (r < AD_RY - 1) ? v[r + 1][c] : srow[c];
+                    const T vw = (c > 0) ? cur[c - 1] : w_in;
+                    const T ve = (c < AD_RX - 1) ? cur[c + 1] : e_in;
+                    const int slot = (r * AD_RX + c) * nthr + tid;
+                    T u, ax, ay;
+                    if constexpr (FP32) {
+                        u = ur[FP32 ? r : 0][FP32 ? c : 0];
+                        ax = cax[slot];
+                        ay = cay[slot];
+                    } else {
+                        u = us[slot];
+                        const size_t k = (size_t)(j0 + r) * n + (i0 + c);
+                        ax = __ldg(gax + k);
+                        ay = __ldg(gay + k);
+                    }
+                    v[r][c] = adv_stage(vn, vs, vw, ve, cur[c], u, cc, nud, ax, ay);
+                }
+#pragma unroll
+                for (int c = 0; c < AD_RX; ++c) prev[c] = cur[c];
+            }
+            if (DBUF) buf ^= 1;
+        }
+#pragma unroll
+        for (int r = 0; r < AD_RY; ++r)
+#pragma unroll
+            for (int c = 0; c < AD_RX; ++c) {
+                if constexpr (FP32) ur[FP32 ? r : 0][FP32 ? c : 0] = v[r][c];
+                else us[(r * AD_RX + c) * nthr + tid] = v[r][c];
+            }
+    }
+    // all remote reads of this CTA's row buffer are done before anyone exits
+    cluster.sync();
+    const double *xn = a.x + mb + (size_t)slice * nn;
+#pragma unroll
+    for (int r = 0; r < AD_RY; ++r)
+#pragma unroll
+        for (int c = 0; c < AD_RX; ++c) {
+            const size_t k = (size_t)(j0 + r) * n + (i0 + c);
+            if constexpr (FP32) {
+                if (a.y32) {
+                    a.y32[mb + (size_t)slice * nn + k] = d2f_rn(xn[k]) - v[r][c];
+                    continue;
+                }
+            }
+            double f;
+            if constexpr (FP32) f = f2d(v[r][c]);
+            else f = v[r][c];
+            double *yo = a.y + mb + (size_t)slice * nn;
+            if (a.mode == FINE_APPLY) yo[k] = xn[k] - f;
+            else if (a.mode == FINE_RESIDUAL) yo[k] = f - xn[k];
+            else yo[k] = f;
+        }
+    if (slice == 1 && a.mode != 2) {
+        // row 0 of eq. (4) for this CTA's rows
+        const double *x0 = a.x + mb;
+        const size_t k0 = (size_t)rank * AD_ROWS * n, k1 = k0 + (size_t)AD_ROWS * n;
+        for (size_t k = k0 + tid; k < k1; k += nthr) {
+            if constexpr (FP32) {
+                if (a.y32) {
+                    a.y32[mb + k] = d2f_rn(x0[k]);
+                    continue;
+                }
+            }
+            a.y[mb + k] = (a.mode == FINE_APPLY) ? x0[k] : a.y0[(size_t)b * nn + k] - x0[k];
+        }
+    }
+}
+
+template <class T, bool DBUF>
+size_t adv_smem(int n) {
+    const size_t nthr = (size_t)n;   // TX * 8 = n
+    const size_t nb = DBUF ? 2 : 1;
+    size_t s = 32 + (nb * 2 * AD_TY * (size_t)n + nb * AD_TY * 4 * AD_RY) * sizeof(T);
+    if (std::is_same<T, float>::value) s += 2 * (size_t)AD_RY * AD_RX * nthr * sizeof(T);
+    else s += (size_t)AD_RY * AD_RX * nthr * sizeof(T);
+    return s;
+}
+
+AdvArgs adv_args(Problem *p, const double *x, double *y, float *y32, int mode,
+                 const MemberState *st, bool fp32) {
+    AdvArgs a{};
+    a.x = x;
+    a.y = y;
+    a.y32 = y32;
+    a.y0 = p->y0.as<double>();
+    a.ax = fp32 ? (const void *)p->vx32.ptr : (const void *)p->vx64.ptr;
+    a.ay = fp32 ? (const void *)p->vy32.ptr : (const void *)p->vy64.ptr;
+    a.n = p->nx;
+    a.N = p->N;
+    a.batch = p->batch;
+    a.blen = p->blen;
+    a.n_first = 1;
+    a.mode = mode;
+    a.steps = p->fine_steps;
+    const double dt = p->dT / p->fine_steps;
+    a.c[0] = dt / 4.0;
+    a.c[1] = dt / 3.0;
+    a.c[2] = dt / 2.0;
+    a.c[3] = dt;
+    const double h = 1.0 / p->nx;
+    a.nud = p->nu / (h * h);
+    a.st = st;
+    return a;
+}
+
+template <class T, bool DBUF>
+pit_status launch_adv_fine_v(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
+    const int n = p->nx;
+    const int CS = n / AD_ROWS;
+    const size_t sm = adv_smem<T, DBUF>(n);
+    PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<T, DBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+    if (CS > 8)
+        PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<T, DBUF>,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    a.N = nslices;   // slices in this launch (output blocks n_first .. n_first + nslices - 1)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(CS * nslices * p->batch), 1, 1);
+    cfg.blockDim = dim3((unsigned)n, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PIT_CUDA(cudaLaunchKernelEx(&cfg, k_advdiff_fine<T, DBUF>, a));
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// double-buffered row exchange when it fits, single-buffered otherwise
+template <class T>
+pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
+    if (adv_smem<T, true>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, true>(p, a, nslices, s);
+    if (adv_smem<T, false>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, false>(p, a, nslices, s);
+    set_error("advdiff2d: the slice does not fit the cluster's shared memory");
     return PIT_E_UNSUPPORTED;
 }
-pit_status advdiff_apply_F(Problem *, const double *, double *, int, int, const MemberState *,
-                          cudaStream_t) {
-    return PIT_E_UNSUPPORTED;
+
+// ------------------------------------------------------------------ sweep
+constexpr int SWA_THREADS = 256;
+constexpr long long SWA_SPIN = 1LL << 24;
+
+template <class T>
+struct AdSweepArgs {
+    const double *q;
+    double *z;
+    int n, N, batch, K, R;     // grid, slices, members, Jacobi iterations, rows per CTA
+    size_t blen;
+    double dT, nud, omega;
+    const T *ax, *ay;
+    T *halo;                   // [2][G][2][n]: top / bottom rows per band, by step parity
+    unsigned *flags;           // [G]: steps completed
+    int *err;
+    const MemberState *st;
+};
+
+// (A w)_p = w_p - dT (L w)_p on this CTA's band; wb holds the band with one
+// halo row above (row 0) and below (row R+1).
+template <class T>
+__device__ __forceinline__ T apply_A(const T *wb, int n, int rl, int i, T ax, T ay, T dT, T nud) {
+    const T *row = wb + (size_t)(rl + 1) * n;
+    const T vc = row[i];
+    const T vw = row[(i + n - 1) % n], ve = row[(i + 1) % n];
+    const T vn = wb[(size_t)rl * n + i], vs = wb[(size_t)(rl + 2) * n + i];
+    const T lap = fma(T(-4), vc, (ve + vw) + (vn + vs));
+    const T dX = (ax >= T(0)) ? (vc - vw) : (ve - vc);
+    const T dY = (ay >= T(0)) ? (vc - vn) : (vs - vc);
+    const T Lw = fma(nud, lap, -fma(ay, dY, ax * dX));
+    return fma(-dT, Lw, vc);
 }
-pit_status advdiff_sweep(Problem *, const double *, double *, int, const MemberState *,
-                        cudaStream_t) {
-    return PIT_E_UNSUPPORTED;
+
+template <class T>
+__global__ void __launch_bounds__(SWA_THREADS, 1) k_advdiff_sweep(AdSweepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *wb = reinterpret_cast<T *>(smem_raw);          // (R + 2) x n band with halos
+    __shared__ int ok;
+    const int g = blockIdx.x, G = gridDim.x;
+    const int up = (g + G - 1) % G, down = (g + 1) % G;
+    const int n = a.n, R = a.R;
+    const int band = R * n;
+    const int r0 = g * R;
+    const T dT = (T)a.dT, nud = (T)a.nud, om = (T)a.omega;
+    constexpr int PPT = 32;                            // points per thread (band <= 8192)
+    T b_[PPT], w_[PPT];
+    unsigned step = 0;
+    if (threadIdx.x == 0) ok = 1;
+    __syncthreads();
+    for (int mbr = 0; mbr < a.batch; ++mbr) {
+        if (!(a.st == nullptr || (a.st[mbr].active && !a.st[mbr].skip && !a.st[mbr].half))) continue;
+        const size_t mb = (size_t)mbr * a.blen;
+        // z_0 = q_0
+#pragma unroll
+        for (int e = 0; e < PPT; ++e) {
+            const int p = threadIdx.x + e * SWA_THREADS;
+            if (p < band) {
+                const size_t k = (size_t)r0 * n + p;
+                const double q0 = a.q[mb + k];
+                a.z[mb + k] = q0;
+                b_[e] = (T)q0;
+            }
+        }
+        for (int sl = 1; sl <= a.N; ++sl) {
+#pragma unroll
+            for (int e = 0; e < PPT; ++e) w_[e] = b_[e];       // start from w = b
+            for (int it = 0; it < a.K; ++it, ++step) {
+                // band into shared memory; edge rows to the global halo buffer
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) {
+                    const int p = threadIdx.x + e * SWA_THREADS;
+                    if (p < band) {
+                        wb[n + p] = w_[e];
+                        const int rl = p / n, i = p % n;
+                        T *hslot = a.halo + ((size_t)((step & 1u) * G + g) * 2) * n;
+                        if (rl == 0) __stcg(hslot + i, w_[e]);
+                        if (rl == R - 1) __stcg(hslot + n + i, w_[e]);
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    atomicExch(a.flags + g, step + 1);
+                    // wait for both neighbours to publish this step (bounded)
+                    long long spins = 0;
+                    while (*(volatile unsigned *)(a.flags + up) < step + 1 ||
+                           *(volatile unsigned *)(a.flags + down) < step + 1) {
+                        if (++spins > SWA_SPIN || *(volatile int *)a.err) {
+                            atomicExch(a.err, PIT_E_TIMEOUT);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    __threadfence();
+                }
+                __syncthreads();
+                if (!ok) return;
+                // halo rows: bottom row of the band above, top row of the band below
+                for (int i = threadIdx.x; i < n; i += SWA_THREADS) {
+                    const T *hu = a.halo + ((size_t)((step & 1u) * G + up) * 2) * n;
+                    const T *hd = a.halo + ((size_t)((step & 1u) * G + down) * 2) * n;
+                    wb[i] = __ldcg(hu + n + i);
+                    wb[(size_t)(R + 1) * n + i] = __ldcg(hd + i);
+                }
+                __syncthreads();
+                // damped Jacobi: w += omega D^{-1} (b - A w), D = 1 + dT (4 nud + |ax| + |ay|)
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) {
+                    const int p = threadIdx.x + e * SWA_THREADS;
+                    if (p < band) {
+                        const int rl = p / n, i = p % n;
+                        const size_t k = (size_t)(r0 + rl) * n + i;
+                        const T ax = __ldg(a.ax + k), ay = __ldg(a.ay + k);
+                        const T Aw = apply_A(wb, n, rl, i, ax, ay, dT, nud);
+                        const T D = fma(dT, fma(T(4), nud, fabs(ax) + fabs(ay)), T(1));
+                        w_[e] = fma(om / D, b_[e] - Aw, w_[e]);
+                    }
+                }
+                __syncthreads();
+            }
+            // z_sl = q_sl + G z_{sl-1}
+#pragma unroll
+            for (int e = 0; e < PPT; ++e) {
+                const int p = threadIdx.x + e * SWA_THREADS;
+                if (p < band) {
+                    const size_t k = mb + (size_t)sl * n * n + (size_t)r0 * n + p;
+                    const double zz = a.q[k] + (double)w_[e];
+                    a.z[k] = zz;
+                    b_[e] = (T)zz;
+                }
+            }
+        }
+    }
 }
-pit_status advdiff_fine_one(Problem *, const double *, double *, int, cudaStream_t) {
-    return PIT_E_UNSUPPORTED;
+
+template <class T>
+pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax, const T *ay,
+                            const MemberState *st, cudaStream_t s) {
+    const int n = p->nx;
+    // bands of R rows: R * n <= 8192 points per CTA, and n / R CTAs co-resident
+    int dev = 0, sms = 0;
+    PIT_CUDA(cudaGetDevice(&dev));
+    PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int R = 1;
+    while (n % (2 * R) == 0 && (n / R) > sms) R *= 2;
+    while (R * n > 32 * SWA_THREADS && R > 1) R /= 2;
+    if (n % R != 0 || R * n > 32 * SWA_THREADS || n / R > sms) {
+        set_error("advdiff sweep: grid does not fit the band decomposition");
+        return PIT_E_UNSUPPORTED;
+    }
+    const int G = n / R;
+    const size_t smem = (size_t)(R + 2) * n * sizeof(T);
+    PIT_CUDA(cudaFuncSetAttribute(k_advdiff_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    int per_sm = 0;
+    PIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_advdiff_sweep<T>, SWA_THREADS, smem));
+    if (per_sm * sms < G) {
+        set_error("advdiff sweep: bands cannot all be resident");
+        return PIT_E_UNSUPPORTED;
+    }
+    const size_t hbytes = (size_t)2 * G * 2 * n * sizeof(T);
+    PIT_TRY(p->adv_scratch.ensure(hbytes + (size_t)G * sizeof(unsigned) + 256));
+    T *halo = p->adv_scratch.as<T>();
+    unsigned *flags = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(p->adv_scratch.ptr) + hbytes);
+    PIT_CUDA(cudaMemsetAsync(flags, 0, (size_t)G * sizeof(unsigned), s));
+    AdSweepArgs<T> a{q, z, n, p->N, p->batch, p->adv_K, R, p->blen, p->dT / p->coarse_steps,
+                     p->nu * n * (double)n, 2.0 / 3.0, ax, ay, halo, flags, p->errword.as<int>(), st};
+    void *args[] = {&a};
+    PIT_CUDA(cudaLaunchCooperativeKernel((const void *)k_advdiff_sweep<T>, dim3(G), dim3(SWA_THREADS),
+                                         args, smem, s));
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
 }
+
+__global__ void k_scale_coeff(const double *v, double *o64, float *o32, double scale, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double x = v[i] * scale;
+        o64[i] = x;
+        o32[i] = d2f_rn(x);
+    }
+}
+
+}  // namespace
+
+pit_status advdiff_setup(Problem *p) {
+    if (p->nx != p->ny) {
+        set_error("advdiff2d: only square grids are supported");
+        return PIT_E_UNSUPPORTED;
+    }
+    const int n = p->nx;
+    if (!(n == 32 || n == 64 || n == 128 || n == 256 || n == 512)) {
+        set_error("advdiff2d: n must be 32, 64, 128, 256 or 512");
+        return PIT_E_UNSUPPORTED;
+    }
+    if (p->fine_kind != PIT_STEP_RK4 || p->coarse_kind != PIT_STEP_IE || p->coarse_steps != 1) {
+        set_error("advdiff2d: fine must be RK4 and coarse one implicit-Euler step");
+        return PIT_E_UNSUPPORTED;
+    }
+    // coefficients ax = vx / h, ay = vy / h (FP64 in place, FP32 copies)
+    const size_t M = p->M;
+    PIT_TRY(p->vx32.ensure(M * sizeof(float)));
+    PIT_TRY(p->vy32.ensure(M * sizeof(float)));
+    k_scale_coeff<<<256, 256, 0, p->stream>>>(p->vx64.as<double>(), p->vx64.as<double>(),
+                                              p->vx32.as<float>(), (double)n, M);
+    PIT_LAUNCH_CHECK();
+    k_scale_coeff<<<256, 256, 0, p->stream>>>(p->vy64.as<double>(), p->vy64.as<double>(),
+                                              p->vy32.as<float>(), (double)n, M);
+    PIT_LAUNCH_CHECK();
+    p->adv_K = 6;
+    // the cluster shape must be schedulable (n / 32 CTAs of one SM each)
+    const int CS = n / AD_ROWS > 0 ? n / AD_ROWS : 1;
+    const size_t sm = adv_smem<float, true>(n);
+    PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (CS > 8)
+        PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<float, true>,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)CS, 1, 1);
+    cfg.blockDim = dim3((unsigned)n, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    PIT_CUDA(cudaOccupancyMaxActiveClusters(&clusters, k_advdiff_fine<float, true>, &cfg));
+    if (clusters < 1) {
+        set_error("advdiff2d: the " + std::to_string(CS) + "-CTA cluster of the fine kernel cannot be scheduled");
+        return PIT_E_UNSUPPORTED;
+    }
+    return PIT_OK;
+}
+
+pit_status advdiff_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
+                           const MemberState *st, cudaStream_t s) {
+    if (prec == PIT_MIXED) return launch_adv_fine<float>(p, adv_args(p, x, y, nullptr, mode, st, true), p->N, s);
+    return launch_adv_fine<double>(p, adv_args(p, x, y, nullptr, mode, st, false), p->N, s);
+}
+
+pit_status advdiff_fine_f32out(Problem *p, const double *x, float *q32, const MemberState *st,
+                               cudaStream_t s) {
+    return launch_adv_fine<float>(p, adv_args(p, x, nullptr, q32, FINE_APPLY, st, true), p->N, s);
+}
+
+pit_status advdiff_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
+    AdvArgs a;
+    if (prec == PIT_MIXED) {
+        a = adv_args(p, x, y - (size_t)p->M, nullptr, 2, nullptr, true);
+        return launch_adv_fine<float>(p, a, 1, s);
+    }
+    a = adv_args(p, x, y - (size_t)p->M, nullptr, 2, nullptr, false);
+    return launch_adv_fine<double>(p, a, 1, s);
+}
+
+pit_status advdiff_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
+                         cudaStream_t s) {
+    if (prec == PIT_MIXED)
+        return launch_adv_sweep<float>(p, q, z, p->vx32.as<float>(), p->vy32.as<float>(), st, s);
+    return launch_adv_sweep<double>(p, q, z, p->vx64.as<double>(), p->vy64.as<double>(), st, s);
+}
+
 }  // namespace pit

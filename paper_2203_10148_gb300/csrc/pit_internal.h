@@ -123,8 +123,9 @@ struct Problem {
     DevBuf hat;                   // sweep scratch: transformed blocks
 
     // advdiff2d: per-point velocities (FP64 and FP32)
-    DevBuf vx64, vy64, vx32, vy32;
+    DevBuf vx64, vy64, vx32, vy32;   // after set-up: ax = vx/h, ay = vy/h
     DevBuf adv_scratch;
+    int adv_K = 6;                // damped-Jacobi iterations of the coarse IE step
 
     // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)
     DevBuf PhiF64, G64, PhiF_hi, PhiF_lo, G32;
