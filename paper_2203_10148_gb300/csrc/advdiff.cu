@@ -31,6 +31,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -354,18 +355,22 @@ pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
 
 // ------------------------------------------------------------------ sweep
 constexpr int SWA_THREADS = 256;
-constexpr long long SWA_SPIN = 1LL << 24;
+constexpr int SWA_PPT = 8;                     // points per thread: bands of <= 2048 points
+constexpr int SWA_KMAX = 16;
+constexpr long long SWA_SPIN = 1LL << 26;
 
 template <class T>
 struct AdSweepArgs {
     const double *q;
     double *z;
-    int n, N, batch, K, R;     // grid, slices, members, Jacobi iterations, rows per CTA
+    int n, N, batch, K, R;     // grid, slices, members, Chebyshev steps, rows per CTA
     size_t blen;
-    double dT, nud, omega;
+    double dT, nud;
+    double inv_theta;          // first direction d_0 = D^{-1} r_0 / theta
+    double c1[SWA_KMAX], c2[SWA_KMAX];   // d_{k+1} = c1_k d_k + c2_k D^{-1} r_{k+1}
     const T *ax, *ay;
     T *halo;                   // [2][G][2][n]: top / bottom rows per band, by step parity
-    unsigned *flags;           // [G]: steps completed
+    unsigned *flags;           // [G]: halo exchanges completed
     int *err;
     const MemberState *st;
 };
@@ -376,7 +381,7 @@ template <class T>
 __device__ __forceinline__ T apply_A(const T *wb, int n, int rl, int i, T ax, T ay, T dT, T nud) {
     const T *row = wb + (size_t)(rl + 1) * n;
     const T vc = row[i];
-    const T vw = row[(i + n - 1) % n], ve = row[(i + 1) % n];
+    const T vw = row[i == 0 ? n - 1 : i - 1], ve = row[i == n - 1 ? 0 : i + 1];
     const T vn = wb[(size_t)rl * n + i], vs = wb[(size_t)(rl + 2) * n + i];
     const T lap = fma(T(-4), vc, (ve + vw) + (vn + vs));
     const T dX = (ax >= T(0)) ? (vc - vw) : (ve - vc);
@@ -385,6 +390,55 @@ __device__ __forceinline__ T apply_A(const T *wb, int n, int rl, int i, T ax, T 
     return fma(-dT, Lw, vc);
 }
 
+// Puts this thread's points of a vector into the band buffer and the band's
+// edge rows into the global halo slot, then waits (bounded) until both
+// neighbouring bands have published the same exchange and copies their edge
+// rows into the halo rows of the band buffer.
+template <class T>
+__device__ bool exchange(const AdSweepArgs<T> &a, T *wb, const T (&val)[SWA_PPT], unsigned &step,
+                         int g, int G, int up, int down, int *ok) {
+    const int n = a.n, band = a.R * n;
+    T *hslot = a.halo + ((size_t)((step & 1u) * G + g) * 2) * n;
+#pragma unroll
+    for (int e = 0; e < SWA_PPT; ++e) {
+        const int p = threadIdx.x + e * SWA_THREADS;
+        if (p < band) {
+            wb[n + p] = val[e];
+            if (p < n) __stcg(hslot + p, val[e]);
+            if (p >= band - n) __stcg(hslot + n + (p - (band - n)), val[e]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(a.flags + g, step + 1);
+        long long spins = 0;
+        while (*(volatile unsigned *)(a.flags + up) < step + 1 ||
+               *(volatile unsigned *)(a.flags + down) < step + 1) {
+            if (++spins > SWA_SPIN || *(volatile int *)a.err) {
+                atomicExch(a.err, PIT_E_TIMEOUT);
+                *ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (!*ok) return false;
+    const T *hu = a.halo + ((size_t)((step & 1u) * G + up) * 2) * n;
+    const T *hd = a.halo + ((size_t)((step & 1u) * G + down) * 2) * n;
+    for (int i = threadIdx.x; i < n; i += SWA_THREADS) {
+        wb[i] = __ldcg(hu + n + i);
+        wb[(size_t)(a.R + 1) * n + i] = __ldcg(hd + i);
+    }
+    __syncthreads();
+    ++step;
+    return true;
+}
+
+// z_0 = q_0, z_n = q_n + G z_{n-1}, G b ~ (I - dT L)^{-1} b by K Chebyshev
+// steps on the Jacobi-scaled system from x = b (fixed coefficients, so G is
+// a fixed polynomial in D^{-1} A).
 template <class T>
 __global__ void __launch_bounds__(SWA_THREADS, 1) k_advdiff_sweep(AdSweepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -395,93 +449,66 @@ __global__ void __launch_bounds__(SWA_THREADS, 1) k_advdiff_sweep(AdSweepArgs<T>
     const int n = a.n, R = a.R;
     const int band = R * n;
     const int r0 = g * R;
-    const T dT = (T)a.dT, nud = (T)a.nud, om = (T)a.omega;
-    constexpr int PPT = 32;                            // points per thread (band <= 8192)
-    T b_[PPT], w_[PPT];
+    const T dT = (T)a.dT, nud = (T)a.nud;
+    T bv[SWA_PPT], x[SWA_PPT], r[SWA_PPT], d[SWA_PPT], Dinv[SWA_PPT], axv[SWA_PPT], ayv[SWA_PPT];
+    int rlv[SWA_PPT], iv[SWA_PPT];
+#pragma unroll
+    for (int e = 0; e < SWA_PPT; ++e) {
+        const int p = min(threadIdx.x + e * SWA_THREADS, band - 1);
+        rlv[e] = p / n;
+        iv[e] = p % n;
+        const size_t k = (size_t)(r0 + rlv[e]) * n + iv[e];
+        axv[e] = a.ax[k];
+        ayv[e] = a.ay[k];
+        Dinv[e] = T(1) / fma(dT, fma(T(4), nud, fabs(axv[e]) + fabs(ayv[e])), T(1));
+    }
     unsigned step = 0;
     if (threadIdx.x == 0) ok = 1;
     __syncthreads();
     for (int mbr = 0; mbr < a.batch; ++mbr) {
         if (!(a.st == nullptr || (a.st[mbr].active && !a.st[mbr].skip && !a.st[mbr].half))) continue;
         const size_t mb = (size_t)mbr * a.blen;
-        // z_0 = q_0
 #pragma unroll
-        for (int e = 0; e < PPT; ++e) {
+        for (int e = 0; e < SWA_PPT; ++e) {
             const int p = threadIdx.x + e * SWA_THREADS;
             if (p < band) {
-                const size_t k = (size_t)r0 * n + p;
-                const double q0 = a.q[mb + k];
-                a.z[mb + k] = q0;
-                b_[e] = (T)q0;
+                const size_t k = mb + (size_t)r0 * n + p;
+                const double q0 = a.q[k];
+                a.z[k] = q0;
+                bv[e] = (T)q0;
             }
         }
         for (int sl = 1; sl <= a.N; ++sl) {
+            // x = b; r = b - A b; d = D^{-1} r / theta
+            if (!exchange(a, wb, bv, step, g, G, up, down, &ok)) return;
 #pragma unroll
-            for (int e = 0; e < PPT; ++e) w_[e] = b_[e];       // start from w = b
-            for (int it = 0; it < a.K; ++it, ++step) {
-                // band into shared memory; edge rows to the global halo buffer
-#pragma unroll
-                for (int e = 0; e < PPT; ++e) {
-                    const int p = threadIdx.x + e * SWA_THREADS;
-                    if (p < band) {
-                        wb[n + p] = w_[e];
-                        const int rl = p / n, i = p % n;
-                        T *hslot = a.halo + ((size_t)((step & 1u) * G + g) * 2) * n;
-                        if (rl == 0) __stcg(hslot + i, w_[e]);
-                        if (rl == R - 1) __stcg(hslot + n + i, w_[e]);
-                    }
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    __threadfence();
-                    atomicExch(a.flags + g, step + 1);
-                    // wait for both neighbours to publish this step (bounded)
-                    long long spins = 0;
-                    while (*(volatile unsigned *)(a.flags + up) < step + 1 ||
-                           *(volatile unsigned *)(a.flags + down) < step + 1) {
-                        if (++spins > SWA_SPIN || *(volatile int *)a.err) {
-                            atomicExch(a.err, PIT_E_TIMEOUT);
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                    __threadfence();
-                }
-                __syncthreads();
-                if (!ok) return;
-                // halo rows: bottom row of the band above, top row of the band below
-                for (int i = threadIdx.x; i < n; i += SWA_THREADS) {
-                    const T *hu = a.halo + ((size_t)((step & 1u) * G + up) * 2) * n;
-                    const T *hd = a.halo + ((size_t)((step & 1u) * G + down) * 2) * n;
-                    wb[i] = __ldcg(hu + n + i);
-                    wb[(size_t)(R + 1) * n + i] = __ldcg(hd + i);
-                }
-                __syncthreads();
-                // damped Jacobi: w += omega D^{-1} (b - A w), D = 1 + dT (4 nud + |ax| + |ay|)
-#pragma unroll
-                for (int e = 0; e < PPT; ++e) {
-                    const int p = threadIdx.x + e * SWA_THREADS;
-                    if (p < band) {
-                        const int rl = p / n, i = p % n;
-                        const size_t k = (size_t)(r0 + rl) * n + i;
-                        const T ax = __ldg(a.ax + k), ay = __ldg(a.ay + k);
-                        const T Aw = apply_A(wb, n, rl, i, ax, ay, dT, nud);
-                        const T D = fma(dT, fma(T(4), nud, fabs(ax) + fabs(ay)), T(1));
-                        w_[e] = fma(om / D, b_[e] - Aw, w_[e]);
-                    }
-                }
-                __syncthreads();
+            for (int e = 0; e < SWA_PPT; ++e) {
+                x[e] = bv[e];
+                r[e] = bv[e] - apply_A(wb, n, rlv[e], iv[e], axv[e], ayv[e], dT, nud);
+                d[e] = (T)a.inv_theta * Dinv[e] * r[e];
             }
-            // z_sl = q_sl + G z_{sl-1}
+            for (int k = 0; k < a.K; ++k) {
 #pragma unroll
-            for (int e = 0; e < PPT; ++e) {
+                for (int e = 0; e < SWA_PPT; ++e) x[e] += d[e];
+                if (k == a.K - 1) break;
+                __syncthreads();                      // band buffer reused for d
+                if (!exchange(a, wb, d, step, g, G, up, down, &ok)) return;
+                const T c1 = (T)a.c1[k], c2 = (T)a.c2[k];
+#pragma unroll
+                for (int e = 0; e < SWA_PPT; ++e) {
+                    r[e] -= apply_A(wb, n, rlv[e], iv[e], axv[e], ayv[e], dT, nud);
+                    d[e] = fma(c1, d[e], c2 * Dinv[e] * r[e]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < SWA_PPT; ++e) {
                 const int p = threadIdx.x + e * SWA_THREADS;
                 if (p < band) {
                     const size_t k = mb + (size_t)sl * n * n + (size_t)r0 * n + p;
-                    const double zz = a.q[k] + (double)w_[e];
+                    const double zz = a.q[k] + (double)x[e];
                     a.z[k] = zz;
-                    b_[e] = (T)zz;
+                    bv[e] = (T)zz;
                 }
             }
         }
@@ -492,14 +519,13 @@ template <class T>
 pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax, const T *ay,
                             const MemberState *st, cudaStream_t s) {
     const int n = p->nx;
-    // bands of R rows: R * n <= 8192 points per CTA, and n / R CTAs co-resident
     int dev = 0, sms = 0;
     PIT_CUDA(cudaGetDevice(&dev));
     PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // bands of R rows with R * n <= SWA_PPT * SWA_THREADS, as many bands as fit
     int R = 1;
-    while (n % (2 * R) == 0 && (n / R) > sms) R *= 2;
-    while (R * n > 32 * SWA_THREADS && R > 1) R /= 2;
-    if (n % R != 0 || R * n > 32 * SWA_THREADS || n / R > sms) {
+    while (R * n < n * n && (n / R) > sms) R *= 2;
+    if (R * n > SWA_PPT * SWA_THREADS || n % R != 0 || n / R > sms) {
         set_error("advdiff sweep: grid does not fit the band decomposition");
         return PIT_E_UNSUPPORTED;
     }
@@ -518,8 +544,28 @@ pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax,
     T *halo = p->adv_scratch.as<T>();
     unsigned *flags = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(p->adv_scratch.ptr) + hbytes);
     PIT_CUDA(cudaMemsetAsync(flags, 0, (size_t)G * sizeof(unsigned), s));
-    AdSweepArgs<T> a{q, z, n, p->N, p->batch, p->adv_K, R, p->blen, p->dT / p->coarse_steps,
-                     p->nu * n * (double)n, 2.0 / 3.0, ax, ay, halo, flags, p->errword.as<int>(), st};
+    AdSweepArgs<T> a{};
+    a.q = q;
+    a.z = z;
+    a.n = n;
+    a.N = p->N;
+    a.batch = p->batch;
+    a.K = p->adv_K;
+    a.R = R;
+    a.blen = p->blen;
+    a.dT = p->dT / p->coarse_steps;
+    a.nud = p->nu * n * (double)n;
+    a.inv_theta = p->adv_inv_theta;
+    for (int k = 0; k < SWA_KMAX; ++k) {
+        a.c1[k] = p->adv_c1[k];
+        a.c2[k] = p->adv_c2[k];
+    }
+    a.ax = ax;
+    a.ay = ay;
+    a.halo = halo;
+    a.flags = flags;
+    a.err = p->errword.as<int>();
+    a.st = st;
     void *args[] = {&a};
     PIT_CUDA(cudaLaunchCooperativeKernel((const void *)k_advdiff_sweep<T>, dim3(G), dim3(SWA_THREADS),
                                          args, smem, s));
@@ -562,7 +608,31 @@ pit_status advdiff_setup(Problem *p) {
     k_scale_coeff<<<256, 256, 0, p->stream>>>(p->vy64.as<double>(), p->vy64.as<double>(),
                                               p->vy32.as<float>(), (double)n, M);
     PIT_LAUNCH_CHECK();
-    p->adv_K = 6;
+    // Chebyshev coefficients on the Jacobi-scaled IE system: the spectrum of
+    // D^{-1} A lies in the Gershgorin disc |z - 1| <= rho, rho = max (D - 1)/D,
+    // taken as the real interval [1 - rho, 1 + rho]
+    {
+        std::vector<double> vx(M), vy(M);
+        PIT_CUDA(cudaMemcpy(vx.data(), p->vx64.ptr, M * sizeof(double), cudaMemcpyDeviceToHost));
+        PIT_CUDA(cudaMemcpy(vy.data(), p->vy64.ptr, M * sizeof(double), cudaMemcpyDeviceToHost));
+        const double dtc = p->dT / p->coarse_steps, nud = p->nu * n * (double)n;
+        double rho = 0.0;
+        for (size_t i = 0; i < M; ++i) {
+            const double D = 1.0 + dtc * (4.0 * nud + fabs(vx[i]) + fabs(vy[i]));
+            rho = std::max(rho, (D - 1.0) / D);
+        }
+        const double lmin = 1.0 - rho, lmax = 1.0 + rho;
+        const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+        p->adv_K = 8;
+        p->adv_inv_theta = 1.0 / theta;
+        double r = 1.0 / sigma;
+        for (int k = 0; k < 16; ++k) {
+            const double rn = 1.0 / (2.0 * sigma - r);
+            p->adv_c1[k] = rn * r;
+            p->adv_c2[k] = 2.0 * rn / delta;
+            r = rn;
+        }
+    }
     // the cluster shape must be schedulable (n / 32 CTAs of one SM each)
     const int CS = n / AD_ROWS > 0 ? n / AD_ROWS : 1;
     const size_t sm = adv_smem<float, true>(n);

@@ -125,7 +125,8 @@ struct Problem {
     // advdiff2d: per-point velocities (FP64 and FP32)
     DevBuf vx64, vy64, vx32, vy32;   // after set-up: ax = vx/h, ay = vy/h
     DevBuf adv_scratch;
-    int adv_K = 6;                // damped-Jacobi iterations of the coarse IE step
+    int adv_K = 8;                // Chebyshev steps of the coarse IE step
+    double adv_inv_theta = 1.0, adv_c1[16] = {}, adv_c2[16] = {};   // Chebyshev coefficients
 
     // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)
     DevBuf PhiF64, G64, PhiF_hi, PhiF_lo, G32;
