@@ -53,6 +53,7 @@ typedef int pit_status;
 #define PIT_E_TIMEOUT      -7   /* a bounded device-side wait expired */
 #define PIT_E_BUSY         -8   /* serving: no free slot and the queue is full */
 #define PIT_E_UNSUPPORTED  -9   /* valid but not implemented combination */
+#define PIT_E_CANCELLED   -10   /* serving: the request was cancelled */
 
 /* Spatial operator families (the operator L of eq. (1), f = 0). */
 #define PIT_OP_HEAT1D       1   /* nu u_xx, Dirichlet 0, nx interior points, h = 1/(nx+1) */
@@ -147,6 +148,9 @@ typedef struct {
     double seconds;        /* wall time of the call */
     int status;            /* pit_status of this member */
     int history_count;     /* entries written to opts->history */
+    double queue_seconds;  /* serving: submission to admission (0 otherwise) */
+    double latency_seconds;  /* serving: submission to result on the host (0 otherwise) */
+    long long device_bytes;  /* serving: peak device bytes the request held (0 otherwise) */
 } pit_solve_info;
 
 /* Fills *opts with defaults: tol 1e-10, eps0 1e-8, max_iter 500, X0 coarse,
@@ -259,6 +263,97 @@ pit_status pit_block_reduce_noalloc(const double *U, const double *V, int nblock
  * Errors: PIT_E_INVALID, PIT_E_NONFINITE (host arrays only), PIT_E_CUDA.
  */
 pit_status pit_problem_set_y0(pit_problem_t prob, const double *y0, int on_device);
+
+/* -------------------------------------------------------------- serving */
+/*
+ * A request server on the current device: continuous batching of PiTSBiCG
+ * solves (the mixed-precision or FP64 solve of pit_bicgstab_solve, Algorithm
+ * 1 on eq. (8)) of different sizes N and grids, submitted while others run.
+ *
+ * max_slots (1..64) worker threads each own a CUDA stream.  A free worker
+ * admits the first queued request whose device footprint
+ * (pit_serve_footprint) fits hbm_budget_bytes next to the running ones,
+ * builds its problem with stream-ordered allocations from a memory pool of
+ * the server, solves it and copies the result to host memory; the GPU work
+ * of up to max_slots requests overlaps.  A request that does not fit may be
+ * overtaken by later, smaller ones 16 times at most.  hbm_budget_bytes = 0
+ * takes 80% of the device's free memory.  Freed pool memory is kept (up to
+ * the budget) for later requests.  Each result does not depend on the
+ * other requests: it equals the result of pit_bicgstab_solve on the same
+ * problem and options alone.
+ *
+ * The server is thread-safe: any thread may submit, poll, wait or cancel.
+ * Kinds served: PIT_OP_HEAT1D and PIT_OP_HEAT2D (PIT_E_UNSUPPORTED
+ * otherwise).  Errors: PIT_E_INVALID (max_slots, null out), PIT_E_CUDA.
+ */
+pit_status pit_server_create(size_t hbm_budget_bytes, int max_slots, pit_server_t *out);
+
+/* Cancels queued requests, asks running ones to stop at their next
+ * iteration, joins the workers and frees everything; results not yet taken
+ * are dropped.  NULL is a no-op. */
+pit_status pit_server_destroy(pit_server_t server);
+
+/*
+ * Queues one request.  Everything is copied: desc (with y0; vx, vy and A are
+ * not used by the served kinds) and opts (its stream, history and
+ * history_len are ignored: the server uses its slot's stream).  *ticket
+ * identifies the request in poll / wait / cancel.  Validation of the
+ * operator's values (finite y0, supported steppers) happens when the
+ * request runs and is reported by poll.
+ * Errors: PIT_E_INVALID (null argument, bad sizes, server stopping),
+ * PIT_E_UNSUPPORTED (kind), PIT_E_NOMEM (the footprint alone exceeds the
+ * budget), PIT_E_BUSY (2^20 requests queued).
+ */
+pit_status pit_serve_submit(pit_server_t server, const pit_problem_desc *desc,
+                            const pit_solve_opts *opts, uint64_t *ticket);
+
+/*
+ * Non-blocking: PIT_PENDING while the request is queued or running.
+ * Otherwise the request's final status (that of pit_bicgstab_solve, or
+ * PIT_E_CANCELLED, or the set-up error), with the result copied to X_out
+ * (host, batch*(N+1)*M doubles; may be NULL) and one pit_solve_info per
+ * member to info (may be NULL; queue_seconds, latency_seconds and
+ * device_bytes filled in); the request is then released and its ticket
+ * becomes unknown (PIT_E_INVALID).  X_out is left untouched when the solve
+ * failed before producing an iterate.
+ */
+pit_status pit_serve_poll(pit_server_t server, uint64_t ticket, double *X_out,
+                          pit_solve_info *info);
+
+/* pit_serve_poll that blocks until the request is done or timeout_s seconds
+ * have passed (PIT_PENDING); timeout_s < 0 waits without limit. */
+pit_status pit_serve_wait(pit_server_t server, uint64_t ticket, double timeout_s,
+                          double *X_out, pit_solve_info *info);
+
+/* A queued request is removed (its poll returns PIT_E_CANCELLED); a running
+ * one stops at its next BiCGStab iteration or refinement round and reports
+ * PIT_E_CANCELLED.  Errors: PIT_E_INVALID (unknown ticket). */
+pit_status pit_serve_cancel(pit_server_t server, uint64_t ticket);
+
+/* Device bytes the server reserves for a request of this description: an
+ * upper bound of what its problem allocates (eight Krylov block vectors,
+ * the FP32 fine output and sine-mode work of the 2D sweep, set-up tables,
+ * reduction partials).  Host-only. */
+pit_status pit_serve_footprint(const pit_problem_desc *desc, size_t *bytes);
+
+typedef struct {
+    long long submitted, completed, failed, cancelled;  /* failed: completed with status != OK */
+    long long queued, running;
+    int max_running;       /* most requests running at once */
+    int slots;
+    double latency_p50, latency_p99, latency_mean;  /* submission to result, seconds */
+    double queue_p50, queue_p99;                    /* submission to admission */
+    double service_p50, service_p99;                /* admission to result */
+    double window_seconds;  /* first submission to last completion */
+    double solves_per_s;    /* successful solves / window */
+    double slice_steps_per_s;  /* fine slice-steps of completed solves / window */
+    size_t hbm_budget, hbm_reserved, hbm_reserved_peak;  /* admission footprints */
+    size_t pool_peak;       /* high-water mark of the pool's reserved device memory */
+} pit_server_stats_t;
+
+/* Statistics of the requests completed since creation or the last reset
+ * (percentiles by nearest rank); reset = 1 starts a new window. */
+pit_status pit_server_stats(pit_server_t server, int reset, pit_server_stats_t *out);
 
 /* ---------------------------------------------------------- diagnostics */
 

@@ -32,11 +32,15 @@ pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line
     return PIT_E_CUDA;
 }
 
+thread_local AllocCtx *tl_alloc = nullptr;
+
 pit_status DevBuf::ensure(size_t n) {
     if (n <= bytes && ptr) return PIT_OK;
     release();
     if (n == 0) return PIT_OK;
-    cudaError_t e = cudaMalloc(&ptr, n);
+    AllocCtx *ctx = tl_alloc;
+    cudaError_t e = ctx ? cudaMallocFromPoolAsync(&ptr, n, ctx->pool, ctx->stream)
+                        : cudaMalloc(&ptr, n);
     if (e != cudaSuccess) {
         ptr = nullptr;
         bytes = 0;
@@ -48,13 +52,27 @@ pit_status DevBuf::ensure(size_t n) {
         return PIT_E_NOMEM;
     }
     bytes = n;
+    if (ctx) {
+        astream = ctx->stream;
+        ctx->cur += n;
+        ctx->peak = std::max(ctx->peak, ctx->cur);
+    }
     return PIT_OK;
 }
 
 void DevBuf::release() {
-    if (ptr) cudaFree(ptr);
+    if (ptr) {
+        if (astream) {
+            cudaFreeAsync(ptr, astream);
+            if (tl_alloc && tl_alloc->stream == astream)
+                tl_alloc->cur -= std::min(tl_alloc->cur, bytes);
+        } else {
+            cudaFree(ptr);
+        }
+    }
     ptr = nullptr;
     bytes = 0;
+    astream = nullptr;
 }
 
 // ------------------------------------------------------------ op timing
@@ -233,6 +251,18 @@ static pit_status apply_GinvF(Problem *p, const double *x, double *y, int prec,
 // ------------------------------------------------------------ the engine
 namespace {
 
+// Pinned staging for the per-iteration state read-back, one per host thread
+// and kept for the thread's life: allocating and freeing pinned memory per
+// solve would synchronise the whole device (and stall concurrent solves).
+struct PinnedStates {
+    MemberState *ptr = nullptr;
+    int cap = 0;
+    ~PinnedStates() {
+        if (ptr) cudaFreeHost(ptr);
+    }
+};
+thread_local PinnedStates tl_pinned;
+
 struct HostStates {
     std::vector<MemberState> v;
     MemberState *pinned = nullptr;
@@ -240,11 +270,15 @@ struct HostStates {
     pit_status init(int b) {
         batch = b;
         v.resize(b);
-        PIT_CUDA(cudaMallocHost(&pinned, sizeof(MemberState) * b));
+        if (tl_pinned.cap < b) {
+            if (tl_pinned.ptr) cudaFreeHost(tl_pinned.ptr);
+            tl_pinned.ptr = nullptr;
+            tl_pinned.cap = 0;
+            PIT_CUDA(cudaMallocHost(&tl_pinned.ptr, sizeof(MemberState) * b));
+            tl_pinned.cap = b;
+        }
+        pinned = tl_pinned.ptr;
         return PIT_OK;
-    }
-    ~HostStates() {
-        if (pinned) cudaFreeHost(pinned);
     }
     pit_status fetch(Problem *p, cudaStream_t s) {
         PIT_CUDA(cudaMemcpyAsync(pinned, p->states.ptr, sizeof(MemberState) * batch,
@@ -259,6 +293,14 @@ struct HostStates {
         return false;
     }
 };
+
+pit_status check_cancel(const Problem *p) {
+    if (p->cancel && *p->cancel) {
+        set_error("the solve was cancelled");
+        return PIT_E_CANCELLED;
+    }
+    return PIT_OK;
+}
 
 struct LoopOut {
     std::vector<MemberState> final_states;
@@ -291,6 +333,7 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
             last_iter = hs.v[0].iter;
         }
         if (!hs.any_active()) break;
+        PIT_TRY(check_cancel(p));
         PIT_TRY(apply_GinvF(p, p->P.as<double>(), p->D.as<double>(), prec, st, s));   // D = G^-1 F P
         PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_sigma(p, s));                             // alpha
         PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_update_S(p, s));                          // S = R - alpha D
@@ -376,7 +419,12 @@ size_t pit_last_error(char *buf, size_t n) {
     return e.size();
 }
 
-pit_status pit_problem_create(const pit_problem_desc *d, pit_problem_t *out) {
+}  // extern "C"
+
+namespace pit {
+
+pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
+                          pit_problem_t *out) {
     if (!d || !out) {
         set_error("pit_problem_create: null argument");
         return PIT_E_INVALID;
@@ -445,15 +493,21 @@ pit_status pit_problem_create(const pit_problem_desc *d, pit_problem_t *out) {
     };
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__));
-    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamDefault);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__));
+    if (ext_stream) {
+        p->stream = ext_stream;
+        p->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&p->stream, cudaStreamDefault);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__));
+    }
     if ((s = p->y0.ensure(M * d->batch * sizeof(double))) != PIT_OK) return fail(s);
-    e = cudaMemcpy(p->y0.ptr, d->y0, M * d->batch * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(p->y0.ptr, d->y0, M * d->batch * sizeof(double), cudaMemcpyHostToDevice,
+                        p->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "copy y0", __FILE__, __LINE__));
     if ((s = p->fine_tmp.ensure(std::max<size_t>(4096, 64 * (size_t)d->batch))) != PIT_OK)
         return fail(s);
     if ((s = p->errword.ensure(sizeof(int))) != PIT_OK) return fail(s);
-    e = cudaMemset(p->errword.ptr, 0, sizeof(int));
+    e = cudaMemsetAsync(p->errword.ptr, 0, sizeof(int), p->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "clear error word", __FILE__, __LINE__));
     switch (p->kind) {
     case PIT_OP_HEAT1D: s = heat1d_setup(p); break;
@@ -484,6 +538,14 @@ pit_status pit_problem_create(const pit_problem_desc *d, pit_problem_t *out) {
     return PIT_OK;
 }
 
+}  // namespace pit
+
+extern "C" {
+
+pit_status pit_problem_create(const pit_problem_desc *d, pit_problem_t *out) {
+    return problem_create(d, nullptr, out);
+}
+
 pit_status pit_problem_destroy(pit_problem_t h) {
     if (!h) return PIT_OK;
     Problem *p = &h->p;
@@ -500,7 +562,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
     for (DevBuf *b : bufs) b->release();
     dense_teardown(p);
     p->timer.destroy();
-    if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->stream && p->own_stream) cudaStreamDestroy(p->stream);
     delete h;
     return PIT_OK;
 }
@@ -687,6 +749,7 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
             }
             if (o->history && hc < o->history_len) o->history[hc++] = rtrue[0];
             if (!any) break;
+            PIT_TRY(check_cancel(p));
             for (int b = 0; b < B; ++b)
                 if (done[b])
                     PIT_CUDA(cudaMemsetAsync(Wr + (size_t)b * p->blen, 0,

@@ -235,7 +235,7 @@ void thomas_factors(int M, double r, std::vector<double> &fm, std::vector<double
     }
 }
 
-pit_status upload_factors(int M, double r, DevBuf &b64, DevBuf &b32) {
+pit_status upload_factors(int M, double r, DevBuf &b64, DevBuf &b32, cudaStream_t s) {
     std::vector<double> fm, inv, cp;
     thomas_factors(M, r, fm, inv, cp);
     std::vector<double> all(3 * (size_t)M);
@@ -248,8 +248,8 @@ pit_status upload_factors(int M, double r, DevBuf &b64, DevBuf &b32) {
     for (size_t i = 0; i < all.size(); ++i) all32[i] = (float)all[i];
     PIT_TRY(b64.ensure(all.size() * sizeof(double)));
     PIT_TRY(b32.ensure(all32.size() * sizeof(float)));
-    PIT_CUDA(cudaMemcpy(b64.ptr, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
-    PIT_CUDA(cudaMemcpy(b32.ptr, all32.data(), all32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    PIT_CUDA(cudaMemcpyAsync(b64.ptr, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    PIT_CUDA(cudaMemcpyAsync(b32.ptr, all32.data(), all32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     return PIT_OK;
 }
 
@@ -333,8 +333,8 @@ pit_status heat1d_setup(Problem *p) {
     const double rf = (p->dT / p->fine_steps) * p->nu / (h * h);
     const double rc = (p->dT / p->coarse_steps) * p->nu / (h * h);
     // fine factors in fine_inv64/32, coarse in coarse_inv64/32 (fm | inv | cp)
-    PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32));
-    PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32));
+    PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32, p->stream));
+    PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32, p->stream));
     return PIT_OK;
 }
 

@@ -578,9 +578,9 @@ pit_status heat2d_setup(Problem *p) {
     PIT_TRY(p->S64.ensure(S.size() * sizeof(double)));
     PIT_TRY(p->S32.ensure(S32.size() * sizeof(float)));
     PIT_TRY(p->gmode.ensure(g.size() * sizeof(double)));
-    PIT_CUDA(cudaMemcpy(p->S64.ptr, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
-    PIT_CUDA(cudaMemcpy(p->S32.ptr, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice));
-    PIT_CUDA(cudaMemcpy(p->gmode.ptr, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice));
+    PIT_CUDA(cudaMemcpyAsync(p->S64.ptr, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    PIT_CUDA(cudaMemcpyAsync(p->S32.ptr, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    PIT_CUDA(cudaMemcpyAsync(p->gmode.ptr, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     // autotune the FP32 fine kernel's thread tile (4 or 8 columns) on this shape
     if (p->precision == PIT_MIXED) {
         DevBuf xin, qout;

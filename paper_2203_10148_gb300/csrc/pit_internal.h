@@ -41,10 +41,22 @@ extern std::atomic<unsigned long long> g_launches;
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
+    cudaStream_t astream = nullptr;   // stream of a pool allocation (nullptr: cudaMalloc)
     pit_status ensure(size_t n);   // grows (never shrinks) the allocation
     void release();
     template <class T> T *as() const { return static_cast<T *>(ptr); }
 };
+
+// Allocation context of the calling host thread.  When set (a serving slot),
+// DevBuf allocations are stream-ordered allocations from `pool` on `stream`
+// (no device-wide synchronisation on free, memory reused across requests)
+// and are counted in cur / peak.
+struct AllocCtx {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t stream = nullptr;
+    size_t cur = 0, peak = 0;
+};
+extern thread_local AllocCtx *tl_alloc;
 
 // Per-member solver state, resident on the device (Algorithm 1 scalars).
 struct MemberState {
@@ -110,6 +122,8 @@ struct Problem {
     size_t vlen = 0;              // batch*(N+1)*M
     int device = 0;
     cudaStream_t stream = nullptr;
+    bool own_stream = true;       // false: the stream belongs to a serving slot
+    const volatile int *cancel = nullptr;   // serving: nonzero asks the solve to stop
 
     DevBuf y0;                    // batch*M
 
@@ -207,6 +221,10 @@ pit_status autotune(const std::string &key, int ncand, const std::function<pit_s
                     cudaStream_t s, int *choice);
 
 // ------------------------------------------------------------ Krylov API
+// pit_problem_create with an optional caller stream (not owned; nullptr: a
+// stream of the problem's own).
+pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
+                          pit_problem_t *out);
 pit_status krylov_prepare(Problem *p);   // allocates vectors, partials, states
 // block copy of y0 into block 0 of each member and zeros elsewhere
 pit_status build_rhs(Problem *p, double *B, cudaStream_t s);

@@ -20,8 +20,10 @@ _lib: Optional[C.CDLL] = None
 PIT_OK, PIT_PENDING = 0, 1
 PIT_E_INVALID, PIT_E_NOMEM, PIT_E_CUDA, PIT_E_BREAKDOWN = -1, -2, -3, -4
 PIT_E_MAXITER, PIT_E_NONFINITE, PIT_E_TIMEOUT, PIT_E_BUSY, PIT_E_UNSUPPORTED = -5, -6, -7, -8, -9
+PIT_E_CANCELLED = -10
 STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "nomem", -3: "cuda", -4: "breakdown",
-                -5: "maxiter", -6: "nonfinite", -7: "timeout", -8: "busy", -9: "unsupported"}
+                -5: "maxiter", -6: "nonfinite", -7: "timeout", -8: "busy", -9: "unsupported",
+                -10: "cancelled"}
 
 PIT_OP = {"heat1d": 1, "heat2d": 2, "advdiff2d": 3, "dense": 4}
 PIT_STEP = {"ie": 1, "rk4": 2}
@@ -60,12 +62,31 @@ class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("matvecs", C.c_int), ("restarts", C.c_int),
                 ("refinements", C.c_int), ("fine_slice_steps", C.c_longlong),
                 ("r0", C.c_double), ("precond_resid", C.c_double), ("seconds", C.c_double),
-                ("status", C.c_int), ("history_count", C.c_int)]
+                ("status", C.c_int), ("history_count", C.c_int),
+                ("queue_seconds", C.c_double), ("latency_seconds", C.c_double),
+                ("device_bytes", C.c_longlong)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
         return d
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong),
+                ("failed", C.c_longlong), ("cancelled", C.c_longlong),
+                ("queued", C.c_longlong), ("running", C.c_longlong),
+                ("max_running", C.c_int), ("slots", C.c_int),
+                ("latency_p50", C.c_double), ("latency_p99", C.c_double),
+                ("latency_mean", C.c_double), ("queue_p50", C.c_double),
+                ("queue_p99", C.c_double), ("service_p50", C.c_double),
+                ("service_p99", C.c_double), ("window_seconds", C.c_double),
+                ("solves_per_s", C.c_double), ("slice_steps_per_s", C.c_double),
+                ("hbm_budget", C.c_size_t), ("hbm_reserved", C.c_size_t),
+                ("hbm_reserved_peak", C.c_size_t), ("pool_peak", C.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PitError(RuntimeError):
@@ -79,7 +100,9 @@ EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_cre
            "pit_problem_destroy", "pit_problem_shape", "pit_apply_operator", "pit_serial_fine",
            "pit_bicgstab_solve", "pit_parareal_solve", "pit_block_reduce",
            "pit_problem_set_y0", "pit_kernel_launches", "pit_set_timing", "pit_get_timing",
-           "pit_block_reduce_noalloc", "pit_selftest_convert"]
+           "pit_block_reduce_noalloc", "pit_selftest_convert", "pit_server_create",
+           "pit_server_destroy", "pit_serve_submit", "pit_serve_poll", "pit_serve_wait",
+           "pit_serve_cancel", "pit_serve_footprint", "pit_server_stats"]
 
 TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4,
                 "fine_ff": 5}
@@ -120,6 +143,15 @@ def load() -> C.CDLL:
     lib.pit_kernel_launches.restype = C.c_ulonglong
     lib.pit_set_timing.argtypes = [P, C.c_int]
     lib.pit_get_timing.argtypes = [P, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
+    lib.pit_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(P)]
+    lib.pit_server_destroy.argtypes = [P]
+    lib.pit_serve_submit.argtypes = [P, C.POINTER(ProblemDesc), C.POINTER(SolveOpts),
+                                     C.POINTER(C.c_uint64)]
+    lib.pit_serve_poll.argtypes = [P, C.c_uint64, P, C.POINTER(SolveInfo)]
+    lib.pit_serve_wait.argtypes = [P, C.c_uint64, C.c_double, P, C.POINTER(SolveInfo)]
+    lib.pit_serve_cancel.argtypes = [P, C.c_uint64]
+    lib.pit_serve_footprint.argtypes = [C.POINTER(ProblemDesc), C.POINTER(C.c_size_t)]
+    lib.pit_server_stats.argtypes = [P, C.c_int, C.POINTER(ServerStats)]
     for name in EXPORTS:
         if name not in ("pit_default_opts", "pit_version", "pit_last_error", "pit_kernel_launches"):
             getattr(lib, name).restype = C.c_int
@@ -166,6 +198,40 @@ def _array_arg(x) -> Tuple[int, int, object]:
     raise TypeError(f"unsupported array type {type(x)}")
 
 
+def problem_desc(w, precision: int) -> Tuple[ProblemDesc, list]:
+    """pit_problem_desc of a workload, and the arrays it points into."""
+    keep = []
+    y0 = np.ascontiguousarray(np.asarray(w.y0, dtype=np.float64).reshape(-1))
+    keep.append(y0)
+    op = OperatorDesc(PIT_OP[w.kind], w.nx, w.ny, float(w.nu), None, None, None)
+    if w.kind == "advdiff2d":
+        vx = np.ascontiguousarray(w.vx, dtype=np.float64)
+        vy = np.ascontiguousarray(w.vy, dtype=np.float64)
+        keep += [vx, vy]
+        op.vx, op.vy = _dptr(vx), _dptr(vy)
+    if w.kind == "dense":
+        A = np.ascontiguousarray(w.A, dtype=np.float64)
+        keep.append(A)
+        op.A = _dptr(A)
+    desc = ProblemDesc(op, _dptr(y0), int(w.batch), float(w.T), int(w.N),
+                       StepperDesc(PIT_STEP[w.fine[0]], int(w.fine[1])),
+                       StepperDesc(PIT_STEP[w.coarse[0]], int(w.coarse[1])), precision)
+    return desc, keep
+
+
+def solve_opts(tol: float = 1e-10, eps0: float = 1e-8, max_iter: int = 500,
+               x0: str = "coarse", refine_max: int = 8, inner_tol: float = 1e-4,
+               tol_mode: str = "r0", residual_precision: str = "ff") -> SolveOpts:
+    opts = SolveOpts()
+    load().pit_default_opts(C.byref(opts))
+    opts.tol, opts.restart_eps0, opts.max_iter = tol, eps0, max_iter
+    opts.x0_mode = X0[x0]
+    opts.refine_max, opts.inner_tol = refine_max, inner_tol
+    opts.tol_mode = TOL_MODE[tol_mode]
+    opts.residual_precision = PRECISION[residual_precision]
+    return opts
+
+
 class Problem:
     """A libpit problem built from a workload (paper_2203_10148_gb300.inputs.Workload)."""
 
@@ -173,22 +239,7 @@ class Problem:
         lib = load()
         self.w = w
         self.precision = PRECISION[precision or w.precision]
-        self._keep = []
-        y0 = np.ascontiguousarray(np.asarray(w.y0, dtype=np.float64).reshape(-1))
-        self._keep.append(y0)
-        op = OperatorDesc(PIT_OP[w.kind], w.nx, w.ny, float(w.nu), None, None, None)
-        if w.kind == "advdiff2d":
-            vx = np.ascontiguousarray(w.vx, dtype=np.float64)
-            vy = np.ascontiguousarray(w.vy, dtype=np.float64)
-            self._keep += [vx, vy]
-            op.vx, op.vy = _dptr(vx), _dptr(vy)
-        if w.kind == "dense":
-            A = np.ascontiguousarray(w.A, dtype=np.float64)
-            self._keep.append(A)
-            op.A = _dptr(A)
-        desc = ProblemDesc(op, _dptr(y0), int(w.batch), float(w.T), int(w.N),
-                           StepperDesc(PIT_STEP[w.fine[0]], int(w.fine[1])),
-                           StepperDesc(PIT_STEP[w.coarse[0]], int(w.coarse[1])), self.precision)
+        desc, self._keep = problem_desc(w, self.precision)
         h = C.c_void_p()
         check(lib.pit_problem_create(C.byref(desc), C.byref(h)))
         self.handle = h
@@ -247,13 +298,8 @@ class Problem:
                        residual_precision: str = "ff"):
         """pit_bicgstab_solve; returns (X, [info dict per member])."""
         lib = load()
-        opts = SolveOpts()
-        lib.pit_default_opts(C.byref(opts))
-        opts.tol, opts.restart_eps0, opts.max_iter = tol, eps0, max_iter
-        opts.x0_mode = X0["given" if (x0 == "given") else x0]
-        opts.refine_max, opts.inner_tol = refine_max, inner_tol
-        opts.tol_mode = TOL_MODE[tol_mode]
-        opts.residual_precision = PRECISION[residual_precision]
+        opts = solve_opts(tol, eps0, max_iter, x0, refine_max, inner_tol, tol_mode,
+                          residual_precision)
         hist = None
         if history_len:
             hist = np.zeros(history_len)
@@ -299,6 +345,83 @@ class Problem:
         if st in (PIT_E_INVALID, PIT_E_NOMEM, PIT_E_CUDA, PIT_E_UNSUPPORTED):
             check(st)
         return X, [i.as_dict() for i in infos]
+
+
+class Server:
+    """pit_server_*: continuous batching of solves submitted from any thread."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_slots: int = 4):
+        h = C.c_void_p()
+        check(load().pit_server_create(int(hbm_budget_bytes), int(max_slots), C.byref(h)))
+        self.handle = h
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pit_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, w, precision: Optional[str] = None, **opts) -> int:
+        """Queues workload ``w`` with solve options (as Problem.bicgstab_solve); a ticket."""
+        desc, keep = problem_desc(w, PRECISION[precision or w.precision])
+        o = solve_opts(**opts)
+        t = C.c_uint64()
+        check(load().pit_serve_submit(self.handle, C.byref(desc), C.byref(o), C.byref(t)))
+        self._shapes[t.value] = (int(w.batch), int(w.N) + 1, int(w.M))
+        del keep
+        return t.value
+
+    def _take(self, fn, ticket: int, *args):
+        shape = self._shapes.get(ticket)
+        if shape is None:   # not issued here, or taken: the library reports it
+            info = SolveInfo()
+            check(fn(self.handle, C.c_uint64(ticket), *args, None, C.byref(info)))
+            return None
+        X = np.empty(shape, dtype=np.float64)
+        infos = (SolveInfo * shape[0])()
+        st = fn(self.handle, C.c_uint64(ticket), *args, X.ctypes.data, infos)
+        if st == PIT_PENDING:
+            return None
+        if st == PIT_E_INVALID:
+            check(st)
+        del self._shapes[ticket]
+        return st, X, [i.as_dict() for i in infos]
+
+    def poll(self, ticket: int):
+        """None while pending, else (status, X, [info per member])."""
+        return self._take(load().pit_serve_poll, ticket)
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """Blocks until done (or the timeout: None); as poll."""
+        return self._take(load().pit_serve_wait, ticket, C.c_double(timeout))
+
+    def cancel(self, ticket: int):
+        check(load().pit_serve_cancel(self.handle, C.c_uint64(ticket)))
+
+    def stats(self, reset: bool = False) -> dict:
+        s = ServerStats()
+        check(load().pit_server_stats(self.handle, int(reset), C.byref(s)))
+        return s.as_dict()
+
+
+def serve_footprint(w) -> int:
+    """pit_serve_footprint: device bytes the server reserves for workload ``w``."""
+    desc, keep = problem_desc(w, PRECISION[w.precision])
+    b = C.c_size_t()
+    check(load().pit_serve_footprint(C.byref(desc), C.byref(b)))
+    return int(b.value)
 
 
 def kernel_launches() -> int:

@@ -81,3 +81,39 @@ def test_null_arguments(lib):
     assert lib.pit_apply_operator(None, 1, 0, None, None, 0, None) == pit.PIT_E_INVALID
     assert lib.pit_bicgstab_solve(None, None, None, 0, None) == pit.PIT_E_INVALID
     assert lib.pit_parareal_solve(None, 3, 0.0, None, 0, None) == pit.PIT_E_INVALID
+
+
+def test_serve_footprint_is_host_only_and_monotone(lib):
+    from paper_2203_10148_gb300 import inputs, pit
+    small = inputs.serving_request(0, m1d=(100, 101), nslices=(16, 17))[1]
+    f = pit.serve_footprint
+    base = inputs.heat1d()
+    b1 = f(base)
+    base.N *= 2
+    assert f(base) > b1
+    w2 = inputs.heat2d(n=32, N=16)
+    w1 = inputs.heat1d()
+    w1.nx, w1.N = 1024, 16
+    # the 2D sweep's sine-mode work makes a 2D request larger than a 1D one of equal size
+    assert f(w2) > f(w1)
+    # eight Krylov block vectors at least
+    vlen = (w2.N + 1) * w2.M * w2.batch
+    assert f(w2) >= 64 * vlen
+    assert f(small) > 0
+    bad = pit.ProblemDesc()
+    out = C.c_size_t()
+    assert lib.pit_serve_footprint(C.byref(bad), C.byref(out)) == pit.PIT_E_INVALID
+
+
+def test_server_calls_reject_null_handles(lib):
+    from paper_2203_10148_gb300 import pit
+    info = pit.SolveInfo()
+    st = pit.ServerStats()
+    assert lib.pit_serve_poll(None, 1, None, C.byref(info)) == pit.PIT_E_INVALID
+    assert lib.pit_serve_wait(None, 1, C.c_double(0.0), None, C.byref(info)) == pit.PIT_E_INVALID
+    assert lib.pit_serve_cancel(None, 1) == pit.PIT_E_INVALID
+    assert lib.pit_server_stats(None, 0, C.byref(st)) == pit.PIT_E_INVALID
+    t = C.c_uint64()
+    assert lib.pit_serve_submit(None, None, None, C.byref(t)) == pit.PIT_E_INVALID
+    assert lib.pit_server_destroy(None) == pit.PIT_OK
+    assert lib.pit_server_create(0, 0, None) == pit.PIT_E_INVALID
