@@ -2,12 +2,16 @@
 // interior points, h = 1/(n+1), 5-point Laplacian.
 //
 // Fine batch (the N independent slice problems of eq. (2), fused with the
-// shift-subtract of eq. (4)): one CTA per slice keeps the slice's whole
+// shift-subtract of eq. (4)): one CTA (n <= 128) or one thread-block
+// cluster of C CTAs (128 < n <= 256) per slice keeps the slice's whole
 // state on chip across all RK4 steps.  Thread (tx, ty) owns an RY x RX tile
 // of points; the west/east halo columns come from the neighbouring lanes
 // by warp shuffle (a row of thread tiles never straddles a warp) and the
 // north/south halo rows through a double-buffered shared-memory row buffer,
-// so each RK4 stage costs one CTA barrier.  RK4 for the linear autonomous
+// so each RK4 stage costs one CTA barrier.  In a cluster, CTA c owns the
+// row band [c BH, (c+1) BH) and reads the halo rows across band edges from
+// its neighbours' row buffers (distributed shared memory); the stage
+// barrier is then the cluster barrier.  RK4 for the linear autonomous
 // u' = L u is applied in nested (Horner) form
 //   w = u + (dt/4) L u;  w = u + (dt/3) L w;  w = u + (dt/2) L w;  u <- u + dt L w,
 // which is the same polynomial 1 + Z + Z^2/2 + Z^3/6 + Z^4/24 of Z = dt L as the
@@ -27,13 +31,18 @@
 #include <type_traits>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "pit_internal.h"
 #include "stencil_arith.cuh"
 
 namespace pit {
 namespace {
 
-constexpr int RY = 8;   // rows per thread tile (columns: Arith<V>::kRX)
+namespace cg = cooperative_groups;
+
+constexpr int RY8 = 8;   // rows per thread tile of the one-CTA kernels
+constexpr int CL_W = 256;    // padded row width of the cluster kernels (32 lanes x 8 columns)
 
 struct Heat2dArgs {
     const double *x;
@@ -46,6 +55,7 @@ struct Heat2dArgs {
     int steps;
     double c[4];    // stage coefficients dt/4, dt/3, dt/2, dt times nu/h^2
     int TX, TXp, TY;
+    int C;          // CTAs per slice (cluster size; 1 without clusters)
     const MemberState *st;
     float *y32;     // FP32 output of the block-operator rows (mixed G^{-1}F path) or null
 };
@@ -54,17 +64,18 @@ __device__ __forceinline__ bool runs(const MemberState *st, int b) {
     return st == nullptr || (st[b].active && !st[b].skip && !st[b].half);
 }
 
-// One CTA per (slice, member).  Threads: TXp * TYp (multiple of 32);
-// thread tiles with tx >= TX or ty >= TY hold zeros.  V is the arithmetic
-// (float, double or float-float); u lives in registers for FP32 and in a
-// thread-private shared-memory layout (us[k * threads + tid]) otherwise.
-template <class V, int RX>
-__global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
+// One CTA (CL = false) or one cluster of a.C CTAs (CL = true) per (slice,
+// member).  Threads per CTA: TXp * TYp (multiple of 32); thread tiles with
+// tx >= TX or rows >= n hold zeros.  V is the arithmetic (float, double or
+// float-float); u lives in registers for FP32 and in a thread-private
+// shared-memory layout (us[k * threads + tid]) otherwise.
+template <class V, int RX, int RY, bool CL>
+__global__ void __launch_bounds__(CL ? 256 : 2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
     using A = Arith<V>;
     constexpr bool kPacked = std::is_same<V, float>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = blockIdx.y;
-    if (!runs(a.st, b)) return;
+    if (!runs(a.st, b)) return;   // uniform over a cluster (same member)
     const int n = a.n;
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -76,9 +87,19 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
     V *us = rows + 4 * (size_t)TYp * W;           // u, thread-private layout
     constexpr bool U_SMEM = A::kUInSmem;
 
-    const int i0 = tx * RX, j0 = ty * RY;
+    // band of rows owned by this CTA (the whole grid without clusters)
+    const int rank = CL ? (int)(blockIdx.x % (unsigned)a.C) : 0;
+    const int jb = rank * TYp * RY;
+    [[maybe_unused]] const V *rows_up = rows;     // neighbours' row buffers
+    [[maybe_unused]] const V *rows_dn = rows;
+    if constexpr (CL) {
+        cg::cluster_group cl = cg::this_cluster();
+        if (rank > 0) rows_up = cl.map_shared_rank(rows, rank - 1);
+        if (rank < a.C - 1) rows_dn = cl.map_shared_rank(rows, rank + 1);
+    }
+    const int i0 = tx * RX, j0 = jb + ty * RY;
     const bool edge = (i0 + RX > n) || (j0 + RY > n);
-    const int slice = a.n_first + blockIdx.x;     // output block 1..N
+    const int slice = a.n_first + (CL ? (int)(blockIdx.x / (unsigned)a.C) : (int)blockIdx.x);
     const size_t mb = (size_t)b * a.blen;
     const double *xin = a.x + mb + (size_t)(slice - 1) * n * n;
 
@@ -99,7 +120,16 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
     // stage coefficients dt/4, dt/3, dt/2, dt (times nu/h^2), converted once
     if (tid < 4) ccs[tid] = A::from_d(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
     const bool west_zero = (tx == 0), east_zero = (tx == a.TXp - 1);
-    const bool north_zero = (ty == 0), south_zero = (ty == TYp - 1);
+    const bool north_remote = CL && ty == 0 && rank > 0;
+    const bool south_remote = CL && ty == TYp - 1 && rank < a.C - 1;
+    const bool north_zero = (ty == 0) && !north_remote;
+    const bool south_zero = (ty == TYp - 1) && !south_remote;
+    // thread row whose bottom (north halo) / top (south halo) row is read,
+    // in this CTA's buffer or in the neighbour's
+    const int nty = north_remote ? TYp - 1 : (north_zero ? ty : ty - 1);
+    const int sty = south_remote ? 0 : (south_zero ? ty : ty + 1);
+    const V *nbuf = north_remote ? rows_up : rows;
+    const V *sbuf = south_remote ? rows_dn : rows;
     // packed FP32 path: halo masks as multipliers
     [[maybe_unused]] const float mw = west_zero ? 0.f : 1.f, me = east_zero ? 0.f : 1.f;
     [[maybe_unused]] const float2 mn2 = north_zero ? make_float2(0.f, 0.f) : make_float2(1.f, 1.f);
@@ -116,7 +146,8 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
                 A::st4(rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0 + q, t0);
                 A::st4(rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0 + q, t1);
             }
-            __syncthreads();
+            if constexpr (CL) cg::this_cluster().sync();
+            else __syncthreads();
             const V cc = ccs[stage];
             [[maybe_unused]] float2 cc2;
             if constexpr (kPacked) cc2 = make_float2(cc, cc);
@@ -125,7 +156,7 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
 #pragma unroll
             for (int q = 0; q < RX; q += 4) {
                 V t[4];
-                A::ld4(rows + ((size_t)(buf * 2 + 1) * TYp + (north_zero ? ty : ty - 1)) * W + i0 + q, t);
+                A::ld4(nbuf + ((size_t)(buf * 2 + 1) * TYp + nty) * W + i0 + q, t);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) prev[q + c] = t[c];
             }
@@ -140,7 +171,7 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
 #pragma unroll
                     for (int q = 0; q < RX; q += 4) {
                         V t[4];
-                        A::ld4(rows + ((size_t)(buf * 2 + 0) * TYp + (south_zero ? ty : ty + 1)) * W + i0 + q, t);
+                        A::ld4(sbuf + ((size_t)(buf * 2 + 0) * TYp + sty) * W + i0 + q, t);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) srow[q + c] = t[c];
                     }
@@ -216,8 +247,11 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
                 else ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = v[r][c];
             }
     }
+    // no CTA of a cluster leaves while its row buffer may still be read
+    if constexpr (CL) cg::this_cluster().sync();
     // epilogue: row `slice` of the block operator
     const double *xn = a.x + mb + (size_t)slice * n * n;
+    const int cstride = CL ? a.C : 1;   // slice-0 copy split over the cluster
     if constexpr (std::is_same<V, float>::value) if (a.y32) {
         // FP32 rows q_n = x_n - F(x_{n-1}) for the FP32 sweep (apply mode)
         float *yo = a.y32 + mb + (size_t)slice * n * n;
@@ -235,7 +269,7 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
             const double *x0 = a.x + mb;
             float *y0o = a.y32 + mb;
             const int nn = n * n;
-            for (int k = tid; k < nn; k += nthr) y0o[k] = d2f_rn(x0[k]);
+            for (int k = rank * nthr + tid; k < nn; k += nthr * cstride) y0o[k] = d2f_rn(x0[k]);
         }
         return;
     }
@@ -257,21 +291,23 @@ __global__ void __launch_bounds__(2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
         const double *x0 = a.x + mb;
         double *y0o = a.y + mb;
         const int nn = n * n;
-        for (int k = tid; k < nn; k += nthr)
+        for (int k = rank * nthr + tid; k < nn; k += nthr * cstride)
             y0o[k] = (a.mode == FINE_APPLY) ? x0[k] : a.y0[(size_t)b * nn + k] - x0[k];
     }
 }
 
 // ------------------------------------------------------- sine transforms
-// out_b = scale * (A_b S)^T for every n x n block b (n <= 128), i.e.
+// out_b = scale * (A_b S)^T for every n x n block b (n <= 256), i.e.
 // out_b[k][j] = scale * sum_i A_b[j][i] S[i][k].  Applied twice it gives
-// scale^2 S A S (S symmetric).  One CTA of 256 threads per block; thread
-// (tx, ty) owns output rows j in {4ty..4ty+3, 64+4ty..64+4ty+3} and columns
+// scale^2 S A S (S symmetric).  One CTA of 256 threads per 128 x 128 output
+// tile of a block (one tile for n <= 128, four for n <= 256); the sum over i
+// runs in ascending chunks of 128, each staged in shared memory.  Thread
+// (tx, ty) owns tile rows j in {4ty..4ty+3, 64+4ty..64+4ty+3} and columns
 // k in {4tx..4tx+3, 64+4tx..64+4tx+3}, so the per-i operands are four
 // 16-byte shared loads (the S row loads contiguous across the lanes).  A_b is
-// staged transposed and both operands are zero-padded to 128, so the inner
-// loop has no conditionals.  S is staged in shared memory for FP32 and read
-// through L1/L2 for FP64.
+// staged transposed and both operands are zero-padded to the tile, so the
+// inner loop has no conditionals.  S is staged in shared memory for FP32 and
+// read through L1/L2 for FP64.
 // FP64 <-> FP32 conversions on the integer pipe (see stencil_arith.cuh)
 template <class To, class From>
 __device__ __forceinline__ To cvt(From x) {
@@ -305,68 +341,82 @@ struct Vec4<double> {
 template <class Tin, class T, class Tout>
 __global__ void __launch_bounds__(PT) k_block_xS_T(const Tin *__restrict__ A, Tout *__restrict__ out,
                                                    const T *__restrict__ S, int n, int nblk,
-                                                   double scale, const MemberState *st) {
+                                                   int tiles, double scale, const MemberState *st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool S_SMEM = sizeof(T) == 4;
-    const int blk = blockIdx.x;
+    const int nt2 = tiles * tiles;
+    const int blk = blockIdx.x / nt2;
+    const int tile = blockIdx.x % nt2;
+    const int jo = (tile / tiles) * PN, ko = (tile % tiles) * PN;   // tile origin
     const int member = blk / nblk;
     if (!runs(st, member)) return;
-    T *At = reinterpret_cast<T *>(smem_raw);       // At[i][j] = A[j][i], PN x PLD
-    T *Ss = At + (size_t)PN * PLD;                 // S[i][k] (FP32 only), PN x PLD
+    T *At = reinterpret_cast<T *>(smem_raw);       // At[i][j] = A[jo+j][ic+i], PN x PLD
+    T *Ss = At + (size_t)PN * PLD;                 // S[ic+i][ko+k] (FP32 only), PN x PLD
     const size_t nn = (size_t)n * n;
     const Tin *Ab = A + (size_t)blk * nn;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    // stage A_b transposed and S, zero-padded to PN x PN
-    for (int j = ty; j < PN; j += 16)
-        for (int i = tx; i < PN; i += 16) {
-            const bool ok = (i < n && j < n);
-            const T v = ok ? cvt<T>(Ab[(size_t)min(j, n - 1) * n + min(i, n - 1)]) : T(0);
-            At[(size_t)i * PLD + j] = v;
-            if (S_SMEM) Ss[(size_t)j * PLD + i] = ok ? S[(size_t)min(j, n - 1) * n + min(i, n - 1)] : T(0);
-        }
-    __syncthreads();
     T acc[8][8];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = T(0);
     const int ja = 4 * ty, jb = 64 + 4 * ty, ka = 4 * tx, kb = 64 + 4 * tx;
-    for (int i = 0; i < n; ++i) {
-        T a0[4], a1[4], s0[4], s1[4];
-        const T *arow = At + (size_t)i * PLD;
-        Vec4<T>::ld(arow + ja, a0);
-        Vec4<T>::ld(arow + jb, a1);
-        if (S_SMEM) {
-            const T *srow = Ss + (size_t)i * PLD;
-            Vec4<T>::ld(srow + ka, s0);
-            Vec4<T>::ld(srow + kb, s1);
-        } else {
-            const T *srow = S + (size_t)i * n;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                s0[c] = (ka + c < n) ? __ldg(srow + min(ka + c, n - 1)) : T(0);
-                s1[c] = (kb + c < n) ? __ldg(srow + min(kb + c, n - 1)) : T(0);
+    for (int ic = 0; ic < n; ic += PN) {
+        if (ic > 0) __syncthreads();   // the previous chunk is consumed
+        // stage the chunk of A_b transposed and of S, zero-padded to PN x PN
+        for (int r = ty; r < PN; r += 16)
+            for (int c = tx; c < PN; c += 16) {
+                const int j = jo + r, i = ic + c;
+                const bool ok = (i < n && j < n);
+                At[(size_t)c * PLD + r] =
+                    ok ? cvt<T>(Ab[(size_t)min(j, n - 1) * n + min(i, n - 1)]) : T(0);
+                if (S_SMEM) {
+                    const int si = ic + r, sk = ko + c;
+                    const bool oks = (si < n && sk < n);
+                    Ss[(size_t)r * PLD + c] =
+                        oks ? S[(size_t)min(si, n - 1) * n + min(sk, n - 1)] : T(0);
+                }
             }
+        __syncthreads();
+        const int ilen = min(PN, n - ic);
+        for (int i = 0; i < ilen; ++i) {
+            T a0[4], a1[4], s0[4], s1[4];
+            const T *arow = At + (size_t)i * PLD;
+            Vec4<T>::ld(arow + ja, a0);
+            Vec4<T>::ld(arow + jb, a1);
+            if (S_SMEM) {
+                const T *srow = Ss + (size_t)i * PLD;
+                Vec4<T>::ld(srow + ka, s0);
+                Vec4<T>::ld(srow + kb, s1);
+            } else {
+                const T *srow = S + (size_t)(ic + i) * n + ko;
+                const int kl = n - ko;   // valid columns of this tile
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    s0[c] = (ka + c < kl) ? __ldg(srow + min(ka + c, kl - 1)) : T(0);
+                    s1[c] = (kb + c < kl) ? __ldg(srow + min(kb + c, kl - 1)) : T(0);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc[r][c] = fma(a0[r], s0[c], acc[r][c]);
+                    acc[r][c + 4] = fma(a0[r], s1[c], acc[r][c + 4]);
+                    acc[r + 4][c] = fma(a1[r], s0[c], acc[r + 4][c]);
+                    acc[r + 4][c + 4] = fma(a1[r], s1[c], acc[r + 4][c + 4]);
+                }
         }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                acc[r][c] = fma(a0[r], s0[c], acc[r][c]);
-                acc[r][c + 4] = fma(a0[r], s1[c], acc[r][c + 4]);
-                acc[r + 4][c] = fma(a1[r], s0[c], acc[r + 4][c]);
-                acc[r + 4][c + 4] = fma(a1[r], s1[c], acc[r + 4][c + 4]);
-            }
     }
     Tout *ob = out + (size_t)blk * nn;
     const T sc = (T)scale;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const int k = (c < 4) ? ka + c : kb + c - 4;
+        const int k = ko + ((c < 4) ? ka + c : kb + c - 4);
         if (k >= n) continue;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-            const int j = (r < 4) ? ja + r : jb + r - 4;
+            const int j = jo + ((r < 4) ? ja + r : jb + r - 4);
             if (j < n) ob[(size_t)k * n + j] = cvt<Tout>(sc * acc[r][c]);
         }
     }
@@ -428,7 +478,7 @@ __global__ void k_rec_apply(T *__restrict__ hat, const double *__restrict__ ends
 
 constexpr int REC_CHUNK = 16;   // blocks per scan chunk
 
-template <class V, int RX>
+template <class V, int RX, int RY>
 size_t fine_smem(int TXp, int TYp) {
     size_t s = 32 + 4 * (size_t)TYp * TXp * RX * sizeof(V);
     if (Arith<V>::kUInSmem) s += (size_t)TXp * TYp * RY * RX * sizeof(V);
@@ -439,7 +489,7 @@ void tile_shape(int n, int RX, int &TX, int &TXp, int &TY, int &TYp) {
     TX = (n + RX - 1) / RX;
     TXp = 1;
     while (TXp < TX) TXp <<= 1;
-    TY = (n + RY - 1) / RY;
+    TY = (n + RY8 - 1) / RY8;
     const int threads = ((TXp * TY + 31) / 32) * 32;
     TYp = threads / TXp;
 }
@@ -451,19 +501,61 @@ pit_status launch_fine_rx(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s)
     a.TX = TX;
     a.TXp = TXp;
     a.TY = TY;
+    a.C = 1;
     const int threads = TXp * TYp;
-    const size_t sm = fine_smem<T, RX>(TXp, TYp);
-    PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T, RX>,
+    const size_t sm = fine_smem<T, RX, RY8>(TXp, TYp);
+    PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T, RX, RY8, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_heat2d_fine<T, RX><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
+    k_heat2d_fine<T, RX, RY8, false><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
 
-// FP32: tile width chosen by the autotuner (4 or 8 columns per thread);
-// FP64 and float-float: 4 columns.
+// 128 < n <= 256: a cluster of C = ceil(n / BH) CTAs per slice, each a band
+// of BH rows (64 for FP32; 32 for FP64 and float-float, whose u and row
+// buffers take twice the shared memory) on 32 x 8 threads of 8 columns.
+template <class T>
+struct ClusterShape {
+    static constexpr int RX = 8;
+    static constexpr int RY = std::is_same<T, float>::value ? 8 : 4;
+    static constexpr int TYp = 8;
+    static constexpr int BH = RY * TYp;
+};
+
+template <class T>
+pit_status launch_fine_cluster(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
+    using CS = ClusterShape<T>;
+    const int n = p->nx;
+    a.TX = (n + CS::RX - 1) / CS::RX;
+    a.TXp = CL_W / CS::RX;
+    a.TY = (n + CS::RY - 1) / CS::RY;
+    a.C = (n + CS::BH - 1) / CS::BH;
+    const int threads = a.TXp * CS::TYp;
+    const size_t sm = fine_smem<T, CS::RX, CS::RY>(a.TXp, CS::TYp);
+    auto kern = k_heat2d_fine<T, CS::RX, CS::RY, true>;
+    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nslices * a.C), (unsigned)p->batch);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PIT_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
+// n <= 128, FP32: tile width chosen by the autotuner (4 or 8 columns per
+// thread); FP64 and float-float: 4 columns.  128 < n <= 256: clusters.
 template <class T>
 pit_status launch_fine(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
+    if (p->nx > 128) return launch_fine_cluster<T>(p, a, nslices, s);
     if constexpr (std::is_same<T, float>::value) {
         if (p->tile_rx == 8) return launch_fine_rx<float, 8>(p, a, nslices, s);
     }
@@ -502,7 +594,9 @@ pit_status launch_xS(Problem *p, const Tin *A, Tout *out, const T *S, double sca
     PIT_CUDA(cudaFuncSetAttribute(k_block_xS_T<Tin, T, Tout>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int nblk = p->N + 1;
-    k_block_xS_T<Tin, T, Tout><<<nblk * p->batch, PT, sm, s>>>(A, out, S, n, nblk, scale, st);
+    const int tiles = (n + PN - 1) / PN;
+    k_block_xS_T<Tin, T, Tout><<<nblk * p->batch * tiles * tiles, PT, sm, s>>>(A, out, S, n, nblk,
+                                                                              tiles, scale, st);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
@@ -553,8 +647,8 @@ pit_status heat2d_setup(Problem *p) {
         set_error("heat2d: fine must be RK4 and coarse implicit Euler");
         return PIT_E_UNSUPPORTED;
     }
-    if (p->nx > 128) {
-        set_error("heat2d: n > 128 is not supported by the single-CTA slice kernel");
+    if (p->nx > 256) {
+        set_error("heat2d: n > 256 is not supported (one cluster of at most 8 CTAs per slice)");
         return PIT_E_UNSUPPORTED;
     }
     const int n = p->nx;
@@ -582,7 +676,8 @@ pit_status heat2d_setup(Problem *p) {
     PIT_CUDA(cudaMemcpyAsync(p->S32.ptr, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     PIT_CUDA(cudaMemcpyAsync(p->gmode.ptr, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     // autotune the FP32 fine kernel's thread tile (4 or 8 columns) on this shape
-    if (p->precision == PIT_MIXED) {
+    // (n > 128 runs the cluster kernel, which has a single tile shape)
+    if (p->precision == PIT_MIXED && p->nx <= 128) {
         DevBuf xin, qout;
         PIT_TRY(xin.ensure(p->vlen * sizeof(double)));
         PIT_TRY(qout.ensure(p->vlen * sizeof(float)));
