@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=1)
-    ap.add_argument("--workload", default="heat2d", choices=["heat2d", "dense", "advdiff"],
+    ap.add_argument("--workload", default="heat2d",
+                    choices=["heat2d", "dense", "advdiff", "serving"],
                     help="heat2d: 2D heat 128^2, N = 512 (the headline); dense: M = 1024, "
                          "N = 4096; advdiff: periodic 512^2, N = 256")
     ap.add_argument("--n", type=int, default=128)
@@ -74,6 +75,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--requests", type=int, default=128,
+                    help="serving: requests of the Poisson stream per step")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent solves")
     ap.add_argument("--tol", type=float, default=1e-7,
                     help="tolerance relative to ||G^-1 B|| (error target 1e-6)")
     return ap.parse_args()
@@ -456,10 +461,184 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# -------------------------------------------------------------- serving leg
+
+def serving_steps(args, rank, steps):
+    """Requests of each step: consecutive pieces of one seeded Poisson stream
+    (arrival times relative to the start of their step)."""
+    out = []
+    for st in range(steps):
+        first = (rank * 100003 + st) * args.requests
+        t, ws = 0.0, []
+        for j in range(args.requests):
+            gap, w = inputs.serving_request(first + j, rate=args.rate)
+            t += gap
+            w.arrival = t
+            ws.append(w)
+        out.append(ws)
+    return out
+
+
+def run_serving(args):
+    """Open-loop serving: each step submits `--requests` requests of the Poisson
+    stream at their arrival times to one server and waits for all results."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world,
+                                device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_10148_gb300 import pit
+
+    K, W = args.steps, args.warmup
+    steps = serving_steps(args, rank, W + K + 1)
+    opts = dict(tol=args.tol, tol_mode="rhs", max_iter=200, refine_max=8,
+                inner_tol=args.inner_tol, residual_precision="ff")
+    srv = pit.Server(hbm_budget_bytes=0, max_slots=args.slots)
+
+    def one(ws, open_loop=True):
+        t0 = time.perf_counter()
+        tickets = []
+        for w in ws:
+            if open_loop:
+                dt = w.arrival - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            tickets.append(srv.submit(w, **opts))
+        return [srv.wait(t) for t in tickets]
+
+    for s in range(W):
+        one(steps[s])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    srv.stats(reset=True)
+    launches0 = pit.kernel_launches()
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                    f"clocks_rank{rank}.csv"))
+    results = []
+    with clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(K):
+            results.append(one(steps[W + s]))
+        torch.cuda.synchronize()
+        total_s = time.perf_counter() - t0
+    launches = pit.kernel_launches() - launches0
+    st = srv.stats(reset=True)
+    # capacity: one more step submitted at once (closed loop)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    burst = one(steps[W + K], open_loop=False)
+    burst_s = time.perf_counter() - t1
+    if dist:
+        t = torch.tensor([total_s, burst_s], device=torch.device("cuda", local))
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s, burst_s = float(t[0]), float(t[1])
+    nreq = args.requests * K
+    ok = sum(1 for step in results for r in step if r[0] == pit.PIT_OK)
+    value = ok * world / total_s
+    slice_steps = sum(i["fine_slice_steps"] for step in results for r in step for i in r[2])
+    # accuracy: the sampled requests with the least fine work, against the FP64 GPU path
+    last = steps[W + K - 1]
+    order = sorted(range(len(last)), key=lambda j: last[j].N * last[j].fine[1] * last[j].M)
+    rel = 0.0
+    for j in order[:4]:
+        w = last[j]
+        with pit.Problem(w, "fp64") as p:
+            lam = p.serial_fine("fp64")
+        X = results[-1][j][1]
+        rel = max(rel, float(np.linalg.norm(X - lam) / np.linalg.norm(lam)))
+    line = None
+    if rank == 0:
+        peaks = load_peaks()
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+        peak = FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12
+        pts = sum(i["fine_slice_steps"] * w.M for step_w, step in zip(steps[W:W + K], results)
+                  for w, r in zip(step_w, step) for i in r[2])
+        ach = pts * OPS_PER_POINT_STEP["fine_fp32"] / total_s / 1e12
+        mix = [w for step in steps[W:W + K] for w in step]
+        h2d = sum(w.y0.size * 8 for w in mix) / K
+        d2h = sum(w.batch * (w.N + 1) * w.M * 8 for w in mix) / K
+        line = {"metric": "PiT solves/s & p50/p99 latency, serving (rel err <= 1e-6 vs FP64 path)",
+                "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": total_s * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 fine / f64 krylov", "data": "synthetic",
+                "config": {"workload": f"serving_poisson_{args.rate:g}rps_{args.requests}req_per_step",
+                           "mix": "50% heat1d M~U{63..4095} IE 100 steps/slice, 50% heat2d n~U{32..256} "
+                                  "RK4 m=max(50, dT nu/(0.2 h^2)); N~U{16..1024}; nu log-uniform [1e-3, 1e-1]",
+                           "slots": args.slots, "hbm_budget_bytes": st["hbm_budget"],
+                           "tol": args.tol, "tol_mode": "rhs", "inner_tol": args.inner_tol,
+                           "timer": "host wall clock around the open-loop stream, device synchronised",
+                           "l2": "working set > L2 (concurrent requests' Krylov vectors)",
+                           "parallelism": f"replicas x{world}"},
+                "latency_s": {"p50": st["latency_p50"], "p99": st["latency_p99"],
+                              "mean": st["latency_mean"], "queue_p50": st["queue_p50"],
+                              "queue_p99": st["queue_p99"], "service_p50": st["service_p50"],
+                              "service_p99": st["service_p99"]},
+                "fine_slice_steps_per_s": slice_steps * world / total_s,
+                "capacity_solves_per_s": args.requests * world / burst_s,
+                "completed": st["completed"], "failed": st["failed"], "requests": nreq,
+                "max_running": st["max_running"], "hbm_reserved_peak": st["hbm_reserved_peak"],
+                "pool_peak_bytes": st["pool_peak"], "rel_err_max_sampled": rel,
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "alu", "kernel": "whole serving run (all fine kernels)",
+                             "achieved": ach, "peak": peak, "unit": "Tops/s (FP32 pipe lane-ops)",
+                             "frac": ach / peak, "traffic": None,
+                             "note": "fine slice-steps x points x 20 lane-ops (FP32 count) / wall time",
+                             "peak_source": f"derived: 128 lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz"},
+                "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h),
+                        "note": "the serving value is host to host: y0 in, X out per request"},
+                "clocks": clk.summary(local)}
+        if rel > 1e-6:
+            line["invalid"] = f"rel err {rel:.3e} > 1e-6"
+        if not args.no_cpu:
+            try:
+                line["cpu_baseline"] = serving_cpu_baseline(last, results[-1])
+            except Exception as e:
+                line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1,
+                                        "kind": "oracle", "sample": f"failed: {e}"}
+    srv.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def serving_cpu_baseline(ws, res, budget_s=20.0):
+    """Oracle seconds per request, estimated on a bounded sample: for requests
+    of the stream (in order, until about `budget_s` of CPU time), the oracle's
+    G^{-1}F on up to 8 slices scaled to N plus one full sweep, times the number
+    of matvecs the GPU solve of that request took."""
+    tot, cnt, t_start = 0.0, 0, time.perf_counter()
+    for w, r in zip(ws, res):
+        if time.perf_counter() - t_start > budget_s and cnt >= 2:
+            break
+        if w.N * w.fine[1] * w.M > 4e8:
+            continue
+        t_f, t_s = oracle_sample(w, min(w.N, 8))
+        tot += (t_f + t_s) * r[2][0]["matvecs"]
+        cnt += 1
+    return {"value": cnt / tot if tot else None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 numpy/scipy oracle, 1 thread, {cnt} requests of the stream (fine "
+                       f"work <= 4e8 point-steps per matvec): G^-1F on up to 8 slices scaled to N "
+                       f"+ one full sweep, x the GPU solve's matvec count")}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -151,6 +151,7 @@ typedef struct {
     double queue_seconds;  /* serving: submission to admission (0 otherwise) */
     double latency_seconds;  /* serving: submission to result on the host (0 otherwise) */
     long long device_bytes;  /* serving: peak device bytes the request held (0 otherwise) */
+    int graph_iterations;  /* BiCGStab iterations run as replays of the captured CUDA graph */
 } pit_solve_info;
 
 /* Fills *opts with defaults: tol 1e-10, eps0 1e-8, max_iter 500, X0 coarse,
@@ -211,6 +212,15 @@ pit_status pit_serial_fine(pit_problem_t prob, int precision, double *Lam, int o
  * refinement: FP64 true residual G^{-1}(B - F64 X), an FP32-fine / FP64-Krylov
  * inner solve of the correction to inner_tol, X += correction, until the
  * true preconditioned residual is <= tol * its initial value.
+ * For PIT_OP_HEAT1D and PIT_OP_HEAT2D one iteration (two applications of
+ * G^{-1}F and the fused vector kernels) is captured as a CUDA graph after
+ * the first, eager, iteration of each inner solve and replayed for the
+ * others; the graph is kept with the problem (re-captured when the stream
+ * or the timing mode changes) and info.graph_iterations counts the
+ * replays.  Results are bit for bit those of eager launches.  The
+ * environment variable PIT_GRAPHS=0, read by pit_problem_create, turns the
+ * graphs off; a stream that cannot be captured (the legacy default stream)
+ * runs every iteration eagerly.
  * Synchronous.  Returns the worst member status (PIT_E_MAXITER,
  * PIT_E_BREAKDOWN, PIT_E_NONFINITE) or PIT_OK.
  */

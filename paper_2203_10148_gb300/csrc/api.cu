@@ -17,6 +17,7 @@
 namespace pit {
 
 std::atomic<unsigned long long> g_launches{0};
+thread_local unsigned long long tl_launches = 0;
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
@@ -33,11 +34,16 @@ pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line
 }
 
 thread_local AllocCtx *tl_alloc = nullptr;
+thread_local bool tl_capturing = false;
 
 pit_status DevBuf::ensure(size_t n) {
     if (n <= bytes && ptr) return PIT_OK;
     release();
     if (n == 0) return PIT_OK;
+    if (tl_capturing) {
+        set_error("device allocation requested during CUDA graph capture");
+        return PIT_E_CUDA;
+    }
     AllocCtx *ctx = tl_alloc;
     cudaError_t e = ctx ? cudaMallocFromPoolAsync(&ptr, n, ctx->pool, ctx->stream)
                         : cudaMalloc(&ptr, n);
@@ -88,7 +94,7 @@ cudaEvent_t OpTimer::get() {
 }
 
 pit_status OpTimer::begin(int cls, cudaStream_t s, Rec &r) {
-    if (pending.size() > 4096) PIT_TRY(resolve());
+    if (pending.size() > 4096 && !capture_into) PIT_TRY(resolve());
     r.cls = cls;
     r.a = get();
     r.b = get();
@@ -96,14 +102,39 @@ pit_status OpTimer::begin(int cls, cudaStream_t s, Rec &r) {
         set_error("cudaEventCreate failed");
         return PIT_E_CUDA;
     }
-    PIT_CUDA(cudaEventRecord(r.a, s));
+    if (capture_into) PIT_CUDA(cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal));
+    else PIT_CUDA(cudaEventRecord(r.a, s));
     return PIT_OK;
 }
 
 pit_status OpTimer::end(Rec &r, cudaStream_t s) {
+    if (capture_into) {
+        PIT_CUDA(cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal));
+        capture_into->push_back(r);
+        return PIT_OK;
+    }
     PIT_CUDA(cudaEventRecord(r.b, s));
     pending.push_back(r);
     return PIT_OK;
+}
+
+pit_status OpTimer::collect(const std::vector<Rec> &recs) {
+    for (const Rec &r : recs) {
+        PIT_CUDA(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        PIT_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.cls] += t;
+        calls[r.cls] += 1;
+    }
+    return PIT_OK;
+}
+
+void OpTimer::release(std::vector<Rec> &recs) {
+    for (Rec &r : recs) {
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    recs.clear();
 }
 
 pit_status OpTimer::resolve() {
@@ -294,6 +325,66 @@ struct HostStates {
     }
 };
 
+// CUDA graphs for the iteration: 2D and 1D heat (their launches are plain
+// and cluster kernel launches on one stream).
+bool graphs_apply(const Problem *p) {
+    return p->use_graphs && (p->kind == PIT_OP_HEAT1D || p->kind == PIT_OP_HEAT2D);
+}
+
+void iter_graph_drop(Problem *p, IterGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    p->timer.release(g.recs);
+}
+
+// Captures (or re-captures, when the stream, the buffers or the timing mode
+// changed) the iteration; on a stream that cannot be captured the graph is
+// marked failed and the iterations run eagerly.
+template <class Fn>
+pit_status iter_graph_ready(Problem *p, IterGraph &g, cudaStream_t s, Fn &&iteration) {
+    const void *ptrs[5] = {p->P.ptr, p->D.ptr, p->S.ptr, p->K.ptr, p->states.ptr};
+    const bool same = g.exec && g.stream == s && g.timed == p->timer.enabled &&
+                      std::equal(ptrs, ptrs + 5, g.ptrs);
+    if (same) return PIT_OK;
+    iter_graph_drop(p, g);
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        g.failed = true;
+        return PIT_OK;
+    }
+    tl_capturing = true;
+    p->timer.capture_into = p->timer.enabled ? &g.recs : nullptr;
+    const unsigned long long k0 = tl_launches;
+    const pit_status st = iteration();
+    // captured launches do not run: the counter counts each replay instead
+    g.kernels = tl_launches - k0;
+    g_launches -= g.kernels;
+    p->timer.capture_into = nullptr;
+    tl_capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != PIT_OK || e != cudaSuccess || !graph) {
+        (void)cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        p->timer.release(g.recs);
+        g.failed = true;
+        return PIT_OK;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        (void)cudaGetLastError();
+        g.exec = nullptr;
+        p->timer.release(g.recs);
+        g.failed = true;
+        return PIT_OK;
+    }
+    g.stream = s;
+    g.timed = p->timer.enabled;
+    std::copy(ptrs, ptrs + 5, g.ptrs);
+    return PIT_OK;
+}
+
 pit_status check_cancel(const Problem *p) {
     if (p->cancel && *p->cancel) {
         set_error("the solve was cancelled");
@@ -305,6 +396,7 @@ pit_status check_cancel(const Problem *p) {
 struct LoopOut {
     std::vector<MemberState> final_states;
     int history_count = 0;
+    int graph_iterations = 0;     // iterations run as replays of the captured graph
 };
 
 // Algorithm 1 on the workspace: X holds X^0.  If r_given, R already holds
@@ -324,16 +416,9 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
     PIT_TRY(hs.init(p->batch));
     int hc = history_offset;
     int last_iter = -1;
-    // iteration guard: every member stops by max_iter, plus one restart per iteration
-    const long guard = 2L * (max_iter + 2) + 4;
-    for (long it = 0; it < guard; ++it) {
-        PIT_TRY(hs.fetch(p, s));
-        if (history && hc < history_len && hs.v[0].iter != last_iter) {
-            history[hc++] = hs.v[0].rnorm;       // ||R^k||_{N,inf} of member 0
-            last_iter = hs.v[0].iter;
-        }
-        if (!hs.any_active()) break;
-        PIT_TRY(check_cancel(p));
+    // one iteration: every launch depends on device state only (members that
+    // converged or restarted are masked on the device), so it is replayable
+    auto iteration = [&]() -> pit_status {
         PIT_TRY(apply_GinvF(p, p->P.as<double>(), p->D.as<double>(), prec, st, s));   // D = G^-1 F P
         PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_sigma(p, s));                             // alpha
         PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_update_S(p, s));                          // S = R - alpha D
@@ -341,8 +426,38 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
         PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_omega(p, s));                             // omega
         PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_update_XR(p, s));                         // X, R, beta
         PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_update_P(p, s));                          // P
+        return PIT_OK;
+    };
+    IterGraph *g = graphs_apply(p) ? &p->igraph[prec == PIT_FP64 ? 0 : 1] : nullptr;
+    bool collect = false;
+    // iteration guard: every member stops by max_iter, plus one restart per iteration
+    const long guard = 2L * (max_iter + 2) + 4;
+    for (long it = 0; it < guard; ++it) {
+        PIT_TRY(hs.fetch(p, s));
+        if (collect) PIT_TRY(p->timer.collect(g->recs));
+        collect = false;
+        if (history && hc < history_len && hs.v[0].iter != last_iter) {
+            history[hc++] = hs.v[0].rnorm;       // ||R^k||_{N,inf} of member 0
+            last_iter = hs.v[0].iter;
+        }
+        if (!hs.any_active()) break;
+        PIT_TRY(check_cancel(p));
+        // the first iteration runs eagerly (it allocates every buffer the
+        // iteration uses); later ones replay the captured graph
+        if (g && it > 0 && !g->failed) {
+            PIT_TRY(iter_graph_ready(p, *g, s, iteration));
+            if (g->exec) {
+                PIT_CUDA(cudaGraphLaunch(g->exec, s));
+                g_launches += g->kernels;
+                out.graph_iterations += 1;
+                collect = g->timed;
+                continue;
+            }
+        }
+        PIT_TRY(iteration());
     }
     PIT_TRY(hs.fetch(p, s));
+    if (collect) PIT_TRY(p->timer.collect(g->recs));
     out.final_states = hs.v;
     out.history_count = hc - history_offset;
     return PIT_OK;
@@ -486,6 +601,10 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
     p->precision = d->precision;
     p->blen = (size_t)(p->N + 1) * M;
     p->vlen = p->blen * p->batch;
+    {
+        const char *g = getenv("PIT_GRAPHS");
+        p->use_graphs = !(g && g[0] == '0');
+    }
     pit_status s = PIT_OK;
     auto fail = [&](pit_status e) {
         pit_problem_destroy(h);
@@ -559,6 +678,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32,
                       &p->errword, &p->PhiTh, &p->PhiTl, &p->tc_split};
+    for (IterGraph &g : p->igraph) iter_graph_drop(p, g);
     for (DevBuf *b : bufs) b->release();
     dense_teardown(p);
     p->timer.destroy();
@@ -703,6 +823,7 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
             inf[b].precond_resid = m.rnorm;
             inf[b].status = m.status;
             inf[b].history_count = (b == 0) ? lo.history_count : 0;
+            inf[b].graph_iterations = lo.graph_iterations;
             status[b] = m.status;
         }
     } else {
@@ -762,6 +883,7 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
                 if (done[b]) continue;
                 const MemberState &m = lo.final_states[b];
                 inf[b].iterations += m.iter;
+                inf[b].graph_iterations += lo.graph_iterations;
                 inf[b].matvecs += m.matvecs - 1;   // R^0 was given: no matvec
                 inf[b].restarts += m.restarts;
                 inf[b].refinements += 1;

@@ -29,11 +29,13 @@ pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line
         if (s_ != PIT_OK) return s_;                                          \
     } while (0)
 
-extern std::atomic<unsigned long long> g_launches;
+extern std::atomic<unsigned long long> g_launches;   // all threads
+extern thread_local unsigned long long tl_launches;   // this thread
 
 #define PIT_LAUNCH_CHECK()                                                    \
     do {                                                                      \
         g_launches.fetch_add(1, std::memory_order_relaxed);                   \
+        ++tl_launches;                                                        \
         PIT_CUDA(cudaGetLastError());                                         \
     } while (0)
 
@@ -57,6 +59,10 @@ struct AllocCtx {
     size_t cur = 0, peak = 0;
 };
 extern thread_local AllocCtx *tl_alloc;
+// Set while this thread captures a CUDA graph: DevBuf::ensure must not
+// allocate then (the capture is abandoned and the work runs eagerly).
+extern thread_local bool tl_capturing;
+
 
 // Per-member solver state, resident on the device (Algorithm 1 scalars).
 struct MemberState {
@@ -101,14 +107,31 @@ struct OpTimer {
     };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
+    // while a CUDA graph is captured: records go here (external event-record
+    // nodes that fire at every replay) instead of `pending`
+    std::vector<Rec> *capture_into = nullptr;
     long long calls[PIT_TIME_CLASSES] = {};
     double ms[PIT_TIME_CLASSES] = {};
     cudaEvent_t get();
     pit_status begin(int cls, cudaStream_t s, Rec &r);
     pit_status end(Rec &r, cudaStream_t s);
     pit_status resolve();
+    pit_status collect(const std::vector<Rec> &recs);   // one replay of a timed graph
+    void release(std::vector<Rec> &recs);              // events back to the pool
     void reset();
     void destroy();
+};
+
+// One BiCGStab iteration (Algorithm 1: two applications of G^{-1}F and the
+// fused vector updates) captured as a CUDA graph and replayed.
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    const void *ptrs[5] = {};     // buffers the captured kernels use
+    bool timed = false;
+    bool failed = false;          // capture not possible on this stream: run eagerly
+    unsigned long long kernels = 0;   // kernel launches one replay stands for
+    std::vector<OpTimer::Rec> recs;
 };
 
 // ---------------------------------------------------------------- problem
@@ -160,6 +183,8 @@ struct Problem {
     int tile_rx = 4;              // heat2d FP32 thread-tile width (autotuned)
     ReduceLayout rl{};
     OpTimer timer;
+    IterGraph igraph[2];          // [0]: FP64 iterations, [1]: mixed (FP32 fine) iterations
+    bool use_graphs = true;       // PIT_GRAPHS=0 in the environment turns graphs off
 };
 
 // Modes of the fused block-operator epilogue.

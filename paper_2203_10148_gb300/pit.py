@@ -64,7 +64,7 @@ class SolveInfo(C.Structure):
                 ("r0", C.c_double), ("precond_resid", C.c_double), ("seconds", C.c_double),
                 ("status", C.c_int), ("history_count", C.c_int),
                 ("queue_seconds", C.c_double), ("latency_seconds", C.c_double),
-                ("device_bytes", C.c_longlong)]
+                ("device_bytes", C.c_longlong), ("graph_iterations", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
