@@ -37,6 +37,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2203_10148_gb300 import inputs  # noqa: E402
+from paper_2203_10148_gb300.replicas import (dist_env, max_over_ranks, replica_seed,  # noqa: E402
+                                             whole_job_rate)
 
 GOLDEN_SOLVE = os.path.join(ROOT, "tests", "golden", "oracle_solve_heat2d_128_N512.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
@@ -84,21 +86,14 @@ def parse():
     return ap.parse_args()
 
 
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
 def workload(args, rank, step=0):
     if args.workload == "dense":
-        seed = inputs.SEED_DENSE + 7919 * rank + 104729 * step
+        seed = replica_seed(inputs.SEED_DENSE, rank, step)
         return inputs.dense(batch=args.batch, seed=seed, tol=1e-6)
     if args.workload == "advdiff":
-        seed = inputs.SEED_ADVDIFF2D + 7919 * rank + 104729 * step
+        seed = replica_seed(inputs.SEED_ADVDIFF2D, rank, step)
         return inputs.advdiff2d(batch=args.batch, seed=seed, tol=1e-6)
-    seed = inputs.SEED_HEAT2D + 7919 * rank + 104729 * step
+    seed = replica_seed(inputs.SEED_HEAT2D, rank, step)
     return inputs.heat2d(n=args.n, N=args.N, batch=args.batch, seed=seed, tol=1e-6)
 
 
@@ -355,12 +350,9 @@ def run_ours(args):
     total_ms = ev[0].elapsed_time(ev[K])
     timing = prob.timing()
     prob.set_timing(False)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks([total_ms], dev)[0]
     solves = w.batch * K * world
-    value = solves / (total_ms / 1e3)
+    value = whole_job_rate(w.batch * K, world, total_ms / 1e3)
     slice_steps = sum(i["fine_slice_steps"] for inf in infos for i in inf) * world
     # accuracy of the last step against the FP64 serial fine trajectory (FP64 path)
     lam = torch.empty(shape, dtype=torch.float64, device=dev)
@@ -420,10 +412,7 @@ def run_ours(args):
             one_host(W + s)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks([e2e_s], dev)[0]
         if rank == 0:
             line["e2e"] = {"value": solves / e2e_s, "unit": "solves/s",
                            "h2d_bytes_per_step": w.batch * w.M * 8,
@@ -536,10 +525,7 @@ def run_serving(args):
     t1 = time.perf_counter()
     burst = one(steps[W + K], open_loop=False)
     burst_s = time.perf_counter() - t1
-    if dist:
-        t = torch.tensor([total_s, burst_s], device=torch.device("cuda", local))
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, burst_s = float(t[0]), float(t[1])
+    total_s, burst_s = max_over_ranks([total_s, burst_s], torch.device("cuda", local))
     nreq = args.requests * K
     ok = sum(1 for step in results for r in step if r[0] == pit.PIT_OK)
     value = ok * world / total_s

@@ -26,6 +26,8 @@
 // with qhat = S q S and z = (2/(n+1))^2 S zhat S.  The transforms are batched
 // block products; the recurrence is a chunked scan over n.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include <string>
 #include <type_traits>
@@ -42,7 +44,6 @@ namespace {
 namespace cg = cooperative_groups;
 
 constexpr int RY8 = 8;   // rows per thread tile of the one-CTA kernels
-constexpr int CL_W = 256;    // padded row width of the cluster kernels (32 lanes x 8 columns)
 
 struct Heat2dArgs {
     const double *x;
@@ -70,7 +71,9 @@ __device__ __forceinline__ bool runs(const MemberState *st, int b) {
 // float-float); u lives in registers for FP32 and in a thread-private
 // shared-memory layout (us[k * threads + tid]) otherwise.
 template <class V, int RX, int RY, bool CL>
-__global__ void __launch_bounds__(CL ? 256 : 2048 / RX, 1) k_heat2d_fine(Heat2dArgs a) {
+__global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
+                                  (CL && RY == 4 && std::is_same<V, float>::value) ? 2 : 1)
+    k_heat2d_fine(Heat2dArgs a) {
     using A = Arith<V>;
     constexpr bool kPacked = std::is_same<V, float>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -511,28 +514,24 @@ pit_status launch_fine_rx(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s)
     return PIT_OK;
 }
 
-// 128 < n <= 256: a cluster of C = ceil(n / BH) CTAs per slice, each a band
-// of BH rows (64 for FP32; 32 for FP64 and float-float, whose u and row
-// buffers take twice the shared memory) on 32 x 8 threads of 8 columns.
-template <class T>
-struct ClusterShape {
-    static constexpr int RX = 8;
-    static constexpr int RY = std::is_same<T, float>::value ? 8 : 4;
-    static constexpr int TYp = 8;
-    static constexpr int BH = RY * TYp;
-};
-
-template <class T>
+// Clusters: C = ceil(n / BH) CTAs of 256 threads per slice, each thread an
+// RY x 8 tile, TXp = 2^ceil(log2(n/8)) <= 32 threads per row of tiles and
+// TYp = 256 / TXp rows of them, so a CTA owns a band of BH = TYp * RY rows.
+// For n > 128: RY = 8 for FP32, 4 for FP64 and float-float (whose u and row
+// buffers take twice the shared memory); for n <= 128 (variant 2): RY = 4.
+template <class T, int RY>
 pit_status launch_fine_cluster(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
-    using CS = ClusterShape<T>;
+    constexpr int RX = 8, THREADS = 256;
     const int n = p->nx;
-    a.TX = (n + CS::RX - 1) / CS::RX;
-    a.TXp = CL_W / CS::RX;
-    a.TY = (n + CS::RY - 1) / CS::RY;
-    a.C = (n + CS::BH - 1) / CS::BH;
-    const int threads = a.TXp * CS::TYp;
-    const size_t sm = fine_smem<T, CS::RX, CS::RY>(a.TXp, CS::TYp);
-    auto kern = k_heat2d_fine<T, CS::RX, CS::RY, true>;
+    a.TX = (n + RX - 1) / RX;
+    a.TXp = 1;
+    while (a.TXp < a.TX) a.TXp <<= 1;
+    const int TYp = THREADS / a.TXp;
+    a.TY = (n + RY - 1) / RY;
+    a.C = (n + TYp * RY - 1) / (TYp * RY);
+    const int threads = THREADS;
+    const size_t sm = fine_smem<T, RX, RY>(a.TXp, TYp);
+    auto kern = k_heat2d_fine<T, RX, RY, true>;
     PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nslices * a.C), (unsigned)p->batch);
@@ -551,13 +550,16 @@ pit_status launch_fine_cluster(Problem *p, Heat2dArgs a, int nslices, cudaStream
     return PIT_OK;
 }
 
-// n <= 128, FP32: tile width chosen by the autotuner (4 or 8 columns per
-// thread); FP64 and float-float: 4 columns.  128 < n <= 256: clusters.
+// n <= 128: the variant chosen by the autotuner (FP32, float-float); FP64
+// runs one CTA of 4-column tiles.  128 < n <= 256: clusters.
 template <class T>
 pit_status launch_fine(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
-    if (p->nx > 128) return launch_fine_cluster<T>(p, a, nslices, s);
-    if constexpr (std::is_same<T, float>::value) {
-        if (p->tile_rx == 8) return launch_fine_rx<float, 8>(p, a, nslices, s);
+    constexpr bool F32 = std::is_same<T, float>::value;
+    if (p->nx > 128) return launch_fine_cluster<T, F32 ? 8 : 4>(p, a, nslices, s);
+    const int var = F32 ? p->fine_var32 : std::is_same<T, ff>::value ? p->fine_var_ff : 0;
+    if (var == 2) return launch_fine_cluster<T, 4>(p, a, nslices, s);
+    if constexpr (F32) {
+        if (var == 1) return launch_fine_rx<float, 8>(p, a, nslices, s);
     }
     return launch_fine_rx<T, 4>(p, a, nslices, s);
 }
@@ -675,28 +677,50 @@ pit_status heat2d_setup(Problem *p) {
     PIT_CUDA(cudaMemcpyAsync(p->S64.ptr, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     PIT_CUDA(cudaMemcpyAsync(p->S32.ptr, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     PIT_CUDA(cudaMemcpyAsync(p->gmode.ptr, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-    // autotune the FP32 fine kernel's thread tile (4 or 8 columns) on this shape
-    // (n > 128 runs the cluster kernel, which has a single tile shape)
+    // autotune the fine kernels' variant on this shape: FP32 (inner solves)
+    // among one CTA of 4- or 8-column tiles and a cluster of 8 x 4 tiles;
+    // float-float (true residuals) between one CTA and a cluster.  Every
+    // variant evaluates the same arithmetic per point: results do not depend
+    // on the choice.  (n > 128 runs clusters only.)
     if (p->precision == PIT_MIXED && p->nx <= 128) {
         DevBuf xin, qout;
         PIT_TRY(xin.ensure(p->vlen * sizeof(double)));
-        PIT_TRY(qout.ensure(p->vlen * sizeof(float)));
+        PIT_TRY(qout.ensure(p->vlen * sizeof(double)));
         PIT_CUDA(cudaMemsetAsync(xin.ptr, 0, p->vlen * sizeof(double), p->stream));
-        const std::string key = "heat2d_fp32_tile|n" + std::to_string(p->nx) + "|slices" +
-                                std::to_string((long long)p->N * p->batch) + "|m" +
-                                std::to_string(p->fine_steps);
+        const std::string shape = "|n" + std::to_string(p->nx) + "|slices" +
+                                  std::to_string((long long)p->N * p->batch) + "|m" +
+                                  std::to_string(p->fine_steps);
         int choice = 0;
-        const pit_status st = autotune(
-            key, 2,
+        pit_status st = autotune(
+            "heat2d_fp32_variant" + shape, 3,
             [&](int c) {
-                p->tile_rx = c == 0 ? 4 : 8;
+                p->fine_var32 = c;
                 return heat2d_fine_f32out(p, xin.as<double>(), qout.as<float>(), nullptr, p->stream);
             },
-            p->stream, &choice);
-        p->tile_rx = choice == 0 ? 4 : 8;
+            p->stream, &choice, p->nx >= 64 ? 1 : 0);
+        p->fine_var32 = choice;
+        if (st == PIT_OK) {
+            st = autotune(
+                "heat2d_ff_variant" + shape, 2,
+                [&](int c) {
+                    p->fine_var_ff = c == 0 ? 0 : 2;
+                    Heat2dArgs a = make_args(p, xin.as<double>(), qout.as<double>(), FINE_APPLY, nullptr);
+                    return launch_fine<ff>(p, a, p->N, p->stream);
+                },
+                p->stream, &choice, p->nx > 64 ? 1 : 0);
+            p->fine_var_ff = choice == 0 ? 0 : 2;
+        }
         xin.release();
         qout.release();
         if (st != PIT_OK) return st;
+    }
+    // PIT_HEAT2D_VARIANTS="<fp32>,<ff>" overrides the choices (0..2 each)
+    if (const char *ov = getenv("PIT_HEAT2D_VARIANTS")) {
+        int v32 = -1, vff = -1;
+        if (sscanf(ov, "%d,%d", &v32, &vff) == 2 && v32 >= 0 && v32 <= 2 && (vff == 0 || vff == 2)) {
+            p->fine_var32 = v32;
+            p->fine_var_ff = vff;
+        }
     }
     return PIT_OK;
 }

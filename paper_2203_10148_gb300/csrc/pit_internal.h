@@ -180,7 +180,10 @@ struct Problem {
     DevBuf partials, states, flags_host_mirror;
     DevBuf fine_tmp;              // serial / misc scratch
     DevBuf q32;                   // FP32 block-operator rows of the mixed G^{-1}F
-    int tile_rx = 4;              // heat2d FP32 thread-tile width (autotuned)
+    // heat2d fine-kernel variant for n <= 128 (autotuned for FP32 and
+    // float-float): 0 one CTA of 4-column tiles, 1 one CTA of 8-column tiles
+    // (FP32 only), 2 a cluster of CTAs with 8 x 4 tiles
+    int fine_var32 = 0, fine_var_ff = 0;
     ReduceLayout rl{};
     OpTimer timer;
     IterGraph igraph[2];          // [0]: FP64 iterations, [1]: mixed (FP32 fine) iterations
@@ -243,7 +246,8 @@ pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, in
 // Autotuner (tune.cu): index of the fastest of ncand variants run(c), timed
 // with CUDA events on stream s; cached per key, device SM count and process.
 pit_status autotune(const std::string &key, int ncand, const std::function<pit_status(int)> &run,
-                    cudaStream_t s, int *choice);
+                    cudaStream_t s, int *choice, int fallback = 0);
+extern thread_local bool tl_tune_fallback;
 
 // ------------------------------------------------------------ Krylov API
 // pit_problem_create with an optional caller stream (not owned; nullptr: a

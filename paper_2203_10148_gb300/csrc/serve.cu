@@ -98,7 +98,7 @@ size_t serve_footprint(const pit_problem_desc *d) {
         const size_t ends = (size_t)d->batch * ((nblk + 15) / 16) * nn * 8;
         b += 4 * vlen + 16 * vlen + ends;                    // FP32 fine output, sweep modes
         b += 24 * nn;                                        // sine basis, mode factors
-        b = std::max(b, 12 * vlen + 24 * nn + 4096);         // set-up (tile autotuning)
+        b = std::max(b, 16 * vlen + 24 * nn + 4096);         // set-up (variant autotuning)
     } else {
         b += 48 * M;                                         // Thomas factors
     }
@@ -189,6 +189,7 @@ struct pit_server_s {
     void worker(Slot *slot) {
         cudaSetDevice(device);
         tl_alloc = &slot->ctx;
+        tl_tune_fallback = true;   // no timing runs per request shape
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
             Request *r = nullptr;

@@ -2,7 +2,9 @@
 // timing each on the problem's own shapes with CUDA events, once per
 // (kernel, shape, device) key.  Choices are cached for the process and,
 // when the environment variable PIT_AUTOTUNE_CACHE names a file, persisted
-// there as "key choice" lines.  PIT_AUTOTUNE=0 disables timing (variant 0).
+// there as "key choice" lines.  PIT_AUTOTUNE=0, or a thread that set
+// tl_tune_fallback (serving workers, whose requests rarely share a shape),
+// takes the caller's fallback variant for shapes not yet tuned.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -50,8 +52,11 @@ void append_file_locked(const std::string &key, int choice) {
 
 }  // namespace
 
+thread_local bool tl_tune_fallback = false;
+
 pit_status autotune(const std::string &key_base, int ncand,
-                    const std::function<pit_status(int)> &run, cudaStream_t s, int *choice) {
+                    const std::function<pit_status(int)> &run, cudaStream_t s, int *choice,
+                    int fallback) {
     int dev = 0, sms = 0;
     PIT_CUDA(cudaGetDevice(&dev));
     PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -66,8 +71,8 @@ pit_status autotune(const std::string &key_base, int ncand,
         }
     }
     const char *off = getenv("PIT_AUTOTUNE");
-    if (off && strcmp(off, "0") == 0) {
-        *choice = 0;
+    if ((off && strcmp(off, "0") == 0) || tl_tune_fallback) {
+        *choice = fallback;
         return PIT_OK;
     }
     cudaEvent_t e0, e1;

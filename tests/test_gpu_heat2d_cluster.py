@@ -126,3 +126,27 @@ def test_cluster_served_equals_solo():
         with pit.Problem(w) as p:
             Xs, _ = p.bicgstab_solve(**opts)
         assert np.array_equal(X, Xs), w.name
+
+
+@pytest.mark.parametrize("variants", ["0,0", "1,0", "2,2"])
+@pytest.mark.parametrize("case", [dict(n=128, N=3, fine_steps=3), dict(n=100, N=2, fine_steps=4, batch=2),
+                                  dict(n=37, N=3, fine_steps=4)])
+def test_fine_variants_small_grids(variants, case, monkeypatch):
+    """Every fine-kernel variant for n <= 128 (one CTA of 4- or 8-column tiles,
+    a cluster of 8 x 4 tiles) matches the oracle and the others bit for bit."""
+    pit = _pit()
+    monkeypatch.setenv("PIT_HEAT2D_VARIANTS", variants)
+    w = inputs.heat2d(**case)
+    X = _rand_block(w, 34)
+    with pit.Problem(w, "mixed") as p:
+        g32 = p.apply("F", X, precision="mixed")
+        gff = p.apply("F", X, precision="ff")
+    ref = _oracle_apply(w, "F", X)
+    assert _rel(g32, ref) < 2e-5
+    assert _rel(gff, ref) < 1e-11 or w.nu * (w.T / w.N / w.fine[1]) * 8 * (w.nx + 1) ** 2 >= 2.78
+    monkeypatch.setenv("PIT_HEAT2D_VARIANTS", "0,0")
+    with pit.Problem(w, "mixed") as p:
+        b32 = p.apply("F", X, precision="mixed")
+        bff = p.apply("F", X, precision="ff")
+    assert np.array_equal(g32, b32)
+    assert np.array_equal(gff, bff)
