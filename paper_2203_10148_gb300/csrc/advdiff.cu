@@ -19,14 +19,16 @@
 //
 // Coarse sweep (eq. (7), right): G is one implicit-Euler step,
 // (I - dT L) w = b.  L has variable coefficients and is not symmetric, so no
-// transform diagonalises it; G is applied as a fixed linear operator: K
-// damped-Jacobi iterations w <- w + (2/3) D^{-1} (b - (I - dT L) w) started
-// from w = b (the IE step is the identity plus O(dT) on smooth modes, and
-// damped Jacobi removes the oscillatory part).  Any fixed linear
-// preconditioner leaves the solution of eq. (4) unchanged; only the
-// iteration count depends on it.  The sweep runs in one cooperative launch:
-// each CTA owns a band of rows, and exchanges its edge rows with the two
-// neighbouring bands through global memory with per-CTA progress flags
+// transform diagonalises it; G is applied as a fixed linear operator: K = 8
+// steps of the Chebyshev semi-iteration on the Jacobi-scaled system
+// D^{-1} (I - dT L) w = D^{-1} b, started from w = b, for the eigenvalue
+// interval [1 - rho, 1 + rho] with rho = max_p (D_p - 1) / D_p (the
+// Gershgorin bound of the scaled system).  The coefficients depend on the
+// problem only, so G is a fixed polynomial in D^{-1}(I - dT L): any fixed
+// linear preconditioner leaves the solution of eq. (4) unchanged, and only
+// the iteration count depends on it.  The sweep runs in one cooperative
+// launch: each CTA owns a band of rows, and exchanges its edge rows with the
+// two neighbouring bands through global memory with per-CTA progress flags
 // (bounded waits).
 #include <cooperative_groups.h>
 #include <math.h>
