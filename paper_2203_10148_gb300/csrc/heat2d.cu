@@ -697,7 +697,7 @@ pit_status heat2d_setup(Problem *p) {
                 p->fine_var32 = c;
                 return heat2d_fine_f32out(p, xin.as<double>(), qout.as<float>(), nullptr, p->stream);
             },
-            p->stream, &choice, p->nx >= 64 ? 1 : 0);
+            p->stream, &choice, p->nx > 112 ? 1 : 0);
         p->fine_var32 = choice;
         if (st == PIT_OK) {
             st = autotune(
@@ -707,7 +707,7 @@ pit_status heat2d_setup(Problem *p) {
                     Heat2dArgs a = make_args(p, xin.as<double>(), qout.as<double>(), FINE_APPLY, nullptr);
                     return launch_fine<ff>(p, a, p->N, p->stream);
                 },
-                p->stream, &choice, p->nx > 64 ? 1 : 0);
+                p->stream, &choice, 0);
             p->fine_var_ff = choice == 0 ? 0 : 2;
         }
         xin.release();

@@ -181,8 +181,8 @@ struct Problem {
     DevBuf fine_tmp;              // serial / misc scratch
     DevBuf q32;                   // FP32 block-operator rows of the mixed G^{-1}F
     // heat2d fine-kernel variant for n <= 128 (autotuned for FP32 and
-    // float-float): 0 one CTA of 4-column tiles, 1 one CTA of 8-column tiles
-    // (FP32 only), 2 a cluster of CTAs with 8 x 4 tiles
+    // float-float): 0 one CTA of 4-column tiles, 1 one CTA of 8-column
+    // tiles (FP32 only), 2 a cluster of CTAs with 8 x 4 tiles
     int fine_var32 = 0, fine_var_ff = 0;
     ReduceLayout rl{};
     OpTimer timer;
