@@ -29,6 +29,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -425,6 +426,118 @@ __global__ void __launch_bounds__(PT) k_block_xS_T(const Tin *__restrict__ A, To
     }
 }
 
+// Persistent form of the FP32 transform for n <= 128, n % 4 == 0 (the
+// inner-solve sweeps, whose inputs are FP32): out_b = scale * S A_b^T, i.e.
+// out_b[k][j] = scale * sum_i S[i][k] A_b[j][i], the same sums in the same
+// order as k_block_xS_T (so the same results).  Each CTA stages S once and
+// walks blocks b = blockIdx.x, blockIdx.x + gridDim.x, ...; the next block
+// streams into the second buffer (cp.async, 16-byte chunks) while the
+// current one is multiplied.  Both operands stay in their natural row-major
+// layout: per i-quad a thread reads A_b[j][i..i+3] for its 8 rows j and
+// S[i..i+3][k..] for its 8 columns k, 16 16-byte shared loads per 256 FMAs.
+constexpr int XP_LD = PN + 4;   // padded row (528 bytes, keeps 16-byte alignment)
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// rows j < n of an n x n FP32 block into a [PN][XP_LD] buffer
+__device__ __forceinline__ void stage_rows(float *dst, const float *src, int n) {
+    const int q4 = n >> 2;
+    const int chunks = n * q4;
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+        const int r = c / q4, c4 = c - r * q4;
+        cp_async16(dst + (size_t)r * XP_LD + 4 * c4, src + (size_t)r * n + 4 * c4);
+    }
+}
+
+template <class Tout>
+__global__ void __launch_bounds__(PT, 1)
+    k_xform_persist(const float *__restrict__ A, Tout *__restrict__ out, const float *__restrict__ S,
+                    int n, int nblk, int total, double scale, const MemberState *st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Ss = reinterpret_cast<float *>(smem_raw);     // S[i][k], PN x XP_LD
+    float *As0 = Ss + (size_t)PN * XP_LD;                 // A_b[j][i], two buffers
+    const size_t nn = (size_t)n * n;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int ja = 4 * ty, jb = 64 + 4 * ty, ka = 4 * tx, kb = 64 + 4 * tx;
+    int blk = blockIdx.x;
+    if (blk >= total) return;
+    stage_rows(Ss, S, n);
+    stage_rows(As0, A + (size_t)blk * nn, n);
+    cp_async_commit();
+    const float sc = (float)scale;
+    int buf = 0;
+    for (; blk < total; blk += gridDim.x) {
+        const int next = blk + gridDim.x;
+        float *As = As0 + (size_t)buf * PN * XP_LD;
+        if (next < total) {
+            stage_rows(As0 + (size_t)(buf ^ 1) * PN * XP_LD, A + (size_t)next * nn, n);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (runs(st, blk / nblk)) {
+            float acc[8][8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+            for (int i = 0; i < n; i += 4) {
+                float4 a[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int j = (r < 4) ? ja + r : jb + r - 4;
+                    a[r] = *reinterpret_cast<const float4 *>(As + (size_t)j * XP_LD + i);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 s0 = *reinterpret_cast<const float4 *>(Ss + (size_t)(i + q) * XP_LD + ka);
+                    const float4 s1 = *reinterpret_cast<const float4 *>(Ss + (size_t)(i + q) * XP_LD + kb);
+                    const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const float av = q == 0 ? a[r].x : q == 1 ? a[r].y : q == 2 ? a[r].z : a[r].w;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av, sv[c], acc[r][c]);
+                    }
+                }
+            }
+            Tout *ob = out + (size_t)blk * nn;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int k = (c < 4) ? ka + c : kb + c - 4;
+                if (k >= n) continue;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j0 = h == 0 ? ja : jb;
+                    if (j0 >= n) continue;   // n % 4 == 0: a group of 4 rows is all in or all out
+                    Tout v[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) v[r] = cvt<Tout>(sc * acc[h * 4 + r][c]);
+                    if constexpr (sizeof(Tout) == 4) {
+                        *reinterpret_cast<float4 *>(ob + (size_t)k * n + j0) =
+                            make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+                    } else {
+                        reinterpret_cast<double2 *>(ob + (size_t)k * n + j0)[0] = make_double2(v[0], v[1]);
+                        reinterpret_cast<double2 *>(ob + (size_t)k * n + j0)[1] = make_double2(v[2], v[3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the buffer is refilled two blocks later
+        buf ^= 1;
+    }
+}
+
 // Chunked scan of zhat_n = qhat_n + g zhat_{n-1} over the N+1 blocks of each
 // member, mode by mode, with an FP64 running value.
 // pass 1: chunk-local recurrences from zero -> ends[member][chunk][mode]
@@ -592,6 +705,21 @@ template <class Tin, class T, class Tout>
 pit_status launch_xS(Problem *p, const Tin *A, Tout *out, const T *S, double scale,
                      const MemberState *st, cudaStream_t s) {
     const int n = p->nx;
+    if constexpr (std::is_same<Tin, float>::value && std::is_same<T, float>::value) {
+        if (n <= PN && n % 4 == 0) {
+            const size_t sm = (size_t)3 * PN * XP_LD * sizeof(float);
+            PIT_CUDA(cudaFuncSetAttribute(k_xform_persist<Tout>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            const int total = (p->N + 1) * p->batch;
+            int dev = 0, sms = 0;
+            PIT_CUDA(cudaGetDevice(&dev));
+            PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            const int grid = std::min(total, sms);
+            k_xform_persist<Tout><<<grid, PT, sm, s>>>(A, out, S, n, p->N + 1, total, scale, st);
+            PIT_LAUNCH_CHECK();
+            return PIT_OK;
+        }
+    }
     const size_t sm = (size_t)PN * PLD * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
     PIT_CUDA(cudaFuncSetAttribute(k_block_xS_T<Tin, T, Tout>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
