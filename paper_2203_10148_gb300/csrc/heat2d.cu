@@ -219,6 +219,31 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
                 }
                 w_in = A::sel(west_zero, A::zero(), w_in);
                 e_in = A::sel(east_zero, A::zero(), e_in);
+                if constexpr (std::is_same<V, ff>::value) {
+                    // float-float, two columns per packed instruction
+                    const float2 cch = make_float2(cc.hi, cc.hi), ccl = make_float2(cc.lo, cc.lo);
+#pragma unroll
+                    for (int q = 0; q < RX; q += 2) {
+                        const V s0 = (r < RY - 1) ? v[r + 1][q] : srow[q];
+                        const V s1 = (r < RY - 1) ? v[r + 1][q + 1] : srow[q + 1];
+                        const V w0 = (q > 0) ? cur[q - 1] : w_in;
+                        const V e1 = (q + 2 < RX) ? cur[q + 2] : e_in;
+                        const V u0 = us[(size_t)(r * RX + q) * nthr + tid];
+                        const V u1 = us[(size_t)(r * RX + q + 1) * nthr + tid];
+                        const ff2 w = ff_stage2(
+                            ff2{make_float2(prev[q].hi, prev[q + 1].hi), make_float2(prev[q].lo, prev[q + 1].lo)},
+                            ff2{make_float2(s0.hi, s1.hi), make_float2(s0.lo, s1.lo)},
+                            ff2{make_float2(w0.hi, cur[q].hi), make_float2(w0.lo, cur[q].lo)},
+                            ff2{make_float2(cur[q + 1].hi, e1.hi), make_float2(cur[q + 1].lo, e1.lo)},
+                            ff2{make_float2(cur[q].hi, cur[q + 1].hi), make_float2(cur[q].lo, cur[q + 1].lo)},
+                            ff2{make_float2(u0.hi, u1.hi), make_float2(u0.lo, u1.lo)}, cch, ccl);
+                        v[r][q] = ff{w.hi.x, w.lo.x};
+                        v[r][q + 1] = ff{w.hi.y, w.lo.y};
+                    }
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) prev[c] = cur[c];
+                    continue;
+                }
 #pragma unroll
                 for (int c = 0; c < RX; ++c) {
                     const V vn = prev[c];

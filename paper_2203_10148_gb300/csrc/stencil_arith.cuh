@@ -142,6 +142,53 @@ struct Arith<double> {
     }
 };
 
+// ----------------------------------------------------- packed float-float
+// Two points per instruction: the same operations as Arith<ff>::stage, each
+// on an f32x2 pair (__fadd2_rn, __fmul2_rn, __ffma2_rn round each lane to
+// nearest like their scalar forms; a - b is the exact-product FMA
+// b * (-1) + a), so a packed stage gives the scalar stage's results bit for
+// bit while issuing half the FP32 instructions.
+struct ff2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = f2_sub(s, a);
+    e = __fadd2_rn(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+}
+
+// w = u + cc (vn + vs + vw + ve - 4 vc) for two points, cc = (cch, ccl)
+__device__ __forceinline__ ff2 ff_stage2(const ff2 &vn, const ff2 &vs, const ff2 &vw,
+                                         const ff2 &ve, const ff2 &vc, const ff2 &u,
+                                         float2 cch, float2 ccl) {
+    const float2 m4 = make_float2(-4.f, -4.f);
+    float2 ah, al, bh, bl, ch, cl, dh, dl;
+    two_sum2(vn.hi, vs.hi, ah, al);
+    two_sum2(vw.hi, ve.hi, bh, bl);
+    two_sum2(ah, bh, ch, cl);
+    two_sum2(ch, __fmul2_rn(m4, vc.hi), dh, dl);
+    const float2 lo = __ffma2_rn(
+        m4, vc.lo,
+        __fadd2_rn(__fadd2_rn(__fadd2_rn(al, bl), __fadd2_rn(cl, dl)),
+                   __fadd2_rn(__fadd2_rn(vn.lo, vs.lo), __fadd2_rn(vw.lo, ve.lo))));
+    const float2 p = __fmul2_rn(cch, dh);
+    float2 e = __ffma2_rn(cch, dh, make_float2(-p.x, -p.y));
+    e = __ffma2_rn(cch, lo, e);
+    e = __ffma2_rn(ccl, dh, e);
+    float2 sh, sl;
+    two_sum2(u.hi, p, sh, sl);
+    const float2 t = __fadd2_rn(sl, __fadd2_rn(u.lo, e));
+    ff2 w;
+    w.hi = __fadd2_rn(sh, t);
+    w.lo = f2_sub(t, f2_sub(w.hi, sh));
+    return w;
+}
+
 template <>
 struct Arith<ff> {
     static constexpr bool kUInSmem = true;
