@@ -46,7 +46,8 @@ from paper_2203_10148_gb300.replicas import (dist_env, max_over_ranks, replica_s
 GOLDEN_SOLVE = os.path.join(ROOT, "tests", "golden", "oracle_solve_heat2d_128_N512.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FINE_SRC = os.path.join(ROOT, "paper_2203_10148_gb300", "csrc", "heat2d.cu")
+FINE_SRCS = [os.path.join(ROOT, "paper_2203_10148_gb300", "csrc", f)
+             for f in ("heat2d.cu", "stencil_arith.cuh")]
 
 FLOP_PER_POINT_STEP = 28       # RK4 Horner: 4 stages x (3 add + 2 FMA) = 4 x 7 flop
 # pipe operations per point and fine step (FADD, FMUL, FFMA count one each):
@@ -57,10 +58,16 @@ OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 192, "fine_fp64": 20}
 # periodic advection-diffusion: 4 stages x 14 (5 for the Laplacian, 2 x 3 for the
 # upwind differences, 2 for the advection sum, 1 to combine)
 ADV_OPS_PER_POINT_STEP = 56
+# float-float advection-diffusion stage: 33 (Laplacian sum) + 16 (upwind
+# differences) + 12 (three products with error terms) + 16 (their sum) + 15
+# (u + cc L) = 92 FP32 operations, 4 stages
+ADV_FF_OPS_PER_POINT_STEP = 368
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2          # 1.25 TFLOP/s nominal FP64 = 2 FMA/clk/SM at 2.07 GHz x 152 SMs
 KERNEL_NAMES = {"fine_fp32": "k_heat2d_fine<float>", "fine_ff": "k_heat2d_fine<ff>",
                 "fine_fp64": "k_heat2d_fine<double>"}
+ADV_KERNEL_NAMES = {"fine_fp32": "k_advdiff_fine<float>", "fine_ff": "k_advdiff_fine<ff>",
+                    "fine_fp64": "k_advdiff_fine<double>"}
 
 
 def parse():
@@ -118,17 +125,21 @@ def load_peaks():
         return None
 
 
-def src_hash(path):
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+def src_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+def traffic_for(kernel, units):
+    """DRAM bytes per launch of `units` point-slices, from a committed ncu
+    capture (scaled by units), if the kernel sources are unchanged since."""
     try:
         t = json.load(open(TRAFFIC))
         e = t.get(kernel)
-        if e and e.get("source_sha") == src_hash(FINE_SRC):
-            return e
+        if e and e.get("source_sha") == src_hash(FINE_SRCS):
+            return e["dram_bytes"] * units / e["units"]
     except Exception:
         pass
     return None
@@ -283,15 +294,21 @@ def roofline(w, timing, peaks, nsm):
     point_steps = w.batch * w.N * w.fine[1] * w.M
     lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
     peak = lanes * nsm * sm_max * 1e6 / 1e12
-    ops = ADV_OPS_PER_POINT_STEP if w.kind == "advdiff2d" else OPS_PER_POINT_STEP[dom]
+    if w.kind == "advdiff2d":
+        ops = ADV_FF_OPS_PER_POINT_STEP if dom == "fine_ff" else ADV_OPS_PER_POINT_STEP
+    else:
+        ops = OPS_PER_POINT_STEP[dom]
     achieved = point_steps * ops / (avg_ms / 1e3) / 1e12
-    kname = KERNEL_NAMES[dom] if w.kind == "heat2d" else "k_advdiff_fine<%s>" % dom
-    tr = traffic_for(kname)
+    kname = KERNEL_NAMES[dom] if w.kind == "heat2d" else ADV_KERNEL_NAMES[dom]
+    units = w.batch * w.N * w.M                     # point-slices per launch
+    tr = traffic_for(kname, units) if w.kind == "heat2d" else None
+    # algorithmic bytes: x_{n-1} and x_n read (FP64), the block-operator row
+    # written (FP32 for the inner solves, FP64 for residuals)
+    alg_bytes = units * (8 + 8 + (4 if dom == "fine_fp32" else 8))
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "Tops/s (%s pipe lane-ops)" % ("FP64" if dom == "fine_fp64" else "FP32"),
             "frac": achieved / peak,
-            "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "algorithmic_bytes": 2 * 8 * point_steps // (w.fine[1]),
+            "traffic": tr, "algorithmic_bytes": alg_bytes,
             "launch_ms": avg_ms, "launches": calls,
             "flop_rate_tflops": point_steps * FLOP_PER_POINT_STEP / (avg_ms / 1e3) / 1e12,
             "peak_source": f"derived: {lanes} lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz (max SM clock)"}
@@ -331,7 +348,7 @@ def run_ours(args):
     X = torch.zeros(shape, dtype=torch.float64, device=dev)
     solve_kw = dict(tol=args.tol, tol_mode="rhs", max_iter=200, refine_max=8,
                     inner_tol=args.inner_tol,
-                    residual_precision="ff" if w.kind == "heat2d" else "fp64")
+                    residual_precision="fp64" if w.kind == "dense" else "ff")
 
     def one(step):
         prob.set_y0(y0s[step])
@@ -392,7 +409,8 @@ def run_ours(args):
                 "config": {"workload": w.name, "batch_per_gpu": w.batch, "grid": [w.nx, w.ny],
                            "N": w.N, "fine": list(w.fine), "coarse": list(w.coarse),
                            "precision": "mixed", "tol": args.tol, "tol_mode": "rhs",
-                           "inner_tol": args.inner_tol, "true_residual": "float-float",
+                           "inner_tol": args.inner_tol,
+                           "true_residual": "fp64" if w.kind == "dense" else "float-float",
                            "l2": "working set > L2 (9 Krylov vectors x %.0f MB)" % (w.batch * (w.N + 1) * w.M * 8 / 1e6),
                            "parallelism": f"replicas x{world}"},
                 "fine_slice_steps_per_s": slice_steps / (total_ms / 1e3),

@@ -77,13 +77,97 @@ __device__ __forceinline__ T adv_stage(T vn, T vs, T vw, T ve, T vc, T u, T cc, 
     return fma(cc, fma(nud, lap, -adv), u);
 }
 
+// Float-float stage (the residual arithmetic, about 48 significant bits on
+// the FP32 pipe): the sums of high parts are exact TwoSums, their errors and
+// the low parts are summed in FP32, products keep their exact FMA error
+// terms, one renormalisation at the end.  The upwind side follows the sign
+// of the coefficient's high part (the sign of the FP64 coefficient).
+template <>
+__device__ __forceinline__ ff adv_stage<ff>(ff vn, ff vs, ff vw, ff ve, ff vc, ff u, ff cc,
+                                            ff nud, ff ax, ff ay) {
+    // Laplacian sum vE + vW + vN + vS - 4 vC
+    const ff a = two_sum(ve.hi, vw.hi);
+    const ff b = two_sum(vn.hi, vs.hi);
+    const ff c = two_sum(a.hi, b.hi);
+    const ff d = two_sum(c.hi, __fmul_rn(-4.f, vc.hi));
+    const float lap_lo = fmaf(-4.f, vc.lo, ((a.lo + b.lo) + (c.lo + d.lo)) +
+                                              ((ve.lo + vw.lo) + (vn.lo + vs.lo)));
+    // upwind differences
+    const ff x1 = ax.hi >= 0.f ? vc : ve, x2 = ax.hi >= 0.f ? vw : vc;
+    const ff y1 = ay.hi >= 0.f ? vc : vs, y2 = ay.hi >= 0.f ? vn : vc;
+    const ff dx = two_sum(x1.hi, -x2.hi);
+    const float dx_lo = dx.lo + (x1.lo - x2.lo);
+    const ff dy = two_sum(y1.hi, -y2.hi);
+    const float dy_lo = dy.lo + (y1.lo - y2.lo);
+    // nud lap - ax dX - ay dY, each product with its exact error term
+    const float p1 = __fmul_rn(nud.hi, d.hi);
+    float e1 = fmaf(nud.hi, d.hi, -p1);
+    e1 = fmaf(nud.hi, lap_lo, e1);
+    e1 = fmaf(nud.lo, d.hi, e1);
+    const float p2 = __fmul_rn(ax.hi, dx.hi);
+    float e2 = fmaf(ax.hi, dx.hi, -p2);
+    e2 = fmaf(ax.hi, dx_lo, e2);
+    e2 = fmaf(ax.lo, dx.hi, e2);
+    const float p3 = __fmul_rn(ay.hi, dy.hi);
+    float e3 = fmaf(ay.hi, dy.hi, -p3);
+    e3 = fmaf(ay.hi, dy_lo, e3);
+    e3 = fmaf(ay.lo, dy.hi, e3);
+    const ff s1 = two_sum(p1, -p2);
+    const ff s2 = two_sum(s1.hi, -p3);
+    const float l_lo = (s1.lo + s2.lo) + ((e1 - e2) - e3);
+    // u + cc L
+    const float p = __fmul_rn(cc.hi, s2.hi);
+    float e = fmaf(cc.hi, s2.hi, -p);
+    e = fmaf(cc.hi, l_lo, e);
+    e = fmaf(cc.lo, s2.hi, e);
+    const ff t = two_sum(u.hi, p);
+    return fast_two_sum(t.hi, t.lo + (u.lo + e));
+}
+
+template <class T>
+__device__ __forceinline__ T adv_zero() { return T(0); }
+template <>
+__device__ __forceinline__ ff adv_zero<ff>() { return ff{0.f, 0.f}; }
+
+template <class T>
+__device__ __forceinline__ T adv_from_d(double x) { return (T)x; }
+template <>
+__device__ __forceinline__ float adv_from_d<float>(double x) { return d2f_rn(x); }
+template <>
+__device__ __forceinline__ ff adv_from_d<ff>(double x) { return ff_from_double(x); }
+
+__device__ __forceinline__ double adv_to_d(float v) { return f2d(v); }
+__device__ __forceinline__ double adv_to_d(double v) { return v; }
+__device__ __forceinline__ double adv_to_d(ff v) { return f2d(v.hi) + f2d(v.lo); }
+
+template <class T>
+__device__ __forceinline__ T shfl_idx(T v, int src) { return __shfl_sync(kFullMask, v, src); }
+template <class T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(kFullMask, v, 1); }
+template <class T>
+__device__ __forceinline__ T shfl_down1(T v) { return __shfl_down_sync(kFullMask, v, 1); }
+template <>
+__device__ __forceinline__ ff shfl_idx<ff>(ff v, int src) {
+    return ff{__shfl_sync(kFullMask, v.hi, src), __shfl_sync(kFullMask, v.lo, src)};
+}
+template <>
+__device__ __forceinline__ ff shfl_up1<ff>(ff v) {
+    return ff{__shfl_up_sync(kFullMask, v.hi, 1), __shfl_up_sync(kFullMask, v.lo, 1)};
+}
+template <>
+__device__ __forceinline__ ff shfl_down1<ff>(ff v) {
+    return ff{__shfl_down_sync(kFullMask, v.hi, 1), __shfl_down_sync(kFullMask, v.lo, 1)};
+}
+
 // One cluster of CS = n/32 CTAs per (slice, member).  Threads: TX * 8 with
 // TX = n/8 thread columns (n <= 512).  T = float (state in registers,
-// coefficients in shared memory) or double (state in shared memory,
-// coefficients read through L1).
+// coefficients in shared memory), double or float-float (state in shared
+// memory, coefficients read through L1; float-float coefficients are
+// (hi, lo) float pairs).
 template <class T, bool DBUF>
 __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
     constexpr bool FP32 = std::is_same<T, float>::value;
+    constexpr bool FF = std::is_same<T, ff>::value;
     constexpr int NB = DBUF ? 2 : 1;               // row-buffer copies
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -109,7 +193,7 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
     T *rowbuf = reinterpret_cast<T *>(smem_raw + 32);
     T *colbuf = rowbuf + (size_t)NB * 2 * AD_TY * n;
     T *tail = colbuf + NB * AD_TY * 4 * AD_RY;
-    if (tid < 4) ccs[tid] = (T)(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
+    if (tid < 4) ccs[tid] = adv_from_d<T>(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
     const size_t mb = (size_t)b * a.blen;
     const size_t nn = (size_t)n * n;
     const double *xin = a.x + mb + (size_t)(slice - 1) * nn;
@@ -120,17 +204,16 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
     T *cax = tail, *cay = tail + (size_t)AD_RY * AD_RX * nthr;   // float: coefficients
     const T *gax = reinterpret_cast<const T *>(a.ax);
     const T *gay = reinterpret_cast<const T *>(a.ay);
+    [[maybe_unused]] const float2 *gax2 = reinterpret_cast<const float2 *>(a.ax);
+    [[maybe_unused]] const float2 *gay2 = reinterpret_cast<const float2 *>(a.ay);
 #pragma unroll
     for (int r = 0; r < AD_RY; ++r)
 #pragma unroll
         for (int c = 0; c < AD_RX; ++c) {
             const size_t k = (size_t)(j0 + r) * n + (i0 + c);
             const int slot = (r * AD_RX + c) * nthr + tid;
-            T val = T(0);
-            if (active) {
-                if constexpr (FP32) val = d2f_rn(xin[k]);
-                else val = xin[k];
-            }
+            T val = adv_zero<T>();
+            if (active) val = adv_from_d<T>(xin[k]);
             v[r][c] = val;
             if constexpr (FP32) {
                 ur[FP32 ? r : 0][FP32 ? c : 0] = val;
@@ -140,7 +223,7 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
                 us[slot] = val;
             }
         }
-    const T nud = (T)a.nud;
+    const T nud = adv_from_d<T>(a.nud);
     int buf = 0;
     const int up_rank = (rank + CS - 1) % CS, down_rank = (rank + 1) % CS;
     for (int s = 0; s < a.steps; ++s) {
@@ -184,12 +267,12 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
                 if (row_in_warp) {
                     // the thread row lies in one warp: lanes tx-1 / tx+1 modulo TX
                     const int seg = (lane / TX) * TX;
-                    w_in = __shfl_sync(kFullMask, v[r][AD_RX - 1], seg + (tx + TX - 1) % TX);
-                    e_in = __shfl_sync(kFullMask, v[r][0], seg + (tx + 1) % TX);
+                    w_in = shfl_idx(v[r][AD_RX - 1], seg + (tx + TX - 1) % TX);
+                    e_in = shfl_idx(v[r][0], seg + (tx + 1) % TX);
                 } else {
                     // two warps per thread row: the edge lanes read the other warp's column
-                    w_in = __shfl_up_sync(kFullMask, v[r][AD_RX - 1], 1);
-                    e_in = __shfl_down_sync(kFullMask, v[r][0], 1);
+                    w_in = shfl_up1(v[r][AD_RX - 1]);
+                    e_in = shfl_down1(v[r][0]);
                     const int other = 1 - warp_in_row;
                     if (lane == 0)
                         w_in = colbuf[((size_t)(buf * AD_TY + ty) * 4 + 2 + other) * AD_RY + r];
@@ -220,6 +303,12 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
                         u = ur[FP32 ? r : 0][FP32 ? c : 0];
                         ax = cax[slot];
                         ay = cay[slot];
+                    } else if constexpr (FF) {
+                        u = us[slot];
+                        const size_t k = (size_t)(j0 + r) * n + (i0 + c);
+                        const float2 cx = __ldg(gax2 + k), cy = __ldg(gay2 + k);
+                        ax = ff{cx.x, cx.y};
+                        ay = ff{cy.x, cy.y};
                     } else {
                         u = us[slot];
                         const size_t k = (size_t)(j0 + r) * n + (i0 + c);
@@ -255,9 +344,7 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
                     continue;
                 }
             }
-            double f;
-            if constexpr (FP32) f = f2d(v[r][c]);
-            else f = v[r][c];
+            const double f = adv_to_d(v[r][c]);
             double *yo = a.y + mb + (size_t)slice * nn;
             if (a.mode == FINE_APPLY) yo[k] = xn[k] - f;
             else if (a.mode == FINE_RESIDUAL) yo[k] = f - xn[k];
@@ -279,6 +366,15 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
     }
 }
 
+// x = hi + lo with hi = RN32(x), lo = RN32(x - hi)
+__global__ void k_split_ff(const double *__restrict__ x, float2 *__restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float hi = __double2float_rn(x[i]);
+        out[i] = make_float2(hi, __double2float_rn(x[i] - (double)hi));
+    }
+}
+
 template <class T, bool DBUF>
 size_t adv_smem(int n) {
     const size_t nthr = (size_t)n;   // TX * 8 = n
@@ -289,15 +385,17 @@ size_t adv_smem(int n) {
     return s;
 }
 
+// coefficient arrays: prec = PIT_MIXED (float), PIT_FP64 (double) or PIT_FF
+// ((hi, lo) float pairs)
 AdvArgs adv_args(Problem *p, const double *x, double *y, float *y32, int mode,
-                 const MemberState *st, bool fp32) {
+                 const MemberState *st, int prec) {
     AdvArgs a{};
     a.x = x;
     a.y = y;
     a.y32 = y32;
     a.y0 = p->y0.as<double>();
-    a.ax = fp32 ? (const void *)p->vx32.ptr : (const void *)p->vx64.ptr;
-    a.ay = fp32 ? (const void *)p->vy32.ptr : (const void *)p->vy64.ptr;
+    a.ax = prec == PIT_MIXED ? p->vx32.ptr : prec == PIT_FF ? p->vxff.ptr : p->vx64.ptr;
+    a.ay = prec == PIT_MIXED ? p->vy32.ptr : prec == PIT_FF ? p->vyff.ptr : p->vy64.ptr;
     a.n = p->nx;
     a.N = p->N;
     a.batch = p->batch;
@@ -610,6 +708,13 @@ pit_status advdiff_setup(Problem *p) {
     k_scale_coeff<<<256, 256, 0, p->stream>>>(p->vy64.as<double>(), p->vy64.as<double>(),
                                               p->vy32.as<float>(), (double)n, M);
     PIT_LAUNCH_CHECK();
+    // float-float copies (hi, lo) for the residual arithmetic
+    PIT_TRY(p->vxff.ensure(M * sizeof(float2)));
+    PIT_TRY(p->vyff.ensure(M * sizeof(float2)));
+    k_split_ff<<<256, 256, 0, p->stream>>>(p->vx64.as<double>(), p->vxff.as<float2>(), M);
+    PIT_LAUNCH_CHECK();
+    k_split_ff<<<256, 256, 0, p->stream>>>(p->vy64.as<double>(), p->vyff.as<float2>(), M);
+    PIT_LAUNCH_CHECK();
     // Chebyshev coefficients on the Jacobi-scaled IE system: the spectrum of
     // D^{-1} A lies in the Gershgorin disc |z - 1| <= rho, rho = max (D - 1)/D,
     // taken as the real interval [1 - rho, 1 + rho]
@@ -664,22 +769,21 @@ pit_status advdiff_setup(Problem *p) {
 
 pit_status advdiff_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                            const MemberState *st, cudaStream_t s) {
-    if (prec == PIT_MIXED) return launch_adv_fine<float>(p, adv_args(p, x, y, nullptr, mode, st, true), p->N, s);
-    return launch_adv_fine<double>(p, adv_args(p, x, y, nullptr, mode, st, false), p->N, s);
+    const AdvArgs a = adv_args(p, x, y, nullptr, mode, st, prec);
+    if (prec == PIT_MIXED) return launch_adv_fine<float>(p, a, p->N, s);
+    if (prec == PIT_FF) return launch_adv_fine<ff>(p, a, p->N, s);
+    return launch_adv_fine<double>(p, a, p->N, s);
 }
 
 pit_status advdiff_fine_f32out(Problem *p, const double *x, float *q32, const MemberState *st,
                                cudaStream_t s) {
-    return launch_adv_fine<float>(p, adv_args(p, x, nullptr, q32, FINE_APPLY, st, true), p->N, s);
+    return launch_adv_fine<float>(p, adv_args(p, x, nullptr, q32, FINE_APPLY, st, PIT_MIXED), p->N, s);
 }
 
 pit_status advdiff_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
-    AdvArgs a;
-    if (prec == PIT_MIXED) {
-        a = adv_args(p, x, y - (size_t)p->M, nullptr, 2, nullptr, true);
-        return launch_adv_fine<float>(p, a, 1, s);
-    }
-    a = adv_args(p, x, y - (size_t)p->M, nullptr, 2, nullptr, false);
+    const AdvArgs a = adv_args(p, x, y - (size_t)p->M, nullptr, 2, nullptr, prec);
+    if (prec == PIT_MIXED) return launch_adv_fine<float>(p, a, 1, s);
+    if (prec == PIT_FF) return launch_adv_fine<ff>(p, a, 1, s);
     return launch_adv_fine<double>(p, a, 1, s);
 }
 

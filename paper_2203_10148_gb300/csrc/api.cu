@@ -186,7 +186,7 @@ static int sweep_cls(int prec) { return prec == PIT_MIXED ? PIT_TIME_SWEEP_MIXED
 // --------------------------------------------------------- operator switch
 pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                       const MemberState *st, cudaStream_t s) {
-    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D) prec = PIT_FP64;
+    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D && p->kind != PIT_OP_ADVDIFF2D) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_apply_F(p, x, y, mode, prec, st, s);
     case PIT_OP_HEAT2D: return heat2d_apply_F(p, x, y, mode, prec, st, s);
@@ -210,7 +210,7 @@ pit_status op_sweep(Problem *p, const double *q, double *z, int prec, const Memb
 }
 
 static pit_status fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
-    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D) prec = PIT_FP64;
+    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D && p->kind != PIT_OP_ADVDIFF2D) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_fine_one(p, x, y, prec, s);
     case PIT_OP_HEAT2D: return heat2d_fine_one(p, x, y, prec, s);
@@ -673,7 +673,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
     DevBuf *bufs[] = {&p->y0, &p->fine_inv64, &p->fine_cp64, &p->coarse_inv64, &p->coarse_cp64,
                       &p->fine_inv32, &p->fine_cp32, &p->coarse_inv32, &p->coarse_cp32,
                       &p->S64, &p->S32, &p->gmode, &p->hat, &p->vx64, &p->vy64, &p->vx32,
-                      &p->vy32, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
+                      &p->vy32, &p->vxff, &p->vyff, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32,

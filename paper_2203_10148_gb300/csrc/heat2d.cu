@@ -563,33 +563,76 @@ __global__ void __launch_bounds__(PT, 1)
     }
 }
 
+constexpr int REC_CHUNK = 16;   // blocks per scan chunk
+
 // Chunked scan of zhat_n = qhat_n + g zhat_{n-1} over the N+1 blocks of each
-// member, mode by mode, with an FP64 running value.
+// member, mode by mode.  Running values: FP64 for FP64 data; float-float
+// (about 48 bits, on the FP32 pipe) for FP32 data, whose FP64 alternative
+// would put one FP64 FMA and two conversions per element on the 2-lane FP64
+// pipe.  Each thread loads its chunk's 16 values before the recurrence.
+template <class T>
+struct RecVal;
+template <>
+struct RecVal<double> {
+    using V = double;
+    __device__ static V from_d(double x) { return x; }
+    __device__ static double to_d(V z) { return z; }
+    __device__ static V step(double g, double, V z, double h) { return fma(g, z, h); }
+    __device__ static V zero() { return 0.0; }
+    __device__ static double out(V z) { return z; }
+};
+template <>
+struct RecVal<float> {
+    using V = ff;
+    __device__ static V from_d(double x) { return ff_from_double(x); }
+    __device__ static double to_d(V z) { return ff_to_double(z); }
+    // z <- g z + h with g = (gh, gl) and an FP32 h
+    __device__ static V step(float gh, float gl, V z, float h) {
+        const ff p = ff_mul(ff{gh, gl}, z);
+        const ff s = two_sum(p.hi, h);
+        return fast_two_sum(s.hi, s.lo + p.lo);
+    }
+    __device__ static V zero() { return ff{0.f, 0.f}; }
+    __device__ static float out(V z) { return __fadd_rn(z.hi, z.lo); }
+};
+
 // pass 1: chunk-local recurrences from zero -> ends[member][chunk][mode]
 template <class T>
 __global__ void k_rec_local(const T *__restrict__ hat, double *__restrict__ ends,
-                            const double *__restrict__ g, int nn, int nblk, int clen,
-                            int nchunks, const MemberState *st) {
+                            const double *__restrict__ g, int nn, int nblk, int nchunks,
+                            const MemberState *st) {
+    using R = RecVal<T>;
     const int mode = blockIdx.x * blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y, member = blockIdx.z;
     if (mode >= nn || !runs(st, member)) return;
     const double gm = g[mode];
-    const int k0 = chunk * clen, k1 = min(nblk, k0 + clen);
+    const auto gv = R::from_d(gm);
+    const int k0 = chunk * REC_CHUNK;
     const T *h = hat + (size_t)member * nblk * nn + mode;
-    double z = 0.0;
-    for (int k = k0; k < k1; ++k) z = fma(gm, z, (double)h[(size_t)k * nn]);
-    ends[((size_t)member * nchunks + chunk) * nn + mode] = z;
+    T hv[REC_CHUNK];
+#pragma unroll
+    for (int t = 0; t < REC_CHUNK; ++t)
+        hv[t] = (k0 + t < nblk) ? h[(size_t)min(k0 + t, nblk - 1) * nn] : T(0);
+    auto z = R::zero();
+#pragma unroll
+    for (int t = 0; t < REC_CHUNK; ++t) {
+        if (k0 + t < nblk) {
+            if constexpr (std::is_same<T, float>::value) z = R::step(gv.hi, gv.lo, z, hv[t]);
+            else z = R::step(gm, 0.0, z, hv[t]);
+        }
+    }
+    ends[((size_t)member * nchunks + chunk) * nn + mode] = R::to_d(z);
 }
 
-// pass 2: carries into each chunk (sequential over chunks, in place)
+// pass 2: carries into each chunk (sequential over chunks, in place, FP64)
 __global__ void k_rec_carry(double *__restrict__ ends, const double *__restrict__ g, int nn,
-                            int clen, int nchunks, const MemberState *st) {
+                            int nchunks, const MemberState *st) {
     const int mode = blockIdx.x * blockDim.x + threadIdx.x;
     const int member = blockIdx.y;
     if (mode >= nn || !runs(st, member)) return;
     double gl = 1.0;
     const double gm = g[mode];
-    for (int k = 0; k < clen; ++k) gl *= gm;
+    for (int k = 0; k < REC_CHUNK; ++k) gl *= gm;
     double carry = 0.0;
     double *e = ends + (size_t)member * nchunks * nn + mode;
     for (int c = 0; c < nchunks; ++c) {
@@ -602,22 +645,31 @@ __global__ void k_rec_carry(double *__restrict__ ends, const double *__restrict_
 // pass 3: replay each chunk from its carry and write zhat
 template <class T>
 __global__ void k_rec_apply(T *__restrict__ hat, const double *__restrict__ ends,
-                            const double *__restrict__ g, int nn, int nblk, int clen,
-                            int nchunks, const MemberState *st) {
+                            const double *__restrict__ g, int nn, int nblk, int nchunks,
+                            const MemberState *st) {
+    using R = RecVal<T>;
     const int mode = blockIdx.x * blockDim.x + threadIdx.x;
     const int chunk = blockIdx.y, member = blockIdx.z;
     if (mode >= nn || !runs(st, member)) return;
     const double gm = g[mode];
-    const int k0 = chunk * clen, k1 = min(nblk, k0 + clen);
+    const auto gv = R::from_d(gm);
+    const int k0 = chunk * REC_CHUNK;
     T *h = hat + (size_t)member * nblk * nn + mode;
-    double z = ends[((size_t)member * nchunks + chunk) * nn + mode];
-    for (int k = k0; k < k1; ++k) {
-        z = fma(gm, z, (double)h[(size_t)k * nn]);
-        h[(size_t)k * nn] = (T)z;
+    T hv[REC_CHUNK];
+#pragma unroll
+    for (int t = 0; t < REC_CHUNK; ++t)
+        hv[t] = (k0 + t < nblk) ? h[(size_t)min(k0 + t, nblk - 1) * nn] : T(0);
+    auto z = R::from_d(ends[((size_t)member * nchunks + chunk) * nn + mode]);
+#pragma unroll
+    for (int t = 0; t < REC_CHUNK; ++t) {
+        if (k0 + t < nblk) {
+            if constexpr (std::is_same<T, float>::value) z = R::step(gv.hi, gv.lo, z, hv[t]);
+            else z = R::step(gm, 0.0, z, hv[t]);
+            h[(size_t)(k0 + t) * nn] = R::out(z);
+        }
     }
 }
 
-constexpr int REC_CHUNK = 16;   // blocks per scan chunk
 
 template <class V, int RX, int RY>
 size_t fine_smem(int TXp, int TYp) {
@@ -775,14 +827,12 @@ pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const Member
     // recurrence over slices, mode by mode
     const int RT = 256;
     dim3 g1((unsigned)((nn + RT - 1) / RT), nchunks, p->batch);
-    k_rec_local<T><<<g1, RT, 0, s>>>(h2, ends, p->gmode.as<double>(), (int)nn, nblk, REC_CHUNK,
-                                     nchunks, st);
+    k_rec_local<T><<<g1, RT, 0, s>>>(h2, ends, p->gmode.as<double>(), (int)nn, nblk, nchunks, st);
     PIT_LAUNCH_CHECK();
     k_rec_carry<<<dim3((unsigned)((nn + RT - 1) / RT), p->batch), RT, 0, s>>>(
-        ends, p->gmode.as<double>(), (int)nn, REC_CHUNK, nchunks, st);
+        ends, p->gmode.as<double>(), (int)nn, nchunks, st);
     PIT_LAUNCH_CHECK();
-    k_rec_apply<T><<<g1, RT, 0, s>>>(h2, ends, p->gmode.as<double>(), (int)nn, nblk, REC_CHUNK,
-                                     nchunks, st);
+    k_rec_apply<T><<<g1, RT, 0, s>>>(h2, ends, p->gmode.as<double>(), (int)nn, nblk, nchunks, st);
     PIT_LAUNCH_CHECK();
     // z = (2/(n+1))^2 S zhat S
     const double sc = 2.0 / (n + 1);

@@ -161,6 +161,7 @@ struct Problem {
 
     // advdiff2d: per-point velocities (FP64 and FP32)
     DevBuf vx64, vy64, vx32, vy32;   // after set-up: ax = vx/h, ay = vy/h
+    DevBuf vxff, vyff;            // advdiff coefficients as float-float (hi, lo) pairs
     DevBuf adv_scratch;
     int adv_K = 8;                // Chebyshev steps of the coarse IE step
     double adv_inv_theta = 1.0, adv_c1[16] = {}, adv_c2[16] = {};   // Chebyshev coefficients

@@ -79,8 +79,11 @@ def test_advdiff_fine_operator_fp64_and_fp32(case):
     with pit.Problem(w, "mixed") as p:
         got64 = p.apply("F", X, precision="fp64")
         got32 = p.apply("F", X, precision="mixed")
+        gotff = p.apply("F", X, precision="ff")
     assert _rel(got64, ref) < 1e-12
     assert _rel(got32, ref) < 2e-5
+    # float-float: about 48 significant bits per operation
+    assert _rel(gotff, ref) < 1e-11
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -105,10 +108,14 @@ def test_advdiff_solves_reach_serial_trajectory():
     with pit.Problem(w, "mixed") as p:
         X, info = p.bicgstab_solve(tol=1e-8, tol_mode="rhs", inner_tol=1e-5, residual_precision="fp64")
         lam_gpu = p.serial_fine("fp64")
-    assert i64[0]["status"] == 0 and info[0]["status"] == 0
+        Xf, infof = p.bicgstab_solve(tol=1e-8, tol_mode="rhs", inner_tol=1e-5, residual_precision="ff")
+        lam_ff = p.serial_fine("ff")
+    assert i64[0]["status"] == 0 and info[0]["status"] == 0 and infof[0]["status"] == 0
     assert np.linalg.norm(X64[0] - lam) / np.linalg.norm(lam) < 1e-9
     assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
+    assert np.linalg.norm(Xf[0] - lam) / np.linalg.norm(lam) < 1e-6
     assert _rel(lam_gpu[0], lam) < 1e-12
+    assert _rel(lam_ff[0], lam) < 1e-10
 
 
 def test_advdiff_full_size_sampled():
@@ -122,7 +129,9 @@ def test_advdiff_full_size_sampled():
     with pit.Problem(w, "mixed") as p:
         Y32 = p.apply("F", Xd, precision="mixed").cpu().numpy()[0]
         Y64 = p.apply("F", Xd, precision="fp64").cpu().numpy()[0]
+        Yff = p.apply("F", Xd, precision="ff").cpu().numpy()[0]
     rows = [1, 2, 128, 255, 256]
     ref = X[0][rows] - o.F(X[0][[r - 1 for r in rows]])
     assert _rel(Y64[rows], ref) < 1e-12
+    assert _rel(Yff[rows], ref) < 1e-11
     assert _rel(Y32[rows], ref) < 1e-4
