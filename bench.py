@@ -74,6 +74,9 @@ def parse():
     args = _parser().parse_args()
     if args.batch is None:
         args.batch = 8 if args.workload == "heat2d" else 1
+    args.N_given = args.N is not None
+    if args.N is None:
+        args.N = 512
     return args
 
 
@@ -91,7 +94,8 @@ def _parser():
                     help="heat2d: 2D heat 128^2, N = 512 (the headline); dense: M = 1024, "
                          "N = 4096; advdiff: periodic 512^2, N = 256")
     ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--N", type=int, default=512)
+    ap.add_argument("--N", type=int, default=None,
+                    help="slices (default: 512 for heat2d, 256 for advdiff)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
@@ -111,7 +115,8 @@ def workload(args, rank, step=0):
         return inputs.dense(batch=args.batch, seed=seed, tol=1e-6)
     if args.workload == "advdiff":
         seed = replica_seed(inputs.SEED_ADVDIFF2D, rank, step)
-        return inputs.advdiff2d(batch=args.batch, seed=seed, tol=1e-6)
+        return inputs.advdiff2d(batch=args.batch, seed=seed, tol=1e-6,
+                                N=args.N if args.N_given else 256)
     seed = replica_seed(inputs.SEED_HEAT2D, rank, step)
     return inputs.heat2d(n=args.n, N=args.N, batch=args.batch, seed=seed, tol=1e-6)
 

@@ -32,6 +32,7 @@
 // (bounded waits).
 #include <cooperative_groups.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <type_traits>
@@ -159,6 +160,66 @@ __device__ __forceinline__ ff shfl_down1<ff>(ff v) {
     return ff{__shfl_down_sync(kFullMask, v.hi, 1), __shfl_down_sync(kFullMask, v.lo, 1)};
 }
 
+// A thread's 8 consecutive values of a row buffer are stored as 16-byte
+// chunks in chunk-major order: chunk q of thread column tx at element
+// q * TX * CW + tx * CW (CW values per 16 bytes), so that a warp's 16-byte
+// accesses to one chunk are contiguous (no shared-memory bank conflicts).
+template <class T>
+struct RowChunks;
+template <>
+struct RowChunks<float> {
+    __device__ static void store(float *row, int tx, int TX, const float (&v)[AD_RX]) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            *reinterpret_cast<float4 *>(row + (size_t)q * TX * 4 + (size_t)tx * 4) =
+                make_float4(v[q * 4], v[q * 4 + 1], v[q * 4 + 2], v[q * 4 + 3]);
+    }
+    __device__ static void load(const float *row, int tx, int TX, float (&v)[AD_RX]) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float4 t = *reinterpret_cast<const float4 *>(row + (size_t)q * TX * 4 + (size_t)tx * 4);
+            v[q * 4] = t.x;
+            v[q * 4 + 1] = t.y;
+            v[q * 4 + 2] = t.z;
+            v[q * 4 + 3] = t.w;
+        }
+    }
+};
+template <>
+struct RowChunks<double> {
+    __device__ static void store(double *row, int tx, int TX, const double (&v)[AD_RX]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<double2 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2) =
+                make_double2(v[q * 2], v[q * 2 + 1]);
+    }
+    __device__ static void load(const double *row, int tx, int TX, double (&v)[AD_RX]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 t = *reinterpret_cast<const double2 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2);
+            v[q * 2] = t.x;
+            v[q * 2 + 1] = t.y;
+        }
+    }
+};
+template <>
+struct RowChunks<ff> {
+    __device__ static void store(ff *row, int tx, int TX, const ff (&v)[AD_RX]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<float4 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2) =
+                make_float4(v[q * 2].hi, v[q * 2].lo, v[q * 2 + 1].hi, v[q * 2 + 1].lo);
+    }
+    __device__ static void load(const ff *row, int tx, int TX, ff (&v)[AD_RX]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2);
+            v[q * 2] = ff{t.x, t.y};
+            v[q * 2 + 1] = ff{t.z, t.w};
+        }
+    }
+};
+
 // One cluster of CS = n/32 CTAs per (slice, member).  Threads: TX * 8 with
 // TX = n/8 thread columns (n <= 512).  T = float (state in registers,
 // coefficients in shared memory), double or float-float (state in shared
@@ -232,13 +293,8 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
             // single buffer: every read of the previous stage's rows is done first
             if (!DBUF) cluster.sync();
             // publish top / bottom rows and the warp-edge columns
-            T *top = rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + ty) * n + i0;
-            T *bot = rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + ty) * n + i0;
-#pragma unroll
-            for (int c = 0; c < AD_RX; ++c) {
-                top[c] = v[0][c];
-                bot[c] = v[AD_RY - 1][c];
-            }
+            RowChunks<T>::store(rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + ty) * n, tx, TX, v[0]);
+            RowChunks<T>::store(rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + ty) * n, tx, TX, v[AD_RY - 1]);
             if (lane == 0 || lane == 31) {
                 // colbuf[buf][ty][slot][r]: slot 0/1 = west column of warp 0/1,
                 // slot 2/3 = east column of warp 0/1
@@ -252,11 +308,10 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
             // CTA edge from the neighbouring CTA's shared memory (periodic)
             T prev[AD_RX];
             {
-                const T *src = (ty > 0) ? rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + (ty - 1)) * n + i0
+                const T *src = (ty > 0) ? rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + (ty - 1)) * n
                                         : cluster.map_shared_rank(rowbuf, up_rank) +
-                                              ((size_t)(buf * 2 + 1) * AD_TY + (AD_TY - 1)) * n + i0;
-#pragma unroll
-                for (int c = 0; c < AD_RX; ++c) prev[c] = src[c];
+                                              ((size_t)(buf * 2 + 1) * AD_TY + (AD_TY - 1)) * n;
+                RowChunks<T>::load(src, tx, TX, prev);
             }
             // west/east neighbours of the tile's first/last column (periodic in x)
             const int row_base = (tid / 32) * 32;   // lanes of this warp
@@ -285,11 +340,10 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
                 for (int c = 0; c < AD_RX; ++c) cur[c] = v[r][c];
                 T srow[AD_RX];
                 if (r == AD_RY - 1) {
-                    const T *srs = (ty < AD_TY - 1) ? rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + (ty + 1)) * n + i0
+                    const T *srs = (ty < AD_TY - 1) ? rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + (ty + 1)) * n
                                                     : cluster.map_shared_rank(rowbuf, down_rank) +
-                                                          ((size_t)(buf * 2 + 0) * AD_TY + 0) * n + i0;
-#pragma unroll
-                    for (int c = 0; c < AD_RX; ++c) srow[c] = srs[c];
+                                                          ((size_t)(buf * 2 + 0) * AD_TY + 0) * n;
+                    RowChunks<T>::load(srs, tx, TX, srow);
                 }
 #pragma unroll
                 for (int c = 0; c < AD_RX; ++c) {
