@@ -190,9 +190,10 @@ pit_status pit_problem_shape(pit_problem_t prob, int *M, int *N, int *batch);
  * PIT_APPLY_F (eq. (4)), PIT_APPLY_GINV (eq. (7) right, sequential in n),
  * PIT_APPLY_GINV_F (eq. (8)), PIT_APPLY_RESIDUAL (G^{-1}(B - F x)).
  * precision selects the fine arithmetic (PIT_FP64, PIT_MIXED = FP32 fine
- * stepping from FP64 inputs, or PIT_FF = float-float stepping, about 48
- * significant bits on the FP32 pipe, for PIT_OP_HEAT2D and
- * PIT_OP_ADVDIFF2D; PIT_FF means PIT_FP64 for the other kinds).  G^{-1} runs
+ * stepping from FP64 inputs, or PIT_FF = float-float arithmetic, about 48
+ * significant bits on the FP32 pipe: stepping for PIT_OP_HEAT2D and
+ * PIT_OP_ADVDIFF2D, a compensated product for PIT_OP_DENSE with M a
+ * multiple of 64; PIT_FF means PIT_FP64 otherwise).  G^{-1} runs
  * in reduced precision for PIT_MIXED (2D heat: FP32 sine transforms with
  * float-float running sums; advection-diffusion and dense: FP32) and in
  * FP64 otherwise.  x and y may not overlap.

@@ -186,7 +186,7 @@ static int sweep_cls(int prec) { return prec == PIT_MIXED ? PIT_TIME_SWEEP_MIXED
 // --------------------------------------------------------- operator switch
 pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                       const MemberState *st, cudaStream_t s) {
-    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D && p->kind != PIT_OP_ADVDIFF2D) prec = PIT_FP64;
+    if (prec == PIT_FF && p->kind == PIT_OP_HEAT1D) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_apply_F(p, x, y, mode, prec, st, s);
     case PIT_OP_HEAT2D: return heat2d_apply_F(p, x, y, mode, prec, st, s);

@@ -56,6 +56,122 @@ __global__ void k_copy_f32(const double *X, float *Y, size_t n) {
         Y[i] = d2f_rn(X[i]);
 }
 
+// x = hi + lo, hi = RN32(x), lo = RN32(x - hi): the float-float form of x
+__global__ void k_split_ff(const double *X, float *hi, float *lo, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float h = d2f_rn(X[i]);
+        hi[i] = h;
+        lo[i] = d2f_rn(X[i] - f2d(h));
+    }
+}
+
+// ------------------------------------------------ float-float product
+// C[g][c] = sum_k X[g][k] Phi[c][k] for the rows g = (member, slice < N) of
+// the block vector, with X and Phi as float-float pairs (hi, lo) and the
+// sum accumulated in the compensated form of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", 2005, Dot2) extended to two-word inputs:
+// per term p = RN(ah bh) with its exact error e (FMA), the cross terms
+// ah bl + al bh added to e, s <- TwoSum(s, p) with the rounding error of
+// the sum and e collected in a second FP32 accumulator; the result is
+// s + c in FP64.  Error about eps32 |sum| + (n eps32)^2 sum |x phi|.  The
+// arithmetic runs two columns per packed f32x2 instruction.  One 64 x 64
+// output tile per CTA of 256 threads (4 x 4 outputs each), K in steps of 16
+// staged in shared memory, transposed so a thread's 4 rows / 4 columns are
+// one 16-byte load.
+constexpr int FG_B = 64, FG_K = 16, FG_T = 256;
+
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+__global__ void __launch_bounds__(FG_T) k_gemm_ff(const float *__restrict__ Xh, const float *__restrict__ Xl,
+                                                  const float *__restrict__ Ph, const float *__restrict__ Pl,
+                                                  double *__restrict__ C, int M, int N, size_t blen,
+                                                  size_t cstride, int rows, const MemberState *st) {
+    __shared__ __align__(16) float xs_h[FG_K][FG_B], xs_l[FG_K][FG_B];
+    __shared__ __align__(16) float ps_h[FG_K][FG_B], ps_l[FG_K][FG_B];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int g0 = blockIdx.y * FG_B, c0 = blockIdx.x * FG_B;
+    // staging: each thread moves 4 values of each operand tile per K step
+    const int lr = tid >> 2, lk = (tid & 3) * 4;     // tile row 0..63, k 0..12 step 4
+    const int gl = g0 + lr;
+    const bool grow_ok = gl < rows;
+    const int gmem = grow_ok ? gl / N : 0, gsl = grow_ok ? gl % N : 0;
+    const bool live = grow_ok && (st == nullptr || (st[gmem].active && !st[gmem].skip && !st[gmem].half));
+    const size_t xrow = (size_t)gmem * blen + (size_t)gsl * M;
+    const size_t prow = (size_t)(c0 + lr) * M;
+    float2 s2[4][2], c2[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            s2[i][j] = make_float2(0.f, 0.f);
+            c2[i][j] = make_float2(0.f, 0.f);
+        }
+    for (int k0 = 0; k0 < M; k0 += FG_K) {
+        {
+            float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh;
+            if (live) {
+                xh = *reinterpret_cast<const float4 *>(Xh + xrow + k0 + lk);
+                xl = *reinterpret_cast<const float4 *>(Xl + xrow + k0 + lk);
+            }
+            const float4 ph = *reinterpret_cast<const float4 *>(Ph + prow + k0 + lk);
+            const float4 pl = *reinterpret_cast<const float4 *>(Pl + prow + k0 + lk);
+            xs_h[lk][lr] = xh.x; xs_h[lk + 1][lr] = xh.y; xs_h[lk + 2][lr] = xh.z; xs_h[lk + 3][lr] = xh.w;
+            xs_l[lk][lr] = xl.x; xs_l[lk + 1][lr] = xl.y; xs_l[lk + 2][lr] = xl.z; xs_l[lk + 3][lr] = xl.w;
+            ps_h[lk][lr] = ph.x; ps_h[lk + 1][lr] = ph.y; ps_h[lk + 2][lr] = ph.z; ps_h[lk + 3][lr] = ph.w;
+            ps_l[lk][lr] = pl.x; ps_l[lk + 1][lr] = pl.y; ps_l[lk + 2][lr] = pl.z; ps_l[lk + 3][lr] = pl.w;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < FG_K; ++k) {
+            const float4 ah = *reinterpret_cast<const float4 *>(&xs_h[k][ty * 4]);
+            const float4 al = *reinterpret_cast<const float4 *>(&xs_l[k][ty * 4]);
+            const float4 bh = *reinterpret_cast<const float4 *>(&ps_h[k][tx * 4]);
+            const float4 bl = *reinterpret_cast<const float4 *>(&ps_l[k][tx * 4]);
+            const float2 bh2[2] = {make_float2(bh.x, bh.y), make_float2(bh.z, bh.w)};
+            const float2 bl2[2] = {make_float2(bl.x, bl.y), make_float2(bl.z, bl.w)};
+            const float ahv[4] = {ah.x, ah.y, ah.z, ah.w};
+            const float alv[4] = {al.x, al.y, al.z, al.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 a2 = make_float2(ahv[i], ahv[i]);
+                const float2 na2 = make_float2(-ahv[i], -ahv[i]);
+                const float2 l2 = make_float2(alv[i], alv[i]);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float2 p = __fmul2_rn(a2, bh2[j]);
+                    const float2 ne = __ffma2_rn(na2, bh2[j], p);          // -(exact error of p)
+                    const float2 s = __fadd2_rn(s2[i][j], p);               // TwoSum(s, p)
+                    const float2 bb = f2sub(s, s2[i][j]);
+                    const float2 sig = __fadd2_rn(f2sub(s2[i][j], f2sub(s, bb)), f2sub(p, bb));
+                    s2[i][j] = s;
+                    float2 c = __fadd2_rn(c2[i][j], sig);
+                    c = f2sub(c, ne);
+                    c = __ffma2_rn(a2, bl2[j], c);
+                    c2[i][j] = __ffma2_rn(l2, bh2[j], c);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int g = g0 + ty * 4 + i;
+        if (g >= rows) continue;
+        const int mbr = g / N, sl = g % N;
+        if (st && !(st[mbr].active && !st[mbr].skip && !st[mbr].half)) continue;
+        double *crow = C + (size_t)mbr * cstride + (size_t)sl * M + c0 + tx * 4;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            crow[2 * j] = f2d(s2[i][j].x) + f2d(c2[i][j].x);
+            crow[2 * j + 1] = f2d(s2[i][j].y) + f2d(c2[i][j].y);
+        }
+    }
+}
+
 __global__ void k_transpose_scale(const double *X, double *Y, int M, double s) {
     const size_t n = (size_t)M * M;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
@@ -529,10 +645,13 @@ pit_status dense_setup(Problem *p) {
         k_copy_f32<<<blocks, 256, 0, s>>>(Res, p->GL32.as<float>(), mm2);
         PIT_LAUNCH_CHECK();
     }
-    // FP32 copies for the mixed path
+    // FP32 copies for the mixed path; Phi also as float-float (hi, lo) for
+    // the residual product
     PIT_TRY(p->PhiF_hi.ensure(mm2 * sizeof(float)));
+    PIT_TRY(p->PhiF_lo.ensure(mm2 * sizeof(float)));
     PIT_TRY(p->G32.ensure(mm2 * sizeof(float)));
-    k_copy_f32<<<blocks, 256, 0, s>>>(p->PhiF64.as<double>(), p->PhiF_hi.as<float>(), mm2);
+    k_split_ff<<<blocks, 256, 0, s>>>(p->PhiF64.as<double>(), p->PhiF_hi.as<float>(),
+                                      p->PhiF_lo.as<float>(), mm2);
     PIT_LAUNCH_CHECK();
     k_copy_f32<<<blocks, 256, 0, s>>>(G, p->G32.as<float>(), mm2);
     PIT_LAUNCH_CHECK();
@@ -545,7 +664,8 @@ pit_status dense_setup(Problem *p) {
 }
 
 // C (batch x N x M, row n = Phi x_n for n < N) in FP64 or FP32.
-static pit_status dense_product(Problem *p, const double *x, int prec, cudaStream_t s) {
+static pit_status dense_product(Problem *p, const double *x, int prec, const MemberState *st,
+                                cudaStream_t s) {
     const int M = p->M, N = p->N;
     cublasHandle_t h = handle(p);
     PIT_CUBLAS(cublasSetStream(h, s));
@@ -567,6 +687,22 @@ static pit_status dense_product(Problem *p, const double *x, int prec, cudaStrea
         return PIT_OK;
     }
     PIT_TRY(p->dense_scratch.ensure((size_t)p->batch * cstride * sizeof(double)));
+    if (prec == PIT_FF && M % FG_B == 0) {
+        // float-float product: X split once, then the compensated GEMM
+        PIT_TRY(p->q32.ensure(2 * p->vlen * sizeof(float)));
+        float *xh = p->q32.as<float>(), *xl = xh + p->vlen;
+        int blocks;
+        grid_for(p->vlen, blocks);
+        k_split_ff<<<blocks, 256, 0, s>>>(x, xh, xl, p->vlen);
+        PIT_LAUNCH_CHECK();
+        const int rows = p->batch * N;
+        dim3 grid((unsigned)(M / FG_B), (unsigned)((rows + FG_B - 1) / FG_B));
+        k_gemm_ff<<<grid, FG_T, 0, s>>>(xh, xl, p->PhiF_hi.as<float>(), p->PhiF_lo.as<float>(),
+                                        p->dense_scratch.as<double>(), M, N, p->blen, cstride,
+                                        rows, st);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
     const double one = 1.0, zero = 0.0;
     PIT_CUBLAS(cublasDgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, M, N, M, &one,
                                          p->PhiF64.as<double>(), M, 0, x, M, (long long)p->blen,
@@ -578,7 +714,7 @@ static pit_status dense_product(Problem *p, const double *x, int prec, cudaStrea
 pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                          const MemberState *st, cudaStream_t s) {
     if (prec == PIT_MIXED && p->use_tc) return dense_tc_apply(p, x, y, nullptr, mode, st, s);
-    PIT_TRY(dense_product(p, x, prec, s));
+    PIT_TRY(dense_product(p, x, prec, st, s));
     int blocks;
     grid_for(p->blen, blocks);
     const size_t cstride = (size_t)p->N * p->M;

@@ -62,6 +62,23 @@ def test_dense_fine_product_fp32(case):
     assert _rel(got, _oracle(w, "F", X)) < 2e-5
 
 
+@pytest.mark.parametrize("case", [dict(M=64, N=8, T=1.0, fine_steps=37),
+                                  dict(M=128, N=5, T=2.0, fine_steps=20, batch=2),
+                                  dict(M=256, N=70, T=10.0 * 70 / 4096, fine_steps=200)])
+def test_dense_float_float_product(case):
+    """The compensated float-float product (Dot2 form on (hi, lo) pairs) used
+    by the mixed path's true residual: within 1e-11 of the FP64 oracle, on
+    row counts that are not multiples of the 64-row tile."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(**case)
+    X = _rand(w, 5)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("F", X, precision="ff")
+        res = p.apply("residual", X, precision="ff")
+    assert _rel(got, _oracle(w, "F", X)) < 1e-11
+    assert _rel(res, _oracle(w, "residual", X)) < 1e-10
+
+
 def test_dense_fp64_bicgstab_matches_oracle():
     from paper_2203_10148_gb300 import pit
     w = inputs.dense(M=64, N=32, T=1.0, fine_steps=50, precision="fp64")
@@ -99,9 +116,11 @@ def test_dense_full_size_sampled():
     with pit.Problem(w, "mixed") as p:
         Y = p.apply("F", Xd, precision="fp64").cpu().numpy()[0]
         Y32 = p.apply("F", Xd, precision="mixed").cpu().numpy()[0]
+        Yff = p.apply("F", Xd, precision="ff").cpu().numpy()[0]
     rows = [1, 2, 777, 2048, 4095, 4096]
     ref = X[0][rows] - o.F(X[0][[r - 1 for r in rows]])
     assert _rel(Y[rows], ref) < 1e-12
+    assert _rel(Yff[rows], ref) < 1e-11
     assert _rel(Y32[rows], ref) < 1e-4
     np.testing.assert_array_equal(Y[0], X[0][0])
 
