@@ -388,12 +388,109 @@ __device__ __forceinline__ void rows_dot(const T *Gm, const T *v, int M, int row
 // whose chunk has ended (or whose member is inactive) keep their value.
 // Warps split the columns, and split k as well when there are fewer columns
 // than warps; partial sums meet in shared memory.
+// Warps own columns (at least as many columns as warps, M <= 32 x 8 x W,
+// M % W == 0), SW_CP at a time: the lanes hold the SW_CP columns in
+// registers (eight 16-byte loads per column each), every 16-byte vector of
+// the CTA's G rows read from shared memory feeds all SW_CP columns, and lane
+// r finishes row r0 + r of each column after a butterfly reduction, so a
+// step has no CTA barrier.
+constexpr int SW_CP = 4;
+
+template <class T>
+__device__ void sweep_step_warpcols(const SweepArgs<T> &a, const T *Gm, const T *in, T *out, int i,
+                                    bool from_zero, bool store, int r0) {
+    constexpr int NW = SW_THREADS / 32;
+    constexpr int W = Vec16<T>::W;
+    constexpr int U = 8;
+    using V = typename Vec16<T>::V;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncols = a.batch * a.C;
+    const int nvec = a.M / W;                      // 16-byte vectors per column
+    const int row = r0 + lane;
+    const bool row_ok = lane < a.rows && row < a.M;
+    for (int base = warp * SW_CP; base < ncols; base += NW * SW_CP) {
+        V x[SW_CP][U];
+        double qv[SW_CP];
+        bool live[SW_CP];
+#pragma unroll
+        for (int cp = 0; cp < SW_CP; ++cp) {
+            const int col = base + cp;
+            const bool ok = col < ncols;
+            if (ok && !from_zero) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int vi = lane + 32 * u;
+                    if (vi < nvec) x[cp][u] = ldcg16(in + (size_t)col * a.M + (size_t)vi * W);
+                }
+            }
+            const int b = ok ? col / a.C : 0, c = ok ? col % a.C : 0;
+            const int blk = c * a.L + i;
+            live[cp] = ok && blk <= a.N &&
+                       (a.st == nullptr || (a.st[b].active && !a.st[b].skip && !a.st[b].half));
+            qv[cp] = (live[cp] && row_ok) ? __ldcg(a.q + (size_t)b * a.blen + (size_t)blk * a.M + row) : 0.0;
+        }
+        T acc[SW_CP][SW_MAXROWS];
+#pragma unroll
+        for (int cp = 0; cp < SW_CP; ++cp)
+#pragma unroll
+            for (int r = 0; r < SW_MAXROWS; ++r) acc[cp][r] = T(0);
+        if (!from_zero) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int vi = lane + 32 * u;
+                if (vi < nvec) {
+#pragma unroll
+                    for (int r = 0; r < SW_MAXROWS; ++r) {
+                        const V g = *reinterpret_cast<const V *>(Gm + (size_t)r * a.M + (size_t)vi * W);
+#pragma unroll
+                        for (int cp = 0; cp < SW_CP; ++cp)
+#pragma unroll
+                            for (int e = 0; e < W; ++e)
+                                acc[cp][r] = fma(vget(g, e), vget(x[cp][u], e), acc[cp][r]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int cp = 0; cp < SW_CP; ++cp)
+#pragma unroll
+            for (int r = 0; r < SW_MAXROWS; ++r)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[cp][r] += __shfl_xor_sync(0xffffffffu, acc[cp][r], o);
+        if (row_ok) {
+#pragma unroll
+            for (int cp = 0; cp < SW_CP; ++cp) {
+                const int col = base + cp;
+                if (col >= ncols) continue;
+                T val = acc[cp][0];
+#pragma unroll
+                for (int rr = 1; rr < SW_MAXROWS; ++rr) val = (lane == rr) ? acc[cp][rr] : val;
+                T res;
+                if (live[cp]) {
+                    res = (T)qv[cp] + val;
+                    if (store) {
+                        const int b = col / a.C, blk = (col % a.C) * a.L + i;
+                        a.z[(size_t)b * a.blen + (size_t)blk * a.M + row] = (double)res;
+                    }
+                } else {
+                    res = from_zero ? T(0) : ld_cg(in + (size_t)col * a.M + row);
+                }
+                __stcg(out + (size_t)col * a.M + row, res);
+            }
+        }
+    }
+}
+
 template <class T>
 __device__ void sweep_step(const SweepArgs<T> &a, const T *Gm, const T *in, T *out, int i,
                            bool from_zero, bool store, int r0, T *red) {
     constexpr int NW = SW_THREADS / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ncols = a.batch * a.C;
+    if (ncols >= NW && a.M % Vec16<T>::W == 0 && a.M <= 32 * 8 * Vec16<T>::W) {
+        sweep_step_warpcols(a, Gm, in, out, i, from_zero, store, r0);
+        return;
+    }
     const int S = ncols >= NW ? 1 : NW / ncols;        // k segments per column
     const int per_round = NW / S;                        // columns per round
     const int seg_len = (((a.M + S - 1) / S) + 3) & ~3;
