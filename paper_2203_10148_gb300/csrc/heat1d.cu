@@ -16,9 +16,11 @@
 // state stays in registers across all fine steps.
 #include <math.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "pit_internal.h"
+#include "stencil_arith.cuh"
 
 namespace pit {
 namespace {
@@ -42,7 +44,7 @@ __device__ __forceinline__ T shfl_dir(T v, int o, bool rev) {
 }
 
 // Exclusive scan of affine maps over the CTA.  Scan order is thread order
-// (REV = false) or reversed thread order (REV = true).  sh: 2*NT/32 values.
+// (REV = false) or reversed thread order (REV = true).  sh: 4*NT/32 values.
 template <class T, int NT, bool REV>
 __device__ Aff<T> cta_affine_excl(Aff<T> v, T *sh) {
     constexpr int W = NT / 32;
@@ -67,55 +69,85 @@ __device__ Aff<T> cta_affine_excl(Aff<T> v, T *sh) {
         sh[W + warp] = inc.c;
     }
     __syncthreads();
-    Aff<T> wp{T(1), T(0)};
-    if (!REV) {
-        for (int w2 = 0; w2 < warp; ++w2) wp = comp(Aff<T>{sh[w2], sh[W + w2]}, wp);
-    } else {
-        for (int w2 = W - 1; w2 > warp; --w2) wp = comp(Aff<T>{sh[w2], sh[W + w2]}, wp);
+    // prefix over the warps' aggregates: warp 0 scans them with shuffles
+    // (lane l holds warp l's map, W <= 32) and leaves each warp's exclusive
+    // prefix in shared memory
+    if (warp == 0) {
+        Aff<T> wv = (lane < W) ? Aff<T>{sh[lane], sh[W + lane]} : Aff<T>{T(1), T(0)};
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T a = shfl_dir(wv.a, o, REV);
+            const T c = shfl_dir(wv.c, o, REV);
+            const bool ok = REV ? (lane + o < 32) : (lane >= o);
+            if (ok) wv = comp(wv, Aff<T>{a, c});
+        }
+        // inclusive prefix at lane l -/+ 1 is the exclusive prefix of warp l
+        const T pa = shfl_dir(wv.a, 1, REV);
+        const T pc = shfl_dir(wv.c, 1, REV);
+        const bool none = REV ? (lane == W - 1) : (lane == 0);
+        __syncwarp();
+        if (lane < W) {
+            sh[2 * W + lane] = none ? T(1) : pa;
+            sh[3 * W + lane] = none ? T(0) : pc;
+        }
     }
+    __syncthreads();
+    const Aff<T> wp{sh[2 * W + warp], sh[3 * W + warp]};
     return comp(exw, wp);
 }
 
+// Thomas factors of this thread's E points, loaded once per kernel:
+// fm_i = -a inv_i, inv_i, ncp_i = -c'_i; padding points (i >= M) get the
+// identity map (fm = 1, inv = 0, ncp = 1) and never feed a valid point.
+template <class T, int E>
+struct Factors {
+    T fm[E], inv[E], ncp[E];
+    bool ok[E];
+    __device__ void load(const T *__restrict__ fmg, const T *__restrict__ invg,
+                         const T *__restrict__ cpg, int M) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = threadIdx.x * E + e;
+            ok[e] = i < M;
+            const int ic = min(i, M - 1);
+            fm[e] = ok[e] ? fmg[ic] : T(1);
+            inv[e] = ok[e] ? invg[ic] : T(0);
+            ncp[e] = ok[e] ? -cpg[ic] : T(1);
+        }
+    }
+};
+
 // One implicit-Euler step on the CTA-distributed state u (E points per
-// thread, thread t owns points t*E .. t*E+E-1).  fm_i = -a inv_i,
-// inv_i, cp_i = c'_i (cp_{M-1} = 0).
+// thread, thread t owns points t*E .. t*E+E-1).
 template <class T, int E, int NT>
-__device__ __forceinline__ void ie_step(T (&u)[E], const T *__restrict__ fm,
-                                        const T *__restrict__ inv, const T *__restrict__ cp,
-                                        int M, T *sh) {
-    const int i0 = threadIdx.x * E;
+__device__ __forceinline__ void ie_step(T (&u)[E], const Factors<T, E> &f, T *sh) {
     // forward: d'_i = fm_i d'_{i-1} + inv_i d_i
     Aff<T> agg{T(1), T(0)};
-    T lm[E], lc[E];
+    T lc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int i = i0 + e;
-        const int ic = min(i, M - 1);
-        lm[e] = (i < M) ? fm[ic] : T(1);
-        lc[e] = (i < M) ? inv[ic] * u[e] : T(0);
-        agg = comp(Aff<T>{lm[e], lc[e]}, agg);
+        lc[e] = f.inv[e] * u[e];
+        agg = comp(Aff<T>{f.fm[e], lc[e]}, agg);
     }
     Aff<T> pre = cta_affine_excl<T, NT, false>(agg, sh);
     T y = pre.c;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        y = fma(lm[e], y, lc[e]);
+        y = fma(f.fm[e], y, lc[e]);
         u[e] = y;                       // d'_i
     }
     // backward: x_i = -cp_i x_{i+1} + d'_i, scanned from the last point
     agg = Aff<T>{T(1), T(0)};
 #pragma unroll
     for (int e = E - 1; e >= 0; --e) {
-        const int i = i0 + e;
-        lm[e] = (i < M) ? -cp[min(i, M - 1)] : T(1);
-        lc[e] = (i < M) ? u[e] : T(0);
-        agg = comp(Aff<T>{lm[e], lc[e]}, agg);
+        lc[e] = f.ok[e] ? u[e] : T(0);
+        agg = comp(Aff<T>{f.ncp[e], lc[e]}, agg);
     }
-    pre = cta_affine_excl<T, NT, true>(agg, sh + 2 * (NT / 32));
+    pre = cta_affine_excl<T, NT, true>(agg, sh + 4 * (NT / 32));
     y = pre.c;
 #pragma unroll
     for (int e = E - 1; e >= 0; --e) {
-        y = fma(lm[e], y, lc[e]);
+        y = fma(f.ncp[e], y, lc[e]);
         u[e] = y;
     }
 }
@@ -142,7 +174,7 @@ template <class T, int E, int NT>
 __global__ void __launch_bounds__(NT) k_heat1d_fine(Heat1dArgs a, const T *__restrict__ fm,
                                                     const T *__restrict__ inv,
                                                     const T *__restrict__ cp) {
-    __shared__ T sh[4 * (NT / 32)];
+    __shared__ T sh[8 * (NT / 32)];
     const int b = blockIdx.y;
     if (!runs(a.st, b)) return;
     const int n = a.n_first + blockIdx.x;    // output block, 1..N
@@ -152,17 +184,23 @@ __global__ void __launch_bounds__(NT) k_heat1d_fine(Heat1dArgs a, const T *__res
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = threadIdx.x * E + e;
-        const T ld = (T)xin[min(i, a.M - 1)];
+        T ld;
+        if constexpr (std::is_same<T, float>::value) ld = d2f_rn(xin[min(i, a.M - 1)]);  // integer pipe
+        else ld = xin[min(i, a.M - 1)];
         u[e] = (i < a.M) ? ld : T(0);
     }
-    for (int s = 0; s < a.steps; ++s) ie_step<T, E, NT>(u, fm, inv, cp, a.M, sh);
+    Factors<T, E> f;
+    f.load(fm, inv, cp, a.M);
+    for (int s = 0; s < a.steps; ++s) ie_step<T, E, NT>(u, f, sh);
     double *yo = a.y + mb + (size_t)n * a.M;
     const double *xn = a.x + mb + (size_t)n * a.M;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = threadIdx.x * E + e;
         if (i < a.M) {
-            const double f = (double)u[e];
+            double f;
+            if constexpr (std::is_same<T, float>::value) f = f2d(u[e]);
+            else f = u[e];
             if (a.mode == FINE_APPLY) yo[i] = xn[i] - f;
             else if (a.mode == FINE_RESIDUAL) yo[i] = f - xn[i];
             else yo[i] = f;
@@ -178,8 +216,69 @@ __global__ void __launch_bounds__(NT) k_heat1d_fine(Heat1dArgs a, const T *__res
 }
 
 // Coarse sweep z_0 = q_0, z_n = q_n + G(z_{n-1}), one CTA per member,
-// sequential in n.  G is `steps` IE steps in arithmetic T; the running sum
-// z_n is kept in FP64.
+// sequential in n.  G is `steps` IE steps in arithmetic T.  FP64: the
+// running sum z_n is FP64.  FP32 (the mixed path): everything is FP32 and
+// the FP64 <-> FP32 conversions run on the integer pipe, so a step has no
+// FP64-pipe work (one CTA runs the whole sweep, and the FP64 pipe of one SM
+// is 2 lanes wide); G(z_{n-1}) is an FP32 solve in both forms, so the FP32
+// running sum costs no accuracy the FP64 one had.
+template <int E, int NT>
+__global__ void __launch_bounds__(NT) k_heat1d_sweep_f32(const double *q, double *z, int M, int N,
+                                                        size_t blen, int steps,
+                                                        const float *__restrict__ fm,
+                                                        const float *__restrict__ inv,
+                                                        const float *__restrict__ cp,
+                                                        const MemberState *st) {
+    __shared__ float sh[8 * (NT / 32)];
+    const int b = blockIdx.x;
+    if (!runs(st, b)) return;
+    const size_t mb = (size_t)b * blen;
+    Factors<float, E> fac;
+    fac.load(fm, inv, cp, M);
+    float zz[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        const double ld = q[mb + min(i, M - 1)];
+        zz[e] = (i < M) ? d2f_rn(ld) : 0.f;
+        if (i < M) z[mb + i] = ld;          // z_0 = q_0 exactly
+    }
+    // q_n is loaded one slice ahead so that its latency overlaps a solve
+    double qnext[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        qnext[e] = (i < M && N >= 1) ? q[mb + (size_t)M + i] : 0.0;
+    }
+    for (int n = 1; n <= N; ++n) {
+        const size_t off = mb + (size_t)n * M;
+        float qn[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) qn[e] = d2f_rn(qnext[e]);
+        if (n < N) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = threadIdx.x * E + e;
+                qnext[e] = (i < M) ? q[off + (size_t)M + i] : 0.0;
+            }
+        }
+        float u[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) u[e] = zz[e];
+        for (int s = 0; s < steps; ++s) ie_step<float, E, NT>(u, fac, sh);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = threadIdx.x * E + e;
+            if (i < M) {
+                zz[e] = qn[e] + u[e];
+                z[off + i] = f2d(zz[e]);
+            } else {
+                zz[e] = 0.f;
+            }
+        }
+    }
+}
+
 template <class T, int E, int NT>
 __global__ void __launch_bounds__(NT) k_heat1d_sweep(const double *q, double *z, int M, int N,
                                                      size_t blen, int steps,
@@ -187,10 +286,12 @@ __global__ void __launch_bounds__(NT) k_heat1d_sweep(const double *q, double *z,
                                                      const T *__restrict__ inv,
                                                      const T *__restrict__ cp,
                                                      const MemberState *st) {
-    __shared__ T sh[4 * (NT / 32)];
+    __shared__ T sh[8 * (NT / 32)];
     const int b = blockIdx.x;
     if (!runs(st, b)) return;
     const size_t mb = (size_t)b * blen;
+    Factors<T, E> fac;
+    fac.load(fm, inv, cp, M);
     double zz[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -200,16 +301,23 @@ __global__ void __launch_bounds__(NT) k_heat1d_sweep(const double *q, double *z,
         if (i < M) z[mb + i] = zz[e];
     }
     for (int n = 1; n <= N; ++n) {
+        const size_t off = mb + (size_t)n * M;
+        // q_n is loaded before the solve so that its latency overlaps it
+        double qn[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = threadIdx.x * E + e;
+            qn[e] = (i < M) ? q[off + i] : 0.0;
+        }
         T u[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) u[e] = (T)zz[e];
-        for (int s = 0; s < steps; ++s) ie_step<T, E, NT>(u, fm, inv, cp, M, sh);
-        const size_t off = mb + (size_t)n * M;
+        for (int s = 0; s < steps; ++s) ie_step<T, E, NT>(u, fac, sh);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i = threadIdx.x * E + e;
             if (i < M) {
-                zz[e] = q[off + i] + (double)u[e];
+                zz[e] = qn[e] + (double)u[e];
                 z[off + i] = zz[e];
             } else {
                 zz[e] = 0.0;
@@ -261,11 +369,13 @@ const T *fptr(const DevBuf &b, int M, int which) {
 // Threads and points per thread for a state of M points.
 template <class F>
 pit_status dispatch_1d(int M, F &&f) {
+    // a few points per thread: the CTA scans cost shuffles per warp, the
+    // per-thread compositions cost a dependent chain per point
     if (M <= 64) return f.template run<1, 64>();
-    if (M <= 256) return f.template run<1, 256>();
-    if (M <= 1024) return f.template run<1, 1024>();
-    if (M <= 2048) return f.template run<2, 1024>();
-    if (M <= 4096) return f.template run<4, 1024>();
+    if (M <= 256) return f.template run<2, 128>();
+    if (M <= 1024) return f.template run<4, 256>();
+    if (M <= 2048) return f.template run<8, 256>();
+    if (M <= 4096) return f.template run<8, 512>();
     if (M <= 8192) return f.template run<8, 1024>();
     set_error("heat1d: M > 8192 is not supported");
     return PIT_E_UNSUPPORTED;
@@ -301,9 +411,15 @@ struct SweepLaunch {
     pit_status run() {
         const T *base = fac->as<T>();
         const int M = p->M;
-        k_heat1d_sweep<T, E, NT><<<p->batch, NT, 0, s>>>(q, z, M, p->N, p->blen,
-                                                          p->coarse_steps, base, base + M,
-                                                          base + 2 * M, st);
+        if constexpr (std::is_same<T, float>::value) {
+            k_heat1d_sweep_f32<E, NT><<<p->batch, NT, 0, s>>>(q, z, M, p->N, p->blen,
+                                                              p->coarse_steps, base, base + M,
+                                                              base + 2 * M, st);
+        } else {
+            k_heat1d_sweep<T, E, NT><<<p->batch, NT, 0, s>>>(q, z, M, p->N, p->blen,
+                                                              p->coarse_steps, base, base + M,
+                                                              base + 2 * M, st);
+        }
         PIT_LAUNCH_CHECK();
         return PIT_OK;
     }

@@ -397,7 +397,12 @@ class Server:
         if st == PIT_E_INVALID:
             check(st)
         del self._shapes[ticket]
-        return st, X, [i.as_dict() for i in infos]
+        out = [i.as_dict() for i in infos]
+        if st != PIT_OK:
+            msg = last_error()
+            for d in out:
+                d["error"] = msg
+        return st, X, out
 
     def poll(self, ticket: int):
         """None while pending, else (status, X, [info per member])."""

@@ -54,12 +54,13 @@ def test_served_equals_solo_and_oracle():
         tickets = [srv.submit(w, **OPTS) for w in ws]
         results = [srv.wait(t, timeout=300.0) for t in tickets]
         stats = srv.stats()
+    bad = [(w.name, r[0] if r else None, r[2][0] if r else None) for w, r in zip(ws, results)
+           if r is None or r[0] != pit.PIT_OK]
+    assert not bad, bad
     assert stats["completed"] == len(ws) and stats["failed"] == 0
     assert stats["max_running"] >= 2, "requests submitted together must overlap"
     for w, res in zip(ws, results):
-        assert res is not None, w.name
         st, X, info = res
-        assert st == pit.PIT_OK, (w.name, info)
         assert info[0]["latency_seconds"] >= info[0]["queue_seconds"] >= 0.0
         assert 0 < info[0]["device_bytes"] <= pit.serve_footprint(w), w.name
         with pit.Problem(w) as p:
@@ -94,7 +95,8 @@ def test_budget_admission_and_queueing():
         tickets = [srv.submit(w, **OPTS) for w in ws]
         results = [srv.wait(t, timeout=300.0) for t in tickets]
         stats = srv.stats()
-    assert all(r is not None and r[0] == pit.PIT_OK for r in results)
+    bad = [(w.name, r[0], r[2][0]) for w, r in zip(ws, results) if r is None or r[0] != pit.PIT_OK]
+    assert not bad, bad
     assert stats["hbm_reserved_peak"] <= budget
     assert stats["hbm_reserved"] == 0 and stats["running"] == 0
     assert stats["completed"] == len(ws)
@@ -180,7 +182,8 @@ def test_open_loop_poisson_stream():
         res = [srv.wait(t, timeout=300.0) for t in tickets]
         s = srv.stats(reset=True)
         s2 = srv.stats()
-    assert all(r[0] == pit.PIT_OK for r in res)
+    bad = [(w.name, r[0], r[2][0]) for w, r in zip(ws, res) if r[0] != pit.PIT_OK]
+    assert not bad, bad
     assert s["completed"] == len(ws) and s["submitted"] == len(ws)
     assert s["solves_per_s"] > 0 and s["slice_steps_per_s"] > 0
     assert s["latency_p99"] >= s["latency_p50"] > 0
