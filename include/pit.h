@@ -171,10 +171,11 @@ size_t pit_last_error(char *buf, size_t n);
  * Copies y0, A, vx, vy into library-owned device memory (the caller may free
  * its arrays on return) and runs the set-up: stepper factorisations, the
  * sine-basis tables of the 2D heat coarse solver, or the dense propagator
- * R(dt A)^steps and G = (I - dT A)^{-1} for PIT_OP_DENSE.
- * Supported: HEAT1D with IE or RK4 fine and IE coarse; HEAT2D (nx = ny) with
- * RK4 fine and IE coarse; ADVDIFF2D with RK4 fine and IE coarse; DENSE with
- * RK4 fine and IE coarse.  Others return PIT_E_UNSUPPORTED.
+ * (R(dt A) or (I - dt A)^{-1})^steps and G = (I - dT A)^{-1} for PIT_OP_DENSE.
+ * Supported: HEAT1D with IE fine and IE coarse; HEAT2D (nx = ny <= 256) with
+ * RK4 fine and IE coarse; ADVDIFF2D (n = 32 .. 512, a power of two) with RK4
+ * fine and one IE coarse step; DENSE with RK4 or IE fine and IE coarse.
+ * Others return PIT_E_UNSUPPORTED.
  * Errors: PIT_E_INVALID (bad sizes, non-finite values), PIT_E_NOMEM, PIT_E_CUDA.
  */
 pit_status pit_problem_create(const pit_problem_desc *desc, pit_problem_t *out);

@@ -1,11 +1,13 @@
 // Dense-propagator mode: y' = A y with a dense M x M matrix A.
 //
-// Set-up: the fine propagator of one slice is the RK4 step matrix raised to
-// the number of fine steps, Phi = R(dt A)^m with R(Z) = I + Z + Z^2/2 + Z^3/6
-// + Z^4/24 (nested form), by binary powering; the coarse propagator is one
-// implicit-Euler step, G = (I - dT A)^{-1}, by Newton-Schulz iteration
-// X <- X (2I - B X) on B = I - dT A from the scaled start X = B^T/(|B|_1 |B|_inf).
-// Both are FP64 matrix products (cuBLAS DGEMM, once per problem).
+// Set-up: the fine propagator of one slice is the one-step matrix raised to
+// the number of fine steps by binary powering, Phi = W^m, with W the RK4
+// step matrix R(dt A), R(Z) = I + Z + Z^2/2 + Z^3/6 + Z^4/24 (nested form),
+// or the implicit-Euler step (I - dt A)^{-1}; the coarse propagator is one
+// implicit-Euler step, G = (I - dT A)^{-1}.  Inverses by Newton-Schulz
+// iteration X <- X (2I - B X) on B = I - d A from the scaled start
+// X = B^T/(|B|_1 |B|_inf).  All are FP64 matrix products (cuBLAS DGEMM, once
+// per problem).
 //
 // Fine batch (the N independent slice problems of eq. (2)): all slices at
 // once as one product C = Phi [x_0 ... x_{N-1}], then the shift-subtract of
@@ -616,8 +618,8 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
 }  // namespace
 
 pit_status dense_setup(Problem *p) {
-    if (p->fine_kind != PIT_STEP_RK4 || p->coarse_kind != PIT_STEP_IE) {
-        set_error("dense: fine must be RK4 (precomputed propagator) and coarse implicit Euler");
+    if ((p->fine_kind != PIT_STEP_RK4 && p->fine_kind != PIT_STEP_IE) || p->coarse_kind != PIT_STEP_IE) {
+        set_error("dense: fine must be RK4 or implicit Euler (precomputed propagator), coarse implicit Euler");
         return PIT_E_UNSUPPORTED;
     }
     const int M = p->M;
@@ -628,21 +630,19 @@ pit_status dense_setup(Problem *p) {
     PIT_CUBLAS(cublasSetStream(h, p->stream));
     PIT_CUBLAS(cublasSetMathMode(h, CUBLAS_DEFAULT_MATH));
     DevBuf work;
-    PIT_TRY(work.ensure(4 * mm2 * sizeof(double) + 64));
+    PIT_TRY(work.ensure(5 * mm2 * sizeof(double) + 64));
     double *A = p->PhiF64.as<double>();      // staged by pit_problem_create
     double *T1 = work.as<double>(), *T2 = T1 + mm2, *T3 = T2 + mm2, *T4 = T3 + mm2;
-    double *scal = T4 + mm2;
+    double *T5 = T4 + mm2;
+    double *scal = T5 + mm2;
     int blocks;
     grid_for(mm2, blocks);
     cudaStream_t s = p->stream;
-    // G = (I - dTc A)^{-c}: Newton-Schulz for (I - dTc A)^{-1}, then its c-th power
-    PIT_TRY(p->G64.ensure(mm2 * sizeof(double)));
-    double *G = p->G64.as<double>();
-    {
-        const double dtc = p->dT / p->coarse_steps;
+    // (I - d A)^{-1} by Newton-Schulz iteration into `out` (work: T1..T4)
+    auto ns_inverse = [&](double d, double *out) -> pit_status {
         double *Bm = T1, *X = T2, *P = T3, *Xn = T4;
         PIT_CUDA(cudaMemsetAsync(Bm, 0, mm2 * sizeof(double), s));
-        k_axpby_identity<<<blocks, 256, 0, s>>>(Bm, A, -dtc, 0.0, 1.0, M);   // B = I - dtc A
+        k_axpby_identity<<<blocks, 256, 0, s>>>(Bm, A, -d, 0.0, 1.0, M);   // B = I - d A
         PIT_LAUNCH_CHECK();
         k_norms_1_inf<<<1, 256, 0, s>>>(Bm, M, scal);
         PIT_LAUNCH_CHECK();
@@ -673,31 +673,45 @@ pit_status dense_setup(Problem *p) {
             std::swap(X, Xn);
         }
         if (!ok) {
-            set_error("dense: Newton-Schulz inverse of I - dT A did not converge");
+            set_error("dense: Newton-Schulz inverse of I - dt A did not converge");
             return PIT_E_INVALID;
         }
-        // G = X^c by repeated products (c coarse steps)
+        PIT_CUDA(cudaMemcpyAsync(out, X, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return PIT_OK;
+    };
+    // G = (I - dTc A)^{-c}: the inverse, then its c-th power
+    PIT_TRY(p->G64.ensure(mm2 * sizeof(double)));
+    double *G = p->G64.as<double>();
+    {
+        PIT_TRY(ns_inverse(p->dT / p->coarse_steps, T5));
+        double *X = T5, *P = T1;
         PIT_CUDA(cudaMemcpyAsync(G, X, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
         for (int c = 1; c < p->coarse_steps; ++c) {
             PIT_TRY(mm(h, M, G, X, P));
             PIT_CUDA(cudaMemcpyAsync(G, P, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
         }
     }
-    // Phi = R(dt A)^m, R(Z) = I + Z (I + Z/2 (I + Z/3 (I + Z/4)))
+    // Phi = W^m with the one-step matrix W: RK4, R(dt A) with
+    // R(Z) = I + Z (I + Z/2 (I + Z/3 (I + Z/4))); implicit Euler, (I - dt A)^{-1}
     {
         const double dt = p->dT / p->fine_steps;
         double *R = T1, *W = T2, *Base = T3, *Res = T4;
-        // W = I + (dt/4) A
-        PIT_CUDA(cudaMemsetAsync(W, 0, mm2 * sizeof(double), s));
-        k_axpby_identity<<<blocks, 256, 0, s>>>(W, A, dt / 4.0, 0.0, 1.0, M);
-        PIT_LAUNCH_CHECK();
-        const double coef[3] = {dt / 3.0, dt / 2.0, dt};
-        for (int k = 0; k < 3; ++k) {
-            // W <- I + coef_k A W
-            PIT_TRY(mm(h, M, A, W, R, coef[k], 0.0));
+        if (p->fine_kind == PIT_STEP_IE) {
+            PIT_TRY(ns_inverse(dt, T5));
+            W = T5;
+        } else {
+            // W = I + (dt/4) A
             PIT_CUDA(cudaMemsetAsync(W, 0, mm2 * sizeof(double), s));
-            k_axpby_identity<<<blocks, 256, 0, s>>>(W, R, 1.0, 0.0, 1.0, M);
+            k_axpby_identity<<<blocks, 256, 0, s>>>(W, A, dt / 4.0, 0.0, 1.0, M);
             PIT_LAUNCH_CHECK();
+            const double coef[3] = {dt / 3.0, dt / 2.0, dt};
+            for (int k = 0; k < 3; ++k) {
+                // W <- I + coef_k A W
+                PIT_TRY(mm(h, M, A, W, R, coef[k], 0.0));
+                PIT_CUDA(cudaMemsetAsync(W, 0, mm2 * sizeof(double), s));
+                k_axpby_identity<<<blocks, 256, 0, s>>>(W, R, 1.0, 0.0, 1.0, M);
+                PIT_LAUNCH_CHECK();
+            }
         }
         // binary powering of W to the m-th power
         PIT_CUDA(cudaMemcpyAsync(Base, W, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -240,6 +240,64 @@ def dense(M: int = 1024, T: float = 10.0, N: int = 4096, fine_steps: int = 200,
                     ("ie", coarse_steps), y0, A=A, tol=tol, precision=precision)
 
 
+# The three test problems of Sec. 4 (eq. (9), read as
+# y_t + u . grad y - div(mu grad y) + r y = 0 with y = 0 on the boundary):
+# (mu, r, advection by the rotation u = (-y, x)).
+PAPER_PDES = {
+    "diffusion": (1.0, 0.0, False),
+    "diffusion_reaction": (1.0, 1.5, False),
+    "advection_diffusion_reaction": (0.1, 0.5, True),
+}
+
+
+def paper_pde(pde: str = "diffusion", n: int = 49, N: int = 4, T: float = 6.4,
+              dt: float = 1e-3, center: Tuple[float, float] = (0.2, 0.0),
+              width: float = 0.1, batch: int = 1, tol: float = 1e-10,
+              precision: str = "fp64") -> Workload:
+    """A Sec. 4 test problem as a dense-operator workload.
+
+    Unit square centred at the origin, n x n interior points of a grid with
+    h = 1/(n+1) (n = 49: the paper's h = 2e-2), Dirichlet 0.  Finite
+    differences stand in for the paper's finite elements: the 5-point
+    Laplacian times mu, central differences for u . grad y, and -r y, as a
+    dense M x M matrix A (M = n^2, row-major states).  Fine propagator:
+    backward Euler with the paper's dt = 1e-3 (round(T / (N dt)) steps per
+    slice); coarse: one backward-Euler step per slice.  y0: a Gaussian of
+    standard deviation `width` at `center` (off the centre, so that the
+    rotation moves it).
+    """
+    mu, r, adv = PAPER_PDES[pde]
+    h = 1.0 / (n + 1)
+    xs = -0.5 + h * np.arange(1, n + 1)
+    M = n * n
+    A = np.zeros((M, M))
+    idx = np.arange(M).reshape(n, n)          # idx[j, i]: point (x_i, y_j)
+    diag = -4.0 * mu / h ** 2 - r
+    A[idx.ravel(), idx.ravel()] = diag
+    for dj, di in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+        j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        jj, ii = j + dj, i + di
+        ok = (jj >= 0) & (jj < n) & (ii >= 0) & (ii < n)
+        rows = idx[j[ok], i[ok]]
+        cols = idx[jj[ok], ii[ok]]
+        val = np.full(rows.shape, mu / h ** 2)
+        if adv:
+            # -(u_x dy/dx + u_y dy/dy), u = (-y, x), central differences
+            ux = -xs[j[ok]]
+            uy = xs[i[ok]]
+            if di != 0:
+                val = val - ux * di / (2.0 * h)
+            else:
+                val = val - uy * dj / (2.0 * h)
+        A[rows, cols] += val
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    g = np.exp(-((X - center[0]) ** 2 + (Y - center[1]) ** 2) / (2.0 * width ** 2)).ravel()
+    y0 = np.tile(g, (batch, 1))
+    m = max(1, int(round(T / (N * dt))))
+    return Workload(f"paper_{pde}_n{n}_N{N}", "dense", M, 1, 0.0, T, N, ("ie", m), ("ie", 1),
+                    y0, A=A, tol=tol, precision=precision)
+
+
 def serving_request(j: int, rate: float = 200.0, seed: int = SEED_SERVING,
                     m1d: Tuple[int, int] = (63, 4095), n2d: Tuple[int, int] = (32, 256),
                     nslices: Tuple[int, int] = (16, 1024),

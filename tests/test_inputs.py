@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_2203_10148_gb300 import inputs
 
@@ -81,3 +82,33 @@ def test_serving_stream():
             assert 32 <= w.nx <= 256 and w.fine[1] >= 50
     again = inputs.serving_stream(count=64)
     np.testing.assert_array_equal(again[17].y0, reqs[17].y0)
+
+
+@pytest.mark.parametrize("pde", ["diffusion", "diffusion_reaction", "advection_diffusion_reaction"])
+def test_paper_pde_operator_is_consistent(pde):
+    """The finite-difference operator of the Sec. 4 test problems applied to
+    f = cos(pi x) cos(pi y) (zero on the boundary of the centred unit square)
+    matches mu Lap f - u . grad f - r f to O(h^2), u = (-y, x)."""
+    mu, r, adv = inputs.PAPER_PDES[pde]
+    errs = []
+    for n in (19, 39):
+        w = inputs.paper_pde(pde, n=n, N=4)
+        h = 1.0 / (n + 1)
+        xs = -0.5 + h * np.arange(1, n + 1)
+        X, Y = np.meshgrid(xs, xs, indexing="xy")
+        f = np.cos(np.pi * X) * np.cos(np.pi * Y)
+        fx = -np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y)
+        fy = -np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+        Lf = -2 * np.pi ** 2 * mu * f - r * f
+        if adv:
+            Lf = Lf - ((-Y) * fx + X * fy)
+        got = (w.A @ f.ravel()).reshape(n, n)
+        errs.append(np.abs(got - Lf).max() / np.abs(Lf).max())
+    assert errs[0] < 5e-3 and errs[1] < errs[0] / 3.0     # second order
+
+
+def test_paper_pde_shapes_and_steps():
+    w = inputs.paper_pde("advection_diffusion_reaction", n=49, N=16)
+    assert w.M == 2401 and w.A.shape == (2401, 2401)
+    assert w.fine == ("ie", 400) and w.coarse == ("ie", 1) and w.T == 6.4
+    assert abs(w.y0.max() - 1.0) < 1e-12
