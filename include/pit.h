@@ -371,6 +371,21 @@ typedef struct {
  * (percentiles by nearest rank); reset = 1 starts a new window. */
 pit_status pit_server_stats(pit_server_t server, int reset, pit_server_stats_t *out);
 
+/*
+ * A time-independent source: the problem becomes y' = L y + f (eq. (1) with
+ * f != 0), f holding batch * M values (host or device; NULL removes the
+ * source).  The fine propagator is then affine, F_f(x) = F(x) + c with
+ * c = F_f(0), so the rows n >= 1 of eq. (4) read lambda_n - F(lambda_{n-1})
+ * = c and B = (y0, c, ..., c); the Krylov operator G^{-1} F stays linear.
+ * c is computed here in FP64 as y* - F(y*) from the steady state y*
+ * (L y* = -f), which both fine steppers keep fixed.  Afterwards every
+ * residual, right-hand side and serial trajectory includes the source.
+ * Supported for PIT_OP_HEAT1D, PIT_OP_HEAT2D (nu > 0) and PIT_OP_DENSE (A
+ * invertible).  Synchronous.
+ * Errors: PIT_E_INVALID, PIT_E_NONFINITE, PIT_E_UNSUPPORTED, PIT_E_CUDA.
+ */
+pit_status pit_problem_set_source(pit_problem_t prob, const double *f, int on_device);
+
 /* ---------------------------------------------------------- diagnostics */
 
 /* Number of kernels libpit has launched in this process (all problems). */

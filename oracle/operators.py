@@ -8,7 +8,8 @@ product path never calls it.  It shares no code with the CUDA library.
 Every function names the passage of Riahi, "PiTSBiCG: Parallel in Time Stable
 Bi-Conjugate Gradient Algorithm" (arXiv 2203.10148) it follows:
 
-* Sec. 2, eq. (1): the Cauchy problem y' = A y (+ f) on [0, T];
+* Sec. 2, eq. (1): the Cauchy problem y' = A y + f on [0, T] (f a
+  time-independent source, 0 unless given);
 * Sec. 2, eq. (2): N equal slices, each started from lambda_n;
 * Sec. 2, eq. (3): continuity lambda_{n+1} = F(lambda_n);
 * Sec. 2, eq. (4): the all-at-once block bidiagonal system  F Lambda = B;
@@ -113,8 +114,9 @@ def _identity_like(L):
     return sp.identity(n, format="csc") if sp.issparse(L) else np.eye(n)
 
 
-def implicit_euler_propagator(L, dT: float, steps: int) -> Propagator:
-    """u <- (I - dt L)^{-1} u, repeated ``steps`` times with dt = dT/steps.
+def implicit_euler_propagator(L, dT: float, steps: int, source=None) -> Propagator:
+    """u <- (I - dt L)^{-1} (u + dt f), repeated ``steps`` times with dt = dT/steps
+    (f = 0 without a source: the linear propagator).
 
     Acts on the rows of a (k, M) array.  The linear solve uses a direct LU
     factorisation (SuperLU for sparse L, LAPACK for dense L).
@@ -128,26 +130,30 @@ def implicit_euler_propagator(L, dT: float, steps: int) -> Propagator:
         fac = sla.lu_factor(Msys)
         solve = lambda rhs: sla.lu_solve(fac, rhs)
 
+    f = None if source is None else np.asarray(source, dtype=np.float64).reshape(-1, 1)
+
     def apply(X: np.ndarray) -> np.ndarray:
         U = np.array(X, dtype=np.float64).T.copy()    # (M, k): one state per column
         for _ in range(steps):
-            U = solve(U)
+            U = solve(U if f is None else U + dt * f)
         return U.T.copy()
 
     return apply
 
 
-def rk4_propagator(L, dT: float, steps: int) -> Propagator:
-    """Classical four-stage Runge-Kutta (stage form) for u' = L u, dt = dT/steps."""
+def rk4_propagator(L, dT: float, steps: int, source=None) -> Propagator:
+    """Classical four-stage Runge-Kutta (stage form) for u' = L u + f, dt = dT/steps
+    (f = 0 without a source)."""
     dt = dT / steps
+    f = 0.0 if source is None else np.asarray(source, dtype=np.float64).reshape(-1, 1)
 
     def apply(X: np.ndarray) -> np.ndarray:
         U = np.array(X, dtype=np.float64).T.copy()
         for _ in range(steps):
-            k1 = L @ U
-            k2 = L @ (U + 0.5 * dt * k1)
-            k3 = L @ (U + 0.5 * dt * k2)
-            k4 = L @ (U + dt * k3)
+            k1 = L @ U + f
+            k2 = L @ (U + 0.5 * dt * k1) + f
+            k3 = L @ (U + 0.5 * dt * k2) + f
+            k4 = L @ (U + dt * k3) + f
             U = U + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
         return U.T.copy()
 
@@ -201,13 +207,19 @@ class OracleProblem:
     """
 
     def __init__(self, fine: Propagator, coarse: Propagator, y0: np.ndarray, N: int,
-                 T: float = 1.0, L=None):
+                 T: float = 1.0, L=None, fine_forced: Optional[Propagator] = None):
         self.F = fine
         self.G = coarse
         self.y0 = np.asarray(y0, dtype=np.float64).reshape(-1)
         self.N = int(N)
         self.T = float(T)
         self.M = self.y0.size
+        # A source f (eq. (1)) makes the fine propagator affine,
+        # F_f(lam) = F(lam) + c with c = F_f(0), the same for every slice of a
+        # time-independent source; the rows n >= 1 of eq. (4) then read
+        # lam_n - F(lam_{n-1}) = c.
+        self.F_forced = fine_forced
+        self.c = None if fine_forced is None else fine_forced(np.zeros((1, self.M)))[0]
         self.L = L
 
     @classmethod
@@ -232,7 +244,16 @@ class OracleProblem:
             raise ValueError(ck)
         y0 = np.asarray(w.y0)
         y0 = y0[member] if y0.ndim == 2 else y0
-        return cls(F, G, y0, w.N, w.T, L)
+        Ff = None
+        src = getattr(w, "f", None)
+        if src is not None:
+            src = np.asarray(src)
+            src = src[member] if src.ndim == 2 else src
+            if fk == "ie":
+                Ff = implicit_euler_propagator(L, dT, fm, source=src)
+            else:
+                Ff = rk4_propagator(L, dT, fm, source=src)
+        return cls(F, G, y0, w.N, w.T, L, fine_forced=Ff)
 
     @classmethod
     def from_propagators(cls, Phi_F: np.ndarray, Phi_G: np.ndarray, y0, N: int) -> "OracleProblem":
@@ -243,9 +264,12 @@ class OracleProblem:
         return np.zeros((self.N + 1, self.M))
 
     def rhs(self) -> np.ndarray:
-        """B = (y0, 0, ..., 0), the right-hand side of eq. (4)."""
+        """B = (y0, 0, ..., 0), the right-hand side of eq. (4); with a source
+        B = (y0, c, ..., c)."""
         B = self.zeros()
         B[0] = self.y0
+        if self.c is not None:
+            B[1:] = self.c
         return B
 
     def apply_F(self, Lam: np.ndarray) -> np.ndarray:
@@ -278,11 +302,13 @@ class OracleProblem:
 
     def serial_fine(self) -> np.ndarray:
         """lam_0 = y0, lam_n = F(lam_{n-1}): the serial fine trajectory, which is
-        F^{-1} B by the forward substitution of eq. (7), left."""
+        F^{-1} B by the forward substitution of eq. (7), left.  With a source
+        the affine fine propagator itself is stepped (not F + c)."""
+        F = self.F if self.F_forced is None else self.F_forced
         Lam = self.zeros()
         Lam[0] = self.y0
         for n in range(1, self.N + 1):
-            Lam[n] = self.F(Lam[n - 1][None, :])[0]
+            Lam[n] = F(Lam[n - 1][None, :])[0]
         return Lam
 
     def coarse_prediction(self) -> np.ndarray:

@@ -187,14 +187,17 @@ static int sweep_cls(int prec) { return prec == PIT_MIXED ? PIT_TIME_SWEEP_MIXED
 pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                       const MemberState *st, cudaStream_t s) {
     if (prec == PIT_FF && p->kind == PIT_OP_HEAT1D) prec = PIT_FP64;
+    pit_status st_ = PIT_E_INVALID;
     switch (p->kind) {
-    case PIT_OP_HEAT1D: return heat1d_apply_F(p, x, y, mode, prec, st, s);
-    case PIT_OP_HEAT2D: return heat2d_apply_F(p, x, y, mode, prec, st, s);
-    case PIT_OP_ADVDIFF2D: return advdiff_apply_F(p, x, y, mode, prec, st, s);
-    case PIT_OP_DENSE: return dense_apply_F(p, x, y, mode, prec, st, s);
+    case PIT_OP_HEAT1D: st_ = heat1d_apply_F(p, x, y, mode, prec, st, s); break;
+    case PIT_OP_HEAT2D: st_ = heat2d_apply_F(p, x, y, mode, prec, st, s); break;
+    case PIT_OP_ADVDIFF2D: st_ = advdiff_apply_F(p, x, y, mode, prec, st, s); break;
+    case PIT_OP_DENSE: st_ = dense_apply_F(p, x, y, mode, prec, st, s); break;
+    default: set_error("unknown operator kind"); return PIT_E_INVALID;
     }
-    set_error("unknown operator kind");
-    return PIT_E_INVALID;
+    // residual B - F x with a source: rows n >= 1 gain c (F_f(x) = F(x) + c)
+    if (st_ == PIT_OK && p->has_src && mode == FINE_RESIDUAL) st_ = add_source_rows(p, y, s);
+    return st_;
 }
 
 pit_status op_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
@@ -222,17 +225,130 @@ static pit_status fine_one(Problem *p, const double *x, double *y, int prec, cud
 }
 
 // y = B for every member: block 0 = y0, other blocks 0.
+// y[b][n][i] += c[b][i] for blocks n in [n0, n1) of every member
+__global__ void k_add_source(double *y, const double *c, int M, int n0, int n1, size_t blen,
+                             int batch) {
+    const size_t per = (size_t)(n1 - n0) * M;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < per * batch;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = t / per, r = t % per;
+        const size_t n = n0 + r / M, i = r % M;
+        y[b * blen + n * M + i] += c[b * M + i];
+    }
+}
+
+static pit_status add_source_blocks(Problem *p, double *y, int n0, int n1, cudaStream_t s) {
+    const size_t work = (size_t)(n1 - n0) * p->M * p->batch;
+    const int blocks = (int)std::min<size_t>((work + 255) / 256, 152 * 8);
+    if (work == 0) return PIT_OK;
+    k_add_source<<<blocks, 256, 0, s>>>(y, p->cvec.as<double>(), p->M, n0, n1, p->blen, p->batch);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
+pit_status add_source_rows(Problem *p, double *y, cudaStream_t s) {
+    return add_source_blocks(p, y, 1, p->N + 1, s);
+}
+
+// B = (y0, 0, ..., 0), or (y0, c, ..., c) with a source (rows n >= 1 of eq. (4))
 pit_status build_rhs(Problem *p, double *B, cudaStream_t s) {
     PIT_CUDA(cudaMemsetAsync(B, 0, p->vlen * sizeof(double), s));
     PIT_CUDA(cudaMemcpy2DAsync(B, p->blen * sizeof(double), p->y0.ptr, p->M * sizeof(double),
                                p->M * sizeof(double), p->batch, cudaMemcpyDeviceToDevice, s));
+    if (p->has_src) PIT_TRY(add_source_rows(p, B, s));
     return PIT_OK;
 }
 
 pit_status op_serial(Problem *p, double *Lam, int prec, cudaStream_t s) {
     PIT_TRY(build_rhs(p, Lam, s));
-    for (int n = 1; n <= p->N; ++n)
+    for (int n = 1; n <= p->N; ++n) {
         PIT_TRY(fine_one(p, Lam + (size_t)(n - 1) * p->M, Lam + (size_t)n * p->M, prec, s));
+        // with a source: lam_n = F(lam_{n-1}) + c
+        if (p->has_src) PIT_TRY(add_source_blocks(p, Lam, n, n + 1, s));
+    }
+    return PIT_OK;
+}
+
+// The offset c = F_f(0) of a source f (time-independent, y' = L y + f): both
+// steppers keep the steady state y* (L y* = -f) fixed, and F_f(x) - y* =
+// F(x - y*), so c = y* - F(y*) with the linear fine propagator F (FP64).
+// y*: Thomas solve (1D heat), sine-basis solve (2D heat), LU (dense).
+pit_status source_offset(Problem *p, const double *f) {
+    const int M = p->M, B = p->batch;
+    std::vector<double> ys((size_t)B * M, 0.0);
+    if (p->kind == PIT_OP_HEAT1D || p->kind == PIT_OP_HEAT2D) {
+        if (!(p->nu > 0.0)) {
+            set_error("source: nu = 0 leaves no steady state");
+            return PIT_E_UNSUPPORTED;
+        }
+    }
+    if (p->kind == PIT_OP_HEAT1D) {
+        // (nu/h^2)(y_{i-1} - 2 y_i + y_{i+1}) = -f_i, y_{-1} = y_M = 0
+        const double h = 1.0 / (M + 1), k = p->nu / (h * h);
+        std::vector<double> cp(M), dp(M);
+        for (int b = 0; b < B; ++b) {
+            const double *fb = f + (size_t)b * M;
+            for (int i = 0; i < M; ++i) {
+                const double den = -2.0 * k - (i > 0 ? k * cp[i - 1] : 0.0);
+                cp[i] = k / den;
+                dp[i] = (-fb[i] - (i > 0 ? k * dp[i - 1] : 0.0)) / den;
+            }
+            double *yb = ys.data() + (size_t)b * M;
+            yb[M - 1] = dp[M - 1];
+            for (int i = M - 2; i >= 0; --i) yb[i] = dp[i] - cp[i] * yb[i + 1];
+        }
+    } else if (p->kind == PIT_OP_HEAT2D) {
+        // sine basis: Fh = S F S, Yh = -Fh / (nu (mu_a + mu_b)), Y = (2/(n+1))^2 S Yh S
+        const int n = p->nx;
+        const double h = 1.0 / (n + 1);
+        std::vector<double> S((size_t)n * n), mu(n), T1((size_t)n * n), T2((size_t)n * n);
+        for (int a = 0; a < n; ++a) {
+            for (int j = 0; j < n; ++j)
+                S[(size_t)a * n + j] = sin(M_PI * (double)(a + 1) * (double)(j + 1) / (n + 1));
+            const double sk = sin(M_PI * (a + 1) * h / 2.0);
+            mu[a] = -4.0 / (h * h) * sk * sk;
+        }
+        auto mul = [&](const double *X, const double *Y, double *Z) {   // Z = X Y (n x n)
+            for (int r = 0; r < n; ++r)
+                for (int c = 0; c < n; ++c) {
+                    double acc = 0.0;
+                    for (int k2 = 0; k2 < n; ++k2) acc += X[(size_t)r * n + k2] * Y[(size_t)k2 * n + c];
+                    Z[(size_t)r * n + c] = acc;
+                }
+        };
+        const double sc = (2.0 / (n + 1)) * (2.0 / (n + 1));
+        for (int b = 0; b < B; ++b) {
+            mul(S.data(), f + (size_t)b * M, T1.data());
+            mul(T1.data(), S.data(), T2.data());
+            for (int a = 0; a < n; ++a)
+                for (int c = 0; c < n; ++c) T2[(size_t)a * n + c] *= -1.0 / (p->nu * (mu[a] + mu[c]));
+            mul(S.data(), T2.data(), T1.data());
+            mul(T1.data(), S.data(), ys.data() + (size_t)b * M);
+            for (int i = 0; i < M; ++i) ys[(size_t)b * M + i] *= sc;
+        }
+    } else if (p->kind == PIT_OP_DENSE) {
+        PIT_TRY(dense_steady_state(p, f, ys.data()));
+    } else {
+        set_error("source: supported for HEAT1D, HEAT2D and DENSE");
+        return PIT_E_UNSUPPORTED;
+    }
+    // F(y*) on the device: y* in block 0 of each member, F(y*) into block 1
+    cudaStream_t s = p->stream;
+    DevBuf tmp;
+    PIT_TRY(tmp.ensure(p->vlen * sizeof(double)));
+    PIT_CUDA(cudaMemsetAsync(tmp.ptr, 0, p->vlen * sizeof(double), s));
+    PIT_CUDA(cudaMemcpy2DAsync(tmp.ptr, p->blen * sizeof(double), ys.data(), M * sizeof(double),
+                               M * sizeof(double), B, cudaMemcpyHostToDevice, s));
+    PIT_TRY(fine_one(p, tmp.as<double>(), tmp.as<double>() + M, PIT_FP64, s));
+    std::vector<double> fy((size_t)B * M);
+    PIT_CUDA(cudaMemcpy2DAsync(fy.data(), M * sizeof(double), tmp.as<double>() + M,
+                               p->blen * sizeof(double), M * sizeof(double), B,
+                               cudaMemcpyDeviceToHost, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < fy.size(); ++i) fy[i] = ys[i] - fy[i];
+    PIT_TRY(p->cvec.ensure((size_t)B * M * sizeof(double)));
+    PIT_CUDA(cudaMemcpyAsync(p->cvec.ptr, fy.data(), fy.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
     return PIT_OK;
 }
 
@@ -673,7 +789,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
     DevBuf *bufs[] = {&p->y0, &p->fine_inv64, &p->fine_cp64, &p->coarse_inv64, &p->coarse_cp64,
                       &p->fine_inv32, &p->fine_cp32, &p->coarse_inv32, &p->coarse_cp32,
                       &p->S64, &p->S32, &p->gmode, &p->hat, &p->vx64, &p->vy64, &p->vx32,
-                      &p->vy32, &p->vxff, &p->vyff, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
+                      &p->vy32, &p->vxff, &p->vyff, &p->A64, &p->cvec, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32,
@@ -996,6 +1112,34 @@ pit_status pit_problem_set_y0(pit_problem_t h, const double *y0, int on_device) 
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              p->stream));
     PIT_CUDA(cudaStreamSynchronize(p->stream));
+    return PIT_OK;
+}
+
+pit_status pit_problem_set_source(pit_problem_t h, const double *f, int on_device) {
+    if (!h) {
+        set_error("pit_problem_set_source: null problem");
+        return PIT_E_INVALID;
+    }
+    Problem *p = &h->p;
+    PIT_CUDA(cudaSetDevice(p->device));
+    if (!f) {
+        p->has_src = false;
+        return PIT_OK;
+    }
+    const size_t n = (size_t)p->M * p->batch;
+    std::vector<double> fh(n);
+    if (on_device) {
+        PIT_CUDA(cudaMemcpy(fh.data(), f, n * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        std::copy(f, f + n, fh.begin());
+    }
+    if (!all_finite(fh.data(), n)) {
+        set_error("pit_problem_set_source: non-finite value in f");
+        return PIT_E_NONFINITE;
+    }
+    p->has_src = false;
+    PIT_TRY(source_offset(p, fh.data()));
+    p->has_src = true;
     return PIT_OK;
 }
 

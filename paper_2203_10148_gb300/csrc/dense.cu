@@ -632,6 +632,8 @@ pit_status dense_setup(Problem *p) {
     DevBuf work;
     PIT_TRY(work.ensure(5 * mm2 * sizeof(double) + 64));
     double *A = p->PhiF64.as<double>();      // staged by pit_problem_create
+    PIT_TRY(p->A64.ensure(mm2 * sizeof(double)));
+    PIT_CUDA(cudaMemcpyAsync(p->A64.ptr, A, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
     double *T1 = work.as<double>(), *T2 = T1 + mm2, *T3 = T2 + mm2, *T4 = T3 + mm2;
     double *T5 = T4 + mm2;
     double *scal = T5 + mm2;
@@ -825,6 +827,7 @@ static pit_status dense_product(Problem *p, const double *x, int prec, const Mem
 pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                          const MemberState *st, cudaStream_t s) {
     if (prec == PIT_MIXED && p->use_tc) return dense_tc_apply(p, x, y, nullptr, mode, st, s);
+    // (the source rows of a residual are added by the caller)
     PIT_TRY(dense_product(p, x, prec, st, s));
     int blocks;
     grid_for(p->blen, blocks);
@@ -850,6 +853,49 @@ pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cuda
     const double one = 1.0, zero = 0.0;
     PIT_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, p->batch, M, &one, p->PhiF64.as<double>(),
                            M, x, (int)p->blen, &zero, y, (int)p->blen));
+    return PIT_OK;
+}
+
+// Steady states y* with A y* = -f for every member (f_host, ys_host: batch
+// x M): LU factorisation of A with partial pivoting (cuBLAS, FP64) and two
+// triangular solves per member.
+pit_status dense_steady_state(Problem *p, const double *f_host, double *ys_host) {
+    const int M = p->M, B = p->batch;
+    const size_t mm2 = (size_t)M * M;
+    cublasHandle_t h = handle(p);
+    cudaStream_t s = p->stream;
+    PIT_CUBLAS(cublasSetStream(h, s));
+    DevBuf lu, rhs, piv, ptrs, info;
+    PIT_TRY(lu.ensure(mm2 * sizeof(double)));
+    PIT_TRY(rhs.ensure((size_t)B * M * sizeof(double)));
+    PIT_TRY(piv.ensure((size_t)M * sizeof(int)));
+    PIT_TRY(ptrs.ensure(2 * sizeof(double *)));
+    PIT_TRY(info.ensure(sizeof(int)));
+    // row-major A is the column-major A^T: factor A^T and solve A^T' y = b
+    // with the transposed solve (op = T)
+    PIT_CUDA(cudaMemcpyAsync(lu.ptr, p->A64.ptr, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    std::vector<double> negf((size_t)B * M);
+    for (size_t i = 0; i < negf.size(); ++i) negf[i] = -f_host[i];
+    PIT_CUDA(cudaMemcpyAsync(rhs.ptr, negf.data(), negf.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    double *hp[2] = {lu.as<double>(), rhs.as<double>()};
+    PIT_CUDA(cudaMemcpyAsync(ptrs.ptr, hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    double **dA = reinterpret_cast<double **>(ptrs.ptr);
+    PIT_CUBLAS(cublasDgetrfBatched(h, M, dA, M, piv.as<int>(), info.as<int>(), 1));
+    int hinfo = 0;
+    PIT_CUDA(cudaMemcpyAsync(&hinfo, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
+    if (hinfo != 0) {
+        set_error("dense: A is singular, the source has no steady state");
+        return PIT_E_UNSUPPORTED;
+    }
+    int sinfo = 0;
+    PIT_CUBLAS(cublasDgetrsBatched(h, CUBLAS_OP_T, M, B, dA, M, piv.as<int>(), dA + 1, M, &sinfo, 1));
+    PIT_CUDA(cudaMemcpyAsync(ys_host, rhs.ptr, (size_t)B * M * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PIT_CUDA(cudaStreamSynchronize(s));
+    if (sinfo != 0) {
+        set_error("dense: steady-state solve failed");
+        return PIT_E_CUDA;
+    }
     return PIT_OK;
 }
 

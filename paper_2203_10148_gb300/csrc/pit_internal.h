@@ -168,6 +168,11 @@ struct Problem {
 
     // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)
     DevBuf PhiF64, G64, PhiF_hi, PhiF_lo, G32;
+    DevBuf A64;                   // dense: a copy of A (steady states of a source)
+    // source f of y' = L y + f (time-independent): the fine propagator is
+    // affine, F_f(x) = F(x) + c, c = F_f(0) per member (batch x M, FP64)
+    DevBuf cvec;
+    bool has_src = false;
     DevBuf dense_scratch;
     void *blas = nullptr;         // cuBLAS handle (dense set-up and FP64 products)
     DevBuf GL32;                  // G^L (FP32) for the chunked dense sweep
@@ -238,6 +243,11 @@ pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int p
 pit_status dense_sweep(Problem *p, const double *q, double *z, int prec,
                        const MemberState *st, cudaStream_t s);
 pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s);
+pit_status dense_steady_state(Problem *p, const double *f_host, double *ys_host);
+// c = F_f(0) per member for a source f (host, batch x M); see source.cu
+pit_status source_offset(Problem *p, const double *f_host);
+// y[b][n][:] += c[b][:] for n = 1..N of every member (forced rows of eq. (4))
+pit_status add_source_rows(Problem *p, double *y, cudaStream_t s);
 void dense_teardown(Problem *p);
 bool dense_tc_supported(const Problem *p);
 pit_status dense_tc_split_phi(Problem *p);

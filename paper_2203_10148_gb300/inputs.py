@@ -117,6 +117,7 @@ class Workload:
     tol: float = 1e-6
     precision: str = "fp64"
     arrival: float = 0.0
+    f: Optional[np.ndarray] = None     # time-independent source (batch, M) of y' = L y + f
 
     @property
     def M(self) -> int:
@@ -131,7 +132,8 @@ class Workload:
         return self.T / self.N
 
     def member(self, b: int) -> "Workload":
-        return dataclasses.replace(self, y0=self.y0[b:b + 1].copy())
+        return dataclasses.replace(self, y0=self.y0[b:b + 1].copy(),
+                                   f=None if self.f is None else self.f[b:b + 1].copy())
 
     def describe(self) -> dict:
         return {"workload": self.name, "kind": self.kind, "grid": [self.nx, self.ny],
@@ -238,6 +240,32 @@ def dense(M: int = 1024, T: float = 10.0, N: int = 4096, fine_steps: int = 200,
     y0 = np.stack([s.normal(M) for _ in range(batch)])
     return Workload(f"dense_M{M}_N{N}", "dense", M, 1, 0.0, T, N, ("rk4", fine_steps),
                     ("ie", coarse_steps), y0, A=A, tol=tol, precision=precision)
+
+
+def with_source(w: Workload, seed: int = 0x50495405, amplitude: float = 1.0) -> Workload:
+    """The workload with a seeded smooth time-independent source f (one per
+    member): a few products of sine modes for grids, normal values scaled by
+    1/sqrt(M) for dense operators."""
+    s = SeededStream(seed)
+    if w.kind in ("heat2d", "advdiff2d"):
+        n = w.nx
+        xs = np.arange(1, n + 1) / (n + 1.0)
+        fs = []
+        for _ in range(w.batch):
+            kx = s.integers(1, 5, 3)
+            ky = s.integers(1, 5, 3)
+            a = s.normal(3)
+            g = sum(a[i] * np.outer(np.sin(ky[i] * np.pi * xs), np.sin(kx[i] * np.pi * xs))
+                    for i in range(3))
+            fs.append(g.ravel())
+        f = np.stack(fs)
+    elif w.kind == "heat1d":
+        xs = np.arange(1, w.M + 1) / (w.M + 1.0)
+        f = np.stack([sum(s.normal(1)[0] * np.sin(k * np.pi * xs) for k in (1, 2, 5))
+                      for _ in range(w.batch)])
+    else:
+        f = s.normal(w.batch * w.M).reshape(w.batch, w.M) / math.sqrt(w.M)
+    return dataclasses.replace(w, f=amplitude * f, name=w.name + "_forced")
 
 
 # The three test problems of Sec. 4 (eq. (9), read as

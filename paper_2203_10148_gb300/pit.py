@@ -102,7 +102,8 @@ EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_cre
            "pit_problem_set_y0", "pit_kernel_launches", "pit_set_timing", "pit_get_timing",
            "pit_block_reduce_noalloc", "pit_selftest_convert", "pit_server_create",
            "pit_server_destroy", "pit_serve_submit", "pit_serve_poll", "pit_serve_wait",
-           "pit_serve_cancel", "pit_serve_footprint", "pit_server_stats"]
+           "pit_serve_cancel", "pit_serve_footprint", "pit_server_stats",
+           "pit_problem_set_source"]
 
 TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4,
                 "fine_ff": 5}
@@ -138,6 +139,7 @@ def load() -> C.CDLL:
     lib.pit_block_reduce.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
     lib.pit_block_reduce_noalloc.argtypes = [P, P, C.c_int, C.c_int, P, P, P]
     lib.pit_problem_set_y0.argtypes = [P, P, C.c_int]
+    lib.pit_problem_set_source.argtypes = [P, P, C.c_int]
     lib.pit_selftest_convert.argtypes = [P, C.c_int, P, P]
     lib.pit_kernel_launches.argtypes = []
     lib.pit_kernel_launches.restype = C.c_ulonglong
@@ -243,6 +245,8 @@ class Problem:
         h = C.c_void_p()
         check(lib.pit_problem_create(C.byref(desc), C.byref(h)))
         self.handle = h
+        if getattr(w, "f", None) is not None:
+            self.set_source(np.ascontiguousarray(np.asarray(w.f, dtype=np.float64).reshape(w.batch, -1)))
         self.M, self.N, self.batch = w.M, w.N, w.batch
         self.shape = (self.batch, self.N + 1, self.M)
         self._keep = []
@@ -323,6 +327,14 @@ class Problem:
         p, dev, _ = _array_arg(y0)
         check(load().pit_problem_set_y0(self.handle, p, dev))
 
+    def set_source(self, f):
+        """pit_problem_set_source: time-independent source (batch x M) or None."""
+        if f is None:
+            check(load().pit_problem_set_source(self.handle, None, 0))
+            return
+        p, dev, _ = _array_arg(f)
+        check(load().pit_problem_set_source(self.handle, p, dev))
+
     def set_timing(self, enable: bool = True):
         check(load().pit_set_timing(self.handle, int(enable)))
 
@@ -375,6 +387,8 @@ class Server:
 
     def submit(self, w, precision: Optional[str] = None, **opts) -> int:
         """Queues workload ``w`` with solve options (as Problem.bicgstab_solve); a ticket."""
+        if getattr(w, "f", None) is not None:
+            raise ValueError("the server takes problems without a source term")
         desc, keep = problem_desc(w, PRECISION[precision or w.precision])
         o = solve_opts(**opts)
         t = C.c_uint64()

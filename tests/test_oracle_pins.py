@@ -345,3 +345,44 @@ def test_parareal_matches_predictor_corrector_eq5():
         X, _ = parareal(prob, kmax=k + 1)
         np.testing.assert_allclose(X, nxt, atol=1e-13)
         prev = nxt
+
+
+# ------------------------------------------------------------ sources (f != 0)
+def test_forced_scalar_closed_forms():
+    """y' = a y + b from 0 over one slice: implicit Euler gives
+    y* (1 - (1 - a dt)^(-m)) and RK4 gives y* (1 - R(a dt)^m), y* = -b/a
+    (both methods keep the steady state y* exactly)."""
+    from oracle.operators import implicit_euler_propagator, rk4_propagator
+    a, b, dT, m = -3.0, 0.7, 0.4, 9
+    dt = dT / m
+    ys = -b / a
+    L = np.array([[a]])
+    c_ie = implicit_euler_propagator(L, dT, m, source=[b])(np.zeros((1, 1)))[0, 0]
+    assert c_ie == pytest.approx(ys * (1 - (1 - a * dt) ** (-m)), rel=1e-13)
+    z = a * dt
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    c_rk = rk4_propagator(L, dT, m, source=[b])(np.zeros((1, 1)))[0, 0]
+    assert c_rk == pytest.approx(ys * (1 - R ** m), rel=1e-12)
+    # the steady state is a fixed point of both
+    assert implicit_euler_propagator(L, dT, m, source=[b])(np.array([[ys]]))[0, 0] == pytest.approx(ys, rel=1e-14)
+    assert rk4_propagator(L, dT, m, source=[b])(np.array([[ys]]))[0, 0] == pytest.approx(ys, rel=1e-14)
+
+
+@pytest.mark.parametrize("fine", [("ie", 7), ("rk4", 5)])
+def test_forced_system_solution_is_forced_serial_trajectory(fine):
+    """With a source, the solution of F Lambda = B (B = (y0, c, ..., c)),
+    solved densely, is the serial trajectory of the affine fine propagator,
+    and parareal reaches it after N corrections."""
+    w = inputs.with_source(inputs.heat1d(M=9, N=6, fine_steps=fine[1]))
+    w.fine = fine
+    o = OracleProblem.from_workload(w)
+    lam = o.serial_fine()
+    n = (w.N + 1) * w.M
+    E = np.eye(n)
+    Fm = np.stack([o.apply_F(E[i].reshape(w.N + 1, w.M)).ravel() for i in range(n)], axis=1)
+    X = np.linalg.solve(Fm, o.rhs().ravel()).reshape(w.N + 1, w.M)
+    assert np.abs(X - lam).max() <= 1e-12 * np.abs(lam).max()
+    Xp, _ = parareal(o, kmax=w.N)
+    assert np.abs(Xp - lam).max() <= 1e-12 * np.abs(lam).max()
+    Xb, info = pitsbicg(o, tol=1e-13)
+    assert np.abs(Xb - lam).max() <= 1e-10 * np.abs(lam).max()
