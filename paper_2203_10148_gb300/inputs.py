@@ -278,10 +278,56 @@ PAPER_PDES = {
 }
 
 
+def fem_p1_matrices(n: int, velocity: bool):
+    """P1 finite elements on the centred unit square: n x n interior nodes of a
+    uniform grid (h = 1/(n+1)), every cell cut along its diagonal from
+    (x_i, y_j) to (x_i + h, y_j + h).  Returns the mass matrix Mm, the
+    stiffness matrix K and the convection matrix C (C_ij = int phi_i u . grad
+    phi_j with u = (-y, x), three-midpoint quadrature, exact here), all on the
+    interior nodes (Dirichlet 0), dense, row-major node order j * n + i."""
+    h = 1.0 / (n + 1)
+    nn = n + 2                                   # nodes per side with the boundary
+    xs = -0.5 + h * np.arange(nn)
+    full = nn * nn
+    Mm = np.zeros((full, full))
+    K = np.zeros((full, full))
+    C = np.zeros((full, full))
+    area = h * h / 2.0
+    Me = area / 12.0 * np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]])
+
+    def add(nodes):
+        P = np.array([[xs[i], xs[j]] for (i, j) in nodes])
+        Bm = np.array([P[1] - P[0], P[2] - P[0]]).T          # columns: edges
+        Binv = np.linalg.inv(Bm)
+        # gradients of the barycentric functions
+        g = np.array([-Binv[0] - Binv[1], Binv[0], Binv[1]])
+        Ke = area * (g @ g.T)
+        idx = [j * nn + i for (i, j) in nodes]
+        Mm[np.ix_(idx, idx)] += Me
+        K[np.ix_(idx, idx)] += Ke
+        if velocity:
+            mids = [(P[0] + P[1]) / 2, (P[1] + P[2]) / 2, (P[2] + P[0]) / 2]
+            lam = [np.array([0.5, 0.5, 0.0]), np.array([0.0, 0.5, 0.5]), np.array([0.5, 0.0, 0.5])]
+            Ce = np.zeros((3, 3))
+            for q in range(3):
+                ux, uy = -mids[q][1], mids[q][0]
+                adv = g @ np.array([ux, uy])                 # u . grad phi_j
+                Ce += (area / 3.0) * np.outer(lam[q], adv)
+            C[np.ix_(idx, idx)] += Ce
+
+    for j in range(nn - 1):
+        for i in range(nn - 1):
+            add([(i, j), (i + 1, j), (i + 1, j + 1)])
+            add([(i, j), (i + 1, j + 1), (i, j + 1)])
+    inner = np.array([j * nn + i for j in range(1, nn - 1) for i in range(1, nn - 1)])
+    sel = np.ix_(inner, inner)
+    return Mm[sel], K[sel], C[sel]
+
+
 def paper_pde(pde: str = "diffusion", n: int = 49, N: int = 4, T: float = 6.4,
               dt: float = 1e-3, center: Tuple[float, float] = (0.2, 0.0),
               width: float = 0.1, batch: int = 1, tol: float = 1e-10,
-              precision: str = "fp64") -> Workload:
+              precision: str = "fp64", discretization: str = "fd") -> Workload:
     """A Sec. 4 test problem as a dense-operator workload.
 
     Unit square centred at the origin, n x n interior points of a grid with
@@ -292,12 +338,26 @@ def paper_pde(pde: str = "diffusion", n: int = 49, N: int = 4, T: float = 6.4,
     backward Euler with the paper's dt = 1e-3 (round(T / (N dt)) steps per
     slice); coarse: one backward-Euler step per slice.  y0: a Gaussian of
     standard deviation `width` at `center` (off the centre, so that the
-    rotation moves it).
+    rotation moves it).  discretization = "fem": P1 finite elements (the
+    paper's discretisation, `fem_p1_matrices`), the semi-discrete system
+    Mm y' = -(mu K + C + r Mm) y written as y' = A y with
+    A = -Mm^{-1}(mu K + C) - r I, so that backward Euler on it is the
+    mass-matrix step (Mm + dt (mu K + C + r Mm)) y+ = Mm y.
     """
     mu, r, adv = PAPER_PDES[pde]
     h = 1.0 / (n + 1)
     xs = -0.5 + h * np.arange(1, n + 1)
     M = n * n
+    if discretization == "fem":
+        Mm, K, C = fem_p1_matrices(n, adv)
+        A = -np.linalg.solve(Mm, mu * K + C) - r * np.eye(M)
+        X, Y = np.meshgrid(xs, xs, indexing="xy")
+        g = np.exp(-((X - center[0]) ** 2 + (Y - center[1]) ** 2) / (2.0 * width ** 2)).ravel()
+        m = max(1, int(round(T / (N * dt))))
+        return Workload(f"paper_{pde}_fem_n{n}_N{N}", "dense", M, 1, 0.0, T, N, ("ie", m),
+                        ("ie", 1), np.tile(g, (batch, 1)), A=A, tol=tol, precision=precision)
+    if discretization != "fd":
+        raise ValueError(discretization)
     A = np.zeros((M, M))
     idx = np.arange(M).reshape(n, n)          # idx[j, i]: point (x_i, y_j)
     diag = -4.0 * mu / h ** 2 - r

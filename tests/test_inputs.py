@@ -112,3 +112,57 @@ def test_paper_pde_shapes_and_steps():
     assert w.M == 2401 and w.A.shape == (2401, 2401)
     assert w.fine == ("ie", 400) and w.coarse == ("ie", 1) and w.T == 6.4
     assert abs(w.y0.max() - 1.0) < 1e-12
+
+
+def test_fem_p1_matrices_exact_properties():
+    """P1 assembly on the uniform triangulation cut along one diagonal has
+    closed forms: K is the 5-point stencil (4 on the diagonal, -1 for the
+    four axis neighbours, 0 for the diagonal ones), Mm has h^2/2 on the
+    diagonal and h^2/12 for each of the six edge neighbours (axis and the
+    (+1, +1) / (-1, -1) diagonal), and the convection matrix of the
+    divergence-free u = (-y, x) is skew-symmetric once Dirichlet nodes are
+    removed."""
+    n = 9
+    Mm, K, C = inputs.fem_p1_matrices(n, True)
+    h = 1.0 / (n + 1)
+    Kx = np.zeros((n * n, n * n))
+    Mx = np.zeros((n * n, n * n))
+    for j in range(n):
+        for i in range(n):
+            r = j * n + i
+            Kx[r, r] = 4.0
+            Mx[r, r] = h * h / 2.0
+            for di, dj, k, m in ((1, 0, -1, 1), (-1, 0, -1, 1), (0, 1, -1, 1), (0, -1, -1, 1),
+                                 (1, 1, 0, 1), (-1, -1, 0, 1)):
+                if 0 <= i + di < n and 0 <= j + dj < n:
+                    Kx[r, (j + dj) * n + i + di] = k
+                    Mx[r, (j + dj) * n + i + di] = m * h * h / 12.0
+    np.testing.assert_allclose(K, Kx, atol=1e-13)
+    np.testing.assert_allclose(Mm, Mx, atol=1e-16)
+    assert np.abs(C + C.T).max() < 1e-14
+    assert np.abs(C).max() > 0.01 * h
+
+
+@pytest.mark.parametrize("pde", ["diffusion", "advection_diffusion_reaction"])
+def test_fem_operator_is_consistent(pde):
+    """-Mm^{-1}(mu K + C) - r applied to cos(pi x) cos(pi y) approaches
+    mu Lap f - u . grad f - r f at second order on the uniform mesh."""
+    mu, r, adv = inputs.PAPER_PDES[pde]
+    errs = []
+    for n in (11, 23):
+        w = inputs.paper_pde(pde, n=n, N=4, discretization="fem")
+        h = 1.0 / (n + 1)
+        xs = -0.5 + h * np.arange(1, n + 1)
+        X, Y = np.meshgrid(xs, xs, indexing="xy")
+        f = np.cos(np.pi * X) * np.cos(np.pi * Y)
+        fx = -np.pi * np.sin(np.pi * X) * np.cos(np.pi * Y)
+        fy = -np.pi * np.cos(np.pi * X) * np.sin(np.pi * Y)
+        Lf = -2 * np.pi ** 2 * mu * f - r * f
+        if adv:
+            Lf = Lf - ((-Y) * fx + X * fy)
+        got = (w.A @ f.ravel()).reshape(n, n)
+        # in the middle half of the square (the consistent mass matrix spreads
+        # the first-order boundary error of the convection term a few rows in)
+        q = n // 4
+        errs.append(np.abs(got - Lf)[q:-q, q:-q].max() / np.abs(Lf).max())
+    assert errs[1] < errs[0] / 3.0 and errs[1] < 5e-3

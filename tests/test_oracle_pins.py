@@ -386,3 +386,23 @@ def test_forced_system_solution_is_forced_serial_trajectory(fine):
     assert np.abs(Xp - lam).max() <= 1e-12 * np.abs(lam).max()
     Xb, info = pitsbicg(o, tol=1e-13)
     assert np.abs(Xb - lam).max() <= 1e-10 * np.abs(lam).max()
+
+
+def test_fem_backward_euler_is_the_mass_matrix_step():
+    """Sec. 4 (FEM, backward Euler): with A = -Mm^{-1}(mu K + C) - r I the
+    oracle's implicit Euler step (I - dt A)^{-1} is the mass-matrix step
+    (Mm + dt (mu K + C + r Mm)) y+ = Mm y, solved here directly from the
+    assembled matrices, and the fine propagator is its m-th power."""
+    from oracle.operators import implicit_euler_propagator
+    n, dt, m = 7, 1e-3, 5
+    for pde in inputs.PAPER_PDES:
+        mu, r, adv = inputs.PAPER_PDES[pde]
+        w = inputs.paper_pde(pde, n=n, N=4, T=4 * m * dt, dt=dt, discretization="fem")
+        assert w.fine == ("ie", m)
+        Mm, K, C = inputs.fem_p1_matrices(n, adv)
+        S = Mm + dt * (mu * K + C + r * Mm)
+        y = w.y0[0]
+        for _ in range(m):
+            y = np.linalg.solve(S, Mm @ y)
+        got = implicit_euler_propagator(w.A, w.T / w.N, m)(w.y0)[0]
+        np.testing.assert_allclose(got, y, rtol=1e-11, atol=1e-14)
