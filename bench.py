@@ -405,7 +405,21 @@ def run_ours(args):
     slice_steps = sum(i["fine_slice_steps"] for inf in infos for i in inf) * world
     # accuracy of the last step against the FP64 serial fine trajectory (FP64 path)
     lam = torch.empty(shape, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t_ser = time.perf_counter()
     prob.serial_fine("fp64", out=lam)
+    torch.cuda.synchronize()
+    t_ser64 = time.perf_counter() - t_ser
+    # the no-PiT comparator: the same trajectory stepped slice after slice
+    # in FP32 (one launch per slice for the whole batch), and its accuracy
+    lam32 = torch.empty(shape, dtype=torch.float64, device=dev)
+    t_ser = time.perf_counter()
+    prob.serial_fine("mixed", out=lam32)
+    torch.cuda.synchronize()
+    t_ser32 = time.perf_counter() - t_ser
+    e32 = (((lam32 - lam).reshape(w.batch, -1).norm(dim=1)
+            / lam.reshape(w.batch, -1).norm(dim=1)).max().item())
+    del lam32
     d = (X - lam).reshape(w.batch, -1)
     rel = (d.norm(dim=1) / lam.reshape(w.batch, -1).norm(dim=1)).max().item()
     relN = ((X[:, -1] - lam[:, -1]).norm(dim=1) / lam[:, -1].norm(dim=1)).max().item()
@@ -437,6 +451,10 @@ def run_ours(args):
                 "refinements": [i["refinements"] for inf in infos for i in inf],
                 "matvecs": [i["matvecs"] for inf in infos for i in inf],
                 "gpu_launches": int(launches), "roofline": roof, "breakdown": breakdown,
+                "serial_fine": {"fp64_s_per_batch": t_ser64, "fp32_s_per_batch": t_ser32,
+                                "fp32_rel_err": e32, "batch": w.batch,
+                                "note": "slice after slice on this GPU (no parallel in time), "
+                                        "one launch per slice for the whole batch"},
                 "clocks": clocks}
         if rel > 1e-6:
             line["invalid"] = f"rel err {rel:.3e} > 1e-6"

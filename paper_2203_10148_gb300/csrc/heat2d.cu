@@ -778,6 +778,20 @@ Heat2dArgs make_args(Problem *p, const double *x, double *y, int mode, const Mem
     return a;
 }
 
+// FP64 -> FP32 (round to nearest, as the transforms' own staging converts)
+// of the running members' blocks, two doubles per thread-iteration; lets an
+// FP64-input sweep use the persistent FP32 transform.
+__global__ void k_d2f_blocks(const double *__restrict__ x, float *__restrict__ y, size_t mlen2,
+                             int batch, const MemberState *st) {
+    const size_t total = mlen2 * (size_t)batch;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        if (!runs(st, (int)(i / mlen2))) continue;
+        const double2 v = reinterpret_cast<const double2 *>(x)[i];
+        reinterpret_cast<float2 *>(y)[i] = make_float2(d2f_rn(v.x), d2f_rn(v.y));
+    }
+}
+
 template <class Tin, class T, class Tout>
 pit_status launch_xS(Problem *p, const Tin *A, Tout *out, const T *S, double scale,
                      const MemberState *st, cudaStream_t s) {
@@ -821,9 +835,41 @@ pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const Member
     T *h1 = p->hat.as<T>();
     T *h2 = h1 + hat_elems;
     double *ends = reinterpret_cast<double *>(h2 + hat_elems);
-    // qhat = S q S
-    PIT_TRY((launch_xS<Tin, T, T>(p, q, h1, S, 1.0, st, s)));
-    PIT_TRY((launch_xS<T, T, T>(p, h1, h2, S, 1.0, st, s)));
+    // FP32 transforms: an FP64 q is converted first (into h2, free until the
+    // second transform) so that the persistent kernels (tensor-core or
+    // FP32-pipe) run; the conversion rounds to nearest like the tiled
+    // transform's own staging
+    const float *q32 = nullptr;
+    const bool xf_pad = n <= PN && n % 4 == 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if constexpr (std::is_same<Tin, double>::value) {
+            if (xf_pad && reinterpret_cast<uintptr_t>(q) % 16 == 0) {
+                const size_t mlen2 = (size_t)nblk * nn / 2;
+                int dev = 0, sms = 0;
+                PIT_CUDA(cudaGetDevice(&dev));
+                PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                k_d2f_blocks<<<sms * 8, 256, 0, s>>>(q, h2, mlen2, p->batch, st);
+                PIT_LAUNCH_CHECK();
+                q32 = h2;
+            }
+        } else {
+            if (xf_pad && reinterpret_cast<uintptr_t>(q) % 16 == 0) q32 = q;
+        }
+    }
+    const bool tc = std::is_same<T, float>::value && p->xform_tc && q32 != nullptr;
+    const double sc = 2.0 / (n + 1);
+    if (tc) {
+        // qhat = S q S on the tensor cores (two passes, each out = (A S)^T per block)
+        float *f1 = reinterpret_cast<float *>(h1), *f2 = reinterpret_cast<float *>(h2);
+        PIT_TRY(heat2d_tc_xform(p, q32, f1, false, 1.0, st, s));
+        PIT_TRY(heat2d_tc_xform(p, f1, f2, false, 1.0, st, s));
+    } else {
+        // qhat = S q S
+        if (q32) PIT_TRY((launch_xS<float, float, float>(p, q32, reinterpret_cast<float *>(h1),
+                                                         reinterpret_cast<const float *>(S), 1.0, st, s)));
+        else PIT_TRY((launch_xS<Tin, T, T>(p, q, h1, S, 1.0, st, s)));
+        PIT_TRY((launch_xS<T, T, T>(p, h1, h2, S, 1.0, st, s)));
+    }
     // recurrence over slices, mode by mode
     const int RT = 256;
     dim3 g1((unsigned)((nn + RT - 1) / RT), nchunks, p->batch);
@@ -835,7 +881,12 @@ pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const Member
     k_rec_apply<T><<<g1, RT, 0, s>>>(h2, ends, p->gmode.as<double>(), (int)nn, nblk, nchunks, st);
     PIT_LAUNCH_CHECK();
     // z = (2/(n+1))^2 S zhat S
-    const double sc = 2.0 / (n + 1);
+    if (tc) {
+        float *f1 = reinterpret_cast<float *>(h1), *f2 = reinterpret_cast<float *>(h2);
+        PIT_TRY(heat2d_tc_xform(p, f2, f1, false, sc, st, s));
+        PIT_TRY(heat2d_tc_xform(p, f1, z, true, sc, st, s));
+        return PIT_OK;
+    }
     PIT_TRY((launch_xS<T, T, T>(p, h2, h1, S, sc, st, s)));
     PIT_TRY((launch_xS<T, T, double>(p, h1, z, S, sc, st, s)));
     return PIT_OK;
@@ -880,6 +931,13 @@ pit_status heat2d_setup(Problem *p) {
     PIT_CUDA(cudaMemcpyAsync(p->S64.ptr, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     PIT_CUDA(cudaMemcpyAsync(p->S32.ptr, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     PIT_CUDA(cudaMemcpyAsync(p->gmode.ptr, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    // FP32 sweeps of the mixed path transform on the tensor cores where the
+    // grid fits one 128 x 128 tile (PIT_HEAT2D_TC=0 keeps the FP32-pipe kernels)
+    {
+        const char *env = getenv("PIT_HEAT2D_TC");
+        p->xform_tc = (p->precision == PIT_MIXED && heat2d_tc_usable(p) && !(env && env[0] == '0')) ? 1 : 0;
+        if (p->xform_tc) PIT_TRY(heat2d_tc_setup(p, S.data()));
+    }
     // autotune the fine kernels' variant on this shape: FP32 (inner solves)
     // among one CTA of 4- or 8-column tiles and a cluster of 8 x 4 tiles;
     // float-float (true residuals) between one CTA and a cluster.  Every

@@ -157,6 +157,8 @@ struct Problem {
 
     // heat2d: sine basis S_jk = sin(pi j k/(n+1)) and coarse mode factors
     DevBuf S64, S32, gmode;       // gmode: (1 - dTc nu (mu_k + mu_l))^{-c}
+    DevBuf xtc_S;                 // TF32 parts (hi, lo) of S for the tensor-core transforms
+    int xform_tc = 0;             // 2D heat sweeps transform on the tensor cores
     DevBuf hat;                   // sweep scratch: transformed blocks
 
     // advdiff2d: per-point velocities (FP64 and FP32)
@@ -253,6 +255,13 @@ bool dense_tc_supported(const Problem *p);
 pit_status dense_tc_split_phi(Problem *p);
 pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, int mode,
                           const MemberState *st, cudaStream_t s);
+// 2D heat sine transforms on the tensor cores (xform_tc.cu), 96 <= n <= 128,
+// n % 4 == 0: out_b = scale (A_b S)^T for every n x n block b of A (FP32,
+// 16-byte aligned), out FP32 or FP64.
+bool heat2d_tc_usable(const Problem *p);
+pit_status heat2d_tc_setup(Problem *p, const double *S);
+pit_status heat2d_tc_xform(Problem *p, const float *A, void *out, bool out64, double scale,
+                           const MemberState *st, cudaStream_t s);
 
 // Autotuner (tune.cu): index of the fastest of ncand variants run(c), timed
 // with CUDA events on stream s; cached per key, device SM count and process.
