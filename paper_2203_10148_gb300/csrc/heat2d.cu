@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
     k_heat2d_fine(Heat2dArgs a) {
     using A = Arith<V>;
     constexpr bool kPacked = std::is_same<V, float>::value;
+    constexpr bool kFF = std::is_same<V, ff>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = blockIdx.y;
     if (!runs(a.st, b)) return;   // uniform over a cluster (same member)
@@ -118,9 +119,18 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
             const V ld = A::from_d(xin[(size_t)min(j, n - 1) * n + min(i, n - 1)]);
             const V val = A::sel(ok, ld, A::zero());
             v[r][c] = val;
-            if constexpr (U_SMEM) us[(size_t)(r * RX + c) * nthr + tid] = val;
-            else ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = val;
+            if constexpr (U_SMEM && !kFF) us[(size_t)(r * RX + c) * nthr + tid] = val;
+            else if constexpr (!U_SMEM) ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = val;
         }
+    // float-float: u stored per row pair (r, r + RY/2) as {hi_r, hi_r+H, lo_r, lo_r+H}
+    [[maybe_unused]] float4 *us4 = reinterpret_cast<float4 *>(us);
+    if constexpr (kFF) {
+#pragma unroll
+        for (int r = 0; r < RY / 2; ++r)
+#pragma unroll
+            for (int c = 0; c < RX; ++c)
+                us4[(size_t)(r * RX + c) * nthr + tid] = ff_pack_pair(v[r][c], v[r + RY / 2][c]);
+    }
     // stage coefficients dt/4, dt/3, dt/2, dt (times nu/h^2), converted once
     if (tid < 4) ccs[tid] = A::from_d(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
     const bool west_zero = (tx == 0), east_zero = (tx == a.TXp - 1);
@@ -168,6 +178,57 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
 #pragma unroll
                 for (int c = 0; c < RX; ++c) prev[c] = A::sel(north_zero, A::zero(), prev[c]);
             }
+            if constexpr (kFF) {
+                // float-float, rows r and r + H in the two lanes of each packed
+                // instruction: every neighbour operand of a pair is itself a
+                // pair of the state, except the halo rows of pair rows 0 and H-1
+                constexpr int H = RY / 2;
+                V srow[RX], rowH[RX], pB[RX];
+#pragma unroll
+                for (int q = 0; q < RX; q += 4) {
+                    V t[4];
+                    A::ld4(sbuf + ((size_t)(buf * 2 + 0) * TYp + sty) * W + i0 + q, t);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) srow[q + c] = A::sel(south_zero, A::zero(), t[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < RX; ++c) {
+                    rowH[c] = v[H][c];       // south neighbour of row H-1, before its update
+                    pB[c] = v[H - 1][c];     // north neighbour of row H, before its update
+                }
+                const float2 cch = make_float2(cc.hi, cc.hi), ccl = make_float2(cc.lo, cc.lo);
+#pragma unroll
+                for (int r = 0; r < H; ++r) {
+                    V cA[RX], cB[RX];
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) {
+                        cA[c] = v[r][c];
+                        cB[c] = v[r + H][c];
+                    }
+                    const V wA = A::sel(west_zero, A::zero(), A::shfl_up(cA[RX - 1]));
+                    const V wB = A::sel(west_zero, A::zero(), A::shfl_up(cB[RX - 1]));
+                    const V eA = A::sel(east_zero, A::zero(), A::shfl_down(cA[0]));
+                    const V eB = A::sel(east_zero, A::zero(), A::shfl_down(cB[0]));
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) {
+                        const V sA = (r < H - 1) ? v[r + 1][c] : rowH[c];
+                        const V sB = (r < H - 1) ? v[r + H + 1][c] : srow[c];
+                        const V xwA = (c > 0) ? cA[c - 1] : wA, xwB = (c > 0) ? cB[c - 1] : wB;
+                        const V xeA = (c < RX - 1) ? cA[c + 1] : eA, xeB = (c < RX - 1) ? cB[c + 1] : eB;
+                        const float4 u4 = us4[(size_t)(r * RX + c) * nthr + tid];
+                        const ff2 w = ff_stage2(ff_pair(prev[c], pB[c]), ff_pair(sA, sB), ff_pair(xwA, xwB),
+                                                ff_pair(xeA, xeB), ff_pair(cA[c], cB[c]),
+                                                ff2{make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)}, cch, ccl);
+                        v[r][c] = ff{w.hi.x, w.lo.x};
+                        v[r + H][c] = ff{w.hi.y, w.lo.y};
+                    }
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) {
+                        prev[c] = cA[c];
+                        pB[c] = cB[c];
+                    }
+                }
+            } else {
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 V srow[RX];
@@ -219,31 +280,6 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
                 }
                 w_in = A::sel(west_zero, A::zero(), w_in);
                 e_in = A::sel(east_zero, A::zero(), e_in);
-                if constexpr (std::is_same<V, ff>::value) {
-                    // float-float, two columns per packed instruction
-                    const float2 cch = make_float2(cc.hi, cc.hi), ccl = make_float2(cc.lo, cc.lo);
-#pragma unroll
-                    for (int q = 0; q < RX; q += 2) {
-                        const V s0 = (r < RY - 1) ? v[r + 1][q] : srow[q];
-                        const V s1 = (r < RY - 1) ? v[r + 1][q + 1] : srow[q + 1];
-                        const V w0 = (q > 0) ? cur[q - 1] : w_in;
-                        const V e1 = (q + 2 < RX) ? cur[q + 2] : e_in;
-                        const V u0 = us[(size_t)(r * RX + q) * nthr + tid];
-                        const V u1 = us[(size_t)(r * RX + q + 1) * nthr + tid];
-                        const ff2 w = ff_stage2(
-                            ff2{make_float2(prev[q].hi, prev[q + 1].hi), make_float2(prev[q].lo, prev[q + 1].lo)},
-                            ff2{make_float2(s0.hi, s1.hi), make_float2(s0.lo, s1.lo)},
-                            ff2{make_float2(w0.hi, cur[q].hi), make_float2(w0.lo, cur[q].lo)},
-                            ff2{make_float2(cur[q + 1].hi, e1.hi), make_float2(cur[q + 1].lo, e1.lo)},
-                            ff2{make_float2(cur[q].hi, cur[q + 1].hi), make_float2(cur[q].lo, cur[q + 1].lo)},
-                            ff2{make_float2(u0.hi, u1.hi), make_float2(u0.lo, u1.lo)}, cch, ccl);
-                        v[r][q] = ff{w.hi.x, w.lo.x};
-                        v[r][q + 1] = ff{w.hi.y, w.lo.y};
-                    }
-#pragma unroll
-                    for (int c = 0; c < RX; ++c) prev[c] = cur[c];
-                    continue;
-                }
 #pragma unroll
                 for (int c = 0; c < RX; ++c) {
                     const V vn = prev[c];
@@ -258,6 +294,7 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
 #pragma unroll
                 for (int c = 0; c < RX; ++c) prev[c] = cur[c];
             }
+            }
             if (edge) {
 #pragma unroll
                 for (int r = 0; r < RY; ++r)
@@ -268,13 +305,21 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
             buf ^= 1;
         }
         // end of step: u <- v
+        if constexpr (kFF) {
 #pragma unroll
-        for (int r = 0; r < RY; ++r)
+            for (int r = 0; r < RY / 2; ++r)
 #pragma unroll
-            for (int c = 0; c < RX; ++c) {
-                if constexpr (U_SMEM) us[(size_t)(r * RX + c) * nthr + tid] = v[r][c];
-                else ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = v[r][c];
-            }
+                for (int c = 0; c < RX; ++c)
+                    us4[(size_t)(r * RX + c) * nthr + tid] = ff_pack_pair(v[r][c], v[r + RY / 2][c]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int c = 0; c < RX; ++c) {
+                    if constexpr (U_SMEM) us[(size_t)(r * RX + c) * nthr + tid] = v[r][c];
+                    else ur[U_SMEM ? 0 : r][U_SMEM ? 0 : c] = v[r][c];
+                }
+        }
     }
     // no CTA of a cluster leaves while its row buffer may still be read
     if constexpr (CL) cg::this_cluster().sync();

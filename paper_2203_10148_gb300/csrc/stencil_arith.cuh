@@ -162,6 +162,16 @@ __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &
     e = __fadd2_rn(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
 }
 
+// two float-float values as the lanes of a packed pair
+__device__ __forceinline__ ff2 ff_pair(const ff &a, const ff &b) {
+    return ff2{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)};
+}
+
+// {a.hi, b.hi, a.lo, b.lo}: one 16-byte record per pair
+__device__ __forceinline__ float4 ff_pack_pair(const ff &a, const ff &b) {
+    return make_float4(a.hi, b.hi, a.lo, b.lo);
+}
+
 // w = u + cc (vn + vs + vw + ve - 4 vc) for two points, cc = (cch, ccl)
 __device__ __forceinline__ ff2 ff_stage2(const ff2 &vn, const ff2 &vs, const ff2 &vw,
                                          const ff2 &ve, const ff2 &vc, const ff2 &u,
