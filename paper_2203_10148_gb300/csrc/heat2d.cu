@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
                     pB[c] = v[H - 1][c];     // north neighbour of row H, before its update
                 }
                 const float2 cch = make_float2(cc.hi, cc.hi), ccl = make_float2(cc.lo, cc.lo);
+                const float2 ncch = make_float2(-cc.hi, -cc.hi);
 #pragma unroll
                 for (int r = 0; r < H; ++r) {
                     V cA[RX], cB[RX];
@@ -218,7 +219,8 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
                         const float4 u4 = us4[(size_t)(r * RX + c) * nthr + tid];
                         const ff2 w = ff_stage2(ff_pair(prev[c], pB[c]), ff_pair(sA, sB), ff_pair(xwA, xwB),
                                                 ff_pair(xeA, xeB), ff_pair(cA[c], cB[c]),
-                                                ff2{make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)}, cch, ccl);
+                                                ff2{make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)}, cch,
+                                                ncch, ccl);
                         v[r][c] = ff{w.hi.x, w.lo.x};
                         v[r + H][c] = ff{w.hi.y, w.lo.y};
                     }
@@ -304,13 +306,17 @@ __global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
             }
             buf ^= 1;
         }
-        // end of step: u <- v
+        // end of step: u <- v (float-float: renormalised once per step)
         if constexpr (kFF) {
 #pragma unroll
             for (int r = 0; r < RY / 2; ++r)
 #pragma unroll
-                for (int c = 0; c < RX; ++c)
+                for (int c = 0; c < RX; ++c) {
+                    const ff2 w = ff_renorm2(ff_pair(v[r][c], v[r + RY / 2][c]));
+                    v[r][c] = ff{w.hi.x, w.lo.x};
+                    v[r + RY / 2][c] = ff{w.hi.y, w.lo.y};
                     us4[(size_t)(r * RX + c) * nthr + tid] = ff_pack_pair(v[r][c], v[r + RY / 2][c]);
+                }
         } else {
 #pragma unroll
             for (int r = 0; r < RY; ++r)

@@ -172,30 +172,50 @@ __device__ __forceinline__ float4 ff_pack_pair(const ff &a, const ff &b) {
     return make_float4(a.hi, b.hi, a.lo, b.lo);
 }
 
-// w = u + cc (vn + vs + vw + ve - 4 vc) for two points, cc = (cch, ccl)
+// w = u + cc (vn + vs + vw + ve - 4 vc) for two points, cc = (cch, ccl),
+// ncch = -cch.  Same scheme as Arith<ff>::stage in 44 FP32 operations:
+// the fourth TwoSum takes its operand -4 vc.hi as exact FMA products
+// (no separate multiply), the product error term starts from -p (no
+// negation), and the result is left unnormalised -- w.hi is the TwoSum of
+// u.hi and p, w.lo collects the rest, a few ulp of w.hi at most -- which
+// costs nothing in accuracy because every low part is summed in FP32 next
+// to exact sums of the high parts; ff_renorm2 restores |lo| <= ulp(hi)/2
+// once per time step.
 __device__ __forceinline__ ff2 ff_stage2(const ff2 &vn, const ff2 &vs, const ff2 &vw,
                                          const ff2 &ve, const ff2 &vc, const ff2 &u,
-                                         float2 cch, float2 ccl) {
+                                         float2 cch, float2 ncch, float2 ccl) {
     const float2 m4 = make_float2(-4.f, -4.f);
-    float2 ah, al, bh, bl, ch, cl, dh, dl;
+    float2 ah, al, bh, bl, ch, cl;
     two_sum2(vn.hi, vs.hi, ah, al);
     two_sum2(vw.hi, ve.hi, bh, bl);
     two_sum2(ah, bh, ch, cl);
-    two_sum2(ch, __fmul2_rn(m4, vc.hi), dh, dl);
+    // TwoSum(ch, -4 vc.hi): s = dh, -bb = ch - dh, e = (ch - (s - bb)) + (b - bb)
+    const float2 dh = __ffma2_rn(m4, vc.hi, ch);
+    const float2 nbb = f2_sub(ch, dh);
+    const float2 dl = __fadd2_rn(f2_sub(ch, __fadd2_rn(dh, nbb)), __ffma2_rn(m4, vc.hi, nbb));
     const float2 lo = __ffma2_rn(
         m4, vc.lo,
         __fadd2_rn(__fadd2_rn(__fadd2_rn(al, bl), __fadd2_rn(cl, dl)),
                    __fadd2_rn(__fadd2_rn(vn.lo, vs.lo), __fadd2_rn(vw.lo, ve.lo))));
-    const float2 p = __fmul2_rn(cch, dh);
-    float2 e = __ffma2_rn(cch, dh, make_float2(-p.x, -p.y));
+    const float2 pn = __fmul2_rn(ncch, dh);      // -p, p = cch dh
+    float2 e = __ffma2_rn(cch, dh, pn);          // p's rounding error, exact
     e = __ffma2_rn(cch, lo, e);
     e = __ffma2_rn(ccl, dh, e);
-    float2 sh, sl;
-    two_sum2(u.hi, p, sh, sl);
-    const float2 t = __fadd2_rn(sl, __fadd2_rn(u.lo, e));
+    // TwoSum(u.hi, p) with p = -pn
+    const float2 sh = f2_sub(u.hi, pn);
+    const float2 nb2 = f2_sub(u.hi, sh);
+    const float2 sl = __fadd2_rn(f2_sub(u.hi, __fadd2_rn(sh, nb2)), f2_sub(nb2, pn));
     ff2 w;
-    w.hi = __fadd2_rn(sh, t);
-    w.lo = f2_sub(t, f2_sub(w.hi, sh));
+    w.hi = sh;
+    w.lo = __fadd2_rn(sl, __fadd2_rn(u.lo, e));
+    return w;
+}
+
+// FastTwoSum renormalisation of two float-float values (|lo| <= a few ulp(hi))
+__device__ __forceinline__ ff2 ff_renorm2(const ff2 &v) {
+    ff2 w;
+    w.hi = __fadd2_rn(v.hi, v.lo);
+    w.lo = f2_sub(v.lo, f2_sub(w.hi, v.hi));
     return w;
 }
 
