@@ -891,7 +891,7 @@ pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const Member
     // FP32-pipe) run; the conversion rounds to nearest like the tiled
     // transform's own staging
     const float *q32 = nullptr;
-    const bool xf_pad = n <= PN && n % 4 == 0;
+    const bool xf_pad = n % 4 == 0 && (n <= PN || p->xform_tc);
     if constexpr (std::is_same<T, float>::value) {
         if constexpr (std::is_same<Tin, double>::value) {
             if (xf_pad && reinterpret_cast<uintptr_t>(q) % 16 == 0) {
@@ -982,8 +982,8 @@ pit_status heat2d_setup(Problem *p) {
     PIT_CUDA(cudaMemcpyAsync(p->S64.ptr, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     PIT_CUDA(cudaMemcpyAsync(p->S32.ptr, S32.data(), S32.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     PIT_CUDA(cudaMemcpyAsync(p->gmode.ptr, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
-    // FP32 sweeps of the mixed path transform on the tensor cores where the
-    // grid fits one 128 x 128 tile (PIT_HEAT2D_TC=0 keeps the FP32-pipe kernels)
+    // FP32 sweeps of the mixed path transform on the tensor cores for
+    // 96 <= n <= 256, n % 4 == 0 (PIT_HEAT2D_TC=0 keeps the FP32-pipe kernels)
     {
         const char *env = getenv("PIT_HEAT2D_TC");
         p->xform_tc = (p->precision == PIT_MIXED && heat2d_tc_usable(p) && !(env && env[0] == '0')) ? 1 : 0;

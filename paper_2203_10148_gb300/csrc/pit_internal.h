@@ -255,7 +255,7 @@ bool dense_tc_supported(const Problem *p);
 pit_status dense_tc_split_phi(Problem *p);
 pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, int mode,
                           const MemberState *st, cudaStream_t s);
-// 2D heat sine transforms on the tensor cores (xform_tc.cu), 96 <= n <= 128,
+// 2D heat sine transforms on the tensor cores (xform_tc.cu), 96 <= n <= 256,
 // n % 4 == 0: out_b = scale (A_b S)^T for every n x n block b of A (FP32,
 // 16-byte aligned), out FP32 or FP64.
 bool heat2d_tc_usable(const Problem *p);

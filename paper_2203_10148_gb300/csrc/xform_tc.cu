@@ -15,11 +15,13 @@
 // transforms it replaces.  The sweep only preconditions (its FP32 error
 // enters the inner solve's operator, not the float-float true residual).
 //
-// Kernel: persistent, one CTA per SM, blocks b = blockIdx.x, +gridDim.x, ...
-// for 96 <= n <= 128 (n % 4 == 0: one 128 x 128 tile per block, rows and
-// columns beyond n read as zero or are not stored).  Warp roles:
-//   warp 0      TMA: Sh and Sl once (resident, 128 KB), then the block's
-//               four 32-column chunks of A into a 3-stage ring;
+// Kernel: persistent, one CTA per SM, output tiles t = blockIdx.x,
+// +gridDim.x, ... of 128 x 128 (one per block for 96 <= n <= 128, 2 x 2 for
+// 128 < n <= 256; n % 4 == 0; rows and columns beyond n read as zero or are
+// not stored).  Warp roles:
+//   warp 0      TMA: for n <= 128 Sh and Sl once (resident, 128 KB), then
+//               each tile's ceil(n/32) chunks of A (32 columns, and for
+//               n > 128 the matching chunks of Sh and Sl) into a 3-stage ring;
 //   warp 1      one thread issues tcgen05.mma (kind::tf32, M = N = 128,
 //               K = 8) into one of two TMEM accumulators (2 x 128 columns);
 //   warps 2..5  split each landed chunk in place into Ah and Al;
@@ -42,20 +44,26 @@ namespace {
 
 constexpr int XT_T = 128;                              // tile rows (TMEM lanes) = columns
 constexpr int XT_BK = 32;                              // K per chunk (128 bytes of FP32)
-constexpr int XT_KCH = XT_T / XT_BK;                   // chunks per tile
 constexpr int XT_STAGES = 3;
 constexpr int XT_CH = XT_T * XT_BK * 4;                // 16 KB: one chunk of one operand part
-constexpr int XT_S_BYTES = XT_KCH * XT_CH;             // 64 KB: one part of S
-constexpr int XT_STAGE_BYTES = 2 * XT_CH;              // Ah (landed by TMA, split in place) + Al
-constexpr int XT_BAR_OFF = 2 * XT_S_BYTES + XT_STAGES * XT_STAGE_BYTES;
-constexpr int XT_SMEM = 1024 + XT_BAR_OFF + 128;       // alignment slack + ring + barriers
+constexpr int XT_S_BYTES = (XT_T / XT_BK) * XT_CH;     // 64 KB: one part of a resident S (n <= 128)
 constexpr int XT_THREADS = 320;
 constexpr int XT_CONV_THREADS = 128;
 constexpr uint32_t kXtIdesc = tc_idesc_tf32(XT_T, XT_T);
 
-__device__ __forceinline__ bool xt_live(const MemberState *st, int t, int nblk) {
+// Shared memory: S resident (n <= 128): [Sh 64 KB][Sl 64 KB] + 3 stages of
+// [Ah][Al]; S streamed (n > 128): 3 stages of [Ah][Al][Sh][Sl].
+template <bool SRES>
+struct XtLayout {
+    static constexpr int kStage = SRES ? 2 * XT_CH : 4 * XT_CH;
+    static constexpr int kRing = SRES ? 2 * XT_S_BYTES : 0;
+    static constexpr int kBar = kRing + XT_STAGES * kStage;
+    static constexpr int kSmem = 1024 + kBar + 128;
+};
+
+__device__ __forceinline__ bool xt_live(const MemberState *st, int b) {
     if (st == nullptr) return true;
-    const MemberState &m = st[t / nblk];
+    const MemberState &m = st[b];
     return m.active && !m.skip && !m.half;
 }
 
@@ -65,26 +73,32 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(h);
 }
 
-template <bool OUT64>
+// Output tiles t = (block, tj, tk), TN x TN of them per block (TN = 1 for
+// n <= 128, 2 for n <= 256): rows j = 128 tj + lane, columns k = 128 tk + ...;
+// K in KC = ceil(n / 32) chunks.
+template <bool OUT64, bool SRES>
 __global__ void __launch_bounds__(XT_THREADS, 1)
     k_xform_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmSh,
-               const __grid_constant__ CUtensorMap tmSl, void *out_raw, int n, int total, int nblk,
-               float scale, const MemberState *st, int *err) {
+               const __grid_constant__ CUtensorMap tmSl, void *out_raw, int n, int total_tiles,
+               int TN, int nblk, float scale, const MemberState *st, int *err) {
+    using LY = XtLayout<SRES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char *Sh = base, *Sl = base + XT_S_BYTES;
-    unsigned char *ring = base + 2 * XT_S_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + XT_BAR_OFF);
+    unsigned char *Sres = base;                          // resident Sh, then Sl (SRES)
+    unsigned char *ring = base + LY::kRing;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + LY::kBar);
     uint64_t *full = bars;                       // chunk landed (TMA)
     uint64_t *conv = bars + XT_STAGES;           // chunk split (converters)
     uint64_t *empty = bars + 2 * XT_STAGES;      // chunk consumed (tensor core)
     uint64_t *tfull = bars + 3 * XT_STAGES;      // accumulator complete, 2 buffers
     uint64_t *tempty = tfull + 2;                // accumulator drained, 2 buffers
-    uint64_t *sbar = tempty + 2;                 // S resident
+    uint64_t *sbar = tempty + 2;                 // resident S landed
     uint64_t *mdone = sbar + 1;                  // all products issued have finished
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int KC = (n + XT_BK - 1) / XT_BK;
+    const int tpb = TN * TN;                     // tiles per block
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < XT_STAGES; ++s) {
@@ -115,40 +129,48 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- TMA producer
-            mbar_expect_tx(sbar, 2 * XT_S_BYTES);
-            for (int c = 0; c < XT_KCH; ++c) {
-                tma_load_2d(Sh + c * XT_CH, &tmSh, c * XT_BK, 0, sbar);
-                tma_load_2d(Sl + c * XT_CH, &tmSl, c * XT_BK, 0, sbar);
+            if constexpr (SRES) {
+                mbar_expect_tx(sbar, 2 * XT_S_BYTES);
+                for (int c = 0; c < XT_T / XT_BK; ++c) {
+                    tma_load_2d(Sres + c * XT_CH, &tmSh, c * XT_BK, 0, sbar);
+                    tma_load_2d(Sres + XT_S_BYTES + c * XT_CH, &tmSl, c * XT_BK, 0, sbar);
+                }
             }
             int last_use[XT_STAGES];
             for (int s = 0; s < XT_STAGES; ++s) last_use[s] = -1;
             int q = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                if (!xt_live(st, t, nblk)) continue;
-                for (int c = 0; c < XT_KCH; ++c, ++q) {
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                const int b = t / tpb, tj = (t % tpb) / TN, tk = t % TN;
+                if (!xt_live(st, b / nblk)) continue;
+                for (int c = 0; c < KC; ++c, ++q) {
                     const int s = q % XT_STAGES, u = q / XT_STAGES;
                     if (!tc_mbar_wait(&empty[s], (uint32_t)(u & 1) ^ 1u, err)) {
                         ok = false;
                         break;
                     }
-                    mbar_expect_tx(&full[s], XT_CH);
-                    tma_load_2d(ring + s * XT_STAGE_BYTES, &tmA, c * XT_BK, t * n, &full[s]);
+                    unsigned char *stg = ring + s * LY::kStage;
+                    mbar_expect_tx(&full[s], SRES ? XT_CH : 3 * XT_CH);
+                    tma_load_2d(stg, &tmA, c * XT_BK, b * n + tj * XT_T, &full[s]);
+                    if constexpr (!SRES) {
+                        tma_load_2d(stg + 2 * XT_CH, &tmSh, c * XT_BK, tk * XT_T, &full[s]);
+                        tma_load_2d(stg + 3 * XT_CH, &tmSl, c * XT_BK, tk * XT_T, &full[s]);
+                    }
                     last_use[s] = u;
                 }
             }
             // no copy of this CTA may still be writing shared memory at exit
-            tc_mbar_drain(sbar, 0u);
+            if constexpr (SRES) tc_mbar_drain(sbar, 0u);
             for (int s = 0; s < XT_STAGES; ++s)
                 if (last_use[s] >= 0) tc_mbar_drain(&full[s], (uint32_t)(last_use[s] & 1));
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            bool ok = tc_mbar_wait(sbar, 0u, err);
+            bool ok = SRES ? tc_mbar_wait(sbar, 0u, err) : true;
             int q = 0, L = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                if (!xt_live(st, t, nblk)) continue;
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                if (!xt_live(st, (t / tpb) / nblk)) continue;
                 const int buf = L & 1, v = L >> 1;
                 if (!tc_mbar_wait(&tempty[buf], (uint32_t)(v & 1) ^ 1u, err)) {
                     ok = false;
@@ -156,16 +178,17 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(buf * XT_T);
-                for (int c = 0; c < XT_KCH; ++c, ++q) {
+                for (int c = 0; c < KC; ++c, ++q) {
                     const int s = q % XT_STAGES, u = q / XT_STAGES;
                     if (!tc_mbar_wait(&conv[s], (uint32_t)(u & 1), err)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    unsigned char *stg = ring + s * XT_STAGE_BYTES;
+                    unsigned char *stg = ring + s * LY::kStage;
                     const uint64_t ah = smem_desc(stg), al = smem_desc(stg + XT_CH);
-                    const uint64_t bh = smem_desc(Sh + c * XT_CH), bl = smem_desc(Sl + c * XT_CH);
+                    const uint64_t bh = SRES ? smem_desc(Sres + c * XT_CH) : smem_desc(stg + 2 * XT_CH);
+                    const uint64_t bl = SRES ? smem_desc(Sres + XT_S_BYTES + c * XT_CH) : smem_desc(stg + 3 * XT_CH);
 #pragma unroll
                     for (int j = 0; j < XT_BK / 8; ++j) {
                         const uint64_t adv = (uint64_t)(j * 32) >> 4;   // 8 TF32 = 32 bytes along K
@@ -187,16 +210,16 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         const int ct = threadIdx.x - 64;
         int q = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-            if (!xt_live(st, t, nblk)) continue;
-            for (int c = 0; c < XT_KCH; ++c, ++q) {
+        for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+            if (!xt_live(st, (t / tpb) / nblk)) continue;
+            for (int c = 0; c < KC; ++c, ++q) {
                 const int s = q % XT_STAGES, u = q / XT_STAGES;
                 if (!tc_mbar_wait(&full[s], (uint32_t)(u & 1), err)) {
                     ok = false;
                     break;
                 }
-                float4 *hi = reinterpret_cast<float4 *>(ring + s * XT_STAGE_BYTES);
-                float4 *lo = reinterpret_cast<float4 *>(ring + s * XT_STAGE_BYTES + XT_CH);
+                float4 *hi = reinterpret_cast<float4 *>(ring + s * LY::kStage);
+                float4 *lo = reinterpret_cast<float4 *>(ring + s * LY::kStage + XT_CH);
 #pragma unroll 4
                 for (int i = ct; i < XT_CH / 16; i += XT_CONV_THREADS) {
                     const float4 a = hi[i];
@@ -218,36 +241,34 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             }
         }
     } else {
-        // ---- epilogue: TMEM lanes 32 (warp % 4) .. +31 are the tile rows j
+        // ---- epilogue: TMEM lanes 32 (warp % 4) .. +31 are the tile rows
         const int quad = warp & 3;
-        const int j = quad * 32 + lane;
         const size_t nn = (size_t)n * n;
         int L = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
-            if (!xt_live(st, t, nblk)) continue;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+            const int b = t / tpb, tj = (t % tpb) / TN, tk = t % TN;
+            if (!xt_live(st, b / nblk)) continue;
             const int buf = L & 1, v = L >> 1;
             const bool ok = __all_sync(0xffffffffu, tc_mbar_wait(&tfull[buf], (uint32_t)(v & 1), err) ? 1 : 0) != 0;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int j = tj * XT_T + quad * 32 + lane;
 #pragma unroll 1
             for (int cc = 0; cc < XT_T / 32; ++cc) {
                 float vals[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * XT_T + cc * 32), vals);
+                const int k0 = tk * XT_T + cc * 32;
                 if (j < n) {
                     if constexpr (OUT64) {
-                        double *ob = reinterpret_cast<double *>(out_raw) + (size_t)t * nn + j;
+                        double *ob = reinterpret_cast<double *>(out_raw) + (size_t)b * nn + j;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int k = cc * 32 + i;
-                            if (k < n) ob[(size_t)k * n] = f2d(scale * vals[i]);
-                        }
+                        for (int i = 0; i < 32; ++i)
+                            if (k0 + i < n) ob[(size_t)(k0 + i) * n] = f2d(scale * vals[i]);
                     } else {
-                        float *ob = reinterpret_cast<float *>(out_raw) + (size_t)t * nn + j;
+                        float *ob = reinterpret_cast<float *>(out_raw) + (size_t)b * nn + j;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const int k = cc * 32 + i;
-                            if (k < n) ob[(size_t)k * n] = scale * vals[i];
-                        }
+                        for (int i = 0; i < 32; ++i)
+                            if (k0 + i < n) ob[(size_t)(k0 + i) * n] = scale * vals[i];
                     }
                 }
             }
@@ -263,6 +284,18 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * XT_T));
     }
+}
+
+template <bool OUT64, bool SRES>
+pit_status launch_xform_tc(const CUtensorMap &tA, const CUtensorMap &tSh, const CUtensorMap &tSl,
+                           void *out, int n, int total_tiles, int TN, int nblk, float scale,
+                           const MemberState *st, int *err, int grid, cudaStream_t s) {
+    auto kern = k_xform_tc<OUT64, SRES>;
+    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<SRES>::kSmem));
+    kern<<<grid, XT_THREADS, XtLayout<SRES>::kSmem, s>>>(tA, tSh, tSl, out, n, total_tiles, TN, nblk,
+                                                          scale, st, err);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
 }
 
 uint32_t tf32_rna_host(float x) {
@@ -282,7 +315,7 @@ float bits_to_float(uint32_t b) {
 }  // namespace
 
 bool heat2d_tc_usable(const Problem *p) {
-    return p->nx >= 96 && p->nx <= XT_T && p->nx % 4 == 0 && tc_encode_fn() != nullptr;
+    return p->nx >= 96 && p->nx <= 2 * XT_T && p->nx % 4 == 0 && tc_encode_fn() != nullptr;
 }
 
 pit_status heat2d_tc_setup(Problem *p, const double *S) {
@@ -304,27 +337,26 @@ pit_status heat2d_tc_setup(Problem *p, const double *S) {
 pit_status heat2d_tc_xform(Problem *p, const float *A, void *out, bool out64, double scale,
                            const MemberState *st, cudaStream_t s) {
     const int n = p->nx;
-    const int total = p->batch * (p->N + 1);
+    const int blocks = p->batch * (p->N + 1);
+    const int TN = (n + XT_T - 1) / XT_T;
+    const int total_tiles = blocks * TN * TN;
     const float *Sh = p->xtc_S.as<float>();
     CUtensorMap tA, tSh, tSl;
-    PIT_TRY(tc_make_map(&tA, A, total * n, n, XT_BK, XT_T));
+    PIT_TRY(tc_make_map(&tA, A, blocks * n, n, XT_BK, XT_T));
     PIT_TRY(tc_make_map(&tSh, Sh, n, n, XT_BK, XT_T));
     PIT_TRY(tc_make_map(&tSl, Sh + (size_t)n * n, n, n, XT_BK, XT_T));
     int dev = 0, sms = 0;
     PIT_CUDA(cudaGetDevice(&dev));
     PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = std::min(total, sms);
-    if (out64) {
-        PIT_CUDA(cudaFuncSetAttribute(k_xform_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM));
-        k_xform_tc<true><<<grid, XT_THREADS, XT_SMEM, s>>>(tA, tSh, tSl, out, n, total, p->N + 1,
-                                                           (float)scale, st, p->errword.as<int>());
-    } else {
-        PIT_CUDA(cudaFuncSetAttribute(k_xform_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM));
-        k_xform_tc<false><<<grid, XT_THREADS, XT_SMEM, s>>>(tA, tSh, tSl, out, n, total, p->N + 1,
-                                                            (float)scale, st, p->errword.as<int>());
+    const int grid = std::min(total_tiles, sms);
+    int *err = p->errword.as<int>();
+    const float sc = (float)scale;
+    if (TN == 1) {
+        if (out64) return launch_xform_tc<true, true>(tA, tSh, tSl, out, n, total_tiles, TN, p->N + 1, sc, st, err, grid, s);
+        return launch_xform_tc<false, true>(tA, tSh, tSl, out, n, total_tiles, TN, p->N + 1, sc, st, err, grid, s);
     }
-    PIT_LAUNCH_CHECK();
-    return PIT_OK;
+    if (out64) return launch_xform_tc<true, false>(tA, tSh, tSl, out, n, total_tiles, TN, p->N + 1, sc, st, err, grid, s);
+    return launch_xform_tc<false, false>(tA, tSh, tSl, out, n, total_tiles, TN, p->N + 1, sc, st, err, grid, s);
 }
 
 }  // namespace pit

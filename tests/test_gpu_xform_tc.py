@@ -2,8 +2,9 @@
 eq. (7) in the sine basis, split-TF32 tcgen05 products) against the FP64
 oracle and against the FP32-pipe transforms they replace.
 
-Grids 96 <= n <= 128 (n % 4 == 0) use them in the mixed path; both kinds of
-input are covered (FP64 blocks, converted first, and the FP32 rows of the
+Grids 96 <= n <= 256 (n % 4 == 0) use them in the mixed path (one 128^2
+output tile per block with S resident up to n = 128, 2 x 2 tiles with S
+streamed beyond); both kinds of input are covered (FP64 blocks, converted first, and the FP32 rows of the
 fine kernel), single and several tiles per CTA (N + 1 above the SM count:
 both accumulators and every stage parity reused), batches, and solves that
 mask converged members.  Tolerances: 2e-5 against the oracle, as for every
@@ -20,7 +21,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 CASES = [dict(n=128, N=3, fine_steps=3), dict(n=100, N=2, fine_steps=2, batch=2),
-         dict(n=96, N=4, fine_steps=2), dict(n=124, N=2, fine_steps=3)]
+         dict(n=96, N=4, fine_steps=2), dict(n=124, N=2, fine_steps=3),
+         # 2 x 2 output tiles per block, S streamed with A
+         dict(n=256, N=3, fine_steps=3), dict(n=160, N=2, fine_steps=2, batch=2),
+         dict(n=132, N=2, fine_steps=2), dict(n=200, N=3, fine_steps=2)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -75,10 +79,12 @@ def test_tc_sweep_matches_oracle_and_fp32_pipe(case, which, monkeypatch):
     assert np.array_equal(got, again)
 
 
-def test_tc_sweep_many_tiles_per_cta(monkeypatch):
-    """N + 1 = 301 blocks of 128^2 on one launch of at most one CTA per SM:
-    every CTA walks several blocks."""
-    w = inputs.heat2d(n=128, N=300, fine_steps=2)
+@pytest.mark.parametrize("n,N", [(128, 300), (256, 80)])
+def test_tc_sweep_many_tiles_per_cta(n, N, monkeypatch):
+    """More output tiles than SMs (301 blocks of 128^2; 81 blocks of 256^2 =
+    324 tiles) on one launch of at most one CTA per SM: every CTA walks
+    several tiles, both accumulators and every stage parity are reused."""
+    w = inputs.heat2d(n=n, N=N, fine_steps=2)
     X = _rand_block(w, 52)
     got = _apply(w, "Ginv", X, True, monkeypatch)
     alt = _apply(w, "Ginv", X, False, monkeypatch)
@@ -92,7 +98,8 @@ def test_tc_sweep_many_tiles_per_cta(monkeypatch):
 
 
 @pytest.mark.parametrize("case", [dict(n=128, N=24, fine_steps=50, batch=2),
-                                  dict(n=112, N=16, fine_steps=40)])
+                                  dict(n=112, N=16, fine_steps=40),
+                                  dict(n=192, N=16, fine_steps=80, batch=2)])
 def test_tc_mixed_solve_reaches_serial(case, monkeypatch):
     """Mixed solves whose sweeps run on the tensor cores: every member within
     1e-6 of the FP64 serial fine trajectory (converged members are masked)."""
