@@ -792,7 +792,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->vy32, &p->vxff, &p->vyff, &p->A64, &p->cvec, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
-                      &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32,
+                      &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32, &p->GLL32, &p->xtc_S,
                       &p->errword, &p->PhiTh, &p->PhiTl, &p->tc_split};
     for (IterGraph &g : p->igraph) iter_graph_drop(p, g);
     for (DevBuf *b : bufs) b->release();

@@ -265,10 +265,15 @@ pit_status grid_for(size_t n, int &blocks) {
 // cooperative launch.  The N+1 blocks are cut into C chunks of L blocks.
 //   phase 1: every chunk runs the recurrence from zero; only its last value
 //            w_c is kept (L sequential steps, the C chunks side by side);
-//   phase 2: carries e_c = w_c + G^L e_{c-1} into each chunk (C steps);
+//   phase 2: carries e_c = w_{c-1} + G^L e_{c-1} into each chunk, a
+//            recurrence of the same form scanned the same way: super-chunks
+//            of L2 chunks from zero (L2 steps), their carries with G^(L L2)
+//            (C2 - 1 steps), and the re-run from those (L2 steps);
 //   phase 3: every chunk re-runs the recurrence from its carry and stores
 //            each z_n (L steps).
-// Every CTA keeps `rows` rows of G (and of G^L) in shared memory and computes
+// With L = round((N+1)^(1/3)) and L2 = round(sqrt(C)) a sweep of N + 1 =
+// 4097 blocks takes 80 dependent steps (194 with one level).
+// Every CTA keeps `rows` rows of G, G^L and G^(L L2) in shared memory and computes
 // those rows of G v for all columns (chunks x members) each step; columns
 // live in global memory (read through L2) between steps, separated by a
 // grid barrier.  With C = 1 this is the plain sequential sweep.
@@ -283,8 +288,10 @@ struct SweepArgs {
     int M, N, batch;
     size_t blen;
     int L, C, rows;
-    const T *G, *GL;
+    int L2, C2;           // carry scan: super-chunks of L2 chunks, C2 of them
+    const T *G, *GL, *GLL;
     T *Za, *Zb, *E;
+    T *F0, *F1, *Gc;      // carry scan: running super-chunk values (ping-pong), super-chunk carries
     unsigned *bar;        // [0] arrivals, [1] generation
     int *err;
     const MemberState *st;
@@ -543,19 +550,72 @@ __device__ void sweep_step(const SweepArgs<T> &a, const T *Gm, const T *in, T *o
     }
 }
 
+// out(col, row) = add(col, row) + (Xm in(col))[row] for this CTA's rows and
+// every live column col < ncols; in(col) == nullptr reads as zero.  Warps
+// split the columns (and k, when there are fewer columns than warps);
+// partial sums meet in shared memory.
+template <class T, class InF, class AddF, class OutF, class LiveF>
+__device__ void gen_step(const T *Xm, int M, int rows, int r0, int ncols, InF in_of, AddF add_of,
+                         OutF out_of, LiveF live_of, T *red) {
+    constexpr int NW = SW_THREADS / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = ncols >= NW ? 1 : NW / ncols;        // k segments per column
+    const int per_round = NW / S;                        // columns per round
+    const int seg_len = (((M + S - 1) / S) + 3) & ~3;
+    for (int base = 0; base < ncols; base += per_round) {
+        const int cl = warp / S, seg = warp % S;
+        const int col = base + cl;
+        T acc[SW_MAXROWS];
+#pragma unroll
+        for (int r = 0; r < SW_MAXROWS; ++r) acc[r] = T(0);
+        if (col < ncols && live_of(col)) {
+            const T *v = in_of(col);
+            if (v != nullptr) {
+                const int k0 = seg * seg_len, k1 = min(M, k0 + seg_len);
+                rows_dot(Xm, v, M, rows, k0, k1, acc);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < SW_MAXROWS; ++r) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int r = 0; r < SW_MAXROWS; ++r) red[(cl * NW + seg) * SW_MAXROWS + r] = acc[r];
+        }
+        __syncthreads();
+        const int t = threadIdx.x;
+        if (t < per_round * SW_MAXROWS) {
+            const int cl2 = t / SW_MAXROWS, r = t % SW_MAXROWS;
+            const int col2 = base + cl2, row = r0 + r;
+            if (col2 < ncols && r < rows && row < M && live_of(col2)) {
+                T val = T(0);
+                for (int sg = 0; sg < S; ++sg) val += red[(cl2 * NW + sg) * SW_MAXROWS + r];
+                out_of(col2, row, add_of(col2, row) + val);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Gs = reinterpret_cast<T *>(smem_raw);
     T *GLs = Gs + (size_t)SW_MAXROWS * a.M;
-    T *red = GLs + (size_t)SW_MAXROWS * a.M;    // (SW_THREADS / 32)^2 * SW_MAXROWS partials
+    T *GLLs = GLs + (size_t)SW_MAXROWS * a.M;
+    T *red = GLLs + (size_t)SW_MAXROWS * a.M;   // (SW_THREADS / 32)^2 * SW_MAXROWS partials
     const int r0 = blockIdx.x * a.rows;
     const unsigned nb = gridDim.x;
     for (size_t t = threadIdx.x; t < (size_t)SW_MAXROWS * a.M; t += SW_THREADS) {
         const int r = (int)(t / a.M), k = (int)(t % a.M);
         const bool ok = r < a.rows && r0 + r < a.M;     // rows beyond this CTA's share: zero
         Gs[t] = ok ? a.G[(size_t)(r0 + r) * a.M + k] : T(0);
-        if (a.C > 1) GLs[t] = ok ? a.GL[(size_t)(r0 + r) * a.M + k] : T(0);
+        if (a.C > 1) {
+            GLs[t] = ok ? a.GL[(size_t)(r0 + r) * a.M + k] : T(0);
+            GLLs[t] = ok ? a.GLL[(size_t)(r0 + r) * a.M + k] : T(0);
+        }
     }
     __syncthreads();
     T *in = a.Za, *out = a.Zb;
@@ -566,39 +626,54 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
             if (!grid_barrier(a.bar, a.err, nb)) return;
             T *t = in; in = out; out = t;
         }
-        // phase 2: carries E[c] = W[c-1] + G^L E[c-1], E[0] = 0 (columns of `in` hold W)
-        for (int c = 0; c < a.C; ++c) {
-            for (int b = 0; b < a.batch; ++b) {
-                T acc[SW_MAXROWS];
-#pragma unroll
-                for (int r = 0; r < SW_MAXROWS; ++r) acc[r] = T(0);
-                constexpr int NW = SW_THREADS / 32;
-                const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                const int col = b * a.C + c;
-                const int seg_len = (((a.M + NW - 1) / NW) + 3) & ~3;
-                if (c > 0) {
-                    const int k0 = warp * seg_len, k1 = min(a.M, k0 + seg_len);
-                    rows_dot(GLs, a.E + (size_t)(col - 1) * a.M, a.M, a.rows, k0, k1, acc);
-                }
-#pragma unroll
-                for (int r = 0; r < SW_MAXROWS; ++r) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int r = 0; r < SW_MAXROWS; ++r) red[warp * SW_MAXROWS + r] = acc[r];
-                }
-                __syncthreads();
-                if (threadIdx.x < a.rows && r0 + (int)threadIdx.x < a.M) {
-                    const int r = threadIdx.x, row = r0 + r;
-                    T val = T(0);
-                    for (int w = 0; w < NW; ++w) val += red[w * SW_MAXROWS + r];
-                    const T wv = (c > 0) ? ld_cg(in + (size_t)(col - 1) * a.M + row) : T(0);
-                    __stcg(a.E + (size_t)col * a.M + row, wv + val);
-                }
-                __syncthreads();
-            }
+        // phase 2: carries E[c] = u_c + A E[c-1] with A = G^L, u_c = W[c-1] (the
+        // end of chunk c-1 from phase 1, columns of `in`), u_0 = 0, E[-1] = 0;
+        // itself a chunked scan over super-chunks of L2 chunks:
+        //   2a  F[s][k] = u_{s L2 + k} + A F[s][k-1] from F[s][-1] = 0 (L2 steps),
+        //   2b  g_s = E[s L2 - 1]: g_0 = 0, g_s = F[s-1][L2-1] + A^L2 g_{s-1} (C2 - 1 steps),
+        //   2c  E[s L2 + k] = u_{s L2 + k} + A E[s L2 + k - 1] from g_s (L2 steps).
+        const T *W = in;
+        const int C = a.C, L2 = a.L2, C2 = a.C2, M = a.M;
+        auto member_live = [&](int b) {
+            return a.st == nullptr || (a.st[b].active && !a.st[b].skip && !a.st[b].half);
+        };
+        auto u_of = [&](int b, int c, int row) -> T {
+            return c == 0 ? T(0) : ld_cg(W + ((size_t)b * C + c - 1) * M + row);
+        };
+        T *Fi = a.F0, *Fo = a.F1;
+        for (int k = 0; k < L2; ++k) {
+            gen_step(GLs, M, a.rows, r0, a.batch * C2,
+                     [&](int col) -> const T * { return k == 0 ? nullptr : Fi + (size_t)col * M; },
+                     [&](int col, int row) -> T { return u_of(col / C2, (col % C2) * L2 + k, row); },
+                     [&](int col, int row, T v) { __stcg(Fo + (size_t)col * M + row, v); },
+                     [&](int col) { return (col % C2) * L2 + k < C && member_live(col / C2); }, red);
+            if (!grid_barrier(a.bar, a.err, nb)) return;
+            // columns whose super-chunk ended keep F[s][last] in Fi: copy forward
+            // (only full super-chunks feed 2b, so the partial last one needs no copy)
+            T *t = Fi; Fi = Fo; Fo = t;
+        }
+        // Fi: F[s][L2-1] for every full super-chunk s
+        for (int sc = 1; sc < C2; ++sc) {
+            gen_step(GLLs, M, a.rows, r0, a.batch,
+                     [&](int b) -> const T * { return sc == 1 ? nullptr : a.Gc + ((size_t)b * C2 + sc - 1) * M; },
+                     [&](int b, int row) -> T { return ld_cg(Fi + ((size_t)b * C2 + sc - 1) * M + row); },
+                     [&](int b, int row, T v) { __stcg(a.Gc + ((size_t)b * C2 + sc) * M + row, v); },
+                     [&](int b) { return member_live(b); }, red);
+            if (!grid_barrier(a.bar, a.err, nb)) return;
+        }
+        for (int k = 0; k < L2; ++k) {
+            gen_step(GLs, M, a.rows, r0, a.batch * C2,
+                     [&](int col) -> const T * {
+                         const int b = col / C2, sc = col % C2, c = sc * L2 + k;
+                         if (k > 0) return a.E + ((size_t)b * C + c - 1) * M;
+                         return sc == 0 ? nullptr : a.Gc + ((size_t)b * C2 + sc) * M;
+                     },
+                     [&](int col, int row) -> T { return u_of(col / C2, (col % C2) * L2 + k, row); },
+                     [&](int col, int row, T v) {
+                         const int b = col / C2, c = (col % C2) * L2 + k;
+                         __stcg(a.E + ((size_t)b * C + c) * M + row, v);
+                     },
+                     [&](int col) { return (col % C2) * L2 + k < C && member_live(col / C2); }, red);
             if (!grid_barrier(a.bar, a.err, nb)) return;
         }
         // phase 3 starts from the carries
@@ -734,10 +809,15 @@ pit_status dense_setup(Problem *p) {
         }
         PIT_CUDA(cudaMemcpyAsync(p->PhiF64.ptr, Res, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    // G^L for the chunked sweep of the mixed path, L = ceil(sqrt(N + 1))
+    // G^L and G^(L L2) for the chunked sweep of the mixed path: chunks of
+    // L = round((N + 1)^(1/3)) blocks, their carries scanned in super-chunks
+    // of L2 = round(sqrt(C)) chunks (about 2L + 2 L2 + C / L2 dependent steps)
     {
-        int L = (int)ceil(sqrt((double)(p->N + 1)));
+        int L = std::max(1, (int)lround(cbrt((double)(p->N + 1))));
+        const int C = (p->N + L) / L;
+        const int L2 = std::max(1, (int)lround(sqrt((double)C)));
         p->sweep_L = L;
+        p->sweep_L2 = L2;
         double *Res = T1, *Base = T2, *R = T3;
         PIT_CUDA(cudaMemcpyAsync(Base, G, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
         PIT_CUDA(cudaMemsetAsync(Res, 0, mm2 * sizeof(double), s));
@@ -756,6 +836,28 @@ pit_status dense_setup(Problem *p) {
         }
         PIT_TRY(p->GL32.ensure(mm2 * sizeof(float)));
         k_copy_f32<<<blocks, 256, 0, s>>>(Res, p->GL32.as<float>(), mm2);
+        PIT_LAUNCH_CHECK();
+        // (G^L)^L2 by binary powering from Base2 = G^L (T4, T5 and the two of
+        // T1..T3 that do not hold G^L are free here)
+        double *Base2 = T4, *Res2 = T5, *R2 = (Res == T1) ? T2 : T1;
+        PIT_CUDA(cudaMemcpyAsync(Base2, Res, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        PIT_CUDA(cudaMemsetAsync(Res2, 0, mm2 * sizeof(double), s));
+        k_axpby_identity<<<blocks, 256, 0, s>>>(Res2, Res2, 0.0, 0.0, 1.0, M);
+        PIT_LAUNCH_CHECK();
+        int e = L2;
+        while (e > 0) {
+            if (e & 1) {
+                PIT_TRY(mm(h, M, Res2, Base2, R2));
+                std::swap(Res2, R2);
+            }
+            e >>= 1;
+            if (e) {
+                PIT_TRY(mm(h, M, Base2, Base2, R2));
+                std::swap(Base2, R2);
+            }
+        }
+        PIT_TRY(p->GLL32.ensure(mm2 * sizeof(float)));
+        k_copy_f32<<<blocks, 256, 0, s>>>(Res2, p->GLL32.as<float>(), mm2);
         PIT_LAUNCH_CHECK();
     }
     // FP32 copies for the mixed path; Phi also as float-float (hi, lo) for
@@ -906,8 +1008,8 @@ void dense_teardown(Problem *p) {
 
 template <class T>
 static pit_status persistent_sweep(Problem *p, const double *q, double *z, const T *G, const T *GL,
-                                   int L, int C, const MemberState *st, cudaStream_t s,
-                                   bool *launched) {
+                                   const T *GLL, int L, int C, int L2, const MemberState *st,
+                                   cudaStream_t s, bool *launched) {
     *launched = false;
     int dev = 0, sms = 0, coop = 0;
     PIT_CUDA(cudaGetDevice(&dev));
@@ -917,7 +1019,7 @@ static pit_status persistent_sweep(Problem *p, const double *q, double *z, const
     const int rows = (M + sms - 1) / sms;
     if (!coop || rows > SW_MAXROWS) return PIT_OK;            // caller falls back
     const int grid = (M + rows - 1) / rows;
-    const size_t smem = (2 * (size_t)SW_MAXROWS * M + (size_t)SW_MAXROWS * 64) * sizeof(T);
+    const size_t smem = (3 * (size_t)SW_MAXROWS * M + (size_t)SW_MAXROWS * 64) * sizeof(T);
     if (smem > 200 * 1024) return PIT_OK;
     PIT_CUDA(cudaFuncSetAttribute(k_dense_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
@@ -925,16 +1027,23 @@ static pit_status persistent_sweep(Problem *p, const double *q, double *z, const
     PIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_sweep<T>, SW_THREADS,
                                                            smem));
     if (per_sm * sms < grid) return PIT_OK;
+    const int C2 = (C + L2 - 1) / L2;
     const size_t ncols = (size_t)p->batch * C;
+    const size_t ncols2 = (size_t)p->batch * C2;
     const size_t colbytes = ncols * M * sizeof(T);
-    PIT_TRY(p->hat.ensure(3 * colbytes + 64));
+    const size_t colbytes2 = ncols2 * M * sizeof(T);
+    PIT_TRY(p->hat.ensure(3 * colbytes + 3 * colbytes2 + 64));
     T *Za = p->hat.as<T>();
     T *Zb = Za + ncols * M;
     T *E = Zb + ncols * M;
-    unsigned *bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(p->hat.ptr) + 3 * colbytes);
+    T *F0 = E + ncols * M;
+    T *F1 = F0 + ncols2 * M;
+    T *Gc = F1 + ncols2 * M;
+    unsigned *bar = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(p->hat.ptr) + 3 * colbytes +
+                                                 3 * colbytes2);
     PIT_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
-    SweepArgs<T> a{q, z, M, p->N, p->batch, p->blen, L, C, rows, G, GL, Za, Zb, E, bar,
-                   p->errword.as<int>(), st};
+    SweepArgs<T> a{q, z, M, p->N, p->batch, p->blen, L, C, rows, L2, C2, G, GL, GLL, Za, Zb, E,
+                   F0, F1, Gc, bar, p->errword.as<int>(), st};
     void *args[] = {&a};
     PIT_CUDA(cudaLaunchCooperativeKernel((const void *)k_dense_sweep<T>, dim3(grid), dim3(SW_THREADS),
                                          args, smem, s));
@@ -948,11 +1057,11 @@ pit_status dense_sweep(Problem *p, const double *q, double *z, int prec, const M
     bool done = false;
     if (prec == PIT_MIXED) {
         const int L = p->sweep_L, C = (p->N + L) / L;   // ceil((N + 1) / L)
-        PIT_TRY(persistent_sweep<float>(p, q, z, p->G32.as<float>(), p->GL32.as<float>(), L, C, st,
-                                        s, &done));
+        PIT_TRY(persistent_sweep<float>(p, q, z, p->G32.as<float>(), p->GL32.as<float>(),
+                                        p->GLL32.as<float>(), L, C, p->sweep_L2, st, s, &done));
     } else {
-        PIT_TRY(persistent_sweep<double>(p, q, z, p->G64.as<double>(), nullptr, p->N + 1, 1, st, s,
-                                         &done));
+        PIT_TRY(persistent_sweep<double>(p, q, z, p->G64.as<double>(), nullptr, nullptr, p->N + 1, 1,
+                                         1, st, s, &done));
     }
     if (done) return PIT_OK;
     // fallback: one FP64 product per slice

@@ -178,7 +178,9 @@ struct Problem {
     DevBuf dense_scratch;
     void *blas = nullptr;         // cuBLAS handle (dense set-up and FP64 products)
     DevBuf GL32;                  // G^L (FP32) for the chunked dense sweep
+    DevBuf GLL32;                 // G^(L L2) (FP32): carries across super-chunks
     int sweep_L = 1;              // chunk length of the dense sweep
+    int sweep_L2 = 1;             // chunks per super-chunk of the carry scan
     DevBuf errword;               // device-side error word of bounded waits (0 = none)
     DevBuf PhiTh, PhiTl, tc_split;  // TF32 splits of Phi and of the input block vector
     bool use_tc = false;          // dense FP32-class product on the tensor cores
