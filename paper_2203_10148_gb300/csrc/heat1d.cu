@@ -15,6 +15,7 @@
 // and every thread replays its points from the scanned prefix.  A slice's
 // state stays in registers across all fine steps.
 #include <math.h>
+#include <stdlib.h>
 
 #include <type_traits>
 #include <vector>
@@ -451,6 +452,28 @@ pit_status heat1d_setup(Problem *p) {
     // fine factors in fine_inv64/32, coarse in coarse_inv64/32 (fm | inv | cp)
     PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32, p->stream));
     PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32, p->stream));
+    // mixed path: the coarse step (I - dTc nu D2)^{-c} is diagonal in the sine
+    // basis (eigenvalues mu_k = -4/h^2 sin^2(k pi h / 2), k = 1..M), so the
+    // FP32 sweep runs as two sine transforms on the tensor cores around a
+    // per-mode recurrence over the slices (PIT_HEAT1D_TC=0 keeps the
+    // sequential Thomas sweep)
+    const char *env = getenv("PIT_HEAT1D_TC");
+    p->xform_tc = (p->precision == PIT_MIXED && p->M >= 16 && !(env && env[0] == '0') &&
+                   heat1d_tc_setup(p) == PIT_OK) ? 1 : 0;
+    if (p->xform_tc) {
+        const int Mp = heat1d_tc_padded(p->M);
+        const double dtc = p->dT / p->coarse_steps;
+        std::vector<double> g(Mp, 0.0);
+        for (int k = 0; k < p->M; ++k) {
+            const double sk = sin(M_PI * (k + 1) * h / 2.0);
+            const double mu = -4.0 / (h * h) * sk * sk;
+            g[k] = pow(1.0 - dtc * p->nu * mu, -(double)p->coarse_steps);
+        }
+        PIT_TRY(p->gmode.ensure(Mp * sizeof(double)));
+        PIT_CUDA(cudaMemcpyAsync(p->gmode.ptr, g.data(), Mp * sizeof(double), cudaMemcpyHostToDevice,
+                                 p->stream));
+        PIT_CUDA(cudaStreamSynchronize(p->stream));
+    }
     return PIT_OK;
 }
 
@@ -474,6 +497,20 @@ pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec, const 
     if (prec == PIT_FP64) {
         SweepLaunch<double> f{p, q, z, &p->coarse_inv64, st, s};
         return dispatch_1d(p->M, f);
+    }
+    if (p->xform_tc) {
+        // q -> padded FP32 rows -> qhat = q S -> recurrence per mode -> z = (2/(M+1)) zhat S
+        const int M = p->M, Mp = heat1d_tc_padded(M);
+        const size_t R = (size_t)p->batch * (p->N + 1);
+        const int nchunks = (p->N + 1 + 15) / 16;
+        const size_t ends_bytes = (size_t)p->batch * nchunks * Mp * sizeof(double);
+        PIT_TRY(p->hat.ensure(2 * R * Mp * sizeof(float) + ends_bytes));
+        float *h1 = p->hat.as<float>(), *h2 = h1 + R * Mp;
+        double *ends = reinterpret_cast<double *>(h2 + R * Mp);
+        PIT_TRY(heat1d_tc_pack(p, q, h1, s));
+        PIT_TRY(heat1d_tc_xform(p, h1, h2, false, Mp, Mp, 1.0, st, s));
+        PIT_TRY(sine_mode_recurrence(p, h2, ends, Mp, st, s));
+        return heat1d_tc_xform(p, h2, z, true, M, M, 2.0 / (M + 1), st, s);
     }
     SweepLaunch<float> f{p, q, z, &p->coarse_inv32, st, s};
     return dispatch_1d(p->M, f);

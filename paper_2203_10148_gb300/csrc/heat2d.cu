@@ -945,6 +945,26 @@ pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const Member
 
 }  // namespace
 
+// The per-mode recurrence z_n[k] = q_n[k] + g_k z_{n-1}[k] over the N+1
+// blocks of every member, in place on hat ([batch][N+1][nn] FP32, g_k in
+// p->gmode), as the chunked scan of the 2D sweep; ends holds
+// batch * ceil((N+1)/16) * nn doubles.
+pit_status sine_mode_recurrence(Problem *p, float *hat, double *ends, int nn, const MemberState *st,
+                                cudaStream_t s) {
+    const int nblk = p->N + 1;
+    const int nchunks = (nblk + REC_CHUNK - 1) / REC_CHUNK;
+    const int RT = 256;
+    dim3 g1((unsigned)((nn + RT - 1) / RT), nchunks, p->batch);
+    k_rec_local<float><<<g1, RT, 0, s>>>(hat, ends, p->gmode.as<double>(), nn, nblk, nchunks, st);
+    PIT_LAUNCH_CHECK();
+    k_rec_carry<<<dim3((unsigned)((nn + RT - 1) / RT), p->batch), RT, 0, s>>>(
+        ends, p->gmode.as<double>(), nn, nchunks, st);
+    PIT_LAUNCH_CHECK();
+    k_rec_apply<float><<<g1, RT, 0, s>>>(hat, ends, p->gmode.as<double>(), nn, nblk, nchunks, st);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
 pit_status heat2d_setup(Problem *p) {
     if (p->nx != p->ny) {
         set_error("heat2d: only square grids (nx == ny) are supported");

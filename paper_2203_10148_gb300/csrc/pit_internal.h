@@ -158,7 +158,7 @@ struct Problem {
     // heat2d: sine basis S_jk = sin(pi j k/(n+1)) and coarse mode factors
     DevBuf S64, S32, gmode;       // gmode: (1 - dTc nu (mu_k + mu_l))^{-c}
     DevBuf xtc_S;                 // TF32 parts (hi, lo) of S for the tensor-core transforms
-    int xform_tc = 0;             // 2D heat sweeps transform on the tensor cores
+    int xform_tc = 0;             // 2D / 1D heat sweeps transform on the tensor cores
     DevBuf hat;                   // sweep scratch: transformed blocks
 
     // advdiff2d: per-point velocities (FP64 and FP32)
@@ -261,6 +261,16 @@ pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, in
 // n % 4 == 0: out_b = scale (A_b S)^T for every n x n block b of A (FP32,
 // 16-byte aligned), out FP32 or FP64.
 bool heat2d_tc_usable(const Problem *p);
+// 1D heat sweep in the sine basis on the tensor cores (mixed path): rows of
+// length M padded to heat1d_tc_padded(M); S generated on the device.
+int heat1d_tc_padded(int M);
+pit_status heat1d_tc_setup(Problem *p);
+pit_status heat1d_tc_pack(Problem *p, const double *q, float *out, cudaStream_t s);
+pit_status heat1d_tc_xform(Problem *p, const float *A, void *out, bool out64, int nout, int ldo,
+                           double scale, const MemberState *st, cudaStream_t s);
+// per-mode recurrence of the sine-basis sweeps (heat2d.cu)
+pit_status sine_mode_recurrence(Problem *p, float *hat, double *ends, int nn, const MemberState *st,
+                                cudaStream_t s);
 pit_status heat2d_tc_setup(Problem *p, const double *S);
 pit_status heat2d_tc_xform(Problem *p, const float *A, void *out, bool out64, double scale,
                            const MemberState *st, cudaStream_t s);

@@ -97,10 +97,17 @@ size_t serve_footprint(const pit_problem_desc *d) {
         const size_t nn = M;
         const size_t ends = (size_t)d->batch * ((nblk + 15) / 16) * nn * 8;
         b += 4 * vlen + 16 * vlen + ends;                    // FP32 fine output, sweep modes
-        b += 24 * nn;                                        // sine basis, mode factors
-        b = std::max(b, 16 * vlen + 24 * nn + 4096);         // set-up (variant autotuning)
+        b += 32 * nn;                                        // sine bases (FP64, FP32, TF32 parts), mode factors
+        b = std::max(b, 16 * vlen + 32 * nn + 4096);         // set-up (variant autotuning)
     } else {
         b += 48 * M;                                         // Thomas factors
+        if (d->precision == PIT_MIXED) {
+            // sine-basis sweep: TF32 parts of S, two padded FP32 row sets,
+            // chunk ends and mode factors
+            const size_t Mp = (M + 31) / 32 * 32;
+            const size_t rows = nblk * d->batch;
+            b += 8 * Mp * Mp + 8 * rows * Mp + (size_t)d->batch * ((nblk + 15) / 16) * Mp * 8 + 8 * Mp;
+        }
     }
     return b + (256u << 10);                                 // small buffers
 }

@@ -33,6 +33,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "pit_internal.h"
@@ -76,11 +77,19 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // Output tiles t = (block, tj, tk), TN x TN of them per block (TN = 1 for
 // n <= 128, 2 for n <= 256): rows j = 128 tj + lane, columns k = 128 tk + ...;
 // K in KC = ceil(n / 32) chunks.
-template <bool OUT64, bool SRES>
+//
+// ROW1D (1D heat): one matrix of R = batch (N+1) rows of length n (padded),
+// out[r][k] = scale sum_i S[k][i] A[r][i] for k < nout, stored row-major with
+// stride ldo; tiles t = (tk, ti) over 128 modes x 128 rows, the tensor core
+// computing D[k][r] (S as the A operand, the data as B) so that TMEM lanes
+// are modes and a warp's stores cover 32 consecutive k of one row.
+template <bool OUT64, bool SRES, bool ROW1D>
 __global__ void __launch_bounds__(XT_THREADS, 1)
     k_xform_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmSh,
                const __grid_constant__ CUtensorMap tmSl, void *out_raw, int n, int total_tiles,
-               int TN, int nblk, float scale, const MemberState *st, int *err) {
+               int TN, int nblk, int R, int nout, int ldo, float scale, const MemberState *st,
+               int *err) {
+    static_assert(!(ROW1D && SRES), "the 1D transform streams S");
     using LY = XtLayout<SRES>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -141,8 +150,16 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             int q = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-                const int b = t / tpb, tj = (t % tpb) / TN, tk = t % TN;
-                if (!xt_live(st, b / nblk)) continue;
+                int arow, srow;       // first data row and first S row of the tile
+                if constexpr (ROW1D) {
+                    arow = (t % TN) * XT_T;
+                    srow = (t / TN) * XT_T;
+                } else {
+                    const int b = t / tpb, tj = (t % tpb) / TN, tk = t % TN;
+                    if (!xt_live(st, b / nblk)) continue;
+                    arow = b * n + tj * XT_T;
+                    srow = tk * XT_T;
+                }
                 for (int c = 0; c < KC; ++c, ++q) {
                     const int s = q % XT_STAGES, u = q / XT_STAGES;
                     if (!tc_mbar_wait(&empty[s], (uint32_t)(u & 1) ^ 1u, err)) {
@@ -151,10 +168,10 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     }
                     unsigned char *stg = ring + s * LY::kStage;
                     mbar_expect_tx(&full[s], SRES ? XT_CH : 3 * XT_CH);
-                    tma_load_2d(stg, &tmA, c * XT_BK, b * n + tj * XT_T, &full[s]);
+                    tma_load_2d(stg, &tmA, c * XT_BK, arow, &full[s]);
                     if constexpr (!SRES) {
-                        tma_load_2d(stg + 2 * XT_CH, &tmSh, c * XT_BK, tk * XT_T, &full[s]);
-                        tma_load_2d(stg + 3 * XT_CH, &tmSl, c * XT_BK, tk * XT_T, &full[s]);
+                        tma_load_2d(stg + 2 * XT_CH, &tmSh, c * XT_BK, srow, &full[s]);
+                        tma_load_2d(stg + 3 * XT_CH, &tmSl, c * XT_BK, srow, &full[s]);
                     }
                     last_use[s] = u;
                 }
@@ -170,7 +187,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             bool ok = SRES ? tc_mbar_wait(sbar, 0u, err) : true;
             int q = 0, L = 0;
             for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-                if (!xt_live(st, (t / tpb) / nblk)) continue;
+                if (!ROW1D && !xt_live(st, (t / tpb) / nblk)) continue;
                 const int buf = L & 1, v = L >> 1;
                 if (!tc_mbar_wait(&tempty[buf], (uint32_t)(v & 1) ^ 1u, err)) {
                     ok = false;
@@ -192,9 +209,16 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < XT_BK / 8; ++j) {
                         const uint64_t adv = (uint64_t)(j * 32) >> 4;   // 8 TF32 = 32 bytes along K
-                        tc_mma_tf32(d, ah + adv, bh + adv, kXtIdesc, (c > 0 || j > 0) ? 1u : 0u);
-                        tc_mma_tf32(d, ah + adv, bl + adv, kXtIdesc, 1u);
-                        tc_mma_tf32(d, al + adv, bh + adv, kXtIdesc, 1u);
+                        if constexpr (ROW1D) {
+                            // D[k][r]: S rows as the A operand, data rows as B
+                            tc_mma_tf32(d, bh + adv, ah + adv, kXtIdesc, (c > 0 || j > 0) ? 1u : 0u);
+                            tc_mma_tf32(d, bl + adv, ah + adv, kXtIdesc, 1u);
+                            tc_mma_tf32(d, bh + adv, al + adv, kXtIdesc, 1u);
+                        } else {
+                            tc_mma_tf32(d, ah + adv, bh + adv, kXtIdesc, (c > 0 || j > 0) ? 1u : 0u);
+                            tc_mma_tf32(d, ah + adv, bl + adv, kXtIdesc, 1u);
+                            tc_mma_tf32(d, al + adv, bh + adv, kXtIdesc, 1u);
+                        }
                     }
                     mma_commit(&empty[s]);    // chunk free once these products finish
                 }
@@ -211,7 +235,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         int q = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-            if (!xt_live(st, (t / tpb) / nblk)) continue;
+            if (!ROW1D && !xt_live(st, (t / tpb) / nblk)) continue;
             for (int c = 0; c < KC; ++c, ++q) {
                 const int s = q % XT_STAGES, u = q / XT_STAGES;
                 if (!tc_mbar_wait(&full[s], (uint32_t)(u & 1), err)) {
@@ -247,11 +271,38 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
         int L = 0;
         for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
             const int b = t / tpb, tj = (t % tpb) / TN, tk = t % TN;
-            if (!xt_live(st, b / nblk)) continue;
+            if (!ROW1D && !xt_live(st, b / nblk)) continue;
             const int buf = L & 1, v = L >> 1;
             const bool ok = __all_sync(0xffffffffu, tc_mbar_wait(&tfull[buf], (uint32_t)(v & 1), err) ? 1 : 0) != 0;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if constexpr (ROW1D) {
+                // lane = mode k, columns = rows r of the data
+                const int k = (t / TN) * XT_T + quad * 32 + lane;
+                const int rbase = (t % TN) * XT_T;
+#pragma unroll 1
+                for (int cc = 0; cc < XT_T / 32; ++cc) {
+                    float vals[32];
+                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * XT_T + cc * 32), vals);
+                    if (k < nout) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int r = rbase + cc * 32 + i;
+                            if (r < R && xt_live(st, r / nblk)) {
+                                if constexpr (OUT64)
+                                    reinterpret_cast<double *>(out_raw)[(size_t)r * ldo + k] = f2d(scale * vals[i]);
+                                else
+                                    reinterpret_cast<float *>(out_raw)[(size_t)r * ldo + k] = scale * vals[i];
+                            }
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+                ++L;
+                continue;
+            }
             const int j = tj * XT_T + quad * 32 + lane;
 #pragma unroll 1
             for (int cc = 0; cc < XT_T / 32; ++cc) {
@@ -286,14 +337,15 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     }
 }
 
-template <bool OUT64, bool SRES>
+template <bool OUT64, bool SRES, bool ROW1D = false>
 pit_status launch_xform_tc(const CUtensorMap &tA, const CUtensorMap &tSh, const CUtensorMap &tSl,
                            void *out, int n, int total_tiles, int TN, int nblk, float scale,
-                           const MemberState *st, int *err, int grid, cudaStream_t s) {
-    auto kern = k_xform_tc<OUT64, SRES>;
+                           const MemberState *st, int *err, int grid, cudaStream_t s, int R = 0,
+                           int nout = 0, int ldo = 0) {
+    auto kern = k_xform_tc<OUT64, SRES, ROW1D>;
     PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<SRES>::kSmem));
     kern<<<grid, XT_THREADS, XtLayout<SRES>::kSmem, s>>>(tA, tSh, tSl, out, n, total_tiles, TN, nblk,
-                                                          scale, st, err);
+                                                          R, nout, ldo, scale, st, err);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
@@ -357,6 +409,93 @@ pit_status heat2d_tc_xform(Problem *p, const float *A, void *out, bool out64, do
     }
     if (out64) return launch_xform_tc<true, false>(tA, tSh, tSl, out, n, total_tiles, TN, p->N + 1, sc, st, err, grid, s);
     return launch_xform_tc<false, false>(tA, tSh, tSl, out, n, total_tiles, TN, p->N + 1, sc, st, err, grid, s);
+}
+
+// ------------------------------------------------------------ 1D heat
+namespace {
+
+// S[k][i] = sin(pi (k+1)(i+1) / (M+1)) for k, i < M, zero padding to Mp;
+// split into TF32 parts hi = rna(fl32(S)), lo = rna(fl32(S - hi)).  The
+// argument is reduced exactly in integers, (k+1)(i+1) mod 2(M+1).
+__global__ void k_make_dst1d(float *Sh, float *Sl, int M, int Mp) {
+    const size_t total = (size_t)Mp * Mp;
+    const long long period = 2LL * (M + 1);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / Mp), i = (int)(e % Mp);
+        float h = 0.f, l = 0.f;
+        if (k < M && i < M) {
+            const long long m = ((long long)(k + 1) * (i + 1)) % period;
+            const double v = sinpi((double)m / (double)(M + 1));
+            h = tf32_rna(__double2float_rn(v));
+            l = tf32_rna(__double2float_rn(v - (double)h));
+        }
+        Sh[e] = h;
+        Sl[e] = l;
+    }
+}
+
+// rows of length M (FP64 or FP32) into rows of length Mp (FP32, zero padded)
+template <class Tin>
+__global__ void k_pack_rows(const Tin *__restrict__ q, float *__restrict__ out, int R, int M, int Mp) {
+    const size_t total = (size_t)R * Mp;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / Mp), i = (int)(e % Mp);
+        float v = 0.f;
+        if (i < M) {
+            if constexpr (std::is_same<Tin, double>::value) v = d2f_rn(q[(size_t)r * M + i]);
+            else v = q[(size_t)r * M + i];
+        }
+        out[e] = v;
+    }
+}
+
+}  // namespace
+
+int heat1d_tc_padded(int M) { return (M + 31) / 32 * 32; }
+
+pit_status heat1d_tc_setup(Problem *p) {
+    const int M = p->M, Mp = heat1d_tc_padded(M);
+    PIT_TRY(p->xtc_S.ensure(2 * (size_t)Mp * Mp * sizeof(float)));
+    float *Sh = p->xtc_S.as<float>();
+    k_make_dst1d<<<1024, 256, 0, p->stream>>>(Sh, Sh + (size_t)Mp * Mp, M, Mp);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
+// out = scale * (S A^T)^T for the rows of A: A (R x Mp FP32, zero padded),
+// out R x nout with row stride ldo (FP32 or FP64)
+pit_status heat1d_tc_xform(Problem *p, const float *A, void *out, bool out64, int nout, int ldo,
+                           double scale, const MemberState *st, cudaStream_t s) {
+    const int M = p->M, Mp = heat1d_tc_padded(M);
+    const int R = p->batch * (p->N + 1);
+    const int RT = (R + XT_T - 1) / XT_T, KT = (Mp + XT_T - 1) / XT_T;
+    const int total_tiles = RT * KT;
+    const float *Sh = p->xtc_S.as<float>();
+    CUtensorMap tA, tSh, tSl;
+    PIT_TRY(tc_make_map(&tA, A, R, Mp, XT_BK, XT_T));
+    PIT_TRY(tc_make_map(&tSh, Sh, Mp, Mp, XT_BK, XT_T));
+    PIT_TRY(tc_make_map(&tSl, Sh + (size_t)Mp * Mp, Mp, Mp, XT_BK, XT_T));
+    int dev = 0, sms = 0;
+    PIT_CUDA(cudaGetDevice(&dev));
+    PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::min(total_tiles, sms);
+    int *err = p->errword.as<int>();
+    const float sc = (float)scale;
+    if (out64)
+        return launch_xform_tc<true, false, true>(tA, tSh, tSl, out, Mp, total_tiles, RT, p->N + 1, sc,
+                                                  st, err, grid, s, R, nout, ldo);
+    return launch_xform_tc<false, false, true>(tA, tSh, tSl, out, Mp, total_tiles, RT, p->N + 1, sc,
+                                               st, err, grid, s, R, nout, ldo);
+}
+
+pit_status heat1d_tc_pack(Problem *p, const double *q, float *out, cudaStream_t s) {
+    const int M = p->M, Mp = heat1d_tc_padded(M);
+    const int R = p->batch * (p->N + 1);
+    k_pack_rows<double><<<1024, 256, 0, s>>>(q, out, R, M, Mp);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
 }
 
 }  // namespace pit
