@@ -72,7 +72,7 @@ __device__ __forceinline__ bool runs(const MemberState *st, int b) {
 // float-float); u lives in registers for FP32 and in a thread-private
 // shared-memory layout (us[k * threads + tid]) otherwise.
 template <class V, int RX, int RY, bool CL>
-__global__ void __launch_bounds__(CL ? 256 : 2048 / RX,
+__global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY),
                                   (CL && RY == 4 && std::is_same<V, float>::value) ? 2 : 1)
     k_heat2d_fine(Heat2dArgs a) {
     using A = Arith<V>;
@@ -729,28 +729,28 @@ size_t fine_smem(int TXp, int TYp) {
     return s;
 }
 
-void tile_shape(int n, int RX, int &TX, int &TXp, int &TY, int &TYp) {
+void tile_shape(int n, int RX, int RY, int &TX, int &TXp, int &TY, int &TYp) {
     TX = (n + RX - 1) / RX;
     TXp = 1;
     while (TXp < TX) TXp <<= 1;
-    TY = (n + RY8 - 1) / RY8;
+    TY = (n + RY - 1) / RY;
     const int threads = ((TXp * TY + 31) / 32) * 32;
     TYp = threads / TXp;
 }
 
-template <class T, int RX>
+template <class T, int RX, int RY = RY8>
 pit_status launch_fine_rx(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
     int TX, TXp, TY, TYp;
-    tile_shape(p->nx, RX, TX, TXp, TY, TYp);
+    tile_shape(p->nx, RX, RY, TX, TXp, TY, TYp);
     a.TX = TX;
     a.TXp = TXp;
     a.TY = TY;
     a.C = 1;
     const int threads = TXp * TYp;
-    const size_t sm = fine_smem<T, RX, RY8>(TXp, TYp);
-    PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T, RX, RY8, false>,
+    const size_t sm = fine_smem<T, RX, RY>(TXp, TYp);
+    PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T, RX, RY, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_heat2d_fine<T, RX, RY8, false><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
+    k_heat2d_fine<T, RX, RY, false><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
@@ -801,6 +801,7 @@ pit_status launch_fine(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
     if (var == 2) return launch_fine_cluster<T, 4>(p, a, nslices, s);
     if constexpr (F32) {
         if (var == 1) return launch_fine_rx<float, 8>(p, a, nslices, s);
+        if (var == 3) return launch_fine_rx<float, 4, 4>(p, a, nslices, s);   // 4 x 4 tiles, 1024 threads at n = 128
     }
     return launch_fine_rx<T, 4>(p, a, nslices, s);
 }
@@ -1010,7 +1011,8 @@ pit_status heat2d_setup(Problem *p) {
         if (p->xform_tc) PIT_TRY(heat2d_tc_setup(p, S.data()));
     }
     // autotune the fine kernels' variant on this shape: FP32 (inner solves)
-    // among one CTA of 4- or 8-column tiles and a cluster of 8 x 4 tiles;
+    // among one CTA of 4- or 8-column tiles of 8 rows, one CTA of 4 x 4 tiles
+    // and a cluster of 8 x 4 tiles;
     // float-float (true residuals) between one CTA and a cluster.  Every
     // variant evaluates the same arithmetic per point: results do not depend
     // on the choice.  (n > 128 runs clusters only.)
@@ -1024,7 +1026,7 @@ pit_status heat2d_setup(Problem *p) {
                                   std::to_string(p->fine_steps);
         int choice = 0;
         pit_status st = autotune(
-            "heat2d_fp32_variant" + shape, 3,
+            "heat2d_fp32_variant" + shape, 4,
             [&](int c) {
                 p->fine_var32 = c;
                 return heat2d_fine_f32out(p, xin.as<double>(), qout.as<float>(), nullptr, p->stream);
@@ -1046,10 +1048,10 @@ pit_status heat2d_setup(Problem *p) {
         qout.release();
         if (st != PIT_OK) return st;
     }
-    // PIT_HEAT2D_VARIANTS="<fp32>,<ff>" overrides the choices (0..2 each)
+    // PIT_HEAT2D_VARIANTS="<fp32>,<ff>" overrides the choices (FP32 0..3, ff 0 or 2)
     if (const char *ov = getenv("PIT_HEAT2D_VARIANTS")) {
         int v32 = -1, vff = -1;
-        if (sscanf(ov, "%d,%d", &v32, &vff) == 2 && v32 >= 0 && v32 <= 2 && (vff == 0 || vff == 2)) {
+        if (sscanf(ov, "%d,%d", &v32, &vff) == 2 && v32 >= 0 && v32 <= 3 && (vff == 0 || vff == 2)) {
             p->fine_var32 = v32;
             p->fine_var_ff = vff;
         }

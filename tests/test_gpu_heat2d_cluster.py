@@ -128,12 +128,13 @@ def test_cluster_served_equals_solo():
         assert np.array_equal(X, Xs), w.name
 
 
-@pytest.mark.parametrize("variants", ["0,0", "1,0", "2,2"])
+@pytest.mark.parametrize("variants", ["0,0", "1,0", "2,2", "3,0"])
 @pytest.mark.parametrize("case", [dict(n=128, N=3, fine_steps=3), dict(n=100, N=2, fine_steps=4, batch=2),
                                   dict(n=37, N=3, fine_steps=4)])
 def test_fine_variants_small_grids(variants, case, monkeypatch):
-    """Every fine-kernel variant for n <= 128 (one CTA of 4- or 8-column tiles,
-    a cluster of 8 x 4 tiles) matches the oracle and the others bit for bit."""
+    """Every fine-kernel variant for n <= 128 (one CTA of 4- or 8-column tiles
+    of 8 rows, one CTA of 4 x 4 tiles, a cluster of 8 x 4 tiles) matches the
+    oracle and the others bit for bit."""
     pit = _pit()
     monkeypatch.setenv("PIT_HEAT2D_VARIANTS", variants)
     w = inputs.heat2d(**case)
