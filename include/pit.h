@@ -176,6 +176,18 @@ size_t pit_last_error(char *buf, size_t n);
  * RK4 fine and IE coarse; ADVDIFF2D (n = 32 .. 512, a power of two) with RK4
  * fine and one IE coarse step; DENSE with RK4 or IE fine and IE coarse.
  * Others return PIT_E_UNSUPPORTED.
+ * Set-up reads these environment variables (none changes a result beyond
+ * rounding: every choice computes the same operator):
+ *   PIT_GRAPHS=0           per-iteration CUDA graphs off (pit_bicgstab_solve);
+ *   PIT_HEAT2D_TC=0        mixed 2D heat sweeps (96 <= n <= 256) on the FP32
+ *                          pipe instead of the tensor cores;
+ *   PIT_HEAT1D_TC=0        mixed 1D heat sweeps as sequential FP32 Thomas
+ *                          solves instead of sine transforms on the tensor cores;
+ *   PIT_HEAT2D_VARIANTS=a,b  2D heat fine-kernel variants for n <= 128 (FP32
+ *                          a in 0..3, float-float b in {0, 2}) instead of the
+ *                          autotuner's choice (bit-identical results);
+ *   PIT_AUTOTUNE=0         untuned shapes take the built-in variant;
+ *   PIT_AUTOTUNE_CACHE=f   persist the autotuner's choices in file f.
  * Errors: PIT_E_INVALID (bad sizes, non-finite values), PIT_E_NOMEM, PIT_E_CUDA.
  */
 pit_status pit_problem_create(const pit_problem_desc *desc, pit_problem_t *out);
@@ -195,9 +207,10 @@ pit_status pit_problem_shape(pit_problem_t prob, int *M, int *N, int *batch);
  * significant bits on the FP32 pipe: stepping for PIT_OP_HEAT2D and
  * PIT_OP_ADVDIFF2D, a compensated product for PIT_OP_DENSE with M a
  * multiple of 64; PIT_FF means PIT_FP64 otherwise).  G^{-1} runs
- * in reduced precision for PIT_MIXED (2D heat: FP32 sine transforms with
- * float-float running sums; advection-diffusion and dense: FP32) and in
- * FP64 otherwise.  x and y may not overlap.
+ * in reduced precision for PIT_MIXED (2D heat and 1D heat: split-TF32 sine
+ * transforms on the tensor cores with float-float running sums in the sine
+ * basis; advection-diffusion and dense: FP32) and in FP64 otherwise.
+ * x and y may not overlap.
  * With on_device = 0 the call copies through device memory and synchronises.
  */
 pit_status pit_apply_operator(pit_problem_t prob, int which, int precision,
