@@ -106,7 +106,9 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     uint64_t *mdone = sbar + 1;                  // all products issued have finished
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int KC = (n + XT_BK - 1) / XT_BK;
+    // K chunks per tile: all four for a resident S (n <= 128, chunks past n
+    // read as zero), ceil(n / 32) otherwise
+    const int KC = SRES ? XT_T / XT_BK : (n + XT_BK - 1) / XT_BK;
     const int tpb = TN * TN;                     // tiles per block
 
     if (threadIdx.x == 0) {
