@@ -72,7 +72,7 @@ __device__ __forceinline__ bool runs(const MemberState *st, int b) {
 // float-float); u lives in registers for FP32 and in a thread-private
 // shared-memory layout (us[k * threads + tid]) otherwise.
 template <class V, int RX, int RY, bool CL>
-__global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY),
+__global__ void __launch_bounds__(CL ? (RX == 4 ? 512 : 256) : 16384 / (RX * RY),
                                   (CL && RY == 4 && std::is_same<V, float>::value) ? 2 : 1)
     k_heat2d_fine(Heat2dArgs a) {
     using A = Arith<V>;
@@ -91,6 +91,13 @@ __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY),
     V *rows = reinterpret_cast<V *>(smem_raw + 32);   // [2 buf][2 top/bot][TYp][W]
     V *us = rows + 4 * (size_t)TYp * W;           // u, thread-private layout
     constexpr bool U_SMEM = A::kUInSmem;
+    // rows of more than 32 thread columns span two warps: the west / east
+    // neighbours across the warp boundary go through a column buffer
+    // [2 buf][TYp][2 warps][2 west/east][RY] published with the row buffers
+    V *colb = us + (U_SMEM ? (size_t)a.TXp * TYp * RY * RX : 0);
+    constexpr bool kWide = CL && RX == 4;         // only the 4-column clusters have such rows
+    const bool wide = kWide && a.TXp > 32;
+    const int lane = tid & 31, wir = (tid % a.TXp) >> 5;   // warp within the thread row
 
     // band of rows owned by this CTA (the whole grid without clusters)
     const int rank = CL ? (int)(blockIdx.x % (unsigned)a.C) : 0;
@@ -160,6 +167,11 @@ __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY),
                 A::st4(rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0 + q, t0);
                 A::st4(rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0 + q, t1);
             }
+            if (kWide && wide && (lane == 0 || lane == 31)) {
+                V *cb = colb + (((size_t)(buf * TYp + ty) * 2 + wir) * 2 + (lane == 0 ? 0 : 1)) * RY;
+#pragma unroll
+                for (int r = 0; r < RY; ++r) cb[r] = (lane == 0) ? v[r][0] : v[r][RX - 1];
+            }
             if constexpr (CL) cg::this_cluster().sync();
             else __syncthreads();
             const V cc = ccs[stage];
@@ -206,10 +218,23 @@ __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY),
                         cA[c] = v[r][c];
                         cB[c] = v[r + H][c];
                     }
-                    const V wA = A::sel(west_zero, A::zero(), A::shfl_up(cA[RX - 1]));
-                    const V wB = A::sel(west_zero, A::zero(), A::shfl_up(cB[RX - 1]));
-                    const V eA = A::sel(east_zero, A::zero(), A::shfl_down(cA[0]));
-                    const V eB = A::sel(east_zero, A::zero(), A::shfl_down(cB[0]));
+                    V wA = A::shfl_up(cA[RX - 1]), wB = A::shfl_up(cB[RX - 1]);
+                    V eA = A::shfl_down(cA[0]), eB = A::shfl_down(cB[0]);
+                    if (kWide && wide) {
+                        const V *cbt = colb + (size_t)(buf * TYp + ty) * 4 * RY;
+                        if (lane == 0 && wir == 1) {      // east column of warp 0
+                            wA = cbt[(0 * 2 + 1) * RY + r];
+                            wB = cbt[(0 * 2 + 1) * RY + r + H];
+                        }
+                        if (lane == 31 && wir == 0) {     // west column of warp 1
+                            eA = cbt[(1 * 2 + 0) * RY + r];
+                            eB = cbt[(1 * 2 + 0) * RY + r + H];
+                        }
+                    }
+                    wA = A::sel(west_zero, A::zero(), wA);
+                    wB = A::sel(west_zero, A::zero(), wB);
+                    eA = A::sel(east_zero, A::zero(), eA);
+                    eB = A::sel(east_zero, A::zero(), eB);
 #pragma unroll
                     for (int c = 0; c < RX; ++c) {
                         const V sA = (r < H - 1) ? v[r + 1][c] : rowH[c];
@@ -249,6 +274,11 @@ __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY),
                 }
                 V w_in = A::shfl_up(v[r][RX - 1]);
                 V e_in = A::shfl_down(v[r][0]);
+                if (kWide && wide) {
+                    const V *cbt = colb + (size_t)(buf * TYp + ty) * 4 * RY;
+                    if (lane == 0 && wir == 1) w_in = cbt[(0 * 2 + 1) * RY + r];
+                    if (lane == 31 && wir == 0) e_in = cbt[(1 * 2 + 0) * RY + r];
+                }
                 V cur[RX];
 #pragma unroll
                 for (int c = 0; c < RX; ++c) cur[c] = v[r][c];
@@ -726,6 +756,7 @@ template <class V, int RX, int RY>
 size_t fine_smem(int TXp, int TYp) {
     size_t s = 32 + 4 * (size_t)TYp * TXp * RX * sizeof(V);
     if (Arith<V>::kUInSmem) s += (size_t)TXp * TYp * RY * RX * sizeof(V);
+    s += (size_t)2 * TYp * 4 * RY * sizeof(V);   // column buffer of two-warp rows
     return s;
 }
 
@@ -755,14 +786,16 @@ pit_status launch_fine_rx(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s)
     return PIT_OK;
 }
 
-// Clusters: C = ceil(n / BH) CTAs of 256 threads per slice, each thread an
-// RY x 8 tile, TXp = 2^ceil(log2(n/8)) <= 32 threads per row of tiles and
-// TYp = 256 / TXp rows of them, so a CTA owns a band of BH = TYp * RY rows.
-// For n > 128: RY = 8 for FP32, 4 for FP64 and float-float (whose u and row
-// buffers take twice the shared memory); for n <= 128 (variant 2): RY = 4.
-template <class T, int RY>
+// Clusters: C = ceil(n / BH) CTAs per slice, each thread an RY x RX tile,
+// TXp = 2^ceil(log2(n/RX)) threads per row of tiles and TYp = threads / TXp
+// rows of them, so a CTA owns a band of BH = TYp * RY rows.  RX = 8: 256
+// threads (TXp <= 32); for n > 128 RY = 8 for FP32, 4 for FP64 and
+// float-float (whose u and row buffers take twice the shared memory); for
+// n <= 128 (variant 2) RY = 4.  RX = 4 (the wide variant for n > 128): 512
+// threads, TXp = 64 (rows of two warps), RY = 8, bands of 64 rows.
+template <class T, int RY, int RX = 8>
 pit_status launch_fine_cluster(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
-    constexpr int RX = 8, THREADS = 256;
+    constexpr int THREADS = RX == 4 ? 512 : 256;
     const int n = p->nx;
     a.TX = (n + RX - 1) / RX;
     a.TXp = 1;
@@ -792,11 +825,18 @@ pit_status launch_fine_cluster(Problem *p, Heat2dArgs a, int nslices, cudaStream
 }
 
 // n <= 128: the variant chosen by the autotuner (FP32, float-float); FP64
-// runs one CTA of 4-column tiles.  128 < n <= 256: clusters.
+// runs one CTA of 4-column tiles.  128 < n <= 256: clusters (FP32 and
+// float-float: 8-column or, wide, 4-column tiles, as autotuned).
 template <class T>
 pit_status launch_fine(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
     constexpr bool F32 = std::is_same<T, float>::value;
-    if (p->nx > 128) return launch_fine_cluster<T, F32 ? 8 : 4>(p, a, nslices, s);
+    if (p->nx > 128) {
+        if constexpr (!std::is_same<T, double>::value) {
+            const int vb = F32 ? p->fine_var32_big : p->fine_var_ff_big;
+            if (vb == 1) return launch_fine_cluster<T, 8, 4>(p, a, nslices, s);
+        }
+        return launch_fine_cluster<T, F32 ? 8 : 4>(p, a, nslices, s);
+    }
     const int var = F32 ? p->fine_var32 : std::is_same<T, ff>::value ? p->fine_var_ff : 0;
     if (var == 2) return launch_fine_cluster<T, 4>(p, a, nslices, s);
     if constexpr (F32) {
@@ -1048,12 +1088,53 @@ pit_status heat2d_setup(Problem *p) {
         qout.release();
         if (st != PIT_OK) return st;
     }
-    // PIT_HEAT2D_VARIANTS="<fp32>,<ff>" overrides the choices (FP32 0..3, ff 0 or 2)
+    // n > 128: 8-column clusters (256 threads) or wide 4-column ones (512
+    // threads, rows of two warps), FP32 and float-float tuned separately
+    if (p->precision == PIT_MIXED && p->nx > 128) {
+        DevBuf xin, qout;
+        PIT_TRY(xin.ensure(p->vlen * sizeof(double)));
+        PIT_TRY(qout.ensure(p->vlen * sizeof(double)));
+        PIT_CUDA(cudaMemsetAsync(xin.ptr, 0, p->vlen * sizeof(double), p->stream));
+        const std::string shape = "|n" + std::to_string(p->nx) + "|slices" +
+                                  std::to_string((long long)p->N * p->batch) + "|m" +
+                                  std::to_string(p->fine_steps);
+        int choice = 0;
+        pit_status st = autotune(
+            "heat2d_big_fp32_variant" + shape, 2,
+            [&](int c) {
+                p->fine_var32_big = c;
+                return heat2d_fine_f32out(p, xin.as<double>(), qout.as<float>(), nullptr, p->stream);
+            },
+            p->stream, &choice, 0);
+        p->fine_var32_big = choice;
+        if (st == PIT_OK) {
+            st = autotune(
+                "heat2d_big_ff_variant" + shape, 2,
+                [&](int c) {
+                    p->fine_var_ff_big = c;
+                    Heat2dArgs a = make_args(p, xin.as<double>(), qout.as<double>(), FINE_APPLY, nullptr);
+                    return launch_fine<ff>(p, a, p->N, p->stream);
+                },
+                // untuned (serving): the wide clusters measured 4-14% faster from n = 192
+                p->stream, &choice, p->nx >= 192 ? 1 : 0);
+            p->fine_var_ff_big = choice;
+        }
+        xin.release();
+        qout.release();
+        if (st != PIT_OK) return st;
+    }
+    // PIT_HEAT2D_VARIANTS="<fp32>,<ff>[,<fp32 n>128>,<ff n>128>]" overrides the
+    // choices (FP32 0..3, ff 0 or 2; n > 128: 0 or 1 each)
     if (const char *ov = getenv("PIT_HEAT2D_VARIANTS")) {
-        int v32 = -1, vff = -1;
-        if (sscanf(ov, "%d,%d", &v32, &vff) == 2 && v32 >= 0 && v32 <= 3 && (vff == 0 || vff == 2)) {
+        int v32 = -1, vff = -1, b32 = -1, bff = -1;
+        const int got = sscanf(ov, "%d,%d,%d,%d", &v32, &vff, &b32, &bff);
+        if (got >= 2 && v32 >= 0 && v32 <= 3 && (vff == 0 || vff == 2)) {
             p->fine_var32 = v32;
             p->fine_var_ff = vff;
+        }
+        if (got == 4 && (b32 == 0 || b32 == 1) && (bff == 0 || bff == 1)) {
+            p->fine_var32_big = b32;
+            p->fine_var_ff_big = bff;
         }
     }
     return PIT_OK;

@@ -151,3 +151,24 @@ def test_fine_variants_small_grids(variants, case, monkeypatch):
         bff = p.apply("F", X, precision="ff")
     assert np.array_equal(g32, b32)
     assert np.array_equal(gff, bff)
+
+
+@pytest.mark.parametrize("case", [dict(n=256, N=2, fine_steps=3), dict(n=160, N=3, fine_steps=2, batch=2),
+                                  dict(n=201, N=2, fine_steps=3), dict(n=129, N=2, fine_steps=2)])
+def test_wide_clusters_equal_narrow_ones(case, monkeypatch):
+    """For n > 128 the clusters of 4-column tiles (512 threads, thread rows of
+    two warps whose boundary columns go through shared memory) give the
+    8-column clusters' results bit for bit, FP32 and float-float, and match
+    the oracle."""
+    pit = _pit()
+    w = inputs.heat2d(**case)
+    X = _rand_block(w, 35)
+    out = {}
+    for big in ("0,0", "1,1"):
+        monkeypatch.setenv("PIT_HEAT2D_VARIANTS", "0,0," + big)
+        with pit.Problem(w, "mixed") as p:
+            out[big] = (p.apply("F", X, precision="mixed"), p.apply("F", X, precision="ff"))
+    assert np.array_equal(out["0,0"][0], out["1,1"][0])
+    assert np.array_equal(out["0,0"][1], out["1,1"][1])
+    ref = _oracle_apply(w, "F", X)
+    assert _rel(out["1,1"][0], ref) < 2e-5
