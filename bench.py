@@ -37,6 +37,8 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# directory for the clock samples taken during the timed region
+CLOCKS_DIR = os.environ.get("PIT_BENCH_CLOCKS_DIR", ROOT)
 sys.path.insert(0, ROOT)
 
 from paper_2203_10148_gb300 import inputs  # noqa: E402
@@ -390,7 +392,7 @@ def run_ours(args):
     # timed mode there); the clock sampler starts before the warm-up too, so
     # its start-up does not fall into the timed region
     prob.set_timing(True)
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+    clk = ClockSampler(os.path.join(CLOCKS_DIR,
                                     f"clocks_rank{rank}.csv"))
     with clk:
         with torch.cuda.stream(stream):
@@ -596,7 +598,7 @@ def run_serving(args):
         dist.barrier()
     srv.stats(reset=True)
     launches0 = pit.kernel_launches()
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+    clk = ClockSampler(os.path.join(CLOCKS_DIR,
                                     f"clocks_rank{rank}.csv"))
     results = []
     with clk:

@@ -16,7 +16,7 @@ Bi-Conjugate Gradient Algorithm" (arXiv 2203.10148) it follows:
 * Sec. 3, eq. (7): the inverses of the block operators; G^{-1} is applied
   by forward substitution (a sequential sweep, Sec. 3 text after Alg. 1).
 
-Readings of points the paper leaves open (each listed in the design doc):
+Readings of points the paper leaves open:
 
 * Lambda has N+1 blocks lambda_0..lambda_N (eq. (7) shows F^N in the
   bottom-left corner and the text after Algorithm 1 places the iterates in
