@@ -276,7 +276,10 @@ def run_reference(args):
     cb["value"] = v
     line = {"impl": "reference", "metric": "PiT solves/s (rel err <= 1e-6 vs FP64 path)",
             "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup,
+            # the oracle's estimated time for one step of this workload (a batch of solves)
+            "ms_per_step": (1e3 * w.batch / v) if v else None,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "batch": w.batch, "grid": [w.nx, w.ny], "N": w.N,
                        "fine": list(w.fine), "coarse": list(w.coarse), "tol": 1e-6},
