@@ -62,8 +62,9 @@ OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 179, "fine_fp64": 20}
 ADV_OPS_PER_POINT_STEP = 56
 # float-float advection-diffusion stage: 33 (Laplacian sum) + 16 (upwind
 # differences) + 12 (three products with error terms) + 16 (their sum) + 15
-# (u + cc L) = 92 FP32 operations, 4 stages
-ADV_FF_OPS_PER_POINT_STEP = 368
+# (u + cc L) = 92 FP32 operations, 4 stages; 90 when the coefficients are
+# FP32 values (their low-part terms vanish), as in the synthetic workload
+ADV_FF_OPS_PER_POINT_STEP = 360
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2          # 1.25 TFLOP/s nominal FP64 = 2 FMA/clk/SM at 2.07 GHz x 152 SMs
 KERNEL_NAMES = {"fine_fp32": "k_heat2d_fine<float>", "fine_ff": "k_heat2d_fine<ff>",

@@ -32,6 +32,7 @@
 // (bounded waits).
 #include <cooperative_groups.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -117,6 +118,43 @@ __device__ __forceinline__ ff adv_stage<ff>(ff vn, ff vs, ff vw, ff ve, ff vc, f
     const ff s2 = two_sum(s1.hi, -p3);
     const float l_lo = (s1.lo + s2.lo) + ((e1 - e2) - e3);
     // u + cc L
+    const float p = __fmul_rn(cc.hi, s2.hi);
+    float e = fmaf(cc.hi, s2.hi, -p);
+    e = fmaf(cc.hi, l_lo, e);
+    e = fmaf(cc.lo, s2.hi, e);
+    const ff t = two_sum(u.hi, p);
+    return fast_two_sum(t.hi, t.lo + (u.lo + e));
+}
+
+// The same stage for coefficients that are FP32 values (low parts zero):
+// the low-part terms of the two coefficient products vanish (90 operations).
+__device__ __forceinline__ ff adv_stage_c32(ff vn, ff vs, ff vw, ff ve, ff vc, ff u, ff cc, ff nud,
+                                            float ax, float ay) {
+    const ff a = two_sum(ve.hi, vw.hi);
+    const ff b = two_sum(vn.hi, vs.hi);
+    const ff c = two_sum(a.hi, b.hi);
+    const ff d = two_sum(c.hi, __fmul_rn(-4.f, vc.hi));
+    const float lap_lo = fmaf(-4.f, vc.lo, ((a.lo + b.lo) + (c.lo + d.lo)) +
+                                              ((ve.lo + vw.lo) + (vn.lo + vs.lo)));
+    const ff x1 = ax >= 0.f ? vc : ve, x2 = ax >= 0.f ? vw : vc;
+    const ff y1 = ay >= 0.f ? vc : vs, y2 = ay >= 0.f ? vn : vc;
+    const ff dx = two_sum(x1.hi, -x2.hi);
+    const float dx_lo = dx.lo + (x1.lo - x2.lo);
+    const ff dy = two_sum(y1.hi, -y2.hi);
+    const float dy_lo = dy.lo + (y1.lo - y2.lo);
+    const float p1 = __fmul_rn(nud.hi, d.hi);
+    float e1 = fmaf(nud.hi, d.hi, -p1);
+    e1 = fmaf(nud.hi, lap_lo, e1);
+    e1 = fmaf(nud.lo, d.hi, e1);
+    const float p2 = __fmul_rn(ax, dx.hi);
+    float e2 = fmaf(ax, dx.hi, -p2);
+    e2 = fmaf(ax, dx_lo, e2);
+    const float p3 = __fmul_rn(ay, dy.hi);
+    float e3 = fmaf(ay, dy.hi, -p3);
+    e3 = fmaf(ay, dy_lo, e3);
+    const ff s1 = two_sum(p1, -p2);
+    const ff s2 = two_sum(s1.hi, -p3);
+    const float l_lo = (s1.lo + s2.lo) + ((e1 - e2) - e3);
     const float p = __fmul_rn(cc.hi, s2.hi);
     float e = fmaf(cc.hi, s2.hi, -p);
     e = fmaf(cc.hi, l_lo, e);
@@ -225,7 +263,7 @@ struct RowChunks<ff> {
 // coefficients in shared memory), double or float-float (state in shared
 // memory, coefficients read through L1; float-float coefficients are
 // (hi, lo) float pairs).
-template <class T, bool DBUF>
+template <class T, bool DBUF, bool C32 = false>
 __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
     constexpr bool FP32 = std::is_same<T, float>::value;
     constexpr bool FF = std::is_same<T, ff>::value;
@@ -360,6 +398,14 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
                     } else if constexpr (FF) {
                         u = us[slot];
                         const size_t k = (size_t)(j0 + r) * n + (i0 + c);
+                        if constexpr (C32) {
+                            // FP32 coefficients: the low parts are zero
+                            const float* fx = reinterpret_cast<const float *>(a.ax);
+                            const float* fy = reinterpret_cast<const float *>(a.ay);
+                            v[r][c] = adv_stage_c32(vn, vs, vw, ve, cur[c], u, cc, nud, __ldg(fx + k),
+                                                    __ldg(fy + k));
+                            continue;
+                        }
                         const float2 cx = __ldg(gax2 + k), cy = __ldg(gay2 + k);
                         ax = ff{cx.x, cx.y};
                         ay = ff{cy.x, cy.y};
@@ -468,16 +514,15 @@ AdvArgs adv_args(Problem *p, const double *x, double *y, float *y32, int mode,
     return a;
 }
 
-template <class T, bool DBUF>
+template <class T, bool DBUF, bool C32 = false>
 pit_status launch_adv_fine_v(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
     const int n = p->nx;
     const int CS = n / AD_ROWS;
     const size_t sm = adv_smem<T, DBUF>(n);
-    PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<T, DBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm));
+    auto kern = k_advdiff_fine<T, DBUF, C32>;
+    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (CS > 8)
-        PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<T, DBUF>,
-                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     a.N = nslices;   // slices in this launch (output blocks n_first .. n_first + nslices - 1)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(CS * nslices * p->batch), 1, 1);
@@ -491,16 +536,25 @@ pit_status launch_adv_fine_v(Problem *p, AdvArgs a, int nslices, cudaStream_t s)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    PIT_CUDA(cudaLaunchKernelEx(&cfg, k_advdiff_fine<T, DBUF>, a));
+    PIT_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
-// double-buffered row exchange when it fits, single-buffered otherwise
+// double-buffered row exchange when it fits, single-buffered otherwise;
+// float-float with FP32 coefficients reads them as FP32 values
 template <class T>
 pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
+    if constexpr (std::is_same<T, ff>::value) {
+        if (p->adv_coef32) {
+            a.ax = p->vx32.ptr;
+            a.ay = p->vy32.ptr;
+            if (adv_smem<T, true>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, true, true>(p, a, nslices, s);
+            if (adv_smem<T, false>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, false, true>(p, a, nslices, s);
+        }
+    }
     if (adv_smem<T, true>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, true>(p, a, nslices, s);
     if (adv_smem<T, false>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, false>(p, a, nslices, s);
     set_error("advdiff2d: the slice does not fit the cluster's shared memory");
@@ -777,6 +831,11 @@ pit_status advdiff_setup(Problem *p) {
         PIT_CUDA(cudaMemcpy(vx.data(), p->vx64.ptr, M * sizeof(double), cudaMemcpyDeviceToHost));
         PIT_CUDA(cudaMemcpy(vy.data(), p->vy64.ptr, M * sizeof(double), cudaMemcpyDeviceToHost));
         const double dtc = p->dT / p->coarse_steps, nud = p->nu * n * (double)n;
+        // every coefficient an FP32 value: the float-float stage can drop their low parts
+        bool c32 = !(getenv("PIT_ADV_COEF32") && getenv("PIT_ADV_COEF32")[0] == '0');
+        for (size_t i = 0; i < M && c32; ++i)
+            c32 = (double)(float)vx[i] == vx[i] && (double)(float)vy[i] == vy[i];
+        p->adv_coef32 = c32 ? 1 : 0;
         double rho = 0.0;
         for (size_t i = 0; i < M; ++i) {
             const double D = 1.0 + dtc * (4.0 * nud + fabs(vx[i]) + fabs(vy[i]));

@@ -166,6 +166,7 @@ struct Problem {
     DevBuf vxff, vyff;            // advdiff coefficients as float-float (hi, lo) pairs
     DevBuf adv_scratch;
     int adv_K = 8;                // Chebyshev steps of the coarse IE step
+    int adv_coef32 = 0;           // every coefficient v / h is an FP32 value (float-float lo parts zero)
     double adv_inv_theta = 1.0, adv_c1[16] = {}, adv_c2[16] = {};   // Chebyshev coefficients
 
     // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)

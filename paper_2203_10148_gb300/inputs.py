@@ -213,7 +213,10 @@ def advdiff2d(n: int = 512, nu: float = 5e-3, T: float = 0.5, N: int = 256,
         dpsi_dy += a[j] * 2.0 * np.pi * k[j, 1] * np.cos(arg)
     vx, vy = dpsi_dy, -dpsi_dx
     scale = 1.0 / np.max(np.sqrt(vx * vx + vy * vy))
-    vx, vy = vx * scale, vy * scale
+    # the velocity field sampled as FP32 values (every coefficient v / h of a
+    # power-of-two grid is then exact in FP32); both sides read these arrays
+    vx = (vx * scale).astype(np.float32).astype(np.float64)
+    vy = (vy * scale).astype(np.float32).astype(np.float64)
     y0s = []
     for _ in range(batch):
         kk = _integer_modes(s, u_modes, 4)

@@ -135,3 +135,24 @@ def test_advdiff_full_size_sampled():
     assert _rel(Y64[rows], ref) < 1e-12
     assert _rel(Yff[rows], ref) < 1e-11
     assert _rel(Y32[rows], ref) < 1e-4
+
+
+@pytest.mark.parametrize("case", [dict(n=64, N=3, batch=2), dict(n=128, N=2)])
+def test_advdiff_float_float_fp32_coefficients(case, monkeypatch):
+    """The workload's velocities are FP32 values, so every coefficient v / h
+    is exact in FP32 and the float-float kernel reads them as such (their low
+    parts are zero): the same results bit for bit as the general (hi, lo)
+    kernel, and the oracle's within 1e-11."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.advdiff2d(**case, T=0.5 * case["N"] / 256)
+    assert np.array_equal(w.vx.astype(np.float32).astype(np.float64), w.vx)
+    X = _rand(w, 91)
+    monkeypatch.setenv("PIT_ADV_COEF32", "1")
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("F", X, precision="ff")
+    monkeypatch.setenv("PIT_ADV_COEF32", "0")
+    with pit.Problem(w, "mixed") as p:
+        gen = p.apply("F", X, precision="ff")
+    assert np.array_equal(got, gen)
+    ref = np.stack([OracleProblem.from_workload(w, member=b).apply_F(X[b]) for b in range(w.batch)])
+    assert _rel(got, ref) < 1e-11
