@@ -178,7 +178,9 @@ size_t pit_last_error(char *buf, size_t n);
  * Others return PIT_E_UNSUPPORTED.
  * Set-up reads these environment variables (none changes a result beyond
  * rounding: every choice computes the same operator):
- *   PIT_GRAPHS=0           per-iteration CUDA graphs off (pit_bicgstab_solve);
+ *   PIT_GRAPHS=0           CUDA graphs of the iterations off (pit_bicgstab_solve);
+ *   PIT_GRAPH_LOOP=k       iterations per launch of the loop graph (default
+ *                          16; 0: one graph launch per iteration);
  *   PIT_HEAT2D_TC=0        mixed 2D heat sweeps (96 <= n <= 256) on the FP32
  *                          pipe instead of the tensor cores;
  *   PIT_HEAT1D_TC=0        mixed 1D heat sweeps as sequential FP32 Thomas
@@ -236,7 +238,15 @@ pit_status pit_serial_fine(pit_problem_t prob, int precision, double *Lam, int o
  * the first, eager, iteration of each inner solve and replayed for the
  * others; the graph is kept with the problem (re-captured when the stream
  * or the timing mode changes) and info.graph_iterations counts the
- * replays.  Results are bit for bit those of eager launches.  The
+ * replays.  By default the replays run as a loop graph: a conditional
+ * while node around the captured iteration and a one-warp condition kernel
+ * that stops it once no member is active or after PIT_GRAPH_LOOP (16)
+ * iterations, so that the host reads the member states once per launch
+ * instead of once per iteration (cancellation and the iteration guard are
+ * checked between launches).  With event timing (pit_set_timing)
+ * or a residual history (opts.history) one graph launch runs one
+ * iteration.  Results are bit for bit those of eager launches; the loop
+ * graph launches one condition kernel more per iteration.  The
  * environment variable PIT_GRAPHS=0, read by pit_problem_create, turns the
  * graphs off; a stream that cannot be captured (the legacy default stream)
  * runs every iteration eagerly.

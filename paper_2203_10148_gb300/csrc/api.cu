@@ -5,6 +5,7 @@
 // member is still iterating.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -417,21 +418,30 @@ struct HostStates {
     pit_status init(int b) {
         batch = b;
         v.resize(b);
-        if (tl_pinned.cap < b) {
+        // one record more than the batch: its first bytes take the loop
+        // graph's iteration count
+        if (tl_pinned.cap < b + 1) {
             if (tl_pinned.ptr) cudaFreeHost(tl_pinned.ptr);
             tl_pinned.ptr = nullptr;
             tl_pinned.cap = 0;
-            PIT_CUDA(cudaMallocHost(&tl_pinned.ptr, sizeof(MemberState) * b));
-            tl_pinned.cap = b;
+            PIT_CUDA(cudaMallocHost(&tl_pinned.ptr, sizeof(MemberState) * (b + 1)));
+            tl_pinned.cap = b + 1;
         }
         pinned = tl_pinned.ptr;
         return PIT_OK;
     }
-    pit_status fetch(Problem *p, cudaStream_t s) {
+    // The member states and, with `count_dev`, the int it points to (into
+    // *count), after one stream synchronisation.
+    pit_status fetch(Problem *p, cudaStream_t s, const int *count_dev = nullptr,
+                     int *count = nullptr) {
+        int *cnt_pinned = reinterpret_cast<int *>(pinned + batch);
+        if (count_dev)
+            PIT_CUDA(cudaMemcpyAsync(cnt_pinned, count_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
         PIT_CUDA(cudaMemcpyAsync(pinned, p->states.ptr, sizeof(MemberState) * batch,
                                  cudaMemcpyDeviceToHost, s));
         PIT_CUDA(cudaStreamSynchronize(s));
         std::copy(pinned, pinned + batch, v.begin());
+        if (count_dev && count) *count = *cnt_pinned;
         return PIT_OK;
     }
     bool any_active() const {
@@ -501,6 +511,86 @@ pit_status iter_graph_ready(Problem *p, IterGraph &g, cudaStream_t s, Fn &&itera
     return PIT_OK;
 }
 
+// Condition of the loop graph's while node, run after every iteration of
+// its body: count the iteration and go on while some member is active and
+// fewer than `limit` iterations ran in this launch (the host reads the
+// states and the count between launches: cancellation, the iteration guard).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const MemberState *__restrict__ st,
+                            int batch, int *count, int limit) {
+    int any = 0;
+    for (int b = threadIdx.x; b < batch; b += 32) any |= st[b].active;
+    any = __any_sync(0xffffffffu, any);
+    if (threadIdx.x == 0) {
+        const int c = *count + 1;
+        *count = c;
+        cudaGraphSetConditional(h, (any && c < limit) ? 1u : 0u);
+    }
+}
+
+// The iteration loop as one graph: a conditional while node (its value set
+// to 1 at every launch) whose body is the captured iteration followed by
+// k_loop_cond, so that up to p->loop_chunk iterations run per launch with
+// no host round trip between them.  The host clears p->loopctl before each
+// launch.  Event-record nodes cannot sit in a conditional body, so timed
+// solves keep the per-iteration graph; where the loop graph cannot be built
+// it is marked failed and the per-iteration graph runs instead.
+template <class Fn>
+pit_status loop_graph_ready(Problem *p, IterGraph &g, cudaStream_t s, Fn &&iteration) {
+    const void *ptrs[5] = {p->P.ptr, p->D.ptr, p->S.ptr, p->K.ptr, p->states.ptr};
+    if (g.exec && g.stream == s && std::equal(ptrs, ptrs + 5, g.ptrs)) return PIT_OK;
+    iter_graph_drop(p, g);
+    cudaGraph_t graph = nullptr;
+    auto give_up = [&]() {
+        (void)cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        g.failed = true;
+        return PIT_OK;
+    };
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return give_up();
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return give_up();
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) return give_up();
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return give_up();
+    tl_capturing = true;
+    const unsigned long long k0 = tl_launches;
+    pit_status st = iteration();
+    if (st == PIT_OK) {
+        k_loop_cond<<<1, 32, 0, s>>>(h, p->states.as<MemberState>(), p->batch,
+                                     p->loopctl.as<int>(), p->loop_chunk);
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        ++tl_launches;
+        if (cudaGetLastError() != cudaSuccess) st = PIT_E_CUDA;
+    }
+    // captured launches do not run: the counter counts each iteration instead
+    g.kernels = tl_launches - k0;
+    g_launches -= g.kernels;
+    tl_capturing = false;
+    cudaGraph_t captured = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &captured);
+    if (st != PIT_OK || e != cudaSuccess || captured != body) return give_up();
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    graph = nullptr;
+    if (ei != cudaSuccess) {
+        g.exec = nullptr;
+        return give_up();
+    }
+    g.stream = s;
+    g.timed = false;
+    std::copy(ptrs, ptrs + 5, g.ptrs);
+    return PIT_OK;
+}
+
 pit_status check_cancel(const Problem *p) {
     if (p->cancel && *p->cancel) {
         set_error("the solve was cancelled");
@@ -545,35 +635,66 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
         return PIT_OK;
     };
     IterGraph *g = graphs_apply(p) ? &p->igraph[prec == PIT_FP64 ? 0 : 1] : nullptr;
-    bool collect = false;
+    // the loop graph runs several iterations per launch: not where the host
+    // records member 0's residual after every iteration, nor with event timing
+    IterGraph *lg = (g && p->loop_chunk > 0 && !history && !p->timer.enabled)
+                        ? &p->lgraph[prec == PIT_FP64 ? 0 : 1]
+                        : nullptr;
+    bool collect = false, looped = false;
     // iteration guard: every member stops by max_iter, plus one restart per iteration
     const long guard = 2L * (max_iter + 2) + 4;
-    for (long it = 0; it < guard; ++it) {
-        PIT_TRY(hs.fetch(p, s));
+    long done = 0;                        // iterations run
+    for (;;) {
+        int ran = 0;
+        PIT_TRY(hs.fetch(p, s, looped ? p->loopctl.as<int>() : nullptr, &ran));
+        if (looped) {
+            looped = false;
+            if (ran <= 0 || ran > p->loop_chunk) {
+                // not the count the condition kernel keeps: stop using the loop graph
+                lg->failed = true;
+                set_error("the loop graph reported " + std::to_string(ran) + " iterations");
+                return PIT_E_CUDA;
+            }
+            g_launches += (unsigned long long)ran * lg->kernels;
+            out.graph_iterations += ran;
+            done += ran;
+        }
         if (collect) PIT_TRY(p->timer.collect(g->recs));
         collect = false;
         if (history && hc < history_len && hs.v[0].iter != last_iter) {
             history[hc++] = hs.v[0].rnorm;       // ||R^k||_{N,inf} of member 0
             last_iter = hs.v[0].iter;
         }
-        if (!hs.any_active()) break;
+        if (!hs.any_active() || done >= guard) break;
         PIT_TRY(check_cancel(p));
         // the first iteration runs eagerly (it allocates every buffer the
-        // iteration uses); later ones replay the captured graph
-        if (g && it > 0 && !g->failed) {
-            PIT_TRY(iter_graph_ready(p, *g, s, iteration));
-            if (g->exec) {
-                PIT_CUDA(cudaGraphLaunch(g->exec, s));
-                g_launches += g->kernels;
-                out.graph_iterations += 1;
-                collect = g->timed;
-                continue;
+        // iteration uses); later ones replay a captured graph: the loop graph
+        // where it applies, else one graph per iteration
+        if (g && done > 0) {
+            if (lg && !lg->failed) {
+                PIT_TRY(loop_graph_ready(p, *lg, s, iteration));
+                if (lg->exec) {
+                    PIT_CUDA(cudaMemsetAsync(p->loopctl.ptr, 0, sizeof(int), s));
+                    PIT_CUDA(cudaGraphLaunch(lg->exec, s));
+                    looped = true;
+                    continue;
+                }
+            }
+            if (!g->failed) {
+                PIT_TRY(iter_graph_ready(p, *g, s, iteration));
+                if (g->exec) {
+                    PIT_CUDA(cudaGraphLaunch(g->exec, s));
+                    g_launches += g->kernels;
+                    out.graph_iterations += 1;
+                    collect = g->timed;
+                    ++done;
+                    continue;
+                }
             }
         }
         PIT_TRY(iteration());
+        ++done;
     }
-    PIT_TRY(hs.fetch(p, s));
-    if (collect) PIT_TRY(p->timer.collect(g->recs));
     out.final_states = hs.v;
     out.history_count = hc - history_offset;
     return PIT_OK;
@@ -720,6 +841,9 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
     {
         const char *g = getenv("PIT_GRAPHS");
         p->use_graphs = !(g && g[0] == '0');
+        // PIT_GRAPH_LOOP=k: k iterations per launch of the loop graph (0: off)
+        const char *l = getenv("PIT_GRAPH_LOOP");
+        if (l && l[0]) p->loop_chunk = std::max(0, std::min(4096, atoi(l)));
     }
     pit_status s = PIT_OK;
     auto fail = [&](pit_status e) {
@@ -742,6 +866,7 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
     if ((s = p->fine_tmp.ensure(std::max<size_t>(4096, 64 * (size_t)d->batch))) != PIT_OK)
         return fail(s);
     if ((s = p->errword.ensure(sizeof(int))) != PIT_OK) return fail(s);
+    if ((s = p->loopctl.ensure(sizeof(int))) != PIT_OK) return fail(s);
     e = cudaMemsetAsync(p->errword.ptr, 0, sizeof(int), p->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "clear error word", __FILE__, __LINE__));
     switch (p->kind) {
@@ -793,8 +918,9 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32, &p->GLL32, &p->xtc_S,
-                      &p->errword, &p->PhiTh, &p->PhiTl, &p->tc_split};
+                      &p->errword, &p->loopctl, &p->PhiTh, &p->PhiTl, &p->tc_split};
     for (IterGraph &g : p->igraph) iter_graph_drop(p, g);
+    for (IterGraph &g : p->lgraph) iter_graph_drop(p, g);
     for (DevBuf *b : bufs) b->release();
     dense_teardown(p);
     p->timer.destroy();

@@ -199,6 +199,11 @@ struct Problem {
     ReduceLayout rl{};
     OpTimer timer;
     IterGraph igraph[2];          // [0]: FP64 iterations, [1]: mixed (FP32 fine) iterations
+    // the iteration loop as one graph (a conditional while node around the
+    // captured iteration): [0] FP64, [1] mixed
+    IterGraph lgraph[2];
+    DevBuf loopctl;               // iterations run by the current loop-graph launch (one int)
+    int loop_chunk = 16;          // iterations per loop-graph launch; 0: per-iteration graphs
     bool use_graphs = true;       // PIT_GRAPHS=0 in the environment turns graphs off
 };
 
