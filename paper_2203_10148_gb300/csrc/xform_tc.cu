@@ -20,13 +20,18 @@
 // 128 < n <= 256; n % 4 == 0; rows and columns beyond n read as zero or are
 // not stored).  Warp roles:
 //   warp 0      TMA: for n <= 128 Sh and Sl once (resident, 128 KB), then
-//               each tile's ceil(n/32) chunks of A (32 columns, and for
-//               n > 128 the matching chunks of Sh and Sl) into a 3-stage ring;
+//               each tile's chunks of A (32 columns) into a 4-stage ring of
+//               raw chunks; for n > 128 each chunk of A with the matching
+//               chunks of Sh and Sl into a 3-stage ring;
 //   warp 1      one thread issues tcgen05.mma (kind::tf32, M = N = 128,
 //               K = 8) into one of two TMEM accumulators (2 x 128 columns);
-//   warps 2..5  split each landed chunk in place into Ah and Al;
-//   warps 6..9  drain an accumulator with tcgen05.ld (one row per thread)
-//               and write the block transposed: for each k the 32 lanes of a
+//   warps 2..5  split each landed chunk into Ah and Al: with S resident
+//               into one split buffer, releasing the raw stage at once (so
+//               that up to four chunk loads are in flight while the tensor
+//               core works); with S streamed in place in the stage;
+//   warps 6..13 drain an accumulator with tcgen05.ld (one row per thread;
+//               two warps per 32-lane quarter of TMEM, 64 columns each) and
+//               write the block transposed: for each k the 32 lanes of a
 //               warp store 32 consecutive j (coalesced), scaled, FP32 or FP64.
 // Stage and accumulator hand-offs are mbarriers; every wait is bounded and
 // reports PIT_E_TIMEOUT through the problem's error word.
@@ -45,21 +50,26 @@ namespace {
 
 constexpr int XT_T = 128;                              // tile rows (TMEM lanes) = columns
 constexpr int XT_BK = 32;                              // K per chunk (128 bytes of FP32)
-constexpr int XT_STAGES = 3;
+constexpr int XT_STAGES = 3;                           // S streamed: stages of [Ah][Al][Sh][Sl]
+constexpr int XT_RAW = 4;                              // S resident: raw A chunks in flight
 constexpr int XT_CH = XT_T * XT_BK * 4;                // 16 KB: one chunk of one operand part
 constexpr int XT_S_BYTES = (XT_T / XT_BK) * XT_CH;     // 64 KB: one part of a resident S (n <= 128)
-constexpr int XT_THREADS = 320;
+constexpr int XT_EPI_WARPS = 8;                        // two per TMEM lane quarter
+constexpr int XT_THREADS = 32 * (6 + XT_EPI_WARPS);
 constexpr int XT_CONV_THREADS = 128;
 constexpr uint32_t kXtIdesc = tc_idesc_tf32(XT_T, XT_T);
 
-// Shared memory: S resident (n <= 128): [Sh 64 KB][Sl 64 KB] + 3 stages of
-// [Ah][Al]; S streamed (n > 128): 3 stages of [Ah][Al][Sh][Sl].
+// Shared memory: S resident (n <= 128): [Sh 64 KB][Sl 64 KB] + 4 raw A
+// chunks + one split buffer [Ah][Al]; S streamed (n > 128): 3 stages of
+// [Ah][Al][Sh][Sl].  Then 18 mbarriers and the TMEM address.
 template <bool SRES>
 struct XtLayout {
-    static constexpr int kStage = SRES ? 2 * XT_CH : 4 * XT_CH;
+    static constexpr int kStages = SRES ? XT_RAW : XT_STAGES;
+    static constexpr int kStage = SRES ? XT_CH : 4 * XT_CH;
     static constexpr int kRing = SRES ? 2 * XT_S_BYTES : 0;
-    static constexpr int kBar = kRing + XT_STAGES * kStage;
-    static constexpr int kSmem = 1024 + kBar + 128;
+    static constexpr int kSplit = kRing + kStages * kStage;   // S resident: the split buffer
+    static constexpr int kBar = kSplit + (SRES ? 2 * XT_CH : 0);
+    static constexpr int kSmem = 1024 + kBar + 256;
 };
 
 __device__ __forceinline__ bool xt_live(const MemberState *st, int b) {
@@ -68,10 +78,14 @@ __device__ __forceinline__ bool xt_live(const MemberState *st, int b) {
     return m.active && !m.skip && !m.half;
 }
 
+// x rounded to TF32 (10 mantissa bits), to nearest with ties away from
+// zero: half a TF32 ulp added to the magnitude bits, the 13 low bits
+// cleared (a carry moves into the next binade; overflow gives infinity).
+// Infinities and NaNs pass unchanged.  Integer-pipe work only.
 __device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    return __uint_as_float(h);
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t r = (b + 0x1000u) & 0xffffe000u;
+    return __uint_as_float((b & 0x7f800000u) == 0x7f800000u ? b : r);
 }
 
 // Output tiles t = (block, tj, tk), TN x TN of them per block (TN = 1 for
@@ -97,14 +111,21 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     unsigned char *Sres = base;                          // resident Sh, then Sl (SRES)
     unsigned char *ring = base + LY::kRing;
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + LY::kBar);
-    uint64_t *full = bars;                       // chunk landed (TMA)
-    uint64_t *conv = bars + XT_STAGES;           // chunk split (converters)
-    uint64_t *empty = bars + 2 * XT_STAGES;      // chunk consumed (tensor core)
-    uint64_t *tfull = bars + 3 * XT_STAGES;      // accumulator complete, 2 buffers
+    constexpr int NS = LY::kStages;
+    // S streamed: full (TMA landed), conv (split in place), empty (consumed
+    // by the tensor core) per stage.  S resident: full (raw chunk landed),
+    // empty (raw chunk read by the converters), and conv[0] / conv[1] the
+    // split buffer written / consumed by the tensor core.
+    uint64_t *full = bars;
+    uint64_t *conv = bars + 4;
+    uint64_t *empty = bars + 8;
+    uint64_t *tfull = bars + 12;                 // accumulator complete, 2 buffers
     uint64_t *tempty = tfull + 2;                // accumulator drained, 2 buffers
     uint64_t *sbar = tempty + 2;                 // resident S landed
     uint64_t *mdone = sbar + 1;                  // all products issued have finished
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
+    float4 *split_hi = reinterpret_cast<float4 *>(base + LY::kSplit);   // S resident
+    float4 *split_lo = reinterpret_cast<float4 *>(base + LY::kSplit + XT_CH);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // K chunks per tile: all four for a resident S (n <= 128, chunks past n
     // read as zero), ceil(n / 32) otherwise
@@ -112,14 +133,18 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     const int tpb = TN * TN;                     // tiles per block
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < XT_STAGES; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&conv[s], XT_CONV_THREADS);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], SRES ? XT_CONV_THREADS : 1);
+            if (!SRES) mbar_init(&conv[s], XT_CONV_THREADS);
+        }
+        if (SRES) {
+            mbar_init(&conv[0], XT_CONV_THREADS);
+            mbar_init(&conv[1], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], XT_EPI_WARPS);
         }
         mbar_init(sbar, 1);
         mbar_init(mdone, 1);
@@ -147,8 +172,8 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     tma_load_2d(Sres + XT_S_BYTES + c * XT_CH, &tmSl, c * XT_BK, 0, sbar);
                 }
             }
-            int last_use[XT_STAGES];
-            for (int s = 0; s < XT_STAGES; ++s) last_use[s] = -1;
+            int last_use[NS];
+            for (int s = 0; s < NS; ++s) last_use[s] = -1;
             int q = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
@@ -163,7 +188,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     srow = tk * XT_T;
                 }
                 for (int c = 0; c < KC; ++c, ++q) {
-                    const int s = q % XT_STAGES, u = q / XT_STAGES;
+                    const int s = q % NS, u = q / NS;
                     if (!tc_mbar_wait(&empty[s], (uint32_t)(u & 1) ^ 1u, err)) {
                         ok = false;
                         break;
@@ -180,7 +205,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             }
             // no copy of this CTA may still be writing shared memory at exit
             if constexpr (SRES) tc_mbar_drain(sbar, 0u);
-            for (int s = 0; s < XT_STAGES; ++s)
+            for (int s = 0; s < NS; ++s)
                 if (last_use[s] >= 0) tc_mbar_drain(&full[s], (uint32_t)(last_use[s] & 1));
         }
     } else if (warp == 1) {
@@ -198,14 +223,16 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(buf * XT_T);
                 for (int c = 0; c < KC; ++c, ++q) {
-                    const int s = q % XT_STAGES, u = q / XT_STAGES;
-                    if (!tc_mbar_wait(&conv[s], (uint32_t)(u & 1), err)) {
+                    const int s = q % NS, u = q / NS;
+                    // S resident: the q-th split of the one split buffer
+                    if (!tc_mbar_wait(SRES ? &conv[0] : &conv[s], (uint32_t)((SRES ? q : u) & 1), err)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     unsigned char *stg = ring + s * LY::kStage;
-                    const uint64_t ah = smem_desc(stg), al = smem_desc(stg + XT_CH);
+                    const uint64_t ah = SRES ? smem_desc(split_hi) : smem_desc(stg);
+                    const uint64_t al = SRES ? smem_desc(split_lo) : smem_desc(stg + XT_CH);
                     const uint64_t bh = SRES ? smem_desc(Sres + c * XT_CH) : smem_desc(stg + 2 * XT_CH);
                     const uint64_t bl = SRES ? smem_desc(Sres + XT_S_BYTES + c * XT_CH) : smem_desc(stg + 3 * XT_CH);
 #pragma unroll
@@ -222,7 +249,8 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                             tc_mma_tf32(d, al + adv, bh + adv, kXtIdesc, 1u);
                         }
                     }
-                    mma_commit(&empty[s]);    // chunk free once these products finish
+                    // chunk (S resident: the split buffer) free once these products finish
+                    mma_commit(SRES ? &conv[1] : &empty[s]);
                 }
                 if (!ok) break;
                 mma_commit(&tfull[buf]);      // accumulator complete
@@ -232,23 +260,30 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             tc_mbar_drain(mdone, 0u);
         }
     } else if (warp < 6) {
-        // ---- split: Ah = rna_tf32(a) in place, Al = rna_tf32(a - Ah)
+        // ---- split: Ah = rna_tf32(a), Al = rna_tf32(a - Ah), in place (S
+        // streamed) or into the split buffer (S resident)
         const int ct = threadIdx.x - 64;
         int q = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
             if (!ROW1D && !xt_live(st, (t / tpb) / nblk)) continue;
             for (int c = 0; c < KC; ++c, ++q) {
-                const int s = q % XT_STAGES, u = q / XT_STAGES;
+                const int s = q % NS, u = q / NS;
                 if (!tc_mbar_wait(&full[s], (uint32_t)(u & 1), err)) {
                     ok = false;
                     break;
                 }
-                float4 *hi = reinterpret_cast<float4 *>(ring + s * LY::kStage);
-                float4 *lo = reinterpret_cast<float4 *>(ring + s * LY::kStage + XT_CH);
+                // S resident: the split buffer's previous products have finished
+                if (SRES && !tc_mbar_wait(&conv[1], (uint32_t)(q & 1) ^ 1u, err)) {
+                    ok = false;
+                    break;
+                }
+                const float4 *src = reinterpret_cast<const float4 *>(ring + s * LY::kStage);
+                float4 *hi = SRES ? split_hi : reinterpret_cast<float4 *>(ring + s * LY::kStage);
+                float4 *lo = SRES ? split_lo : reinterpret_cast<float4 *>(ring + s * LY::kStage + XT_CH);
 #pragma unroll 4
                 for (int i = ct; i < XT_CH / 16; i += XT_CONV_THREADS) {
-                    const float4 a = hi[i];
+                    const float4 a = src[i];
                     float4 h, l;
                     h.x = tf32_rna(a.x);
                     h.y = tf32_rna(a.y);
@@ -261,14 +296,17 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                     hi[i] = h;
                     lo[i] = l;
                 }
+                if (SRES) mbar_arrive(&empty[s]);   // raw chunk read: the TMA may refill it
                 // generic-proxy writes become visible to the tensor core
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&conv[s]);
+                mbar_arrive(SRES ? &conv[0] : &conv[s]);
             }
         }
     } else {
-        // ---- epilogue: TMEM lanes 32 (warp % 4) .. +31 are the tile rows
-        const int quad = warp & 3;
+        // ---- epilogue: TMEM lanes 32 (warp % 4) .. +31 are the tile rows;
+        // this warp drains columns 64 half .. 64 half + 63
+        const int quad = warp & 3, half = (warp - 6) >> 2;
+        constexpr int CPW = XT_T / 32 / (XT_EPI_WARPS / 4);   // 32-column groups per warp
         const size_t nn = (size_t)n * n;
         int L = 0;
         for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -283,7 +321,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                 const int k = (t / TN) * XT_T + quad * 32 + lane;
                 const int rbase = (t % TN) * XT_T;
 #pragma unroll 1
-                for (int cc = 0; cc < XT_T / 32; ++cc) {
+                for (int cc = half * CPW; cc < (half + 1) * CPW; ++cc) {
                     float vals[32];
                     tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * XT_T + cc * 32), vals);
                     if (k < nout) {
@@ -307,7 +345,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             }
             const int j = tj * XT_T + quad * 32 + lane;
 #pragma unroll 1
-            for (int cc = 0; cc < XT_T / 32; ++cc) {
+            for (int cc = half * CPW; cc < (half + 1) * CPW; ++cc) {
                 float vals[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * XT_T + cc * 32), vals);
                 const int k0 = tk * XT_T + cc * 32;
