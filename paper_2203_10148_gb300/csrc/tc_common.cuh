@@ -99,6 +99,16 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t tmem, uint64_t a, uint64_t 
         "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 
+// D (+)= A B^T with A (M = 128 rows in the 128 lanes, K = 8 TF32 columns)
+// read from tensor memory at column address `a_tmem` and B from shared memory.
+__device__ __forceinline__ void tc_mma_tf32_ts(uint32_t tmem, uint32_t a_tmem, uint64_t b,
+                                               uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accum));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
@@ -120,6 +130,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive 32-bit columns into this thread's TMEM lane (warp-collective;
+// the warp's lanes are its 32-lane quarter of tensor memory)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
 }
 
 inline PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {

@@ -20,16 +20,20 @@
 // 128 < n <= 256; n % 4 == 0; rows and columns beyond n read as zero or are
 // not stored).  Warp roles:
 //   warp 0      TMA: for n <= 128 Sh and Sl once (resident, 128 KB), then
-//               each tile's chunks of A (32 columns) into a 4-stage ring of
+//               each tile's chunks of A (32 columns) into a 6-stage ring of
 //               raw chunks; for n > 128 each chunk of A with the matching
 //               chunks of Sh and Sl into a 3-stage ring;
 //   warp 1      one thread issues tcgen05.mma (kind::tf32, M = N = 128,
 //               K = 8) into one of two TMEM accumulators (2 x 128 columns);
-//   warps 2..5  split each landed chunk into Ah and Al: with S resident
-//               into one split buffer, releasing the raw stage at once (so
-//               that up to four chunk loads are in flight while the tensor
-//               core works); with S streamed in place in the stage;
-//   warps 6..13 drain an accumulator with tcgen05.ld (one row per thread;
+//   warps 2..9  split each landed chunk into Ah and Al.  S resident: each
+//               thread reads its row of the chunk (the 128-byte swizzle
+//               undone in the address) and writes its parts into one of two
+//               A buffers in tensor memory (tcgen05.st, 2 x 64 columns), the
+//               raw stage freed at once; the products read A from tensor
+//               memory, so splitting the next chunk overlaps them and the
+//               shared-memory port carries only the TMA writes, the split's
+//               reads and the B operand.  S streamed: in place in the stage;
+//   warps 10..17 drain an accumulator with tcgen05.ld (one row per thread;
 //               two warps per 32-lane quarter of TMEM, 64 columns each) and
 //               write the block transposed: for each k the 32 lanes of a
 //               warp store 32 consecutive j (coalesced), scaled, FP32 or FP64.
@@ -51,25 +55,29 @@ namespace {
 constexpr int XT_T = 128;                              // tile rows (TMEM lanes) = columns
 constexpr int XT_BK = 32;                              // K per chunk (128 bytes of FP32)
 constexpr int XT_STAGES = 3;                           // S streamed: stages of [Ah][Al][Sh][Sl]
-constexpr int XT_RAW = 4;                              // S resident: raw A chunks in flight
+constexpr int XT_RAW = 6;                              // S resident: raw A chunks in flight
+constexpr int XT_ABUF = 2 * XT_T;                      // S resident: first TMEM column of the A buffers
 constexpr int XT_CH = XT_T * XT_BK * 4;                // 16 KB: one chunk of one operand part
 constexpr int XT_S_BYTES = (XT_T / XT_BK) * XT_CH;     // 64 KB: one part of a resident S (n <= 128)
+constexpr int XT_CONV_WARPS = 8;                       // split a 16 KB chunk: 4 float4 per thread
 constexpr int XT_EPI_WARPS = 8;                        // two per TMEM lane quarter
-constexpr int XT_THREADS = 32 * (6 + XT_EPI_WARPS);
-constexpr int XT_CONV_THREADS = 128;
+constexpr int XT_THREADS = 32 * (2 + XT_CONV_WARPS + XT_EPI_WARPS);
+constexpr int XT_CONV_THREADS = 32 * XT_CONV_WARPS;
+constexpr int XT_EPI0 = 2 + XT_CONV_WARPS;             // first epilogue warp
 constexpr uint32_t kXtIdesc = tc_idesc_tf32(XT_T, XT_T);
 
-// Shared memory: S resident (n <= 128): [Sh 64 KB][Sl 64 KB] + 4 raw A
-// chunks + one split buffer [Ah][Al]; S streamed (n > 128): 3 stages of
-// [Ah][Al][Sh][Sl].  Then 18 mbarriers and the TMEM address.
+// Shared memory: S resident (n <= 128): [Sh 64 KB][Sl 64 KB] + 6 raw A
+// chunks; S streamed (n > 128): 3 stages of [Ah][Al][Sh][Sl].  Then 26
+// mbarriers and the TMEM address.  Tensor memory: two accumulators (256
+// columns) and, S resident, two A buffers [Ah 32 columns][Al 32 columns].
 template <bool SRES>
 struct XtLayout {
     static constexpr int kStages = SRES ? XT_RAW : XT_STAGES;
     static constexpr int kStage = SRES ? XT_CH : 4 * XT_CH;
     static constexpr int kRing = SRES ? 2 * XT_S_BYTES : 0;
-    static constexpr int kSplit = kRing + kStages * kStage;   // S resident: the split buffer
-    static constexpr int kBar = kSplit + (SRES ? 2 * XT_CH : 0);
+    static constexpr int kBar = kRing + kStages * kStage;
     static constexpr int kSmem = 1024 + kBar + 256;
+    static constexpr uint32_t kTmemCols = SRES ? 4 * XT_T : 2 * XT_T;
 };
 
 __device__ __forceinline__ bool xt_live(const MemberState *st, int b) {
@@ -113,19 +121,18 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + LY::kBar);
     constexpr int NS = LY::kStages;
     // S streamed: full (TMA landed), conv (split in place), empty (consumed
-    // by the tensor core) per stage.  S resident: full (raw chunk landed),
-    // empty (raw chunk read by the converters), and conv[0] / conv[1] the
-    // split buffer written / consumed by the tensor core.
+    // by the tensor core) per stage.  S resident: full (raw chunk landed)
+    // and empty (raw chunk read by the converters) per stage, conv[a] (A
+    // buffer a written) and conv[2 + a] (A buffer a consumed by the
+    // tensor core) for the two TMEM A buffers.
     uint64_t *full = bars;
-    uint64_t *conv = bars + 4;
     uint64_t *empty = bars + 8;
-    uint64_t *tfull = bars + 12;                 // accumulator complete, 2 buffers
+    uint64_t *conv = bars + 16;
+    uint64_t *tfull = bars + 20;                 // accumulator complete, 2 buffers
     uint64_t *tempty = tfull + 2;                // accumulator drained, 2 buffers
     uint64_t *sbar = tempty + 2;                 // resident S landed
     uint64_t *mdone = sbar + 1;                  // all products issued have finished
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
-    float4 *split_hi = reinterpret_cast<float4 *>(base + LY::kSplit);   // S resident
-    float4 *split_lo = reinterpret_cast<float4 *>(base + LY::kSplit + XT_CH);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // K chunks per tile: all four for a resident S (n <= 128, chunks past n
     // read as zero), ceil(n / 32) otherwise
@@ -139,8 +146,10 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             if (!SRES) mbar_init(&conv[s], XT_CONV_THREADS);
         }
         if (SRES) {
-            mbar_init(&conv[0], XT_CONV_THREADS);
-            mbar_init(&conv[1], 1);
+            for (int a = 0; a < 2; ++a) {
+                mbar_init(&conv[a], XT_CONV_THREADS);
+                mbar_init(&conv[2 + a], 1);
+            }
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(2 * XT_T));
+                     "r"(LY::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -224,17 +233,36 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                 const uint32_t d = tmem + (uint32_t)(buf * XT_T);
                 for (int c = 0; c < KC; ++c, ++q) {
                     const int s = q % NS, u = q / NS;
-                    // S resident: the q-th split of the one split buffer
-                    if (!tc_mbar_wait(SRES ? &conv[0] : &conv[s], (uint32_t)((SRES ? q : u) & 1), err)) {
+                    if constexpr (SRES) {
+                        // A parts of chunk q in TMEM buffer q & 1
+                        const int a = q & 1, ua = q >> 1;
+                        if (!tc_mbar_wait(&conv[a], (uint32_t)(ua & 1), err)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t ahi = tmem + (uint32_t)(XT_ABUF + a * 2 * XT_BK);
+                        const uint64_t bh = smem_desc(Sres + c * XT_CH);
+                        const uint64_t bl = smem_desc(Sres + XT_S_BYTES + c * XT_CH);
+#pragma unroll
+                        for (int j = 0; j < XT_BK / 8; ++j) {
+                            const uint64_t adv = (uint64_t)(j * 32) >> 4;   // 8 TF32 = 32 bytes along K
+                            const uint32_t acol = (uint32_t)(j * 8);        // 8 TF32 = 8 TMEM columns
+                            tc_mma_tf32_ts(d, ahi + acol, bh + adv, kXtIdesc, (c > 0 || j > 0) ? 1u : 0u);
+                            tc_mma_tf32_ts(d, ahi + acol, bl + adv, kXtIdesc, 1u);
+                            tc_mma_tf32_ts(d, ahi + XT_BK + acol, bh + adv, kXtIdesc, 1u);
+                        }
+                        mma_commit(&conv[2 + a]);    // A buffer free once these products finish
+                        continue;
+                    }
+                    if (!tc_mbar_wait(&conv[s], (uint32_t)(u & 1), err)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     unsigned char *stg = ring + s * LY::kStage;
-                    const uint64_t ah = SRES ? smem_desc(split_hi) : smem_desc(stg);
-                    const uint64_t al = SRES ? smem_desc(split_lo) : smem_desc(stg + XT_CH);
-                    const uint64_t bh = SRES ? smem_desc(Sres + c * XT_CH) : smem_desc(stg + 2 * XT_CH);
-                    const uint64_t bl = SRES ? smem_desc(Sres + XT_S_BYTES + c * XT_CH) : smem_desc(stg + 3 * XT_CH);
+                    const uint64_t ah = smem_desc(stg), al = smem_desc(stg + XT_CH);
+                    const uint64_t bh = smem_desc(stg + 2 * XT_CH), bl = smem_desc(stg + 3 * XT_CH);
 #pragma unroll
                     for (int j = 0; j < XT_BK / 8; ++j) {
                         const uint64_t adv = (uint64_t)(j * 32) >> 4;   // 8 TF32 = 32 bytes along K
@@ -249,8 +277,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
                             tc_mma_tf32(d, al + adv, bh + adv, kXtIdesc, 1u);
                         }
                     }
-                    // chunk (S resident: the split buffer) free once these products finish
-                    mma_commit(SRES ? &conv[1] : &empty[s]);
+                    mma_commit(&empty[s]);    // stage free once these products finish
                 }
                 if (!ok) break;
                 mma_commit(&tfull[buf]);      // accumulator complete
@@ -259,53 +286,90 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
             mma_commit(mdone);
             tc_mbar_drain(mdone, 0u);
         }
-    } else if (warp < 6) {
-        // ---- split: Ah = rna_tf32(a), Al = rna_tf32(a - Ah), in place (S
-        // streamed) or into the split buffer (S resident)
-        const int ct = threadIdx.x - 64;
-        int q = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
-            if (!ROW1D && !xt_live(st, (t / tpb) / nblk)) continue;
-            for (int c = 0; c < KC; ++c, ++q) {
-                const int s = q % NS, u = q / NS;
-                if (!tc_mbar_wait(&full[s], (uint32_t)(u & 1), err)) {
-                    ok = false;
-                    break;
+    } else if (warp < XT_EPI0) {
+        // ---- split: Ah = rna_tf32(a), Al = rna_tf32(a - Ah)
+        if constexpr (SRES) {
+            // into TMEM: warp quarter (warp % 4) owns rows 32 quarter .. +31
+            // (its TMEM lanes); two warps per quarter, 16 columns each
+            const int quarter = warp & 3, half = (warp - 2) >> 2;
+            const int r = quarter * 32 + lane;
+            const uint32_t tl = (uint32_t)(quarter * 32) << 16;
+            int q = 0;
+            for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+                if (!xt_live(st, (t / tpb) / nblk)) continue;
+                bool ok = true;
+                for (int c = 0; c < KC; ++c, ++q) {
+                    const int s = q % NS, u = q / NS, a = q & 1, ua = q >> 1;
+                    // chunk landed, and the products that read A buffer a
+                    // (chunk q - 2) have finished
+                    ok = __all_sync(0xffffffffu, tc_mbar_wait(&full[s], (uint32_t)(u & 1), err) &&
+                                                     tc_mbar_wait(&conv[2 + a], (uint32_t)(ua & 1) ^ 1u, err)) != 0;
+                    if (!ok) break;
+                    // row r of the chunk: 16-byte granule g sits at g ^ (r % 8)
+                    const unsigned char *row = ring + s * LY::kStage + r * (XT_BK * 4);
+                    uint32_t h[16], l[16];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        const float4 x = *reinterpret_cast<const float4 *>(
+                            row + (((half * 4 + g) ^ (r & 7)) << 4));
+                        const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float hv = tf32_rna(xs[e]);
+                            h[4 * g + e] = __float_as_uint(hv);
+                            l[4 * g + e] = __float_as_uint(tf32_rna(xs[e] - hv));
+                        }
+                    }
+                    mbar_arrive(&empty[s]);   // raw chunk read: the TMA may refill it
+                    const uint32_t col = tmem + tl + (uint32_t)(XT_ABUF + a * 2 * XT_BK + half * 16);
+                    tmem_st16(col, h);
+                    tmem_st16(col + XT_BK, l);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&conv[a]);
                 }
-                // S resident: the split buffer's previous products have finished
-                if (SRES && !tc_mbar_wait(&conv[1], (uint32_t)(q & 1) ^ 1u, err)) {
-                    ok = false;
-                    break;
+                if (!ok) break;
+            }
+        } else {
+            // in place in the stage (S streamed)
+            const int ct = threadIdx.x - 64;
+            int q = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total_tiles && ok; t += gridDim.x) {
+                if (!ROW1D && !xt_live(st, (t / tpb) / nblk)) continue;
+                for (int c = 0; c < KC; ++c, ++q) {
+                    const int s = q % NS, u = q / NS;
+                    if (!tc_mbar_wait(&full[s], (uint32_t)(u & 1), err)) {
+                        ok = false;
+                        break;
+                    }
+                    float4 *hi = reinterpret_cast<float4 *>(ring + s * LY::kStage);
+                    float4 *lo = reinterpret_cast<float4 *>(ring + s * LY::kStage + XT_CH);
+#pragma unroll
+                    for (int i = ct; i < XT_CH / 16; i += XT_CONV_THREADS) {
+                        const float4 a = hi[i];
+                        float4 h, l;
+                        h.x = tf32_rna(a.x);
+                        h.y = tf32_rna(a.y);
+                        h.z = tf32_rna(a.z);
+                        h.w = tf32_rna(a.w);
+                        l.x = tf32_rna(a.x - h.x);
+                        l.y = tf32_rna(a.y - h.y);
+                        l.z = tf32_rna(a.z - h.z);
+                        l.w = tf32_rna(a.w - h.w);
+                        hi[i] = h;
+                        lo[i] = l;
+                    }
+                    // generic-proxy writes become visible to the tensor core
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(&conv[s]);
                 }
-                const float4 *src = reinterpret_cast<const float4 *>(ring + s * LY::kStage);
-                float4 *hi = SRES ? split_hi : reinterpret_cast<float4 *>(ring + s * LY::kStage);
-                float4 *lo = SRES ? split_lo : reinterpret_cast<float4 *>(ring + s * LY::kStage + XT_CH);
-#pragma unroll 4
-                for (int i = ct; i < XT_CH / 16; i += XT_CONV_THREADS) {
-                    const float4 a = src[i];
-                    float4 h, l;
-                    h.x = tf32_rna(a.x);
-                    h.y = tf32_rna(a.y);
-                    h.z = tf32_rna(a.z);
-                    h.w = tf32_rna(a.w);
-                    l.x = tf32_rna(a.x - h.x);
-                    l.y = tf32_rna(a.y - h.y);
-                    l.z = tf32_rna(a.z - h.z);
-                    l.w = tf32_rna(a.w - h.w);
-                    hi[i] = h;
-                    lo[i] = l;
-                }
-                if (SRES) mbar_arrive(&empty[s]);   // raw chunk read: the TMA may refill it
-                // generic-proxy writes become visible to the tensor core
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(SRES ? &conv[0] : &conv[s]);
             }
         }
     } else {
         // ---- epilogue: TMEM lanes 32 (warp % 4) .. +31 are the tile rows;
         // this warp drains columns 64 half .. 64 half + 63
-        const int quad = warp & 3, half = (warp - 6) >> 2;
+        const int quad = warp & 3, half = (warp - XT_EPI0) >> 2;
         constexpr int CPW = XT_T / 32 / (XT_EPI_WARPS / 4);   // 32-column groups per warp
         const size_t nn = (size_t)n * n;
         int L = 0;
@@ -373,7 +437,7 @@ __global__ void __launch_bounds__(XT_THREADS, 1)
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * XT_T));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LY::kTmemCols));
     }
 }
 
