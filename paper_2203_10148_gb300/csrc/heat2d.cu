@@ -752,6 +752,70 @@ __global__ void k_rec_apply(T *__restrict__ hat, const double *__restrict__ ends
 }
 
 
+// The whole recurrence of a mode in one pass, for batches with enough
+// members x modes to fill the GPU: each thread steps zhat_n = qhat_n + g
+// zhat_{n-1} through all N+1 blocks in place, loading the next 16 blocks'
+// values while it steps through the current 16 (one read and one write of
+// the array, against two reads and a write for the chunked scan).
+template <class T>
+__global__ void __launch_bounds__(256) k_rec_full(T *__restrict__ hat, const double *__restrict__ g,
+                                                  int nn, int nblk, const MemberState *st) {
+    using R = RecVal<T>;
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    const int member = blockIdx.y;
+    if (mode >= nn || !runs(st, member)) return;
+    const double gm = g[mode];
+    const auto gv = R::from_d(gm);
+    T *h = hat + (size_t)member * nblk * nn + mode;
+    T cur[REC_CHUNK], nxt[REC_CHUNK];
+#pragma unroll
+    for (int t = 0; t < REC_CHUNK; ++t) cur[t] = t < nblk ? h[(size_t)t * nn] : T(0);
+    auto z = R::zero();
+    for (int k0 = 0; k0 < nblk; k0 += REC_CHUNK) {
+        const int k1 = k0 + REC_CHUNK;
+#pragma unroll
+        for (int t = 0; t < REC_CHUNK; ++t) nxt[t] = k1 + t < nblk ? h[(size_t)(k1 + t) * nn] : T(0);
+#pragma unroll
+        for (int t = 0; t < REC_CHUNK; ++t) {
+            if (k0 + t < nblk) {
+                if constexpr (std::is_same<T, float>::value) z = R::step(gv.hi, gv.lo, z, cur[t]);
+                else z = R::step(gm, 0.0, z, cur[t]);
+                h[(size_t)(k0 + t) * nn] = R::out(z);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < REC_CHUNK; ++t) cur[t] = nxt[t];
+    }
+}
+
+// zhat_n = qhat_n + g zhat_{n-1} over the N+1 blocks of every member, mode by
+// mode, in place on hat ([batch][N+1][nn]): one pass per mode when batch x
+// nn threads fill the GPU (at least 2^16), else the chunked scan (local
+// recurrences, carries across chunks, replay) with ends holding
+// batch * ceil((N+1)/16) * nn doubles.
+template <class T>
+pit_status mode_recurrence(Problem *p, T *hat, double *ends, int nn, const MemberState *st,
+                           cudaStream_t s) {
+    const int nblk = p->N + 1;
+    const int RT = 256;
+    if ((size_t)p->batch * nn >= (1u << 16)) {
+        k_rec_full<T><<<dim3((unsigned)((nn + RT - 1) / RT), p->batch), RT, 0, s>>>(
+            hat, p->gmode.as<double>(), nn, nblk, st);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
+    const int nchunks = (nblk + REC_CHUNK - 1) / REC_CHUNK;
+    dim3 g1((unsigned)((nn + RT - 1) / RT), nchunks, p->batch);
+    k_rec_local<T><<<g1, RT, 0, s>>>(hat, ends, p->gmode.as<double>(), nn, nblk, nchunks, st);
+    PIT_LAUNCH_CHECK();
+    k_rec_carry<<<dim3((unsigned)((nn + RT - 1) / RT), p->batch), RT, 0, s>>>(
+        ends, p->gmode.as<double>(), nn, nchunks, st);
+    PIT_LAUNCH_CHECK();
+    k_rec_apply<T><<<g1, RT, 0, s>>>(hat, ends, p->gmode.as<double>(), nn, nblk, nchunks, st);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
 template <class V, int RX, int RY>
 size_t fine_smem(int TXp, int TYp) {
     size_t s = 32 + 4 * (size_t)TYp * TXp * RX * sizeof(V);
@@ -963,15 +1027,7 @@ pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const Member
         PIT_TRY((launch_xS<T, T, T>(p, h1, h2, S, 1.0, st, s)));
     }
     // recurrence over slices, mode by mode
-    const int RT = 256;
-    dim3 g1((unsigned)((nn + RT - 1) / RT), nchunks, p->batch);
-    k_rec_local<T><<<g1, RT, 0, s>>>(h2, ends, p->gmode.as<double>(), (int)nn, nblk, nchunks, st);
-    PIT_LAUNCH_CHECK();
-    k_rec_carry<<<dim3((unsigned)((nn + RT - 1) / RT), p->batch), RT, 0, s>>>(
-        ends, p->gmode.as<double>(), (int)nn, nchunks, st);
-    PIT_LAUNCH_CHECK();
-    k_rec_apply<T><<<g1, RT, 0, s>>>(h2, ends, p->gmode.as<double>(), (int)nn, nblk, nchunks, st);
-    PIT_LAUNCH_CHECK();
+    PIT_TRY(mode_recurrence<T>(p, h2, ends, (int)nn, st, s));
     // z = (2/(n+1))^2 S zhat S
     if (tc) {
         float *f1 = reinterpret_cast<float *>(h1), *f2 = reinterpret_cast<float *>(h2);
@@ -988,22 +1044,11 @@ pit_status sweep_t(Problem *p, const Tin *q, double *z, const T *S, const Member
 
 // The per-mode recurrence z_n[k] = q_n[k] + g_k z_{n-1}[k] over the N+1
 // blocks of every member, in place on hat ([batch][N+1][nn] FP32, g_k in
-// p->gmode), as the chunked scan of the 2D sweep; ends holds
-// batch * ceil((N+1)/16) * nn doubles.
+// p->gmode), as in the 2D sweep (one pass per mode, or the chunked scan for
+// few members x modes); ends holds batch * ceil((N+1)/16) * nn doubles.
 pit_status sine_mode_recurrence(Problem *p, float *hat, double *ends, int nn, const MemberState *st,
                                 cudaStream_t s) {
-    const int nblk = p->N + 1;
-    const int nchunks = (nblk + REC_CHUNK - 1) / REC_CHUNK;
-    const int RT = 256;
-    dim3 g1((unsigned)((nn + RT - 1) / RT), nchunks, p->batch);
-    k_rec_local<float><<<g1, RT, 0, s>>>(hat, ends, p->gmode.as<double>(), nn, nblk, nchunks, st);
-    PIT_LAUNCH_CHECK();
-    k_rec_carry<<<dim3((unsigned)((nn + RT - 1) / RT), p->batch), RT, 0, s>>>(
-        ends, p->gmode.as<double>(), nn, nchunks, st);
-    PIT_LAUNCH_CHECK();
-    k_rec_apply<float><<<g1, RT, 0, s>>>(hat, ends, p->gmode.as<double>(), nn, nblk, nchunks, st);
-    PIT_LAUNCH_CHECK();
-    return PIT_OK;
+    return mode_recurrence<float>(p, hat, ends, nn, st, s);
 }
 
 pit_status heat2d_setup(Problem *p) {
