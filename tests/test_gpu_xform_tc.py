@@ -9,6 +9,11 @@ fine kernel), single and several tiles per CTA (N + 1 above the SM count:
 both accumulators and every stage parity reused), batches, and solves that
 mask converged members.  Tolerances: 2e-5 against the oracle, as for every
 FP32 sweep; 1e-5 between the two FP32-class transforms.
+
+The per-mode recurrence between the transforms runs in one pass per mode
+when members x modes reach 2^16 (n = 256 here, n = 192 with two members,
+the 128^2 bench batch) and as the chunked scan below that (the other
+cases); both against the oracle.
 """
 import numpy as np
 import pytest
