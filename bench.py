@@ -73,8 +73,8 @@ ADV_KERNEL_NAMES = {"fine_fp32": "k_advdiff_fine<float>", "fine_ff": "k_advdiff_
                     "fine_fp64": "k_advdiff_fine<double>"}
 
 
-def parse():
-    args = _parser().parse_args()
+def parse(argv=None):
+    args = _parser().parse_args(argv)
     if args.batch is None:
         args.batch = 8 if args.workload == "heat2d" else 1
     args.N_given = args.N is not None
