@@ -70,13 +70,14 @@ typedef int pit_status;
 /* Arithmetic of the fine propagator. */
 #define PIT_FP64            0   /* FP64 throughout */
 #define PIT_MIXED           1   /* FP32 fine stepping (split-precision tensor-core GEMM for
-                                   PIT_OP_DENSE), FP64 Krylov vectors and scalars, true
-                                   residuals in PIT_FF (HEAT2D) or FP64 with iterative
-                                   refinement */
-#define PIT_FF              2   /* float-float fine stepping: each value an unevaluated sum
+                                   PIT_OP_DENSE), FP64 Krylov vectors and scalars, and
+                                   iterative refinement on true residuals computed in
+                                   PIT_FF by default (PIT_FP64 on request; HEAT1D: FP64) */
+#define PIT_FF              2   /* float-float fine arithmetic: each value an unevaluated sum
                                    of two FP32 numbers (about 48 significant bits) on the
-                                   FP32 pipe, FP64 inputs and outputs; HEAT2D only, other
-                                   operators treat it as PIT_FP64 */
+                                   FP32 pipe, FP64 inputs and outputs: stepping for HEAT2D
+                                   and ADVDIFF2D, a compensated product for DENSE; HEAT1D
+                                   treats it as PIT_FP64 */
 
 /* pit_apply_operator: which operator. */
 #define PIT_APPLY_F         1   /* y = F x, the block operator of eq. (4) */
@@ -190,7 +191,9 @@ size_t pit_last_error(char *buf, size_t n);
  *                          autotuner's choice (bit-identical results);
  *   PIT_AUTOTUNE=0         untuned shapes take the built-in variant;
  *   PIT_AUTOTUNE_CACHE=f   persist the autotuner's choices in file f.
- * Errors: PIT_E_INVALID (bad sizes, non-finite values), PIT_E_NOMEM, PIT_E_CUDA.
+ * Errors: PIT_E_INVALID (bad sizes, including N + 1 > 65535 or batch > 65535:
+ * the vector kernels put one grid row per block and one grid layer per
+ * member), PIT_E_NONFINITE (non-finite values), PIT_E_NOMEM, PIT_E_CUDA.
  */
 pit_status pit_problem_create(const pit_problem_desc *desc, pit_problem_t *out);
 
@@ -230,9 +233,12 @@ pit_status pit_serial_fine(pit_problem_t prob, int precision, double *Lam, int o
  * X (batch*(N+1)*M): initial guess on entry when x0_mode = PIT_X0_GIVEN,
  * the solution on return.  info: array of batch entries (may be NULL).
  * PIT_FP64: every step in FP64 on the device.  PIT_MIXED: iterative
- * refinement: FP64 true residual G^{-1}(B - F64 X), an FP32-fine / FP64-Krylov
- * inner solve of the correction to inner_tol, X += correction, until the
- * true preconditioned residual is <= tol * its initial value.
+ * refinement: the true residual G^{-1}(B - F X) with the fine propagations
+ * in opts.residual_precision (PIT_FF, float-float on the FP32 pipe, by
+ * default; PIT_FP64 on request; HEAT1D always FP64), an FP32-fine /
+ * FP64-Krylov inner solve of the correction to inner_tol, X += correction,
+ * until the true preconditioned residual is <= tol * its reference
+ * (opts.tol_mode).
  * For PIT_OP_HEAT1D and PIT_OP_HEAT2D one iteration (two applications of
  * G^{-1}F and the fused vector kernels) is captured as a CUDA graph after
  * the first, eager, iteration of each inner solve and replayed for the
@@ -272,7 +278,8 @@ pit_status pit_parareal_solve(pit_problem_t prob, int kmax, double tol, double *
  * *dot = sum of U.V over all entries (the block inner product, Sec. 3 text
  * after Algorithm 1), norms[n] = ||U_n||_2, *norm_inf = max_n norms[n]
  * (the ||.||_{N,inf} of Algorithm 1).  Device pointers; synchronous.
- * norms may be NULL.
+ * norms may be NULL.  1 <= nblocks <= 65535 (one grid row per block) and
+ * M >= 1, else PIT_E_INVALID before any device call.
  */
 pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M,
                             double *dot, double *norms, double *norm_inf);
@@ -286,8 +293,8 @@ pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M
  * cannot pay for cudaMalloc/cudaFree.  The partial sums live in a fixed
  * 1 MiB array compiled into the library, which every device that loads the
  * library keeps until the process exits; it holds nblocks * ceil(M/2048)
- * <= 65536 chunks, and larger sizes return PIT_E_INVALID without touching
- * the device.  The first call on a device looks up the array's device
+ * <= 65536 chunks, and larger sizes (or nblocks > 65535, as for
+ * pit_block_reduce) return PIT_E_INVALID without touching the device.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  All calls share the array: calls that
  * overlap on the GPU (from several threads or streams) race and must be

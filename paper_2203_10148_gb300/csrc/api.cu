@@ -793,6 +793,11 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
         set_error("pit_problem_create: invalid sizes, steps, T, precision or null y0");
         return PIT_E_INVALID;
     }
+    if (d->N + 1 > PIT_MAX_BLOCKS || d->batch > PIT_MAX_BLOCKS) {
+        set_error("pit_problem_create: N + 1 and batch must be <= 65535 (grid rows of the "
+                  "vector kernels)");
+        return PIT_E_INVALID;
+    }
     if ((op.kind == PIT_OP_HEAT1D || op.kind == PIT_OP_DENSE) && op.ny != 1) {
         set_error("pit_problem_create: HEAT1D and DENSE need ny = 1");
         return PIT_E_INVALID;
@@ -1296,6 +1301,10 @@ pit_status pit_block_reduce(const double *U, const double *V, int nblocks, int M
                             double *norms, double *norm_inf) {
     if (!U || !V || !dot || !norm_inf || nblocks < 1 || M < 1) {
         set_error("pit_block_reduce: bad argument");
+        return PIT_E_INVALID;
+    }
+    if (nblocks > PIT_MAX_BLOCKS) {
+        set_error("pit_block_reduce: nblocks exceeds 65535 (one grid row per block)");
         return PIT_E_INVALID;
     }
     PIT_TRY(block_reduce(U, V, nblocks, M, dot, norms, norm_inf, 0));

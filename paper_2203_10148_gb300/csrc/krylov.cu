@@ -640,6 +640,10 @@ extern "C" pit_status pit_block_reduce_noalloc(const double *U, const double *V,
         set_error("pit_block_reduce_noalloc: bad argument");
         return PIT_E_INVALID;
     }
+    if (nblocks > PIT_MAX_BLOCKS) {
+        set_error("pit_block_reduce_noalloc: nblocks exceeds 65535 (one grid row per block)");
+        return PIT_E_INVALID;
+    }
     VecGeom g;
     g.M = M;
     g.nblk = nblocks;

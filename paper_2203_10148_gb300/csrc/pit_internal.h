@@ -13,6 +13,11 @@
 
 namespace pit {
 
+// The vector kernels put one grid row (gridDim.y) per block of a block
+// vector and one grid layer (gridDim.z) per batch member; both are limited
+// to 65535.
+constexpr int PIT_MAX_BLOCKS = 65535;
+
 // ---------------------------------------------------------------- errors
 void set_error(const std::string &msg);
 pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);

@@ -56,7 +56,7 @@ def _desc(pit, y0, **kw):
 
 @pytest.mark.parametrize("bad", [dict(N=0), dict(T=0.0), dict(T=-1.0), dict(fine_steps=0),
                                  dict(kind=9), dict(batch=0), dict(precision=7), dict(ny=3),
-                                 dict(nu=-1.0)])
+                                 dict(nu=-1.0), dict(N=65535), dict(batch=65536)])
 def test_create_rejects_invalid_descriptors(lib, bad):
     from paper_2203_10148_gb300 import pit
     y0 = np.ones(8)
@@ -117,3 +117,15 @@ def test_server_calls_reject_null_handles(lib):
     assert lib.pit_serve_submit(None, None, None, C.byref(t)) == pit.PIT_E_INVALID
     assert lib.pit_server_destroy(None) == pit.PIT_OK
     assert lib.pit_server_create(0, 0, None) == pit.PIT_E_INVALID
+
+
+@pytest.mark.parametrize("name", ["pit_block_reduce", "pit_block_reduce_noalloc"])
+def test_reductions_reject_more_blocks_than_grid_rows(lib, name):
+    """One grid row per block: nblocks > 65535 is refused before any device
+    call (the pointers are never dereferenced), also where the allocation-free
+    variant's scratch would hold the partial sums (M = 1)."""
+    from paper_2203_10148_gb300 import pit
+    fake = C.c_void_p(256)
+    st = getattr(lib, name)(fake, fake, 65536, 1, fake, None, fake)
+    assert st == pit.PIT_E_INVALID
+    assert "65535" in pit.last_error()

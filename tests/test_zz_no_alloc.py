@@ -56,3 +56,16 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                              out.data_ptr(), None, out.data_ptr() + 8)
     assert st == pit.PIT_E_INVALID
     assert "fixed scratch" in pit.last_error()
+
+
+def test_noalloc_rejects_more_blocks_than_grid_rows():
+    """65536 blocks of one value fit the scratch (65536 chunks) but not the
+    grid (one grid row per block, at most 65535): refused as invalid, not
+    reported as a failed launch."""
+    from paper_2203_10148_gb300 import pit
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    st = pit.load().pit_block_reduce_noalloc(x.data_ptr(), x.data_ptr(), 65536, 1,
+                                             out.data_ptr(), None, out.data_ptr() + 8)
+    assert st == pit.PIT_E_INVALID
+    assert "65535" in pit.last_error()
