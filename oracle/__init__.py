@@ -17,12 +17,14 @@ Parity unpinned: the paper prints no iteration counts or residual values
 (its Fig. 1 images are missing), so iteration *counts* of the paper's runs
 cannot be pinned.
 """
-from .operators import (OracleProblem, block_dot, block_norms, dense_rk4_propagator_matrix,
+from .operators import (OracleProblem, block_dot, block_norms, chebyshev_ie_propagator,
+                        dense_rk4_propagator_matrix,
                         implicit_euler_propagator, matrix_propagator, norm2, norm_N_inf,
                         rk4_propagator, rk4_step_matrix, spatial_operator)
 from .solvers import SolveInfo, parareal, pitsbicg
 
-__all__ = ["OracleProblem", "block_dot", "block_norms", "dense_rk4_propagator_matrix",
+__all__ = ["OracleProblem", "block_dot", "block_norms", "chebyshev_ie_propagator",
+           "dense_rk4_propagator_matrix",
            "implicit_euler_propagator", "matrix_propagator", "norm2", "norm_N_inf",
            "rk4_propagator", "rk4_step_matrix", "spatial_operator", "SolveInfo",
            "parareal", "pitsbicg"]

@@ -28,7 +28,8 @@ seeded finite-difference workloads of the same family stand in for them):
                   n x n points x_i = i/n; v = curl of a random stream function
                   (8 Fourier modes) scaled to max |v| = 1; upwind advection,
                   central diffusion; fine = RK4 with
-                  dt = min(0.4 h/|v|max, 0.2 h^2/nu); coarse = IE 1 step.
+                  dt = min(0.4 h/|v|max, 0.2 h^2/nu); coarse = IE 1 step
+                  whose linear solve is ``coarse_inner`` Chebyshev steps.
 * ``dense``    -- y' = A y, A = -(S S^T/M + 0.1 I) + 0.5 (K - K^T)/sqrt(M);
                   fine = RK4 with ``steps`` steps per slice (applied as one
                   precomputed dense propagator), coarse = IE 1 step.
@@ -118,6 +119,9 @@ class Workload:
     precision: str = "fp64"
     arrival: float = 0.0
     f: Optional[np.ndarray] = None     # time-independent source (batch, M) of y' = L y + f
+    # advdiff2d: Chebyshev steps replacing each implicit-Euler solve of the
+    # coarse step (0: the library's default)
+    coarse_inner: int = 0
 
     @property
     def M(self) -> int:
@@ -139,6 +143,7 @@ class Workload:
         return {"workload": self.name, "kind": self.kind, "grid": [self.nx, self.ny],
                 "M": self.M, "N": self.N, "batch": self.batch, "T": self.T, "nu": self.nu,
                 "fine": list(self.fine), "coarse": list(self.coarse), "tol": self.tol,
+                **({"coarse_inner": self.coarse_inner} if self.coarse_inner else {}),
                 "precision": self.precision}
 
 
@@ -195,7 +200,7 @@ def advdiff2d_rk4_steps(n: int, nu: float, dT: float, vmax: float = 1.0) -> int:
 
 
 def advdiff2d(n: int = 512, nu: float = 5e-3, T: float = 0.5, N: int = 256,
-              fine_steps: Optional[int] = None, coarse_steps: int = 1,
+              fine_steps: Optional[int] = None, coarse_steps: int = 1, coarse_inner: int = 8,
               psi_modes: int = 8, u_modes: int = 16, batch: int = 1,
               seed: int = SEED_ADVDIFF2D, tol: float = 1e-6,
               precision: str = "mixed") -> Workload:
@@ -230,7 +235,8 @@ def advdiff2d(n: int = 512, nu: float = 5e-3, T: float = 0.5, N: int = 256,
         fine_steps = advdiff2d_rk4_steps(n, nu, T / N)
     return Workload(f"advdiff2d_{n}x{n}_N{N}", "advdiff2d", n, n, nu, T, N, ("rk4", fine_steps),
                     ("ie", coarse_steps), np.stack(y0s), vx=vx.reshape(-1).copy(),
-                    vy=vy.reshape(-1).copy(), tol=tol, precision=precision)
+                    vy=vy.reshape(-1).copy(), tol=tol, precision=precision,
+                    coarse_inner=coarse_inner)
 
 
 def dense(M: int = 1024, T: float = 10.0, N: int = 4096, fine_steps: int = 200,

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle import (OracleProblem, block_dot, dense_rk4_propagator_matrix,
+from oracle import (OracleProblem, block_dot, chebyshev_ie_propagator, dense_rk4_propagator_matrix,
                     implicit_euler_propagator, matrix_propagator, norm_N_inf, parareal, pitsbicg,
                     rk4_propagator, rk4_step_matrix, spatial_operator)
 from paper_2203_10148_gb300 import inputs
@@ -126,6 +126,92 @@ def test_advdiff_fourier_modes_constant_velocity(vx, vy):
         lam -= vx * (1 - np.exp(-1j * tx)) / h if vx >= 0 else vx * (np.exp(1j * tx) - 1) / h
         lam -= vy * (1 - np.exp(-1j * ty)) / h if vy >= 0 else vy * (np.exp(1j * ty) - 1) / h
         np.testing.assert_allclose(L @ e, lam * e, atol=1e-9 * abs(lam))
+
+
+def _chebyshev_T(K, z):
+    """Chebyshev polynomial of the first kind, T_K(z) = cosh(K arccosh z),
+    evaluated directly at a complex point (not by the three-term recurrence)."""
+    return np.cosh(K * np.arccosh(complex(z)))
+
+
+@pytest.mark.parametrize("vx,vy", [(0.6, 0.3), (-0.5, 0.8)])
+@pytest.mark.parametrize("K", [1, 2, 5, 8, 13])
+def test_chebyshev_ie_step_is_the_chebyshev_polynomial_on_fourier_modes(vx, vy, K):
+    """Constant velocity on the periodic grid: the diagonal of I - dT L is one
+    number D, every Fourier mode b is an eigenvector of I - dT L with
+    eigenvalue mu (from the difference symbols), and the scaled eigenvalue is
+    lambda = mu / D.  K steps of Chebyshev acceleration on [1 - rho, 1 + rho]
+    from w = b leave the residual b - (I - dT L) w_K = P_K(lambda)(1 - mu) b
+    with the residual polynomial P_K(lambda) = T_K((1 - lambda)/rho) / T_K(1/rho)
+    (Saad, Sec. 12.3).  Modes up to the grid's Nyquist frequency, where the
+    advection symbol puts lambda off the real interval."""
+    n, nu, dT = 16, 0.02, 0.2
+    h = 1.0 / n
+    L = spatial_operator("advdiff2d", n, n, nu, np.full(n * n, vx), np.full(n * n, vy))
+    D = 1.0 + dT * (4 * nu / h ** 2 + abs(vx) / h + abs(vy) / h)
+    rho = (D - 1.0) / D
+    assert 0.8 < rho < 0.95                 # the stiff regime of the 512^2 workload
+    G = chebyshev_ie_propagator(L, dT, 1, K)
+    xs = np.arange(n) / n
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    for kx, ky in ((0, 0), (1, 0), (2, -3), (4, 4), (-7, 5), (8, 8)):
+        tx, ty = 2 * math.pi * kx * h, 2 * math.pi * ky * h
+        b = np.exp(2j * math.pi * (kx * X + ky * Y)).reshape(-1)
+        ell = nu * (2 * math.cos(tx) - 2 + 2 * math.cos(ty) - 2) / h ** 2
+        ell -= vx * (1 - np.exp(-1j * tx)) / h if vx >= 0 else vx * (np.exp(1j * tx) - 1) / h
+        ell -= vy * (1 - np.exp(-1j * ty)) / h if vy >= 0 else vy * (np.exp(1j * ty) - 1) / h
+        mu = 1.0 - dT * ell
+        lam = mu / D
+        P = _chebyshev_T(K, (1.0 - lam) / rho) / _chebyshev_T(K, 1.0 / rho)
+        w = G(b[None, :])[0]
+        resid = b - (w - dT * (L @ w))
+        np.testing.assert_allclose(resid, P * (1.0 - mu) * b, rtol=0,
+                                   atol=1e-12 * max(1.0, abs(1.0 - mu)))
+
+
+def test_chebyshev_ie_step_tends_to_the_implicit_euler_step():
+    """With many steps the Chebyshev coarse step converges to the exact
+    implicit-Euler step (sparse LU) on the variable-velocity workload field,
+    in the regime of the 512^2 workload: diffusion-dominated (cell Peclet
+    number |v| h / nu about 0.4, so the scaled spectrum hugs the real
+    interval) and stiff (nu dT / h^2 about 2.6, rho about 0.9).  With K = 8 it
+    is still far from it on rough data, which is why the coarse step is
+    defined by K."""
+    w = inputs.advdiff2d(n=32, nu=0.08, N=1, T=0.0312)
+    L = spatial_operator(w.kind, w.nx, w.ny, w.nu, w.vx, w.vy)
+    exact = implicit_euler_propagator(L, w.T, 1)
+    b = inputs.SeededStream(5).normal(2 * w.M).reshape(2, w.M)
+    b[1] = w.y0[0]
+    ref = exact(b)
+    got = chebyshev_ie_propagator(L, w.T, 1, 160)(b)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    rough8 = chebyshev_ie_propagator(L, w.T, 1, 8)(b[:1])
+    assert np.abs(rough8 - ref[:1]).max() > 1e-3 * np.abs(ref[:1]).max()
+
+
+def test_chebyshev_ie_step_with_one_step_is_scaled_richardson():
+    """K = 1: w_1 = b + D^{-1}(b - (I - dT L) b) (theta = 1), a closed form."""
+    w = inputs.advdiff2d(n=16, N=1, T=0.1)
+    L = spatial_operator(w.kind, w.nx, w.ny, w.nu, w.vx, w.vy)
+    A = (np.eye(w.M) - w.T * L.toarray())
+    b = w.y0[0]
+    expect = b + (b - A @ b) / np.diag(A)
+    np.testing.assert_allclose(chebyshev_ie_propagator(L, w.T, 1, 1)(b[None])[0], expect,
+                               rtol=0, atol=1e-13 * np.abs(expect).max())
+
+
+def test_advdiff_workload_coarse_step_is_the_chebyshev_step():
+    """The advection-diffusion workloads name their coarse step's Chebyshev
+    count, and the oracle problem applies that operator (K = 0: exact IE)."""
+    w = inputs.advdiff2d(n=16, N=2, T=0.05)
+    assert w.coarse_inner == 8
+    L = spatial_operator(w.kind, w.nx, w.ny, w.nu, w.vx, w.vy)
+    b = w.y0
+    np.testing.assert_array_equal(OracleProblem.from_workload(w).G(b),
+                                  chebyshev_ie_propagator(L, w.dT, 1, 8)(b))
+    w.coarse_inner = 0
+    np.testing.assert_array_equal(OracleProblem.from_workload(w).G(b),
+                                  implicit_euler_propagator(L, w.dT, 1)(b))
 
 
 def test_advdiff_workload_energy_does_not_grow():
