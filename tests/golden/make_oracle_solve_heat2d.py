@@ -8,7 +8,14 @@ matvec counts, the residual history, the error against the serial fine
 trajectory, and sampled solution values (every 64th slice at 16 fixed
 points) so that full-size GPU results can be checked point by point.
 
+Also writes tests/golden/oracle_serial_heat2d_128_N512_every32.npy: the
+oracle's serial fine trajectory (the exact solution of eq. (4)) on every
+32nd slice boundary, lambda_0, lambda_32, ..., lambda_512 = y(T), in full
+(17 x 16384 float64 values), for element-by-element checks of full-size
+GPU solves.
+
 Run:  python tests/golden/make_oracle_solve_heat2d.py   (several minutes)
+      python tests/golden/make_oracle_solve_heat2d.py --serial-only   (the .npy alone)
 """
 import json
 import os
@@ -26,6 +33,12 @@ from paper_2203_10148_gb300 import inputs  # noqa: E402
 SAMPLE_POINTS = [0, 1, 127, 128, 1000, 4095, 5000, 8191, 8256, 9999, 12000, 16000, 16255,
                  16256, 16382, 16383]
 SAMPLE_SLICES = list(range(0, 513, 64))
+EVERY = 32
+SERIAL_NPY = os.path.join(HERE, "oracle_serial_heat2d_128_N512_every32.npy")
+
+
+def write_serial_slices(lam):
+    np.save(SERIAL_NPY, np.ascontiguousarray(lam[::EVERY], dtype=np.float64))
 
 
 def main():
@@ -34,6 +47,10 @@ def main():
     t0 = time.time()
     lam = o.serial_fine()
     t_serial = time.time() - t0
+    write_serial_slices(lam)
+    if "--serial-only" in sys.argv:
+        print(f"wrote {SERIAL_NPY} ({t_serial:.1f} s)")
+        return
     t0 = time.time()
     X, info = pitsbicg(o, tol=1e-6)
     t_solve = time.time() - t0

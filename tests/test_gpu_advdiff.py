@@ -1,24 +1,22 @@
 """GPU parity of the periodic advection-diffusion path (cluster/DSMEM fine
 kernel, band-parallel coarse sweep) against the FP64 oracle.
 
-The coarse propagator on the GPU is a fixed linear approximation of the
-implicit-Euler step (K Chebyshev steps on the Jacobi-scaled system from
-x = b, interval [1 - rho, 1 + rho] with rho = max (D - 1)/D); it is restated
-here in numpy on the oracle's assembled operator to check the sweep element
-by element.  The solution of eq. (4) does not depend on G, so converged
-solves are compared with the oracle's serial fine trajectory.
+The coarse propagator is implicit Euler with its linear solve replaced by K
+Chebyshev steps (the workload's ``coarse_inner``); the oracle states that
+operator in ``oracle.chebyshev_ie_propagator`` (pinned against the closed
+Chebyshev form and the exact implicit-Euler step in the oracle pins), so the
+sweep, the operators and fixed-k iterates of Algorithm 1 are compared with
+the oracle element by element.  The solution of eq. (4) does not depend on G,
+so converged solves are also compared with the serial fine trajectory.
 """
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
-from oracle import OracleProblem, spatial_operator
+from oracle import OracleProblem, pitsbicg
 from paper_2203_10148_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-K_CHEB = 8
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,34 +35,9 @@ def _rand(w, seed):
     return inputs.SeededStream(seed).normal(w.batch * (w.N + 1) * w.M).reshape(w.batch, w.N + 1, w.M)
 
 
-def _jacobi_sweep(w, Q, K=K_CHEB):
-    """z_0 = q_0, z_n = q_n + Gt z_{n-1}; Gt b = K Chebyshev steps for
-    (I - dT L) x = b with diagonal scaling, from x = b (Saad, Iterative
-    Methods for Sparse Linear Systems, Alg. 12.1)."""
-    L = spatial_operator(w.kind, w.nx, w.ny, w.nu, w.vx, w.vy)
-    A = (sp.identity(w.M) - (w.T / w.N) * L).tocsr()
-    D = A.diagonal()
-    rho = np.max((D - 1) / D)
-    theta, delta = 1.0, rho
-    sigma = theta / delta
-    Z = np.empty_like(Q)
-    Z[0] = Q[0]
-    for n in range(1, w.N + 1):
-        b = Z[n - 1]
-        x = b.copy()
-        r = b - A @ x
-        d = r / D / theta
-        rk = 1.0 / sigma
-        for k in range(K):
-            x = x + d
-            if k == K - 1:
-                break
-            r = r - A @ d
-            rn = 1.0 / (2 * sigma - rk)
-            d = rn * rk * d + (2 * rn / delta) * (r / D)
-            rk = rn
-        Z[n] = Q[n] + x
-    return Z
+def _oracle_sweep(w, X):
+    return np.stack([OracleProblem.from_workload(w, member=b).sweep_Ginv(X[b])
+                     for b in range(w.batch)])
 
 
 CASES = [dict(n=32, N=3), dict(n=64, N=4, batch=2), dict(n=128, N=2)]
@@ -87,16 +60,61 @@ def test_advdiff_fine_operator_fp64_and_fp32(case):
 
 
 @pytest.mark.parametrize("case", CASES)
-def test_advdiff_sweep_matches_jacobi_restatement(case):
+def test_advdiff_sweep_matches_oracle(case):
     from paper_2203_10148_gb300 import pit
     w = inputs.advdiff2d(T=0.5 * case["N"] / 256, **case)
     X = _rand(w, 2)
-    ref = np.stack([_jacobi_sweep(w.member(b) if w.batch > 1 else w, X[b]) for b in range(w.batch)])
+    ref = _oracle_sweep(w, X)
     with pit.Problem(w, "mixed") as p:
         got64 = p.apply("Ginv", X, precision="fp64")
         got32 = p.apply("Ginv", X, precision="mixed")
     assert _rel(got64, ref) < 1e-12
     assert _rel(got32, ref) < 1e-5
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 24, 64])
+def test_advdiff_sweep_chebyshev_count(K):
+    """The coarse step's Chebyshev count is part of the problem: every count
+    from 1 to the maximum gives the oracle's operator."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.advdiff2d(n=64, N=3, T=0.5 * 3 / 256, coarse_inner=K)
+    X = _rand(w, 12)
+    ref = _oracle_sweep(w, X)
+    with pit.Problem(w, "fp64") as p:
+        got = p.apply("Ginv", X, precision="fp64")
+    assert _rel(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("case", [dict(n=64, N=6), dict(n=128, N=4, coarse_inner=24)])
+def test_advdiff_bicgstab_fixed_iterations_match_oracle(case):
+    """k iterations of Algorithm 1 in FP64 (k = 1, 2, 3): the iterates agree
+    with the oracle's to 1e-12 and the matvec counts are identical."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.advdiff2d(T=0.5 * case["N"] / 256, precision="fp64", **case)
+    o = OracleProblem.from_workload(w)
+    with pit.Problem(w, "fp64") as p:
+        for k in (1, 2, 3):
+            X, info = p.bicgstab_solve(tol=0.0, max_iter=k)
+            Xo, oi = pitsbicg(o, tol=0.0, max_iter=k)
+            assert info[0]["iterations"] == k and oi.iterations == k
+            assert info[0]["matvecs"] == oi.matvecs
+            assert _rel(X[0], Xo) < 1e-12
+
+
+def test_advdiff_bicgstab_converged_matches_oracle_iterations():
+    """Converged FP64 solve: the same iteration count as the oracle's
+    Algorithm 1 and the serial fine trajectory within the tolerance."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.advdiff2d(n=64, N=8, T=0.5 * 8 / 256, precision="fp64")
+    o = OracleProblem.from_workload(w)
+    lam = o.serial_fine()
+    Xo, oi = pitsbicg(o, tol=1e-10)
+    with pit.Problem(w, "fp64") as p:
+        X, info = p.bicgstab_solve(tol=1e-10)
+    assert info[0]["status"] == 0 and oi.status == "ok"
+    assert info[0]["iterations"] == oi.iterations
+    assert _rel(X[0], Xo) < 1e-10
+    assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-8
 
 
 def test_advdiff_solves_reach_serial_trajectory():

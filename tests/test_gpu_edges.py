@@ -45,15 +45,6 @@ def _oracle_apply(w, which, X):
     out = []
     for b in range(w.batch):
         o = OracleProblem.from_workload(w, member=b)
-        if w.kind == "advdiff2d" and which != "F":
-            # the advection-diffusion coarse step is the fixed Chebyshev
-            # polynomial of the implicit-Euler system (restated in the
-            # advection-diffusion tests), not its exact solve
-            from test_gpu_advdiff import _jacobi_sweep
-            q = {"Ginv": X[b], "GinvF": o.apply_F(X[b]),
-                 "residual": o.rhs() - o.apply_F(X[b])}[which]
-            out.append(_jacobi_sweep(w, q))
-            continue
         fn = {"F": o.apply_F, "Ginv": o.sweep_Ginv, "GinvF": o.apply_GinvF,
               "residual": o.residual}[which]
         out.append(fn(X[b]))

@@ -1,10 +1,13 @@
 """Full-size parity on the benchmark workload (2D heat 128 x 128, N = 512,
 50 RK4 fine steps per slice): the GPU against the oracle's own Algorithm 1
-run stored in tests/golden/oracle_solve_heat2d_128_N512.json (written by
-tests/golden/make_oracle_solve_heat2d.py, which calls only oracle/).
-Compared: iteration and matvec counts, the residual history, and sampled
-solution values (every 64th slice at 16 points), on the launch
-configuration bench.py times."""
+run stored in tests/golden/oracle_solve_heat2d_128_N512.json and the
+oracle's serial fine trajectory (the exact solution of eq. (4)) on every
+32nd slice boundary in full, tests/golden/oracle_serial_heat2d_128_N512_every32.npy
+(both written by tests/golden/make_oracle_solve_heat2d.py, which calls only
+oracle/).  Compared: iteration and matvec counts, the residual history,
+sampled solution values (every 64th slice at 16 points), and 17 x 16384
+values per solve, on the launch configuration bench.py times (a batch of 8
+members, event timing on, the one-pass sine-mode recurrence of the sweep)."""
 import json
 import os
 
@@ -16,6 +19,8 @@ from paper_2203_10148_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "oracle_solve_heat2d_128_N512.json")
+SERIAL = os.path.join(os.path.dirname(__file__), "golden", "oracle_serial_heat2d_128_N512_every32.npy")
+EVERY = 32
 
 
 @pytest.fixture(scope="module")
@@ -58,3 +63,60 @@ def test_mixed_path_full_size_within_1e6(gold):
     sref = np.array(gold["serial_samples"])
     assert info[0]["status"] == 0
     assert np.abs(_samples(Xh, gold) - sref).max() <= 1e-6 * np.abs(sref).max()
+
+
+def _rel_max(a, ref):
+    return np.abs(a - ref).max() / np.abs(ref).max()
+
+
+def test_serial_trajectory_every_32nd_slice_fp64_and_ff(gold):
+    """The GPU's serial fine trajectory in FP64 and in float-float against the
+    oracle's, 17 slice boundaries x 16384 points."""
+    from paper_2203_10148_gb300 import pit
+    ref = np.load(SERIAL)
+    w = inputs.heat2d()
+    with pit.Problem(w, "mixed") as p:
+        lam64 = p.serial_fine("fp64")[0]
+        lamff = p.serial_fine("ff")[0]
+    assert lam64[::EVERY].shape == ref.shape
+    assert _rel_max(lam64[::EVERY], ref) <= 1e-12
+    assert _rel_max(lamff[::EVERY], ref) <= 1e-10
+
+
+def test_mixed_batch8_solve_every_32nd_slice(gold):
+    """The benchmark's batch of 8 with the oracle's member in slot 5: the
+    mixed solve (bench options: tolerance 1e-7 relative to ||G^-1 B||, inner
+    tolerance 1e-5, event timing on) within 1e-6 of the oracle's exact
+    solution at every one of the 17 x 16384 stored values; the other members
+    within 1e-6 of the GPU's FP64 serial trajectory."""
+    from paper_2203_10148_gb300 import pit
+    ref = np.load(SERIAL)
+    w = inputs.heat2d(batch=8, seed=0x5049E001)
+    y0 = w.y0.copy()
+    y0[5] = inputs.heat2d().y0[0]
+    w.y0 = y0
+    with pit.Problem(w, "mixed") as p:
+        p.set_timing(True)
+        X = torch.zeros((8, w.N + 1, w.M), dtype=torch.float64, device="cuda")
+        X, info = p.bicgstab_solve(X, tol=1e-7, tol_mode="rhs", inner_tol=1e-5, max_iter=200)
+        lam = p.serial_fine("fp64")
+    Xh = X.cpu().numpy()
+    assert all(i["status"] == 0 for i in info)
+    assert _rel_max(Xh[5][::EVERY], ref) <= 1e-6
+    for b in range(8):
+        assert np.linalg.norm(Xh[b] - lam[b]) / np.linalg.norm(lam[b]) <= 1e-6
+    assert _rel_max(lam[5][::EVERY], ref) <= 1e-12
+
+
+def test_fp64_solve_every_32nd_slice(gold):
+    """The FP64 path's solve (tolerance 1e-10) against the oracle's exact
+    solution in full on the stored slices: the error of a converged solve,
+    not only sampled points."""
+    from paper_2203_10148_gb300 import pit
+    ref = np.load(SERIAL)
+    w = inputs.heat2d()
+    with pit.Problem(w, "fp64") as p:
+        X = torch.zeros((1, w.N + 1, w.M), dtype=torch.float64, device="cuda")
+        X, info = p.bicgstab_solve(X, tol=1e-10, max_iter=50)
+    assert info[0]["status"] == 0
+    assert _rel_max(X.cpu().numpy()[0][::EVERY], ref) <= 1e-9

@@ -170,3 +170,18 @@ def test_fem_operator_is_consistent(pde):
         q = n // 4
         errs.append(np.abs(got - Lf)[q:-q, q:-q].max() / np.abs(Lf).max())
     assert errs[1] < errs[0] / 3.0 and errs[1] < 5e-3
+
+
+def test_stored_serial_slices_agree_with_the_stored_oracle_run():
+    """The full-slice fixture and the sampled oracle run were written by the
+    same oracle script: slice 0 is the workload's y0, and every 64th slice
+    holds the sampled serial values of the JSON fixture."""
+    import json
+    import os
+    gdir = os.path.join(os.path.dirname(__file__), "golden")
+    lam = np.load(os.path.join(gdir, "oracle_serial_heat2d_128_N512_every32.npy"))
+    g = json.load(open(os.path.join(gdir, "oracle_solve_heat2d_128_N512.json")))
+    assert lam.shape == (17, 128 * 128)
+    np.testing.assert_array_equal(lam[0], inputs.heat2d().y0[0])
+    got = np.array([[lam[n // 32, i] for i in g["sample_points"]] for n in g["sample_slices"]])
+    np.testing.assert_allclose(got, np.array(g["serial_samples"]), rtol=1e-14, atol=1e-300)
