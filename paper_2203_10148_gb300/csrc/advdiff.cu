@@ -19,8 +19,9 @@
 //
 // Coarse sweep (eq. (7), right): G is one implicit-Euler step,
 // (I - dT L) w = b.  L has variable coefficients and is not symmetric, so no
-// transform diagonalises it; G is applied as a fixed linear operator: K = 8
-// steps of the Chebyshev semi-iteration on the Jacobi-scaled system
+// transform diagonalises it; G is applied as a fixed linear operator: K
+// (the coarse stepper's inner count, 48 by default) steps of the Chebyshev
+// semi-iteration on the Jacobi-scaled system
 // D^{-1} (I - dT L) w = D^{-1} b, started from w = b, for the eigenvalue
 // interval [1 - rho, 1 + rho] with rho = max_p (D_p - 1) / D_p (the
 // Gershgorin bound of the scaled system).  The coefficients depend on the
@@ -564,7 +565,7 @@ pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
 // ------------------------------------------------------------------ sweep
 constexpr int SWA_THREADS = 256;
 constexpr int SWA_PPT = 8;                     // points per thread: bands of <= 2048 points
-constexpr int SWA_KMAX = 16;
+constexpr int SWA_KMAX = 64;     // Chebyshev steps per coarse solve, at most
 constexpr long long SWA_SPIN = 1LL << 26;
 
 template <class T>
@@ -843,14 +844,19 @@ pit_status advdiff_setup(Problem *p) {
         }
         const double lmin = 1.0 - rho, lmax = 1.0 + rho;
         const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-        p->adv_K = 8;
+        p->adv_K = p->coarse_inner > 0 ? p->coarse_inner : 48;
         p->adv_inv_theta = 1.0 / theta;
         double r = 1.0 / sigma;
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < SWA_KMAX; ++k) {
             const double rn = 1.0 / (2.0 * sigma - r);
             p->adv_c1[k] = rn * r;
             p->adv_c2[k] = 2.0 * rn / delta;
             r = rn;
+        }
+        if (!(delta > 0.0)) {
+            // nu = 0 and v = 0: I - dT L = I, and w = b after one step is exact
+            p->adv_K = 1;
+            for (int k = 0; k < SWA_KMAX; ++k) p->adv_c1[k] = p->adv_c2[k] = 0.0;
         }
     }
     // the cluster shape must be schedulable (n / 32 CTAs of one SM each)

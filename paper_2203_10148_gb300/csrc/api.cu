@@ -789,6 +789,7 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
     }
     if (op.nx < 1 || op.ny < 1 || d->N < 1 || d->batch < 1 || !(d->T > 0.0) ||
         d->fine.steps < 1 || d->coarse.steps < 1 || !d->y0 ||
+        d->coarse.inner < 0 || d->coarse.inner > 64 ||
         (d->precision != PIT_FP64 && d->precision != PIT_MIXED)) {
         set_error("pit_problem_create: invalid sizes, steps, T, precision or null y0");
         return PIT_E_INVALID;
@@ -840,6 +841,7 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
     p->fine_steps = d->fine.steps;
     p->coarse_kind = d->coarse.kind;
     p->coarse_steps = d->coarse.steps;
+    p->coarse_inner = d->coarse.inner;
     p->precision = d->precision;
     p->blen = (size_t)(p->N + 1) * M;
     p->vlen = p->blen * p->batch;

@@ -145,6 +145,7 @@ struct Problem {
     int kind = 0, nx = 0, ny = 0, M = 0, N = 0, batch = 0;
     double T = 0, dT = 0, nu = 0;
     int fine_kind = 0, fine_steps = 0, coarse_kind = 0, coarse_steps = 0;
+    int coarse_inner = 0;   // advdiff coarse IE: Chebyshev steps per solve (0: default)
     int precision = PIT_FP64;
     size_t blen = 0;              // (N+1)*M
     size_t vlen = 0;              // batch*(N+1)*M
@@ -172,7 +173,7 @@ struct Problem {
     DevBuf adv_scratch;
     int adv_K = 8;                // Chebyshev steps of the coarse IE step
     int adv_coef32 = 0;           // every coefficient v / h is an FP32 value (float-float lo parts zero)
-    double adv_inv_theta = 1.0, adv_c1[16] = {}, adv_c2[16] = {};   // Chebyshev coefficients
+    double adv_inv_theta = 1.0, adv_c1[64] = {}, adv_c2[64] = {};   // Chebyshev coefficients
 
     // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)
     DevBuf PhiF64, G64, PhiF_hi, PhiF_lo, G32;

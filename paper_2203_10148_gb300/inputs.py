@@ -200,7 +200,7 @@ def advdiff2d_rk4_steps(n: int, nu: float, dT: float, vmax: float = 1.0) -> int:
 
 
 def advdiff2d(n: int = 512, nu: float = 5e-3, T: float = 0.5, N: int = 256,
-              fine_steps: Optional[int] = None, coarse_steps: int = 1, coarse_inner: int = 8,
+              fine_steps: Optional[int] = None, coarse_steps: int = 1, coarse_inner: int = 48,
               psi_modes: int = 8, u_modes: int = 16, batch: int = 1,
               seed: int = SEED_ADVDIFF2D, tol: float = 1e-6,
               precision: str = "mixed") -> Workload:

@@ -42,7 +42,7 @@ class OperatorDesc(C.Structure):
 
 
 class StepperDesc(C.Structure):
-    _fields_ = [("kind", C.c_int), ("steps", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("steps", C.c_int), ("inner", C.c_int)]
 
 
 class ProblemDesc(C.Structure):
@@ -217,7 +217,8 @@ def problem_desc(w, precision: int) -> Tuple[ProblemDesc, list]:
         op.A = _dptr(A)
     desc = ProblemDesc(op, _dptr(y0), int(w.batch), float(w.T), int(w.N),
                        StepperDesc(PIT_STEP[w.fine[0]], int(w.fine[1])),
-                       StepperDesc(PIT_STEP[w.coarse[0]], int(w.coarse[1])), precision)
+                       StepperDesc(PIT_STEP[w.coarse[0]], int(w.coarse[1]),
+                                   int(getattr(w, "coarse_inner", 0))), precision)
     return desc, keep
 
 

@@ -52,7 +52,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     from paper_2203_10148_gb300 import pit
     x = torch.zeros(8, dtype=torch.float64, device="cuda")
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
-    st = pit.load().pit_block_reduce_noalloc(x.data_ptr(), x.data_ptr(), 65537, 1,
+    # 2 blocks of 2048 * 40000 values: 80000 chunks (the pointers are never read)
+    st = pit.load().pit_block_reduce_noalloc(x.data_ptr(), x.data_ptr(), 2, 2048 * 40000,
                                              out.data_ptr(), None, out.data_ptr() + 8)
     assert st == pit.PIT_E_INVALID
     assert "fixed scratch" in pit.last_error()
