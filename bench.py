@@ -56,7 +56,12 @@ FLOP_PER_POINT_STEP = 28       # RK4 Horner: 4 stages x (3 add + 2 FMA) = 4 x 7 
 # FP32 4 stages x 5; float-float 4 stages x 44 FP32 ops (four TwoSums of 6,
 # 8 for the low parts, a 4-op product, a TwoSum of 6 and 2 to collect the low
 # part) + a 3-op renormalisation per step; FP64 4 x 5 FP64 ops
-OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 179, "fine_fp64": 20}
+OPS_PER_POINT_STEP = {"fine_fp32": 20, "fine_ff": 179, "fine_fp64": 20, "fine_split": 69}
+# the method's own work per point and RK4 step (Horner form, 4 stages x
+# (3 FADD + 2 FFMA)), whatever arithmetic carries it out: the roofline's frac
+METHOD_OPS_PER_POINT_STEP = 20
+# split RK4 (true residuals): 44 for the float-float first-order stage (the
+# float-float stage above), 3 x 5 for the FP32 stages, 10 for the final sum
 # periodic advection-diffusion: 4 stages x 14 (5 for the Laplacian, 2 x 3 for the
 # upwind differences, 2 for the advection sum, 1 to combine)
 ADV_OPS_PER_POINT_STEP = 56
@@ -68,7 +73,7 @@ ADV_FF_OPS_PER_POINT_STEP = 360
 FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2          # 1.25 TFLOP/s nominal FP64 = 2 FMA/clk/SM at 2.07 GHz x 152 SMs
 KERNEL_NAMES = {"fine_fp32": "k_heat2d_fine<float>", "fine_ff": "k_heat2d_fine<ff>",
-                "fine_fp64": "k_heat2d_fine<double>"}
+                "fine_fp64": "k_heat2d_fine<double>", "fine_split": "k_heat2d_split"}
 ADV_KERNEL_NAMES = {"fine_fp32": "k_advdiff_fine<float>", "fine_ff": "k_advdiff_fine<ff>",
                     "fine_fp64": "k_advdiff_fine<double>"}
 
@@ -109,6 +114,9 @@ def _parser():
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent solves")
     ap.add_argument("--tol", type=float, default=1e-7,
                     help="tolerance relative to ||G^-1 B|| (error target 1e-6)")
+    ap.add_argument("--residual", default="split", choices=["split", "ff", "fp64"],
+                    help="arithmetic of the true residual's fine propagations (heat2d: split RK4 "
+                         "where 8 nu dt/h^2 <= 1/8; other operators: split means float-float)")
     return ap
 
 
@@ -299,7 +307,10 @@ def cpu_baseline(w, slices=32, all_cores=True):
                       f"{t_mv:.2f} s per G^-1F matvec; x {mv} matvecs of the oracle's own "
                       f"Algorithm 1 solve of this workload (tests/golden)"),
            "seconds_per_matvec": t_mv,
-           "fine_slice_steps_per_s": w.N * w.fine[1] / t_f}
+           "fine_slice_steps_per_s": w.N * w.fine[1] / t_f,
+           # not a timed whole solve: the fine propagator is timed on `slices`
+           # slices and scaled to N, and the matvec count is the oracle's own
+           "extrapolated_from_slices": slices, "of_slices": w.N, "matvecs_assumed": mv}
     out["value"] = (1.0 / (t_mv * mv)) if mv else None
     if all_cores and mv:
         try:
@@ -320,10 +331,12 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload(args, 0)
-    vals = []
+    vals, step_s = [], []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         cb = cpu_baseline(w, slices=8)
         if i >= args.warmup:
+            step_s.append(time.perf_counter() - t0)
             vals.append(cb.get("all_cores", {}).get("value") or cb["value"])
     v = float(np.median(vals)) if vals and vals[0] else None
     # the reference arm is the oracle on all the host's cores (falling back to
@@ -336,16 +349,33 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "PiT solves/s (rel err <= 1e-6 vs FP64 path)",
             "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup,
-            # the oracle's estimated time for one step of this workload (a batch of solves)
-            "ms_per_step": (1e3 * w.batch / v) if v else None,
+            # wall time of each timed step: the bounded oracle sample, not a
+            # whole batch of solves (value extrapolates the sample to solves)
+            "ms_per_step": 1e3 * float(np.mean(step_s)) if step_s else None,
+            "oracle_ms_per_batch_estimated": (1e3 * w.batch / v) if v else None,
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "batch": w.batch, "grid": [w.nx, w.ny], "N": w.N,
-                       "fine": list(w.fine), "coarse": list(w.coarse), "tol": 1e-6},
+            "config": bench_config(args, w, 1),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def bench_config(args, w, world):
+    """The workload description both arms print (the reference arm names the
+    same workload it samples)."""
+    cfg = {"workload": w.name, "batch_per_gpu": w.batch, "grid": [w.nx, w.ny],
+           "N": w.N, "fine": list(w.fine), "coarse": list(w.coarse),
+           "precision": "mixed", "tol": args.tol, "tol_mode": "rhs",
+           "inner_tol": args.inner_tol,
+           "true_residual": {"split": "split RK4 (float-float first-order term, FP32 higher-order terms)",
+                             "ff": "float-float", "fp64": "fp64"}[args.residual],
+           "l2": "working set > L2 (9 Krylov vectors x %.0f MB)" % (w.batch * (w.N + 1) * w.M * 8 / 1e6),
+           "parallelism": f"replicas x{world}"}
+    if getattr(w, "coarse_inner", 0):
+        cfg["coarse_chebyshev_steps"] = w.coarse_inner
+    return cfg
 
 
 # ----------------------------------------------------------------- roofline
@@ -353,7 +383,8 @@ def run_reference(args):
 def roofline(w, timing, peaks, nsm):
     """Roofline of the dominant fine-propagator kernel class, from the
     per-class CUDA-event times recorded inside the timed solves."""
-    fine = {k: timing[k] for k in ("fine_fp32", "fine_ff", "fine_fp64") if timing[k][0]}
+    fine = {k: timing[k] for k in ("fine_fp32", "fine_ff", "fine_fp64", "fine_split")
+            if timing.get(k, (0, 0.0))[0]}
     if not fine:
         return None
     dom = max(fine, key=lambda k: fine[k][1])
@@ -391,27 +422,33 @@ def roofline(w, timing, peaks, nsm):
     lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
     peak = lanes * nsm * sm_max * 1e6 / 1e12
     if w.kind == "advdiff2d":
-        ops = ADV_FF_OPS_PER_POINT_STEP if dom == "fine_ff" else ADV_OPS_PER_POINT_STEP
+        method = ADV_OPS_PER_POINT_STEP
+        executed = ADV_FF_OPS_PER_POINT_STEP if dom in ("fine_ff", "fine_split") else ADV_OPS_PER_POINT_STEP
     else:
-        ops = OPS_PER_POINT_STEP[dom]
-    achieved = point_steps * ops / (avg_ms / 1e3) / 1e12
-    kname = KERNEL_NAMES[dom] if w.kind == "heat2d" else ADV_KERNEL_NAMES[dom]
+        method = METHOD_OPS_PER_POINT_STEP
+        executed = OPS_PER_POINT_STEP[dom]
+    secs = avg_ms / 1e3
+    kname = KERNEL_NAMES[dom] if w.kind == "heat2d" else ADV_KERNEL_NAMES.get(dom, ADV_KERNEL_NAMES["fine_ff"])
     units = w.batch * w.N * w.M                     # point-slices per launch
     tr = traffic_for(kname, units) if w.kind == "heat2d" else None
-    # algorithmic bytes: x_{n-1} and x_n read (FP64), the block-operator row
-    # written (FP32 for the inner solves, FP64 for residuals)
-    alg_bytes = units * (8 + 8 + (4 if dom == "fine_fp32" else 8))
-    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-            "unit": "Tops/s (%s pipe lane-ops)" % ("FP64" if dom == "fine_fp64" else "FP32"),
-            "frac": achieved / peak,
+    # algorithmic bytes per point-slice: x_{n-1} read and the block-operator
+    # row written once (x_n and x_{n-1} are the same array, read once over
+    # the launch): FP64 in, FP64 out (residuals) or FP32 out (inner solves)
+    alg_bytes = units * (8 + (4 if dom == "fine_fp32" else 8))
+    roof = {"bound": "alu", "kernel": kname,
+            "achieved": point_steps * method / secs / 1e12, "peak": peak,
+            "unit": "Tops/s (%s pipe lane-ops of the method: %d per point-step)"
+                    % ("FP64" if dom == "fine_fp64" else "FP32", method),
+            "frac": point_steps * method / secs / 1e12 / peak,
+            "frac_executed": point_steps * executed / secs / 1e12 / peak,
+            "executed_ops_per_point_step": executed,
             "traffic": tr, "algorithmic_bytes": alg_bytes,
             "launch_ms": avg_ms, "launches": calls,
-            "flop_rate_tflops": point_steps * FLOP_PER_POINT_STEP / (avg_ms / 1e3) / 1e12,
+            "flop_rate_tflops": point_steps * FLOP_PER_POINT_STEP / secs / 1e12,
             "peak_source": f"derived: {lanes} lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz (max SM clock)"}
     f32 = timing["fine_fp32"]
     if f32[0]:
-        ops32 = ADV_OPS_PER_POINT_STEP if w.kind == "advdiff2d" else OPS_PER_POINT_STEP["fine_fp32"]
-        a32 = point_steps * ops32 / (f32[1] / f32[0] / 1e3) / 1e12
+        a32 = point_steps * method / (f32[1] / f32[0] / 1e3) / 1e12
         roof["fine_fp32"] = {"launch_ms": f32[1] / f32[0], "achieved": a32,
                              "frac": a32 / (FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12)}
     return roof
@@ -444,7 +481,7 @@ def run_ours(args):
     X = torch.zeros(shape, dtype=torch.float64, device=dev)
     solve_kw = dict(tol=args.tol, tol_mode="rhs", max_iter=200, refine_max=8,
                     inner_tol=args.inner_tol,
-                    residual_precision="ff")
+                    residual_precision=args.residual)
 
     def one(step):
         prob.set_y0(y0s[step])
@@ -499,6 +536,19 @@ def run_ours(args):
     t_ser32 = time.perf_counter() - t_ser
     e32 = (((lam32 - lam).reshape(w.batch, -1).norm(dim=1)
             / lam.reshape(w.batch, -1).norm(dim=1)).max().item())
+    # the no-PiT comparators that meet the 1e-6 bar: the serial trajectory in
+    # float-float and in the split RK4 arithmetic (heat2d; float-float elsewhere)
+    ser = {}
+    for prec in ("ff", "split"):
+        if prec == "split" and w.kind != "heat2d":
+            continue
+        torch.cuda.synchronize()
+        t_ser = time.perf_counter()
+        prob.serial_fine(prec, out=lam32)
+        torch.cuda.synchronize()
+        ser[prec] = (time.perf_counter() - t_ser,
+                     (((lam32 - lam).reshape(w.batch, -1).norm(dim=1)
+                       / lam.reshape(w.batch, -1).norm(dim=1)).max().item()))
     del lam32
     d = (X - lam).reshape(w.batch, -1)
     rel = (d.norm(dim=1) / lam.reshape(w.batch, -1).norm(dim=1)).max().item()
@@ -516,13 +566,7 @@ def run_ours(args):
                 "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32 fine / f64 krylov", "data": "synthetic",
-                "config": {"workload": w.name, "batch_per_gpu": w.batch, "grid": [w.nx, w.ny],
-                           "N": w.N, "fine": list(w.fine), "coarse": list(w.coarse),
-                           "precision": "mixed", "tol": args.tol, "tol_mode": "rhs",
-                           "inner_tol": args.inner_tol,
-                           "true_residual": "float-float",
-                           "l2": "working set > L2 (9 Krylov vectors x %.0f MB)" % (w.batch * (w.N + 1) * w.M * 8 / 1e6),
-                           "parallelism": f"replicas x{world}"},
+                "config": bench_config(args, w, world),
                 "fine_slice_steps_per_s": slice_steps / (total_ms / 1e3),
                 "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                                "p99": float(np.percentile(step_ms, 99))},
@@ -533,6 +577,13 @@ def run_ours(args):
                 "gpu_launches": int(launches), "roofline": roof, "breakdown": breakdown,
                 "serial_fine": {"fp64_s_per_batch": t_ser64, "fp32_s_per_batch": t_ser32,
                                 "fp32_rel_err": e32, "batch": w.batch,
+                                **{f"{k}_s_per_batch": v[0] for k, v in ser.items()},
+                                **{f"{k}_rel_err": v[1] for k, v in ser.items()},
+                                # the fastest serial trajectory within 1e-6 of FP64 (FP64 itself
+                                # included) against one PiT step of the same batch
+                                "pit_speedup_vs_best_serial_within_1e6": (
+                                    min([v[0] for v in ser.values() if v[1] <= 1e-6] + [t_ser64])
+                                    / (total_ms / 1e3 / K)),
                                 "note": "slice after slice on this GPU (no parallel in time), "
                                         "one launch per slice for the whole batch"},
                 "clocks": clocks}
@@ -639,7 +690,7 @@ def run_serving(args):
     K, W = args.steps, args.warmup
     steps = serving_steps(args, rank, W + K + 1)
     opts = dict(tol=args.tol, tol_mode="rhs", max_iter=200, refine_max=8,
-                inner_tol=args.inner_tol, residual_precision="ff")
+                inner_tol=args.inner_tol, residual_precision=args.residual)
     srv = pit.Server(hbm_budget_bytes=0, max_slots=args.slots)
 
     def one(ws, open_loop=True):

@@ -78,6 +78,16 @@ typedef int pit_status;
                                    FP32 pipe, FP64 inputs and outputs: stepping for HEAT2D
                                    and ADVDIFF2D, a compensated product for DENSE; HEAT1D
                                    treats it as PIT_FP64 */
+#define PIT_SPLIT           3   /* split RK4 (HEAT2D; other operators treat it as PIT_FF):
+                                   each step u + Z u + Z^2 u/2 + Z^3 u/6 + Z^4 u/24 (Z = dt L)
+                                   takes the first-order term Z u in float-float and the
+                                   others in FP32 (nested form) and keeps the state in
+                                   float-float: about 68 FP32 operations per point and step
+                                   against 179.  Used where ||Z|| = 8 nu dt / h^2 <= 1/8, so
+                                   that the FP32 terms are <= 8.1e-3 |u| and their rounding
+                                   costs <= about 5e-10 |u| per step (1.4e-3 and 1e-10 on the
+                                   128^2 workload; far less on smooth components, where the
+                                   terms scale with |Z|^2); larger steps run PIT_FF */
 
 /* pit_apply_operator: which operator. */
 #define PIT_APPLY_F         1   /* y = F x, the block operator of eq. (4) */
@@ -133,7 +143,7 @@ typedef struct {
                               iteration (PIT_FP64) or per refinement round (PIT_MIXED) */
     int history_len;
     int residual_precision; /* PIT_MIXED: arithmetic of the fine propagations inside the
-                               true residual, PIT_FF (default) or PIT_FP64 */
+                               true residual, PIT_FF (default), PIT_SPLIT or PIT_FP64 */
     int tol_mode;          /* PIT_TOL_R0 (default) or PIT_TOL_RHS */
 } pit_solve_opts;
 
@@ -451,7 +461,8 @@ pit_status pit_selftest_convert(const double *in, int n, float *f32, double *bac
 #define PIT_TIME_SWEEP_FP64  3   /* coarse sweep, FP64 */
 #define PIT_TIME_KRYLOV      4   /* fused BiCGStab vector kernels and finishers */
 #define PIT_TIME_FINE_FF     5   /* fine batch, float-float stepping (one kernel per call) */
-#define PIT_TIME_CLASSES     6
+#define PIT_TIME_FINE_SPLIT  6   /* fine batch, split RK4 stepping (one kernel per call) */
+#define PIT_TIME_CLASSES     7
 
 /*
  * enable = 1: every later operator application of this problem is bracketed

@@ -180,13 +180,22 @@ void OpTimer::destroy() {
     } while (0)
 
 static int fine_cls(int prec) {
-    return prec == PIT_FP64 ? PIT_TIME_FINE_FP64 : prec == PIT_FF ? PIT_TIME_FINE_FF : PIT_TIME_FINE_FP32;
+    return prec == PIT_FP64 ? PIT_TIME_FINE_FP64
+         : prec == PIT_FF ? PIT_TIME_FINE_FF
+         : prec == PIT_SPLIT ? PIT_TIME_FINE_SPLIT : PIT_TIME_FINE_FP32;
+}
+
+// The split RK4 arithmetic exists for the 2D heat stepper; elsewhere it
+// means float-float (which HEAT1D, and DENSE outside its product, run in FP64).
+static int split_or_ff(const Problem *p, int prec) {
+    return (prec == PIT_SPLIT && p->kind != PIT_OP_HEAT2D) ? PIT_FF : prec;
 }
 static int sweep_cls(int prec) { return prec == PIT_MIXED ? PIT_TIME_SWEEP_MIXED : PIT_TIME_SWEEP_FP64; }
 
 // --------------------------------------------------------- operator switch
 pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                       const MemberState *st, cudaStream_t s) {
+    prec = split_or_ff(p, prec);
     if (prec == PIT_FF && p->kind == PIT_OP_HEAT1D) prec = PIT_FP64;
     pit_status st_ = PIT_E_INVALID;
     switch (p->kind) {
@@ -214,6 +223,7 @@ pit_status op_sweep(Problem *p, const double *q, double *z, int prec, const Memb
 }
 
 static pit_status fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
+    prec = split_or_ff(p, prec);
     if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D && p->kind != PIT_OP_ADVDIFF2D) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_fine_one(p, x, y, prec, s);
@@ -372,7 +382,7 @@ static int sweep_prec(int prec) { return prec == PIT_MIXED ? PIT_MIXED : PIT_FP6
 
 static pit_status timed_F(Problem *p, const double *x, double *y, int mode, int prec,
                           const MemberState *st, cudaStream_t s) {
-    PIT_TIMED(p, fine_cls(prec), s, op_apply_F(p, x, y, mode, prec, st, s));
+    PIT_TIMED(p, fine_cls(split_or_ff(p, prec)), s, op_apply_F(p, x, y, mode, prec, st, s));
     return PIT_OK;
 }
 
@@ -954,7 +964,8 @@ pit_status pit_apply_operator(pit_problem_t h, int which, int precision, const d
         return PIT_E_INVALID;
     }
     if (which < PIT_APPLY_F || which > PIT_APPLY_RESIDUAL ||
-        (precision != PIT_FP64 && precision != PIT_MIXED && precision != PIT_FF)) {
+        (precision != PIT_FP64 && precision != PIT_MIXED && precision != PIT_FF &&
+         precision != PIT_SPLIT)) {
         set_error("pit_apply_operator: bad operator or precision");
         return PIT_E_INVALID;
     }
@@ -987,7 +998,8 @@ pit_status pit_apply_operator(pit_problem_t h, int which, int precision, const d
 }
 
 pit_status pit_serial_fine(pit_problem_t h, int precision, double *Lam, int on_device) {
-    if (!h || !Lam || (precision != PIT_FP64 && precision != PIT_MIXED && precision != PIT_FF)) {
+    if (!h || !Lam || (precision != PIT_FP64 && precision != PIT_MIXED && precision != PIT_FF &&
+                       precision != PIT_SPLIT)) {
         set_error("pit_serial_fine: bad argument");
         return PIT_E_INVALID;
     }
@@ -1013,7 +1025,8 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
     if (!(o->tol >= 0.0) || o->max_iter < 0 || o->x0_mode < PIT_X0_COARSE ||
         o->x0_mode > PIT_X0_GIVEN || !(o->restart_eps0 >= 0.0) ||
         (o->tol_mode != PIT_TOL_R0 && o->tol_mode != PIT_TOL_RHS) ||
-        (o->residual_precision != PIT_FF && o->residual_precision != PIT_FP64)) {
+        (o->residual_precision != PIT_FF && o->residual_precision != PIT_FP64 &&
+         o->residual_precision != PIT_SPLIT)) {
         set_error("pit_bicgstab_solve: invalid options");
         return PIT_E_INVALID;
     }
@@ -1077,7 +1090,7 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
         }
     } else {
         // Iterative refinement: FP64 true residual, FP32-fine inner solve.
-        const int rprec = o->residual_precision == PIT_FP64 ? PIT_FP64 : PIT_FF;
+        const int rprec = o->residual_precision;
         PIT_TRY(p->W.ensure(vb));
         double *Xo = p->W.as<double>();   // outer solution lives in W
         double *Wr = p->R.as<double>();   // true residual goes straight into R

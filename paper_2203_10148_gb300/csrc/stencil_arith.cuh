@@ -211,6 +211,53 @@ __device__ __forceinline__ ff2 ff_stage2(const ff2 &vn, const ff2 &vs, const ff2
     return w;
 }
 
+// ff_stage2 that also returns -fl(cc.hi * dh), the negated FP32 rounding of
+// the first-order term cc * (vn + vs + vw + ve - 4 vc) it adds to u (the
+// split RK4 step continues from it in FP32); the same operations otherwise.
+__device__ __forceinline__ ff2 ff_stage2_neg_w(const ff2 &vn, const ff2 &vs, const ff2 &vw,
+                                               const ff2 &ve, const ff2 &vc, const ff2 &u,
+                                               float2 cch, float2 ncch, float2 ccl,
+                                               float2 &neg_w) {
+    const float2 m4 = make_float2(-4.f, -4.f);
+    float2 ah, al, bh, bl, ch, cl;
+    two_sum2(vn.hi, vs.hi, ah, al);
+    two_sum2(vw.hi, ve.hi, bh, bl);
+    two_sum2(ah, bh, ch, cl);
+    const float2 dh = __ffma2_rn(m4, vc.hi, ch);
+    const float2 nbb = f2_sub(ch, dh);
+    const float2 dl = __fadd2_rn(f2_sub(ch, __fadd2_rn(dh, nbb)), __ffma2_rn(m4, vc.hi, nbb));
+    const float2 lo = __ffma2_rn(
+        m4, vc.lo,
+        __fadd2_rn(__fadd2_rn(__fadd2_rn(al, bl), __fadd2_rn(cl, dl)),
+                   __fadd2_rn(__fadd2_rn(vn.lo, vs.lo), __fadd2_rn(vw.lo, ve.lo))));
+    const float2 pn = __fmul2_rn(ncch, dh);
+    float2 e = __ffma2_rn(cch, dh, pn);
+    e = __ffma2_rn(cch, lo, e);
+    e = __ffma2_rn(ccl, dh, e);
+    const float2 sh = f2_sub(u.hi, pn);
+    const float2 nb2 = f2_sub(u.hi, sh);
+    const float2 sl = __fadd2_rn(f2_sub(u.hi, __fadd2_rn(sh, nb2)), f2_sub(nb2, pn));
+    neg_w = pn;
+    ff2 w;
+    w.hi = sh;
+    w.lo = __fadd2_rn(sl, __fadd2_rn(u.lo, e));
+    return w;
+}
+
+// s + q for two float-float values s and FP32 values q given negated
+// (nq = -q): TwoSum of the high parts, the low part added, FastTwoSum
+// renormalisation.  10 FP32 operations per point.
+__device__ __forceinline__ ff2 ff_add_neg_f32_2(const ff2 &s, float2 nq) {
+    const float2 h = f2_sub(s.hi, nq);
+    const float2 bb = f2_sub(h, s.hi);                 // the -q actually added
+    const float2 e = f2_sub(f2_sub(s.hi, f2_sub(h, bb)), __fadd2_rn(nq, bb));
+    const float2 lo = __fadd2_rn(e, s.lo);
+    ff2 w;
+    w.hi = __fadd2_rn(h, lo);
+    w.lo = f2_sub(lo, f2_sub(w.hi, h));
+    return w;
+}
+
 // FastTwoSum renormalisation of two float-float values (|lo| <= a few ulp(hi))
 __device__ __forceinline__ ff2 ff_renorm2(const ff2 &v) {
     ff2 w;

@@ -28,8 +28,8 @@ STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "nomem", -3: "cuda", -
 PIT_OP = {"heat1d": 1, "heat2d": 2, "advdiff2d": 3, "dense": 4}
 PIT_STEP = {"ie": 1, "rk4": 2}
 PIT_FP64, PIT_MIXED = 0, 1
-PIT_FF = 2
-PRECISION = {"fp64": PIT_FP64, "mixed": PIT_MIXED, "ff": PIT_FF}
+PIT_FF, PIT_SPLIT = 2, 3
+PRECISION = {"fp64": PIT_FP64, "mixed": PIT_MIXED, "ff": PIT_FF, "split": PIT_SPLIT}
 TOL_MODE = {"r0": 0, "rhs": 1}
 APPLY = {"F": 1, "Ginv": 2, "GinvF": 3, "residual": 4}
 X0 = {"coarse": 0, "zero": 1, "given": 2}
@@ -106,7 +106,7 @@ EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_cre
            "pit_problem_set_source"]
 
 TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4,
-                "fine_ff": 5}
+                "fine_ff": 5, "fine_split": 6}
 
 
 def lib_path() -> str:
