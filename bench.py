@@ -82,6 +82,12 @@ def parse(argv=None):
     args = _parser().parse_args(argv)
     if args.batch is None:
         args.batch = 8 if args.workload == "heat2d" else 1
+    if args.precision is None:
+        args.precision = "fp64" if args.workload == "heat1d" else "mixed"
+    if args.tol is None:
+        args.tol = 1e-10 if args.workload == "heat1d" else 1e-7
+    if args.tol_mode is None:
+        args.tol_mode = "r0" if args.workload == "heat1d" else "rhs"
     args.N_given = args.N is not None
     if args.N is None:
         args.N = 512
@@ -98,7 +104,7 @@ def _parser():
                     help="independent members solved together per step (default: 8 for "
                          "heat2d, 1 for advdiff and dense)")
     ap.add_argument("--workload", default="heat2d",
-                    choices=["heat2d", "dense", "advdiff", "serving"],
+                    choices=["heat2d", "heat1d", "dense", "advdiff", "serving"],
                     help="heat2d: 2D heat 128^2, N = 512 (the headline); dense: M = 1024, "
                          "N = 4096; advdiff: periodic 512^2, N = 256")
     ap.add_argument("--n", type=int, default=128)
@@ -112,8 +118,14 @@ def _parser():
                     help="serving: requests of the Poisson stream per step")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent solves")
-    ap.add_argument("--tol", type=float, default=1e-7,
-                    help="tolerance relative to ||G^-1 B|| (error target 1e-6)")
+    ap.add_argument("--tol", type=float, default=None,
+                    help="relative tolerance (default 1e-7 relative to ||G^-1 B||, error target "
+                         "1e-6; heat1d: 1e-10 relative to ||R^0||)")
+    ap.add_argument("--tol-mode", default=None, choices=["r0", "rhs"])
+    ap.add_argument("--precision", default=None, choices=["mixed", "fp64"],
+                    help="default: fp64 for heat1d (the plain method), mixed otherwise")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="heat2d: skip the short lines of the other configurations")
     ap.add_argument("--residual", default="split", choices=["split", "ff", "fp64"],
                     help="arithmetic of the true residual's fine propagations (heat2d: split RK4 "
                          "where 8 nu dt/h^2 <= 1/8; other operators: split means float-float)")
@@ -121,6 +133,9 @@ def _parser():
 
 
 def workload(args, rank, step=0):
+    if args.workload == "heat1d":
+        seed = replica_seed(inputs.SEED_HEAT1D, rank, step)
+        return inputs.heat1d(batch=args.batch, seed=seed)
     if args.workload == "dense":
         seed = replica_seed(inputs.SEED_DENSE, rank, step)
         return inputs.dense(batch=args.batch, seed=seed, tol=1e-6)
@@ -367,7 +382,7 @@ def bench_config(args, w, world):
     same workload it samples)."""
     cfg = {"workload": w.name, "batch_per_gpu": w.batch, "grid": [w.nx, w.ny],
            "N": w.N, "fine": list(w.fine), "coarse": list(w.coarse),
-           "precision": "mixed", "tol": args.tol, "tol_mode": "rhs",
+           "precision": args.precision, "tol": args.tol, "tol_mode": args.tol_mode,
            "inner_tol": args.inner_tol,
            "true_residual": {"split": "split RK4 (float-float first-order term, FP32 higher-order terms)",
                              "ff": "float-float", "fp64": "fp64"}[args.residual],
@@ -419,6 +434,18 @@ def roofline(w, timing, peaks, nsm):
                 "frac": flop / (avg_ms / 1e3) / 1e12 / peak, "traffic": None, "launch_ms": avg_ms,
                 "launches": calls, "peak_source": "derived: 4 FP64 flop/clk/SM x SMs x max SM clock"}
     point_steps = w.batch * w.N * w.fine[1] * w.M
+    if w.kind == "heat1d":
+        # one implicit-Euler step is a factored tridiagonal solve, two affine
+        # scans of about 2 FMA per point each; at M = 63, N = 16 a launch is a
+        # few microseconds of latency, far from any pipe's roofline
+        flop = point_steps * 8.0
+        peak = FP64_LANES_PER_SM * 2 * nsm * sm_max * 1e6 / 1e12
+        ach = flop / (avg_ms / 1e3) / 1e12
+        return {"bound": "latency", "kernel": "k_heat1d_fine<%s>" % ("double" if dom == "fine_fp64" else "float"),
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64, 8 flop per point-step)",
+                "frac": ach / peak, "traffic": None, "launch_ms": avg_ms, "launches": calls,
+                "note": "latency-bound: one CTA per slice, 63 points",
+                "peak_source": "derived: 4 FP64 flop/clk/SM x SMs x max SM clock"}
     lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
     peak = lanes * nsm * sm_max * 1e6 / 1e12
     if w.kind == "advdiff2d":
@@ -469,19 +496,88 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2203_10148_gb300 import pit
+    ctx = dict(torch=torch, pit=pit, rank=rank, world=world, local=local, dist=dist,
+               dev=torch.device("cuda", local))
+    line = measure_ours(args, ctx)
+    if rank == 0 and world == 1 and args.workload == "heat2d" and not args.no_configs:
+        line["configs"] = other_configs(args, ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
-    dev = torch.device("cuda", local)
+
+SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "rel_err_max",
+            "rel_err_lambda_N", "iterations", "refinements", "matvecs", "status", "gpu_launches",
+            "e2e", "fp64_path", "latency_s", "capacity_solves_per_s", "rel_err_max_sampled",
+            "completed", "failed", "max_running", "fine_slice_steps_per_s", "invalid")
+
+
+def _brief(line):
+    """The parts of a workload's line that the headline line carries."""
+    out = {k: line[k] for k in SUB_KEYS if k in line}
+    out["workload"] = line["config"]["workload"]
+    r = line.get("roofline") or {}
+    out["roofline"] = {k: r.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit", "frac",
+                                             "frac_executed", "launch_ms", "launches") if k in r}
+    if "breakdown" in line:
+        out["breakdown_share"] = {k: round(v["share"], 4) for k, v in line["breakdown"].items()
+                                  if v["calls"]}
+    if "serial_fine" in line:
+        out["serial_fine"] = {k: v for k, v in line["serial_fine"].items() if k != "note"}
+    return out
+
+
+def other_configs(args, ctx):
+    """Short lines of the other configurations after the headline's: the
+    plain FP64 1D heat method (M = 63, N = 16), periodic advection-diffusion
+    512^2 (N = 256), the dense-propagator mode (M = 1024, N = 4096) and
+    serving (a Poisson stream at 200 requests/s), each with its own timed
+    steps, accuracy against the FP64 path, end-to-end rate and roofline."""
+    out = {}
+    plans = [("heat1d_M63_N16_fp64", ["--workload", "heat1d", "--steps", "20", "--warmup", "3"]),
+             ("advdiff2d_512x512_N256", ["--workload", "advdiff", "--steps", "3", "--warmup", "3"]),
+             ("dense_M1024_N4096", ["--workload", "dense", "--steps", "3", "--warmup", "3"])]
+    for name, argv in plans:
+        sub = parse(argv + ["--residual", args.residual, "--no-cpu"] +
+                    (["--no-e2e"] if args.no_e2e else []))
+        t0 = time.perf_counter()
+        try:
+            out[name] = _brief(measure_ours(sub, ctx))
+        except Exception as e:   # a failed sub-line must not lose the headline
+            out[name] = {"failed": str(e)}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    sub = parse(["--workload", "serving", "--steps", "2", "--warmup", "1", "--requests", "64",
+                 "--no-cpu", "--residual", args.residual])
+    t0 = time.perf_counter()
+    try:
+        out["serving_poisson_200rps"] = _brief(measure_serving(sub, ctx))
+    except Exception as e:
+        out["serving_poisson_200rps"] = {"failed": str(e)}
+    out["serving_poisson_200rps"]["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def measure_ours(args, ctx):
+    """One workload through pit_bicgstab_solve: the timed steps, accuracy,
+    roofline, comparators and the end-to-end leg; returns rank 0's line."""
+    torch, pit = ctx["torch"], ctx["pit"]
+    rank, world, local, dist, dev = ctx["rank"], ctx["world"], ctx["local"], ctx["dist"], ctx["dev"]
+    fp64 = args.precision == "fp64"
     stream = torch.cuda.Stream(device=dev)
     w = workload(args, rank)
     shape = (w.batch, w.N + 1, w.M)
     K, W = args.steps, args.warmup
     # distinct initial values per step, resident on the device
     y0s = [torch.from_numpy(workload(args, rank, step=s).y0.copy()).to(dev) for s in range(K + W)]
-    prob = pit.Problem(w, "mixed")
+    prob = pit.Problem(w, args.precision)
     X = torch.zeros(shape, dtype=torch.float64, device=dev)
-    solve_kw = dict(tol=args.tol, tol_mode="rhs", max_iter=200, refine_max=8,
-                    inner_tol=args.inner_tol,
-                    residual_precision=args.residual)
+    if fp64:
+        solve_kw = dict(tol=args.tol, tol_mode=args.tol_mode, max_iter=500)
+    else:
+        solve_kw = dict(tol=args.tol, tol_mode=args.tol_mode, max_iter=200, refine_max=8,
+                        inner_tol=args.inner_tol, residual_precision=args.residual)
 
     def one(step):
         prob.set_y0(y0s[step])
@@ -530,17 +626,19 @@ def run_ours(args):
     # the no-PiT comparator: the same trajectory stepped slice after slice
     # in FP32 (one launch per slice for the whole batch), and its accuracy
     lam32 = torch.empty(shape, dtype=torch.float64, device=dev)
-    t_ser = time.perf_counter()
-    prob.serial_fine("mixed", out=lam32)
-    torch.cuda.synchronize()
-    t_ser32 = time.perf_counter() - t_ser
-    e32 = (((lam32 - lam).reshape(w.batch, -1).norm(dim=1)
-            / lam.reshape(w.batch, -1).norm(dim=1)).max().item())
+    t_ser32 = e32 = None
+    if not fp64:
+        t_ser = time.perf_counter()
+        prob.serial_fine("mixed", out=lam32)
+        torch.cuda.synchronize()
+        t_ser32 = time.perf_counter() - t_ser
+        e32 = (((lam32 - lam).reshape(w.batch, -1).norm(dim=1)
+                / lam.reshape(w.batch, -1).norm(dim=1)).max().item())
     # the no-PiT comparators that meet the 1e-6 bar: the serial trajectory in
     # float-float and in the split RK4 arithmetic (heat2d; float-float elsewhere)
     ser = {}
     for prec in ("ff", "split"):
-        if prec == "split" and w.kind != "heat2d":
+        if fp64 or (prec == "split" and w.kind != "heat2d"):
             continue
         torch.cuda.synchronize()
         t_ser = time.perf_counter()
@@ -565,7 +663,8 @@ def run_ours(args):
         line = {"metric": "PiT solves/s (rel err <= 1e-6 vs FP64 path)", "value": value,
                 "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32 fine / f64 krylov", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if fp64 else "f32 fine / f64 krylov",
+                "data": "synthetic",
                 "config": bench_config(args, w, world),
                 "fine_slice_steps_per_s": slice_steps / (total_ms / 1e3),
                 "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -618,7 +717,7 @@ def run_ours(args):
                            "d2h_bytes_per_step": w.batch * (w.N + 1) * w.M * 8}
 
     # the plain FP64 GPU path on the same workload, for comparison
-    if rank == 0 and not args.no_fp64_path:
+    if rank == 0 and not args.no_fp64_path and not fp64:
         # same workload and batch, every step in FP64 on the device
         w1 = workload(args, 0)
         p64 = pit.Problem(w1, "fp64")
@@ -646,11 +745,7 @@ def run_ours(args):
             line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1,
                                     "kind": "oracle", "sample": f"failed: {e}"}
     prob.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    return line
 
 
 # -------------------------------------------------------------- serving leg
@@ -686,6 +781,19 @@ def run_serving(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2203_10148_gb300 import pit
+    ctx = dict(torch=torch, pit=pit, rank=rank, world=world, local=local, dist=dist,
+               dev=torch.device("cuda", local))
+    line = measure_serving(args, ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def measure_serving(args, ctx):
+    torch, pit = ctx["torch"], ctx["pit"]
+    rank, world, local, dist = ctx["rank"], ctx["world"], ctx["local"], ctx["dist"]
 
     K, W = args.steps, args.warmup
     steps = serving_steps(args, rank, W + K + 1)
@@ -795,11 +903,7 @@ def run_serving(args):
                 line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1,
                                         "kind": "oracle", "sample": f"failed: {e}"}
     srv.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    return line
 
 
 def serving_cpu_baseline(ws, res, budget_s=20.0):

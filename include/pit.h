@@ -72,7 +72,8 @@ typedef int pit_status;
 #define PIT_MIXED           1   /* FP32 fine stepping (split-precision tensor-core GEMM for
                                    PIT_OP_DENSE), FP64 Krylov vectors and scalars, and
                                    iterative refinement on true residuals computed in
-                                   PIT_FF by default (PIT_FP64 on request; HEAT1D: FP64) */
+                                   PIT_SPLIT by default (PIT_FF or PIT_FP64 on request;
+                                   HEAT1D: FP64) */
 #define PIT_FF              2   /* float-float fine arithmetic: each value an unevaluated sum
                                    of two FP32 numbers (about 48 significant bits) on the
                                    FP32 pipe, FP64 inputs and outputs: stepping for HEAT2D
@@ -143,7 +144,7 @@ typedef struct {
                               iteration (PIT_FP64) or per refinement round (PIT_MIXED) */
     int history_len;
     int residual_precision; /* PIT_MIXED: arithmetic of the fine propagations inside the
-                               true residual, PIT_FF (default), PIT_SPLIT or PIT_FP64 */
+                               true residual, PIT_SPLIT (default), PIT_FF or PIT_FP64 */
     int tol_mode;          /* PIT_TOL_R0 (default) or PIT_TOL_RHS */
 } pit_solve_opts;
 
@@ -169,8 +170,9 @@ typedef struct {
 } pit_solve_info;
 
 /* Fills *opts with defaults: tol 1e-10, eps0 1e-8, max_iter 500, X0 coarse,
- * refine_max 8, inner_tol 1e-4, default stream, no history, float-float
- * true residuals, tolerance relative to ||R^0||. */
+ * refine_max 8, inner_tol 1e-4, default stream, no history, PIT_SPLIT true
+ * residuals (split RK4 for HEAT2D where its bound holds, float-float
+ * otherwise), tolerance relative to ||R^0||. */
 void pit_default_opts(pit_solve_opts *opts);
 
 /* Version string of the library. */
@@ -261,8 +263,9 @@ pit_status pit_serial_fine(pit_problem_t prob, int precision, double *Lam, int o
  * the solution on return.  info: array of batch entries (may be NULL).
  * PIT_FP64: every step in FP64 on the device.  PIT_MIXED: iterative
  * refinement: the true residual G^{-1}(B - F X) with the fine propagations
- * in opts.residual_precision (PIT_FF, float-float on the FP32 pipe, by
- * default; PIT_FP64 on request; HEAT1D always FP64), an FP32-fine /
+ * in opts.residual_precision (PIT_SPLIT by default: split RK4 for HEAT2D,
+ * float-float on the FP32 pipe elsewhere; PIT_FF or PIT_FP64 on request;
+ * HEAT1D always FP64), an FP32-fine /
  * FP64-Krylov inner solve of the correction to inner_tol, X += correction,
  * until the true preconditioned residual is <= tol * its reference
  * (opts.tol_mode).

@@ -765,7 +765,7 @@ void pit_default_opts(pit_solve_opts *o) {
     o->x0_mode = PIT_X0_COARSE;
     o->refine_max = 8;
     o->inner_tol = 1e-4;
-    o->residual_precision = PIT_FF;
+    o->residual_precision = PIT_SPLIT;
     o->tol_mode = PIT_TOL_R0;
 }
 

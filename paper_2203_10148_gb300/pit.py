@@ -224,7 +224,7 @@ def problem_desc(w, precision: int) -> Tuple[ProblemDesc, list]:
 
 def solve_opts(tol: float = 1e-10, eps0: float = 1e-8, max_iter: int = 500,
                x0: str = "coarse", refine_max: int = 8, inner_tol: float = 1e-4,
-               tol_mode: str = "r0", residual_precision: str = "ff") -> SolveOpts:
+               tol_mode: str = "r0", residual_precision: str = "split") -> SolveOpts:
     opts = SolveOpts()
     load().pit_default_opts(C.byref(opts))
     opts.tol, opts.restart_eps0, opts.max_iter = tol, eps0, max_iter
@@ -300,7 +300,7 @@ class Problem:
                        max_iter: int = 500, x0: str = "coarse", refine_max: int = 8,
                        inner_tol: float = 1e-4, history_len: int = 0, stream=None,
                        raise_on_status: bool = False, tol_mode: str = "r0",
-                       residual_precision: str = "ff"):
+                       residual_precision: str = "split"):
         """pit_bicgstab_solve; returns (X, [info dict per member])."""
         lib = load()
         opts = solve_opts(tol, eps0, max_iter, x0, refine_max, inner_tol, tol_mode,

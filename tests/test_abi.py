@@ -43,6 +43,7 @@ def test_version_and_defaults(lib):
     o = pit.SolveOpts()
     lib.pit_default_opts(C.byref(o))
     assert o.tol == 1e-10 and o.restart_eps0 == 1e-8 and o.x0_mode == 0 and o.refine_max >= 1
+    assert o.residual_precision == pit.PIT_SPLIT
 
 
 def _desc(pit, y0, **kw):
