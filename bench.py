@@ -156,25 +156,32 @@ def load_peaks():
         return None
 
 
-def _fine_kernel_source(text):
-    """The 2D heat fine kernel's own code in heat2d.cu: its body (from its
-    template line to the closing brace at column 0) and its launch code (shared
-    memory size, tile shapes, launchers: from fine_smem to make_args)."""
+def _fine_kernel_source(text, kernel="k_heat2d_fine"):
+    """A 2D heat fine kernel's own code in heat2d.cu: its body (from its
+    template line to the closing brace at column 0) and its launch code
+    (k_heat2d_fine: from fine_smem to the split kernel's launch code;
+    k_heat2d_split: from split_smem to make_args)."""
+    if kernel == "k_heat2d_split":
+        a = text.index("// ------------------------------------------- split RK4 (true residuals)")
+        b = text.index("\n}\n", text.index("k_heat2d_split(Heat2dArgs a)", a)) + 3
+        c = text.index("size_t split_smem(")
+        d = text.index("Heat2dArgs make_args(")
+        return text[a:b] + text[c:d]
     a = text.index("template <class V, int RX, int RY, bool CL>")
     b = text.index("\n}\n", a) + 3
     c = text.index("size_t fine_smem(")
-    d = text.index("Heat2dArgs make_args(")
+    d = text.index("// Split RK4 (PIT_SPLIT): one CTA")
     return text[a:b] + text[c:d]
 
 
-def src_hash(paths):
+def src_hash(paths, kernel="k_heat2d_fine"):
     """Hash of the sources a committed ncu figure depends on: the whole of
-    every file, except heat2d.cu, of which only the fine kernel's code counts."""
+    every file, except heat2d.cu, of which only the named kernel's code counts."""
     h = hashlib.sha256()
     for p in paths:
         text = open(p, "r").read()
         if os.path.basename(p) == "heat2d.cu":
-            text = _fine_kernel_source(text)
+            text = _fine_kernel_source(text, kernel)
         h.update(text.encode())
     return h.hexdigest()[:16]
 
@@ -185,7 +192,8 @@ def traffic_for(kernel, units):
     try:
         t = json.load(open(TRAFFIC))
         e = t.get(kernel)
-        if e and e.get("source_sha") == src_hash(FINE_SRCS):
+        base = "k_heat2d_split" if kernel == "k_heat2d_split" else "k_heat2d_fine"
+        if e and e.get("source_sha") == src_hash(FINE_SRCS, base):
             return e["dram_bytes"] * units / e["units"]
     except Exception:
         pass

@@ -7,6 +7,8 @@ import json
 import os
 import shutil
 
+import pytest
+
 import bench
 
 UNITS = 8 * 512 * 128 * 128
@@ -28,13 +30,33 @@ def _traffic_file(tmp_path, sha):
     return str(f)
 
 
-def test_committed_figure_follows_the_hash():
-    t = json.load(open(bench.TRAFFIC))["k_heat2d_fine<ff>"]
-    got = bench.traffic_for("k_heat2d_fine<ff>", UNITS)
-    if bench.src_hash(bench.FINE_SRCS) == t["source_sha"]:
+@pytest.mark.parametrize("kernel,base", [("k_heat2d_split", "k_heat2d_split"),
+                                         ("k_heat2d_fine<float>", "k_heat2d_fine")])
+def test_committed_figure_follows_the_hash(kernel, base):
+    t = json.load(open(bench.TRAFFIC))[kernel]
+    got = bench.traffic_for(kernel, UNITS)
+    if bench.src_hash(bench.FINE_SRCS, base) == t["source_sha"]:
         assert got == t["dram_bytes"] * UNITS / t["units"]
     else:
         assert got is None
+
+
+def test_the_split_kernel_has_its_own_hash(tmp_path, monkeypatch):
+    """An edit to the split kernel drops its figure and keeps the FP32 one."""
+    srcs = _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "FINE_SRCS", srcs)
+    t = {"k_heat2d_split": {"dram_bytes": 10, "units": 1, "source_sha": bench.src_hash(srcs, "k_heat2d_split")},
+         "k_heat2d_fine<float>": {"dram_bytes": 10, "units": 1, "source_sha": bench.src_hash(srcs)}}
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(t))
+    monkeypatch.setattr(bench, "TRAFFIC", str(f))
+    assert bench.traffic_for("k_heat2d_split", 2) == 20
+    heat2d = next(p for p in srcs if p.endswith("heat2d.cu"))
+    text = open(heat2d).read()
+    marker = "k_heat2d_split(Heat2dArgs a) {"
+    open(heat2d, "w").write(text.replace(marker, marker + "\n    // edited", 1))
+    assert bench.traffic_for("k_heat2d_split", 2) is None
+    assert bench.traffic_for("k_heat2d_fine<float>", 2) == 20
 
 
 def test_edits_outside_the_fine_kernel_keep_the_figure(tmp_path, monkeypatch):
