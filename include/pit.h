@@ -219,7 +219,13 @@ size_t pit_last_error(char *buf, size_t n);
  *                          a in 0..3, float-float b in {0, 2}) instead of the
  *                          autotuner's choice (bit-identical results);
  *   PIT_AUTOTUNE=0         untuned shapes take the built-in variant;
- *   PIT_AUTOTUNE_CACHE=f   persist the autotuner's choices in file f.
+ *   PIT_AUTOTUNE_CACHE=f   persist the autotuner's choices in file f;
+ *   PIT_SPIN_LIMIT=k       polls of each bounded wait of the ADVDIFF2D coarse
+ *                          sweep (neighbouring bands' progress flags) before
+ *                          the call reports PIT_E_TIMEOUT (default 2^26; a
+ *                          small k exercises the timeout path: the sweep's
+ *                          CTAs all return, the call fails with
+ *                          PIT_E_TIMEOUT and the context stays usable).
  * Errors: PIT_E_INVALID (bad sizes, including N + 1 > 65535 or batch > 65535:
  * the vector kernels put one grid row per block and one grid layer per
  * member), PIT_E_NONFINITE (non-finite values), PIT_E_NOMEM, PIT_E_CUDA.
@@ -239,8 +245,11 @@ pit_status pit_problem_shape(pit_problem_t prob, int *M, int *N, int *batch);
  * precision selects the fine arithmetic (PIT_FP64, PIT_MIXED = FP32 fine
  * stepping from FP64 inputs, or PIT_FF = float-float arithmetic, about 48
  * significant bits on the FP32 pipe: stepping for PIT_OP_HEAT2D and
- * PIT_OP_ADVDIFF2D, a compensated product for PIT_OP_DENSE with M a
- * multiple of 64; PIT_FF means PIT_FP64 otherwise).  G^{-1} runs
+ * PIT_OP_ADVDIFF2D, a compensated product for PIT_OP_DENSE; PIT_SPLIT is
+ * split RK4 for PIT_OP_HEAT2D and PIT_FF elsewhere; HEAT1D runs PIT_FF and
+ * PIT_SPLIT in FP64).  Every dense product runs on the library's kernels for
+ * any M (tcgen05 split TF32 for PIT_MIXED, rows padded to 128; float-float
+ * for PIT_FF, padded to 64; FP64 tiles for PIT_FP64).  G^{-1} runs
  * in reduced precision for PIT_MIXED (2D heat and 1D heat: split-TF32 sine
  * transforms on the tensor cores with float-float running sums in the sine
  * basis; advection-diffusion and dense: FP32) and in FP64 otherwise.

@@ -566,13 +566,13 @@ pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
 constexpr int SWA_THREADS = 256;
 constexpr int SWA_PPT = 8;                     // points per thread: bands of <= 2048 points
 constexpr int SWA_KMAX = 64;     // Chebyshev steps per coarse solve, at most
-constexpr long long SWA_SPIN = 1LL << 26;
 
 template <class T>
 struct AdSweepArgs {
     const double *q;
     double *z;
     int n, N, batch, K, R;     // grid, slices, members, Chebyshev steps, rows per CTA
+    long long spin;            // polls of a neighbour's flag before PIT_E_TIMEOUT
     size_t blen;
     double dT, nud;
     double inv_theta;          // first direction d_0 = D^{-1} r_0 / theta
@@ -624,7 +624,7 @@ __device__ bool exchange(const AdSweepArgs<T> &a, T *wb, const T (&val)[SWA_PPT]
         long long spins = 0;
         while (*(volatile unsigned *)(a.flags + up) < step + 1 ||
                *(volatile unsigned *)(a.flags + down) < step + 1) {
-            if (++spins > SWA_SPIN || *(volatile int *)a.err) {
+            if (++spins > a.spin || *(volatile int *)a.err) {
                 atomicExch(a.err, PIT_E_TIMEOUT);
                 *ok = 0;
                 break;
@@ -760,6 +760,7 @@ pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax,
     a.N = p->N;
     a.batch = p->batch;
     a.K = p->adv_K;
+    a.spin = p->adv_spin;
     a.R = R;
     a.blen = p->blen;
     a.dT = p->dT / p->coarse_steps;
@@ -837,6 +838,12 @@ pit_status advdiff_setup(Problem *p) {
         for (size_t i = 0; i < M && c32; ++i)
             c32 = (double)(float)vx[i] == vx[i] && (double)(float)vy[i] == vy[i];
         p->adv_coef32 = c32 ? 1 : 0;
+        // PIT_SPIN_LIMIT: polls of each bounded wait of the sweep (tests of the timeout path)
+        if (const char *sl = getenv("PIT_SPIN_LIMIT")) {
+            char *end = nullptr;
+            const long long v = strtoll(sl, &end, 10);
+            if (end != sl && v >= 0) p->adv_spin = v;
+        }
         double rho = 0.0;
         for (size_t i = 0; i < M; ++i) {
             const double D = 1.0 + dtc * (4.0 * nud + fabs(vx[i]) + fabs(vy[i]));

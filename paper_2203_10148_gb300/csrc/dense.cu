@@ -58,13 +58,24 @@ __global__ void k_copy_f32(const double *X, float *Y, size_t n) {
         Y[i] = d2f_rn(X[i]);
 }
 
-// x = hi + lo, hi = RN32(x), lo = RN32(x - hi): the float-float form of x
-__global__ void k_split_ff(const double *X, float *hi, float *lo, size_t n) {
+// x = hi + lo, hi = RN32(x), lo = RN32(x - hi): the float-float form of x,
+// for an rows_out x Mp array from the rows_src x M row-major X (zero where
+// r >= rows_src or c >= M: the padding of the float-float product).
+__global__ void k_split_ff(const double *X, float *hi, float *lo, int rows_src, int rows_out, int M,
+                           int Mp) {
+    const size_t n = (size_t)rows_out * Mp;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        const float h = d2f_rn(X[i]);
-        hi[i] = h;
-        lo[i] = d2f_rn(X[i] - f2d(h));
+        const size_t r = i / Mp, c = i % Mp;
+        if (r < (size_t)rows_src && c < (size_t)M) {
+            const double x = X[r * M + c];
+            const float h = d2f_rn(x);
+            hi[i] = h;
+            lo[i] = d2f_rn(x - f2d(h));
+        } else {
+            hi[i] = 0.f;
+            lo[i] = 0.f;
+        }
     }
 }
 
@@ -83,13 +94,19 @@ __global__ void k_split_ff(const double *X, float *hi, float *lo, size_t n) {
 // one 16-byte load.
 constexpr int FG_B = 64, FG_K = 16, FG_T = 256;
 
+// rows of the float-float operands, padded to the product's tile width
+int pad_ff(int M) { return (M + FG_B - 1) / FG_B * FG_B; }
+
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
+// Xh, Xl: the block vector's rows (batch x (N+1) rows of Mp values, zero
+// beyond M); Ph, Pl: Phi as Mp x Mp (zero beyond M); C: rows n < N of every
+// member, M columns.  Mp is M rounded up to FG_B.
 __global__ void __launch_bounds__(FG_T) k_gemm_ff(const float *__restrict__ Xh, const float *__restrict__ Xl,
                                                   const float *__restrict__ Ph, const float *__restrict__ Pl,
-                                                  double *__restrict__ C, int M, int N, size_t blen,
+                                                  double *__restrict__ C, int M, int Mp, int N,
                                                   size_t cstride, int rows, const MemberState *st) {
     __shared__ __align__(16) float xs_h[FG_K][FG_B], xs_l[FG_K][FG_B];
     __shared__ __align__(16) float ps_h[FG_K][FG_B], ps_l[FG_K][FG_B];
@@ -102,8 +119,8 @@ __global__ void __launch_bounds__(FG_T) k_gemm_ff(const float *__restrict__ Xh, 
     const bool grow_ok = gl < rows;
     const int gmem = grow_ok ? gl / N : 0, gsl = grow_ok ? gl % N : 0;
     const bool live = grow_ok && (st == nullptr || (st[gmem].active && !st[gmem].skip && !st[gmem].half));
-    const size_t xrow = (size_t)gmem * blen + (size_t)gsl * M;
-    const size_t prow = (size_t)(c0 + lr) * M;
+    const size_t xrow = ((size_t)gmem * (N + 1) + gsl) * Mp;
+    const size_t prow = (size_t)(c0 + lr) * Mp;
     float2 s2[4][2], c2[4][2];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -112,7 +129,7 @@ __global__ void __launch_bounds__(FG_T) k_gemm_ff(const float *__restrict__ Xh, 
             s2[i][j] = make_float2(0.f, 0.f);
             c2[i][j] = make_float2(0.f, 0.f);
         }
-    for (int k0 = 0; k0 < M; k0 += FG_K) {
+    for (int k0 = 0; k0 < Mp; k0 += FG_K) {
         {
             float4 xh = make_float4(0.f, 0.f, 0.f, 0.f), xl = xh;
             if (live) {
@@ -165,11 +182,104 @@ __global__ void __launch_bounds__(FG_T) k_gemm_ff(const float *__restrict__ Xh, 
         if (g >= rows) continue;
         const int mbr = g / N, sl = g % N;
         if (st && !(st[mbr].active && !st[mbr].skip && !st[mbr].half)) continue;
-        double *crow = C + (size_t)mbr * cstride + (size_t)sl * M + c0 + tx * 4;
+        const int cc = c0 + tx * 4;
+        double *crow = C + (size_t)mbr * cstride + (size_t)sl * M + cc;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            crow[2 * j] = f2d(s2[i][j].x) + f2d(c2[i][j].x);
-            crow[2 * j + 1] = f2d(s2[i][j].y) + f2d(c2[i][j].y);
+            if (cc + 2 * j < M) crow[2 * j] = f2d(s2[i][j].x) + f2d(c2[i][j].x);
+            if (cc + 2 * j + 1 < M) crow[2 * j + 1] = f2d(s2[i][j].y) + f2d(c2[i][j].y);
+        }
+    }
+}
+
+// ----------------------------------------------------- FP64 product
+// C[g][c] = sum_k X[g][k] Phi[c][k] in FP64 for the rows g = (member,
+// slice < N) of the block vector (the FP64 path's fine batch).  One 64 x 64
+// output tile per CTA of 256 threads (4 x 4 outputs each), K in steps of 16
+// staged in shared memory; bound by GB300's FP64 pipe (2 FMA per clock per
+// SM), so plain scalar loads with bounds checks serve any M.
+constexpr int DG_B = 64, DG_K = 16, DG_T = 256;
+
+__global__ void __launch_bounds__(DG_T) k_gemm_f64(const double *__restrict__ X,
+                                                   const double *__restrict__ P,
+                                                   double *__restrict__ C, int M, int N, size_t blen,
+                                                   size_t cstride, int rows, const MemberState *st) {
+    __shared__ __align__(16) double xs[DG_K][DG_B], ps[DG_K][DG_B];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int g0 = blockIdx.y * DG_B, c0 = blockIdx.x * DG_B;
+    const int lr = tid >> 2, lk = (tid & 3) * 4;
+    const int gl = g0 + lr;
+    const bool grow_ok = gl < rows;
+    const int gmem = grow_ok ? gl / N : 0, gsl = grow_ok ? gl % N : 0;
+    const bool live = grow_ok && (st == nullptr || (st[gmem].active && !st[gmem].skip && !st[gmem].half));
+    const double *xr = X + (size_t)gmem * blen + (size_t)gsl * M;
+    const int pc = c0 + lr;
+    const double *pr = P + (size_t)(pc < M ? pc : 0) * M;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < M; k0 += DG_K) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = k0 + lk + e;
+            xs[lk + e][lr] = (live && k < M) ? xr[k] : 0.0;
+            ps[lk + e][lr] = (pc < M && k < M) ? pr[k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < DG_K; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = xs[k][ty * 4 + i];
+                b[i] = ps[k][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int g = g0 + ty * 4 + i;
+        if (g >= rows) continue;
+        const int mbr = g / N, sl = g % N;
+        if (st && !(st[mbr].active && !st[mbr].skip && !st[mbr].half)) continue;
+        double *crow = C + (size_t)mbr * cstride + (size_t)sl * M;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + tx * 4 + j;
+            if (c < M) crow[c] = acc[i][j];
+        }
+    }
+}
+
+// out_b[i] = add_b[i] + sum_k Mat[i][k] in_b[k] for every member b (FP64, one
+// warp per row i, the row's products summed lane-strided then by a fixed
+// shuffle tree): one step of the sequential sweep z_n = q_n + G z_{n-1}
+// (add = out, which holds q_n) or one slice of the serial fine trajectory
+// (add = null).  Mat (M x M, row-major) stays in L2 across the steps.
+__global__ void __launch_bounds__(256) k_gemv_f64(const double *__restrict__ Mat, const double *in,
+                                                  double *out, const double *add, size_t stride,
+                                                  int M, int batch) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= M) return;
+    const double *row = Mat + (size_t)i * M;
+    for (int b = 0; b < batch; ++b) {
+        const double *v = in + (size_t)b * stride;
+        double sum = 0.0;
+        for (int k = lane; k < M; k += 32) sum = fma(row[k], v[k], sum);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) {
+            const size_t j = (size_t)b * stride + i;
+            out[j] = (add ? add[j] : 0.0) + sum;
         }
     }
 }
@@ -862,12 +972,16 @@ pit_status dense_setup(Problem *p) {
     }
     // FP32 copies for the mixed path; Phi also as float-float (hi, lo) for
     // the residual product
-    PIT_TRY(p->PhiF_hi.ensure(mm2 * sizeof(float)));
-    PIT_TRY(p->PhiF_lo.ensure(mm2 * sizeof(float)));
+    {
+        const int Mp = pad_ff(M);
+        const size_t mp2 = (size_t)Mp * Mp;
+        PIT_TRY(p->PhiF_hi.ensure(mp2 * sizeof(float)));
+        PIT_TRY(p->PhiF_lo.ensure(mp2 * sizeof(float)));
+        k_split_ff<<<1024, 256, 0, s>>>(p->PhiF64.as<double>(), p->PhiF_hi.as<float>(),
+                                        p->PhiF_lo.as<float>(), M, Mp, M, Mp);
+        PIT_LAUNCH_CHECK();
+    }
     PIT_TRY(p->G32.ensure(mm2 * sizeof(float)));
-    k_split_ff<<<blocks, 256, 0, s>>>(p->PhiF64.as<double>(), p->PhiF_hi.as<float>(),
-                                      p->PhiF_lo.as<float>(), mm2);
-    PIT_LAUNCH_CHECK();
     k_copy_f32<<<blocks, 256, 0, s>>>(G, p->G32.as<float>(), mm2);
     PIT_LAUNCH_CHECK();
     // TF32 splits of Phi for the tensor-core product
@@ -878,51 +992,34 @@ pit_status dense_setup(Problem *p) {
     return PIT_OK;
 }
 
-// C (batch x N x M, row n = Phi x_n for n < N) in FP64 or FP32.
+// C (batch x N x M, row n = Phi x_n for n < N, FP64): the float-float
+// compensated product (PIT_FF; PIT_MIXED too when the tensor-core product is
+// unavailable) or the FP64 product, both hand-written kernels.
 static pit_status dense_product(Problem *p, const double *x, int prec, const MemberState *st,
                                 cudaStream_t s) {
     const int M = p->M, N = p->N;
-    cublasHandle_t h = handle(p);
-    PIT_CUBLAS(cublasSetStream(h, s));
     const size_t cstride = (size_t)N * M;
-    if (prec == PIT_MIXED) {
-        // FP32 copy of x, then FP32 product
-        PIT_TRY(p->q32.ensure(p->vlen * sizeof(float)));
-        PIT_TRY(p->dense_scratch.ensure((size_t)p->batch * cstride * sizeof(float)));
-        int blocks;
-        grid_for(p->vlen, blocks);
-        k_copy_f32<<<blocks, 256, 0, s>>>(x, p->q32.as<float>(), p->vlen);
-        PIT_LAUNCH_CHECK();
-        const float one = 1.f, zero = 0.f;
-        PIT_CUBLAS(cublasSgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, M, N, M, &one,
-                                             p->PhiF_hi.as<float>(), M, 0, p->q32.as<float>(), M,
-                                             (long long)p->blen, &zero,
-                                             p->dense_scratch.as<float>(), M, (long long)cstride,
-                                             p->batch));
-        return PIT_OK;
-    }
+    const int rows = p->batch * N;
     PIT_TRY(p->dense_scratch.ensure((size_t)p->batch * cstride * sizeof(double)));
-    if (prec == PIT_FF && M % FG_B == 0) {
-        // float-float product: X split once, then the compensated GEMM
-        PIT_TRY(p->q32.ensure(2 * p->vlen * sizeof(float)));
-        float *xh = p->q32.as<float>(), *xl = xh + p->vlen;
-        int blocks;
-        grid_for(p->vlen, blocks);
-        k_split_ff<<<blocks, 256, 0, s>>>(x, xh, xl, p->vlen);
+    if (prec != PIT_FP64) {
+        // X split once into padded float-float rows, then the compensated GEMM
+        const int Mp = pad_ff(M), R = p->batch * (N + 1);
+        const size_t n = (size_t)R * Mp;
+        PIT_TRY(p->q32.ensure(2 * n * sizeof(float)));
+        float *xh = p->q32.as<float>(), *xl = xh + n;
+        k_split_ff<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(x, xh, xl, R, R, M,
+                                                                                     Mp);
         PIT_LAUNCH_CHECK();
-        const int rows = p->batch * N;
-        dim3 grid((unsigned)(M / FG_B), (unsigned)((rows + FG_B - 1) / FG_B));
+        dim3 grid((unsigned)(Mp / FG_B), (unsigned)((rows + FG_B - 1) / FG_B));
         k_gemm_ff<<<grid, FG_T, 0, s>>>(xh, xl, p->PhiF_hi.as<float>(), p->PhiF_lo.as<float>(),
-                                        p->dense_scratch.as<double>(), M, N, p->blen, cstride,
-                                        rows, st);
+                                        p->dense_scratch.as<double>(), M, Mp, N, cstride, rows, st);
         PIT_LAUNCH_CHECK();
         return PIT_OK;
     }
-    const double one = 1.0, zero = 0.0;
-    PIT_CUBLAS(cublasDgemmStridedBatched(h, CUBLAS_OP_T, CUBLAS_OP_N, M, N, M, &one,
-                                         p->PhiF64.as<double>(), M, 0, x, M, (long long)p->blen,
-                                         &zero, p->dense_scratch.as<double>(), M,
-                                         (long long)cstride, p->batch));
+    dim3 grid((unsigned)((M + DG_B - 1) / DG_B), (unsigned)((rows + DG_B - 1) / DG_B));
+    k_gemm_f64<<<grid, DG_T, 0, s>>>(x, p->PhiF64.as<double>(), p->dense_scratch.as<double>(), M, N,
+                                     p->blen, cstride, rows, st);
+    PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
 
@@ -934,14 +1031,9 @@ pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int p
     int blocks;
     grid_for(p->blen, blocks);
     const size_t cstride = (size_t)p->N * p->M;
-    if (prec == PIT_MIXED)
-        k_dense_rows<float><<<dim3(blocks, p->batch), 256, 0, s>>>(
-            x, p->dense_scratch.as<float>(), y, p->y0.as<double>(), p->M, p->N, p->blen, cstride,
-            mode, st);
-    else
-        k_dense_rows<double><<<dim3(blocks, p->batch), 256, 0, s>>>(
-            x, p->dense_scratch.as<double>(), y, p->y0.as<double>(), p->M, p->N, p->blen, cstride,
-            mode, st);
+    k_dense_rows<double><<<dim3(blocks, p->batch), 256, 0, s>>>(
+        x, p->dense_scratch.as<double>(), y, p->y0.as<double>(), p->M, p->N, p->blen, cstride,
+        mode, st);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
@@ -950,11 +1042,8 @@ pit_status dense_fine_one(Problem *p, const double *x, double *y, int prec, cuda
     // y (block n) = Phi x (block n-1) for every member; FP64
     (void)prec;
     const int M = p->M;
-    cublasHandle_t h = handle(p);
-    PIT_CUBLAS(cublasSetStream(h, s));
-    const double one = 1.0, zero = 0.0;
-    PIT_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, p->batch, M, &one, p->PhiF64.as<double>(),
-                           M, x, (int)p->blen, &zero, y, (int)p->blen));
+    k_gemv_f64<<<(M + 7) / 8, 256, 0, s>>>(p->PhiF64.as<double>(), x, y, nullptr, p->blen, M, p->batch);
+    PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
 
@@ -1064,17 +1153,17 @@ pit_status dense_sweep(Problem *p, const double *q, double *z, int prec, const M
                                          1, st, s, &done));
     }
     if (done) return PIT_OK;
-    // fallback: one FP64 product per slice
+    // grids too large for the persistent sweep (M above about 1000 in FP64):
+    // one FP64 matrix-vector step per slice, z_n = q_n + G z_{n-1}
     const int M = p->M;
-    cublasHandle_t h = handle(p);
-    PIT_CUBLAS(cublasSetStream(h, s));
     if (q != z)
         PIT_CUDA(cudaMemcpyAsync(z, q, p->vlen * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    const double one = 1.0;
-    for (int n = 1; n <= p->N; ++n)
-        PIT_CUBLAS(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, M, p->batch, M, &one,
-                               p->G64.as<double>(), M, z + (size_t)(n - 1) * M, (int)p->blen, &one,
-                               z + (size_t)n * M, (int)p->blen));
+    for (int n = 1; n <= p->N; ++n) {
+        double *zn = z + (size_t)n * M;
+        k_gemv_f64<<<(M + 7) / 8, 256, 0, s>>>(p->G64.as<double>(), z + (size_t)(n - 1) * M, zn, zn,
+                                               p->blen, M, p->batch);
+        PIT_LAUNCH_CHECK();
+    }
     return PIT_OK;
 }
 

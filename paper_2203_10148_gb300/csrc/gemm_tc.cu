@@ -6,6 +6,10 @@
 // term is below FP32 resolution).  The epilogue writes the block-operator
 // rows of eq. (4): y_{n+1} = x_{n+1} - C[r] (or the residual form).
 //
+// Any M: the TF32 parts of X and Phi are stored with rows of Mp = M rounded
+// up to 128 (zero columns, and for Phi zero rows, beyond M), K runs over Mp
+// and the epilogue writes the first M columns only.
+//
 // Kernel structure: one 128 x 128 output tile per CTA, K in 32-element
 // (128-byte) stages, 3-stage ring in shared memory filled by TMA
 // (cp.async.bulk.tensor, 128-byte swizzle) and drained by tcgen05.mma
@@ -49,7 +53,7 @@ struct TcEpilogue {
     double *y;            // FP64 rows (or null)
     float *y32;           // FP32 rows (or null): q = fl32(x_{n+1}) - C
     const double *y0;
-    int N, M, batch, mode;
+    int N, M, batch, mode;   // M: columns written (the product runs over the padded width)
     size_t blen;
     const MemberState *st;
 };
@@ -147,17 +151,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int cchunk = 0; cchunk < TC_BN / 32; ++cchunk) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cchunk * 32), v);
-            if (!live) continue;
             const int c0 = n0 + cchunk * 32;
+            if (!live || c0 >= ep.M) continue;
+            const int cn = min(32, ep.M - c0);      // columns of the padding are not written
             const double *xn = ep.x + mb + (size_t)(n + 1) * ep.M + c0;
             if (ep.y32) {
                 float *yo = ep.y32 + mb + (size_t)(n + 1) * ep.M + c0;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) yo[i] = d2f_rn(xn[i]) - v[i];
+                for (int i = 0; i < 32; ++i)
+                    if (i < cn) yo[i] = d2f_rn(xn[i]) - v[i];
             } else {
                 double *yo = ep.y + mb + (size_t)(n + 1) * ep.M + c0;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
+                    if (i >= cn) continue;
                     const double f = f2d(v[i]);
                     yo[i] = (ep.mode == FINE_APPLY) ? xn[i] - f : f - xn[i];
                 }
@@ -168,12 +175,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (ep.y32) {
                     float *yo = ep.y32 + mb + c0;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) yo[i] = d2f_rn(x0[i]);
+                    for (int i = 0; i < 32; ++i)
+                        if (i < cn) yo[i] = d2f_rn(x0[i]);
                 } else {
                     double *yo = ep.y + mb + c0;
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
-                        yo[i] = (ep.mode == FINE_APPLY) ? x0[i] : ep.y0[(size_t)b * ep.M + c0 + i] - x0[i];
+                        if (i < cn)
+                            yo[i] = (ep.mode == FINE_APPLY) ? x0[i] : ep.y0[(size_t)b * ep.M + c0 + i] - x0[i];
                 }
             }
         }
@@ -192,11 +201,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-// hi = TF32 rounding of fl32(x), lo = TF32 rounding of the FP32 remainder.
-__global__ void k_split_tf32(const double *x, float *hi, float *lo, size_t n) {
+// hi = TF32 rounding of fl32(x), lo = TF32 rounding of the FP32 remainder,
+// for an rows_out x Mp array from the rows_src x M row-major x (zero where
+// r >= rows_src or c >= M).
+__global__ void k_split_tf32(const double *x, float *hi, float *lo, int rows_src, int rows_out, int M,
+                             int Mp) {
+    const size_t n = (size_t)rows_out * Mp;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        const float v = d2f_rn(x[i]);
+        const size_t row = i / Mp, col = i % Mp;
+        const float v = (row < (size_t)rows_src && col < (size_t)M) ? d2f_rn(x[row * M + col]) : 0.f;
         uint32_t h, l;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
         const float r = v - __uint_as_float(h);
@@ -208,17 +222,20 @@ __global__ void k_split_tf32(const double *x, float *hi, float *lo, size_t n) {
 
 }  // namespace
 
+static int padded(int M) { return (M + TC_BN - 1) / TC_BN * TC_BN; }
+
 bool dense_tc_supported(const Problem *p) {
-    // tiles of 128 states; K in 32-element stages; 16-byte aligned rows
-    return p->M % TC_BN == 0 && p->M % TC_BK == 0 && tc_encode_fn() != nullptr;
+    (void)p;   // any M (padded to 128 columns); needs the tensor-map encoder
+    return tc_encode_fn() != nullptr;
 }
 
 pit_status dense_tc_split_phi(Problem *p) {
-    const size_t mm2 = (size_t)p->M * p->M;
+    const int Mp = padded(p->M);
+    const size_t mm2 = (size_t)Mp * Mp;
     PIT_TRY(p->PhiTh.ensure(mm2 * sizeof(float)));
     PIT_TRY(p->PhiTl.ensure(mm2 * sizeof(float)));
     k_split_tf32<<<1024, 256, 0, p->stream>>>(p->PhiF64.as<double>(), p->PhiTh.as<float>(),
-                                              p->PhiTl.as<float>(), mm2);
+                                              p->PhiTl.as<float>(), p->M, Mp, p->M, Mp);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
@@ -227,22 +244,23 @@ pit_status dense_tc_split_phi(Problem *p) {
 // or y32 (FP32 rows for the mixed sweep).
 pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, int mode,
                           const MemberState *st, cudaStream_t s) {
-    const int M = p->M;
+    const int M = p->M, Mp = padded(M);
     const int R = p->batch * (p->N + 1);
-    const size_t n = (size_t)R * M;
+    const size_t n = (size_t)R * Mp;
     PIT_TRY(p->tc_split.ensure(2 * n * sizeof(float)));
     float *xh = p->tc_split.as<float>(), *xl = xh + n;
-    k_split_tf32<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(x, xh, xl, n);
+    k_split_tf32<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(x, xh, xl, R, R, M,
+                                                                                    Mp);
     PIT_LAUNCH_CHECK();
     CUtensorMap tAh, tAl, tBh, tBl;
-    PIT_TRY(make_map(&tAh, xh, R, M));
-    PIT_TRY(make_map(&tAl, xl, R, M));
-    PIT_TRY(make_map(&tBh, p->PhiTh.as<float>(), M, M));
-    PIT_TRY(make_map(&tBl, p->PhiTl.as<float>(), M, M));
+    PIT_TRY(make_map(&tAh, xh, R, Mp));
+    PIT_TRY(make_map(&tAl, xl, R, Mp));
+    PIT_TRY(make_map(&tBh, p->PhiTh.as<float>(), Mp, Mp));
+    PIT_TRY(make_map(&tBl, p->PhiTl.as<float>(), Mp, Mp));
     TcEpilogue ep{x, y, y32, p->y0.as<double>(), p->N, M, p->batch, mode, p->blen, st};
     PIT_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    dim3 grid((R + TC_BM - 1) / TC_BM, M / TC_BN);
-    k_gemm_tf32x3<<<grid, TC_THREADS, TC_SMEM, s>>>(tAh, tAl, tBh, tBl, M, R, ep,
+    dim3 grid((R + TC_BM - 1) / TC_BM, Mp / TC_BN);
+    k_gemm_tf32x3<<<grid, TC_THREADS, TC_SMEM, s>>>(tAh, tAl, tBh, tBl, Mp, R, ep,
                                                     p->errword.as<int>());
     PIT_LAUNCH_CHECK();
     return PIT_OK;

@@ -172,6 +172,7 @@ struct Problem {
     DevBuf vxff, vyff;            // advdiff coefficients as float-float (hi, lo) pairs
     DevBuf adv_scratch;
     int adv_K = 8;                // Chebyshev steps of the coarse IE step
+    long long adv_spin = 1LL << 26;   // polls of each bounded wait of the advdiff sweep
     int adv_coef32 = 0;           // every coefficient v / h is an FP32 value (float-float lo parts zero)
     double adv_inv_theta = 1.0, adv_c1[64] = {}, adv_c2[64] = {};   // Chebyshev coefficients
 

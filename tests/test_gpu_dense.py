@@ -64,11 +64,15 @@ def test_dense_fine_product_fp32(case):
 
 @pytest.mark.parametrize("case", [dict(M=64, N=8, T=1.0, fine_steps=37),
                                   dict(M=128, N=5, T=2.0, fine_steps=20, batch=2),
-                                  dict(M=256, N=70, T=10.0 * 70 / 4096, fine_steps=200)])
+                                  dict(M=256, N=70, T=10.0 * 70 / 4096, fine_steps=200),
+                                  dict(M=1, N=3, T=1.0, fine_steps=4),
+                                  dict(M=100, N=5, T=2.0, fine_steps=20, batch=2),
+                                  dict(M=257, N=6, T=10.0 * 6 / 4096, fine_steps=200)])
 def test_dense_float_float_product(case):
     """The compensated float-float product (Dot2 form on (hi, lo) pairs) used
     by the mixed path's true residual: within 1e-11 of the FP64 oracle, on
-    row counts that are not multiples of the 64-row tile."""
+    row counts that are not multiples of the 64-row tile and any M (operand
+    rows padded to 64)."""
     from paper_2203_10148_gb300 import pit
     w = inputs.dense(**case)
     X = _rand(w, 5)
@@ -152,10 +156,12 @@ def test_dense_mixed_sweep_full_size():
     assert _rel(got, ref) < 1e-4
 
 
-@pytest.mark.parametrize("M,N,batch", [(128, 16, 1), (128, 16, 2), (256, 300, 1), (384, 5, 3)])
+@pytest.mark.parametrize("M,N,batch", [(128, 16, 1), (128, 16, 2), (256, 300, 1), (384, 5, 3),
+                                       (1, 4, 1), (24, 9, 2), (100, 33, 1), (257, 7, 2)])
 def test_dense_tensor_core_product(M, N, batch):
-    """The tcgen05 3xTF32 product (M a multiple of 128): block-operator rows
-    against the oracle to FP32 accuracy, including partial row tiles."""
+    """The tcgen05 3xTF32 product for any M (rows padded to 128 columns, the
+    padding never written): block-operator rows against the oracle to FP32
+    accuracy, including partial row tiles."""
     from paper_2203_10148_gb300 import pit
     w = inputs.dense(M=M, N=N, T=N * 10.0 / 4096, fine_steps=200, batch=batch)
     X = _rand(w, 9)
@@ -166,3 +172,33 @@ def test_dense_tensor_core_product(M, N, batch):
     assert _rel(got, ref) < 2e-5
     ref_res = _oracle(w, "residual", X)
     assert _rel(res, ref_res) < 2e-5
+
+
+def test_dense_large_grid_sweep_and_serial_trajectory_fp64():
+    """M = 1100 is beyond the persistent sweep's shared memory in FP64: the
+    sweep runs one matrix-vector kernel per slice, like the serial fine
+    trajectory; both against the oracle."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=1100, N=3, T=3 * 10.0 / 4096, fine_steps=20, precision="fp64", batch=2)
+    X = _rand(w, 13)
+    with pit.Problem(w, "fp64") as p:
+        got = p.apply("Ginv", X)
+        lam = p.serial_fine("fp64")
+    assert _rel(got, _oracle(w, "Ginv", X)) < 1e-12
+    for b in range(w.batch):
+        ref = OracleProblem.from_workload(w, member=b).serial_fine()
+        assert _rel(lam[b], ref) < 1e-12
+
+
+@pytest.mark.parametrize("M", [100, 200])
+def test_dense_mixed_solve_any_M_within_1e6(M):
+    """Mixed solves with M not a multiple of the tensor-core tile (tcgen05
+    inner products, float-float true residuals): within 1e-6 of the serial
+    FP64 trajectory."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=M, N=32, T=32 * 10.0 / 4096, fine_steps=200)
+    lam = OracleProblem.from_workload(w).serial_fine()
+    with pit.Problem(w, "mixed") as p:
+        X, info = p.bicgstab_solve(tol=1e-7, tol_mode="rhs", inner_tol=1e-5)
+    assert info[0]["status"] == 0
+    assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
