@@ -79,6 +79,13 @@ typedef int pit_status;
                                    FP32 pipe, FP64 inputs and outputs: stepping for HEAT2D
                                    and ADVDIFF2D, a compensated product for DENSE; HEAT1D
                                    treats it as PIT_FP64 */
+#define PIT_MIXED_BF16      4   /* problem precision only: PIT_MIXED with the dense fine
+                                   product split in BF16 instead of TF32 ("3xBF16": x = xh + xl
+                                   and Phi = ph + pl with BF16 parts, xh ph + xh pl + xl ph on
+                                   tcgen05 kind::f16 with FP32 accumulation; about 2^-16
+                                   relative per product against 2^-21 for split TF32, twice
+                                   the MMA rate and half the operand bytes); refinement keeps
+                                   results within the tolerance.  Other operators: PIT_MIXED */
 #define PIT_SPLIT           3   /* split RK4 (HEAT2D; other operators treat it as PIT_FF):
                                    each step u + Z u + Z^2 u/2 + Z^3 u/6 + Z^4 u/24 (Z = dt L)
                                    takes the first-order term Z u in float-float and the
@@ -129,7 +136,7 @@ typedef struct {
     int N;                 /* number of time slices, >= 1 */
     pit_stepper_desc fine;
     pit_stepper_desc coarse;
-    int precision;         /* PIT_FP64 or PIT_MIXED */
+    int precision;         /* PIT_FP64, PIT_MIXED or PIT_MIXED_BF16 */
 } pit_problem_desc;
 
 typedef struct {

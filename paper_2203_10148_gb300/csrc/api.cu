@@ -800,7 +800,7 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
     if (op.nx < 1 || op.ny < 1 || d->N < 1 || d->batch < 1 || !(d->T > 0.0) ||
         d->fine.steps < 1 || d->coarse.steps < 1 || !d->y0 ||
         d->coarse.inner < 0 || d->coarse.inner > 64 ||
-        (d->precision != PIT_FP64 && d->precision != PIT_MIXED)) {
+        (d->precision != PIT_FP64 && d->precision != PIT_MIXED && d->precision != PIT_MIXED_BF16)) {
         set_error("pit_problem_create: invalid sizes, steps, T, precision or null y0");
         return PIT_E_INVALID;
     }
@@ -852,7 +852,9 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
     p->coarse_kind = d->coarse.kind;
     p->coarse_steps = d->coarse.steps;
     p->coarse_inner = d->coarse.inner;
-    p->precision = d->precision;
+    // PIT_MIXED_BF16 is the mixed path with the dense product split in BF16
+    p->precision = d->precision == PIT_MIXED_BF16 ? PIT_MIXED : d->precision;
+    p->dense_bf16 = d->precision == PIT_MIXED_BF16 && op.kind == PIT_OP_DENSE;
     p->blen = (size_t)(p->N + 1) * M;
     p->vlen = p->blen * p->batch;
     {
@@ -935,7 +937,8 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32, &p->GLL32, &p->xtc_S,
-                      &p->errword, &p->loopctl, &p->PhiTh, &p->PhiTl, &p->tc_split};
+                      &p->errword, &p->loopctl, &p->PhiTh, &p->PhiTl, &p->tc_split,
+                      &p->PhiBh, &p->PhiBl};
     for (IterGraph &g : p->igraph) iter_graph_drop(p, g);
     for (IterGraph &g : p->lgraph) iter_graph_drop(p, g);
     for (DevBuf *b : bufs) b->release();

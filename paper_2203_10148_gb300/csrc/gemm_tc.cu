@@ -10,6 +10,12 @@
 // up to 128 (zero columns, and for Phi zero rows, beyond M), K runs over Mp
 // and the epilogue writes the first M columns only.
 //
+// The same kernel runs the split in BF16 ("3xBF16", kind::f16 with BF16 A
+// and B): X = Xh + Xl and Phi = Ph + Pl with BF16 parts, the same three
+// products, K in 64-element (128-byte) stages; about 2^-16 relative per
+// product against about 2^-21 for split TF32, at twice the MMA rate and half
+// the operand bytes.
+//
 // Kernel structure: one 128 x 128 output tile per CTA, K in 32-element
 // (128-byte) stages, 3-stage ring in shared memory filled by TMA
 // (cp.async.bulk.tensor, 128-byte swizzle) and drained by tcgen05.mma
@@ -19,6 +25,7 @@
 // the TMA thread, the MMA thread and the tensor core; every wait is
 // bounded and reports PIT_E_TIMEOUT through the problem's error word.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
@@ -33,8 +40,10 @@ constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_STAGES = 3, TC_THREADS = 
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;                  // 16 KB per operand tile
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;                 // Ah, Al, Bh, Bl
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;  // + alignment + barriers
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128.
+// Instruction descriptors: D = F32, A = B = TF32 (or BF16), both K-major, M = 128, N = 128.
 constexpr uint32_t kIdesc = tc_idesc_tf32(TC_BM, TC_BN);
+constexpr uint32_t kIdescBf = tc_idesc_bf16(TC_BM, TC_BN);
+constexpr int TC_BK_BF = 64;   // BF16 elements per 128-byte stage row
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum) {
     tc_mma_tf32(tmem, a, b, kIdesc, accum);
@@ -44,8 +53,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
     return tc_mbar_wait(bar, parity, err);
 }
 
-pit_status make_map(CUtensorMap *tm, const float *ptr, int rows, int cols) {
-    return tc_make_map(tm, ptr, rows, cols, TC_BK, TC_BM);
+pit_status make_map(CUtensorMap *tm, const void *ptr, int rows, int cols, bool bf16) {
+    return tc_make_map(tm, ptr, rows, cols, bf16 ? TC_BK_BF : TC_BK, TC_BM, bf16);
 }
 
 struct TcEpilogue {
@@ -58,6 +67,7 @@ struct TcEpilogue {
     const MemberState *st;
 };
 
+template <bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                   const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -72,7 +82,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-    const int KB = K / TC_BK;
+    constexpr int BKE = BF ? TC_BK_BF : TC_BK;   // K elements per stage
+    const int KB = K / BKE;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
@@ -105,10 +116,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!mbar_wait(&empty[s], ph ^ 1u, err)) break;
             unsigned char *st = base + s * TC_STAGE_BYTES;
             mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-            tma_load_2d(st, &tmAh, kb * TC_BK, m0, &full[s]);
-            tma_load_2d(st + TC_TILE_BYTES, &tmAl, kb * TC_BK, m0, &full[s]);
-            tma_load_2d(st + 2 * TC_TILE_BYTES, &tmBh, kb * TC_BK, n0, &full[s]);
-            tma_load_2d(st + 3 * TC_TILE_BYTES, &tmBl, kb * TC_BK, n0, &full[s]);
+            tma_load_2d(st, &tmAh, kb * BKE, m0, &full[s]);
+            tma_load_2d(st + TC_TILE_BYTES, &tmAl, kb * BKE, m0, &full[s]);
+            tma_load_2d(st + 2 * TC_TILE_BYTES, &tmBh, kb * BKE, n0, &full[s]);
+            tma_load_2d(st + 3 * TC_TILE_BYTES, &tmBl, kb * BKE, n0, &full[s]);
             last_kb[s] = kb;
         }
     } else if (warp == 1 && lane == 0) {
@@ -126,11 +137,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t ah = smem_desc(st), al = smem_desc(st + TC_TILE_BYTES);
             const uint64_t bh = smem_desc(st + 2 * TC_TILE_BYTES), bl = smem_desc(st + 3 * TC_TILE_BYTES);
 #pragma unroll
-            for (int j = 0; j < TC_BK / 8; ++j) {
-                const uint64_t adv = (uint64_t)(j * 32) >> 4;   // 8 TF32 = 32 bytes along K
-                mma_tf32(tmem, ah + adv, bh + adv, (kb > 0 || j > 0) ? 1u : 0u);
-                mma_tf32(tmem, ah + adv, bl + adv, 1u);
-                mma_tf32(tmem, al + adv, bh + adv, 1u);
+            for (int j = 0; j < 4; ++j) {
+                // 8 TF32 or 16 BF16 = 32 bytes along K per instruction
+                const uint64_t adv = (uint64_t)(j * 32) >> 4;
+                if constexpr (BF) {
+                    tc_mma_f16(tmem, ah + adv, bh + adv, kIdescBf, (kb > 0 || j > 0) ? 1u : 0u);
+                    tc_mma_f16(tmem, ah + adv, bl + adv, kIdescBf, 1u);
+                    tc_mma_f16(tmem, al + adv, bh + adv, kIdescBf, 1u);
+                } else {
+                    mma_tf32(tmem, ah + adv, bh + adv, (kb > 0 || j > 0) ? 1u : 0u);
+                    mma_tf32(tmem, ah + adv, bl + adv, 1u);
+                    mma_tf32(tmem, al + adv, bh + adv, 1u);
+                }
             }
             mma_commit(&empty[s]);            // stage free once these products finish
         }
@@ -220,6 +238,21 @@ __global__ void k_split_tf32(const double *x, float *hi, float *lo, int rows_src
     }
 }
 
+// hi = BF16 rounding of fl32(x), lo = BF16 rounding of the FP32 remainder,
+// padded like k_split_tf32.
+__global__ void k_split_bf16(const double *x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, int rows_src,
+                             int rows_out, int M, int Mp) {
+    const size_t n = (size_t)rows_out * Mp;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / Mp, col = i % Mp;
+        const float v = (row < (size_t)rows_src && col < (size_t)M) ? d2f_rn(x[row * M + col]) : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i] = h;
+        lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
 }  // namespace
 
 static int padded(int M) { return (M + TC_BN - 1) / TC_BN * TC_BN; }
@@ -237,31 +270,51 @@ pit_status dense_tc_split_phi(Problem *p) {
     k_split_tf32<<<1024, 256, 0, p->stream>>>(p->PhiF64.as<double>(), p->PhiTh.as<float>(),
                                               p->PhiTl.as<float>(), p->M, Mp, p->M, Mp);
     PIT_LAUNCH_CHECK();
+    if (p->dense_bf16) {
+        PIT_TRY(p->PhiBh.ensure(mm2 * sizeof(__nv_bfloat16)));
+        PIT_TRY(p->PhiBl.ensure(mm2 * sizeof(__nv_bfloat16)));
+        k_split_bf16<<<1024, 256, 0, p->stream>>>(p->PhiF64.as<double>(), p->PhiBh.as<__nv_bfloat16>(),
+                                                  p->PhiBl.as<__nv_bfloat16>(), p->M, Mp, p->M, Mp);
+        PIT_LAUNCH_CHECK();
+    }
     return PIT_OK;
 }
 
 // Block-operator rows of the dense fine batch on the tensor cores: y (FP64)
-// or y32 (FP32 rows for the mixed sweep).
+// or y32 (FP32 rows for the mixed sweep); split BF16 when the problem was
+// created with PIT_MIXED_BF16, split TF32 otherwise.
 pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, int mode,
                           const MemberState *st, cudaStream_t s) {
     const int M = p->M, Mp = padded(M);
     const int R = p->batch * (p->N + 1);
     const size_t n = (size_t)R * Mp;
-    PIT_TRY(p->tc_split.ensure(2 * n * sizeof(float)));
-    float *xh = p->tc_split.as<float>(), *xl = xh + n;
-    k_split_tf32<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(x, xh, xl, R, R, M,
-                                                                                    Mp);
-    PIT_LAUNCH_CHECK();
+    const bool bf = p->dense_bf16;
+    const unsigned sgrid = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
     CUtensorMap tAh, tAl, tBh, tBl;
-    PIT_TRY(make_map(&tAh, xh, R, Mp));
-    PIT_TRY(make_map(&tAl, xl, R, Mp));
-    PIT_TRY(make_map(&tBh, p->PhiTh.as<float>(), Mp, Mp));
-    PIT_TRY(make_map(&tBl, p->PhiTl.as<float>(), Mp, Mp));
+    if (bf) {
+        PIT_TRY(p->tc_split.ensure(2 * n * sizeof(__nv_bfloat16)));
+        __nv_bfloat16 *xh = p->tc_split.as<__nv_bfloat16>(), *xl = xh + n;
+        k_split_bf16<<<sgrid, 256, 0, s>>>(x, xh, xl, R, R, M, Mp);
+        PIT_LAUNCH_CHECK();
+        PIT_TRY(make_map(&tAh, xh, R, Mp, true));
+        PIT_TRY(make_map(&tAl, xl, R, Mp, true));
+        PIT_TRY(make_map(&tBh, p->PhiBh.ptr, Mp, Mp, true));
+        PIT_TRY(make_map(&tBl, p->PhiBl.ptr, Mp, Mp, true));
+    } else {
+        PIT_TRY(p->tc_split.ensure(2 * n * sizeof(float)));
+        float *xh = p->tc_split.as<float>(), *xl = xh + n;
+        k_split_tf32<<<sgrid, 256, 0, s>>>(x, xh, xl, R, R, M, Mp);
+        PIT_LAUNCH_CHECK();
+        PIT_TRY(make_map(&tAh, xh, R, Mp, false));
+        PIT_TRY(make_map(&tAl, xl, R, Mp, false));
+        PIT_TRY(make_map(&tBh, p->PhiTh.as<float>(), Mp, Mp, false));
+        PIT_TRY(make_map(&tBl, p->PhiTl.as<float>(), Mp, Mp, false));
+    }
     TcEpilogue ep{x, y, y32, p->y0.as<double>(), p->N, M, p->batch, mode, p->blen, st};
-    PIT_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    auto kern = bf ? k_gemm_tf32x3<true> : k_gemm_tf32x3<false>;
+    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     dim3 grid((R + TC_BM - 1) / TC_BM, Mp / TC_BN);
-    k_gemm_tf32x3<<<grid, TC_THREADS, TC_SMEM, s>>>(tAh, tAl, tBh, tBl, Mp, R, ep,
-                                                    p->errword.as<int>());
+    kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tAh, tAl, tBh, tBl, Mp, R, ep, p->errword.as<int>());
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }

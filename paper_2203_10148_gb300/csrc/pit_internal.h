@@ -192,6 +192,8 @@ struct Problem {
     DevBuf errword;               // device-side error word of bounded waits (0 = none)
     DevBuf PhiTh, PhiTl, tc_split;  // TF32 splits of Phi and of the input block vector
     bool use_tc = false;          // dense FP32-class product on the tensor cores
+    bool dense_bf16 = false;      // ... in split BF16 (PIT_MIXED_BF16) instead of split TF32
+    DevBuf PhiBh, PhiBl;          // BF16 splits of Phi
 
     // Krylov workspace
     DevBuf X, R, Rt, P, S, D, K, W;

@@ -91,6 +91,22 @@ constexpr uint32_t tc_idesc_tf32(int m, int n) {
            ((uint32_t)(m >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with BF16 operands: D = F32, A = B =
+// BF16 (the same type on both sides), both K-major.
+constexpr uint32_t tc_idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+// D (+)= A B^T, kind::f16 (here BF16 x BF16, K = 16 per instruction)
+__device__ __forceinline__ void tc_mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                           uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
 __device__ __forceinline__ void tc_mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                             uint32_t accum) {
     asm volatile(
@@ -156,20 +172,22 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tc_encode_fn() {
     return fn;
 }
 
-// 2D row-major FP32 matrix rows x cols (cols contiguous), box box_x x box_y,
+// 2D row-major FP32 (or BF16) matrix rows x cols (cols contiguous), box box_x x box_y,
 // 128-byte swizzle; elements outside the matrix read as zero.
-inline pit_status tc_make_map(CUtensorMap *tm, const float *ptr, int rows, int cols, int box_x,
-                              int box_y) {
+inline pit_status tc_make_map(CUtensorMap *tm, const void *ptr, int rows, int cols, int box_x,
+                              int box_y, bool bf16 = false) {
     auto fn = tc_encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available");
         return PIT_E_CUDA;
     }
+    const size_t esz = bf16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
     cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(ptr), dims, strides,
+    CUresult r = fn(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void *>(ptr), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {

@@ -28,8 +28,9 @@ STATUS_NAMES = {0: "ok", 1: "pending", -1: "invalid", -2: "nomem", -3: "cuda", -
 PIT_OP = {"heat1d": 1, "heat2d": 2, "advdiff2d": 3, "dense": 4}
 PIT_STEP = {"ie": 1, "rk4": 2}
 PIT_FP64, PIT_MIXED = 0, 1
-PIT_FF, PIT_SPLIT = 2, 3
-PRECISION = {"fp64": PIT_FP64, "mixed": PIT_MIXED, "ff": PIT_FF, "split": PIT_SPLIT}
+PIT_FF, PIT_SPLIT, PIT_MIXED_BF16 = 2, 3, 4
+PRECISION = {"fp64": PIT_FP64, "mixed": PIT_MIXED, "ff": PIT_FF, "split": PIT_SPLIT,
+             "mixed_bf16": PIT_MIXED_BF16}
 TOL_MODE = {"r0": 0, "rhs": 1}
 APPLY = {"F": 1, "Ginv": 2, "GinvF": 3, "residual": 4}
 X0 = {"coarse": 0, "zero": 1, "given": 2}
@@ -243,6 +244,8 @@ class Problem:
         self.w = w
         self.precision = PRECISION[precision or w.precision]
         desc, self._keep = problem_desc(w, self.precision)
+        if self.precision == PIT_MIXED_BF16:     # a problem setting; applies run as mixed
+            self.precision = PIT_MIXED
         h = C.c_void_p()
         check(lib.pit_problem_create(C.byref(desc), C.byref(h)))
         self.handle = h

@@ -202,3 +202,35 @@ def test_dense_mixed_solve_any_M_within_1e6(M):
         X, info = p.bicgstab_solve(tol=1e-7, tol_mode="rhs", inner_tol=1e-5)
     assert info[0]["status"] == 0
     assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
+
+
+@pytest.mark.parametrize("M,N,batch", [(128, 16, 1), (100, 33, 2), (257, 7, 1)])
+def test_dense_bf16x3_product(M, N, batch):
+    """PIT_MIXED_BF16: the product split in BF16 on tcgen05 kind::f16 (both
+    operands BF16, FP32 accumulation).  Each operand keeps about 17 bits
+    (x - xh - xl <= 2^-18 |x|, the dropped xl pl term about 2^-18), so the
+    rows agree with the oracle to 1e-4 of their maximum, and less closely
+    than the split-TF32 product of the same problem."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=M, N=N, T=N * 10.0 / 4096, fine_steps=200, batch=batch)
+    X = _rand(w, 19)
+    ref = _oracle(w, "F", X)
+    with pit.Problem(w, "mixed_bf16") as p:
+        gbf = p.apply("F", X, precision="mixed")
+    with pit.Problem(w, "mixed") as p:
+        gtf = p.apply("F", X, precision="mixed")
+    ebf, etf = _rel(gbf, ref), _rel(gtf, ref)
+    assert ebf < 1e-4
+    assert etf < ebf
+
+
+def test_dense_bf16x3_mixed_solve_within_1e6():
+    """Refinement with float-float true residuals carries the BF16-split
+    inner solves to the same 1e-6 bar."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=128, N=64, T=64 * 10.0 / 4096, fine_steps=200)
+    lam = OracleProblem.from_workload(w).serial_fine()
+    with pit.Problem(w, "mixed_bf16") as p:
+        X, info = p.bicgstab_solve(tol=1e-7, tol_mode="rhs", inner_tol=1e-5)
+    assert info[0]["status"] == 0
+    assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
