@@ -29,8 +29,10 @@
 // linear preconditioner leaves the solution of eq. (4) unchanged, and only
 // the iteration count depends on it.  The sweep runs in one cooperative
 // launch: each CTA owns a band of rows, and exchanges its edge rows with the
-// two neighbouring bands through global memory with per-CTA progress flags
-// (bounded waits).
+// two neighbouring bands through global memory as tagged words: every 8-byte
+// word carries a 32-bit part of a value and the exchange's sequence number,
+// so that a reader polls the data itself (bounded waits) and one L2 round
+// trip delivers both the value and the news that it is there.
 #include <cooperative_groups.h>
 #include <math.h>
 #include <stdlib.h>
@@ -578,8 +580,7 @@ struct AdSweepArgs {
     double inv_theta;          // first direction d_0 = D^{-1} r_0 / theta
     double c1[SWA_KMAX], c2[SWA_KMAX];   // d_{k+1} = c1_k d_k + c2_k D^{-1} r_{k+1}
     const T *ax, *ay;
-    T *halo;                   // [2][G][2][n]: top / bottom rows per band, by step parity
-    unsigned *flags;           // [G]: halo exchanges completed
+    unsigned long long *halo;  // [2 parity][G][2 top/bottom][n][W] tagged words, W = sizeof(T)/4
     int *err;
     const MemberState *st;
 };
@@ -599,48 +600,132 @@ __device__ __forceinline__ T apply_A(const T *wb, int n, int rl, int i, T ax, T 
     return fma(-dT, Lw, vc);
 }
 
+// A 32-bit part of a halo value with its exchange's sequence number in the
+// other half of one 8-byte word: a single-copy-atomic store and load at GPU
+// scope, so a reader that sees the number also sees the value.
+__device__ __forceinline__ void st_tagged(unsigned long long *p, unsigned v, unsigned tag) {
+    const unsigned long long w = ((unsigned long long)tag << 32) | v;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long *p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+
+template <class T> struct Words;
+template <> struct Words<float> {
+    static constexpr int W = 1;
+    __device__ static void split(float v, unsigned (&u)[1]) { u[0] = __float_as_uint(v); }
+    __device__ static float join(const unsigned (&u)[1]) { return __uint_as_float(u[0]); }
+};
+template <> struct Words<double> {
+    static constexpr int W = 2;
+    __device__ static void split(double v, unsigned (&u)[2]) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        u[0] = (unsigned)b;
+        u[1] = (unsigned)(b >> 32);
+    }
+    __device__ static double join(const unsigned (&u)[2]) {
+        return __longlong_as_double((long long)(((unsigned long long)u[1] << 32) | u[0]));
+    }
+};
+
 // Puts this thread's points of a vector into the band buffer and the band's
-// edge rows into the global halo slot, then waits (bounded) until both
-// neighbouring bands have published the same exchange and copies their edge
-// rows into the halo rows of the band buffer.
+// edge rows, tagged with the exchange number, into the band's global halo
+// slot; then reads the neighbouring bands' edge rows of the same exchange
+// into the halo rows of the band buffer, each word polled until it carries
+// the exchange number (bounded: PIT_E_TIMEOUT after a.spin polls, or at once
+// when another CTA reported an error), and synchronises the CTA.  The slots
+// alternate by the exchange number's parity: a band rewrites a slot only two
+// exchanges later, after both neighbours have published the exchange in
+// between, which they can only do after reading this one.
 template <class T>
 __device__ bool exchange(const AdSweepArgs<T> &a, T *wb, const T (&val)[SWA_PPT], unsigned &step,
                          int g, int G, int up, int down, int *ok) {
+    using Wd = Words<T>;
+    constexpr int W = Wd::W;
     const int n = a.n, band = a.R * n;
-    T *hslot = a.halo + ((size_t)((step & 1u) * G + g) * 2) * n;
+    const unsigned tag = step + 1;
+    unsigned long long *hslot = a.halo + ((size_t)((step & 1u) * G + g) * 2) * n * W;
 #pragma unroll
     for (int e = 0; e < SWA_PPT; ++e) {
         const int p = threadIdx.x + e * SWA_THREADS;
         if (p < band) {
             wb[n + p] = val[e];
-            if (p < n) __stcg(hslot + p, val[e]);
-            if (p >= band - n) __stcg(hslot + n + (p - (band - n)), val[e]);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(a.flags + g, step + 1);
-        long long spins = 0;
-        while (*(volatile unsigned *)(a.flags + up) < step + 1 ||
-               *(volatile unsigned *)(a.flags + down) < step + 1) {
-            if (++spins > a.spin || *(volatile int *)a.err) {
-                atomicExch(a.err, PIT_E_TIMEOUT);
-                *ok = 0;
-                break;
+            unsigned u[W];
+            Wd::split(val[e], u);
+            if (p < n) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) st_tagged(hslot + (size_t)p * W + w, u[w], tag);
+            }
+            if (p >= band - n) {
+                const size_t q = (size_t)n + (p - (band - n));
+#pragma unroll
+                for (int w = 0; w < W; ++w) st_tagged(hslot + q * W + w, u[w], tag);
             }
         }
-        __threadfence();
+    }
+    const unsigned long long *hu = a.halo + ((size_t)((step & 1u) * G + up) * 2) * n * W;
+    const unsigned long long *hd = a.halo + ((size_t)((step & 1u) * G + down) * 2) * n * W;
+    // this thread's halo words: columns i = tid + k * SWA_THREADS (n <= 512), the
+    // row above (the upper band's bottom row) and below (the lower band's top
+    // row); all loads issued first, then the late ones polled again
+    constexpr int KI = 512 / SWA_THREADS;
+    const unsigned long long *src[KI][2];
+    unsigned long long x[KI][2][W];
+#pragma unroll
+    for (int k = 0; k < KI; ++k) {
+        const int i = threadIdx.x + k * SWA_THREADS;
+        src[k][0] = hu + ((size_t)n + (i < n ? i : 0)) * W;
+        src[k][1] = hd + (size_t)(i < n ? i : 0) * W;
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+            for (int w = 0; w < W; ++w) x[k][sd][w] = (i < n) ? ld_tagged(src[k][sd] + w) : 0ull;
+    }
+    bool good = true;
+    long long spins = 0;
+    for (;;) {
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            if (threadIdx.x + k * SWA_THREADS >= n) continue;
+#pragma unroll
+            for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    if ((unsigned)(x[k][sd][w] >> 32) != tag) {
+                        all = false;
+                        x[k][sd][w] = ld_tagged(src[k][sd] + w);
+                    }
+        }
+        if (all) break;
+        if (++spins > a.spin || ((spins & 255) == 0 && *(volatile int *)a.err)) {
+            atomicExch(a.err, PIT_E_TIMEOUT);
+            good = false;
+            break;
+        }
+    }
+    if (good) {
+#pragma unroll
+        for (int k = 0; k < KI; ++k) {
+            const int i = threadIdx.x + k * SWA_THREADS;
+            if (i >= n) continue;
+#pragma unroll
+            for (int sd = 0; sd < 2; ++sd) {
+                unsigned u[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) u[w] = (unsigned)x[k][sd][w];
+                wb[sd == 0 ? (size_t)i : (size_t)(a.R + 1) * n + i] = Wd::join(u);
+            }
+        }
+    } else {
+        *ok = 0;
     }
     __syncthreads();
     if (!*ok) return false;
-    const T *hu = a.halo + ((size_t)((step & 1u) * G + up) * 2) * n;
-    const T *hd = a.halo + ((size_t)((step & 1u) * G + down) * 2) * n;
-    for (int i = threadIdx.x; i < n; i += SWA_THREADS) {
-        wb[i] = __ldcg(hu + n + i);
-        wb[(size_t)(a.R + 1) * n + i] = __ldcg(hd + i);
-    }
-    __syncthreads();
     ++step;
     return true;
 }
@@ -748,11 +833,11 @@ pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax,
         set_error("advdiff sweep: bands cannot all be resident");
         return PIT_E_UNSUPPORTED;
     }
-    const size_t hbytes = (size_t)2 * G * 2 * n * sizeof(T);
-    PIT_TRY(p->adv_scratch.ensure(hbytes + (size_t)G * sizeof(unsigned) + 256));
-    T *halo = p->adv_scratch.as<T>();
-    unsigned *flags = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(p->adv_scratch.ptr) + hbytes);
-    PIT_CUDA(cudaMemsetAsync(flags, 0, (size_t)G * sizeof(unsigned), s));
+    // tagged halo words; zero tags never match an exchange number (they start at 1)
+    const size_t hbytes = (size_t)2 * G * 2 * n * (sizeof(T) / 4) * sizeof(unsigned long long);
+    PIT_TRY(p->adv_scratch.ensure(hbytes + 256));
+    unsigned long long *halo = p->adv_scratch.as<unsigned long long>();
+    PIT_CUDA(cudaMemsetAsync(halo, 0, hbytes, s));
     AdSweepArgs<T> a{};
     a.q = q;
     a.z = z;
@@ -773,7 +858,6 @@ pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax,
     a.ax = ax;
     a.ay = ay;
     a.halo = halo;
-    a.flags = flags;
     a.err = p->errword.as<int>();
     a.st = st;
     void *args[] = {&a};
