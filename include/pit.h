@@ -227,6 +227,13 @@ size_t pit_last_error(char *buf, size_t n);
  *                          autotuner's choice (bit-identical results);
  *   PIT_AUTOTUNE=0         untuned shapes take the built-in variant;
  *   PIT_AUTOTUNE_CACHE=f   persist the autotuner's choices in file f;
+ *   PIT_KRYLOV_CLUSTERS=1  the Krylov kernels reduce a block's 2..8 chunks
+ *                          of 2048 values in a thread-block cluster
+ *                          (distributed shared memory, one partial per
+ *                          block) instead of storing one partial per chunk
+ *                          (the same results bit for bit; measured 6% slower
+ *                          on the Krylov kernels of the 128^2 workload, so
+ *                          off by default);
  *   PIT_SPIN_LIMIT=k       polls of each bounded wait of the ADVDIFF2D coarse
  *                          sweep (neighbouring bands' progress flags) before
  *                          the call reports PIT_E_TIMEOUT (default 2^26; a

@@ -863,6 +863,9 @@ pit_status problem_create(const pit_problem_desc *d, cudaStream_t ext_stream,
         // PIT_GRAPH_LOOP=k: k iterations per launch of the loop graph (0: off)
         const char *l = getenv("PIT_GRAPH_LOOP");
         if (l && l[0]) p->loop_chunk = std::max(0, std::min(4096, atoi(l)));
+        // PIT_KRYLOV_CLUSTERS=1: a block's chunk sums reduced in a cluster
+        const char *kc = getenv("PIT_KRYLOV_CLUSTERS");
+        p->kr_cluster = kc && kc[0] == '1';
     }
     pit_status s = PIT_OK;
     auto fail = [&](pit_status e) {

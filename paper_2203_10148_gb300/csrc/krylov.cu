@@ -1,9 +1,13 @@
 // Fused BiCGStab vector work and device-side scalar control of Algorithm 1
 // (PiTSBiCG, Sec. 3).  All vectors are FP64 block vectors of
 // batch x (N+1) x M values; every reduction is deterministic: a fixed
-// warp-shuffle / shared-memory tree per CTA, partial sums stored per
-// (member, quantity, block, chunk), and one finishing CTA per member that
-// adds the partials in a fixed order.
+// warp-shuffle / shared-memory tree per CTA, partial sums per (member,
+// quantity, block), and one finishing CTA per member that adds the partials
+// in a fixed order.  Optionally (PIT_KRYLOV_CLUSTERS=1) a block of 2 to 8
+// chunks of 2048 values is one thread-block cluster: its CTAs' sums meet in
+// distributed shared memory and the first CTA adds them in rank order, so
+// one partial per block reaches global memory.  Both forms add the chunks'
+// sums in chunk order: the results are the same bit for bit.
 //
 // Block inner product (Sec. 3, text after Algorithm 1): the sum of the
 // Euclidean products of all N+1 blocks.  ||.||_{N,inf} (Algorithm 1, the
@@ -12,6 +16,8 @@
 #include <stdio.h>
 
 #include <mutex>
+
+#include <cooperative_groups.h>
 
 #include "pit_internal.h"
 
@@ -69,7 +75,11 @@ __device__ double cta_max(double v, double *sh) {
 struct VecGeom {
     int M, nblk, chunks;
     size_t blen;   // nblk * M
+    int cl = 0;    // 1: the chunks of a block form a cluster, one partial per block
 };
+
+// partial slots per block: one per chunk, or one per block with clusters
+__device__ __host__ __forceinline__ int pslots(const VecGeom &g) { return g.cl ? 1 : g.chunks; }
 
 __device__ __forceinline__ bool member_runs(const MemberState *st, int b) {
     const MemberState &m = st[b];
@@ -77,7 +87,7 @@ __device__ __forceinline__ bool member_runs(const MemberState *st, int b) {
 }
 
 __device__ __forceinline__ size_t pidx(const VecGeom &g, int b, int q, int Q, int n, int c) {
-    return (((size_t)b * Q + q) * g.nblk + n) * g.chunks + c;
+    return (((size_t)b * Q + q) * g.nblk + n) * pslots(g) + c;
 }
 
 // Writes this CTA's Q partial sums (fixed order: warp q sums quantity q,
@@ -88,17 +98,34 @@ template <int Q>
 __device__ void store_partials(const VecGeom &g, double *part, const double (&acc)[Q]) {
     static_assert(Q <= VT / 32, "one warp per quantity");
     __shared__ double sh[Q][VT];
+    __shared__ double csum[8][Q];   // the first CTA of a cluster: every chunk's sums
     const int b = blockIdx.z, n = blockIdx.y, c = blockIdx.x;
 #pragma unroll
     for (int q = 0; q < Q; ++q) sh[q][threadIdx.x] = acc[q];
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    double r = 0.0;
     if (w < Q) {
-        double r = sh[w][l];
+        r = sh[w][l];
 #pragma unroll
         for (int i = 1; i < VT / 32; ++i) r += sh[w][l + 32 * i];
         r = warp_sum(r);
-        if (l == 0) part[pidx(g, b, w, Q, n, c)] = r;
+        if (l == 0 && !g.cl) part[pidx(g, b, w, Q, n, c)] = r;
+    }
+    if (g.cl) {
+        // the block's chunks are the cluster's CTAs (rank = chunk): each CTA
+        // writes its sums into the first CTA's shared memory (distributed
+        // shared memory), one cluster barrier, and the first CTA adds them in
+        // rank order; the others may leave at once
+        namespace cg = cooperative_groups;
+        cg::cluster_group cluster = cg::this_cluster();
+        if (w < Q && l == 0) cluster.map_shared_rank(&csum[0][0], 0)[c * Q + w] = r;
+        cluster.sync();
+        if (c == 0 && threadIdx.x < Q) {
+            double s = 0.0;
+            for (int k = 0; k < g.chunks; ++k) s += csum[k][threadIdx.x];
+            part[pidx(g, b, threadIdx.x, Q, n, 0)] = s;
+        }
     }
 }
 
@@ -245,6 +272,7 @@ __global__ void __launch_bounds__(VT) k_axpy(VecGeom g, double *__restrict__ X,
 // Sum over the chunks of block n (fixed order) of quantity q.
 __device__ __forceinline__ double block_value(const VecGeom &g, const double *part, int b,
                                               int q, int Q, int n) {
+    if (g.cl) return part[pidx(g, b, q, Q, n, 0)];   // already summed in chunk order
     double s = 0.0;
     for (int c = 0; c < g.chunks; ++c) s += part[pidx(g, b, q, Q, n, c)];
     return s;
@@ -440,10 +468,37 @@ VecGeom geom(const Problem *p) {
     g.nblk = p->N + 1;
     g.chunks = (p->M + CHUNK - 1) / CHUNK;
     g.blen = p->blen;
+    g.cl = (g.chunks >= 2 && g.chunks <= 8 && p->kr_cluster) ? 1 : 0;
     return g;
 }
 
 dim3 vgrid(const Problem *p, const VecGeom &g) { return dim3(g.chunks, g.nblk, p->batch); }
+
+// A vector kernel that stores partial sums: with g.cl, launched as clusters
+// of the block's chunks.
+template <class... KArgs, class... Args>
+pit_status vlaunch(const Problem *p, const VecGeom &g, cudaStream_t s, void (*kern)(KArgs...),
+                   Args &&...args) {
+    if (!g.cl) {
+        kern<<<vgrid(p, g), VT, 0, s>>>(std::forward<Args>(args)...);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = vgrid(p, g);
+    cfg.blockDim = dim3(VT);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)g.chunks;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PIT_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
 
 pit_status finish(Problem *p, int kind, cudaStream_t s, InitArgs ia = InitArgs{},
                   double *out = nullptr) {
@@ -474,9 +529,8 @@ pit_status krylov_prepare(Problem *p) {
 pit_status kr_init(Problem *p, double tol_rel, const double *abs_thresh, double eps0,
                    int max_iter, cudaStream_t s) {
     VecGeom g = geom(p);
-    k_init<<<vgrid(p, g), VT, 0, s>>>(g, p->R.as<double>(), p->Rt.as<double>(),
-                                      p->P.as<double>(), p->partials.as<double>(), nullptr);
-    PIT_LAUNCH_CHECK();
+    PIT_TRY(vlaunch(p, g, s, k_init, g, (const double *)p->R.as<double>(), p->Rt.as<double>(),
+                    p->P.as<double>(), p->partials.as<double>(), (const MemberState *)nullptr));
     InitArgs ia{tol_rel, abs_thresh, eps0, 1e-14, max_iter};
     return finish(p, F_INIT, s, ia);
 }
@@ -484,38 +538,37 @@ pit_status kr_init(Problem *p, double tol_rel, const double *abs_thresh, double 
 pit_status kr_sigma(Problem *p, cudaStream_t s) {
     VecGeom g = geom(p);
     MemberState *st = p->states.as<MemberState>();
-    k_dot2<<<vgrid(p, g), VT, 0, s>>>(g, p->D.as<double>(), p->Rt.as<double>(),
-                                      p->partials.as<double>(), st);
-    PIT_LAUNCH_CHECK();
+    PIT_TRY(vlaunch(p, g, s, k_dot2, g, (const double *)p->D.as<double>(),
+                    (const double *)p->Rt.as<double>(), p->partials.as<double>(),
+                    (const MemberState *)st));
     return finish(p, F_SIGMA, s);
 }
 
 pit_status kr_update_S(Problem *p, cudaStream_t s) {
     VecGeom g = geom(p);
     MemberState *st = p->states.as<MemberState>();
-    k_update_S<<<vgrid(p, g), VT, 0, s>>>(g, p->R.as<double>(), p->D.as<double>(),
-                                          p->S.as<double>(), p->partials.as<double>(), st);
-    PIT_LAUNCH_CHECK();
+    PIT_TRY(vlaunch(p, g, s, k_update_S, g, (const double *)p->R.as<double>(),
+                    (const double *)p->D.as<double>(), p->S.as<double>(), p->partials.as<double>(),
+                    (const MemberState *)st));
     return finish(p, F_S, s);
 }
 
 pit_status kr_omega(Problem *p, cudaStream_t s) {
     VecGeom g = geom(p);
     MemberState *st = p->states.as<MemberState>();
-    k_dot2<<<vgrid(p, g), VT, 0, s>>>(g, p->K.as<double>(), p->S.as<double>(),
-                                      p->partials.as<double>(), st);
-    PIT_LAUNCH_CHECK();
+    PIT_TRY(vlaunch(p, g, s, k_dot2, g, (const double *)p->K.as<double>(),
+                    (const double *)p->S.as<double>(), p->partials.as<double>(),
+                    (const MemberState *)st));
     return finish(p, F_OMEGA, s);
 }
 
 pit_status kr_update_XR(Problem *p, cudaStream_t s) {
     VecGeom g = geom(p);
     MemberState *st = p->states.as<MemberState>();
-    k_update_XR<<<vgrid(p, g), VT, 0, s>>>(g, p->X.as<double>(), p->R.as<double>(),
-                                           p->P.as<double>(), p->S.as<double>(),
-                                           p->K.as<double>(), p->Rt.as<double>(),
-                                           p->partials.as<double>(), st);
-    PIT_LAUNCH_CHECK();
+    PIT_TRY(vlaunch(p, g, s, k_update_XR, g, p->X.as<double>(), p->R.as<double>(),
+                    (const double *)p->P.as<double>(), (const double *)p->S.as<double>(),
+                    (const double *)p->K.as<double>(), (const double *)p->Rt.as<double>(),
+                    p->partials.as<double>(), (const MemberState *)st));
     return finish(p, F_R, s);
 }
 
@@ -531,8 +584,7 @@ pit_status kr_update_P(Problem *p, cudaStream_t s) {
 pit_status kr_block_norm(Problem *p, const double *U, double *out, cudaStream_t s) {
     VecGeom g = geom(p);
     // k_dot2(U, U) stores <U,U> per block as quantity 0 of a Q = 2 layout
-    k_dot2<<<vgrid(p, g), VT, 0, s>>>(g, U, U, p->partials.as<double>(), nullptr);
-    PIT_LAUNCH_CHECK();
+    PIT_TRY(vlaunch(p, g, s, k_dot2, g, U, U, p->partials.as<double>(), (const MemberState *)nullptr));
     return finish(p, F_NORM, s, InitArgs{}, out);
 }
 

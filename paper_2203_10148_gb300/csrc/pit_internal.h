@@ -204,6 +204,7 @@ struct Problem {
     // float-float): 0 one CTA of 4-column tiles, 1 one CTA of 8-column
     // tiles (FP32 only), 2 a cluster of CTAs with 8 x 4 tiles
     int fine_var32 = 0, fine_var_ff = 0;
+    bool kr_cluster = false;      // Krylov partials of 2..8-chunk blocks reduced per cluster
     int fine_var32_big = 0, fine_var_ff_big = 0;   // n > 128: 8-column clusters (0) or wide 4-column ones (1)
     ReduceLayout rl{};
     OpTimer timer;
