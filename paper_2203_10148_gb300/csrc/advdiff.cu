@@ -565,8 +565,8 @@ pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ sweep
-constexpr int SWA_THREADS = 256;
-constexpr int SWA_PPT = 8;                     // points per thread: bands of <= 2048 points
+constexpr int SWA_THREADS = 512;               // 16 warps per SM: the steps' short chains interleave
+constexpr int SWA_PPT = 4;                     // points per thread: bands of <= 2048 points
 constexpr int SWA_KMAX = 64;     // Chebyshev steps per coarse solve, at most
 
 template <class T>
@@ -824,11 +824,11 @@ pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax,
         return PIT_E_UNSUPPORTED;
     }
     const int G = n / R;
+    auto kern = k_advdiff_sweep<T>;
     const size_t smem = (size_t)(R + 2) * n * sizeof(T);
-    PIT_CUDA(cudaFuncSetAttribute(k_advdiff_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    PIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_advdiff_sweep<T>, SWA_THREADS, smem));
+    PIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SWA_THREADS, smem));
     if (per_sm * sms < G) {
         set_error("advdiff sweep: bands cannot all be resident");
         return PIT_E_UNSUPPORTED;
@@ -861,8 +861,7 @@ pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax,
     a.err = p->errword.as<int>();
     a.st = st;
     void *args[] = {&a};
-    PIT_CUDA(cudaLaunchCooperativeKernel((const void *)k_advdiff_sweep<T>, dim3(G), dim3(SWA_THREADS),
-                                         args, smem, s));
+    PIT_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(SWA_THREADS), args, smem, s));
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }

@@ -174,3 +174,18 @@ def test_advdiff_float_float_fp32_coefficients(case, monkeypatch):
     assert np.array_equal(got, gen)
     ref = np.stack([OracleProblem.from_workload(w, member=b).apply_F(X[b]) for b in range(w.batch)])
     assert _rel(got, ref) < 1e-11
+
+
+@pytest.mark.parametrize("n,N,batch", [(256, 3, 2), (512, 2, 1)])
+def test_advdiff_sweep_large_grids(n, N, batch):
+    """Bands of 2 (n = 256) and 4 rows (n = 512, the workload's grid): the
+    FP64 and FP32 sweeps against the oracle's operator."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.advdiff2d(n=n, N=N, T=0.5 * N / 256, batch=batch)
+    X = _rand(w, 31)
+    ref = _oracle_sweep(w, X)
+    with pit.Problem(w, "mixed") as p:
+        got64 = p.apply("Ginv", X, precision="fp64")
+        got32 = p.apply("Ginv", X, precision="mixed")
+    assert _rel(got64, ref) < 1e-12
+    assert _rel(got32, ref) < 1e-5
