@@ -70,18 +70,25 @@ def test_served_equals_solo_and_oracle():
         assert _rel(X[0], lam) <= 1e-6, (w.name, _rel(X[0], lam))
 
 
-def test_served_bitwise_equals_solo():
+@pytest.mark.parametrize("resid", ["ff", "split"])
+def test_served_bitwise_equals_solo(resid):
     """Kernels, launch shapes and reduction orders depend on the request
-    alone, so the served iterate is bit for bit the solo one."""
+    alone, so the served iterate is bit for bit the solo one, with
+    float-float and with split RK4 true residuals (the library default)."""
     pit = _pit()
     ws = _small_stream(6, first=100)
+    opts = dict(OPTS, residual_precision=resid)
     with pit.Server(max_slots=3) as srv:
-        tickets = [srv.submit(w, **OPTS) for w in ws]
+        tickets = [srv.submit(w, **opts) for w in ws]
         results = [srv.wait(t, timeout=300.0) for t in tickets]
     for w, (st, X, _) in zip(ws, results):
+        assert st == pit.PIT_OK, w.name
         with pit.Problem(w) as p:
-            Xs, _ = p.bicgstab_solve(**OPTS)
+            Xs, _ = p.bicgstab_solve(**opts)
         assert np.array_equal(X, Xs), w.name
+        if resid == "split":
+            lam = OracleProblem.from_workload(w).serial_fine()
+            assert _rel(X[0], lam) <= 1e-6, (w.name, _rel(X[0], lam))
 
 
 def test_budget_admission_and_queueing():
