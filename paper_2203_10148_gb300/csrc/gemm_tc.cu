@@ -159,50 +159,56 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // warp-uniform: tcgen05.ld is a warp-collective instruction
     const bool have = __all_sync(0xffffffffu, mbar_wait(accum, 0u, err) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
     if (have) {
+        // Each warp drains its 32 tile rows 32 columns at a time: tcgen05.ld
+        // gives a lane one row; the values go through a padded shared-memory
+        // tile (the stage ring is free once the products are complete) so
+        // that, row by row, the 32 lanes read x and write y as 32 consecutive
+        // columns (coalesced).
+        float *stg = reinterpret_cast<float *>(base) + warp * 32 * 33;
+        // this lane's tile row (member, slice, liveness), broadcast row by row below
         const int nb1 = ep.N + 1;
-        const int b = row / nb1, n = row % nb1;
-        const bool live = row < R && n < ep.N &&
-                          (ep.st == nullptr || (ep.st[b].active && !ep.st[b].skip && !ep.st[b].half));
-        const size_t mb = (size_t)b * ep.blen;
+        const int myrow = m0 + warp * 32 + lane;
+        const int myb = myrow / nb1, myn = myrow % nb1;
+        const bool mylive = myrow < R && myn < ep.N &&
+                            (ep.st == nullptr || (ep.st[myb].active && !ep.st[myb].skip && !ep.st[myb].half));
+        const unsigned livemask = __ballot_sync(0xffffffffu, mylive);
         for (int cchunk = 0; cchunk < TC_BN / 32; ++cchunk) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cchunk * 32), v);
-            const int c0 = n0 + cchunk * 32;
-            if (!live || c0 >= ep.M) continue;
-            const int cn = min(32, ep.M - c0);      // columns of the padding are not written
-            const double *xn = ep.x + mb + (size_t)(n + 1) * ep.M + c0;
-            if (ep.y32) {
-                float *yo = ep.y32 + mb + (size_t)(n + 1) * ep.M + c0;
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    if (i < cn) yo[i] = d2f_rn(xn[i]) - v[i];
-            } else {
-                double *yo = ep.y + mb + (size_t)(n + 1) * ep.M + c0;
+            for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
+            __syncwarp();
+            const int c = n0 + cchunk * 32 + lane;
+            const bool col_ok = c < ep.M;
+            // all x loads of the 32 rows first (independent, in flight together)
+            double xn[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    if (i >= cn) continue;
-                    const double f = f2d(v[i]);
-                    yo[i] = (ep.mode == FINE_APPLY) ? xn[i] - f : f - xn[i];
-                }
+            for (int rr = 0; rr < 32; ++rr) {
+                const int b = __shfl_sync(0xffffffffu, myb, rr), n = __shfl_sync(0xffffffffu, myn, rr);
+                const bool ok = ((livemask >> rr) & 1u) && col_ok;
+                xn[rr] = ok ? ep.x[(size_t)b * ep.blen + (size_t)(n + 1) * ep.M + c] : 0.0;
             }
-            if (n == 0) {
-                // row 0 of eq. (4): x_0 (or y0 - x_0)
-                const double *x0 = ep.x + mb + c0;
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) {
+                const int b = __shfl_sync(0xffffffffu, myb, rr), n = __shfl_sync(0xffffffffu, myn, rr);
+                if (!((livemask >> rr) & 1u) || !col_ok) continue;
+                const float cv = stg[rr * 33 + lane];
+                const size_t mb = (size_t)b * ep.blen;
                 if (ep.y32) {
-                    float *yo = ep.y32 + mb + c0;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (i < cn) yo[i] = d2f_rn(x0[i]);
+                    ep.y32[mb + (size_t)(n + 1) * ep.M + c] = d2f_rn(xn[rr]) - cv;
+                    if (n == 0) ep.y32[mb + c] = d2f_rn(ep.x[mb + c]);   // row 0 of eq. (4): x_0
                 } else {
-                    double *yo = ep.y + mb + c0;
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        if (i < cn)
-                            yo[i] = (ep.mode == FINE_APPLY) ? x0[i] : ep.y0[(size_t)b * ep.M + c0 + i] - x0[i];
+                    const double f = f2d(cv);
+                    ep.y[mb + (size_t)(n + 1) * ep.M + c] = (ep.mode == FINE_APPLY) ? xn[rr] - f : f - xn[rr];
+                    if (n == 0) {
+                        // row 0 of eq. (4): x_0 (or y0 - x_0)
+                        const double x0 = ep.x[mb + c];
+                        ep.y[mb + c] = (ep.mode == FINE_APPLY) ? x0 : ep.y0[(size_t)b * ep.M + c] - x0;
+                    }
                 }
             }
+            __syncwarp();
         }
     }
     if (warp == 0 && lane == 0) {
