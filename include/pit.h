@@ -72,13 +72,12 @@ typedef int pit_status;
 #define PIT_MIXED           1   /* FP32 fine stepping (split-precision tensor-core GEMM for
                                    PIT_OP_DENSE), FP64 Krylov vectors and scalars, and
                                    iterative refinement on true residuals computed in
-                                   PIT_SPLIT by default (PIT_FF or PIT_FP64 on request;
-                                   HEAT1D: FP64) */
+                                   PIT_SPLIT by default (PIT_FF or PIT_FP64 on request) */
 #define PIT_FF              2   /* float-float fine arithmetic: each value an unevaluated sum
                                    of two FP32 numbers (about 48 significant bits) on the
                                    FP32 pipe, FP64 inputs and outputs: stepping for HEAT2D
-                                   and ADVDIFF2D, a compensated product for DENSE; HEAT1D
-                                   treats it as PIT_FP64 */
+                                   and ADVDIFF2D, the Thomas recurrences for HEAT1D, a
+                                   compensated product for DENSE */
 #define PIT_MIXED_BF16      4   /* problem precision only: PIT_MIXED with the dense fine
                                    product split in BF16 instead of TF32 ("3xBF16": x = xh + xl
                                    and Phi = ph + pl with BF16 parts, xh ph + xh pl + xl ph on
@@ -260,8 +259,8 @@ pit_status pit_problem_shape(pit_problem_t prob, int *M, int *N, int *batch);
  * stepping from FP64 inputs, or PIT_FF = float-float arithmetic, about 48
  * significant bits on the FP32 pipe: stepping for PIT_OP_HEAT2D and
  * PIT_OP_ADVDIFF2D, a compensated product for PIT_OP_DENSE; PIT_SPLIT is
- * split RK4 for PIT_OP_HEAT2D and PIT_FF elsewhere; HEAT1D runs PIT_FF and
- * PIT_SPLIT in FP64).  Every dense product runs on the library's kernels for
+ * split RK4 for PIT_OP_HEAT2D and PIT_FF elsewhere; PIT_FF is the
+ * float-float Thomas recurrence for PIT_OP_HEAT1D).  Every dense product runs on the library's kernels for
  * any M (tcgen05 split TF32 for PIT_MIXED, rows padded to 128; float-float
  * for PIT_FF, padded to 64; FP64 tiles for PIT_FP64).  G^{-1} runs
  * in reduced precision for PIT_MIXED (2D heat and 1D heat: split-TF32 sine
@@ -287,8 +286,8 @@ pit_status pit_serial_fine(pit_problem_t prob, int precision, double *Lam, int o
  * PIT_FP64: every step in FP64 on the device.  PIT_MIXED: iterative
  * refinement: the true residual G^{-1}(B - F X) with the fine propagations
  * in opts.residual_precision (PIT_SPLIT by default: split RK4 for HEAT2D,
- * float-float on the FP32 pipe elsewhere; PIT_FF or PIT_FP64 on request;
- * HEAT1D always FP64), an FP32-fine /
+ * float-float on the FP32 pipe elsewhere; PIT_FF or PIT_FP64 on request),
+ * an FP32-fine /
  * FP64-Krylov inner solve of the correction to inner_tol, X += correction,
  * until the true preconditioned residual is <= tol * its reference
  * (opts.tol_mode).

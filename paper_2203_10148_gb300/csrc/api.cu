@@ -186,7 +186,7 @@ static int fine_cls(int prec) {
 }
 
 // The split RK4 arithmetic exists for the 2D heat stepper; elsewhere it
-// means float-float (which HEAT1D, and DENSE outside its product, run in FP64).
+// means float-float (which DENSE outside its product runs in FP64).
 static int split_or_ff(const Problem *p, int prec) {
     return (prec == PIT_SPLIT && p->kind != PIT_OP_HEAT2D) ? PIT_FF : prec;
 }
@@ -196,7 +196,6 @@ static int sweep_cls(int prec) { return prec == PIT_MIXED ? PIT_TIME_SWEEP_MIXED
 pit_status op_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                       const MemberState *st, cudaStream_t s) {
     prec = split_or_ff(p, prec);
-    if (prec == PIT_FF && p->kind == PIT_OP_HEAT1D) prec = PIT_FP64;
     pit_status st_ = PIT_E_INVALID;
     switch (p->kind) {
     case PIT_OP_HEAT1D: st_ = heat1d_apply_F(p, x, y, mode, prec, st, s); break;
@@ -224,7 +223,7 @@ pit_status op_sweep(Problem *p, const double *q, double *z, int prec, const Memb
 
 static pit_status fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
     prec = split_or_ff(p, prec);
-    if (prec == PIT_FF && p->kind != PIT_OP_HEAT2D && p->kind != PIT_OP_ADVDIFF2D) prec = PIT_FP64;
+    if (prec == PIT_FF && p->kind == PIT_OP_DENSE) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_fine_one(p, x, y, prec, s);
     case PIT_OP_HEAT2D: return heat2d_fine_one(p, x, y, prec, s);
@@ -934,7 +933,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
     cudaSetDevice(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
     DevBuf *bufs[] = {&p->y0, &p->fine_inv64, &p->fine_cp64, &p->coarse_inv64, &p->coarse_cp64,
-                      &p->fine_inv32, &p->fine_cp32, &p->coarse_inv32, &p->coarse_cp32,
+                      &p->fine_inv32, &p->fine_cp32, &p->coarse_inv32, &p->coarse_cp32, &p->fine_invff,
                       &p->S64, &p->S32, &p->gmode, &p->hat, &p->vx64, &p->vy64, &p->vx32,
                       &p->vy32, &p->vxff, &p->vyff, &p->A64, &p->cvec, &p->adv_scratch, &p->PhiF64, &p->G64, &p->PhiF_hi,
                       &p->PhiF_lo, &p->G32, &p->dense_scratch, &p->X, &p->R, &p->Rt,

@@ -13,7 +13,10 @@
 // scan: every thread composes the maps of its E contiguous points, the CTA
 // scans the per-thread maps (warp shuffles, then a short pass over warps),
 // and every thread replays its points from the scanned prefix.  A slice's
-// state stays in registers across all fine steps.
+// state stays in registers across all fine steps.  The fine kernel runs in
+// FP64, FP32 or float-float (the true residual of the mixed path: every
+// product and sum of the recurrences as float-float operations on the FP32
+// pipe, Thomas factors stored as (hi, lo) pairs).
 #include <math.h>
 #include <stdlib.h>
 
@@ -28,6 +31,16 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// The arithmetic the recurrences need, for FP32 / FP64 and float-float.
+template <class T> __device__ __forceinline__ T one() { return T(1); }
+template <class T> __device__ __forceinline__ T zero() { return T(0); }
+template <> __device__ __forceinline__ ff one<ff>() { return ff{1.f, 0.f}; }
+template <> __device__ __forceinline__ ff zero<ff>() { return ff{0.f, 0.f}; }
+__device__ __forceinline__ ff operator*(ff a, ff b) { return ff_mul(a, b); }
+__device__ __forceinline__ ff operator-(ff a) { return ff{-a.hi, -a.lo}; }
+template <class T> __device__ __forceinline__ T fmaT(T a, T b, T c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ ff fmaT<ff>(ff a, ff b, ff c) { return ff_add(ff_mul(a, b), c); }
+
 template <class T>
 struct Aff {
     T a, c;
@@ -36,12 +49,16 @@ struct Aff {
 // later o earlier
 template <class T>
 __device__ __forceinline__ Aff<T> comp(Aff<T> later, Aff<T> earlier) {
-    return Aff<T>{later.a * earlier.a, fma(later.a, earlier.c, later.c)};
+    return Aff<T>{later.a * earlier.a, fmaT(later.a, earlier.c, later.c)};
 }
 
 template <class T>
 __device__ __forceinline__ T shfl_dir(T v, int o, bool rev) {
     return rev ? __shfl_down_sync(FULL, v, o) : __shfl_up_sync(FULL, v, o);
+}
+template <>
+__device__ __forceinline__ ff shfl_dir<ff>(ff v, int o, bool rev) {
+    return ff{shfl_dir(v.hi, o, rev), shfl_dir(v.lo, o, rev)};
 }
 
 // Exclusive scan of affine maps over the CTA.  Scan order is thread order
@@ -61,7 +78,7 @@ __device__ Aff<T> cta_affine_excl(Aff<T> v, T *sh) {
     const T ea = shfl_dir(inc.a, 1, REV);
     const T ec = shfl_dir(inc.c, 1, REV);
     const bool first = REV ? (lane == 31) : (lane == 0);
-    Aff<T> exw = first ? Aff<T>{T(1), T(0)} : Aff<T>{ea, ec};
+    Aff<T> exw = first ? Aff<T>{one<T>(), zero<T>()} : Aff<T>{ea, ec};
     if (W == 1) return exw;
     const int last = REV ? 0 : 31;
     __syncthreads();
@@ -74,7 +91,7 @@ __device__ Aff<T> cta_affine_excl(Aff<T> v, T *sh) {
     // (lane l holds warp l's map, W <= 32) and leaves each warp's exclusive
     // prefix in shared memory
     if (warp == 0) {
-        Aff<T> wv = (lane < W) ? Aff<T>{sh[lane], sh[W + lane]} : Aff<T>{T(1), T(0)};
+        Aff<T> wv = (lane < W) ? Aff<T>{sh[lane], sh[W + lane]} : Aff<T>{one<T>(), zero<T>()};
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const T a = shfl_dir(wv.a, o, REV);
@@ -88,8 +105,8 @@ __device__ Aff<T> cta_affine_excl(Aff<T> v, T *sh) {
         const bool none = REV ? (lane == W - 1) : (lane == 0);
         __syncwarp();
         if (lane < W) {
-            sh[2 * W + lane] = none ? T(1) : pa;
-            sh[3 * W + lane] = none ? T(0) : pc;
+            sh[2 * W + lane] = none ? one<T>() : pa;
+            sh[3 * W + lane] = none ? zero<T>() : pc;
         }
     }
     __syncthreads();
@@ -111,9 +128,9 @@ struct Factors {
             const int i = threadIdx.x * E + e;
             ok[e] = i < M;
             const int ic = min(i, M - 1);
-            fm[e] = ok[e] ? fmg[ic] : T(1);
-            inv[e] = ok[e] ? invg[ic] : T(0);
-            ncp[e] = ok[e] ? -cpg[ic] : T(1);
+            fm[e] = ok[e] ? fmg[ic] : one<T>();
+            inv[e] = ok[e] ? invg[ic] : zero<T>();
+            ncp[e] = ok[e] ? -cpg[ic] : one<T>();
         }
     }
 };
@@ -123,7 +140,7 @@ struct Factors {
 template <class T, int E, int NT>
 __device__ __forceinline__ void ie_step(T (&u)[E], const Factors<T, E> &f, T *sh) {
     // forward: d'_i = fm_i d'_{i-1} + inv_i d_i
-    Aff<T> agg{T(1), T(0)};
+    Aff<T> agg{one<T>(), zero<T>()};
     T lc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -134,21 +151,21 @@ __device__ __forceinline__ void ie_step(T (&u)[E], const Factors<T, E> &f, T *sh
     T y = pre.c;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        y = fma(f.fm[e], y, lc[e]);
+        y = fmaT(f.fm[e], y, lc[e]);
         u[e] = y;                       // d'_i
     }
     // backward: x_i = -cp_i x_{i+1} + d'_i, scanned from the last point
-    agg = Aff<T>{T(1), T(0)};
+    agg = Aff<T>{one<T>(), zero<T>()};
 #pragma unroll
     for (int e = E - 1; e >= 0; --e) {
-        lc[e] = f.ok[e] ? u[e] : T(0);
+        lc[e] = f.ok[e] ? u[e] : zero<T>();
         agg = comp(Aff<T>{f.ncp[e], lc[e]}, agg);
     }
     pre = cta_affine_excl<T, NT, true>(agg, sh + 4 * (NT / 32));
     y = pre.c;
 #pragma unroll
     for (int e = E - 1; e >= 0; --e) {
-        y = fma(f.ncp[e], y, lc[e]);
+        y = fmaT(f.ncp[e], y, lc[e]);
         u[e] = y;
     }
 }
@@ -187,8 +204,9 @@ __global__ void __launch_bounds__(NT) k_heat1d_fine(Heat1dArgs a, const T *__res
         const int i = threadIdx.x * E + e;
         T ld;
         if constexpr (std::is_same<T, float>::value) ld = d2f_rn(xin[min(i, a.M - 1)]);  // integer pipe
+        else if constexpr (std::is_same<T, ff>::value) ld = ff_from_double(xin[min(i, a.M - 1)]);
         else ld = xin[min(i, a.M - 1)];
-        u[e] = (i < a.M) ? ld : T(0);
+        u[e] = (i < a.M) ? ld : zero<T>();
     }
     Factors<T, E> f;
     f.load(fm, inv, cp, a.M);
@@ -201,6 +219,7 @@ __global__ void __launch_bounds__(NT) k_heat1d_fine(Heat1dArgs a, const T *__res
         if (i < a.M) {
             double f;
             if constexpr (std::is_same<T, float>::value) f = f2d(u[e]);
+            else if constexpr (std::is_same<T, ff>::value) f = ff_to_double(u[e]);
             else f = u[e];
             if (a.mode == FINE_APPLY) yo[i] = xn[i] - f;
             else if (a.mode == FINE_RESIDUAL) yo[i] = f - xn[i];
@@ -344,7 +363,8 @@ void thomas_factors(int M, double r, std::vector<double> &fm, std::vector<double
     }
 }
 
-pit_status upload_factors(int M, double r, DevBuf &b64, DevBuf &b32, cudaStream_t s) {
+pit_status upload_factors(int M, double r, DevBuf &b64, DevBuf &b32, cudaStream_t s,
+                          DevBuf *bff = nullptr) {
     std::vector<double> fm, inv, cp;
     thomas_factors(M, r, fm, inv, cp);
     std::vector<double> all(3 * (size_t)M);
@@ -359,6 +379,19 @@ pit_status upload_factors(int M, double r, DevBuf &b64, DevBuf &b32, cudaStream_
     PIT_TRY(b32.ensure(all32.size() * sizeof(float)));
     PIT_CUDA(cudaMemcpyAsync(b64.ptr, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     PIT_CUDA(cudaMemcpyAsync(b32.ptr, all32.data(), all32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (bff) {
+        // float-float factors: (hi, lo) with hi = RN32(x), lo = RN32(x - hi)
+        std::vector<float> allff(2 * all.size());
+        for (size_t i = 0; i < all.size(); ++i) {
+            const float hi = (float)all[i];
+            allff[2 * i] = hi;
+            allff[2 * i + 1] = (float)(all[i] - (double)hi);
+        }
+        PIT_TRY(bff->ensure(allff.size() * sizeof(float)));
+        PIT_CUDA(cudaMemcpyAsync(bff->ptr, allff.data(), allff.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, s));
+        PIT_CUDA(cudaStreamSynchronize(s));   // allff is a local buffer
+    }
     return PIT_OK;
 }
 
@@ -431,6 +464,10 @@ pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStre
         FineLaunch<double> f{p, a, nslices, &p->fine_inv64, s};
         return dispatch_1d(p->M, f);
     }
+    if (prec == PIT_FF) {
+        FineLaunch<ff> f{p, a, nslices, &p->fine_invff, s};
+        return dispatch_1d(p->M, f);
+    }
     FineLaunch<float> f{p, a, nslices, &p->fine_inv32, s};
     return dispatch_1d(p->M, f);
 }
@@ -450,7 +487,7 @@ pit_status heat1d_setup(Problem *p) {
     const double rf = (p->dT / p->fine_steps) * p->nu / (h * h);
     const double rc = (p->dT / p->coarse_steps) * p->nu / (h * h);
     // fine factors in fine_inv64/32, coarse in coarse_inv64/32 (fm | inv | cp)
-    PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32, p->stream));
+    PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32, p->stream, &p->fine_invff));
     PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32, p->stream));
     // mixed path: the coarse step (I - dTc nu D2)^{-c} is diagonal in the sine
     // basis (eigenvalues mu_k = -4/h^2 sin^2(k pi h / 2), k = 1..M), so the

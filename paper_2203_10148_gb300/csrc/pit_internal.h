@@ -159,6 +159,7 @@ struct Problem {
     // heat1d: Thomas factors of (I - dt L) for the fine and coarse steps
     DevBuf fine_inv64, fine_cp64, coarse_inv64, coarse_cp64;
     DevBuf fine_inv32, fine_cp32, coarse_inv32, coarse_cp32;
+    DevBuf fine_invff;            // heat1d: fine Thomas factors as float-float (hi, lo) pairs
     double fine_off = 0, coarse_off = 0;   // off-diagonal -dt nu / h^2
 
     // heat2d: sine basis S_jk = sin(pi j k/(n+1)) and coarse mode factors

@@ -100,7 +100,7 @@ size_t serve_footprint(const pit_problem_desc *d) {
         b += 32 * nn;                                        // sine bases (FP64, FP32, TF32 parts), mode factors
         b = std::max(b, 16 * vlen + 32 * nn + 4096);         // set-up (variant autotuning)
     } else {
-        b += 48 * M;                                         // Thomas factors
+        b += 72 * M;                                         // Thomas factors (FP64, FP32, float-float)
         if (d->precision == PIT_MIXED) {
             // sine-basis sweep: TF32 parts of S, two padded FP32 row sets,
             // chunk ends and mode factors

@@ -88,6 +88,42 @@ def test_heat1d_operators_fp32_fine(which):
     assert _rel(got, ref) < 2e-5
 
 
+@pytest.mark.parametrize("case", HEAT1D_CASES)
+def test_heat1d_float_float_fine_matches_oracle(case):
+    """The float-float Thomas recurrences (true residuals of the mixed path):
+    within 1e-11 of the FP64 oracle for every thread layout (M = 1 .. 4095),
+    the serial trajectory too."""
+    pit = _pit()
+    w = inputs.heat1d(**case)
+    X = _rand_block(w, 61)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("F", X, precision="ff")
+        res = p.apply("residual", X, precision="ff")
+        lam = p.serial_fine("ff")
+    assert _rel(got, _oracle_apply(w, "F", X)) < 1e-11
+    # the mixed residual's sweep is FP32-class (it only preconditions)
+    assert _rel(res, _oracle_apply(w, "residual", X)) < max(2e-5, 3e-8 * w.M)
+    for b in range(w.batch):
+        assert _rel(lam[b], OracleProblem.from_workload(w, member=b).serial_fine()) < 1e-11
+
+
+@pytest.mark.parametrize("resid", ["split", "fp64"])
+def test_heat1d_mixed_solve_float_float_residual(resid):
+    """Mixed 1D solves with float-float true residuals (split means
+    float-float for this operator) reach the serial FP64 trajectory within
+    1e-6 in the same refinement rounds as with FP64 residuals."""
+    pit = _pit()
+    w = inputs.heat1d(M=1000, N=64)
+    lam = OracleProblem.from_workload(w).serial_fine()
+    opts = dict(tol=1e-7, tol_mode="rhs", inner_tol=1e-5)
+    with pit.Problem(w, "mixed") as p:
+        X, info = p.bicgstab_solve(residual_precision=resid, **opts)
+        X64, info64 = p.bicgstab_solve(residual_precision="fp64", **opts)
+    assert info[0]["status"] == 0
+    assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
+    assert info[0]["refinements"] == info64[0]["refinements"]
+
+
 def test_heat1d_bicgstab_fixed_iterations_match_oracle():
     """Same k iterations of Algorithm 1: iterates agree to 1e-12."""
     pit = _pit()
