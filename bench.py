@@ -449,10 +449,13 @@ def roofline(w, timing, peaks, nsm):
         flop = point_steps * 8.0
         peak = FP64_LANES_PER_SM * 2 * nsm * sm_max * 1e6 / 1e12
         ach = flop / (avg_ms / 1e3) / 1e12
-        return {"bound": "latency", "kernel": "k_heat1d_fine<%s>" % ("double" if dom == "fine_fp64" else "float"),
+        kname = "k_heat1d_fine_warp" if w.M <= 256 else "k_heat1d_fine"
+        return {"bound": "latency", "kernel": "%s<%s>" % (kname, "double" if dom == "fine_fp64" else "float"),
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64, 8 flop per point-step)",
                 "frac": ach / peak, "traffic": None, "launch_ms": avg_ms, "launches": calls,
-                "note": "latency-bound: one CTA per slice, 63 points",
+                "note": ("one warp per slice, E points per lane: 5E + 8 FP64 warp instructions "
+                         "per implicit-Euler step, issue-bound on one SM sub-partition's FP64 pipe")
+                if w.M <= 256 else "latency-bound: one CTA per slice",
                 "peak_source": "derived: 4 FP64 flop/clk/SM x SMs x max SM clock"}
     lanes = FP64_LANES_PER_SM if dom == "fine_fp64" else FP32_LANES_PER_SM
     peak = lanes * nsm * sm_max * 1e6 / 1e12

@@ -346,6 +346,209 @@ __global__ void __launch_bounds__(NT) k_heat1d_sweep(const double *q, double *z,
     }
 }
 
+// ------------------------------------------------- small grids (M <= 256)
+// One warp per slice, E points per lane.  The multiplier halves of the
+// affine maps in both Thomas scans are products of the constant factors, so
+// the kernel forms, once per launch, each lane's multiplier for every level
+// of the two warp scans and the products of its own points' factors; an
+// implicit-Euler step then carries only data: a lane composes its E points
+// (E - 1 dependent operations), the warp scan takes one fused multiply-add
+// per level, and every point's value is one independent multiply-add from
+// the lane's incoming value.  The state between steps is w = inv .* u (the
+// right-hand side of the forward recurrence), formed in the backward fix-up
+// off the dependent chain.  Per step: 2 (E - 1) + 12 dependent operations.
+// (Each dependent FP64 operation costs about 120 cycles on this part
+// whatever the number of active lanes, so the chain length, not the lane
+// count, sets the time of these latency-bound small-grid solves.)
+constexpr int WARP_MAXM = 256;
+
+template <class T, int E>
+struct WarpThomas {
+    T fm[E], ncp[E], inv[E];
+    T P[E], Q[E], iQ[E];  // prod_{k<=e} fm_k, prod_{k>=e} ncp_k, inv_e Q_e (this lane's points)
+    T fa[5], ba[5];       // level multipliers of the forward / backward scans (0: no partner)
+
+    // Padding points (i >= M) get fm = ncp = inv = 0: they hold 0 and cut
+    // every chain through them.
+    __device__ void load(const T *__restrict__ fmg, const T *__restrict__ invg,
+                         const T *__restrict__ cpg, int M) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = lane * E + e;
+            const bool ok = i < M;
+            const int ic = min(i, M - 1);
+            fm[e] = ok ? fmg[ic] : zero<T>();
+            inv[e] = ok ? invg[ic] : zero<T>();
+            ncp[e] = ok ? -cpg[ic] : zero<T>();
+        }
+        P[0] = fm[0];
+#pragma unroll
+        for (int e = 1; e < E; ++e) P[e] = fm[e] * P[e - 1];
+        Q[E - 1] = ncp[E - 1];
+#pragma unroll
+        for (int e = E - 2; e >= 0; --e) Q[e] = ncp[e] * Q[e + 1];
+#pragma unroll
+        for (int e = 0; e < E; ++e) iQ[e] = inv[e] * Q[e];
+        T A = P[E - 1], B = Q[0];
+        // inclusive scans of the multipliers; level l combines with the lane
+        // 2^l before (forward) / after (backward)
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            const int o = 1 << l;
+            const bool fwd = lane >= o, bwd = lane + o < 32;
+            fa[l] = fwd ? A : zero<T>();
+            ba[l] = bwd ? B : zero<T>();
+            const T Ao = shfl_dir(A, o, false);
+            const T Bo = shfl_dir(B, o, true);
+            if (fwd) A = A * Ao;
+            if (bwd) B = B * Bo;
+        }
+    }
+
+    // One implicit-Euler step: w = inv .* u in, w of the new u out (and the
+    // new u in x when X).  Lane owns points lane*E .. lane*E+E-1.
+    template <bool X>
+    __device__ __forceinline__ void step(T (&w)[E], T (&x)[E]) const {
+        const int lane = threadIdx.x & 31;
+        // forward: d_i = fm_i d_{i-1} + w_i
+        T L[E];
+        L[0] = w[0];
+#pragma unroll
+        for (int e = 1; e < E; ++e) L[e] = fmaT(fm[e], L[e - 1], w[e]);
+        T c = L[E - 1];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) c = fmaT(fa[l], shfl_dir(c, 1 << l, false), c);
+        T pre = shfl_dir(c, 1, false);
+        if (lane == 0) pre = zero<T>();
+        T d[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) d[e] = fmaT(P[e], pre, L[e]);
+        // backward: x_i = -cp_i x_{i+1} + d_i
+        L[E - 1] = d[E - 1];
+#pragma unroll
+        for (int e = E - 2; e >= 0; --e) L[e] = fmaT(ncp[e], L[e + 1], d[e]);
+        c = L[0];
+#pragma unroll
+        for (int l = 0; l < 5; ++l) c = fmaT(ba[l], shfl_dir(c, 1 << l, true), c);
+        pre = shfl_dir(c, 1, true);
+        if (lane == 31) pre = zero<T>();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            w[e] = fmaT(iQ[e], pre, inv[e] * L[e]);
+            if (X) x[e] = fmaT(Q[e], pre, L[e]);
+        }
+    }
+
+    // `steps` implicit-Euler steps on x.
+    __device__ __forceinline__ void run(T (&x)[E], int steps) const {
+        T w[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) w[e] = inv[e] * x[e];
+        for (int s = 0; s + 1 < steps; ++s) step<false>(w, x);
+        if (steps > 0) step<true>(w, x);
+    }
+};
+
+template <class T>
+__device__ __forceinline__ T load_as(const double *p) {
+    if constexpr (std::is_same<T, float>::value) return d2f_rn(*p);
+    else if constexpr (std::is_same<T, ff>::value) return ff_from_double(*p);
+    else return *p;
+}
+template <class T>
+__device__ __forceinline__ double store_as(T v) {
+    if constexpr (std::is_same<T, float>::value) return f2d(v);
+    else if constexpr (std::is_same<T, ff>::value) return ff_to_double(v);
+    else return v;
+}
+
+// Fine batch on small grids: warp (slice n, member b).
+template <class T, int E>
+__global__ void __launch_bounds__(32) k_heat1d_fine_warp(Heat1dArgs a, const T *__restrict__ fm,
+                                                         const T *__restrict__ inv,
+                                                         const T *__restrict__ cp) {
+    const int b = blockIdx.y;
+    if (!runs(a.st, b)) return;
+    const int n = a.n_first + blockIdx.x;
+    const int M = a.M;
+    const size_t mb = (size_t)b * a.blen;
+    const double *xin = a.x + mb + (size_t)(n - 1) * M;
+    T u[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        const T ld = load_as<T>(xin + min(i, M - 1));
+        u[e] = (i < M) ? ld : zero<T>();
+    }
+    WarpThomas<T, E> f;
+    f.load(fm, inv, cp, M);
+    f.run(u, a.steps);
+    double *yo = a.y + mb + (size_t)n * M;
+    const double *xn = a.x + mb + (size_t)n * M;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        if (i < M) {
+            const double v = store_as<T>(u[e]);
+            if (a.mode == FINE_APPLY) yo[i] = xn[i] - v;
+            else if (a.mode == FINE_RESIDUAL) yo[i] = v - xn[i];
+            else yo[i] = v;
+        }
+    }
+    if (n == 1 && a.mode != 2) {
+        // row 0 of eq. (4): (F X)_0 = x_0; residual: y0 - x_0
+        const double *x0 = a.x + mb;
+        double *y0o = a.y + mb;
+        for (int i = threadIdx.x; i < M; i += 32)
+            y0o[i] = (a.mode == FINE_APPLY) ? x0[i] : a.y0[(size_t)b * M + i] - x0[i];
+    }
+}
+
+// FP64 coarse sweep on small grids, one warp per member:
+// z_0 = q_0, z_n = q_n + G z_{n-1}.
+template <int E>
+__global__ void __launch_bounds__(32) k_heat1d_sweep_warp(const double *q, double *z, int M, int N,
+                                                          size_t blen, int steps,
+                                                          const double *__restrict__ fm,
+                                                          const double *__restrict__ inv,
+                                                          const double *__restrict__ cp,
+                                                          const MemberState *st) {
+    const int b = blockIdx.x;
+    if (!runs(st, b)) return;
+    const size_t mb = (size_t)b * blen;
+    WarpThomas<double, E> f;
+    f.load(fm, inv, cp, M);
+    double zz[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = threadIdx.x * E + e;
+        const double ld = q[mb + min(i, M - 1)];
+        zz[e] = (i < M) ? ld : 0.0;
+        if (i < M) z[mb + i] = ld;
+    }
+    for (int n = 1; n <= N; ++n) {
+        const size_t off = mb + (size_t)n * M;
+        double qn[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = threadIdx.x * E + e;
+            qn[e] = (i < M) ? q[off + i] : 0.0;
+        }
+        f.run(zz, steps);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = threadIdx.x * E + e;
+            if (i < M) {
+                zz[e] += qn[e];
+                z[off + i] = zz[e];
+            } else {
+                zz[e] = 0.0;
+            }
+        }
+    }
+}
+
 // Thomas factors of tridiag(a, 1 - 2a, a), a = -dt nu/h^2.
 void thomas_factors(int M, double r, std::vector<double> &fm, std::vector<double> &inv,
                     std::vector<double> &cp) {
@@ -459,7 +662,62 @@ struct SweepLaunch {
     }
 };
 
+template <class T>
+struct FineWarpLaunch {
+    Problem *p;
+    Heat1dArgs a;
+    int nslices;
+    const DevBuf *fac;
+    cudaStream_t s;
+    template <int E>
+    pit_status run() {
+        const T *base = fac->as<T>();
+        const int M = p->M;
+        k_heat1d_fine_warp<T, E><<<dim3(nslices, p->batch), 32, 0, s>>>(a, base, base + M,
+                                                                         base + 2 * M);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
+};
+
+struct SweepWarpLaunch {
+    Problem *p;
+    const double *q;
+    double *z;
+    const MemberState *st;
+    cudaStream_t s;
+    template <int E>
+    pit_status run() {
+        const double *base = p->coarse_inv64.as<double>();
+        const int M = p->M;
+        k_heat1d_sweep_warp<E><<<p->batch, 32, 0, s>>>(q, z, M, p->N, p->blen, p->coarse_steps,
+                                                       base, base + M, base + 2 * M, st);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
+};
+
+// Points per lane of the one-warp kernels (M <= 256).
+template <class F>
+pit_status dispatch_warp(int M, F &&f) {
+    if (M <= 64) return f.template run<2>();
+    if (M <= 128) return f.template run<4>();
+    return f.template run<8>();
+}
+
 pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStream_t s) {
+    if (p->M <= WARP_MAXM && p->heat1d_small) {
+        if (prec == PIT_FP64) {
+            FineWarpLaunch<double> f{p, a, nslices, &p->fine_inv64, s};
+            return dispatch_warp(p->M, f);
+        }
+        if (prec == PIT_FF) {
+            FineWarpLaunch<ff> f{p, a, nslices, &p->fine_invff, s};
+            return dispatch_warp(p->M, f);
+        }
+        FineWarpLaunch<float> f{p, a, nslices, &p->fine_inv32, s};
+        return dispatch_warp(p->M, f);
+    }
     if (prec == PIT_FP64) {
         FineLaunch<double> f{p, a, nslices, &p->fine_inv64, s};
         return dispatch_1d(p->M, f);
@@ -483,6 +741,10 @@ pit_status heat1d_setup(Problem *p) {
         set_error("heat1d: M > 8192 is not supported");
         return PIT_E_UNSUPPORTED;
     }
+    // grids of M <= 256 points run the one-warp kernels unless
+    // PIT_HEAT1D_SMALL=cta selects the CTA-wide scans
+    const char *sq = getenv("PIT_HEAT1D_SMALL");
+    p->heat1d_small = !(sq && !strcmp(sq, "cta"));
     const double h = 1.0 / (p->M + 1);
     const double rf = (p->dT / p->fine_steps) * p->nu / (h * h);
     const double rc = (p->dT / p->coarse_steps) * p->nu / (h * h);
@@ -531,6 +793,10 @@ pit_status heat1d_fine_one(Problem *p, const double *x, double *y, int prec, cud
 
 pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
                         cudaStream_t s) {
+    if (prec == PIT_FP64 && p->M <= WARP_MAXM && p->heat1d_small) {
+        SweepWarpLaunch f{p, q, z, st, s};
+        return dispatch_warp(p->M, f);
+    }
     if (prec == PIT_FP64) {
         SweepLaunch<double> f{p, q, z, &p->coarse_inv64, st, s};
         return dispatch_1d(p->M, f);

@@ -160,6 +160,7 @@ struct Problem {
     DevBuf fine_inv64, fine_cp64, coarse_inv64, coarse_cp64;
     DevBuf fine_inv32, fine_cp32, coarse_inv32, coarse_cp32;
     DevBuf fine_invff;            // heat1d: fine Thomas factors as float-float (hi, lo) pairs
+    int heat1d_small = 0;         // heat1d, M <= 256: one-warp kernels (else CTA-wide scans)
     double fine_off = 0, coarse_off = 0;   // off-diagonal -dt nu / h^2
 
     // heat2d: sine basis S_jk = sin(pi j k/(n+1)) and coarse mode factors

@@ -77,6 +77,33 @@ def test_heat1d_operators_fp64(case, which):
     np.testing.assert_array_equal(got, dev)
 
 
+SMALL_CASES = [dict(M=1, N=3, fine_steps=4), dict(M=31, N=5, fine_steps=7),
+               dict(M=63, N=16, fine_steps=100, batch=3), dict(M=63, N=400, fine_steps=5),
+               dict(M=128, N=7, fine_steps=9, batch=2), dict(M=200, N=300, fine_steps=3),
+               dict(M=256, N=4, fine_steps=6)]
+
+
+@pytest.mark.parametrize("variant", ["warp", "cta"])
+@pytest.mark.parametrize("case", SMALL_CASES)
+def test_heat1d_small_grid_kernels(variant, case, monkeypatch):
+    """Grids of M <= 256 points: the one-warp kernels (scan multipliers formed
+    once per launch; E = 2, 4, 8 points per lane) and the CTA-wide scans,
+    each in FP64, float-float and FP32, against the oracle."""
+    monkeypatch.setenv("PIT_HEAT1D_SMALL", variant)
+    pit = _pit()
+    w = inputs.heat1d(**case)
+    X = _rand_block(w, 71)
+    with pit.Problem(w, "mixed") as p:
+        got = {which: p.apply(which, X, precision="fp64") for which in ("F", "Ginv", "residual")}
+        ff = p.apply("F", X, precision="ff")
+        f32 = p.apply("F", X, precision="mixed")
+    for which, g in got.items():
+        assert _rel(g, _oracle_apply(w, which, X)) < 1e-13, which
+    refF = _oracle_apply(w, "F", X)
+    assert _rel(ff, refF) < 1e-11
+    assert _rel(f32, refF) < 2e-5
+
+
 @pytest.mark.parametrize("which", ["F", "GinvF"])
 def test_heat1d_operators_fp32_fine(which):
     pit = _pit()
