@@ -531,7 +531,8 @@ def _brief(line):
     out["workload"] = line["config"]["workload"]
     r = line.get("roofline") or {}
     out["roofline"] = {k: r.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit", "frac",
-                                             "frac_executed", "launch_ms", "launches") if k in r}
+                                             "frac_executed", "launch_ms", "launches", "note")
+                       if k in r}
     if "breakdown" in line:
         out["breakdown_share"] = {k: round(v["share"], 4) for k, v in line["breakdown"].items()
                                   if v["calls"]}
@@ -685,6 +686,9 @@ def measure_ours(args, ctx):
                 "refinements": [i["refinements"] for inf in infos for i in inf],
                 "matvecs": [i["matvecs"] for inf in infos for i in inf],
                 "gpu_launches": int(launches), "roofline": roof, "breakdown": breakdown,
+                "timing_note": "timed with per-kernel CUDA events on (per-iteration graphs), "
+                               "which the roofline and breakdown need; e2e runs the "
+                               "uninstrumented loop graph",
                 "serial_fine": {"fp64_s_per_batch": t_ser64, "fp32_s_per_batch": t_ser32,
                                 "fp32_rel_err": e32, "batch": w.batch,
                                 **{f"{k}_s_per_batch": v[0] for k, v in ser.items()},
