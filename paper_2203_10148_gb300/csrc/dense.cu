@@ -970,6 +970,51 @@ pit_status dense_setup(Problem *p) {
         k_copy_f32<<<blocks, 256, 0, s>>>(Res2, p->GLL32.as<float>(), mm2);
         PIT_LAUNCH_CHECK();
     }
+    // The tensor-core sweep of the mixed path (one member, M <= 1024): G and
+    // A_s = G^(L 2^s), s < S, as TF32 (hi, lo) parts, A_0 = G^L by binary
+    // powering and A_s = A_{s-1}^2 (T1..T5 are free here).  PIT_DENSE_SWEEP_TC=0
+    // keeps the CUDA-core sweep.
+    p->dtc_on = false;
+    if (!(getenv("PIT_DENSE_SWEEP_TC") && getenv("PIT_DENSE_SWEEP_TC")[0] == '0') &&
+        dense_tc_sweep_fits(p)) {
+        int L, C, S;
+        dense_tc_sweep_shape(p->N, L, C, S);
+        const int Mp = dense_tc_sweep_padded(M);
+        const size_t mp2 = (size_t)Mp * Mp;
+        if (S <= DTC_SMAX) {
+            PIT_TRY(p->dtc_mats.ensure((size_t)(2 + 2 * S) * mp2 * sizeof(float)));
+            float *mats = p->dtc_mats.as<float>();
+            PIT_TRY(tc_split_tf32(G, mats, mats + mp2, M, Mp, M, Mp, s));
+            double *Res = T1, *Base = T2, *R = T3;
+            PIT_CUDA(cudaMemcpyAsync(Base, G, mm2 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            PIT_CUDA(cudaMemsetAsync(Res, 0, mm2 * sizeof(double), s));
+            k_axpby_identity<<<blocks, 256, 0, s>>>(Res, Res, 0.0, 0.0, 1.0, M);
+            PIT_LAUNCH_CHECK();
+            for (int e = L; e > 0;) {
+                if (e & 1) {
+                    PIT_TRY(mm(h, M, Res, Base, R));
+                    std::swap(Res, R);
+                }
+                e >>= 1;
+                if (e) {
+                    PIT_TRY(mm(h, M, Base, Base, R));
+                    std::swap(Base, R);
+                }
+            }
+            for (int k = 0; k < S; ++k) {
+                if (k > 0) {
+                    PIT_TRY(mm(h, M, Res, Res, R));
+                    std::swap(Res, R);
+                }
+                PIT_TRY(tc_split_tf32(Res, mats + (size_t)(2 + 2 * k) * mp2,
+                                      mats + (size_t)(3 + 2 * k) * mp2, M, Mp, M, Mp, s));
+            }
+            const size_t bytes = 6 * (size_t)128 * Mp * sizeof(float) + 64;
+            PIT_TRY(p->dtc_buf.ensure(bytes));
+            PIT_CUDA(cudaMemsetAsync(p->dtc_buf.ptr, 0, bytes, s));
+            p->dtc_on = true;
+        }
+    }
     // FP32 copies for the mixed path; Phi also as float-float (hi, lo) for
     // the residual product
     {
@@ -1144,6 +1189,10 @@ static pit_status persistent_sweep(Problem *p, const double *q, double *z, const
 pit_status dense_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
                        cudaStream_t s) {
     bool done = false;
+    if (prec == PIT_MIXED && p->dtc_on) {
+        PIT_TRY(dense_tc_sweep(p, q, z, st, s, &done));
+        if (done) return PIT_OK;
+    }
     if (prec == PIT_MIXED) {
         const int L = p->sweep_L, C = (p->N + L) / L;   // ceil((N + 1) / L)
         PIT_TRY(persistent_sweep<float>(p, q, z, p->G32.as<float>(), p->GL32.as<float>(),

@@ -263,6 +263,13 @@ __global__ void k_split_bf16(const double *x, __nv_bfloat16 *hi, __nv_bfloat16 *
 
 static int padded(int M) { return (M + TC_BN - 1) / TC_BN * TC_BN; }
 
+pit_status tc_split_tf32(const double *x, float *hi, float *lo, int rows_src, int rows_out, int M,
+                         int Mp, cudaStream_t s) {
+    k_split_tf32<<<1024, 256, 0, s>>>(x, hi, lo, rows_src, rows_out, M, Mp);
+    PIT_LAUNCH_CHECK();
+    return PIT_OK;
+}
+
 bool dense_tc_supported(const Problem *p) {
     (void)p;   // any M (padded to 128 columns); needs the tensor-map encoder
     return tc_encode_fn() != nullptr;

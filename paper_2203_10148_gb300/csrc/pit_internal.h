@@ -196,6 +196,9 @@ struct Problem {
     bool use_tc = false;          // dense FP32-class product on the tensor cores
     bool dense_bf16 = false;      // ... in split BF16 (PIT_MIXED_BF16) instead of split TF32
     DevBuf PhiBh, PhiBl;          // BF16 splits of Phi
+    bool dtc_on = false;          // dense mixed sweep on the tensor cores (dense_sweep_tc.cu)
+    DevBuf dtc_mats;              // its TF32 (hi, lo) splits of G and of G^(L 2^s), s < S
+    DevBuf dtc_buf;               // its chunk states (ping-pong hi, lo, FP32) and barrier words
 
     // Krylov workspace
     DevBuf X, R, Rt, P, S, D, K, W;
@@ -274,6 +277,17 @@ pit_status add_source_rows(Problem *p, double *y, cudaStream_t s);
 void dense_teardown(Problem *p);
 bool dense_tc_supported(const Problem *p);
 pit_status dense_tc_split_phi(Problem *p);
+// TF32 (hi, lo) parts of the rows_src x M row-major FP64 x into rows_out x Mp
+// arrays (zero outside x)
+pit_status tc_split_tf32(const double *x, float *hi, float *lo, int rows_src, int rows_out, int M,
+                         int Mp, cudaStream_t s);
+// dense mixed sweep on the tensor cores: at most 2^DTC_SMAX chunks
+constexpr int DTC_SMAX = 7;
+void dense_tc_sweep_shape(int N, int &L, int &C, int &S);
+int dense_tc_sweep_padded(int M);
+bool dense_tc_sweep_fits(const Problem *p);
+pit_status dense_tc_sweep(Problem *p, const double *q, double *z, const MemberState *st,
+                          cudaStream_t s, bool *launched);
 pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, int mode,
                           const MemberState *st, cudaStream_t s);
 // 2D heat sine transforms on the tensor cores (xform_tc.cu), 96 <= n <= 256,

@@ -234,3 +234,31 @@ def test_dense_bf16x3_mixed_solve_within_1e6():
         X, info = p.bicgstab_solve(tol=1e-7, tol_mode="rhs", inner_tol=1e-5)
     assert info[0]["status"] == 0
     assert np.linalg.norm(X[0] - lam) / np.linalg.norm(lam) < 1e-6
+
+
+@pytest.mark.parametrize("M,N", [(64, 7), (200, 127), (256, 128), (500, 300), (1000, 1), (1024, 700)])
+def test_dense_tensor_core_sweep(M, N, monkeypatch):
+    """The mixed coarse sweep of one member on the tensor cores (chunked scan
+    of at most 128 chunks, doubling scan of the carries, 3xTF32 products
+    summed over an 8-CTA cluster) against the oracle's sequential forward
+    substitution of eq. (7) and against the CUDA-core chunked scan
+    (PIT_DENSE_SWEEP_TC=0): FP32 accuracy on both, by different arithmetic."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=M, N=N, T=N * 10.0 / 4096, fine_steps=10)
+    X = _rand(w, 17)
+    with pit.Problem(w, "mixed") as p:
+        tc = p.apply("Ginv", X, precision="mixed")
+        tcF = p.apply("GinvF", X, precision="mixed")
+    monkeypatch.setenv("PIT_DENSE_SWEEP_TC", "0")
+    with pit.Problem(w, "mixed") as p:
+        cc = p.apply("Ginv", X, precision="mixed")
+        ccF = p.apply("GinvF", X, precision="mixed")
+    ref = _oracle(w, "Ginv", X)
+    assert _rel(tc, ref) < 2e-5
+    assert _rel(cc, ref) < 2e-5
+    # G^{-1} F also carries the FP32-class fine product, common to both paths:
+    # the tensor-core sweep adds no more than the CUDA-core one
+    refF = _oracle(w, "GinvF", X)
+    assert _rel(tcF, refF) < max(1e-4, 2 * _rel(ccF, refF))
+    if N > 1:
+        assert not np.array_equal(tc, cc)
