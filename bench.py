@@ -403,6 +403,26 @@ def bench_config(args, w, world):
 
 # ----------------------------------------------------------------- roofline
 
+SWEEP_KERNELS = {"heat1d": "k_heat1d_sweep_warp / k_heat1d_sweep (FP64), k_xform_tc + k_rec_* (mixed)",
+                 "heat2d": "k_xform_tc x4 + k_rec_full (tcgen05 sine transforms, mixed)",
+                 "advdiff2d": "k_advdiff_sweep (cooperative, Chebyshev steps, tagged halo exchange)",
+                 "dense": "k_dense_sweep_tc (cooperative 8-CTA clusters, tcgen05) or k_dense_sweep"}
+
+
+def sweep_cost(w, timing, total_ms, steps):
+    """The coarse sweep, reported apart from the fine kernel's roofline as
+    the latency-bound step it is: microseconds per sweep (one sweep covers
+    the whole batch), sweeps per timed step and share of the timed steps."""
+    cls = [k for k in ("sweep_mixed", "sweep_fp64") if timing.get(k, (0, 0.0))[0]]
+    if not cls:
+        return None
+    calls = sum(timing[k][0] for k in cls)
+    ms = sum(timing[k][1] for k in cls)
+    return {"kernel": SWEEP_KERNELS.get(w.kind), "bound": "latency",
+            "us_per_sweep": 1e3 * ms / calls, "sweeps_per_step": calls / max(steps, 1),
+            "share": ms / total_ms}
+
+
 def roofline(w, timing, peaks, nsm):
     """Roofline of the dominant fine-propagator kernel class, from the
     per-class CUDA-event times recorded inside the timed solves."""
@@ -437,7 +457,7 @@ def roofline(w, timing, peaks, nsm):
                     "algorithmic_tflops": flop / (avg_ms / 1e3) / 1e12,
                     "peak_source": f"derived: 128 lanes/clk/SM x {nsm} SMs x {sm_max:.0f} MHz"}
         peak = FP64_LANES_PER_SM * 2 * nsm * sm_max * 1e6 / 1e12
-        return {"bound": "alu", "kernel": "cuBLAS DGEMM (FP64 true residual)",
+        return {"bound": "alu", "kernel": "k_gemm_f64 (FP64 true residual)",
                 "achieved": flop / (avg_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s (FP64)",
                 "frac": flop / (avg_ms / 1e3) / 1e12 / peak, "traffic": None, "launch_ms": avg_ms,
                 "launches": calls, "peak_source": "derived: 4 FP64 flop/clk/SM x SMs x max SM clock"}
@@ -519,7 +539,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "rel_err_max",
+SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "rel_err_max", "sweep",
             "rel_err_lambda_N", "iterations", "refinements", "matvecs", "status", "gpu_launches",
             "e2e", "fp64_path", "latency_s", "capacity_solves_per_s", "rel_err_max_sampled",
             "completed", "failed", "max_running", "fine_slice_steps_per_s", "invalid")
@@ -686,6 +706,7 @@ def measure_ours(args, ctx):
                 "refinements": [i["refinements"] for inf in infos for i in inf],
                 "matvecs": [i["matvecs"] for inf in infos for i in inf],
                 "gpu_launches": int(launches), "roofline": roof, "breakdown": breakdown,
+                "sweep": sweep_cost(w, timing, total_ms, K),
                 "timing_note": "timed with per-kernel CUDA events on (per-iteration graphs), "
                                "which the roofline and breakdown need; e2e runs the "
                                "uninstrumented loop graph",
