@@ -53,7 +53,7 @@ constexpr int DS_BN = 80;                          // MMA N: state rows per clus
 constexpr int DS_TMEM = 128;                       // tensor-memory columns allocated (power of 2)
 constexpr int DS_BK = 32;                          // K per stage (128 bytes of FP32)
 constexpr int DS_CL = 8;                           // CTAs per cluster (K splits)
-constexpr int DS_THREADS = 128;
+constexpr int DS_THREADS = 256;                    // 8 warps: two per 32-lane quarter of TMEM
 constexpr int DS_A_BYTES = DS_BM * DS_BK * 4;      // 16 KB per part
 constexpr int DS_B_BYTES = DS_BN * DS_BK * 4;      // 10 KB per part (1024-byte multiple)
 constexpr int DS_PLD = DS_BN + 1;                  // padded row of the partial tile
@@ -74,7 +74,7 @@ struct DsArgs {
     int M, Mp, N, L, C, S;
     float *ph[2], *pl[2];   // the arrays behind the maps: DS_BM rows of Mp
     float *vf[2];           // FP32 carries of the doubling scan, DS_BM rows of Mp
-    unsigned *bar;          // [0] arrivals, [1] generation
+    unsigned *bar;          // [0] arrivals at the grid barrier, all barriers counted
     int *err;
     const MemberState *st;
 };
@@ -88,34 +88,30 @@ __device__ __forceinline__ void split_tf32(float v, float &hi, float &lo) {
     lo = __uint_as_float(l);
 }
 
-// Grid-wide barrier with a bounded wait (one thread per CTA polls); false
-// when it gave up or another CTA reported an error.  The caller does not
-// leave on a false return at once: the CTAs of a cluster share their
-// status at the next step's cluster barrier and leave together.
-__device__ bool ds_grid_barrier(unsigned *bar, int *err, unsigned nblocks) {
+// Grid-wide barrier with a bounded wait: every CTA adds one to a counter
+// that only grows (a release reduction, no reply awaited) and polls it with
+// acquire loads until it holds every CTA's arrivals so far (`target`, the
+// barrier's number times the grid size); false when the wait gave up or
+// another CTA reported an error.  The caller does not leave on a false
+// return at once: the CTAs of a cluster share their status at the next
+// step's cluster barrier and leave together.
+__device__ bool ds_grid_barrier(unsigned *bar, int *err, unsigned target) {
     __shared__ int res;
     __syncthreads();
     if (threadIdx.x == 0) {
         res = 1;
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > DS_SPIN || *(volatile int *)err) {
-                    atomicExch(err, PIT_E_TIMEOUT);
-                    res = 0;
-                    break;
-                }
-
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        long long spins = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (++spins > DS_SPIN || ((spins & 63) == 0 && *(volatile int *)err)) {
+                atomicExch(err, PIT_E_TIMEOUT);
+                res = 0;
+                break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return res != 0;
@@ -166,6 +162,7 @@ __global__ void __launch_bounds__(DS_THREADS, 1)
     uint32_t uses = 0;        // completed phases of full_bar and acc_bar
     bool local_ok = true;     // this CTA's waits all ended in time
     int nstep = 0;
+    unsigned nbar = 0;        // grid barriers passed
     int resident = -1;        // matrix in bsm: 0 = G, 1 + s = G^(L 2^s), -1 none
     bool loads_out = false;   // a TMA copy of this CTA may be in flight (thread 0)
 
@@ -220,13 +217,15 @@ __global__ void __launch_bounds__(DS_THREADS, 1)
             if (threadIdx.x == 0 && have) loads_out = false;   // the products consumed every copy
             resident = have ? mat : -1;
             if (have) {
-#pragma unroll
-                for (int cc = 0; cc < (DS_BN + 31) / 32; ++cc) {
+                // warp w reads TMEM lanes 32 (w % 4) .. + 31 (chunk columns);
+                // warps 0-3 take columns 0-31 and 64-79, warps 4-7 columns 32-63
+                const int q4 = warp & 3;
+                for (int cc = warp >> 2; cc < (DS_BN + 31) / 32; cc += 2) {
                     float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+                    tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(cc * 32), v);
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (cc * 32 + j < DS_BN) part[(warp * 32 + lane) * DS_PLD + cc * 32 + j] = v[j];
+                        if (cc * 32 + j < DS_BN) part[(q4 * 32 + lane) * DS_PLD + cc * 32 + j] = v[j];
                 }
             }
             ++uses;
@@ -328,7 +327,8 @@ __global__ void __launch_bounds__(DS_THREADS, 1)
         }
         // the next step's TMA copies (async proxy) read what these stores wrote
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        if (!ds_grid_barrier(a.bar, a.err, nblocks)) local_ok = false;
+        ++nbar;
+        if (!ds_grid_barrier(a.bar, a.err, nbar * nblocks)) local_ok = false;
         return true;
     };
 
