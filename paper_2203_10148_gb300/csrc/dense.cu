@@ -402,37 +402,32 @@ struct SweepArgs {
     const T *G, *GL, *GLL;
     T *Za, *Zb, *E;
     T *F0, *F1, *Gc;      // carry scan: running super-chunk values (ping-pong), super-chunk carries
-    unsigned *bar;        // [0] arrivals, [1] generation
+    unsigned *bar;        // [0] arrivals at the grid barrier, all barriers counted
     int *err;
     const MemberState *st;
 };
 
-// Grid-wide barrier with a bounded wait; false when it gave up (error set).
-__device__ bool grid_barrier(unsigned *bar, int *err, unsigned nblocks) {
+// Grid-wide barrier with a bounded wait: every CTA adds one to a counter
+// that only grows (a release reduction, no reply awaited) and polls it with
+// acquire loads until it holds every CTA's arrivals so far (`target`, the
+// barrier's number times the grid size); false when it gave up (error set).
+__device__ bool grid_barrier(unsigned *bar, int *err, unsigned target) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > SW_SPIN_LIMIT || *(volatile int *)err) {
-                    atomicExch(err, PIT_E_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        long long spins = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if (++spins > SW_SPIN_LIMIT || ((spins & 63) == 0 && *(volatile int *)err)) {
+                atomicExch(err, PIT_E_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
@@ -718,6 +713,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
     T *red = GLLs + (size_t)SW_MAXROWS * a.M;   // (SW_THREADS / 32)^2 * SW_MAXROWS partials
     const int r0 = blockIdx.x * a.rows;
     const unsigned nb = gridDim.x;
+    unsigned nbar = 0;   // grid barriers passed
     for (size_t t = threadIdx.x; t < (size_t)SW_MAXROWS * a.M; t += SW_THREADS) {
         const int r = (int)(t / a.M), k = (int)(t % a.M);
         const bool ok = r < a.rows && r0 + r < a.M;     // rows beyond this CTA's share: zero
@@ -733,7 +729,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
         // phase 1: chunk-local recurrences from zero
         for (int i = 0; i < a.L; ++i) {
             sweep_step(a, Gs, in, out, i, i == 0, false, r0, red);
-            if (!grid_barrier(a.bar, a.err, nb)) return;
+            if (!grid_barrier(a.bar, a.err, ++nbar * nb)) return;
             T *t = in; in = out; out = t;
         }
         // phase 2: carries E[c] = u_c + A E[c-1] with A = G^L, u_c = W[c-1] (the
@@ -757,7 +753,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
                      [&](int col, int row) -> T { return u_of(col / C2, (col % C2) * L2 + k, row); },
                      [&](int col, int row, T v) { __stcg(Fo + (size_t)col * M + row, v); },
                      [&](int col) { return (col % C2) * L2 + k < C && member_live(col / C2); }, red);
-            if (!grid_barrier(a.bar, a.err, nb)) return;
+            if (!grid_barrier(a.bar, a.err, ++nbar * nb)) return;
             // columns whose super-chunk ended keep F[s][last] in Fi: copy forward
             // (only full super-chunks feed 2b, so the partial last one needs no copy)
             T *t = Fi; Fi = Fo; Fo = t;
@@ -769,7 +765,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
                      [&](int b, int row) -> T { return ld_cg(Fi + ((size_t)b * C2 + sc - 1) * M + row); },
                      [&](int b, int row, T v) { __stcg(a.Gc + ((size_t)b * C2 + sc) * M + row, v); },
                      [&](int b) { return member_live(b); }, red);
-            if (!grid_barrier(a.bar, a.err, nb)) return;
+            if (!grid_barrier(a.bar, a.err, ++nbar * nb)) return;
         }
         for (int k = 0; k < L2; ++k) {
             gen_step(GLs, M, a.rows, r0, a.batch * C2,
@@ -784,7 +780,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
                          __stcg(a.E + ((size_t)b * C + c) * M + row, v);
                      },
                      [&](int col) { return (col % C2) * L2 + k < C && member_live(col / C2); }, red);
-            if (!grid_barrier(a.bar, a.err, nb)) return;
+            if (!grid_barrier(a.bar, a.err, ++nbar * nb)) return;
         }
         // phase 3 starts from the carries
         in = a.E;
@@ -794,7 +790,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_dense_sweep(SweepArgs<T> a) {
     T *ping = a.Za, *pong = a.Zb;
     for (int i = 0; i < a.L; ++i) {
         sweep_step(a, Gs, in, out, i, a.C == 1 && i == 0, true, r0, red);
-        if (!grid_barrier(a.bar, a.err, nb)) return;
+        if (!grid_barrier(a.bar, a.err, ++nbar * nb)) return;
         in = out;
         out = (out == ping) ? pong : ping;
     }

@@ -356,10 +356,9 @@ __global__ void __launch_bounds__(NT) k_heat1d_sweep(const double *q, double *z,
 // per level, and every point's value is one independent multiply-add from
 // the lane's incoming value.  The state between steps is w = inv .* u (the
 // right-hand side of the forward recurrence), formed in the backward fix-up
-// off the dependent chain.  Per step: 2 (E - 1) + 12 dependent operations.
-// (Each dependent FP64 operation costs about 120 cycles on this part
-// whatever the number of active lanes, so the chain length, not the lane
-// count, sets the time of these latency-bound small-grid solves.)
+// off the dependent chain.  Per step: 2 (E - 1) + 12 dependent operations
+// and 12 warp shuffles; the small-grid solves are bound by that chain (FP64
+// result latency and shuffles), not by the FP64 pipe's throughput.
 constexpr int WARP_MAXM = 256;
 
 template <class T, int E>
