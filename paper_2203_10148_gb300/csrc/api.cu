@@ -721,6 +721,15 @@ pit_status from_device(Problem *p, double *dst, const double *src, int on_device
     return PIT_OK;
 }
 
+// The copy stream and events of the early copy of a solution to host memory.
+pit_status ensure_copy_stream(Problem *p) {
+    if (p->copy_stream) return PIT_OK;
+    PIT_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    PIT_CUDA(cudaEventCreateWithFlags(&p->x_ready, cudaEventDisableTiming));
+    PIT_CUDA(cudaEventCreateWithFlags(&p->x_copied, cudaEventDisableTiming));
+    return PIT_OK;
+}
+
 bool all_finite(const double *v, size_t n) {
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(v[i])) return false;
@@ -946,6 +955,9 @@ pit_status pit_problem_destroy(pit_problem_t h) {
     for (DevBuf *b : bufs) b->release();
     dense_teardown(p);
     p->timer.destroy();
+    if (p->x_ready) cudaEventDestroy(p->x_ready);
+    if (p->x_copied) cudaEventDestroy(p->x_copied);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->stream && p->own_stream) cudaStreamDestroy(p->stream);
     delete h;
     return PIT_OK;
@@ -1110,7 +1122,30 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
         std::vector<char> done(B, 0);
         int hc = 0;
         const int rounds = std::max(1, o->refine_max);
+        // To host memory, the solution goes out while its own true residual
+        // is computed (after the first correction): the check reads X and
+        // the copy reads X, and a round that goes on waits for the copy
+        // before it changes X.  When the check passes, the copy is the
+        // result; the call returns once it has landed.
+        bool copy_in_flight = false;
+        // whatever way the call leaves, no copy may still be writing the
+        // caller's buffer
+        struct CopyWait {
+            Problem *p;
+            const bool *live;
+            ~CopyWait() {
+                if (*live) cudaEventSynchronize(p->x_copied);
+            }
+        } copy_wait{p, &copy_in_flight};
         for (int round = 0; round <= rounds; ++round) {
+            if (!on_device && round > 0) {
+                PIT_TRY(ensure_copy_stream(p));
+                PIT_CUDA(cudaEventRecord(p->x_ready, s));
+                PIT_CUDA(cudaStreamWaitEvent(p->copy_stream, p->x_ready, 0));
+                PIT_CUDA(cudaMemcpyAsync(Xu, Xo, vb, cudaMemcpyDeviceToHost, p->copy_stream));
+                PIT_CUDA(cudaEventRecord(p->x_copied, p->copy_stream));
+                copy_in_flight = true;
+            }
             PIT_TRY(timed_F(p, Xo, Wr, FINE_RESIDUAL, rprec, nullptr, s));
             PIT_TRY(timed_sweep(p, Wr, Wr, PIT_MIXED, nullptr, s));
             PIT_TRY(member_norms(p, Wr, rtrue, s));
@@ -1143,6 +1178,11 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
                     PIT_CUDA(cudaMemsetAsync(Wr + (size_t)b * p->blen, 0,
                                              p->blen * sizeof(double), s));
             PIT_CUDA(cudaMemsetAsync(p->X.ptr, 0, vb, s));
+            if (copy_in_flight) {
+                // X changes at the end of this round: the copy must have read it
+                PIT_CUDA(cudaStreamWaitEvent(s, p->x_copied, 0));
+                copy_in_flight = false;
+            }
             LoopOut lo;
             PIT_TRY(run_bicgstab(p, PIT_MIXED, o->inner_tol, nullptr, o->restart_eps0,
                                  o->max_iter, true, s, nullptr, 0, 0, lo));
@@ -1166,7 +1206,12 @@ pit_status pit_bicgstab_solve(pit_problem_t h, const pit_solve_opts *o, double *
             }
             PIT_TRY(kr_axpy(p, Xo, p->X.as<double>(), s));
         }
-        PIT_TRY(from_device(p, Xu, Xo, on_device, s));
+        if (copy_in_flight) {
+            copy_in_flight = false;
+            PIT_CUDA(cudaEventSynchronize(p->x_copied));   // the final X, already on its way
+        } else {
+            PIT_TRY(from_device(p, Xu, Xo, on_device, s));
+        }
         PIT_CUDA(cudaStreamSynchronize(s));
         for (int b = 0; b < B; ++b) {
             inf[b].status = status[b];

@@ -152,6 +152,8 @@ struct Problem {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = true;       // false: the stream belongs to a serving slot
+    cudaStream_t copy_stream = nullptr;   // copy of the solution to host memory, beside the last check
+    cudaEvent_t x_ready = nullptr, x_copied = nullptr;
     const volatile int *cancel = nullptr;   // serving: nonzero asks the solve to stop
 
     DevBuf y0;                    // batch*M
