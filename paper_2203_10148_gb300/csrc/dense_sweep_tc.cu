@@ -23,14 +23,15 @@
 // shared memory, of the matrix rows (the B operand; G stays for the 2L
 // steps that use it); one thread issues the 3xTF32 tcgen05.mma products
 // (M = 128, N = 80, K = 8) into a tensor-memory accumulator stage by stage as
-// the copies land; the four warps move it to shared memory, the cluster
+// the copies land; the eight warps move it to shared memory, the cluster
 // sums its eight partial tiles through distributed shared memory in a fixed
 // order (each CTA 16 chunk columns), adds the step's term, writes the next
 // chunk states (split again) and, in phase 3, z; a bounded grid barrier
 // ends the step.  Every wait is bounded; the CTAs of a cluster post their
-// status before each cluster barrier and leave together.  Arithmetic: split TF32 products (about 2^-21 relative per
-// product) accumulated in FP32, FP32 sums: an FP32-class sweep, like the
-// CUDA-core one it replaces (the sweep only preconditions).
+// status before each cluster barrier and leave together.  Arithmetic: split
+// TF32 products (about 2^-21 relative per product) accumulated in FP32, FP32
+// sums: an FP32-class sweep, like the CUDA-core one it replaces (the sweep
+// only preconditions).
 #include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
