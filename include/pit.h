@@ -487,12 +487,20 @@ pit_status pit_selftest_convert(const double *in, int n, float *f32, double *bac
 #define PIT_TIME_KRYLOV      4   /* fused BiCGStab vector kernels and finishers */
 #define PIT_TIME_FINE_FF     5   /* fine batch, float-float stepping (one kernel per call) */
 #define PIT_TIME_FINE_SPLIT  6   /* fine batch, split RK4 stepping (one kernel per call) */
-#define PIT_TIME_CLASSES     7
+#define PIT_TIME_INNER       7   /* with pit_set_timing(prob, 2): each launch of a solve's
+                                    BiCGStab iterations as a whole (loop graph, iteration
+                                    graph or eager iteration) */
+#define PIT_TIME_CLASSES     8
 
 /*
  * enable = 1: every later operator application of this problem is bracketed
  * by CUDA events on the stream it runs on, and the elapsed times are summed
- * per class; enable = 0 stops recording.  Resets the sums.
+ * per class (the BiCGStab iterations then replay one graph per iteration,
+ * so that each application inside them can be timed); enable = 2: only the
+ * applications outside the iterations (true residuals, the initial sweep)
+ * are timed by class, and each launch of the iterations -- which then run
+ * as the loop graph, as without timing -- as a whole, in PIT_TIME_INNER;
+ * enable = 0 stops recording.  Resets the sums.
  */
 pit_status pit_set_timing(pit_problem_t prob, int enable);
 

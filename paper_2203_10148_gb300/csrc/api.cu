@@ -627,6 +627,23 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
         PIT_TRY(timed_sweep(p, R, R, prec, nullptr, s));
     }
     PIT_TIMED(p, PIT_TIME_KRYLOV, s, kr_init(p, tol_rel, abs_thresh, eps0, max_iter, s));
+    // top-level timing: the iterations run untimed (and so as the loop
+    // graph), each of their launches timed as a whole
+    const bool inner_whole = p->timer.enabled && p->timer.top_only;
+    struct TimerOff {
+        OpTimer *t;
+        bool on;
+        ~TimerOff() {
+            if (on) t->enabled = true;
+        }
+    } timer_off{&p->timer, inner_whole};
+    if (inner_whole) p->timer.enabled = false;
+    auto inner_begin = [&](OpTimer::Rec &r) -> pit_status {
+        return inner_whole ? p->timer.begin(PIT_TIME_INNER, s, r) : PIT_OK;
+    };
+    auto inner_end = [&](OpTimer::Rec &r) -> pit_status {
+        return inner_whole ? p->timer.end(r, s) : PIT_OK;
+    };
     HostStates hs;
     PIT_TRY(hs.init(p->batch));
     int hc = history_offset;
@@ -684,7 +701,10 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
                 PIT_TRY(loop_graph_ready(p, *lg, s, iteration));
                 if (lg->exec) {
                     PIT_CUDA(cudaMemsetAsync(p->loopctl.ptr, 0, sizeof(int), s));
+                    OpTimer::Rec ri{};
+                    PIT_TRY(inner_begin(ri));
                     PIT_CUDA(cudaGraphLaunch(lg->exec, s));
+                    PIT_TRY(inner_end(ri));
                     looped = true;
                     continue;
                 }
@@ -692,7 +712,10 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
             if (!g->failed) {
                 PIT_TRY(iter_graph_ready(p, *g, s, iteration));
                 if (g->exec) {
+                    OpTimer::Rec ri{};
+                    PIT_TRY(inner_begin(ri));
                     PIT_CUDA(cudaGraphLaunch(g->exec, s));
+                    PIT_TRY(inner_end(ri));
                     g_launches += g->kernels;
                     out.graph_iterations += 1;
                     collect = g->timed;
@@ -701,7 +724,12 @@ pit_status run_bicgstab(Problem *p, int prec, double tol_rel, const double *abs_
                 }
             }
         }
-        PIT_TRY(iteration());
+        {
+            OpTimer::Rec ri{};
+            PIT_TRY(inner_begin(ri));
+            PIT_TRY(iteration());
+            PIT_TRY(inner_end(ri));
+        }
         ++done;
     }
     out.final_states = hs.v;
@@ -1348,6 +1376,7 @@ pit_status pit_set_timing(pit_problem_t h, int enable) {
     }
     h->p.timer.reset();
     h->p.timer.enabled = enable != 0;
+    h->p.timer.top_only = enable == 2;
     return PIT_OK;
 }
 

@@ -106,6 +106,7 @@ struct ReduceLayout {
 // Event timing of operator applications (diagnostics).
 struct OpTimer {
     bool enabled = false;
+    bool top_only = false;   // pit_set_timing(prob, 2): BiCGStab iterations timed as a whole
     struct Rec {
         int cls;
         cudaEvent_t a, b;

@@ -107,7 +107,7 @@ EXPORTS = ["pit_default_opts", "pit_version", "pit_last_error", "pit_problem_cre
            "pit_problem_set_source"]
 
 TIME_CLASSES = {"fine_fp32": 0, "fine_fp64": 1, "sweep_mixed": 2, "sweep_fp64": 3, "krylov": 4,
-                "fine_ff": 5, "fine_split": 6}
+                "fine_ff": 5, "fine_split": 6, "inner": 7}
 
 
 def lib_path() -> str:
@@ -339,7 +339,10 @@ class Problem:
         p, dev, _ = _array_arg(f)
         check(load().pit_problem_set_source(self.handle, p, dev))
 
-    def set_timing(self, enable: bool = True):
+    def set_timing(self, enable=True):
+        """pit_set_timing: True (or 1) times every operator class; 2 times the
+        top-level launches and each launch of the BiCGStab iterations as a
+        whole ("inner"), which then run as the uninstrumented loop graph."""
         check(load().pit_set_timing(self.handle, int(enable)))
 
     def timing(self) -> dict:
