@@ -447,11 +447,22 @@ def roofline(w, timing, peaks, nsm, sub_timing=None):
                     "traffic": None, "launch_ms": avg_ms, "launches": calls,
                     "algorithmic_tflops": flop / (avg_ms / 1e3) / 1e12,
                     "peak_source": "measured bf16 burst x 0.5 (nominal TF32/BF16 ratio), of measured"}
+        tc = None
+        t32 = (sub_timing or timing).get("fine_fp32", (0, 0.0))
+        if t32[0]:
+            # the inner solves' split-TF32 tcgen05 product (with its operand split)
+            tms = t32[1] / t32[0]
+            tpeak = 0.5 * (peaks or {}).get("bf16_tflops", 1900.0)
+            tc = {"kernel": "k_gemm_tf32x3_p (tcgen05, persistent)", "launch_ms": tms,
+                  "tflops_executed": 3.0 * flop / (tms / 1e3) / 1e12,
+                  "frac_executed": 3.0 * flop / (tms / 1e3) / 1e12 / tpeak,
+                  "peak": tpeak, "peak_source": "measured bf16 burst x 0.5 (nominal TF32/BF16 ratio)"}
         if dom == "fine_ff":
             # compensated float-float product: 12 FP32 lane-ops per multiply-add
             peak = FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12
             ops = 12.0 * flop / 2.0
             return {"bound": "alu", "kernel": "k_gemm_ff (float-float true residual)",
+                    "tensor_product": tc,
                     "achieved": ops / (avg_ms / 1e3) / 1e12, "peak": peak,
                     "unit": "Tops/s (FP32 pipe lane-ops)",
                     "frac": ops / (avg_ms / 1e3) / 1e12 / peak, "traffic": None,

@@ -16,18 +16,22 @@
 // product against about 2^-21 for split TF32, at twice the MMA rate and half
 // the operand bytes.
 //
-// Kernel structure: one 128 x 128 output tile per CTA, K in 32-element
-// (128-byte) stages, 3-stage ring in shared memory filled by TMA
+// Kernel structure: 128 x 128 output tiles, K in 32-element (128-byte)
+// stages through a 3-stage shared-memory ring filled by TMA
 // (cp.async.bulk.tensor, 128-byte swizzle) and drained by tcgen05.mma
-// (kind::tf32, M = 128, N = 128, K = 8 per instruction) issued by one
-// thread; the FP32 accumulator lives in tensor memory (128 columns) and is
-// read back by four warps with tcgen05.ld.  mbarriers hand stages between
-// the TMA thread, the MMA thread and the tensor core; every wait is
-// bounded and reports PIT_E_TIMEOUT through the problem's error word.
+// (kind::tf32, M = N = 128, K = 8 per instruction) issued by one thread; one
+// persistent CTA per SM loops over the tiles with two FP32 accumulators in
+// tensor memory (128 columns each), so four epilogue warps read one back
+// with tcgen05.ld while the next tile's products fill the other.  mbarriers
+// hand stages and accumulators between the TMA thread, the MMA thread, the
+// tensor core and the epilogue; every wait is bounded and reports
+// PIT_E_TIMEOUT through the problem's error word.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "pit_internal.h"
 #include "stencil_arith.cuh"
@@ -36,10 +40,9 @@
 namespace pit {
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_STAGES = 3, TC_THREADS = 128;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32, TC_STAGES = 3;
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;                  // 16 KB per operand tile
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;                 // Ah, Al, Bh, Bl
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;  // + alignment + barriers
 // Instruction descriptors: D = F32, A = B = TF32 (or BF16), both K-major, M = 128, N = 128.
 constexpr uint32_t kIdesc = tc_idesc_tf32(TC_BM, TC_BN);
 constexpr uint32_t kIdescBf = tc_idesc_bf16(TC_BM, TC_BN);
@@ -67,21 +70,90 @@ struct TcEpilogue {
     const MemberState *st;
 };
 
+// Epilogue of one warp: the 32 tile rows m0 + row0 + lane (TMEM lanes of
+// the warp's quarter, from column address `taddr`) times 128 columns from n0,
+// 32 columns at a time: tcgen05.ld gives a lane one row; the values go
+// through the warp's padded shared-memory tile `stg` (32 x 33 floats) so
+// that, row by row, the 32 lanes read x and write y as 32 consecutive
+// columns (coalesced).
+__device__ __forceinline__ void store_tile_rows(const TcEpilogue &ep, float *stg, uint32_t taddr,
+                                                int m0, int row0, int n0, int R, int lane) {
+    // this lane's tile row (member, slice, liveness), broadcast row by row below
+    const int nb1 = ep.N + 1;
+    const int myrow = m0 + row0 + lane;
+    const int myb = myrow / nb1, myn = myrow % nb1;
+    const bool mylive = myrow < R && myn < ep.N &&
+                        (ep.st == nullptr || (ep.st[myb].active && !ep.st[myb].skip && !ep.st[myb].half));
+    const unsigned livemask = __ballot_sync(0xffffffffu, mylive);
+    for (int cchunk = 0; cchunk < TC_BN / 32; ++cchunk) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(cchunk * 32), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
+        __syncwarp();
+        const int c = n0 + cchunk * 32 + lane;
+        const bool col_ok = c < ep.M;
+        // all x loads of the 32 rows first (independent, in flight together)
+        double xn[32];
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) {
+            const int b = __shfl_sync(0xffffffffu, myb, rr), n = __shfl_sync(0xffffffffu, myn, rr);
+            const bool ok = ((livemask >> rr) & 1u) && col_ok;
+            xn[rr] = ok ? ep.x[(size_t)b * ep.blen + (size_t)(n + 1) * ep.M + c] : 0.0;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 32; ++rr) {
+            const int b = __shfl_sync(0xffffffffu, myb, rr), n = __shfl_sync(0xffffffffu, myn, rr);
+            if (!((livemask >> rr) & 1u) || !col_ok) continue;
+            const float cv = stg[rr * 33 + lane];
+            const size_t mb = (size_t)b * ep.blen;
+            if (ep.y32) {
+                ep.y32[mb + (size_t)(n + 1) * ep.M + c] = d2f_rn(xn[rr]) - cv;
+                if (n == 0) ep.y32[mb + c] = d2f_rn(ep.x[mb + c]);   // row 0 of eq. (4): x_0
+            } else {
+                const double f = f2d(cv);
+                ep.y[mb + (size_t)(n + 1) * ep.M + c] = (ep.mode == FINE_APPLY) ? xn[rr] - f : f - xn[rr];
+                if (n == 0) {
+                    // row 0 of eq. (4): x_0 (or y0 - x_0)
+                    const double x0 = ep.x[mb + c];
+                    ep.y[mb + c] = (ep.mode == FINE_APPLY) ? x0 : ep.y0[(size_t)b * ep.M + c] - x0;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Persistent form: one CTA per SM loops over the output tiles (tile t =
+// blockIdx.x, + gridDim.x, ...).  Warp 0 (one thread) streams the K stages
+// of every tile through the 3-stage ring by TMA; warp 1 (one thread) issues
+// the products into one of two tensor-memory accumulators (128 columns each)
+// in turn; warps 2-5 drain the other accumulator through the epilogue (warp
+// w reads the TMEM lanes of quarter w % 4), so a tile's stores overlap the
+// next tile's products.  mbarriers: stage full / empty, accumulator full
+// (the MMA commit) / empty (one arrival per epilogue warp).  Every wait is
+// bounded; at exit the copies and products still in flight are drained.
+constexpr int TP_EPI = 4;                                          // epilogue warps
+constexpr int TP_THREADS = 64 + 32 * TP_EPI;
+constexpr int TP_STG = TP_EPI * 32 * 33 * 4;                       // epilogue staging tiles
+constexpr int TP_SMEM = TC_STAGES * TC_STAGE_BYTES + TP_STG + 1024 + 256;
+
 template <bool BF>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                  int K, int R, TcEpilogue ep, int *err) {
+__global__ void __launch_bounds__(TP_THREADS, 1)
+    k_gemm_tf32x3_p(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                    int K, int R, int ntn, int ntiles, TcEpilogue ep, int *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // 1024-byte aligned stage ring (the 128-byte swizzle repeats every 1024 bytes)
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + TC_STAGES * TC_STAGE_BYTES);
+    float *stg_all = reinterpret_cast<float *>(base + TC_STAGES * TC_STAGE_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + TC_STAGES * TC_STAGE_BYTES + TP_STG);
     uint64_t *empty = full + TC_STAGES;
-    uint64_t *accum = empty + TC_STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
+    uint64_t *accf = empty + TC_STAGES;     // [2] accumulator complete
+    uint64_t *acce = accf + 2;              // [2] accumulator drained
+    uint64_t *fin = acce + 2;               // the MMA thread's last products, at exit
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fin + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
     constexpr int BKE = BF ? TC_BK_BF : TC_BK;   // K elements per stage
     const int KB = K / BKE;
 
@@ -90,14 +162,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], TP_EPI);
+        }
+        mbar_init(fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(TC_BN));
+                     "r"(2 * TC_BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -105,123 +181,104 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    int last_kb[TC_STAGES];
-#pragma unroll
-    for (int s = 0; s < TC_STAGES; ++s) last_kb[s] = -1;
     if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb % TC_STAGES;
-            const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u, err)) break;
-            unsigned char *st = base + s * TC_STAGE_BYTES;
-            mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-            tma_load_2d(st, &tmAh, kb * BKE, m0, &full[s]);
-            tma_load_2d(st + TC_TILE_BYTES, &tmAl, kb * BKE, m0, &full[s]);
-            tma_load_2d(st + 2 * TC_TILE_BYTES, &tmBh, kb * BKE, n0, &full[s]);
-            tma_load_2d(st + 3 * TC_TILE_BYTES, &tmBl, kb * BKE, n0, &full[s]);
-            last_kb[s] = kb;
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: three TF32 products per K step, one accumulator
+        // TMA producer over every tile's K stages
+        int it = 0;
+        int last_it[TC_STAGES];
+#pragma unroll
+        for (int s = 0; s < TC_STAGES; ++s) last_it[s] = -1;
         bool ok = true;
-        for (int kb = 0; kb < KB && ok; ++kb) {
-            const int s = kb % TC_STAGES;
-            const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, err)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            unsigned char *st = base + s * TC_STAGE_BYTES;
-            const uint64_t ah = smem_desc(st), al = smem_desc(st + TC_TILE_BYTES);
-            const uint64_t bh = smem_desc(st + 2 * TC_TILE_BYTES), bl = smem_desc(st + 3 * TC_TILE_BYTES);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                // 8 TF32 or 16 BF16 = 32 bytes along K per instruction
-                const uint64_t adv = (uint64_t)(j * 32) >> 4;
-                if constexpr (BF) {
-                    tc_mma_f16(tmem, ah + adv, bh + adv, kIdescBf, (kb > 0 || j > 0) ? 1u : 0u);
-                    tc_mma_f16(tmem, ah + adv, bl + adv, kIdescBf, 1u);
-                    tc_mma_f16(tmem, al + adv, bh + adv, kIdescBf, 1u);
-                } else {
-                    mma_tf32(tmem, ah + adv, bh + adv, (kb > 0 || j > 0) ? 1u : 0u);
-                    mma_tf32(tmem, ah + adv, bl + adv, 1u);
-                    mma_tf32(tmem, al + adv, bh + adv, 1u);
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int m0 = (tile / ntn) * TC_BM, n0 = (tile % ntn) * TC_BN;
+            for (int kb = 0; kb < KB; ++kb, ++it) {
+                const int s = it % TC_STAGES;
+                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, err)) {
+                    ok = false;
+                    break;
                 }
+                unsigned char *st = base + s * TC_STAGE_BYTES;
+                mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+                tma_load_2d(st, &tmAh, kb * BKE, m0, &full[s]);
+                tma_load_2d(st + TC_TILE_BYTES, &tmAl, kb * BKE, m0, &full[s]);
+                tma_load_2d(st + 2 * TC_TILE_BYTES, &tmBh, kb * BKE, n0, &full[s]);
+                tma_load_2d(st + 3 * TC_TILE_BYTES, &tmBl, kb * BKE, n0, &full[s]);
+                last_it[s] = it;
             }
-            mma_commit(&empty[s]);            // stage free once these products finish
         }
-        mma_commit(accum);                    // accumulator complete
-    }
-    // epilogue: four warps, warp w reads TMEM lanes 32w..32w+31 (tile rows)
-    __syncwarp();
-    // warp-uniform: tcgen05.ld is a warp-collective instruction
-    const bool have = __all_sync(0xffffffffu, mbar_wait(accum, 0u, err) ? 1 : 0) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (have) {
-        // Each warp drains its 32 tile rows 32 columns at a time: tcgen05.ld
-        // gives a lane one row; the values go through a padded shared-memory
-        // tile (the stage ring is free once the products are complete) so
-        // that, row by row, the 32 lanes read x and write y as 32 consecutive
-        // columns (coalesced).
-        float *stg = reinterpret_cast<float *>(base) + warp * 32 * 33;
-        // this lane's tile row (member, slice, liveness), broadcast row by row below
-        const int nb1 = ep.N + 1;
-        const int myrow = m0 + warp * 32 + lane;
-        const int myb = myrow / nb1, myn = myrow % nb1;
-        const bool mylive = myrow < R && myn < ep.N &&
-                            (ep.st == nullptr || (ep.st[myb].active && !ep.st[myb].skip && !ep.st[myb].half));
-        const unsigned livemask = __ballot_sync(0xffffffffu, mylive);
-        for (int cchunk = 0; cchunk < TC_BN / 32; ++cchunk) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cchunk * 32), v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) stg[lane * 33 + i] = v[i];
-            __syncwarp();
-            const int c = n0 + cchunk * 32 + lane;
-            const bool col_ok = c < ep.M;
-            // all x loads of the 32 rows first (independent, in flight together)
-            double xn[32];
-#pragma unroll
-            for (int rr = 0; rr < 32; ++rr) {
-                const int b = __shfl_sync(0xffffffffu, myb, rr), n = __shfl_sync(0xffffffffu, myn, rr);
-                const bool ok = ((livemask >> rr) & 1u) && col_ok;
-                xn[rr] = ok ? ep.x[(size_t)b * ep.blen + (size_t)(n + 1) * ep.M + c] : 0.0;
-            }
-#pragma unroll
-            for (int rr = 0; rr < 32; ++rr) {
-                const int b = __shfl_sync(0xffffffffu, myb, rr), n = __shfl_sync(0xffffffffu, myn, rr);
-                if (!((livemask >> rr) & 1u) || !col_ok) continue;
-                const float cv = stg[rr * 33 + lane];
-                const size_t mb = (size_t)b * ep.blen;
-                if (ep.y32) {
-                    ep.y32[mb + (size_t)(n + 1) * ep.M + c] = d2f_rn(xn[rr]) - cv;
-                    if (n == 0) ep.y32[mb + c] = d2f_rn(ep.x[mb + c]);   // row 0 of eq. (4): x_0
-                } else {
-                    const double f = f2d(cv);
-                    ep.y[mb + (size_t)(n + 1) * ep.M + c] = (ep.mode == FINE_APPLY) ? xn[rr] - f : f - xn[rr];
-                    if (n == 0) {
-                        // row 0 of eq. (4): x_0 (or y0 - x_0)
-                        const double x0 = ep.x[mb + c];
-                        ep.y[mb + c] = (ep.mode == FINE_APPLY) ? x0 : ep.y0[(size_t)b * ep.M + c] - x0;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-    if (warp == 0 && lane == 0) {
-        // no TMA copy of this CTA may still be writing shared memory at exit
+        // no copy of this CTA may still be writing shared memory at exit
 #pragma unroll
         for (int s = 0; s < TC_STAGES; ++s)
-            if (last_kb[s] >= 0) mbar_wait(&full[s], (uint32_t)(last_kb[s] / TC_STAGES) & 1u, err);
+            if (last_it[s] >= 0) tc_mbar_drain(&full[s], (uint32_t)(last_it[s] / TC_STAGES) & 1u);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: three products per K step into accumulator b = tile count % 2
+        int it = 0, tc = 0;
+        bool ok = true, issued = false;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tc) {
+            const int b = tc & 1;
+            const uint32_t use = (uint32_t)(tc >> 1);
+            if (!mbar_wait(&acce[b], (use & 1u) ^ 1u, err)) break;   // the epilogue drained b
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + (uint32_t)(b * TC_BN);
+            for (int kb = 0; kb < KB; ++kb, ++it) {
+                const int s = it % TC_STAGES;
+                const uint32_t ph = (uint32_t)(it / TC_STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph, err)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char *st = base + s * TC_STAGE_BYTES;
+                const uint64_t ah = smem_desc(st), al = smem_desc(st + TC_TILE_BYTES);
+                const uint64_t bh = smem_desc(st + 2 * TC_TILE_BYTES), bl = smem_desc(st + 3 * TC_TILE_BYTES);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t adv = (uint64_t)(j * 32) >> 4;   // 32 bytes along K
+                    if constexpr (BF) {
+                        tc_mma_f16(acc, ah + adv, bh + adv, kIdescBf, (kb > 0 || j > 0) ? 1u : 0u);
+                        tc_mma_f16(acc, ah + adv, bl + adv, kIdescBf, 1u);
+                        tc_mma_f16(acc, al + adv, bh + adv, kIdescBf, 1u);
+                    } else {
+                        mma_tf32(acc, ah + adv, bh + adv, (kb > 0 || j > 0) ? 1u : 0u);
+                        mma_tf32(acc, ah + adv, bl + adv, 1u);
+                        mma_tf32(acc, al + adv, bh + adv, 1u);
+                    }
+                }
+                issued = true;
+                mma_commit(&empty[s]);          // the stage is free once these products finish
+            }
+            if (!ok) break;
+            mma_commit(&accf[b]);               // accumulator b complete
+        }
+        if (issued) {
+            // every product of this CTA done before the accumulators are freed
+            mma_commit(fin);
+            tc_mbar_drain(fin, 0u);
+        }
+    } else if (warp >= 2) {
+        // epilogue warps: quarter q of the tile rows
+        const int q = warp & 3;
+        float *stg = stg_all + (warp - 2) * 32 * 33;
+        int tc = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tc) {
+            const int b = tc & 1;
+            const uint32_t use = (uint32_t)(tc >> 1);
+            const bool have = __all_sync(0xffffffffu, mbar_wait(&accf[b], use & 1u, err) ? 1 : 0) != 0;
+            if (!have) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (tile / ntn) * TC_BM, n0 = (tile % ntn) * TC_BN;
+            store_tile_rows(ep, stg, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN), m0,
+                            q * 32, n0, R, lane);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN));
     }
 }
 
@@ -324,10 +381,15 @@ pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, in
         PIT_TRY(make_map(&tBl, p->PhiTl.as<float>(), Mp, Mp, false));
     }
     TcEpilogue ep{x, y, y32, p->y0.as<double>(), p->N, M, p->batch, mode, p->blen, st};
-    auto kern = bf ? k_gemm_tf32x3<true> : k_gemm_tf32x3<false>;
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    dim3 grid((R + TC_BM - 1) / TC_BM, Mp / TC_BN);
-    kern<<<grid, TC_THREADS, TC_SMEM, s>>>(tAh, tAl, tBh, tBl, Mp, R, ep, p->errword.as<int>());
+    // persistent: one CTA per SM over all output tiles
+    const int ntn = Mp / TC_BN, ntiles = (R + TC_BM - 1) / TC_BM * ntn;
+    int dev = 0, sms = 0;
+    PIT_CUDA(cudaGetDevice(&dev));
+    PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto kern = bf ? k_gemm_tf32x3_p<true> : k_gemm_tf32x3_p<false>;
+    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM));
+    kern<<<std::min(ntiles, sms), TP_THREADS, TP_SMEM, s>>>(tAh, tAl, tBh, tBl, Mp, R, ntn, ntiles, ep,
+                                                           p->errword.as<int>());
     PIT_LAUNCH_CHECK();
     return PIT_OK;
 }
