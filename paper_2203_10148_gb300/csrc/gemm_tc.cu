@@ -72,12 +72,13 @@ struct TcEpilogue {
 
 // Epilogue of one warp: the 32 tile rows m0 + row0 + lane (TMEM lanes of
 // the warp's quarter, from column address `taddr`) times 128 columns from n0,
-// 32 columns at a time: tcgen05.ld gives a lane one row; the values go
+// 32 columns at a time (nchunks of them): tcgen05.ld gives a lane one row; the values go
 // through the warp's padded shared-memory tile `stg` (32 x 33 floats) so
 // that, row by row, the 32 lanes read x and write y as 32 consecutive
 // columns (coalesced).
 __device__ __forceinline__ void store_tile_rows(const TcEpilogue &ep, float *stg, uint32_t taddr,
-                                                int m0, int row0, int n0, int R, int lane) {
+                                                int m0, int row0, int n0, int R, int lane,
+                                                int nchunks = TC_BN / 32) {
     // this lane's tile row (member, slice, liveness), broadcast row by row below
     const int nb1 = ep.N + 1;
     const int myrow = m0 + row0 + lane;
@@ -85,7 +86,7 @@ __device__ __forceinline__ void store_tile_rows(const TcEpilogue &ep, float *stg
     const bool mylive = myrow < R && myn < ep.N &&
                         (ep.st == nullptr || (ep.st[myb].active && !ep.st[myb].skip && !ep.st[myb].half));
     const unsigned livemask = __ballot_sync(0xffffffffu, mylive);
-    for (int cchunk = 0; cchunk < TC_BN / 32; ++cchunk) {
+    for (int cchunk = 0; cchunk < nchunks; ++cchunk) {
         float v[32];
         tmem_ld32(taddr + (uint32_t)(cchunk * 32), v);
 #pragma unroll
@@ -128,12 +129,12 @@ __device__ __forceinline__ void store_tile_rows(const TcEpilogue &ep, float *stg
 // blockIdx.x, + gridDim.x, ...).  Warp 0 (one thread) streams the K stages
 // of every tile through the 3-stage ring by TMA; warp 1 (one thread) issues
 // the products into one of two tensor-memory accumulators (128 columns each)
-// in turn; warps 2-5 drain the other accumulator through the epilogue (warp
-// w reads the TMEM lanes of quarter w % 4), so a tile's stores overlap the
-// next tile's products.  mbarriers: stage full / empty, accumulator full
+// in turn; warps 2-9 drain the other accumulator through the epilogue (warp
+// w reads the TMEM lanes of quarter w % 4, columns 0-63 for w < 6 and 64-127
+// above), so a tile's stores overlap the next tile's products.  mbarriers: stage full / empty, accumulator full
 // (the MMA commit) / empty (one arrival per epilogue warp).  Every wait is
 // bounded; at exit the copies and products still in flight are drained.
-constexpr int TP_EPI = 4;                                          // epilogue warps
+constexpr int TP_EPI = 8;                                          // epilogue warps: 2 per TMEM quarter
 constexpr int TP_THREADS = 64 + 32 * TP_EPI;
 constexpr int TP_STG = TP_EPI * 32 * 33 * 4;                       // epilogue staging tiles
 constexpr int TP_SMEM = TC_STAGES * TC_STAGE_BYTES + TP_STG + 1024 + 256;
@@ -256,8 +257,8 @@ __global__ void __launch_bounds__(TP_THREADS, 1)
             tc_mbar_drain(fin, 0u);
         }
     } else if (warp >= 2) {
-        // epilogue warps: quarter q of the tile rows
-        const int q = warp & 3;
+        // epilogue warps: quarter q of the tile rows, half h of its columns
+        const int q = warp & 3, h = (warp - 2) >> 2;
         float *stg = stg_all + (warp - 2) * 32 * 33;
         int tc = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tc) {
@@ -267,8 +268,9 @@ __global__ void __launch_bounds__(TP_THREADS, 1)
             if (!have) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m0 = (tile / ntn) * TC_BM, n0 = (tile % ntn) * TC_BN;
-            store_tile_rows(ep, stg, tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN), m0,
-                            q * 32, n0, R, lane);
+            store_tile_rows(ep, stg,
+                            tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TC_BN + h * (TC_BN / 2)),
+                            m0, q * 32, n0 + h * (TC_BN / 2), R, lane, TC_BN / 64);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
