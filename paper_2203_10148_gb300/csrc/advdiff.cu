@@ -50,16 +50,17 @@ namespace cg = cooperative_groups;
 namespace pit {
 namespace {
 
-constexpr int AD_RY = 4, AD_RX = 8;          // thread tile
+constexpr int AD_RY = 8;                     // rows of a thread tile
+constexpr int AD_H = AD_RY / 2;              // rows r and r + AD_H share a packed pair
 constexpr int AD_ROWS = 32;                  // rows per CTA (cluster size = n / 32)
-constexpr int AD_TY = AD_ROWS / AD_RY;       // 8 thread rows per CTA
+constexpr int AD_TY = AD_ROWS / AD_RY;       // 4 thread rows per CTA
 
 struct AdvArgs {
     const double *x;
     double *y;
     float *y32;
     const double *y0;
-    const void *ax, *ay;   // per-point coefficients (float or double), row-major n x n
+    const void *ax, *ay;   // per-point coefficients (float, double or (hi, lo) float pairs), row-major n x n
     int n, N, batch;
     size_t blen;
     int n_first, mode, steps;
@@ -72,104 +73,125 @@ __device__ __forceinline__ bool adv_runs(const MemberState *st, int b) {
     return st == nullptr || (st[b].active && !st[b].skip && !st[b].half);
 }
 
-template <class T>
-__device__ __forceinline__ T adv_stage(T vn, T vs, T vw, T ve, T vc, T u, T cc, T nud, T ax,
-                                       T ay) {
-    const T lap = fma(T(-4), vc, (ve + vw) + (vn + vs));
-    const T dX = (ax >= T(0)) ? (vc - vw) : (ve - vc);
-    const T dY = (ay >= T(0)) ? (vc - vn) : (vs - vc);
-    const T adv = fma(ay, dY, ax * dX);
+// Scalar stage (FP64): w = u + cc L v at one point.
+__device__ __forceinline__ double adv_stage(double vn, double vs, double vw, double ve, double vc,
+                                            double u, double cc, double nud, double ax, double ay) {
+    const double lap = fma(-4.0, vc, (ve + vw) + (vn + vs));
+    const double dX = (ax >= 0.0) ? (vc - vw) : (ve - vc);
+    const double dY = (ay >= 0.0) ? (vc - vn) : (vs - vc);
+    const double adv = fma(ay, dY, ax * dX);
     return fma(cc, fma(nud, lap, -adv), u);
 }
 
-// Float-float stage (the residual arithmetic, about 48 significant bits on
-// the FP32 pipe): the sums of high parts are exact TwoSums, their errors and
-// the low parts are summed in FP32, products keep their exact FMA error
-// terms, one renormalisation at the end.  The upwind side follows the sign
-// of the coefficient's high part (the sign of the FP64 coefficient).
-template <>
-__device__ __forceinline__ ff adv_stage<ff>(ff vn, ff vs, ff vw, ff ve, ff vc, ff u, ff cc,
-                                            ff nud, ff ax, ff ay) {
-    // Laplacian sum vE + vW + vN + vS - 4 vC
-    const ff a = two_sum(ve.hi, vw.hi);
-    const ff b = two_sum(vn.hi, vs.hi);
-    const ff c = two_sum(a.hi, b.hi);
-    const ff d = two_sum(c.hi, __fmul_rn(-4.f, vc.hi));
-    const float lap_lo = fmaf(-4.f, vc.lo, ((a.lo + b.lo) + (c.lo + d.lo)) +
-                                              ((ve.lo + vw.lo) + (vn.lo + vs.lo)));
-    // upwind differences
-    const ff x1 = ax.hi >= 0.f ? vc : ve, x2 = ax.hi >= 0.f ? vw : vc;
-    const ff y1 = ay.hi >= 0.f ? vc : vs, y2 = ay.hi >= 0.f ? vn : vc;
-    const ff dx = two_sum(x1.hi, -x2.hi);
-    const float dx_lo = dx.lo + (x1.lo - x2.lo);
-    const ff dy = two_sum(y1.hi, -y2.hi);
-    const float dy_lo = dy.lo + (y1.lo - y2.lo);
-    // nud lap - ax dX - ay dY, each product with its exact error term
-    const float p1 = __fmul_rn(nud.hi, d.hi);
-    float e1 = fmaf(nud.hi, d.hi, -p1);
-    e1 = fmaf(nud.hi, lap_lo, e1);
-    e1 = fmaf(nud.lo, d.hi, e1);
-    const float p2 = __fmul_rn(ax.hi, dx.hi);
-    float e2 = fmaf(ax.hi, dx.hi, -p2);
-    e2 = fmaf(ax.hi, dx_lo, e2);
-    e2 = fmaf(ax.lo, dx.hi, e2);
-    const float p3 = __fmul_rn(ay.hi, dy.hi);
-    float e3 = fmaf(ay.hi, dy.hi, -p3);
-    e3 = fmaf(ay.hi, dy_lo, e3);
-    e3 = fmaf(ay.lo, dy.hi, e3);
-    const ff s1 = two_sum(p1, -p2);
-    const ff s2 = two_sum(s1.hi, -p3);
-    const float l_lo = (s1.lo + s2.lo) + ((e1 - e2) - e3);
-    // u + cc L
-    const float p = __fmul_rn(cc.hi, s2.hi);
-    float e = fmaf(cc.hi, s2.hi, -p);
-    e = fmaf(cc.hi, l_lo, e);
-    e = fmaf(cc.lo, s2.hi, e);
-    const ff t = two_sum(u.hi, p);
-    return fast_two_sum(t.hi, t.lo + (u.lo + e));
+// FP32 stage on two points per packed instruction, with the scalar stage's
+// roundings: lap = (ve + vw) + (vn + vs) - 4 vc, adv = ay dY + fl(ax dX),
+// w = u + cc (nud lap - adv).  The coefficients come negated (nax = -ax):
+// -fl(ax dX) = fl(nax dX) and -adv = fl(nay dY + fl(nax dX)) exactly, so
+// no negation is issued; ax >= 0 is nax <= 0 (also for signed zeros).
+__device__ __forceinline__ float2 adv_stage_f2(float2 vn, float2 vs, float2 vw, float2 ve, float2 vc,
+                                               float2 u, float2 cc, float2 nud, float2 nax, float2 nay) {
+    const float2 lap = __ffma2_rn(make_float2(-4.f, -4.f), vc,
+                                  __fadd2_rn(__fadd2_rn(ve, vw), __fadd2_rn(vn, vs)));
+    const float2 dW = f2_sub(vc, vw), dE = f2_sub(ve, vc);
+    const float2 dN = f2_sub(vc, vn), dS = f2_sub(vs, vc);
+    const float2 dX = make_float2(nax.x <= 0.f ? dW.x : dE.x, nax.y <= 0.f ? dW.y : dE.y);
+    const float2 dY = make_float2(nay.x <= 0.f ? dN.x : dS.x, nay.y <= 0.f ? dN.y : dS.y);
+    const float2 nadv = __ffma2_rn(nay, dY, __fmul2_rn(nax, dX));
+    return __ffma2_rn(cc, __ffma2_rn(nud, lap, nadv), u);
 }
 
-// The same stage for coefficients that are FP32 values (low parts zero):
-// the low-part terms of the two coefficient products vanish (90 operations).
-__device__ __forceinline__ ff adv_stage_c32(ff vn, ff vs, ff vw, ff ve, ff vc, ff u, ff cc, ff nud,
-                                            float ax, float ay) {
-    const ff a = two_sum(ve.hi, vw.hi);
-    const ff b = two_sum(vn.hi, vs.hi);
-    const ff c = two_sum(a.hi, b.hi);
-    const ff d = two_sum(c.hi, __fmul_rn(-4.f, vc.hi));
-    const float lap_lo = fmaf(-4.f, vc.lo, ((a.lo + b.lo) + (c.lo + d.lo)) +
-                                              ((ve.lo + vw.lo) + (vn.lo + vs.lo)));
-    const ff x1 = ax >= 0.f ? vc : ve, x2 = ax >= 0.f ? vw : vc;
-    const ff y1 = ay >= 0.f ? vc : vs, y2 = ay >= 0.f ? vn : vc;
-    const ff dx = two_sum(x1.hi, -x2.hi);
-    const float dx_lo = dx.lo + (x1.lo - x2.lo);
-    const ff dy = two_sum(y1.hi, -y2.hi);
-    const float dy_lo = dy.lo + (y1.lo - y2.lo);
-    const float p1 = __fmul_rn(nud.hi, d.hi);
-    float e1 = fmaf(nud.hi, d.hi, -p1);
-    e1 = fmaf(nud.hi, lap_lo, e1);
-    e1 = fmaf(nud.lo, d.hi, e1);
-    const float p2 = __fmul_rn(ax, dx.hi);
-    float e2 = fmaf(ax, dx.hi, -p2);
-    e2 = fmaf(ax, dx_lo, e2);
-    const float p3 = __fmul_rn(ay, dy.hi);
-    float e3 = fmaf(ay, dy.hi, -p3);
-    e3 = fmaf(ay, dy_lo, e3);
-    const ff s1 = two_sum(p1, -p2);
-    const ff s2 = two_sum(s1.hi, -p3);
-    const float l_lo = (s1.lo + s2.lo) + ((e1 - e2) - e3);
-    const float p = __fmul_rn(cc.hi, s2.hi);
-    float e = fmaf(cc.hi, s2.hi, -p);
-    e = fmaf(cc.hi, l_lo, e);
-    e = fmaf(cc.lo, s2.hi, e);
-    const ff t = two_sum(u.hi, p);
-    return fast_two_sum(t.hi, t.lo + (u.lo + e));
+// TwoSum(a, -b) on packed pairs: s = fl(a - b) and e = (a - b) - s exactly.
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = f2_sub(a, b);
+    const float2 bb = f2_sub(s, a);   // the -b actually added
+    e = f2_sub(f2_sub(a, f2_sub(s, bb)), __fadd2_rn(b, bb));
 }
 
-template <class T>
-__device__ __forceinline__ T adv_zero() { return T(0); }
-template <>
-__device__ __forceinline__ ff adv_zero<ff>() { return ff{0.f, 0.f}; }
+// Float-float stage on two points per packed instruction (the residual
+// arithmetic, about 48 significant bits on the FP32 pipe).  The upwind term
+// is written |ax| (vc - ux) with ux the upwind neighbour (vw where ax >= 0,
+// else ve), which equals ax dX exactly.  High parts are summed with exact
+// TwoSums, products keep their exact FMA error terms, the errors and the low
+// parts are summed in FP32; the result is left unnormalised (its low part a
+// few ulp of its high part at most, summed in FP32 next to exact sums of high
+// parts by the next stage) and renormalised once per time step.  A
+// coefficient pair is (hi, lo) per lane; C32: coefficients that are FP32
+// values, whose low parts are zero and skipped.
+struct AdCoefFF {
+    float2 hi, lo;
+};
+
+template <bool C32>
+__device__ __forceinline__ ff2 adv_stage_ff2(const ff2 &vn, const ff2 &vs, const ff2 &vw, const ff2 &ve,
+                                             const ff2 &vc, const ff2 &u, float2 cch, float2 ncch, float2 ccl,
+                                             float2 nudh, float2 nnudh, float2 nudl, const AdCoefFF &ax,
+                                             const AdCoefFF &ay) {
+    const float2 m4 = make_float2(-4.f, -4.f);
+    // vn + vs + vw + ve - 4 vc = dh + lap_lo
+    float2 ah, al, bh, bl, ch, cl;
+    two_sum2(vn.hi, vs.hi, ah, al);
+    two_sum2(vw.hi, ve.hi, bh, bl);
+    two_sum2(ah, bh, ch, cl);
+    const float2 dh = __ffma2_rn(m4, vc.hi, ch);
+    const float2 nbb = f2_sub(ch, dh);
+    const float2 dl = __fadd2_rn(f2_sub(ch, __fadd2_rn(dh, nbb)), __ffma2_rn(m4, vc.hi, nbb));
+    const float2 lap_lo = __ffma2_rn(
+        m4, vc.lo,
+        __fadd2_rn(__fadd2_rn(__fadd2_rn(al, bl), __fadd2_rn(cl, dl)),
+                   __fadd2_rn(__fadd2_rn(vn.lo, vs.lo), __fadd2_rn(vw.lo, ve.lo))));
+    // upwind neighbours and coefficient magnitudes, per lane
+    const bool px0 = ax.hi.x >= 0.f, px1 = ax.hi.y >= 0.f;
+    const bool py0 = ay.hi.x >= 0.f, py1 = ay.hi.y >= 0.f;
+    const float2 uxh = make_float2(px0 ? vw.hi.x : ve.hi.x, px1 ? vw.hi.y : ve.hi.y);
+    const float2 uxl = make_float2(px0 ? vw.lo.x : ve.lo.x, px1 ? vw.lo.y : ve.lo.y);
+    const float2 uyh = make_float2(py0 ? vn.hi.x : vs.hi.x, py1 ? vn.hi.y : vs.hi.y);
+    const float2 uyl = make_float2(py0 ? vn.lo.x : vs.lo.x, py1 ? vn.lo.y : vs.lo.y);
+    const float2 axh = make_float2(fabsf(ax.hi.x), fabsf(ax.hi.y));
+    const float2 ayh = make_float2(fabsf(ay.hi.x), fabsf(ay.hi.y));
+    const float2 naxh = make_float2(-axh.x, -axh.y), nayh = make_float2(-ayh.x, -ayh.y);
+    // dx = vc - ux, dy = vc - uy
+    float2 dxh, dxe, dyh, dye;
+    two_diff2(vc.hi, uxh, dxh, dxe);
+    two_diff2(vc.hi, uyh, dyh, dye);
+    const float2 dxl = __fadd2_rn(dxe, f2_sub(vc.lo, uxl));
+    const float2 dyl = __fadd2_rn(dye, f2_sub(vc.lo, uyl));
+    // p1 = fl(nud dh), p2 = fl(|ax| dx), p3 = fl(|ay| dy) taken negated; e_i
+    // collect the products' exact rounding errors and their low-part terms
+    const float2 np1 = __fmul2_rn(nnudh, dh);
+    float2 e1 = __ffma2_rn(nudh, dh, np1);
+    e1 = __ffma2_rn(nudh, lap_lo, e1);
+    e1 = __ffma2_rn(nudl, dh, e1);
+    const float2 np2 = __fmul2_rn(naxh, dxh);
+    float2 e2 = __ffma2_rn(axh, dxh, np2);
+    e2 = __ffma2_rn(axh, dxl, e2);
+    const float2 np3 = __fmul2_rn(nayh, dyh);
+    float2 e3 = __ffma2_rn(ayh, dyh, np3);
+    e3 = __ffma2_rn(ayh, dyl, e3);
+    if constexpr (!C32) {
+        // |ax| = -ax where ax.hi < 0: the low part follows the high part's sign
+        const float2 axl = make_float2(px0 ? ax.lo.x : -ax.lo.x, px1 ? ax.lo.y : -ax.lo.y);
+        const float2 ayl = make_float2(py0 ? ay.lo.x : -ay.lo.x, py1 ? ay.lo.y : -ay.lo.y);
+        e2 = __ffma2_rn(axl, dxh, e2);
+        e3 = __ffma2_rn(ayl, dyh, e3);
+    }
+    // L = p1 - p2 - p3 + (e1 - e2 - e3) = s2h + l_lo
+    float2 s1h, s1e, s2h, s2e;
+    two_diff2(np2, np1, s1h, s1e);   // p1 - p2
+    two_sum2(s1h, np3, s2h, s2e);    // - p3
+    const float2 l_lo = __fadd2_rn(__fadd2_rn(s1e, s2e), f2_sub(f2_sub(e1, e2), e3));
+    // u + cc L, p = fl(cc.hi s2h) taken negated
+    const float2 pn = __fmul2_rn(ncch, s2h);
+    float2 e = __ffma2_rn(cch, s2h, pn);
+    e = __ffma2_rn(cch, l_lo, e);
+    e = __ffma2_rn(ccl, s2h, e);
+    const float2 sh = f2_sub(u.hi, pn);
+    const float2 nb2 = f2_sub(u.hi, sh);
+    const float2 sl = __fadd2_rn(f2_sub(u.hi, __fadd2_rn(sh, nb2)), f2_sub(nb2, pn));
+    ff2 w;
+    w.hi = sh;
+    w.lo = __fadd2_rn(sl, __fadd2_rn(u.lo, e));
+    return w;
+}
 
 template <class T>
 __device__ __forceinline__ T adv_from_d(double x) { return (T)x; }
@@ -182,95 +204,122 @@ __device__ __forceinline__ double adv_to_d(float v) { return f2d(v); }
 __device__ __forceinline__ double adv_to_d(double v) { return v; }
 __device__ __forceinline__ double adv_to_d(ff v) { return f2d(v.hi) + f2d(v.lo); }
 
+// A pair of points of a thread tile, rows r and r + AD_H of one column: the
+// two lanes of every packed instruction.
 template <class T>
-__device__ __forceinline__ T shfl_idx(T v, int src) { return __shfl_sync(kFullMask, v, src); }
-template <class T>
-__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(kFullMask, v, 1); }
-template <class T>
-__device__ __forceinline__ T shfl_down1(T v) { return __shfl_down_sync(kFullMask, v, 1); }
+struct AdPair;
 template <>
-__device__ __forceinline__ ff shfl_idx<ff>(ff v, int src) {
-    return ff{__shfl_sync(kFullMask, v.hi, src), __shfl_sync(kFullMask, v.lo, src)};
-}
+struct AdPair<float> {
+    using P = float2;
+    __device__ static P make(float a, float b) { return make_float2(a, b); }
+    __device__ static float x(const P &p) { return p.x; }
+    __device__ static float y(const P &p) { return p.y; }
+    __device__ static P shfl_idx(const P &p, int s) {
+        return make_float2(__shfl_sync(kFullMask, p.x, s), __shfl_sync(kFullMask, p.y, s));
+    }
+    __device__ static P shfl_up(const P &p) {
+        return make_float2(__shfl_up_sync(kFullMask, p.x, 1), __shfl_up_sync(kFullMask, p.y, 1));
+    }
+    __device__ static P shfl_down(const P &p) {
+        return make_float2(__shfl_down_sync(kFullMask, p.x, 1), __shfl_down_sync(kFullMask, p.y, 1));
+    }
+};
 template <>
-__device__ __forceinline__ ff shfl_up1<ff>(ff v) {
-    return ff{__shfl_up_sync(kFullMask, v.hi, 1), __shfl_up_sync(kFullMask, v.lo, 1)};
-}
+struct AdPair<double> {
+    using P = double2;
+    __device__ static P make(double a, double b) { return make_double2(a, b); }
+    __device__ static double x(const P &p) { return p.x; }
+    __device__ static double y(const P &p) { return p.y; }
+    __device__ static P shfl_idx(const P &p, int s) {
+        return make_double2(__shfl_sync(kFullMask, p.x, s), __shfl_sync(kFullMask, p.y, s));
+    }
+    __device__ static P shfl_up(const P &p) {
+        return make_double2(__shfl_up_sync(kFullMask, p.x, 1), __shfl_up_sync(kFullMask, p.y, 1));
+    }
+    __device__ static P shfl_down(const P &p) {
+        return make_double2(__shfl_down_sync(kFullMask, p.x, 1), __shfl_down_sync(kFullMask, p.y, 1));
+    }
+};
 template <>
-__device__ __forceinline__ ff shfl_down1<ff>(ff v) {
-    return ff{__shfl_down_sync(kFullMask, v.hi, 1), __shfl_down_sync(kFullMask, v.lo, 1)};
-}
+struct AdPair<ff> {
+    using P = ff2;
+    __device__ static P make(ff a, ff b) { return ff_pair(a, b); }
+    __device__ static ff x(const P &p) { return ff{p.hi.x, p.lo.x}; }
+    __device__ static ff y(const P &p) { return ff{p.hi.y, p.lo.y}; }
+    __device__ static P shfl_idx(const P &p, int s) {
+        return ff2{AdPair<float>::shfl_idx(p.hi, s), AdPair<float>::shfl_idx(p.lo, s)};
+    }
+    __device__ static P shfl_up(const P &p) {
+        return ff2{AdPair<float>::shfl_up(p.hi), AdPair<float>::shfl_up(p.lo)};
+    }
+    __device__ static P shfl_down(const P &p) {
+        return ff2{AdPair<float>::shfl_down(p.hi), AdPair<float>::shfl_down(p.lo)};
+    }
+};
 
-// A thread's 8 consecutive values of a row buffer are stored as 16-byte
+// A thread's RX consecutive values of a row buffer are stored as 16-byte
 // chunks in chunk-major order: chunk q of thread column tx at element
 // q * TX * CW + tx * CW (CW values per 16 bytes), so that a warp's 16-byte
 // accesses to one chunk are contiguous (no shared-memory bank conflicts).
-template <class T>
-struct RowChunks;
-template <>
-struct RowChunks<float> {
-    __device__ static void store(float *row, int tx, int TX, const float (&v)[AD_RX]) {
+__device__ __forceinline__ float4 adv_chunk(const float *v) { return make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ float4 adv_chunk(const ff *v) { return make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo); }
+__device__ __forceinline__ double2 adv_chunk(const double *v) { return make_double2(v[0], v[1]); }
+__device__ __forceinline__ void adv_unchunk(float4 t, float *v) {
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void adv_unchunk(float4 t, ff *v) {
+    v[0] = ff{t.x, t.y};
+    v[1] = ff{t.z, t.w};
+}
+__device__ __forceinline__ void adv_unchunk(double2 t, double *v) {
+    v[0] = t.x;
+    v[1] = t.y;
+}
+
+template <class T, int RX>
+struct RowChunks {
+    static constexpr int CW = 16 / (int)sizeof(T);
+    static_assert(RX % CW == 0, "a thread's row segment is whole 16-byte chunks");
+    using C = typename std::conditional<std::is_same<T, double>::value, double2, float4>::type;
+    __device__ static void store(T *row, int tx, int TX, const T (&v)[RX]) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-            *reinterpret_cast<float4 *>(row + (size_t)q * TX * 4 + (size_t)tx * 4) =
-                make_float4(v[q * 4], v[q * 4 + 1], v[q * 4 + 2], v[q * 4 + 3]);
+        for (int q = 0; q < RX / CW; ++q)
+            *reinterpret_cast<C *>(row + (size_t)q * TX * CW + (size_t)tx * CW) = adv_chunk(&v[q * CW]);
     }
-    __device__ static void load(const float *row, int tx, int TX, float (&v)[AD_RX]) {
+    __device__ static void load(const T *row, int tx, int TX, T (&v)[RX]) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float4 t = *reinterpret_cast<const float4 *>(row + (size_t)q * TX * 4 + (size_t)tx * 4);
-            v[q * 4] = t.x;
-            v[q * 4 + 1] = t.y;
-            v[q * 4 + 2] = t.z;
-            v[q * 4 + 3] = t.w;
-        }
-    }
-};
-template <>
-struct RowChunks<double> {
-    __device__ static void store(double *row, int tx, int TX, const double (&v)[AD_RX]) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<double2 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2) =
-                make_double2(v[q * 2], v[q * 2 + 1]);
-    }
-    __device__ static void load(const double *row, int tx, int TX, double (&v)[AD_RX]) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double2 t = *reinterpret_cast<const double2 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2);
-            v[q * 2] = t.x;
-            v[q * 2 + 1] = t.y;
-        }
-    }
-};
-template <>
-struct RowChunks<ff> {
-    __device__ static void store(ff *row, int tx, int TX, const ff (&v)[AD_RX]) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<float4 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2) =
-                make_float4(v[q * 2].hi, v[q * 2].lo, v[q * 2 + 1].hi, v[q * 2 + 1].lo);
-    }
-    __device__ static void load(const ff *row, int tx, int TX, ff (&v)[AD_RX]) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 t = *reinterpret_cast<const float4 *>(row + (size_t)q * TX * 2 + (size_t)tx * 2);
-            v[q * 2] = ff{t.x, t.y};
-            v[q * 2 + 1] = ff{t.z, t.w};
-        }
+        for (int q = 0; q < RX / CW; ++q)
+            adv_unchunk(*reinterpret_cast<const C *>(row + (size_t)q * TX * CW + (size_t)tx * CW), &v[q * CW]);
     }
 };
 
-// One cluster of CS = n/32 CTAs per (slice, member).  Threads: TX * 8 with
-// TX = n/8 thread columns (n <= 512).  T = float (state in registers,
-// coefficients in shared memory), double or float-float (state in shared
-// memory, coefficients read through L1; float-float coefficients are
-// (hi, lo) float pairs).
-template <class T, bool DBUF, bool C32 = false>
-__global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
+// u records of the thread-private shared-memory layout, one 16-byte store each
+__device__ __forceinline__ void adv_store_u(ff2 *p, const ff2 &v) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v.hi.x, v.hi.y, v.lo.x, v.lo.y);
+}
+__device__ __forceinline__ void adv_store_u(double2 *p, const double2 &v) { *p = v; }
+__device__ __forceinline__ void adv_store_u(float2 *, const float2 &) {}
+
+// One cluster of CS = n/32 CTAs per (slice, member); each CTA holds 32 rows
+// for all RK4 steps.  A thread owns an 8 x RX tile (RX = 4: n threads per
+// CTA; RX = 8: n/2) kept as AD_H x RX pairs (rows r and r + 4 of a column).
+// T = float (state, u and stage values in registers, coefficients negated in
+// shared memory, packed f32x2 arithmetic), ff (state in registers, u in
+// shared memory, coefficients read through L1 as 16-byte vectors, packed
+// float-float arithmetic) or double (u in shared memory, scalar arithmetic
+// on each lane).  Row buffers and the warp-edge column buffers are double
+// buffered: one cluster barrier per RK4 stage.
+template <class T, int RX, bool C32 = false>
+__global__ void __launch_bounds__(RX == 4 ? 512 : 256, 1) k_advdiff_fine(AdvArgs a) {
+    using PA = AdPair<T>;
+    using P = typename PA::P;
     constexpr bool FP32 = std::is_same<T, float>::value;
     constexpr bool FF = std::is_same<T, ff>::value;
-    constexpr int NB = DBUF ? 2 : 1;               // row-buffer copies
+    constexpr int H = AD_H;
+    constexpr int NT = 2048 / RX;                   // slot stride of u / coefficient records (threads at n = 512)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
     const int n = a.n;
@@ -281,174 +330,214 @@ __global__ void __launch_bounds__(512, 1) k_advdiff_fine(AdvArgs a) {
     const int slice = a.n_first + slice_lin % a.N;  // output block
     // inactive member: the whole cluster leaves before any cluster barrier
     if (!adv_runs(a.st, b)) return;
-    const bool active = true;
-    const int TX = n / AD_RX;
-    const int nthr = blockDim.x;
+    const int TX = n / RX;                          // thread columns
+    const int nthr = blockDim.x;                    // TX * AD_TY
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int lane = tid & 31, warp_in_row = tx / 32;
-    const int i0 = tx * AD_RX;
-    const int jl0 = ty * AD_RY;                      // local row
-    const int j0 = rank * AD_ROWS + jl0;             // global row
-    // shared memory: [cc 4][rowbuf NB x 2 x TY x n][colbuf NB x TY x 4 x RY][u or coefficients]
+    const int lane = tid & 31;
+    const int W = TX >> 5;                          // warps per thread row (0: part of one warp)
+    const int Wc = W > 0 ? W : 1;
+    const int wir = tx >> 5;                        // warp within the thread row
+    const int i0 = tx * RX;
+    const int j0 = rank * AD_ROWS + ty * AD_RY;     // global row of the tile's row 0
+    // shared memory: [cc 4][rowbuf 2 buf x 2 top/bottom x TY x n]
+    // [colbuf 2 buf x TY x 2 west/east x Wc x H pairs][u or coefficients]
     T *ccs = reinterpret_cast<T *>(smem_raw);
     T *rowbuf = reinterpret_cast<T *>(smem_raw + 32);
-    T *colbuf = rowbuf + (size_t)NB * 2 * AD_TY * n;
-    T *tail = colbuf + NB * AD_TY * 4 * AD_RY;
+    P *colbuf = reinterpret_cast<P *>(rowbuf + (size_t)4 * AD_TY * n);
+    unsigned char *tail = reinterpret_cast<unsigned char *>(colbuf + (size_t)4 * AD_TY * Wc * H);
+    [[maybe_unused]] P *us = reinterpret_cast<P *>(tail);                  // u: [H x RX][NT]
+    [[maybe_unused]] float4 *cx4 = reinterpret_cast<float4 *>(tail);       // FP32: [H x RX/2][NT]
+    [[maybe_unused]] float4 *cy4 = cx4 + (size_t)H * (RX / 2) * NT;
     if (tid < 4) ccs[tid] = adv_from_d<T>(tid == 0 ? a.c[0] : tid == 1 ? a.c[1] : tid == 2 ? a.c[2] : a.c[3]);
     const size_t mb = (size_t)b * a.blen;
     const size_t nn = (size_t)n * n;
     const double *xin = a.x + mb + (size_t)(slice - 1) * nn;
 
-    T v[AD_RY][AD_RX];
-    T ur[FP32 ? AD_RY : 1][FP32 ? AD_RX : 1];
-    T *us = tail;                                    // double: u thread-private
-    T *cax = tail, *cay = tail + (size_t)AD_RY * AD_RX * nthr;   // float: coefficients
-    const T *gax = reinterpret_cast<const T *>(a.ax);
-    const T *gay = reinterpret_cast<const T *>(a.ay);
-    [[maybe_unused]] const float2 *gax2 = reinterpret_cast<const float2 *>(a.ax);
-    [[maybe_unused]] const float2 *gay2 = reinterpret_cast<const float2 *>(a.ay);
+    P v[H][RX];
+    [[maybe_unused]] P ur[FP32 ? H : 1][FP32 ? RX : 1];
 #pragma unroll
-    for (int r = 0; r < AD_RY; ++r)
+    for (int r = 0; r < H; ++r)
 #pragma unroll
-        for (int c = 0; c < AD_RX; ++c) {
-            const size_t k = (size_t)(j0 + r) * n + (i0 + c);
-            const int slot = (r * AD_RX + c) * nthr + tid;
-            T val = adv_zero<T>();
-            if (active) val = adv_from_d<T>(xin[k]);
-            v[r][c] = val;
-            if constexpr (FP32) {
-                ur[FP32 ? r : 0][FP32 ? c : 0] = val;
-                cax[slot] = gax[k];
-                cay[slot] = gay[k];
-            } else {
-                us[slot] = val;
-            }
+        for (int c = 0; c < RX; ++c) {
+            const size_t kA = (size_t)(j0 + r) * n + (i0 + c), kB = kA + (size_t)H * n;
+            v[r][c] = PA::make(adv_from_d<T>(xin[kA]), adv_from_d<T>(xin[kB]));
+            if constexpr (FP32) ur[FP32 ? r : 0][FP32 ? c : 0] = v[r][c];
+            else adv_store_u(us + (size_t)(r * RX + c) * NT + tid, v[r][c]);
         }
+    if constexpr (FP32) {
+        // negated coefficients of the tile, a float4 per two columns of a pair row
+        const float *gx = reinterpret_cast<const float *>(a.ax);
+        const float *gy = reinterpret_cast<const float *>(a.ay);
+#pragma unroll
+        for (int r = 0; r < H; ++r)
+#pragma unroll
+            for (int q = 0; q < RX / 2; ++q) {
+                const size_t kA = (size_t)(j0 + r) * n + (i0 + 2 * q), kB = kA + (size_t)H * n;
+                const size_t slot = (size_t)(r * (RX / 2) + q) * NT + tid;
+                cx4[slot] = make_float4(-gx[kA], -gx[kB], -gx[kA + 1], -gx[kB + 1]);
+                cy4[slot] = make_float4(-gy[kA], -gy[kB], -gy[kA + 1], -gy[kB + 1]);
+            }
+    }
     const T nud = adv_from_d<T>(a.nud);
-    int buf = 0;
+    // north halo: the bottom row of the thread row above (periodic across the
+    // cluster); south halo: the top row of the thread row below
     const int up_rank = (rank + CS - 1) % CS, down_rank = (rank + 1) % CS;
+    const T *nsrc = (ty > 0) ? rowbuf : cluster.map_shared_rank(rowbuf, up_rank);
+    const T *ssrc = (ty < AD_TY - 1) ? rowbuf : cluster.map_shared_rank(rowbuf, down_rank);
+    const int nty = (ty > 0) ? ty - 1 : AD_TY - 1;
+    const int sty = (ty < AD_TY - 1) ? ty + 1 : 0;
+    int buf = 0;
     for (int s = 0; s < a.steps; ++s) {
 #pragma unroll 1
         for (int stage = 0; stage < 4; ++stage) {
-            // single buffer: every read of the previous stage's rows is done first
-            if (!DBUF) cluster.sync();
-            // publish top / bottom rows and the warp-edge columns
-            RowChunks<T>::store(rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + ty) * n, tx, TX, v[0]);
-            RowChunks<T>::store(rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + ty) * n, tx, TX, v[AD_RY - 1]);
-            if (lane == 0 || lane == 31) {
-                // colbuf[buf][ty][slot][r]: slot 0/1 = west column of warp 0/1,
-                // slot 2/3 = east column of warp 0/1
-                T *cb = colbuf + ((size_t)(buf * AD_TY + ty) * 4 + (lane == 0 ? 0 : 2) + warp_in_row) * AD_RY;
+            // publish the tile's top row (row 0) and bottom row (row 7)
+            {
+                T top[RX], bot[RX];
 #pragma unroll
-                for (int r = 0; r < AD_RY; ++r) cb[r] = (lane == 0) ? v[r][0] : v[r][AD_RX - 1];
+                for (int c = 0; c < RX; ++c) {
+                    top[c] = PA::x(v[0][c]);
+                    bot[c] = PA::y(v[H - 1][c]);
+                }
+                RowChunks<T, RX>::store(rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + ty) * n, tx, TX, top);
+                RowChunks<T, RX>::store(rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + ty) * n, tx, TX, bot);
+            }
+            if (W > 1 && (lane == 0 || lane == 31)) {
+                // colbuf[buf][ty][0: west column of warp w, 1: east column][w][pair row]
+                P *cb = colbuf + ((((size_t)buf * AD_TY + ty) * 2 + (lane == 0 ? 0 : 1)) * Wc + wir) * H;
+#pragma unroll
+                for (int r = 0; r < H; ++r) cb[r] = (lane == 0) ? v[r][0] : v[r][RX - 1];
             }
             cluster.sync();
             const T cc = ccs[stage];
-            // north / south rows: from the thread row above / below, across the
-            // CTA edge from the neighbouring CTA's shared memory (periodic)
-            T prev[AD_RX];
+            [[maybe_unused]] float2 cc2, nud2, cch, ncch, ccl, nudh, nnudh, nudl;
+            if constexpr (FP32) {
+                cc2 = make_float2(cc, cc);
+                nud2 = make_float2(nud, nud);
+            } else if constexpr (FF) {
+                cch = make_float2(cc.hi, cc.hi);
+                ncch = make_float2(-cc.hi, -cc.hi);
+                ccl = make_float2(cc.lo, cc.lo);
+                nudh = make_float2(nud.hi, nud.hi);
+                nnudh = make_float2(-nud.hi, -nud.hi);
+                nudl = make_float2(nud.lo, nud.lo);
+            }
+            // north pair of pair row 0: rows -1 (halo) and H - 1 (not yet updated)
+            P prev[RX];
             {
-                const T *src = (ty > 0) ? rowbuf + ((size_t)(buf * 2 + 1) * AD_TY + (ty - 1)) * n
-                                        : cluster.map_shared_rank(rowbuf, up_rank) +
-                                              ((size_t)(buf * 2 + 1) * AD_TY + (AD_TY - 1)) * n;
-                RowChunks<T>::load(src, tx, TX, prev);
-            }
-            // west/east neighbours of the tile's first/last column (periodic in x)
-            const int row_base = (tid / 32) * 32;   // lanes of this warp
-            const bool row_in_warp = TX <= 32;
+                T nh[RX];
+                RowChunks<T, RX>::load(nsrc + ((size_t)(buf * 2 + 1) * AD_TY + nty) * n, tx, TX, nh);
 #pragma unroll
-            for (int r = 0; r < AD_RY; ++r) {
-                T w_in, e_in;
-                if (row_in_warp) {
-                    // the thread row lies in one warp: lanes tx-1 / tx+1 modulo TX
-                    const int seg = (lane / TX) * TX;
-                    w_in = shfl_idx(v[r][AD_RX - 1], seg + (tx + TX - 1) % TX);
-                    e_in = shfl_idx(v[r][0], seg + (tx + 1) % TX);
+                for (int c = 0; c < RX; ++c) prev[c] = PA::make(nh[c], PA::x(v[H - 1][c]));
+            }
+            // row H before its update: the south neighbour of row H - 1
+            T rowH[RX];
+#pragma unroll
+            for (int c = 0; c < RX; ++c) rowH[c] = PA::y(v[0][c]);
+            const P *cbt = colbuf + ((size_t)buf * AD_TY + ty) * 2 * Wc * H;
+#pragma unroll
+            for (int r = 0; r < H; ++r) {
+                // west / east neighbours of the tile's first / last column (periodic in x)
+                P w_in, e_in;
+                if (W <= 1) {
+                    // the thread row lies in one warp: lanes tx - 1 / tx + 1 modulo TX
+                    const int seg = lane - tx;
+                    w_in = PA::shfl_idx(v[r][RX - 1], seg + (tx + TX - 1) % TX);
+                    e_in = PA::shfl_idx(v[r][0], seg + (tx + 1) % TX);
                 } else {
-                    // two warps per thread row: the edge lanes read the other warp's column
-                    w_in = shfl_up1(v[r][AD_RX - 1]);
-                    e_in = shfl_down1(v[r][0]);
-                    const int other = 1 - warp_in_row;
-                    if (lane == 0)
-                        w_in = colbuf[((size_t)(buf * AD_TY + ty) * 4 + 2 + other) * AD_RY + r];
-                    if (lane == 31)
-                        e_in = colbuf[((size_t)(buf * AD_TY + ty) * 4 + 0 + other) * AD_RY + r];
+                    w_in = PA::shfl_up(v[r][RX - 1]);
+                    e_in = PA::shfl_down(v[r][0]);
+                    if (lane == 0) w_in = cbt[(1 * Wc + (wir + W - 1) % W) * H + r];   // east column, warp to the west
+                    if (lane == 31) e_in = cbt[(0 * Wc + (wir + 1) % W) * H + r];      // west column, warp to the east
                 }
-                (void)row_base;
-                T cur[AD_RX];
+                [[maybe_unused]] T sh[RX];
+                if (r == H - 1)
+                    RowChunks<T, RX>::load(ssrc + ((size_t)(buf * 2 + 0) * AD_TY + sty) * n, tx, TX, sh);
+                const size_t kA = (size_t)(j0 + r) * n + i0, kB = kA + (size_t)H * n;
+                // Column by column, in place: prev[c] holds the north pair (pair
+                // row r - 1 before its update) until column c is done, then the
+                // old values of column c, which are the west pair of column c + 1
+                // and the north pair of pair row r + 1.
+                [[maybe_unused]] float4 f4x, f4y;
 #pragma unroll
-                for (int c = 0; c < AD_RX; ++c) cur[c] = v[r][c];
-                T srow[AD_RX];
-                if (r == AD_RY - 1) {
-                    const T *srs = (ty < AD_TY - 1) ? rowbuf + ((size_t)(buf * 2 + 0) * AD_TY + (ty + 1)) * n
-                                                    : cluster.map_shared_rank(rowbuf, down_rank) +
-                                                          ((size_t)(buf * 2 + 0) * AD_TY + 0) * n;
-                    RowChunks<T>::load(srs, tx, TX, srow);
-                }
-#pragma unroll
-                for (int c = 0; c < AD_RX; ++c) {
-                    const T vn = prev[c];
-                    const T vs = (r < AD_RY - 1) ? v[r + 1][c] : srow[c];
-                    const T vw = (c > 0) ? cur[c - 1] : w_in;
-                    const T ve = (c < AD_RX - 1) ? cur[c + 1] : e_in;
-                    const int slot = (r * AD_RX + c) * nthr + tid;
-                    T u, ax, ay;
+                for (int c = 0; c < RX; ++c) {
+                    const P vw = (c > 0) ? prev[c > 0 ? c - 1 : 0] : w_in;
+                    const P ve = (c < RX - 1) ? v[r][c < RX - 1 ? c + 1 : 0] : e_in;
+                    const P vs = (r < H - 1) ? v[r < H - 1 ? r + 1 : 0][c] : PA::make(rowH[c], sh[c]);
+                    P nv;
                     if constexpr (FP32) {
-                        u = ur[FP32 ? r : 0][FP32 ? c : 0];
-                        ax = cax[slot];
-                        ay = cay[slot];
-                    } else if constexpr (FF) {
-                        u = us[slot];
-                        const size_t k = (size_t)(j0 + r) * n + (i0 + c);
-                        if constexpr (C32) {
-                            // FP32 coefficients: the low parts are zero
-                            const float* fx = reinterpret_cast<const float *>(a.ax);
-                            const float* fy = reinterpret_cast<const float *>(a.ay);
-                            v[r][c] = adv_stage_c32(vn, vs, vw, ve, cur[c], u, cc, nud, __ldg(fx + k),
-                                                    __ldg(fy + k));
-                            continue;
+                        // negated coefficients of columns c, c + 1 (one float4)
+                        if ((c & 1) == 0) {
+                            const size_t slot = (size_t)(r * (RX / 2) + c / 2) * NT + tid;
+                            f4x = cx4[slot];
+                            f4y = cy4[slot];
                         }
-                        const float2 cx = __ldg(gax2 + k), cy = __ldg(gay2 + k);
-                        ax = ff{cx.x, cx.y};
-                        ay = ff{cy.x, cy.y};
+                        const float2 nax = (c & 1) ? make_float2(f4x.z, f4x.w) : make_float2(f4x.x, f4x.y);
+                        const float2 nay = (c & 1) ? make_float2(f4y.z, f4y.w) : make_float2(f4y.x, f4y.y);
+                        nv = adv_stage_f2(prev[c], vs, vw, ve, v[r][c], ur[FP32 ? r : 0][FP32 ? c : 0], cc2, nud2,
+                                          nax, nay);
+                    } else if constexpr (FF) {
+                        AdCoefFF qx, qy;
+                        if constexpr (C32) {
+                            const float *gx = reinterpret_cast<const float *>(a.ax);
+                            const float *gy = reinterpret_cast<const float *>(a.ay);
+                            qx = AdCoefFF{make_float2(__ldg(gx + kA + c), __ldg(gx + kB + c)), make_float2(0.f, 0.f)};
+                            qy = AdCoefFF{make_float2(__ldg(gy + kA + c), __ldg(gy + kB + c)), make_float2(0.f, 0.f)};
+                        } else {
+                            const float2 *gx = reinterpret_cast<const float2 *>(a.ax);
+                            const float2 *gy = reinterpret_cast<const float2 *>(a.ay);
+                            const float2 xa = __ldg(gx + kA + c), xb = __ldg(gx + kB + c);
+                            const float2 ya = __ldg(gy + kA + c), yb = __ldg(gy + kB + c);
+                            qx = AdCoefFF{make_float2(xa.x, xb.x), make_float2(xa.y, xb.y)};
+                            qy = AdCoefFF{make_float2(ya.x, yb.x), make_float2(ya.y, yb.y)};
+                        }
+                        const float4 u4 = *reinterpret_cast<const float4 *>(us + (size_t)(r * RX + c) * NT + tid);
+                        const ff2 u = ff2{make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
+                        nv = adv_stage_ff2<C32>(prev[c], vs, vw, ve, v[r][c], u, cch, ncch, ccl, nudh, nnudh, nudl,
+                                                qx, qy);
                     } else {
-                        u = us[slot];
-                        const size_t k = (size_t)(j0 + r) * n + (i0 + c);
-                        ax = __ldg(gax + k);
-                        ay = __ldg(gay + k);
+                        const double *gx = reinterpret_cast<const double *>(a.ax);
+                        const double *gy = reinterpret_cast<const double *>(a.ay);
+                        const double qxa = __ldg(gx + kA + c), qxb = __ldg(gx + kB + c);
+                        const double qya = __ldg(gy + kA + c), qyb = __ldg(gy + kB + c);
+                        const P u = us[(size_t)(r * RX + c) * NT + tid];
+                        const P vn = prev[c], vc = v[r][c];
+                        nv = make_double2(adv_stage(vn.x, vs.x, vw.x, ve.x, vc.x, u.x, cc, nud, qxa, qya),
+                                          adv_stage(vn.y, vs.y, vw.y, ve.y, vc.y, u.y, cc, nud, qxb, qyb));
                     }
-                    v[r][c] = adv_stage(vn, vs, vw, ve, cur[c], u, cc, nud, ax, ay);
+                    prev[c] = v[r][c];
+                    v[r][c] = nv;
                 }
-#pragma unroll
-                for (int c = 0; c < AD_RX; ++c) prev[c] = cur[c];
             }
-            if (DBUF) buf ^= 1;
+            buf ^= 1;
         }
+        // end of the step: the stage value becomes u (float-float renormalised)
 #pragma unroll
-        for (int r = 0; r < AD_RY; ++r)
+        for (int r = 0; r < H; ++r)
 #pragma unroll
-            for (int c = 0; c < AD_RX; ++c) {
+            for (int c = 0; c < RX; ++c) {
+                if constexpr (FF) v[r][c] = ff_renorm2(v[r][c]);
                 if constexpr (FP32) ur[FP32 ? r : 0][FP32 ? c : 0] = v[r][c];
-                else us[(r * AD_RX + c) * nthr + tid] = v[r][c];
+                else adv_store_u(us + (size_t)(r * RX + c) * NT + tid, v[r][c]);
             }
     }
-    // all remote reads of this CTA's row buffer are done before anyone exits
+    // all remote reads of this CTA's row buffers are done before anyone exits
     cluster.sync();
     const double *xn = a.x + mb + (size_t)slice * nn;
+    double *yo = a.y + mb + (size_t)slice * nn;
 #pragma unroll
     for (int r = 0; r < AD_RY; ++r)
 #pragma unroll
-        for (int c = 0; c < AD_RX; ++c) {
+        for (int c = 0; c < RX; ++c) {
             const size_t k = (size_t)(j0 + r) * n + (i0 + c);
+            const T val = (r < H) ? PA::x(v[r < H ? r : 0][c]) : PA::y(v[r < H ? 0 : r - H][c]);
             if constexpr (FP32) {
                 if (a.y32) {
-                    a.y32[mb + (size_t)slice * nn + k] = d2f_rn(xn[k]) - v[r][c];
+                    a.y32[mb + (size_t)slice * nn + k] = d2f_rn(xn[k]) - val;
                     continue;
                 }
             }
-            const double f = adv_to_d(v[r][c]);
-            double *yo = a.y + mb + (size_t)slice * nn;
+            const double f = adv_to_d(val);
             if (a.mode == FINE_APPLY) yo[k] = xn[k] - f;
             else if (a.mode == FINE_RESIDUAL) yo[k] = f - xn[k];
             else yo[k] = f;
@@ -478,13 +567,17 @@ __global__ void k_split_ff(const double *__restrict__ x, float2 *__restrict__ ou
     }
 }
 
-template <class T, bool DBUF>
+// dynamic shared memory of k_advdiff_fine<T, RX>: [cc][row buffers][column
+// buffers][u (ff, double) or the negated coefficients (float)]
+template <class T, int RX>
 size_t adv_smem(int n) {
-    const size_t nthr = (size_t)n;   // TX * 8 = n
-    const size_t nb = DBUF ? 2 : 1;
-    size_t s = 32 + (nb * 2 * AD_TY * (size_t)n + nb * AD_TY * 4 * AD_RY) * sizeof(T);
-    if (std::is_same<T, float>::value) s += 2 * (size_t)AD_RY * AD_RX * nthr * sizeof(T);
-    else s += (size_t)AD_RY * AD_RX * nthr * sizeof(T);
+    const size_t nthr = 2048 / RX;   // the kernel's record stride
+    const size_t TX = (size_t)n / RX;
+    const size_t Wc = TX >= 64 ? TX / 32 : 1;
+    const size_t pair = 2 * sizeof(T);
+    size_t s = 32 + 4 * AD_TY * (size_t)n * sizeof(T) + 4 * AD_TY * Wc * AD_H * pair;
+    if (std::is_same<T, float>::value) s += 2 * (size_t)AD_H * RX * nthr * pair;
+    else s += (size_t)AD_H * RX * nthr * pair;
     return s;
 }
 
@@ -517,19 +610,19 @@ AdvArgs adv_args(Problem *p, const double *x, double *y, float *y32, int mode,
     return a;
 }
 
-template <class T, bool DBUF, bool C32 = false>
+template <class T, int RX, bool C32 = false>
 pit_status launch_adv_fine_v(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
     const int n = p->nx;
     const int CS = n / AD_ROWS;
-    const size_t sm = adv_smem<T, DBUF>(n);
-    auto kern = k_advdiff_fine<T, DBUF, C32>;
+    const size_t sm = adv_smem<T, RX>(n);
+    auto kern = k_advdiff_fine<T, RX, C32>;
     PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (CS > 8)
         PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     a.N = nslices;   // slices in this launch (output blocks n_first .. n_first + nslices - 1)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(CS * nslices * p->batch), 1, 1);
-    cfg.blockDim = dim3((unsigned)n, 1, 1);
+    cfg.blockDim = dim3((unsigned)(n / RX * AD_TY), 1, 1);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -546,22 +639,29 @@ pit_status launch_adv_fine_v(Problem *p, AdvArgs a, int nslices, cudaStream_t s)
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
-// double-buffered row exchange when it fits, single-buffered otherwise;
-// float-float with FP32 coefficients reads them as FP32 values
-template <class T>
-pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
+// 8 x 4 thread tiles (n threads per CTA), or 8 x 8 (n/2 threads, n >= 256)
+// where the problem selects them; float-float with FP32 coefficients reads
+// them as FP32 values
+template <class T, int RX>
+pit_status launch_adv_fine_rx(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
+    if (adv_smem<T, RX>(p->nx) > kSmemLimit) {
+        set_error("advdiff2d: the slice does not fit the cluster's shared memory");
+        return PIT_E_UNSUPPORTED;
+    }
     if constexpr (std::is_same<T, ff>::value) {
         if (p->adv_coef32) {
             a.ax = p->vx32.ptr;
             a.ay = p->vy32.ptr;
-            if (adv_smem<T, true>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, true, true>(p, a, nslices, s);
-            if (adv_smem<T, false>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, false, true>(p, a, nslices, s);
+            return launch_adv_fine_v<T, RX, true>(p, a, nslices, s);
         }
     }
-    if (adv_smem<T, true>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, true>(p, a, nslices, s);
-    if (adv_smem<T, false>(p->nx) <= kSmemLimit) return launch_adv_fine_v<T, false>(p, a, nslices, s);
-    set_error("advdiff2d: the slice does not fit the cluster's shared memory");
-    return PIT_E_UNSUPPORTED;
+    return launch_adv_fine_v<T, RX>(p, a, nslices, s);
+}
+
+template <class T>
+pit_status launch_adv_fine(Problem *p, AdvArgs a, int nslices, cudaStream_t s) {
+    if (p->adv_rx == 8 && p->nx >= 256) return launch_adv_fine_rx<T, 8>(p, a, nslices, s);
+    return launch_adv_fine_rx<T, 4>(p, a, nslices, s);
 }
 
 // ------------------------------------------------------------------ sweep
@@ -875,6 +975,33 @@ __global__ void k_scale_coeff(const double *v, double *o64, float *o32, double s
     }
 }
 
+template <class T, int RX>
+pit_status adv_check_cluster(int n) {
+    const int CS = n / AD_ROWS;
+    const size_t sm = adv_smem<T, RX>(n);
+    auto kern = k_advdiff_fine<T, RX, false>;
+    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (CS > 8) PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)CS, 1, 1);
+    cfg.blockDim = dim3((unsigned)(n / RX * AD_TY), 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    PIT_CUDA(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
+    if (clusters < 1) {
+        set_error("advdiff2d: the " + std::to_string(CS) + "-CTA cluster of the fine kernel cannot be scheduled");
+        return PIT_E_UNSUPPORTED;
+    }
+    return PIT_OK;
+}
+
 }  // namespace
 
 pit_status advdiff_setup(Problem *p) {
@@ -949,29 +1076,14 @@ pit_status advdiff_setup(Problem *p) {
             for (int k = 0; k < SWA_KMAX; ++k) p->adv_c1[k] = p->adv_c2[k] = 0.0;
         }
     }
-    // the cluster shape must be schedulable (n / 32 CTAs of one SM each)
-    const int CS = n / AD_ROWS > 0 ? n / AD_ROWS : 1;
-    const size_t sm = adv_smem<float, true>(n);
-    PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    if (CS > 8)
-        PIT_CUDA(cudaFuncSetAttribute(k_advdiff_fine<float, true>,
-                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)CS, 1, 1);
-    cfg.blockDim = dim3((unsigned)n, 1, 1);
-    cfg.dynamicSmemBytes = sm;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    PIT_CUDA(cudaOccupancyMaxActiveClusters(&clusters, k_advdiff_fine<float, true>, &cfg));
-    if (clusters < 1) {
-        set_error("advdiff2d: the " + std::to_string(CS) + "-CTA cluster of the fine kernel cannot be scheduled");
-        return PIT_E_UNSUPPORTED;
+    // PIT_ADV_RX=8: 8 x 8 thread tiles (n/2 threads per CTA) for n >= 256
+    if (const char *rx = getenv("PIT_ADV_RX")) p->adv_rx = atoi(rx) == 8 ? 8 : 4;
+    // the cluster shapes must be schedulable (n / 32 CTAs of one SM each);
+    // the float-float kernel holds the most shared memory
+    if (p->adv_rx == 8 && n >= 256) {
+        PIT_TRY((adv_check_cluster<ff, 8>(n)));
+    } else {
+        PIT_TRY((adv_check_cluster<ff, 4>(n)));
     }
     return PIT_OK;
 }

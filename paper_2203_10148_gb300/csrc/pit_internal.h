@@ -179,6 +179,7 @@ struct Problem {
     int adv_K = 8;                // Chebyshev steps of the coarse IE step
     long long adv_spin = 1LL << 26;   // polls of each bounded wait of the advdiff sweep
     int adv_coef32 = 0;           // every coefficient v / h is an FP32 value (float-float lo parts zero)
+    int adv_rx = 4;               // columns of the fine kernel's thread tiles (4, or 8 for n >= 256)
     double adv_inv_theta = 1.0, adv_c1[64] = {}, adv_c2[64] = {};   // Chebyshev coefficients
 
     // dense: fine propagator Phi and coarse matrix G (FP64 + split FP32)
