@@ -392,7 +392,10 @@ def bench_config(args, w, world):
            "N": w.N, "fine": list(w.fine), "coarse": list(w.coarse),
            "precision": args.precision, "tol": args.tol, "tol_mode": args.tol_mode,
            "inner_tol": args.inner_tol,
-           "true_residual": {"split": "split RK4 (float-float first-order term, FP32 higher-order terms)",
+           "true_residual": {"split": ("error-free splitting: 7 BF16 digit slices per operand, exact FP32 "
+                                       "diagonal sums on the tensor cores" if w.kind == "dense" else
+                                       "split RK4 (float-float first-order term, FP32 higher-order terms)")
+                             if w.kind in ("dense", "heat2d") else "float-float",
                              "ff": "float-float", "fp64": "fp64"}[args.residual],
            "l2": "working set > L2 (9 Krylov vectors x %.0f MB)" % (w.batch * (w.N + 1) * w.M * 8 / 1e6),
            "parallelism": f"replicas x{world}"}
@@ -457,6 +460,19 @@ def roofline(w, timing, peaks, nsm, sub_timing=None):
                   "tflops_executed": 3.0 * flop / (tms / 1e3) / 1e12,
                   "frac_executed": 3.0 * flop / (tms / 1e3) / 1e12 / tpeak,
                   "peak": tpeak, "peak_source": "measured bf16 burst x 0.5 (nominal TF32/BF16 ratio)"}
+        if dom == "fine_split":
+            # product by error-free splitting: 7 BF16 digit slices per operand,
+            # the 28 slice products of the diagonals s <= 8 on the tensor cores
+            # (the launch time includes splitting the block vector)
+            bf16 = (peaks or {}).get("bf16_tflops", 1900.0)
+            exe = 28.0 * flop
+            return {"bound": "tensor", "kernel": "k_gemm_oz (error-free splitting, tcgen05 BF16) + k_oz_split",
+                    "tensor_product": tc,
+                    "achieved": exe / (avg_ms / 1e3) / 1e12, "peak": bf16, "unit": "TFLOP/s (BF16 executed)",
+                    "frac": exe / (avg_ms / 1e3) / 1e12 / bf16, "traffic": None,
+                    "launch_ms": avg_ms, "launches": calls,
+                    "algorithmic_tflops": flop / (avg_ms / 1e3) / 1e12,
+                    "peak_source": "measured bf16 burst, of measured"}
         if dom == "fine_ff":
             # compensated float-float product: 12 FP32 lane-ops per multiply-add
             peak = FP32_LANES_PER_SM * nsm * sm_max * 1e6 / 1e12

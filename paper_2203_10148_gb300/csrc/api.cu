@@ -185,10 +185,13 @@ static int fine_cls(int prec) {
          : prec == PIT_SPLIT ? PIT_TIME_FINE_SPLIT : PIT_TIME_FINE_FP32;
 }
 
-// The split RK4 arithmetic exists for the 2D heat stepper; elsewhere it
-// means float-float (which DENSE outside its product runs in FP64).
+// PIT_SPLIT is the split RK4 arithmetic of the 2D heat stepper and the
+// product by error-free splitting of DENSE (where its tensor-core kernel
+// serves the problem); elsewhere it means float-float (which DENSE outside
+// its product runs in FP64).
 static int split_or_ff(const Problem *p, int prec) {
-    return (prec == PIT_SPLIT && p->kind != PIT_OP_HEAT2D) ? PIT_FF : prec;
+    if (prec != PIT_SPLIT) return prec;
+    return (p->kind == PIT_OP_HEAT2D || (p->kind == PIT_OP_DENSE && p->oz_on)) ? PIT_SPLIT : PIT_FF;
 }
 static int sweep_cls(int prec) { return prec == PIT_MIXED ? PIT_TIME_SWEEP_MIXED : PIT_TIME_SWEEP_FP64; }
 
@@ -223,7 +226,7 @@ pit_status op_sweep(Problem *p, const double *q, double *z, int prec, const Memb
 
 static pit_status fine_one(Problem *p, const double *x, double *y, int prec, cudaStream_t s) {
     prec = split_or_ff(p, prec);
-    if (prec == PIT_FF && p->kind == PIT_OP_DENSE) prec = PIT_FP64;
+    if ((prec == PIT_FF || prec == PIT_SPLIT) && p->kind == PIT_OP_DENSE) prec = PIT_FP64;
     switch (p->kind) {
     case PIT_OP_HEAT1D: return heat1d_fine_one(p, x, y, prec, s);
     case PIT_OP_HEAT2D: return heat2d_fine_one(p, x, y, prec, s);
@@ -977,7 +980,8 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->P, &p->S, &p->D, &p->K, &p->W, &p->partials, &p->states,
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32, &p->GLL32, &p->xtc_S,
                       &p->errword, &p->loopctl, &p->PhiTh, &p->PhiTl, &p->tc_split,
-                      &p->PhiBh, &p->PhiBl, &p->dtc_mats, &p->dtc_buf};
+                      &p->PhiBh, &p->PhiBl, &p->dtc_mats, &p->dtc_buf, &p->oz_phi, &p->oz_ephi,
+                      &p->oz_x, &p->oz_ex};
     for (IterGraph &g : p->igraph) iter_graph_drop(p, g);
     for (IterGraph &g : p->lgraph) iter_graph_drop(p, g);
     for (DevBuf *b : bufs) b->release();

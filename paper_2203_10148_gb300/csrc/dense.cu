@@ -1028,6 +1028,10 @@ pit_status dense_setup(Problem *p) {
     // TF32 splits of Phi for the tensor-core product
     p->use_tc = dense_tc_supported(p);
     if (p->use_tc) PIT_TRY(dense_tc_split_phi(p));
+    // digit slices of Phi for the true residual by error-free splitting
+    // (PIT_DENSE_OZ=0: the float-float product instead)
+    p->oz_on = dense_oz_supported(p) && !(getenv("PIT_DENSE_OZ") && getenv("PIT_DENSE_OZ")[0] == '0');
+    if (p->oz_on) PIT_TRY(dense_oz_setup(p));
     PIT_CUDA(cudaStreamSynchronize(s));
     work.release();
     return PIT_OK;
@@ -1067,6 +1071,10 @@ static pit_status dense_product(Problem *p, const double *x, int prec, const Mem
 pit_status dense_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                          const MemberState *st, cudaStream_t s) {
     if (prec == PIT_MIXED && p->use_tc) return dense_tc_apply(p, x, y, nullptr, mode, st, s);
+    if (prec == PIT_SPLIT) {
+        if (p->oz_on) return dense_oz_apply(p, x, y, mode, st, s);
+        prec = PIT_FF;
+    }
     // (the source rows of a residual are added by the caller)
     PIT_TRY(dense_product(p, x, prec, st, s));
     int blocks;

@@ -203,6 +203,9 @@ struct Problem {
     bool dtc_on = false;          // dense mixed sweep on the tensor cores (dense_sweep_tc.cu)
     DevBuf dtc_mats;              // its TF32 (hi, lo) splits of G and of G^(L 2^s), s < S
     DevBuf dtc_buf;               // its chunk states (ping-pong hi, lo, FP32) and barrier words
+    bool oz_on = false;           // dense true residual (PIT_SPLIT) by error-free splitting on the tensor cores
+    DevBuf oz_phi, oz_ephi;       // ... BF16 digit slices of Phi and its row exponents
+    DevBuf oz_x, oz_ex;           // ... slices and row exponents of the block vector (per product)
 
     // Krylov workspace
     DevBuf X, R, Rt, P, S, D, K, W;
@@ -281,6 +284,10 @@ pit_status add_source_rows(Problem *p, double *y, cudaStream_t s);
 void dense_teardown(Problem *p);
 bool dense_tc_supported(const Problem *p);
 pit_status dense_tc_split_phi(Problem *p);
+bool dense_oz_supported(const Problem *p);
+pit_status dense_oz_setup(Problem *p);
+pit_status dense_oz_apply(Problem *p, const double *x, double *y, int mode, const MemberState *st,
+                          cudaStream_t s);
 // TF32 (hi, lo) parts of the rows_src x M row-major FP64 x into rows_out x Mp
 // arrays (zero outside x)
 pit_status tc_split_tf32(const double *x, float *hi, float *lo, int rows_src, int rows_out, int M,

@@ -83,6 +83,75 @@ def test_dense_float_float_product(case):
     assert _rel(res, _oracle(w, "residual", X)) < 1e-10
 
 
+SPLIT_CASES = [dict(M=64, N=8, T=1.0, fine_steps=37),
+               dict(M=128, N=5, T=2.0, fine_steps=20, batch=2),
+               dict(M=256, N=70, T=10.0 * 70 / 4096, fine_steps=200),
+               dict(M=1, N=3, T=1.0, fine_steps=4),
+               dict(M=100, N=5, T=2.0, fine_steps=20, batch=2),
+               dict(M=257, N=6, T=10.0 * 6 / 4096, fine_steps=200),
+               dict(M=1000, N=130, T=10.0 * 130 / 4096, fine_steps=200, batch=2)]
+
+
+@pytest.mark.parametrize("case", SPLIT_CASES)
+def test_dense_split_product(case):
+    """The product by error-free splitting on the tensor cores (PIT_SPLIT,
+    the mixed path's default true residual: 7 slices of 6-bit digits per
+    operand, every anti-diagonal of slice products accumulated exactly in
+    FP32): within 1e-11 of the FP64 oracle like the float-float product, on
+    row counts that are not multiples of the 128-row tile, several members
+    and any M up to 1024 (operands padded to 128)."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(**case)
+    X = _rand(w, 5)
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("F", X, precision="split")
+        res = p.apply("residual", X, precision="split")
+    assert _rel(got, _oracle(w, "F", X)) < 1e-11
+    assert _rel(res, _oracle(w, "residual", X)) < 1e-10
+
+
+def test_dense_split_product_rows_of_any_scale():
+    """Each row is split relative to its own largest magnitude: zero rows,
+    rows scaled by 1e-200 and 1e200, rows whose entries span 12 decades and
+    rows of one sign.  Every element of the row x_n - Phi x_(n-1) is within
+    2^-36 sum_k |Phi_ck| |x_(n-1),k| (the splitting's bound, 2^-42 per operand
+    row maximum, with margin) plus the rounding of the final FP64
+    subtraction, 2^-53 |x_n|."""
+    from oracle.operators import dense_rk4_propagator_matrix, spatial_operator
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=128, N=9, T=1.0, fine_steps=37)
+    X = _rand(w, 9)
+    X[0, 1] = 0.0
+    X[0, 2] *= 1e-200
+    X[0, 3] *= 1e200
+    X[0, 4, ::2] *= 1e-12
+    X[0, 5] = np.abs(X[0, 5])
+    X[0, 6] = -np.abs(X[0, 6]) * 1e-30
+    Phi = dense_rk4_propagator_matrix(spatial_operator(w.kind, w.nx, w.ny, w.nu, w.vx, w.vy, w.A),
+                                      w.T / w.N, w.fine[1])
+    with pit.Problem(w, "mixed") as p:
+        got = p.apply("F", X, precision="split")[0]
+    for n in range(1, w.N + 1):
+        prod = Phi @ X[0, n - 1]
+        bound = np.abs(Phi) @ np.abs(X[0, n - 1])
+        err = np.abs(got[n] - (X[0, n] - prod))
+        assert np.all(err <= 2.0 ** -36 * bound + 2.0 ** -53 * np.abs(X[0, n]) + 1e-300), \
+            (n, err.max(), bound.max())
+    np.testing.assert_array_equal(got[0], X[0, 0])
+
+
+def test_dense_split_falls_back_beyond_its_exact_width():
+    """Beyond K = 1024 the diagonal sums are no longer exact in FP32: PIT_SPLIT
+    then runs the float-float product, bit for bit."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.dense(M=1100, N=3, T=10.0 * 3 / 4096, fine_steps=200)
+    X = _rand(w, 4)
+    with pit.Problem(w, "mixed") as p:
+        a = p.apply("F", X, precision="split")
+        b = p.apply("F", X, precision="ff")
+    np.testing.assert_array_equal(a, b)
+
+
 def test_dense_fp64_bicgstab_matches_oracle():
     from paper_2203_10148_gb300 import pit
     w = inputs.dense(M=64, N=32, T=1.0, fine_steps=50, precision="fp64")
@@ -121,10 +190,12 @@ def test_dense_full_size_sampled():
         Y = p.apply("F", Xd, precision="fp64").cpu().numpy()[0]
         Y32 = p.apply("F", Xd, precision="mixed").cpu().numpy()[0]
         Yff = p.apply("F", Xd, precision="ff").cpu().numpy()[0]
+        Ysp = p.apply("F", Xd, precision="split").cpu().numpy()[0]
     rows = [1, 2, 777, 2048, 4095, 4096]
     ref = X[0][rows] - o.F(X[0][[r - 1 for r in rows]])
     assert _rel(Y[rows], ref) < 1e-12
     assert _rel(Yff[rows], ref) < 1e-11
+    assert _rel(Ysp[rows], ref) < 1e-11
     assert _rel(Y32[rows], ref) < 1e-4
     np.testing.assert_array_equal(Y[0], X[0][0])
 
