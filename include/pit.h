@@ -85,7 +85,14 @@ typedef int pit_status;
                                    relative per product against 2^-21 for split TF32, twice
                                    the MMA rate and half the operand bytes); refinement keeps
                                    results within the tolerance.  Other operators: PIT_MIXED */
-#define PIT_SPLIT           3   /* split RK4 (HEAT2D; other operators treat it as PIT_FF):
+#define PIT_SPLIT           3   /* split arithmetic of the true residual.  DENSE: the
+                                   product Phi x by error-free splitting (Ozaki et al. 2012):
+                                   7 BF16 slices of 6-bit digits per row of Phi and of the
+                                   block vector, the slice products of each anti-diagonal
+                                   summed exactly in FP32 on the tensor cores, the sums
+                                   added in float-float (within about 2^-42 of
+                                   sum |phi| |x|); for M <= 1024, PIT_FF above.  HEAT2D:
+                                   split RK4 (other operators treat it as PIT_FF):
                                    each step u + Z u + Z^2 u/2 + Z^3 u/6 + Z^4 u/24 (Z = dt L)
                                    takes the first-order term Z u in float-float and the
                                    others in FP32 (nested form) and keeps the state in
@@ -177,8 +184,9 @@ typedef struct {
 
 /* Fills *opts with defaults: tol 1e-10, eps0 1e-8, max_iter 500, X0 coarse,
  * refine_max 8, inner_tol 1e-4, default stream, no history, PIT_SPLIT true
- * residuals (split RK4 for HEAT2D where its bound holds, float-float
- * otherwise), tolerance relative to ||R^0||. */
+ * residuals (split RK4 for HEAT2D where its bound holds, error-free
+ * splitting for DENSE with M <= 1024, float-float otherwise), tolerance
+ * relative to ||R^0||. */
 void pit_default_opts(pit_solve_opts *opts);
 
 /* Version string of the library. */
@@ -259,7 +267,8 @@ pit_status pit_problem_shape(pit_problem_t prob, int *M, int *N, int *batch);
  * stepping from FP64 inputs, or PIT_FF = float-float arithmetic, about 48
  * significant bits on the FP32 pipe: stepping for PIT_OP_HEAT2D and
  * PIT_OP_ADVDIFF2D, a compensated product for PIT_OP_DENSE; PIT_SPLIT is
- * split RK4 for PIT_OP_HEAT2D and PIT_FF elsewhere; PIT_FF is the
+ * split RK4 for PIT_OP_HEAT2D, the product by error-free splitting on the
+ * tensor cores for PIT_OP_DENSE with M <= 1024, and PIT_FF elsewhere; PIT_FF is the
  * float-float Thomas recurrence for PIT_OP_HEAT1D).  Every dense product runs on the library's kernels for
  * any M (tcgen05 split TF32 for PIT_MIXED, rows padded to 128; float-float
  * for PIT_FF, padded to 64; FP64 tiles for PIT_FP64).  G^{-1} runs
@@ -286,6 +295,7 @@ pit_status pit_serial_fine(pit_problem_t prob, int precision, double *Lam, int o
  * PIT_FP64: every step in FP64 on the device.  PIT_MIXED: iterative
  * refinement: the true residual G^{-1}(B - F X) with the fine propagations
  * in opts.residual_precision (PIT_SPLIT by default: split RK4 for HEAT2D,
+ * error-free splitting on the tensor cores for DENSE with M <= 1024,
  * float-float on the FP32 pipe elsewhere; PIT_FF or PIT_FP64 on request),
  * an FP32-fine /
  * FP64-Krylov inner solve of the correction to inner_tol, X += correction,

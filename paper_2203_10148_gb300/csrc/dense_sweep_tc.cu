@@ -449,20 +449,14 @@ pit_status dense_tc_sweep(Problem *p, const double *q, double *z, const MemberSt
         p->dtc_on = false;   // the CUDA-core sweep takes over
         return PIT_OK;
     }
-    // a cooperative cluster launch where the runtime takes one, else the
-    // clusters alone (all resident by the occupancy check above; the grid
-    // barrier's wait is bounded either way); a refused launch leaves the
-    // sweep to the CUDA-core kernel
+    // only a cooperative launch guarantees that every CTA of the grid
+    // barrier is resident; where the runtime refuses it (a profiler, a
+    // device shared with other work) the CUDA-core sweep takes over
     cudaError_t e = cudaLaunchKernelEx(&cfg, k_dense_sweep_tc, mp, a);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_dense_sweep_tc, mp, a);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            p->dtc_on = false;
-            return PIT_OK;
-        }
+        p->dtc_on = false;
+        return PIT_OK;
     }
     PIT_LAUNCH_CHECK();
     *launched = true;
