@@ -189,3 +189,25 @@ def test_advdiff_sweep_large_grids(n, N, batch):
         got32 = p.apply("Ginv", X, precision="mixed")
     assert _rel(got64, ref) < 1e-12
     assert _rel(got32, ref) < 1e-5
+
+
+@pytest.mark.parametrize("n,N,batch", [(256, 2, 2), (512, 2, 1)])
+def test_advdiff_fine_wide_tiles_match(n, N, batch, monkeypatch):
+    """8 x 8 thread tiles (PIT_ADV_RX=8: n/2 threads per CTA, for n >= 256)
+    against the default 8 x 4 tiles: every point takes the same operations
+    on the same operands (rows r and r + 4 share a packed pair in both), so
+    the FP32, float-float and FP64 fine operators agree bit for bit, and
+    with the oracle."""
+    from paper_2203_10148_gb300 import pit
+    w = inputs.advdiff2d(n=n, N=N, T=0.5 * N / 256, batch=batch)
+    X = _rand(w, 17)
+    out = {}
+    for rx in ("4", "8"):
+        monkeypatch.setenv("PIT_ADV_RX", rx)
+        with pit.Problem(w, "mixed") as p:
+            out[rx] = [p.apply("F", X, precision=pr) for pr in ("mixed", "ff", "fp64")]
+    for a, b in zip(out["4"], out["8"]):
+        np.testing.assert_array_equal(a, b)
+    ref = np.stack([OracleProblem.from_workload(w, member=b).apply_F(X[b]) for b in range(w.batch)])
+    assert _rel(out["8"][2], ref) < 1e-12
+    assert _rel(out["8"][1], ref) < 1e-11
