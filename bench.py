@@ -426,6 +426,17 @@ def sweep_cost(w, timing, total_ms, steps):
             "share": ms / total_ms}
 
 
+def heat1d_uses_matrix(w):
+    """The library's choice for the 1D heat FP64 fine batch: the propagator
+    matrix where M^2 multiply-adds per slice undercut the m stepping
+    instructions (PIT_HEAT1D_PHI=0 keeps the steps)."""
+    if os.environ.get("PIT_HEAT1D_PHI", "1").startswith("0") or w.M > 256:
+        return False
+    m = w.fine[1]
+    E = 2 if w.M <= 64 else 4 if w.M <= 128 else 8
+    return w.M * w.M < 0.5 * m * 32.0 * (5 * E + 8) and w.M * w.M * m <= 1e8
+
+
 def roofline(w, timing, peaks, nsm, sub_timing=None):
     """Roofline of the dominant fine-propagator kernel class, from the
     per-class CUDA-event times recorded inside the timed solves; the FP32
@@ -498,6 +509,17 @@ def roofline(w, timing, peaks, nsm, sub_timing=None):
         flop = point_steps * 8.0
         peak = FP64_LANES_PER_SM * 2 * nsm * sm_max * 1e6 / 1e12
         ach = flop / (avg_ms / 1e3) / 1e12
+        if dom == "fine_fp64" and heat1d_uses_matrix(w):
+            # the m steps of a slice as one product with Phi = A^{-m} (M^2 FMA)
+            mflop = 2.0 * w.batch * w.N * w.M * w.M
+            mach = mflop / (avg_ms / 1e3) / 1e12
+            return {"bound": "latency", "kernel": "k_heat1d_fine_phi (FP64 propagator matrix)",
+                    "achieved": mach, "peak": peak, "unit": "TFLOP/s (FP64, 2 M^2 flop per slice)",
+                    "frac": mach / peak, "traffic": None, "launch_ms": avg_ms, "launches": calls,
+                    "equivalent_step_tflops": ach,
+                    "note": "one CTA per slice, a row per thread: a few microseconds of launch and "
+                            "load latency, far from the FP64 pipe's roofline",
+                    "peak_source": "derived: 4 FP64 flop/clk/SM x SMs x max SM clock"}
         kname = "k_heat1d_fine_warp" if w.M <= 256 else "k_heat1d_fine"
         return {"bound": "latency", "kernel": "%s<%s>" % (kname, "double" if dom == "fine_fp64" else "float"),
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s (FP64, 8 flop per point-step)",

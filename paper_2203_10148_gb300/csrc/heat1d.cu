@@ -20,6 +20,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -504,6 +505,48 @@ __global__ void __launch_bounds__(32) k_heat1d_fine_warp(Heat1dArgs a, const T *
     }
 }
 
+// FP64 fine batch through the propagator matrix (small grids): the m
+// implicit-Euler steps of a slice are one fixed linear map Phi = A^{-m},
+// formed once on the host; one CTA per (slice, member) forms Phi x_{n-1},
+// a row per thread, with x_{n-1} in shared memory and Phi stored by columns
+// (phiT[j * M + i] = Phi_ij: at each j the threads read consecutive words).
+__global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const double *__restrict__ phiT) {
+    extern __shared__ double xs[];
+    const int b = blockIdx.y;
+    if (!runs(a.st, b)) return;
+    const int n = a.n_first + blockIdx.x;
+    const int M = a.M;
+    const size_t mb = (size_t)b * a.blen;
+    const double *xin = a.x + mb + (size_t)(n - 1) * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) xs[i] = xin[i];
+    __syncthreads();
+    double *yo = a.y + mb + (size_t)n * M;
+    const double *xn = a.x + mb + (size_t)n * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        // four partial sums over j mod 4, added pairwise
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = 0;
+        for (; j + 3 < M; j += 4) {
+            s0 = fma(phiT[(size_t)j * M + i], xs[j], s0);
+            s1 = fma(phiT[(size_t)(j + 1) * M + i], xs[j + 1], s1);
+            s2 = fma(phiT[(size_t)(j + 2) * M + i], xs[j + 2], s2);
+            s3 = fma(phiT[(size_t)(j + 3) * M + i], xs[j + 3], s3);
+        }
+        for (; j < M; ++j) s0 = fma(phiT[(size_t)j * M + i], xs[j], s0);
+        const double v = (s0 + s1) + (s2 + s3);
+        if (a.mode == FINE_APPLY) yo[i] = xn[i] - v;
+        else if (a.mode == FINE_RESIDUAL) yo[i] = v - xn[i];
+        else yo[i] = v;
+    }
+    if (n == 1 && a.mode != 2) {
+        // row 0 of eq. (4): (F X)_0 = x_0; residual: y0 - x_0
+        const double *x0 = a.x + mb;
+        double *y0o = a.y + mb;
+        for (int i = threadIdx.x; i < M; i += blockDim.x)
+            y0o[i] = (a.mode == FINE_APPLY) ? x0[i] : a.y0[(size_t)b * M + i] - x0[i];
+    }
+}
+
 // FP64 coarse sweep on small grids, one warp per member:
 // z_0 = q_0, z_n = q_n + G z_{n-1}.
 template <int E>
@@ -705,6 +748,13 @@ pit_status dispatch_warp(int M, F &&f) {
 }
 
 pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStream_t s) {
+    if (prec == PIT_FP64 && p->h1_phi_on) {
+        const int nt = std::min(256, (p->M + 31) / 32 * 32);
+        k_heat1d_fine_phi<<<dim3(nslices, p->batch), nt, (size_t)p->M * sizeof(double), s>>>(
+            a, p->h1_phiT.as<double>());
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
     if (p->M <= WARP_MAXM && p->heat1d_small) {
         if (prec == PIT_FP64) {
             FineWarpLaunch<double> f{p, a, nslices, &p->fine_inv64, s};
@@ -729,6 +779,30 @@ pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStre
     return dispatch_1d(p->M, f);
 }
 
+// Phi = A^{-m}, A = tridiag(-r, 1 + 2r, -r): column j is m Thomas solves of
+// the unit vector e_j in FP64 (A^{-1} contracts, so the rounding of each
+// solve is not amplified); uploaded by columns (phiT[j * M + i] = Phi_ij).
+pit_status upload_fine_matrix(Problem *p, double r) {
+    const int M = p->M, m = p->fine_steps;
+    std::vector<double> fm, inv, cp;
+    thomas_factors(M, r, fm, inv, cp);
+    std::vector<double> phiT((size_t)M * M), d(M);
+    for (int j = 0; j < M; ++j) {
+        for (int i = 0; i < M; ++i) d[i] = (i == j) ? 1.0 : 0.0;
+        for (int s = 0; s < m; ++s) {
+            d[0] = inv[0] * d[0];
+            for (int i = 1; i < M; ++i) d[i] = fm[i] * d[i - 1] + inv[i] * d[i];
+            for (int i = M - 2; i >= 0; --i) d[i] = d[i] - cp[i] * d[i + 1];
+        }
+        for (int i = 0; i < M; ++i) phiT[(size_t)j * M + i] = d[i];
+    }
+    PIT_TRY(p->h1_phiT.ensure(phiT.size() * sizeof(double)));
+    PIT_CUDA(cudaMemcpyAsync(p->h1_phiT.ptr, phiT.data(), phiT.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             p->stream));
+    PIT_CUDA(cudaStreamSynchronize(p->stream));   // phiT is a local buffer
+    return PIT_OK;
+}
+
 }  // namespace
 
 pit_status heat1d_setup(Problem *p) {
@@ -749,6 +823,18 @@ pit_status heat1d_setup(Problem *p) {
     const double rc = (p->dT / p->coarse_steps) * p->nu / (h * h);
     // fine factors in fine_inv64/32, coarse in coarse_inv64/32 (fm | inv | cp)
     PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32, p->stream, &p->fine_invff));
+    // FP64 fine batch as one matrix product where that is cheaper than the
+    // steps: M^2 multiply-adds per slice against m steps of the one-warp
+    // Thomas kernel (about 32 (5E + 8) lane operations each, E = 2, 4, 8
+    // points per lane); PIT_HEAT1D_PHI=0 keeps the steps
+    {
+        const int M = p->M, m = p->fine_steps;
+        const int E = M <= 64 ? 2 : M <= 128 ? 4 : 8;
+        const char *pe = getenv("PIT_HEAT1D_PHI");
+        p->h1_phi_on = M <= WARP_MAXM && (double)M * M < 0.5 * m * 32.0 * (5 * E + 8) &&
+                       (double)M * M * m <= 1e8 && !(pe && pe[0] == '0');
+        if (p->h1_phi_on) PIT_TRY(upload_fine_matrix(p, rf));
+    }
     PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32, p->stream));
     // mixed path: the coarse step (I - dTc nu D2)^{-c} is diagonal in the sine
     // basis (eigenvalues mu_k = -4/h^2 sin^2(k pi h / 2), k = 1..M), so the

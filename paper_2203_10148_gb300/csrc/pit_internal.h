@@ -164,6 +164,8 @@ struct Problem {
     DevBuf fine_inv32, fine_cp32, coarse_inv32, coarse_cp32;
     DevBuf fine_invff;            // heat1d: fine Thomas factors as float-float (hi, lo) pairs
     int heat1d_small = 0;         // heat1d, M <= 256: one-warp kernels (else CTA-wide scans)
+    int h1_phi_on = 0;            // heat1d FP64 fine batch through the propagator matrix A^{-m}
+    DevBuf h1_phiT;               // ... its columns (M x M, FP64)
     double fine_off = 0, coarse_off = 0;   // off-diagonal -dt nu / h^2
 
     // heat2d: sine basis S_jk = sin(pi j k/(n+1)) and coarse mode factors

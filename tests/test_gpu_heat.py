@@ -83,6 +83,30 @@ SMALL_CASES = [dict(M=1, N=3, fine_steps=4), dict(M=31, N=5, fine_steps=7),
                dict(M=256, N=4, fine_steps=6)]
 
 
+PHI_CASES = [dict(M=63, N=16, fine_steps=100, batch=3), dict(M=31, N=5, fine_steps=7),
+             dict(M=1, N=3, fine_steps=4), dict(M=250, N=5, fine_steps=400, batch=2)]
+
+
+@pytest.mark.parametrize("case", PHI_CASES)
+def test_heat1d_fine_propagator_matrix(case, monkeypatch):
+    """Small grids with many fine steps: the FP64 fine batch as one product
+    with Phi = A^{-m} (formed on the host by m Thomas solves of each unit
+    vector) instead of m steps per slice; within 1e-13 of the oracle and of
+    the stepping kernel (PIT_HEAT1D_PHI=0), for F, the residual and a solve."""
+    pit = _pit()
+    w = inputs.heat1d(**case)
+    X = _rand_block(w, 73)
+    out = {}
+    for phi in ("1", "0"):
+        monkeypatch.setenv("PIT_HEAT1D_PHI", phi)
+        with pit.Problem(w, "fp64") as p:
+            out[phi] = [p.apply(which, X) for which in ("F", "residual")]
+    for which, g, t in zip(("F", "residual"), out["1"], out["0"]):
+        ref = _oracle_apply(w, which, X)
+        assert _rel(g, ref) < 1e-13, which
+        assert _rel(g, t) < 1e-13, which
+
+
 @pytest.mark.parametrize("variant", ["warp", "cta"])
 @pytest.mark.parametrize("case", SMALL_CASES)
 def test_heat1d_small_grid_kernels(variant, case, monkeypatch):
@@ -90,6 +114,7 @@ def test_heat1d_small_grid_kernels(variant, case, monkeypatch):
     once per launch; E = 2, 4, 8 points per lane) and the CTA-wide scans,
     each in FP64, float-float and FP32, against the oracle."""
     monkeypatch.setenv("PIT_HEAT1D_SMALL", variant)
+    monkeypatch.setenv("PIT_HEAT1D_PHI", "0")   # the steps, not the propagator matrix
     pit = _pit()
     w = inputs.heat1d(**case)
     X = _rand_block(w, 71)
