@@ -981,7 +981,7 @@ pit_status pit_problem_destroy(pit_problem_t h) {
                       &p->flags_host_mirror, &p->fine_tmp, &p->q32, &p->GL32, &p->GLL32, &p->xtc_S,
                       &p->errword, &p->loopctl, &p->PhiTh, &p->PhiTl, &p->tc_split,
                       &p->PhiBh, &p->PhiBl, &p->dtc_mats, &p->dtc_buf, &p->oz_phi, &p->oz_ephi,
-                      &p->oz_x, &p->oz_ex, &p->h1_phiT};
+                      &p->oz_x, &p->oz_ex, &p->h1_phiT, &p->h1_powT, &p->h1_sweep_t};
     for (IterGraph &g : p->igraph) iter_graph_drop(p, g);
     for (IterGraph &g : p->lgraph) iter_graph_drop(p, g);
     for (DevBuf *b : bufs) b->release();

@@ -547,6 +547,64 @@ __global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const dou
     }
 }
 
+// FP64 coarse sweep on small grids through the powers of G: the solution
+// of eq. (7)'s block-bidiagonal system is z_n = sum_{k <= n} G^(n-k) q_k, so
+// with G^j formed once (j = 1..N, by columns: powT[(j-1) M^2 + c M + r] =
+// (G^j)_rc) every product t_{n,k} = G^(n-k) q_k is independent: one CTA per
+// (n, k) forms it (stage 1), one CTA per n sums t_{n,0..n} in that order
+// (stage 2).  t is laid out per member as (N+1)(N+2)/2 rows of M, pair
+// (n, k) at row n(n+1)/2 + k.  q and z may be the same array.
+__global__ void __launch_bounds__(256) k_heat1d_sweep_pow1(const double *__restrict__ q, double *__restrict__ t,
+                                                           const double *__restrict__ powT, int M, int N,
+                                                           size_t blen, const MemberState *st) {
+    extern __shared__ double qs[];
+    const int b = blockIdx.y;
+    if (!runs(st, b)) return;
+    const int pidx = blockIdx.x;
+    // pair index -> (n, k): n(n+1)/2 <= pidx < (n+1)(n+2)/2
+    int n = (int)((sqrt(8.0 * pidx + 1.0) - 1.0) * 0.5);
+    while ((n + 1) * (n + 2) / 2 <= pidx) ++n;
+    while (n * (n + 1) / 2 > pidx) --n;
+    const int k = pidx - n * (n + 1) / 2;
+    const size_t npairs = (size_t)(N + 1) * (N + 2) / 2;
+    const double *qk = q + (size_t)b * blen + (size_t)k * M;
+    double *tp = t + ((size_t)b * npairs + pidx) * M;
+    if (k == n) {
+        for (int i = threadIdx.x; i < M; i += blockDim.x) tp[i] = qk[i];
+        return;
+    }
+    for (int i = threadIdx.x; i < M; i += blockDim.x) qs[i] = qk[i];
+    __syncthreads();
+    const double *P = powT + (size_t)(n - k - 1) * M * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = 0;
+        for (; j + 3 < M; j += 4) {
+            s0 = fma(P[(size_t)j * M + i], qs[j], s0);
+            s1 = fma(P[(size_t)(j + 1) * M + i], qs[j + 1], s1);
+            s2 = fma(P[(size_t)(j + 2) * M + i], qs[j + 2], s2);
+            s3 = fma(P[(size_t)(j + 3) * M + i], qs[j + 3], s3);
+        }
+        for (; j < M; ++j) s0 = fma(P[(size_t)j * M + i], qs[j], s0);
+        tp[i] = (s0 + s1) + (s2 + s3);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_heat1d_sweep_pow2(const double *__restrict__ t, double *__restrict__ z,
+                                                           int M, int N, size_t blen, const MemberState *st) {
+    const int b = blockIdx.y;
+    if (!runs(st, b)) return;
+    const int n = blockIdx.x;
+    const size_t npairs = (size_t)(N + 1) * (N + 2) / 2;
+    const double *tn = t + ((size_t)b * npairs + (size_t)n * (n + 1) / 2) * M;
+    double *zn = z + (size_t)b * blen + (size_t)n * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k <= n; ++k) acc += tn[(size_t)k * M + i];
+        zn[i] = acc;
+    }
+}
+
 // FP64 coarse sweep on small grids, one warp per member:
 // z_0 = q_0, z_n = q_n + G z_{n-1}.
 template <int E>
@@ -782,6 +840,17 @@ pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStre
 // Phi = A^{-m}, A = tridiag(-r, 1 + 2r, -r): column j is m Thomas solves of
 // the unit vector e_j in FP64 (A^{-1} contracts, so the rounding of each
 // solve is not amplified); uploaded by columns (phiT[j * M + i] = Phi_ij).
+// `times` implicit-Euler solves A d <- d in place (Thomas, FP64).
+void solve_times(const std::vector<double> &fm, const std::vector<double> &inv, const std::vector<double> &cp,
+                 std::vector<double> &d, int times) {
+    const int M = (int)d.size();
+    for (int s = 0; s < times; ++s) {
+        d[0] = inv[0] * d[0];
+        for (int i = 1; i < M; ++i) d[i] = fm[i] * d[i - 1] + inv[i] * d[i];
+        for (int i = M - 2; i >= 0; --i) d[i] = d[i] - cp[i] * d[i + 1];
+    }
+}
+
 pit_status upload_fine_matrix(Problem *p, double r) {
     const int M = p->M, m = p->fine_steps;
     std::vector<double> fm, inv, cp;
@@ -789,17 +858,35 @@ pit_status upload_fine_matrix(Problem *p, double r) {
     std::vector<double> phiT((size_t)M * M), d(M);
     for (int j = 0; j < M; ++j) {
         for (int i = 0; i < M; ++i) d[i] = (i == j) ? 1.0 : 0.0;
-        for (int s = 0; s < m; ++s) {
-            d[0] = inv[0] * d[0];
-            for (int i = 1; i < M; ++i) d[i] = fm[i] * d[i - 1] + inv[i] * d[i];
-            for (int i = M - 2; i >= 0; --i) d[i] = d[i] - cp[i] * d[i + 1];
-        }
+        solve_times(fm, inv, cp, d, m);
         for (int i = 0; i < M; ++i) phiT[(size_t)j * M + i] = d[i];
     }
     PIT_TRY(p->h1_phiT.ensure(phiT.size() * sizeof(double)));
     PIT_CUDA(cudaMemcpyAsync(p->h1_phiT.ptr, phiT.data(), phiT.size() * sizeof(double), cudaMemcpyHostToDevice,
                              p->stream));
     PIT_CUDA(cudaStreamSynchronize(p->stream));   // phiT is a local buffer
+    return PIT_OK;
+}
+
+// G^j = (A_c^{-c})^j for j = 1..N by columns: column c of G^j is c more
+// coarse solves of column c of G^(j-1), so each carries only the rounding
+// of j c contracting solves.
+pit_status upload_sweep_powers(Problem *p, double r) {
+    const int M = p->M, N = p->N, c = p->coarse_steps;
+    std::vector<double> fm, inv, cp;
+    thomas_factors(M, r, fm, inv, cp);
+    std::vector<double> powT((size_t)N * M * M), d(M);
+    for (int col = 0; col < M; ++col) {
+        for (int i = 0; i < M; ++i) d[i] = (i == col) ? 1.0 : 0.0;
+        for (int j = 1; j <= N; ++j) {
+            solve_times(fm, inv, cp, d, c);
+            for (int i = 0; i < M; ++i) powT[(size_t)(j - 1) * M * M + (size_t)col * M + i] = d[i];
+        }
+    }
+    PIT_TRY(p->h1_powT.ensure(powT.size() * sizeof(double)));
+    PIT_CUDA(cudaMemcpyAsync(p->h1_powT.ptr, powT.data(), powT.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             p->stream));
+    PIT_CUDA(cudaStreamSynchronize(p->stream));   // powT is a local buffer
     return PIT_OK;
 }
 
@@ -834,6 +921,16 @@ pit_status heat1d_setup(Problem *p) {
         p->h1_phi_on = M <= WARP_MAXM && (double)M * M < 0.5 * m * 32.0 * (5 * E + 8) &&
                        (double)M * M * m <= 1e8 && !(pe && pe[0] == '0');
         if (p->h1_phi_on) PIT_TRY(upload_fine_matrix(p, rf));
+    }
+    // FP64 sweep through the powers of G where the (N+1)(N+2)/2 independent
+    // products stay small (PIT_HEAT1D_POW=0 keeps the sequential solves)
+    {
+        const int M = p->M, N = p->N;
+        const double pairs = 0.5 * (N + 1.0) * (N + 2.0);
+        const char *pe = getenv("PIT_HEAT1D_POW");
+        p->h1_pow_on = M <= WARP_MAXM && N <= 128 && pairs * M * M <= 4e6 &&
+                       (double)N * M * M * p->coarse_steps <= 1e8 && !(pe && pe[0] == '0');
+        if (p->h1_pow_on) PIT_TRY(upload_sweep_powers(p, rc));
     }
     PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32, p->stream));
     // mixed path: the coarse step (I - dTc nu D2)^{-c} is diagonal in the sine
@@ -878,6 +975,19 @@ pit_status heat1d_fine_one(Problem *p, const double *x, double *y, int prec, cud
 
 pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec, const MemberState *st,
                         cudaStream_t s) {
+    if (prec == PIT_FP64 && p->h1_pow_on) {
+        const int M = p->M, N = p->N;
+        const size_t npairs = (size_t)(N + 1) * (N + 2) / 2;
+        PIT_TRY(p->h1_sweep_t.ensure((size_t)p->batch * npairs * M * sizeof(double)));
+        const int nt = std::min(256, (M + 31) / 32 * 32);
+        k_heat1d_sweep_pow1<<<dim3((unsigned)npairs, p->batch), nt, (size_t)M * sizeof(double), s>>>(
+            q, p->h1_sweep_t.as<double>(), p->h1_powT.as<double>(), M, N, p->blen, st);
+        PIT_LAUNCH_CHECK();
+        k_heat1d_sweep_pow2<<<dim3((unsigned)(N + 1), p->batch), nt, 0, s>>>(p->h1_sweep_t.as<double>(), z, M, N,
+                                                                             p->blen, st);
+        PIT_LAUNCH_CHECK();
+        return PIT_OK;
+    }
     if (prec == PIT_FP64 && p->M <= WARP_MAXM && p->heat1d_small) {
         SweepWarpLaunch f{p, q, z, st, s};
         return dispatch_warp(p->M, f);

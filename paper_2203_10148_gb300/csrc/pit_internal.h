@@ -166,6 +166,8 @@ struct Problem {
     int heat1d_small = 0;         // heat1d, M <= 256: one-warp kernels (else CTA-wide scans)
     int h1_phi_on = 0;            // heat1d FP64 fine batch through the propagator matrix A^{-m}
     DevBuf h1_phiT;               // ... its columns (M x M, FP64)
+    int h1_pow_on = 0;            // heat1d FP64 sweep through the powers G^j (independent products)
+    DevBuf h1_powT, h1_sweep_t;   // ... G^1..G^N by columns, and the products G^(n-k) q_k
     double fine_off = 0, coarse_off = 0;   // off-diagonal -dt nu / h^2
 
     // heat2d: sine basis S_jk = sin(pi j k/(n+1)) and coarse mode factors

@@ -107,6 +107,33 @@ def test_heat1d_fine_propagator_matrix(case, monkeypatch):
         assert _rel(g, t) < 1e-13, which
 
 
+POW_CASES = [dict(), dict(M=31, N=5, fine_steps=7), dict(M=100, N=3, fine_steps=20, batch=2),
+             dict(M=1, N=2, fine_steps=3), dict(M=63, N=40, fine_steps=10, batch=2)]
+
+
+@pytest.mark.parametrize("case", POW_CASES)
+def test_heat1d_sweep_through_powers(case, monkeypatch):
+    """Small grids: the FP64 sweep as the independent products G^(n-k) q_k
+    (G^j formed on the host by j coarse solves per column) summed over k in
+    order, instead of N dependent solves; within 1e-13 of the oracle and of
+    the sequential sweep (PIT_HEAT1D_POW=0), also in place (the solver's use)
+    and through a converged solve."""
+    pit = _pit()
+    w = inputs.heat1d(**case)
+    X = _rand_block(w, 79)
+    out = {}
+    for pw in ("1", "0"):
+        monkeypatch.setenv("PIT_HEAT1D_POW", pw)
+        with pit.Problem(w, "fp64") as p:
+            out[pw] = [p.apply(which, X) for which in ("Ginv", "GinvF", "residual")]
+            Xs, info = p.bicgstab_solve(tol=1e-10)
+            out[pw].append(np.array(Xs))
+    for which, g, t in zip(("Ginv", "GinvF", "residual"), out["1"], out["0"]):
+        assert _rel(g, _oracle_apply(w, which, X)) < 1e-13, which
+        assert _rel(g, t) < 1e-13, which
+    assert _rel(out["1"][3], out["0"][3]) < 1e-11
+
+
 @pytest.mark.parametrize("variant", ["warp", "cta"])
 @pytest.mark.parametrize("case", SMALL_CASES)
 def test_heat1d_small_grid_kernels(variant, case, monkeypatch):
@@ -115,6 +142,7 @@ def test_heat1d_small_grid_kernels(variant, case, monkeypatch):
     each in FP64, float-float and FP32, against the oracle."""
     monkeypatch.setenv("PIT_HEAT1D_SMALL", variant)
     monkeypatch.setenv("PIT_HEAT1D_PHI", "0")   # the steps, not the propagator matrix
+    monkeypatch.setenv("PIT_HEAT1D_POW", "0")   # the sequential sweep, not the powers of G
     pit = _pit()
     w = inputs.heat1d(**case)
     X = _rand_block(w, 71)
