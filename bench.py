@@ -430,7 +430,8 @@ def heat1d_uses_matrix(w):
     """The library's choice for the 1D heat FP64 fine batch: the propagator
     matrix where M^2 multiply-adds per slice undercut the m stepping
     instructions (PIT_HEAT1D_PHI=0 keeps the steps)."""
-    if os.environ.get("PIT_HEAT1D_PHI", "1").startswith("0") or w.M > 256:
+    if (os.environ.get("PIT_HEAT1D_PHI", "1").startswith("0") or w.M > 256
+            or getattr(w, "precision", "fp64") != "fp64"):
         return False
     m = w.fine[1]
     E = 2 if w.M <= 64 else 4 if w.M <= 128 else 8

@@ -910,15 +910,18 @@ pit_status heat1d_setup(Problem *p) {
     const double rc = (p->dT / p->coarse_steps) * p->nu / (h * h);
     // fine factors in fine_inv64/32, coarse in coarse_inv64/32 (fm | inv | cp)
     PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32, p->stream, &p->fine_invff));
-    // FP64 fine batch as one matrix product where that is cheaper than the
-    // steps: M^2 multiply-adds per slice against m steps of the one-warp
-    // Thomas kernel (about 32 (5E + 8) lane operations each, E = 2, 4, 8
-    // points per lane); PIT_HEAT1D_PHI=0 keeps the steps
+    // FP64 problems: the fine batch as one matrix product where that is
+    // cheaper than the steps: M^2 multiply-adds per slice against m steps of
+    // the one-warp Thomas kernel (about 32 (5E + 8) lane operations each,
+    // E = 2, 4, 8 points per lane); PIT_HEAT1D_PHI=0 keeps the steps.  The
+    // matrices are formed on the host at set-up, so problems of the other
+    // precisions (a served request, a mixed solve), whose solves run no FP64
+    // fine batch, keep the steps for the FP64 calls they may make
     {
         const int M = p->M, m = p->fine_steps;
         const int E = M <= 64 ? 2 : M <= 128 ? 4 : 8;
         const char *pe = getenv("PIT_HEAT1D_PHI");
-        p->h1_phi_on = M <= WARP_MAXM && (double)M * M < 0.5 * m * 32.0 * (5 * E + 8) &&
+        p->h1_phi_on = p->precision == PIT_FP64 && M <= WARP_MAXM && (double)M * M < 0.5 * m * 32.0 * (5 * E + 8) &&
                        (double)M * M * m <= 1e8 && !(pe && pe[0] == '0');
         if (p->h1_phi_on) PIT_TRY(upload_fine_matrix(p, rf));
     }
@@ -928,7 +931,7 @@ pit_status heat1d_setup(Problem *p) {
         const int M = p->M, N = p->N;
         const double pairs = 0.5 * (N + 1.0) * (N + 2.0);
         const char *pe = getenv("PIT_HEAT1D_POW");
-        p->h1_pow_on = M <= WARP_MAXM && N <= 128 && pairs * M * M <= 4e6 &&
+        p->h1_pow_on = p->precision == PIT_FP64 && M <= WARP_MAXM && N <= 128 && pairs * M * M <= 4e6 &&
                        (double)N * M * M * p->coarse_steps <= 1e8 && !(pe && pe[0] == '0');
         if (p->h1_pow_on) PIT_TRY(upload_sweep_powers(p, rc));
     }
