@@ -505,13 +505,57 @@ __global__ void __launch_bounds__(32) k_heat1d_fine_warp(Heat1dArgs a, const T *
     }
 }
 
+// y_i = sum_j A_ij x_j for row i = threadIdx.x (the CTA has at least M
+// threads; A stored by columns, At[j * M + i]; x in shared memory): 32
+// columns at a time (contiguous in At) are copied into shared memory with
+// asynchronous 16-byte copies issued back to back by all threads (one memory
+// latency per block of columns, not one per load), then each thread adds its
+// row over them in four partial sums (columns j mod 4, in order); returns
+// (s0 + s1) + (s2 + s3).  `as` is 16-byte aligned.  Every thread of the CTA
+// must call it.
+constexpr int H1_JB = 32;
+// stride of the matrices G^j: M^2 rounded up to even, so that every matrix
+// (and so every 32-column block of it) starts on a 16-byte boundary
+__host__ __device__ __forceinline__ size_t h1_pow_stride(int M) { return ((size_t)M * M + 1) & ~(size_t)1; }
+constexpr int H1_SMEM_MAX = (258 + H1_JB * 256) * (int)sizeof(double);   // M <= 256
+__device__ __forceinline__ double h1_matvec_row(const double *__restrict__ At, const double *xs, double *as,
+                                                int M) {
+    const int i = threadIdx.x;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int j0 = 0; j0 < M; j0 += H1_JB) {
+        const int jn = min(H1_JB, M - j0);
+        const int nd = jn * M;
+        const double *src = At + (size_t)j0 * M;   // 16-byte aligned: j0 M is even
+        __syncthreads();   // the previous block's reads are done (and x is stored)
+        for (int t = threadIdx.x; t < nd / 2; t += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(as + 2 * t)),
+                         "l"(src + 2 * t)
+                         : "memory");
+        if ((nd & 1) && threadIdx.x == 0) as[nd - 1] = src[nd - 1];
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if (i < M) {
+            int j = 0;
+            for (; j + 3 < jn; j += 4) {
+                a0 = fma(as[j * M + i], xs[j0 + j], a0);
+                a1 = fma(as[(j + 1) * M + i], xs[j0 + j + 1], a1);
+                a2 = fma(as[(j + 2) * M + i], xs[j0 + j + 2], a2);
+                a3 = fma(as[(j + 3) * M + i], xs[j0 + j + 3], a3);
+            }
+            for (; j < jn; ++j) a0 = fma(as[j * M + i], xs[j0 + j], a0);
+        }
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
 // FP64 fine batch through the propagator matrix (small grids): the m
 // implicit-Euler steps of a slice are one fixed linear map Phi = A^{-m},
 // formed once on the host; one CTA per (slice, member) forms Phi x_{n-1},
 // a row per thread, with x_{n-1} in shared memory and Phi stored by columns
 // (phiT[j * M + i] = Phi_ij: at each j the threads read consecutive words).
 __global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const double *__restrict__ phiT) {
-    extern __shared__ double xs[];
+    extern __shared__ __align__(16) double xs[];   // x_{n-1}, then 32 columns of Phi
     const int b = blockIdx.y;
     if (!runs(a.st, b)) return;
     const int n = a.n_first + blockIdx.x;
@@ -519,21 +563,10 @@ __global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const dou
     const size_t mb = (size_t)b * a.blen;
     const double *xin = a.x + mb + (size_t)(n - 1) * M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) xs[i] = xin[i];
-    __syncthreads();
+    const double v = h1_matvec_row(phiT, xs, xs + ((M + 1) & ~1), M);
     double *yo = a.y + mb + (size_t)n * M;
     const double *xn = a.x + mb + (size_t)n * M;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        // four partial sums over j mod 4, added pairwise
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int j = 0;
-        for (; j + 3 < M; j += 4) {
-            s0 = fma(phiT[(size_t)j * M + i], xs[j], s0);
-            s1 = fma(phiT[(size_t)(j + 1) * M + i], xs[j + 1], s1);
-            s2 = fma(phiT[(size_t)(j + 2) * M + i], xs[j + 2], s2);
-            s3 = fma(phiT[(size_t)(j + 3) * M + i], xs[j + 3], s3);
-        }
-        for (; j < M; ++j) s0 = fma(phiT[(size_t)j * M + i], xs[j], s0);
-        const double v = (s0 + s1) + (s2 + s3);
+    if (const int i = threadIdx.x; i < M) {
         if (a.mode == FINE_APPLY) yo[i] = xn[i] - v;
         else if (a.mode == FINE_RESIDUAL) yo[i] = v - xn[i];
         else yo[i] = v;
@@ -549,15 +582,15 @@ __global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const dou
 
 // FP64 coarse sweep on small grids through the powers of G: the solution
 // of eq. (7)'s block-bidiagonal system is z_n = sum_{k <= n} G^(n-k) q_k, so
-// with G^j formed once (j = 1..N, by columns: powT[(j-1) M^2 + c M + r] =
-// (G^j)_rc) every product t_{n,k} = G^(n-k) q_k is independent: one CTA per
-// (n, k) forms it (stage 1), one CTA per n sums t_{n,0..n} in that order
-// (stage 2).  t is laid out per member as (N+1)(N+2)/2 rows of M, pair
+// with G^j formed once (j = 1..N, by columns: powT[(j-1) S + c M + r] =
+// (G^j)_rc, S = M^2 rounded up to even) every product t_{n,k} = G^(n-k) q_k
+// is independent: one CTA per (n, k) forms it (stage 1), one CTA per n sums
+// t_{n,0..n} in that order (stage 2).  t is laid out per member as (N+1)(N+2)/2 rows of M, pair
 // (n, k) at row n(n+1)/2 + k.  q and z may be the same array.
 __global__ void __launch_bounds__(256) k_heat1d_sweep_pow1(const double *__restrict__ q, double *__restrict__ t,
                                                            const double *__restrict__ powT, int M, int N,
                                                            size_t blen, const MemberState *st) {
-    extern __shared__ double qs[];
+    extern __shared__ __align__(16) double qs[];   // q_k, then 32 columns of G^(n-k)
     const int b = blockIdx.y;
     if (!runs(st, b)) return;
     const int pidx = blockIdx.x;
@@ -574,20 +607,8 @@ __global__ void __launch_bounds__(256) k_heat1d_sweep_pow1(const double *__restr
         return;
     }
     for (int i = threadIdx.x; i < M; i += blockDim.x) qs[i] = qk[i];
-    __syncthreads();
-    const double *P = powT + (size_t)(n - k - 1) * M * M;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int j = 0;
-        for (; j + 3 < M; j += 4) {
-            s0 = fma(P[(size_t)j * M + i], qs[j], s0);
-            s1 = fma(P[(size_t)(j + 1) * M + i], qs[j + 1], s1);
-            s2 = fma(P[(size_t)(j + 2) * M + i], qs[j + 2], s2);
-            s3 = fma(P[(size_t)(j + 3) * M + i], qs[j + 3], s3);
-        }
-        for (; j < M; ++j) s0 = fma(P[(size_t)j * M + i], qs[j], s0);
-        tp[i] = (s0 + s1) + (s2 + s3);
-    }
+    const double v = h1_matvec_row(powT + (size_t)(n - k - 1) * h1_pow_stride(M), qs, qs + ((M + 1) & ~1), M);
+    if (threadIdx.x < M) tp[threadIdx.x] = v;
 }
 
 __global__ void __launch_bounds__(256) k_heat1d_sweep_pow2(const double *__restrict__ t, double *__restrict__ z,
@@ -808,7 +829,9 @@ pit_status dispatch_warp(int M, F &&f) {
 pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStream_t s) {
     if (prec == PIT_FP64 && p->h1_phi_on) {
         const int nt = std::min(256, (p->M + 31) / 32 * 32);
-        k_heat1d_fine_phi<<<dim3(nslices, p->batch), nt, (size_t)p->M * sizeof(double), s>>>(
+        const size_t sm = (size_t)(((p->M + 1) & ~1) + H1_JB * p->M) * sizeof(double);
+        PIT_CUDA(cudaFuncSetAttribute(k_heat1d_fine_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, H1_SMEM_MAX));
+        k_heat1d_fine_phi<<<dim3(nslices, p->batch), nt, sm, s>>>(
             a, p->h1_phiT.as<double>());
         PIT_LAUNCH_CHECK();
         return PIT_OK;
@@ -875,12 +898,13 @@ pit_status upload_sweep_powers(Problem *p, double r) {
     const int M = p->M, N = p->N, c = p->coarse_steps;
     std::vector<double> fm, inv, cp;
     thomas_factors(M, r, fm, inv, cp);
-    std::vector<double> powT((size_t)N * M * M), d(M);
+    const size_t S = h1_pow_stride(M);
+    std::vector<double> powT((size_t)N * S, 0.0), d(M);
     for (int col = 0; col < M; ++col) {
         for (int i = 0; i < M; ++i) d[i] = (i == col) ? 1.0 : 0.0;
         for (int j = 1; j <= N; ++j) {
             solve_times(fm, inv, cp, d, c);
-            for (int i = 0; i < M; ++i) powT[(size_t)(j - 1) * M * M + (size_t)col * M + i] = d[i];
+            for (int i = 0; i < M; ++i) powT[(size_t)(j - 1) * S + (size_t)col * M + i] = d[i];
         }
     }
     PIT_TRY(p->h1_powT.ensure(powT.size() * sizeof(double)));
@@ -983,7 +1007,10 @@ pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec, const 
         const size_t npairs = (size_t)(N + 1) * (N + 2) / 2;
         PIT_TRY(p->h1_sweep_t.ensure((size_t)p->batch * npairs * M * sizeof(double)));
         const int nt = std::min(256, (M + 31) / 32 * 32);
-        k_heat1d_sweep_pow1<<<dim3((unsigned)npairs, p->batch), nt, (size_t)M * sizeof(double), s>>>(
+        const size_t sm = (size_t)(((M + 1) & ~1) + H1_JB * M) * sizeof(double);
+        PIT_CUDA(cudaFuncSetAttribute(k_heat1d_sweep_pow1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      H1_SMEM_MAX));
+        k_heat1d_sweep_pow1<<<dim3((unsigned)npairs, p->batch), nt, sm, s>>>(
             q, p->h1_sweep_t.as<double>(), p->h1_powT.as<double>(), M, N, p->blen, st);
         PIT_LAUNCH_CHECK();
         k_heat1d_sweep_pow2<<<dim3((unsigned)(N + 1), p->batch), nt, 0, s>>>(p->h1_sweep_t.as<double>(), z, M, N,
