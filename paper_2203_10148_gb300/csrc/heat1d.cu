@@ -506,24 +506,29 @@ __global__ void __launch_bounds__(32) k_heat1d_fine_warp(Heat1dArgs a, const T *
 }
 
 // y_i = sum_j A_ij x_j for row i = threadIdx.x (the CTA has at least M
-// threads; A stored by columns, At[j * M + i]; x in shared memory): 32
-// columns at a time (contiguous in At) are copied into shared memory with
-// asynchronous 16-byte copies issued back to back by all threads (one memory
-// latency per block of columns, not one per load), then each thread adds its
-// row over them in four partial sums (columns j mod 4, in order); returns
-// (s0 + s1) + (s2 + s3).  `as` is 16-byte aligned.  Every thread of the CTA
-// must call it.
-constexpr int H1_JB = 32;
-// stride of the matrices G^j: M^2 rounded up to even, so that every matrix
-// (and so every 32-column block of it) starts on a 16-byte boundary
-__host__ __device__ __forceinline__ size_t h1_pow_stride(int M) { return ((size_t)M * M + 1) & ~(size_t)1; }
+// threads; A stored by columns, At[j * M + i]; x in shared memory): jb
+// columns at a time (contiguous in At; jb a multiple of 4, every column of a
+// small matrix at once) are copied into shared memory with asynchronous
+// 16-byte copies issued back to back by all threads (one memory latency per
+// block of columns, not one per load), then each thread adds its row over
+// them in four partial sums (columns j mod 4, in order); returns (s0 + s1) +
+// (s2 + s3).  `as` is 16-byte aligned.  Every thread of the CTA must call it.
+constexpr int H1_JB = 32;   // columns per block at M = 256 (the shared-memory budget below)
 constexpr int H1_SMEM_MAX = (258 + H1_JB * 256) * (int)sizeof(double);   // M <= 256
+// columns per staged block: as many as the budget takes, a multiple of 4
+inline int h1_jb(int M) {
+    const int jb = (H1_SMEM_MAX / (int)sizeof(double) - 258) / M / 4 * 4;
+    return std::max(4, std::min(jb, (M + 3) / 4 * 4));
+}
+// stride of the matrices G^j: M^2 rounded up to even, so that every matrix
+// (and so every block of its columns) starts on a 16-byte boundary
+__host__ __device__ __forceinline__ size_t h1_pow_stride(int M) { return ((size_t)M * M + 1) & ~(size_t)1; }
 __device__ __forceinline__ double h1_matvec_row(const double *__restrict__ At, const double *xs, double *as,
-                                                int M) {
+                                                int M, int jb) {
     const int i = threadIdx.x;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (int j0 = 0; j0 < M; j0 += H1_JB) {
-        const int jn = min(H1_JB, M - j0);
+    for (int j0 = 0; j0 < M; j0 += jb) {
+        const int jn = min(jb, M - j0);
         const int nd = jn * M;
         const double *src = At + (size_t)j0 * M;   // 16-byte aligned: j0 M is even
         __syncthreads();   // the previous block's reads are done (and x is stored)
@@ -554,7 +559,7 @@ __device__ __forceinline__ double h1_matvec_row(const double *__restrict__ At, c
 // formed once on the host; one CTA per (slice, member) forms Phi x_{n-1},
 // a row per thread, with x_{n-1} in shared memory and Phi stored by columns
 // (phiT[j * M + i] = Phi_ij: at each j the threads read consecutive words).
-__global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const double *__restrict__ phiT) {
+__global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const double *__restrict__ phiT, int jb) {
     extern __shared__ __align__(16) double xs[];   // x_{n-1}, then 32 columns of Phi
     const int b = blockIdx.y;
     if (!runs(a.st, b)) return;
@@ -563,7 +568,7 @@ __global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const dou
     const size_t mb = (size_t)b * a.blen;
     const double *xin = a.x + mb + (size_t)(n - 1) * M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) xs[i] = xin[i];
-    const double v = h1_matvec_row(phiT, xs, xs + ((M + 1) & ~1), M);
+    const double v = h1_matvec_row(phiT, xs, xs + ((M + 1) & ~1), M, jb);
     double *yo = a.y + mb + (size_t)n * M;
     const double *xn = a.x + mb + (size_t)n * M;
     if (const int i = threadIdx.x; i < M) {
@@ -589,7 +594,7 @@ __global__ void __launch_bounds__(256) k_heat1d_fine_phi(Heat1dArgs a, const dou
 // (n, k) at row n(n+1)/2 + k.  q and z may be the same array.
 __global__ void __launch_bounds__(256) k_heat1d_sweep_pow1(const double *__restrict__ q, double *__restrict__ t,
                                                            const double *__restrict__ powT, int M, int N,
-                                                           size_t blen, const MemberState *st) {
+                                                           size_t blen, const MemberState *st, int jb) {
     extern __shared__ __align__(16) double qs[];   // q_k, then 32 columns of G^(n-k)
     const int b = blockIdx.y;
     if (!runs(st, b)) return;
@@ -607,7 +612,7 @@ __global__ void __launch_bounds__(256) k_heat1d_sweep_pow1(const double *__restr
         return;
     }
     for (int i = threadIdx.x; i < M; i += blockDim.x) qs[i] = qk[i];
-    const double v = h1_matvec_row(powT + (size_t)(n - k - 1) * h1_pow_stride(M), qs, qs + ((M + 1) & ~1), M);
+    const double v = h1_matvec_row(powT + (size_t)(n - k - 1) * h1_pow_stride(M), qs, qs + ((M + 1) & ~1), M, jb);
     if (threadIdx.x < M) tp[threadIdx.x] = v;
 }
 
@@ -829,10 +834,11 @@ pit_status dispatch_warp(int M, F &&f) {
 pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStream_t s) {
     if (prec == PIT_FP64 && p->h1_phi_on) {
         const int nt = std::min(256, (p->M + 31) / 32 * 32);
-        const size_t sm = (size_t)(((p->M + 1) & ~1) + H1_JB * p->M) * sizeof(double);
+        const int jb = h1_jb(p->M);
+        const size_t sm = (size_t)(((p->M + 1) & ~1) + jb * p->M) * sizeof(double);
         PIT_CUDA(cudaFuncSetAttribute(k_heat1d_fine_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, H1_SMEM_MAX));
         k_heat1d_fine_phi<<<dim3(nslices, p->batch), nt, sm, s>>>(
-            a, p->h1_phiT.as<double>());
+            a, p->h1_phiT.as<double>(), jb);
         PIT_LAUNCH_CHECK();
         return PIT_OK;
     }
@@ -1007,11 +1013,12 @@ pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec, const 
         const size_t npairs = (size_t)(N + 1) * (N + 2) / 2;
         PIT_TRY(p->h1_sweep_t.ensure((size_t)p->batch * npairs * M * sizeof(double)));
         const int nt = std::min(256, (M + 31) / 32 * 32);
-        const size_t sm = (size_t)(((M + 1) & ~1) + H1_JB * M) * sizeof(double);
+        const int jb = h1_jb(M);
+        const size_t sm = (size_t)(((M + 1) & ~1) + jb * M) * sizeof(double);
         PIT_CUDA(cudaFuncSetAttribute(k_heat1d_sweep_pow1, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       H1_SMEM_MAX));
         k_heat1d_sweep_pow1<<<dim3((unsigned)npairs, p->batch), nt, sm, s>>>(
-            q, p->h1_sweep_t.as<double>(), p->h1_powT.as<double>(), M, N, p->blen, st);
+            q, p->h1_sweep_t.as<double>(), p->h1_powT.as<double>(), M, N, p->blen, st, jb);
         PIT_LAUNCH_CHECK();
         k_heat1d_sweep_pow2<<<dim3((unsigned)(N + 1), p->batch), nt, 0, s>>>(p->h1_sweep_t.as<double>(), z, M, N,
                                                                              p->blen, st);
