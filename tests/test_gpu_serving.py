@@ -54,9 +54,9 @@ def test_served_equals_solo_and_oracle():
         tickets = [srv.submit(w, **OPTS) for w in ws]
         results = [srv.wait(t, timeout=300.0) for t in tickets]
         stats = srv.stats()
-    bad = [(w.name, r[0] if r else None, r[2][0] if r else None) for w, r in zip(ws, results)
+    bad = [(w.name, r[0] if r else None, r[2][0].get("error") if r else None) for w, r in zip(ws, results)
            if r is None or r[0] != pit.PIT_OK]
-    assert not bad, bad
+    assert not bad, bad   # (request, status, the library's error message)
     assert stats["completed"] == len(ws) and stats["failed"] == 0
     assert stats["max_running"] >= 2, "requests submitted together must overlap"
     for w, res in zip(ws, results):
