@@ -616,7 +616,7 @@ pit_status launch_adv_fine_v(Problem *p, AdvArgs a, int nslices, cudaStream_t s)
     const int CS = n / AD_ROWS;
     const size_t sm = adv_smem<T, RX>(n);
     auto kern = k_advdiff_fine<T, RX, C32>;
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PIT_TRY(smem_limit(kern, sm));
     if (CS > 8)
         PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     a.N = nslices;   // slices in this launch (output blocks n_first .. n_first + nslices - 1)
@@ -926,7 +926,7 @@ pit_status launch_adv_sweep(Problem *p, const double *q, double *z, const T *ax,
     const int G = n / R;
     auto kern = k_advdiff_sweep<T>;
     const size_t smem = (size_t)(R + 2) * n * sizeof(T);
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PIT_TRY(smem_limit(kern, smem));
     int per_sm = 0;
     PIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SWA_THREADS, smem));
     if (per_sm * sms < G) {
@@ -980,7 +980,7 @@ pit_status adv_check_cluster(int n) {
     const int CS = n / AD_ROWS;
     const size_t sm = adv_smem<T, RX>(n);
     auto kern = k_advdiff_fine<T, RX, false>;
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PIT_TRY(smem_limit(kern, sm));
     if (CS > 8) PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)CS, 1, 1);

@@ -10,7 +10,10 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "pit_internal.h"
@@ -36,6 +39,19 @@ pit_status cuda_fail(cudaError_t e, const char *what, const char *file, int line
 
 thread_local AllocCtx *tl_alloc = nullptr;
 thread_local bool tl_capturing = false;
+
+pit_status smem_limit_raw(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limits;   // (device, kernel) -> limit set
+    int dev = 0;
+    PIT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = limits[std::make_pair(dev, func)];
+    if (bytes <= cur) return PIT_OK;
+    PIT_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return PIT_OK;
+}
 
 pit_status DevBuf::ensure(size_t n) {
     if (n <= bytes && ptr) return PIT_OK;

@@ -1159,8 +1159,7 @@ static pit_status persistent_sweep(Problem *p, const double *q, double *z, const
     const int grid = (M + rows - 1) / rows;
     const size_t smem = (3 * (size_t)SW_MAXROWS * M + (size_t)SW_MAXROWS * 64) * sizeof(T);
     if (smem > 200 * 1024) return PIT_OK;
-    PIT_CUDA(cudaFuncSetAttribute(k_dense_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    PIT_TRY(smem_limit(k_dense_sweep<T>, smem));
     int per_sm = 0;
     PIT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_sweep<T>, SW_THREADS,
                                                            smem));

@@ -424,7 +424,7 @@ pit_status dense_tc_sweep(Problem *p, const double *q, double *z, const MemberSt
     const int KB = Mp / DS_CL / DS_BK;
     const size_t smem = (size_t)KB * 2 * DS_B_BYTES +
                         std::max((size_t)KB * 2 * DS_A_BYTES, (size_t)DS_BM * DS_PLD * 4) + 1024;
-    PIT_CUDA(cudaFuncSetAttribute(k_dense_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PIT_TRY(smem_limit(k_dense_sweep_tc, smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((Mp + DS_BN - 1) / DS_BN * DS_CL));
     cfg.blockDim = dim3(DS_THREADS);

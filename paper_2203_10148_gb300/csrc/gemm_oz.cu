@@ -369,7 +369,7 @@ pit_status dense_oz_apply(Problem *p, const double *x, double *y, int mode, cons
     int dev = 0, sms = 0;
     PIT_CUDA(cudaGetDevice(&dev));
     PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PIT_CUDA(cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+    PIT_TRY(smem_limit(k_gemm_oz, OZ_SMEM));
     k_gemm_oz<<<std::min(ntiles, sms), OZ_THREADS, OZ_SMEM, s>>>(tA, tB, Kp, R, Rp, Mp, OZ_SMAX, ntn, ntiles, ep,
                                                               p->errword.as<int>());
     PIT_LAUNCH_CHECK();

@@ -389,7 +389,7 @@ pit_status dense_tc_apply(Problem *p, const double *x, double *y, float *y32, in
     PIT_CUDA(cudaGetDevice(&dev));
     PIT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     auto kern = bf ? k_gemm_tf32x3_p<true> : k_gemm_tf32x3_p<false>;
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM));
+    PIT_TRY(smem_limit(kern, TP_SMEM));
     kern<<<std::min(ntiles, sms), TP_THREADS, TP_SMEM, s>>>(tAh, tAl, tBh, tBl, Mp, R, ntn, ntiles, ep,
                                                            p->errword.as<int>());
     PIT_LAUNCH_CHECK();

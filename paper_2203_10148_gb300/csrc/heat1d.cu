@@ -836,7 +836,7 @@ pit_status fine_launch(Problem *p, Heat1dArgs a, int nslices, int prec, cudaStre
         const int nt = std::min(256, (p->M + 31) / 32 * 32);
         const int jb = h1_jb(p->M);
         const size_t sm = (size_t)(((p->M + 1) & ~1) + jb * p->M) * sizeof(double);
-        PIT_CUDA(cudaFuncSetAttribute(k_heat1d_fine_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, H1_SMEM_MAX));
+        PIT_TRY(smem_limit(k_heat1d_fine_phi, H1_SMEM_MAX));
         k_heat1d_fine_phi<<<dim3(nslices, p->batch), nt, sm, s>>>(
             a, p->h1_phiT.as<double>(), jb);
         PIT_LAUNCH_CHECK();
@@ -1015,8 +1015,7 @@ pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec, const 
         const int nt = std::min(256, (M + 31) / 32 * 32);
         const int jb = h1_jb(M);
         const size_t sm = (size_t)(((M + 1) & ~1) + jb * M) * sizeof(double);
-        PIT_CUDA(cudaFuncSetAttribute(k_heat1d_sweep_pow1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      H1_SMEM_MAX));
+        PIT_TRY(smem_limit(k_heat1d_sweep_pow1, H1_SMEM_MAX));
         k_heat1d_sweep_pow1<<<dim3((unsigned)npairs, p->batch), nt, sm, s>>>(
             q, p->h1_sweep_t.as<double>(), p->h1_powT.as<double>(), M, N, p->blen, st, jb);
         PIT_LAUNCH_CHECK();

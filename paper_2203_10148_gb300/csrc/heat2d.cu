@@ -1127,8 +1127,7 @@ pit_status launch_fine_rx(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s)
     a.C = 1;
     const int threads = TXp * TYp;
     const size_t sm = fine_smem<T, RX, RY>(TXp, TYp);
-    PIT_CUDA(cudaFuncSetAttribute(k_heat2d_fine<T, RX, RY, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PIT_TRY(smem_limit(k_heat2d_fine<T, RX, RY, false>, sm));
     k_heat2d_fine<T, RX, RY, false><<<dim3(nslices, p->batch), threads, sm, s>>>(a);
     PIT_LAUNCH_CHECK();
     return PIT_OK;
@@ -1154,7 +1153,7 @@ pit_status launch_fine_cluster(Problem *p, Heat2dArgs a, int nslices, cudaStream
     const int threads = THREADS;
     const size_t sm = fine_smem<T, RX, RY>(a.TXp, TYp);
     auto kern = k_heat2d_fine<T, RX, RY, true>;
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PIT_TRY(smem_limit(kern, sm));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nslices * a.C), (unsigned)p->batch);
     cfg.blockDim = dim3((unsigned)threads);
@@ -1219,8 +1218,7 @@ pit_status launch_split(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
         a.TY = TY;
         a.C = 1;
         const size_t sm = split_smem<RX, RY, false>(TXp, TYp);
-        PIT_CUDA(cudaFuncSetAttribute(k_heat2d_split<RX, RY, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        PIT_TRY(smem_limit(k_heat2d_split<RX, RY, false>, sm));
         k_heat2d_split<RX, RY, false><<<dim3(nslices, p->batch), TXp * TYp, sm, s>>>(a);
         PIT_LAUNCH_CHECK();
         return PIT_OK;
@@ -1234,7 +1232,7 @@ pit_status launch_split(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
     a.C = (n + TYp * RY - 1) / (TYp * RY);
     const size_t sm = split_smem<RX, RY, true>(a.TXp, TYp);
     auto kern = k_heat2d_split<RX, RY, true>;
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PIT_TRY(smem_limit(kern, sm));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nslices * a.C), (unsigned)p->batch);
     cfg.blockDim = dim3((unsigned)THREADS);
@@ -1297,8 +1295,7 @@ pit_status launch_xS(Problem *p, const Tin *A, Tout *out, const T *S, double sca
     if constexpr (std::is_same<Tin, float>::value && std::is_same<T, float>::value) {
         if (n <= PN && n % 4 == 0) {
             const size_t sm = (size_t)3 * PN * XP_LD * sizeof(float);
-            PIT_CUDA(cudaFuncSetAttribute(k_xform_persist<Tout>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            PIT_TRY(smem_limit(k_xform_persist<Tout>, sm));
             const int total = (p->N + 1) * p->batch;
             int dev = 0, sms = 0;
             PIT_CUDA(cudaGetDevice(&dev));
@@ -1310,8 +1307,7 @@ pit_status launch_xS(Problem *p, const Tin *A, Tout *out, const T *S, double sca
         }
     }
     const size_t sm = (size_t)PN * PLD * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
-    PIT_CUDA(cudaFuncSetAttribute(k_block_xS_T<Tin, T, Tout>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    PIT_TRY(smem_limit(k_block_xS_T<Tin, T, Tout>, sm));
     const int nblk = p->N + 1;
     const int tiles = (n + PN - 1) / PN;
     k_block_xS_T<Tin, T, Tout><<<nblk * p->batch * tiles * tiles, PT, sm, s>>>(A, out, S, n, nblk,

@@ -44,6 +44,20 @@ extern thread_local unsigned long long tl_launches;   // this thread
         PIT_CUDA(cudaGetLastError());                                         \
     } while (0)
 
+// Raises the dynamic shared-memory limit of kernel `func` on the current
+// device to at least `bytes` (cudaFuncAttributeMaxDynamicSharedMemorySize).
+// The limit belongs to the function for the whole process, so solves that
+// run at once on several host threads and set it to different values would
+// race: one could lower it between another's set and that one's launch,
+// which then fails.  Here the limit only grows, under a lock, so every
+// launch after the call sees a limit no smaller than its request; a limit
+// already large enough costs a table lookup and no driver call.
+pit_status smem_limit_raw(const void *func, size_t bytes);
+template <class F>
+pit_status smem_limit(F *func, size_t bytes) {
+    return smem_limit_raw(reinterpret_cast<const void *>(func), bytes);
+}
+
 // ------------------------------------------------------- device buffers
 struct DevBuf {
     void *ptr = nullptr;

@@ -447,7 +447,7 @@ pit_status launch_xform_tc(const CUtensorMap &tA, const CUtensorMap &tSh, const 
                            const MemberState *st, int *err, int grid, cudaStream_t s, int R = 0,
                            int nout = 0, int ldo = 0) {
     auto kern = k_xform_tc<OUT64, SRES, ROW1D>;
-    PIT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, XtLayout<SRES>::kSmem));
+    PIT_TRY(smem_limit(kern, XtLayout<SRES>::kSmem));
     kern<<<grid, XT_THREADS, XtLayout<SRES>::kSmem, s>>>(tA, tSh, tSl, out, n, total_tiles, TN, nblk,
                                                           R, nout, ldo, scale, st, err);
     PIT_LAUNCH_CHECK();

@@ -70,6 +70,32 @@ def test_served_equals_solo_and_oracle():
         assert _rel(X[0], lam) <= 1e-6, (w.name, _rel(X[0], lam))
 
 
+def test_served_grid_sizes_alternate_concurrently():
+    """2D heat requests of two grid sizes, solved eight at a time: the same
+    kernels launch at once with different shared-memory sizes from different
+    worker threads.  The kernels' shared-memory limit belongs to the process,
+    so a worker that lowered it under another's launch would fail that
+    launch; every request must succeed and equal its solo solve."""
+    pit = _pit()
+    sizes = (40, 96)
+    ws = [inputs.heat2d(n=sizes[j % 2], N=16, fine_steps=20) for j in range(32)]
+    with pit.Server(max_slots=8) as srv:
+        tickets = [srv.submit(w, **OPTS) for w in ws]
+        results = [srv.wait(t, timeout=300.0) for t in tickets]
+        stats = srv.stats()
+    bad = [(w.name, r[0] if r else None, r[2][0].get("error") if r else None) for w, r in zip(ws, results)
+           if r is None or r[0] != pit.PIT_OK]
+    assert not bad, bad
+    assert stats["max_running"] >= 2, "requests submitted together must overlap"
+    for n in sizes:
+        w = next(w for w in ws if w.nx == n)
+        with pit.Problem(w) as p:
+            Xs, _ = p.bicgstab_solve(**OPTS)
+        for wj, (st, X, info) in zip(ws, results):
+            if wj.nx == n:
+                assert _rel(X, Xs) <= 1e-6, wj.name
+
+
 @pytest.mark.parametrize("resid", ["ff", "split"])
 def test_served_bitwise_equals_solo(resid):
     """Kernels, launch shapes and reduction orders depend on the request
