@@ -922,6 +922,34 @@ pit_status upload_sweep_powers(Problem *p, double r) {
 
 }  // namespace
 
+// FP64 problems: the fine batch as one matrix product where that is cheaper
+// than the steps: M^2 multiply-adds per slice against m steps of the
+// one-warp Thomas kernel (about 32 (5E + 8) lane operations each, E = 2, 4,
+// 8 points per lane), with the matrix formed on the host in bounded time.
+bool heat1d_phi_wanted(int M, int fine_steps, int precision) {
+    const int E = M <= 64 ? 2 : M <= 128 ? 4 : 8;
+    return precision == PIT_FP64 && M <= WARP_MAXM &&
+           (double)M * M < 0.5 * fine_steps * 32.0 * (5 * E + 8) && (double)M * M * fine_steps <= 1e8;
+}
+
+// FP64 problems: the sweep through the powers of G where the (N+1)(N+2)/2
+// independent products stay small and the powers are formed on the host in
+// bounded time.
+bool heat1d_pow_wanted(int M, int N, int coarse_steps, int precision) {
+    const double pairs = 0.5 * (N + 1.0) * (N + 2.0);
+    return precision == PIT_FP64 && M <= WARP_MAXM && N <= 128 && pairs * M * M <= 4e6 &&
+           (double)N * M * M * coarse_steps <= 1e8;
+}
+
+size_t heat1d_table_bytes(int M, int N, int batch, int fine_steps, int coarse_steps, int precision) {
+    size_t b = 0;
+    if (heat1d_phi_wanted(M, fine_steps, precision)) b += (size_t)M * M * sizeof(double);
+    if (heat1d_pow_wanted(M, N, coarse_steps, precision))
+        b += ((size_t)N * h1_pow_stride(M) + (size_t)batch * ((size_t)(N + 1) * (N + 2) / 2) * M) *
+             sizeof(double);
+    return b;
+}
+
 pit_status heat1d_setup(Problem *p) {
     if (p->fine_kind != PIT_STEP_IE || p->coarse_kind != PIT_STEP_IE) {
         set_error("heat1d: fine and coarse steppers must be implicit Euler");
@@ -940,29 +968,21 @@ pit_status heat1d_setup(Problem *p) {
     const double rc = (p->dT / p->coarse_steps) * p->nu / (h * h);
     // fine factors in fine_inv64/32, coarse in coarse_inv64/32 (fm | inv | cp)
     PIT_TRY(upload_factors(p->M, rf, p->fine_inv64, p->fine_inv32, p->stream, &p->fine_invff));
-    // FP64 problems: the fine batch as one matrix product where that is
-    // cheaper than the steps: M^2 multiply-adds per slice against m steps of
-    // the one-warp Thomas kernel (about 32 (5E + 8) lane operations each,
-    // E = 2, 4, 8 points per lane); PIT_HEAT1D_PHI=0 keeps the steps.  The
-    // matrices are formed on the host at set-up, so problems of the other
-    // precisions (a served request, a mixed solve), whose solves run no FP64
-    // fine batch, keep the steps for the FP64 calls they may make
+    // FP64 problems: the fine batch as one product with the propagator
+    // matrix where heat1d_phi_wanted says so (PIT_HEAT1D_PHI=0 keeps the
+    // steps).  The matrices are formed on the host at set-up, so mixed
+    // problems, whose solves run no FP64 fine batch, keep the steps for the
+    // FP64 calls they may make
     {
-        const int M = p->M, m = p->fine_steps;
-        const int E = M <= 64 ? 2 : M <= 128 ? 4 : 8;
         const char *pe = getenv("PIT_HEAT1D_PHI");
-        p->h1_phi_on = p->precision == PIT_FP64 && M <= WARP_MAXM && (double)M * M < 0.5 * m * 32.0 * (5 * E + 8) &&
-                       (double)M * M * m <= 1e8 && !(pe && pe[0] == '0');
+        p->h1_phi_on = heat1d_phi_wanted(p->M, p->fine_steps, p->precision) && !(pe && pe[0] == '0');
         if (p->h1_phi_on) PIT_TRY(upload_fine_matrix(p, rf));
     }
-    // FP64 sweep through the powers of G where the (N+1)(N+2)/2 independent
-    // products stay small (PIT_HEAT1D_POW=0 keeps the sequential solves)
+    // FP64 sweep through the powers of G where heat1d_pow_wanted says so
+    // (PIT_HEAT1D_POW=0 keeps the sequential solves)
     {
-        const int M = p->M, N = p->N;
-        const double pairs = 0.5 * (N + 1.0) * (N + 2.0);
         const char *pe = getenv("PIT_HEAT1D_POW");
-        p->h1_pow_on = p->precision == PIT_FP64 && M <= WARP_MAXM && N <= 128 && pairs * M * M <= 4e6 &&
-                       (double)N * M * M * p->coarse_steps <= 1e8 && !(pe && pe[0] == '0');
+        p->h1_pow_on = heat1d_pow_wanted(p->M, p->N, p->coarse_steps, p->precision) && !(pe && pe[0] == '0');
         if (p->h1_pow_on) PIT_TRY(upload_sweep_powers(p, rc));
     }
     PIT_TRY(upload_factors(p->M, rc, p->coarse_inv64, p->coarse_inv32, p->stream));

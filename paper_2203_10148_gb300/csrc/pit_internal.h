@@ -263,6 +263,12 @@ pit_status op_serial(Problem *p, double *Lam, int precision, cudaStream_t s);
 
 // per-family implementations
 pit_status heat1d_setup(Problem *p);
+// 1D heat, FP64: whether set-up stores the fine propagator matrix A^{-m}
+// and the powers G^j of the coarse propagator (the environment switches
+// aside), and the device bytes those tables and the sweep's products take.
+bool heat1d_phi_wanted(int M, int fine_steps, int precision);
+bool heat1d_pow_wanted(int M, int N, int coarse_steps, int precision);
+size_t heat1d_table_bytes(int M, int N, int batch, int fine_steps, int coarse_steps, int precision);
 pit_status heat1d_apply_F(Problem *p, const double *x, double *y, int mode, int prec,
                           const MemberState *st, cudaStream_t s);
 pit_status heat1d_sweep(Problem *p, const double *q, double *z, int prec,

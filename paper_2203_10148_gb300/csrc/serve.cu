@@ -101,6 +101,8 @@ size_t serve_footprint(const pit_problem_desc *d) {
         b = std::max(b, 16 * vlen + 32 * nn + 4096);         // set-up (variant autotuning)
     } else {
         b += 72 * M;                                         // Thomas factors (FP64, FP32, float-float)
+        // FP64: the stored fine propagator, powers of G and the sweep's products
+        b += heat1d_table_bytes((int)M, d->N, d->batch, d->fine.steps, d->coarse.steps, d->precision);
         if (d->precision == PIT_MIXED) {
             // sine-basis sweep: TF32 parts of S, two padded FP32 row sets,
             // chunk ends and mode factors

@@ -106,6 +106,21 @@ def test_serve_footprint_is_host_only_and_monotone(lib):
     assert lib.pit_serve_footprint(C.byref(bad), C.byref(out)) == pit.PIT_E_INVALID
 
 
+@pytest.mark.parametrize("M,N,batch", [(63, 16, 2), (8, 128, 64)])
+def test_serve_footprint_counts_the_fp64_heat1d_tables(lib, M, N, batch):
+    """An FP64 1D heat request on a small grid stores the fine propagator
+    matrix (M^2 doubles), the N powers of G (M^2 rounded up to even doubles
+    each) and the sweep's (N+1)(N+2)/2 products of M doubles per member; the
+    footprint the server reserves holds them on top of eight Krylov block
+    vectors (at N = 128 the products are eight times those vectors)."""
+    from paper_2203_10148_gb300 import inputs, pit
+    w = inputs.heat1d(M=M, N=N, batch=batch)
+    assert w.precision == "fp64" and w.fine[1] == 100 and w.coarse[1] == 1
+    vlen = (N + 1) * M * batch
+    tables = 8 * (M * M + N * ((M * M + 1) // 2 * 2) + batch * (N + 1) * (N + 2) // 2 * M)
+    assert pit.serve_footprint(w) >= 64 * vlen + tables
+
+
 def test_server_calls_reject_null_handles(lib):
     from paper_2203_10148_gb300 import pit
     info = pit.SolveInfo()
