@@ -441,7 +441,9 @@ pit_status pit_serve_cancel(pit_server_t server, uint64_t ticket);
 /* Device bytes the server reserves for a request of this description: an
  * upper bound of what its problem allocates (eight Krylov block vectors,
  * the FP32 fine output and sine-mode work of the 2D sweep, set-up tables,
- * reduction partials).  Host-only. */
+ * reduction partials; for FP64 1D heat on small grids also the stored fine
+ * propagator matrix, the powers of the coarse propagator and the sweep's
+ * (N+1)(N+2)/2 products per member).  Host-only. */
 pit_status pit_serve_footprint(const pit_problem_desc *desc, size_t *bytes);
 
 typedef struct {
