@@ -121,6 +121,23 @@ def test_serve_footprint_counts_the_fp64_heat1d_tables(lib, M, N, batch):
     assert pit.serve_footprint(w) >= 64 * vlen + tables
 
 
+@pytest.mark.parametrize("M,m", [(17, 100), (63, 100), (63, 3), (100, 7), (128, 50), (200, 40), (200, 400),
+                                 (250, 2000), (256, 100), (257, 1000)])
+def test_bench_matrix_label_agrees_with_the_library(lib, M, m):
+    """bench.py names the 1D heat FP64 roofline kernel after the library's
+    choice of fine batch (the stored propagator matrix, or the steps).  The
+    library's choice is read from the serving footprint, which counts the
+    matrix's M^2 doubles only where set-up stores it: at N = 200 no powers of
+    G are stored, and one fine step stores no matrix on these grids."""
+    import bench
+    from paper_2203_10148_gb300 import inputs, pit
+    w = inputs.heat1d(M=M, N=200, fine_steps=m)
+    one = inputs.heat1d(M=M, N=200, fine_steps=1)
+    stored = pit.serve_footprint(w) - pit.serve_footprint(one)
+    assert stored in (0, 8 * M * M)
+    assert bench.heat1d_uses_matrix(w) == (stored == 8 * M * M)
+
+
 def test_server_calls_reject_null_handles(lib):
     from paper_2203_10148_gb300 import pit
     info = pit.SolveInfo()
