@@ -422,7 +422,17 @@ __global__ void __launch_bounds__(CL ? (RX == 4 ? 512 : 256) : 16384 / (RX * RY)
 // float rows in the first stage, FP32 rows in the three others) and one
 // barrier per stage.  The FP32 stages run on -a (the float-float stage
 // yields -fl(w) at no cost) and the sign is folded into the final sum.
-template <int RX, int RY, bool CL>
+//
+// FOLD: the first stage forms Z applied to the high words only, and the low
+// word's first-order term Z u_lo joins the FP32 terms:
+//   a3 = a + (Z/4) a;  y = (a/2 + u_lo) + (Z/6) a3;  q = Z y
+// so q = Z u_lo + Z^2 u/2 + Z^3 u/6 + Z^4 u/24 up to FP32 rounding, which
+// scales like the other FP32 terms (|Z|^2 |u| on smooth data).  The first
+// stage exchanges FP32 rows (high words) instead of float-float ones and
+// skips the low words' stencil: 65 operations per point and step.  The
+// register slot of the duplicated -a holds -(a/2 + u_lo) instead, and the
+// first FP32 stage takes its base -a from the centre's stage value.
+template <int RX, int RY, bool CL, bool FOLD = false>
 __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY), 1) k_heat2d_split(Heat2dArgs a) {
     using A = Arith<ff>;
     constexpr int H = RY / 2;
@@ -473,8 +483,13 @@ __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY), 1) k_heat2d_spli
         ccs[0] = c3.hi;
         ccs[1] = c3.lo;
         ccs[2] = d2f_rn(a.c[0]);
-        ccs[3] = d2f_rn(a.c[1]);
-        ccs[4] = d2f_rn(a.c[2]);
+        if constexpr (FOLD) {
+            ccs[3] = d2f_rn(a.c[3] / 6.0);
+            ccs[4] = c3.hi;
+        } else {
+            ccs[3] = d2f_rn(a.c[1]);
+            ccs[4] = d2f_rn(a.c[2]);
+        }
     }
     const bool west_zero = (tx == 0), east_zero = (tx == a.TXp - 1);
     const bool north_remote = CL && ty == 0 && rank > 0;
@@ -503,15 +518,100 @@ __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY), 1) k_heat2d_spli
     int buf = 0;
     for (int step = 0; step < a.steps; ++step) {
         // ---- stage 1: s = u + Z u in float-float (u = v), -a = -fl(Z u)
+        if constexpr (FOLD) {
 #pragma unroll
-        for (int q = 0; q < RX; q += 4) {
-            const ff t0[4] = {v[0][q], v[0][q + 1], v[0][q + 2], v[0][q + 3]};
-            const ff t1[4] = {v[RY - 1][q], v[RY - 1][q + 1], v[RY - 1][q + 2], v[RY - 1][q + 3]};
-            A::st4(rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0 + q, t0);
-            A::st4(rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0 + q, t1);
+            for (int q = 0; q < RX; q += 4) {
+                *reinterpret_cast<float4 *>(frow_w(buf, 0, ty) + i0 + q) =
+                    make_float4(v[0][q].hi, v[0][q + 1].hi, v[0][q + 2].hi, v[0][q + 3].hi);
+                *reinterpret_cast<float4 *>(frow_w(buf, 1, ty) + i0 + q) =
+                    make_float4(v[RY - 1][q].hi, v[RY - 1][q + 1].hi, v[RY - 1][q + 2].hi,
+                                v[RY - 1][q + 3].hi);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < RX; q += 4) {
+                const ff t0[4] = {v[0][q], v[0][q + 1], v[0][q + 2], v[0][q + 3]};
+                const ff t1[4] = {v[RY - 1][q], v[RY - 1][q + 1], v[RY - 1][q + 2], v[RY - 1][q + 3]};
+                A::st4(rows + ((size_t)(buf * 2 + 0) * TYp + ty) * W + i0 + q, t0);
+                A::st4(rows + ((size_t)(buf * 2 + 1) * TYp + ty) * W + i0 + q, t1);
+            }
         }
         cluster_or_cta_sync();
-        {
+        if constexpr (FOLD) {
+            // s = u + Z u_hi (float-float); -a = -fl(Z u_hi); the slot of the
+            // duplicated -a takes -(a/2 + u_lo), the base of the second FP32 stage
+            const float2 cch = make_float2(ccs[0], ccs[0]), ccl = make_float2(ccs[1], ccs[1]);
+            const float2 ncch = make_float2(-ccs[0], -ccs[0]);
+            const float2 half2 = make_float2(0.5f, 0.5f);
+            float prev[RX], srow[RX], rowH[RX], pB[RX];
+#pragma unroll
+            for (int q = 0; q < RX; q += 4) {
+                const float4 tn = *reinterpret_cast<const float4 *>(frow(nbuf, buf, 1, nty) + i0 + q);
+                const float4 ts = *reinterpret_cast<const float4 *>(frow(sbuf, buf, 0, sty) + i0 + q);
+                prev[q] = north_zero ? 0.f : tn.x;
+                prev[q + 1] = north_zero ? 0.f : tn.y;
+                prev[q + 2] = north_zero ? 0.f : tn.z;
+                prev[q + 3] = north_zero ? 0.f : tn.w;
+                srow[q] = south_zero ? 0.f : ts.x;
+                srow[q + 1] = south_zero ? 0.f : ts.y;
+                srow[q + 2] = south_zero ? 0.f : ts.z;
+                srow[q + 3] = south_zero ? 0.f : ts.w;
+            }
+#pragma unroll
+            for (int c = 0; c < RX; ++c) {
+                rowH[c] = v[H][c].hi;
+                pB[c] = v[H - 1][c].hi;
+            }
+#pragma unroll
+            for (int r = 0; r < H; ++r) {
+                ff cA[RX], cB[RX];
+#pragma unroll
+                for (int c = 0; c < RX; ++c) {
+                    cA[c] = v[r][c];
+                    cB[c] = v[r + H][c];
+                }
+                float wA = __shfl_up_sync(kFullMask, cA[RX - 1].hi, 1);
+                float wB = __shfl_up_sync(kFullMask, cB[RX - 1].hi, 1);
+                float eA = __shfl_down_sync(kFullMask, cA[0].hi, 1);
+                float eB = __shfl_down_sync(kFullMask, cB[0].hi, 1);
+                wA = west_zero ? 0.f : wA;
+                wB = west_zero ? 0.f : wB;
+                eA = east_zero ? 0.f : eA;
+                eB = east_zero ? 0.f : eB;
+#pragma unroll
+                for (int c = 0; c < RX; ++c) {
+                    const float sA = (r < H - 1) ? v[r + 1][c].hi : rowH[c];
+                    const float sB = (r < H - 1) ? v[r + H + 1][c].hi : srow[c];
+                    const float xwA = (c > 0) ? cA[c - 1].hi : wA, xwB = (c > 0) ? cB[c - 1].hi : wB;
+                    const float xeA = (c < RX - 1) ? cA[c + 1].hi : eA, xeB = (c < RX - 1) ? cB[c + 1].hi : eB;
+                    float2 na;
+                    ff2 sp = ff_stage2_neg_w_hi(make_float2(prev[c], pB[c]), make_float2(sA, sB),
+                                                make_float2(xwA, xwB), make_float2(xeA, xeB),
+                                                ff_pair(cA[c], cB[c]), cch, ncch, ccl, na);
+                    float2 nb = __ffma2_rn(half2, na, make_float2(-cA[c].lo, -cB[c].lo));
+                    if (edge) {
+                        const bool okA = (i0 + c < n) && (j0 + r < n);
+                        const bool okB = (i0 + c < n) && (j0 + r + H < n);
+                        sp.hi.x = okA ? sp.hi.x : 0.f;
+                        sp.lo.x = okA ? sp.lo.x : 0.f;
+                        na.x = okA ? na.x : 0.f;
+                        nb.x = okA ? nb.x : 0.f;
+                        sp.hi.y = okB ? sp.hi.y : 0.f;
+                        sp.lo.y = okB ? sp.lo.y : 0.f;
+                        na.y = okB ? na.y : 0.f;
+                        nb.y = okB ? nb.y : 0.f;
+                    }
+                    us4[(size_t)(r * RX + c) * nthr + tid] = make_float4(sp.hi.x, sp.hi.y, sp.lo.x, sp.lo.y);
+                    v[r][c] = ff{nb.x, na.x};
+                    v[r + H][c] = ff{nb.y, na.y};
+                }
+#pragma unroll
+                for (int c = 0; c < RX; ++c) {
+                    prev[c] = cA[c].hi;
+                    pB[c] = cB[c].hi;
+                }
+            }
+        } else {
             const float2 cch = make_float2(ccs[0], ccs[0]), ccl = make_float2(ccs[1], ccs[1]);
             const float2 ncch = make_float2(-ccs[0], -ccs[0]);
             ff prev[RX], srow[RX], rowH[RX], pB[RX];
@@ -577,79 +677,163 @@ __global__ void __launch_bounds__(CL ? 256 : 16384 / (RX * RY), 1) k_heat2d_spli
         }
         buf ^= 1;
         // ---- stages 2-4 in FP32 on -a: -a3 = -a + (Z/4)(-a), -a2 = -a + (Z/3)(-a3), -q = (Z/2)(-a2)
-#pragma unroll 1
-        for (int stage = 0; stage < 3; ++stage) {
+        if constexpr (FOLD) {
+            // -a3 as above, -y = -(a/2 + u_lo) + (Z/6)(-a3), -q = Z(-y): the same stage as
+            // below, whose first pass takes its base -a from the centre's own stage value
+            // (the slot v.hi holds -(a/2 + u_lo) for the second)
+            auto fp32_stage = [&](const int stage, auto base_is_cur_t) {
+                constexpr bool base_is_cur = decltype(base_is_cur_t)::value;
 #pragma unroll
-            for (int q = 0; q < RX; q += 4) {
-                *reinterpret_cast<float4 *>(frow_w(buf, 0, ty) + i0 + q) =
-                    make_float4(v[0][q].lo, v[0][q + 1].lo, v[0][q + 2].lo, v[0][q + 3].lo);
-                *reinterpret_cast<float4 *>(frow_w(buf, 1, ty) + i0 + q) =
-                    make_float4(v[RY - 1][q].lo, v[RY - 1][q + 1].lo, v[RY - 1][q + 2].lo,
-                                v[RY - 1][q + 3].lo);
-            }
-            cluster_or_cta_sync();
-            const float cc = ccs[2 + stage];
-            const float2 cc2 = make_float2(cc, cc);
-            const bool last = (stage == 2);
-            float prev[RX];
+                for (int q = 0; q < RX; q += 4) {
+                    *reinterpret_cast<float4 *>(frow_w(buf, 0, ty) + i0 + q) =
+                        make_float4(v[0][q].lo, v[0][q + 1].lo, v[0][q + 2].lo, v[0][q + 3].lo);
+                    *reinterpret_cast<float4 *>(frow_w(buf, 1, ty) + i0 + q) =
+                        make_float4(v[RY - 1][q].lo, v[RY - 1][q + 1].lo, v[RY - 1][q + 2].lo,
+                                    v[RY - 1][q + 3].lo);
+                }
+                cluster_or_cta_sync();
+                const float cc = ccs[2 + stage];
+                const float2 cc2 = make_float2(cc, cc);
+                const bool last = (stage == 2);
+                float prev[RX];
 #pragma unroll
-            for (int q = 0; q < RX; q += 4) {
-                const float4 t = *reinterpret_cast<const float4 *>(frow(nbuf, buf, 1, nty) + i0 + q);
-                prev[q] = t.x;
-                prev[q + 1] = t.y;
-                prev[q + 2] = t.z;
-                prev[q + 3] = t.w;
-            }
+                for (int q = 0; q < RX; q += 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(frow(nbuf, buf, 1, nty) + i0 + q);
+                    prev[q] = t.x;
+                    prev[q + 1] = t.y;
+                    prev[q + 2] = t.z;
+                    prev[q + 3] = t.w;
+                }
 #pragma unroll
-            for (int r = 0; r < RY; ++r) {
-                float srow[RX];
-                if (r == RY - 1) {
+                for (int r = 0; r < RY; ++r) {
+                    float srow[RX];
+                    if (r == RY - 1) {
 #pragma unroll
-                    for (int q = 0; q < RX; q += 4) {
-                        const float4 t = *reinterpret_cast<const float4 *>(frow(sbuf, buf, 0, sty) + i0 + q);
-                        srow[q] = t.x;
-                        srow[q + 1] = t.y;
-                        srow[q + 2] = t.z;
-                        srow[q + 3] = t.w;
+                        for (int q = 0; q < RX; q += 4) {
+                            const float4 t = *reinterpret_cast<const float4 *>(frow(sbuf, buf, 0, sty) + i0 + q);
+                            srow[q] = t.x;
+                            srow[q + 1] = t.y;
+                            srow[q + 2] = t.z;
+                            srow[q + 3] = t.w;
+                        }
                     }
+                    float cur[RX];
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) cur[c] = v[r][c].lo;
+                    const float w_in = __shfl_up_sync(kFullMask, cur[RX - 1], 1);
+                    const float e_in = __shfl_down_sync(kFullMask, cur[0], 1);
+                    float hsum[RX];
+                    hsum[0] = fmaf(mw, w_in, cur[1]);
+#pragma unroll
+                    for (int c = 1; c < RX - 1; ++c) hsum[c] = cur[c - 1] + cur[c + 1];
+                    hsum[RX - 1] = fmaf(me, e_in, cur[RX - 2]);
+#pragma unroll
+                    for (int q = 0; q < RX; q += 2) {
+                        const float2 vn2 = make_float2(prev[q], prev[q + 1]);
+                        const float2 vs2 = (r < RY - 1) ? make_float2(v[r + 1][q].lo, v[r + 1][q + 1].lo)
+                                                        : make_float2(srow[q], srow[q + 1]);
+                        float2 t;
+                        if (r == 0) t = __ffma2_rn(mn2, vn2, vs2);
+                        else if (r == RY - 1) t = __ffma2_rn(ms2, vs2, vn2);
+                        else t = __fadd2_rn(vn2, vs2);
+                        t = __fadd2_rn(t, make_float2(hsum[q], hsum[q + 1]));
+                        t = __ffma2_rn(make_float2(-4.f, -4.f), make_float2(cur[q], cur[q + 1]), t);
+                        const float2 base = base_is_cur ? make_float2(cur[q], cur[q + 1])
+                                                        : make_float2(v[r][q].hi, v[r][q + 1].hi);
+                        const float2 w2 = last ? __fmul2_rn(cc2, t) : __ffma2_rn(cc2, t, base);
+                        v[r][q].lo = w2.x;
+                        v[r][q + 1].lo = w2.y;
+                    }
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) prev[c] = cur[c];
                 }
-                float cur[RX];
+                if (edge) {
 #pragma unroll
-                for (int c = 0; c < RX; ++c) cur[c] = v[r][c].lo;
-                const float w_in = __shfl_up_sync(kFullMask, cur[RX - 1], 1);
-                const float e_in = __shfl_down_sync(kFullMask, cur[0], 1);
-                float hsum[RX];
-                hsum[0] = fmaf(mw, w_in, cur[1]);
+                    for (int r = 0; r < RY; ++r)
 #pragma unroll
-                for (int c = 1; c < RX - 1; ++c) hsum[c] = cur[c - 1] + cur[c + 1];
-                hsum[RX - 1] = fmaf(me, e_in, cur[RX - 2]);
+                        for (int c = 0; c < RX; ++c)
+                            if (i0 + c >= n || j0 + r >= n) v[r][c].lo = 0.f;
+                }
+                buf ^= 1;
+            };
+            fp32_stage(0, std::true_type{});
+#pragma unroll 1
+            for (int stage = 1; stage < 3; ++stage) fp32_stage(stage, std::false_type{});
+        } else {
+#pragma unroll 1
+            for (int stage = 0; stage < 3; ++stage) {
 #pragma unroll
-                for (int q = 0; q < RX; q += 2) {
-                    const float2 vn2 = make_float2(prev[q], prev[q + 1]);
-                    const float2 vs2 = (r < RY - 1) ? make_float2(v[r + 1][q].lo, v[r + 1][q + 1].lo)
-                                                    : make_float2(srow[q], srow[q + 1]);
-                    float2 t;
-                    if (r == 0) t = __ffma2_rn(mn2, vn2, vs2);
-                    else if (r == RY - 1) t = __ffma2_rn(ms2, vs2, vn2);
-                    else t = __fadd2_rn(vn2, vs2);
-                    t = __fadd2_rn(t, make_float2(hsum[q], hsum[q + 1]));
-                    t = __ffma2_rn(make_float2(-4.f, -4.f), make_float2(cur[q], cur[q + 1]), t);
-                    const float2 w2 = last ? __fmul2_rn(cc2, t)
-                                           : __ffma2_rn(cc2, t, make_float2(v[r][q].hi, v[r][q + 1].hi));
-                    v[r][q].lo = w2.x;
-                    v[r][q + 1].lo = w2.y;
+                for (int q = 0; q < RX; q += 4) {
+                    *reinterpret_cast<float4 *>(frow_w(buf, 0, ty) + i0 + q) =
+                        make_float4(v[0][q].lo, v[0][q + 1].lo, v[0][q + 2].lo, v[0][q + 3].lo);
+                    *reinterpret_cast<float4 *>(frow_w(buf, 1, ty) + i0 + q) =
+                        make_float4(v[RY - 1][q].lo, v[RY - 1][q + 1].lo, v[RY - 1][q + 2].lo,
+                                    v[RY - 1][q + 3].lo);
+                }
+                cluster_or_cta_sync();
+                const float cc = ccs[2 + stage];
+                const float2 cc2 = make_float2(cc, cc);
+                const bool last = (stage == 2);
+                float prev[RX];
+#pragma unroll
+                for (int q = 0; q < RX; q += 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(frow(nbuf, buf, 1, nty) + i0 + q);
+                    prev[q] = t.x;
+                    prev[q + 1] = t.y;
+                    prev[q + 2] = t.z;
+                    prev[q + 3] = t.w;
                 }
 #pragma unroll
-                for (int c = 0; c < RX; ++c) prev[c] = cur[c];
-            }
-            if (edge) {
+                for (int r = 0; r < RY; ++r) {
+                    float srow[RX];
+                    if (r == RY - 1) {
 #pragma unroll
-                for (int r = 0; r < RY; ++r)
+                        for (int q = 0; q < RX; q += 4) {
+                            const float4 t = *reinterpret_cast<const float4 *>(frow(sbuf, buf, 0, sty) + i0 + q);
+                            srow[q] = t.x;
+                            srow[q + 1] = t.y;
+                            srow[q + 2] = t.z;
+                            srow[q + 3] = t.w;
+                        }
+                    }
+                    float cur[RX];
 #pragma unroll
-                    for (int c = 0; c < RX; ++c)
-                        if (i0 + c >= n || j0 + r >= n) v[r][c].lo = 0.f;
+                    for (int c = 0; c < RX; ++c) cur[c] = v[r][c].lo;
+                    const float w_in = __shfl_up_sync(kFullMask, cur[RX - 1], 1);
+                    const float e_in = __shfl_down_sync(kFullMask, cur[0], 1);
+                    float hsum[RX];
+                    hsum[0] = fmaf(mw, w_in, cur[1]);
+#pragma unroll
+                    for (int c = 1; c < RX - 1; ++c) hsum[c] = cur[c - 1] + cur[c + 1];
+                    hsum[RX - 1] = fmaf(me, e_in, cur[RX - 2]);
+#pragma unroll
+                    for (int q = 0; q < RX; q += 2) {
+                        const float2 vn2 = make_float2(prev[q], prev[q + 1]);
+                        const float2 vs2 = (r < RY - 1) ? make_float2(v[r + 1][q].lo, v[r + 1][q + 1].lo)
+                                                        : make_float2(srow[q], srow[q + 1]);
+                        float2 t;
+                        if (r == 0) t = __ffma2_rn(mn2, vn2, vs2);
+                        else if (r == RY - 1) t = __ffma2_rn(ms2, vs2, vn2);
+                        else t = __fadd2_rn(vn2, vs2);
+                        t = __fadd2_rn(t, make_float2(hsum[q], hsum[q + 1]));
+                        t = __ffma2_rn(make_float2(-4.f, -4.f), make_float2(cur[q], cur[q + 1]), t);
+                        const float2 w2 = last ? __fmul2_rn(cc2, t)
+                                               : __ffma2_rn(cc2, t, make_float2(v[r][q].hi, v[r][q + 1].hi));
+                        v[r][q].lo = w2.x;
+                        v[r][q + 1].lo = w2.y;
+                    }
+#pragma unroll
+                    for (int c = 0; c < RX; ++c) prev[c] = cur[c];
+                }
+                if (edge) {
+#pragma unroll
+                    for (int r = 0; r < RY; ++r)
+#pragma unroll
+                        for (int c = 0; c < RX; ++c)
+                            if (i0 + c >= n || j0 + r >= n) v[r][c].lo = 0.f;
+                }
+                buf ^= 1;
             }
-            buf ^= 1;
         }
         // ---- u <- s + q (v.lo holds -q)
 #pragma unroll
@@ -1218,6 +1402,12 @@ pit_status launch_split(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
         a.TY = TY;
         a.C = 1;
         const size_t sm = split_smem<RX, RY, false>(TXp, TYp);
+        if (p->split_fold) {
+            PIT_TRY(smem_limit(k_heat2d_split<RX, RY, false, true>, sm));
+            k_heat2d_split<RX, RY, false, true><<<dim3(nslices, p->batch), TXp * TYp, sm, s>>>(a);
+            PIT_LAUNCH_CHECK();
+            return PIT_OK;
+        }
         PIT_TRY(smem_limit(k_heat2d_split<RX, RY, false>, sm));
         k_heat2d_split<RX, RY, false><<<dim3(nslices, p->batch), TXp * TYp, sm, s>>>(a);
         PIT_LAUNCH_CHECK();
@@ -1231,7 +1421,7 @@ pit_status launch_split(Problem *p, Heat2dArgs a, int nslices, cudaStream_t s) {
     a.TY = (n + RY - 1) / RY;
     a.C = (n + TYp * RY - 1) / (TYp * RY);
     const size_t sm = split_smem<RX, RY, true>(a.TXp, TYp);
-    auto kern = k_heat2d_split<RX, RY, true>;
+    auto kern = p->split_fold ? k_heat2d_split<RX, RY, true, true> : k_heat2d_split<RX, RY, true>;
     PIT_TRY(smem_limit(kern, sm));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nslices * a.C), (unsigned)p->batch);
@@ -1432,6 +1622,12 @@ pit_status heat2d_setup(Problem *p) {
         const char *env = getenv("PIT_HEAT2D_TC");
         p->xform_tc = (p->precision == PIT_MIXED && heat2d_tc_usable(p) && !(env && env[0] == '0')) ? 1 : 0;
         if (p->xform_tc) PIT_TRY(heat2d_tc_setup(p, S.data()));
+    }
+    // split RK4 residual with the low word's first-order term among the FP32
+    // terms (PIT_SPLIT_FOLD=1; off by default)
+    {
+        const char *env = getenv("PIT_SPLIT_FOLD");
+        p->split_fold = (env && env[0] == '1') ? 1 : 0;
     }
     // autotune the fine kernels' variant on this shape: FP32 (inner solves)
     // among one CTA of 4- or 8-column tiles of 8 rows, one CTA of 4 x 4 tiles

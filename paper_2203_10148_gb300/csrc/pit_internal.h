@@ -188,6 +188,7 @@ struct Problem {
     DevBuf S64, S32, gmode;       // gmode: (1 - dTc nu (mu_k + mu_l))^{-c}
     DevBuf xtc_S;                 // TF32 parts (hi, lo) of S for the tensor-core transforms
     int xform_tc = 0;             // 2D / 1D heat sweeps transform on the tensor cores
+    int split_fold = 0;           // 2D heat split RK4 residual: the Z u_lo term among the FP32 terms
     DevBuf hat;                   // sweep scratch: transformed blocks
 
     // advdiff2d: per-point velocities (FP64 and FP32)
