@@ -229,6 +229,25 @@ size_t pit_last_error(char *buf, size_t n);
  *                          pipe instead of the tensor cores;
  *   PIT_HEAT1D_TC=0        mixed 1D heat sweeps as sequential FP32 Thomas
  *                          solves instead of sine transforms on the tensor cores;
+ *   PIT_HEAT1D_SMALL=cta   1D heat grids of M <= 256 on the CTA-wide scans
+ *                          instead of the one-warp kernels;
+ *   PIT_HEAT1D_PHI=0       FP64 1D heat fine batch by its m implicit-Euler
+ *                          steps instead of one product with the stored
+ *                          propagator matrix A^-m (small grids);
+ *   PIT_HEAT1D_POW=0       FP64 1D heat sweep as N dependent coarse solves
+ *                          instead of the independent products with stored
+ *                          powers of G (small grids, N <= 128);
+ *   PIT_SPLIT_FOLD=1       2D heat split RK4 residual with the low word's
+ *                          first-order term among the FP32 terms (off by
+ *                          default: not yet run on a GPU);
+ *   PIT_ADV_COEF32=0       ADVDIFF2D float-float stages keep the velocity
+ *                          coefficients' low parts even when all are FP32 values;
+ *   PIT_ADV_RX=8           ADVDIFF2D fine kernels on 8 x 8 thread tiles for
+ *                          n >= 256 (default 8 x 4);
+ *   PIT_DENSE_OZ=0         DENSE true residual by the float-float product
+ *                          instead of error-free splitting on the tensor cores;
+ *   PIT_DENSE_SWEEP_TC=0   DENSE sweep on the CUDA cores instead of the
+ *                          tensor-core chunked scan;
  *   PIT_HEAT2D_VARIANTS=a,b  2D heat fine-kernel variants for n <= 128 (FP32
  *                          a in 0..3, float-float b in {0, 2}) instead of the
  *                          autotuner's choice (bit-identical results);

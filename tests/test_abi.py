@@ -37,6 +37,20 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(pit.EXPORTS) <= set(declared)
 
 
+def test_every_environment_switch_is_documented():
+    """Each environment variable the library reads is listed in the public
+    header with its meaning."""
+    csrc = os.path.join(ROOT, "paper_2203_10148_gb300", "csrc")
+    names = set()
+    for f in os.listdir(csrc):
+        if f.endswith((".cu", ".cuh", ".h")):
+            names |= set(re.findall(r'getenv\("([A-Z0-9_]+)"\)', open(os.path.join(csrc, f)).read()))
+    assert names, "no getenv found"
+    header = "".join(open(os.path.join(ROOT, "include", h)).read()
+                     for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h"))
+    assert sorted(n for n in names if n not in header) == []
+
+
 def test_version_and_defaults(lib):
     from paper_2203_10148_gb300 import pit
     assert b"sm_103a" in lib.pit_version()
