@@ -187,33 +187,49 @@ def _torch_stream(x, stream):
     return torch.cuda.current_stream(x.device).cuda_stream
 
 
-def _array_arg(x) -> Tuple[int, int, object]:
-    """(pointer, on_device, keepalive) for a numpy array or a CUDA torch tensor."""
+def _array_arg(x, n: Optional[int] = None) -> Tuple[int, int, object]:
+    """(pointer, on_device, keepalive) for a numpy array or a CUDA torch
+    tensor.  With n, the array must hold exactly n values: the library reads
+    or writes that many through the pointer, so a shorter array would be
+    accessed out of bounds."""
     if isinstance(x, np.ndarray):
         if x.dtype != np.float64 or not x.flags.c_contiguous:
             raise ValueError("host arrays must be C-contiguous float64")
-        return x.ctypes.data, 0, x
-    import torch  # device memory only
-    if isinstance(x, torch.Tensor):
+        out, size = (x.ctypes.data, 0, x), x.size
+    else:
+        import torch  # device memory only
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"unsupported array type {type(x)}")
         if x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda:
             raise ValueError("device tensors must be contiguous CUDA float64")
-        return x.data_ptr(), 1, x
-    raise TypeError(f"unsupported array type {type(x)}")
+        out, size = (x.data_ptr(), 1, x), x.numel()
+    if n is not None and size != n:
+        raise ValueError(f"expected an array of {n} values, got {size}")
+    return out
+
+
+def _host_values(a, n: int, what: str) -> np.ndarray:
+    """a as a C-contiguous float64 host array of exactly n values."""
+    v = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    if v.size != n:
+        raise ValueError(f"{what}: expected {n} values, got {v.size}")
+    return v
 
 
 def problem_desc(w, precision: int) -> Tuple[ProblemDesc, list]:
     """pit_problem_desc of a workload, and the arrays it points into."""
     keep = []
-    y0 = np.ascontiguousarray(np.asarray(w.y0, dtype=np.float64).reshape(-1))
+    M = int(w.nx) * int(w.ny)
+    y0 = _host_values(w.y0, int(w.batch) * M, "y0")
     keep.append(y0)
     op = OperatorDesc(PIT_OP[w.kind], w.nx, w.ny, float(w.nu), None, None, None)
     if w.kind == "advdiff2d":
-        vx = np.ascontiguousarray(w.vx, dtype=np.float64)
-        vy = np.ascontiguousarray(w.vy, dtype=np.float64)
+        vx = _host_values(w.vx, M, "vx")
+        vy = _host_values(w.vy, M, "vy")
         keep += [vx, vy]
         op.vx, op.vy = _dptr(vx), _dptr(vy)
     if w.kind == "dense":
-        A = np.ascontiguousarray(w.A, dtype=np.float64)
+        A = _host_values(w.A, M * M, "A")
         keep.append(A)
         op.A = _dptr(A)
     desc = ProblemDesc(op, _dptr(y0), int(w.batch), float(w.T), int(w.N),
@@ -284,8 +300,9 @@ class Problem:
         """pit_apply_operator: which in {'F', 'Ginv', 'GinvF', 'residual'}."""
         prec = self.precision if precision is None else PRECISION[precision]
         y = self._out_like(x) if out is None else out
-        px, dev, _ = _array_arg(x)
-        py, dev2, _ = _array_arg(y)
+        n = self.batch * (self.N + 1) * self.M
+        px, dev, _ = _array_arg(x, n)
+        py, dev2, _ = _array_arg(y, n)
         if dev != dev2:
             raise ValueError("x and y must both be host or both be device arrays")
         check(load().pit_apply_operator(self.handle, APPLY[which], prec, px, py, dev,
@@ -295,7 +312,7 @@ class Problem:
     def serial_fine(self, precision: Optional[str] = None, out=None):
         prec = self.precision if precision is None else PRECISION[precision]
         y = np.empty(self.shape, dtype=np.float64) if out is None else out
-        py, dev, _ = _array_arg(y)
+        py, dev, _ = _array_arg(y, self.batch * (self.N + 1) * self.M)
         check(load().pit_serial_fine(self.handle, prec, py, dev))
         return y
 
@@ -315,7 +332,7 @@ class Problem:
             opts.history_len = history_len
         if X is None:
             X = np.zeros(self.shape)
-        px, dev, _ = _array_arg(X)
+        px, dev, _ = _array_arg(X, self.batch * (self.N + 1) * self.M)
         opts.stream = _torch_stream(X, stream)
         infos = (SolveInfo * self.batch)()
         st = lib.pit_bicgstab_solve(self.handle, C.byref(opts), px, dev, infos)
@@ -328,7 +345,7 @@ class Problem:
 
     def set_y0(self, y0):
         """pit_problem_set_y0: new initial values (batch x M), host or device."""
-        p, dev, _ = _array_arg(y0)
+        p, dev, _ = _array_arg(y0, self.batch * self.M)
         check(load().pit_problem_set_y0(self.handle, p, dev))
 
     def set_source(self, f):
@@ -336,7 +353,7 @@ class Problem:
         if f is None:
             check(load().pit_problem_set_source(self.handle, None, 0))
             return
-        p, dev, _ = _array_arg(f)
+        p, dev, _ = _array_arg(f, self.batch * self.M)
         check(load().pit_problem_set_source(self.handle, p, dev))
 
     def set_timing(self, enable=True):
@@ -358,7 +375,7 @@ class Problem:
         lib = load()
         if X is None:
             X = np.zeros(self.shape)
-        px, dev, _ = _array_arg(X)
+        px, dev, _ = _array_arg(X, self.batch * (self.N + 1) * self.M)
         infos = (SolveInfo * self.batch)()
         st = lib.pit_parareal_solve(self.handle, int(kmax), float(tol), px, dev, infos)
         if st in (PIT_E_INVALID, PIT_E_NOMEM, PIT_E_CUDA, PIT_E_UNSUPPORTED):
@@ -458,8 +475,8 @@ def block_reduce(U, V, nblocks: int, M: int, noalloc: bool = False):
     """pit_block_reduce (or pit_block_reduce_noalloc) on CUDA tensors:
     (dot, per-block norms, max block norm)."""
     import torch
-    pu, du, _ = _array_arg(U)
-    pv, dv, _ = _array_arg(V)
+    pu, du, _ = _array_arg(U, nblocks * M)
+    pv, dv, _ = _array_arg(V, nblocks * M)
     if not (du and dv):
         raise ValueError("pit_block_reduce takes device tensors")
     out = torch.zeros(2 + nblocks, dtype=torch.float64, device=U.device)

@@ -107,8 +107,7 @@ def test_serve_footprint_is_host_only_and_monotone(lib):
     base.N *= 2
     assert f(base) > b1
     w2 = inputs.heat2d(n=32, N=16)
-    w1 = inputs.heat1d()
-    w1.nx, w1.N = 1024, 16
+    w1 = inputs.heat1d(M=1024, N=16)
     # the 2D sweep's sine-mode work makes a 2D request larger than a 1D one of equal size
     assert f(w2) > f(w1)
     # eight Krylov block vectors at least
@@ -150,6 +149,33 @@ def test_bench_matrix_label_agrees_with_the_library(lib, M, m):
     stored = pit.serve_footprint(w) - pit.serve_footprint(one)
     assert stored in (0, 8 * M * M)
     assert bench.heat1d_uses_matrix(w) == (stored == 8 * M * M)
+
+
+def test_binding_rejects_arrays_of_the_wrong_size():
+    """The library reads or writes a fixed number of values through each
+    array pointer; the binding refuses arrays of another size before any call
+    (a short array would be accessed out of bounds)."""
+    from paper_2203_10148_gb300 import inputs, pit
+    assert pit._array_arg(np.zeros(6), 6)[1] == 0
+    with pytest.raises(ValueError):
+        pit._array_arg(np.zeros(5), 6)
+    with pytest.raises(ValueError):
+        pit._array_arg(np.zeros(6, dtype=np.float32), 6)
+    with pytest.raises(ValueError):
+        pit._array_arg(np.zeros((3, 4)).T, 12)          # not C-contiguous
+    w = inputs.heat1d(M=10, N=3, batch=2)
+    pit.problem_desc(w, pit.PIT_FP64)
+    w.y0 = w.y0[:, :9]                                  # rows of 9 values, M = 10
+    with pytest.raises(ValueError):
+        pit.problem_desc(w, pit.PIT_FP64)
+    d = inputs.dense(M=12, N=2, T=0.1)
+    d.A = d.A[:, :11]
+    with pytest.raises(ValueError):
+        pit.problem_desc(d, pit.PIT_FP64)
+    a = inputs.advdiff2d(n=8, N=2)
+    a.vx = a.vx.reshape(-1)[:-1]
+    with pytest.raises(ValueError):
+        pit.problem_desc(a, pit.PIT_FP64)
 
 
 def test_server_calls_reject_null_handles(lib):
