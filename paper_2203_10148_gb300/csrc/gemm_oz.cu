@@ -18,15 +18,17 @@
 // Slice i holds d_i 2^(-i b), a BF16 value exactly.
 //
 // Exactness: the products of slices i and j are integer multiples of
-// 2^(-(i+j) b); over one anti-diagonal s = i + j and k < K their sum is
-// below K 2^(2b - 2) (s + 1) such units (the two end pairs with the leading
-// digit and s - 3 inner pairs), so with b = 6, K <= 1024 and s <= 15 it
-// stays below 2^24 units: the tensor core's FP32 accumulation of a whole
-// diagonal (every pair, every K step) is exact, whatever order it adds in.
+// 2^(-(i+j) b); over one anti-diagonal s = i + j and k < K their absolute
+// sum is at most K 2^(2b - 2) max(s + 1, 4) such units (the two end pairs
+// with the leading digit and s - 3 inner pairs; for s = 2 the one pair of
+// leading digits), so with b = 6, K <= 1024 and the diagonals formed
+// (s <= 8) it stays below 2^24 units: the tensor core's FP32 accumulation of
+// a whole diagonal (every pair, every K step) is exact, whatever order it
+// adds in.
 // The S diagonal sums (s = 2 .. S + 1) are added in float-float, scaled by
 // 2^(E_g + F_c) and written as FP64 block-operator rows of eq. (4).  Pairs
 // beyond the last diagonal are not formed; with S = 7 the result is within
-// about 2^-42 of sum_k |x_gk| |phi_ck| (relative to the row maxima).
+// about 2^-42 of K max_k |x_gk| max_k |phi_ck| (the rows' maxima).
 //
 // Kernel: persistent, one CTA per SM over 128 x 64 output tiles.  For slice
 // i of X, each 64-wide K stage brings X_i's tile and the tiles of the S - i
