@@ -448,7 +448,9 @@ pit_status pit_serve_poll(pit_server_t server, uint64_t ticket, double *X_out,
                           pit_solve_info *info);
 
 /* pit_serve_poll that blocks until the request is done or timeout_s seconds
- * have passed (PIT_PENDING); timeout_s < 0 waits without limit. */
+ * have passed (PIT_PENDING); timeout_s < 0 waits without limit.  Where
+ * several callers wait on one ticket, the first to wake takes the result and
+ * the others return PIT_E_INVALID. */
 pit_status pit_serve_wait(pit_server_t server, uint64_t ticket, double timeout_s,
                           double *X_out, pit_solve_info *info);
 

@@ -422,14 +422,23 @@ pit_status pit_serve_wait(pit_server_t s, uint64_t ticket, double timeout_s, dou
         set_error("pit_serve_wait: unknown ticket (never issued, or already taken)");
         return PIT_E_INVALID;
     }
-    Request *r = it->second.get();
-    auto done = [&] { return r->state == DONE; };
+    // the request is looked up again after every wake-up: another thread
+    // waiting on the same ticket may have taken (and released) it meanwhile
+    auto done = [&] {
+        auto jt = s->reqs.find(ticket);
+        return jt == s->reqs.end() || jt->second->state == DONE;
+    };
     if (timeout_s < 0) {
         s->cv_done.wait(lk, done);
     } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done)) {
         return PIT_PENDING;
     }
-    return take_locked(s, r, X_out, info);
+    it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        set_error("pit_serve_wait: the result was taken by another caller");
+        return PIT_E_INVALID;
+    }
+    return take_locked(s, it->second.get(), X_out, info);
 }
 
 pit_status pit_serve_cancel(pit_server_t s, uint64_t ticket) {
